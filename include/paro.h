@@ -1,0 +1,204 @@
+/*
+ * paro.h -- C ABI of libparo, a GB300 (sm_103a) implementation of the data-parallel hot path of the
+ * parallel orbital-updating (ParO) plane-wave method for Kohn-Sham DFT (Pan, Dai, de Gironcoli, Gong,
+ * Rignanese, Zhou, arXiv:1702.04045).
+ *
+ * Conventions for every call:
+ *   - Hartree atomic units (Section 2.1). A cutoff given in Ry is converted by the caller (1 Ry = 0.5 Ha).
+ *   - Every function returns a paro_status (0 = PARO_OK, < 0 = error) and never aborts or exits; the
+ *     message of the last error is returned by paro_last_error().
+ *   - Complex arrays are interleaved (re, im). Orbital blocks are row-major "band x plane wave": row b
+ *     holds the npw coefficients c_{b,k+G} of band b in the basis order reported by paro_miller().
+ *   - The caller owns every array argument; the library copies what it keeps. The library owns the
+ *     context and all of its device buffers. Device pointers must stay valid for the duration of the
+ *     call. All GPU work is enqueued on the context's stream; calls that return host data synchronise.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ *   - There is no CPU fallback: every numerical step runs in this library's CUDA kernels.
+ */
+#ifndef PARO_H
+#define PARO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct paro_ctx paro_ctx;
+
+typedef enum {
+  PARO_OK = 0,
+  PARO_ERR_ARG = -1,           /* bad size, index, pointer or unsupported configuration */
+  PARO_ERR_CUDA = -2,          /* a CUDA call failed; the message holds cudaGetErrorString */
+  PARO_ERR_BREAKDOWN = -3,     /* PCG p^H A p <= 0 or NaN, or a Cholesky pivot <= 0 */
+  PARO_ERR_NOT_CONVERGED = -4, /* SCF / ParO iteration limit reached; the last state is kept */
+  PARO_ERR_STATE = -6          /* call out of order (e.g. no potential or orbitals set yet) */
+} paro_status;
+
+typedef enum { PARO_FP64 = 0, PARO_MIXED = 1 } paro_precision;
+typedef enum { PARO_ALG1 = 1, PARO_ALG2 = 2 } paro_algorithm;
+typedef enum { PARO_C64 = 0, PARO_C32 = 1 } paro_dtype; /* complex double / complex float */
+
+/* Energy terms reported by paro_energy / paro_scf (Ha): indices into a double[7]. */
+enum {
+  PARO_E_KINETIC = 0, PARO_E_NONLOCAL = 1, PARO_E_LOCAL = 2, PARO_E_HARTREE = 3,
+  PARO_E_XC = 4, PARO_E_EWALD = 5, PARO_E_TOTAL = 6
+};
+
+/*
+ * paro_create -- cell, cutoff, k-points and band counts (Section 2.2; Eq. e2, Eq. e3).
+ *   lattice   host double[9], rows a1, a2, a3 in Bohr.
+ *   pos       host double[n_atoms*3], Cartesian positions in Bohr.
+ *   ecut_ha   kinetic cutoff: the basis of k is { G : |k+G|^2/2 <= ecut_ha } (Eq. e3), stored in
+ *             lexicographic Miller order (n1, n2, n3).
+ *   k_frac    host double[n_k*3], k in reduced coordinates of the reciprocal lattice (NULL: Gamma only,
+ *             n_k must be 1); k_w host double[n_k], weights summing to 1 (NULL: 1/n_k each).
+ *   n_bands   orbitals per k (occupied + extra); n_occ the occupied ones (occupation 2 each).
+ *   precision PARO_FP64: every step in FP64. PARO_MIXED: FFTs, V.psi, the KB projector GEMMs and
+ *             the inner PCG in FP32 (dot products accumulated in FP64); Gram, Cholesky, Rayleigh-Ritz,
+ *             residual norms and energies in FP64.
+ *   stream    cudaStream_t to enqueue on, or NULL for a stream owned by the context.
+ * The FFT grid is the smallest 2^a 3^b per axis with N_i > m_V,i + s_psi,i (m_V: largest |n_i| of the
+ * density sphere |G|^2/2 <= 4 ecut; s_psi: span of n_i over every k's basis), so that V.psi is alias
+ * free. Errors: PARO_ERR_ARG for non-positive sizes, singular lattice, n_occ > n_bands, n_bands > npw.
+ */
+int paro_create(paro_ctx** out, const double lattice[9], int n_atoms, const double* pos, double ecut_ha,
+                int n_k, const double* k_frac, const double* k_w, int n_bands, int n_occ, int precision,
+                void* stream);
+
+/*
+ * paro_set_local_pp -- local pseudopotential v(r) = -Z erf(r/rc)/r + A exp(-(r/a)^2) on every atom
+ * (Section 2.2, V_loc). V_loc(G) = Omega^{-1} sum_I exp(-i G.R_I) v(G) on the density sphere, with the
+ * divergent -4 pi Z/G^2 dropped at G = 0; V_loc(r) by an inverse 3D FFT on the grid. Also sets
+ * V_eff = V_loc (a fixed potential) until paro_set_veff / paro_set_density / paro_scf replace it.
+ * The ion charge Z also enters the Ewald energy.
+ */
+int paro_set_local_pp(paro_ctx* ctx, double Z, double rc, double A, double a);
+
+/*
+ * paro_set_kb -- Kleinman-Bylander nonlocal part V_nl = sum_{I,j} |beta_Ij> D_{I,l(j)} <beta_Ij|
+ * (Section 2.2, V_nl) with four Gaussian projectors per atom (s, px, py, pz), radius rc (Bohr):
+ * beta_Ij(k+G) = Omega^{-1/2} exp(-i(k+G).R_I) p~_j(k+G), p~_s = N0 pi^{3/2} rc^3 exp(-q^2 rc^2/4),
+ * p~_x = -i N1 (pi^{3/2} rc^5/2) q_x exp(-q^2 rc^2/4), normalised to int p^2 = 1.
+ *   D  host double[n_atoms*2]: strength (Ha) of the s and of the p channel of each atom.
+ */
+int paro_set_kb(paro_ctx* ctx, double rc, const double* D);
+
+/* paro_set_veff -- fixed effective potential V_eff(r) (Ha) on the grid, C order (N1, N2, N3);
+ * host (on_device = 0) or device (on_device = 1) double[N1*N2*N3]. */
+int paro_set_veff(paro_ctx* ctx, const double* v_r, int on_device);
+/* paro_get_veff -- copy the current V_eff(r) to a host double[N1*N2*N3]. */
+int paro_get_veff(paro_ctx* ctx, double* v_r);
+
+/* paro_set_density -- V_eff = V_loc + V_H[rho] + V_xc[rho] from a density rho(r) (electrons/Bohr^3,
+ * C order, host or device double[N1*N2*N3]): Hartree V_H(G) = 4 pi rho(G)/G^2 (G != 0), LDA
+ * Perdew-Zunger exchange-correlation (Section 2.1, V_H and V_xc). Also becomes the SCF input density. */
+int paro_set_density(paro_ctx* ctx, const double* rho, int on_device);
+
+/* Queries: FFT grid, plane-wave count of k-point ik, Miller indices (host int[npw*3]) of its basis,
+ * the PCG shift sigma of the current potential (see paro_solve_source). */
+int paro_grid(const paro_ctx* ctx, int n[3]);
+int paro_npw(const paro_ctx* ctx, int ik, int* npw);
+int paro_miller(const paro_ctx* ctx, int ik, int* hkl);
+int paro_sigma(const paro_ctx* ctx, double* sigma);
+
+/*
+ * paro_apply_h -- H psi for nb orbitals of k-point ik (Eq. e5, with the potential term read as
+ * exp(-i(G_m - G_n).r) and the nonlocal term added):
+ *   (H psi)(G) = |k+G|^2/2 c_G + [FFT(V_eff . IFFT(c))](G) / N_grid + sum_p beta_p(G) D_p <beta_p|c>.
+ *   dtype  PARO_C64 (complex double) or PARO_C32 (complex float): the arithmetic of the whole apply.
+ *   psi    device, nb x npw complex of dtype; hpsi device, same shape (must not alias psi).
+ */
+int paro_apply_h(paro_ctx* ctx, int ik, int nb, int dtype, const void* psi, void* hpsi);
+
+/*
+ * paro_solve_source -- the independent source problems of Algorithm 1, step 3, for nb orbitals:
+ * a(rho; x_i, phi) = (eps_i psi_i, phi), solved shifted as (H - sigma) x_i = (eps_i - sigma) psi_i by
+ * batched preconditioned CG started at x_i = psi_i. sigma is a rigorous lower bound of the spectrum
+ * minus 0.5 Ha (min V_eff plus the attractive KB channels), so H - sigma is positive definite; the
+ * preconditioner is diag(|k+G|^2/2 + mean V_eff - sigma)^{-1}. Each orbital stops once its residual
+ * has dropped by rel_tol, or after max_it steps.
+ *   eps host double[nb]; psi, x device nb x npw of dtype; iters_out host int[nb] or NULL.
+ * Errors: PARO_ERR_BREAKDOWN if p^H A p <= 0 or is not finite for an active orbital.
+ */
+int paro_solve_source(paro_ctx* ctx, int ik, int nb, int dtype, const double* eps, const void* psi, void* x,
+                      double rel_tol, int max_it, int* iters_out);
+
+/*
+ * paro_set_orbitals -- start vectors of k-point ik (Algorithm 1, step 1): n_bands x npw complex double,
+ * host or device. The library orthonormalises them (Cholesky of the Gram matrix, band order) and takes
+ * the Ritz pairs of their span under the current potential.
+ * paro_get_orbitals -- current orbitals of ik (orthonormal, FP64 complex n_bands x npw), host or device.
+ * paro_get_eigenvalues -- current Ritz values, host double[n_k * n_bands], ascending per k.
+ * paro_get_residuals -- ||H psi_i - eps_i psi_i||_2 of the current orbitals, host double[n_k * n_bands].
+ */
+int paro_set_orbitals(paro_ctx* ctx, int ik, const void* psi, int on_device);
+int paro_get_orbitals(paro_ctx* ctx, int ik, void* psi, int on_device);
+int paro_get_eigenvalues(paro_ctx* ctx, double* eps);
+int paro_get_residuals(paro_ctx* ctx, double* res);
+
+/*
+ * paro_step -- one ParO iteration at the fixed current potential, for every k-point:
+ *   PARO_ALG1 (Algorithm 1): source problems (H - sigma) x_i = (eps_i - sigma) psi_i, Cholesky
+ *     orthonormalisation of X, Rayleigh-Ritz in span{x_i}: H_sub = X^H H X, H_sub C = C diag(eps).
+ *   PARO_ALG2 (Algorithm 2): corrections (H - sigma) e_i = -(H psi_i - eps_i psi_i) started at e = 0,
+ *     projected out of span{psi}; Rayleigh-Ritz in span{psi, e} (dimension up to 2 n_bands).
+ *   rel_tol, max_it: inner PCG stopping rule (see paro_solve_source).
+ *   max_resid_out: host, max over k and occupied bands of ||H psi_i - eps_i psi_i|| after the step.
+ */
+int paro_step(paro_ctx* ctx, int alg, double rel_tol, int max_it, double* max_resid_out);
+
+/*
+ * paro_eigh -- Hermitian eigensolver used by the Rayleigh-Ritz step (one CTA, FP64): Householder
+ * tridiagonalisation, implicit-shift QL, back-transformation.
+ *   a  device n x n complex double, row-major, Hermitian (the lower triangle is read); w device double[n]
+ *   ascending eigenvalues; v device n x n complex double, column j = eigenvector j (row-major storage).
+ */
+int paro_eigh(paro_ctx* ctx, int n, const void* a, double* w, void* v);
+
+/* paro_density -- rho(r) = sum_k w_k sum_{i<n_occ} 2 |psi_ik(r)|^2 of the current orbitals
+ * (Section 2.1 and Section 2.2, k-point sum), device double[N1*N2*N3], C order. */
+int paro_density(paro_ctx* ctx, double* rho_dev);
+
+/* paro_energy -- total energy of the current orbitals and their density (terms as PARO_E_*):
+ * sum f <psi|T + V_nl|psi> + int V_loc rho + E_H + E_xc + E_Ewald (point ions, neutralising background). */
+int paro_energy(paro_ctx* ctx, double terms[7]);
+
+typedef struct {
+  int alg;                 /* PARO_ALG1 or PARO_ALG2 */
+  double tol_per_atom;     /* stop when |E^{n+1} - E^n| / n_atoms < tol on two consecutive iterations */
+  int max_iter;            /* ParO/SCF iterations */
+  double inner_rel_tol;    /* PCG residual reduction per source problem */
+  int inner_max_it;        /* PCG steps per source problem */
+  int pulay_depth;         /* Pulay history length (<= 16) */
+  double pulay_beta;       /* Pulay mixing parameter */
+} paro_scf_opts;
+
+typedef struct {
+  int n_iter;
+  int converged;
+  double energy[7];
+  double max_resid;
+} paro_scf_result;
+
+/*
+ * paro_scf_step -- one SCF iteration merged with one ParO iteration (Section 2.3, Algorithm 1):
+ * V^n from rho_in^n drives the source problems; the density of the Cholesky-orthonormalised solutions
+ * is Pulay-mixed into rho_in^{n+1/2}, whose potential drives the Rayleigh-Ritz step; energy terms of
+ * the new orbitals are returned (host double[7]). The first call starts from the uniform density.
+ * paro_scf -- iterate paro_scf_step until the energy criterion of opts holds (PARO_ERR_NOT_CONVERGED
+ * after max_iter, with the last state kept).
+ */
+int paro_scf_step(paro_ctx* ctx, const paro_scf_opts* opts, double energy[7], double* max_resid_out);
+int paro_scf(paro_ctx* ctx, const paro_scf_opts* opts, paro_scf_result* result);
+
+/* paro_last_error -- message of the last failed call on ctx (or of the last failed paro_create when
+ * ctx is NULL); valid until the next call on the same context. */
+const char* paro_last_error(const paro_ctx* ctx);
+
+/* paro_destroy -- free the context and all of its device memory (NULL is accepted). */
+void paro_destroy(paro_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PARO_H */

@@ -1,0 +1,813 @@
+// libparo C ABI (include/paro.h): context setup and the ParO / SCF drivers that sequence the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/paro.h"
+#include "paro_ctx.h"
+
+struct paro_ctx {
+  paro::Ctx c;
+};
+
+namespace paro {
+
+static thread_local std::string g_create_err;
+static const double kPi = 3.14159265358979323846;
+
+int fail(Ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(Ctx* c, cudaError_t e, const char* where) {
+  return fail(c, PARO_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+void* ws_get(Ctx* c, const char* name, size_t bytes) {
+  auto it = c->ws.find(name);
+  if (it != c->ws.end() && it->second.second >= bytes) return it->second.first;
+  if (it != c->ws.end()) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(it->second.first);
+    c->ws.erase(it);
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes > 0 ? bytes : 16);
+  if (e != cudaSuccess) {
+    cuda_fail(c, e, "workspace allocation");
+    return nullptr;
+  }
+  c->ws[name] = std::make_pair(p, bytes);
+  return p;
+}
+
+// ------------------------------------------------------------------------------------------------
+// setup helpers
+// ------------------------------------------------------------------------------------------------
+static int smooth23_above(int m) {
+  for (int x = m + 1;; ++x) {
+    int y = x;
+    while (y % 2 == 0) y /= 2;
+    while (y % 3 == 0) y /= 3;
+    if (y == 1) return x;
+  }
+}
+
+static FftPlan make_plan(int n) {
+  FftPlan p;
+  p.n = n;
+  p.nst = 0;
+  int e2 = 0, e3 = 0, y = n;
+  while (y % 2 == 0) { y /= 2; ++e2; }
+  while (y % 3 == 0) { y /= 3; ++e3; }
+  int n8 = e2 / 3, rem = e2 % 3;
+  std::vector<int> r;
+  if (rem == 1 && n8 > 0) { --n8; r.push_back(4); r.push_back(4); rem = 0; }
+  for (int i = 0; i < n8; ++i) r.insert(r.begin(), 8);
+  if (rem == 2) r.push_back(4);
+  if (rem == 1) r.push_back(2);
+  for (int i = 0; i < e3; ++i) r.push_back(3);
+  for (size_t i = 0; i < r.size() && i < 8; ++i) p.rad[p.nst++] = r[i];
+  return p;
+}
+
+// Miller indices with |k+G|^2/2 <= ecut, lexicographic (n1, n2, n3); kinetic energies.
+static void sphere(const Ctx* c, const double kf[3], double ecut, std::vector<int>& mil, std::vector<double>& kin) {
+  const double* B = c->bmat;
+  double kc[3];
+  for (int x = 0; x < 3; ++x) kc[x] = kf[0] * B[x] + kf[1] * B[3 + x] + kf[2] * B[6 + x];
+  const double gmax = std::sqrt(2.0 * ecut);
+  int lim[3];
+  for (int i = 0; i < 3; ++i) {
+    const double* a = c->lat + 3 * i;
+    const double len = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    lim[i] = (int)std::floor(gmax * len / (2 * kPi) + std::fabs(kf[i])) + 1;
+  }
+  mil.clear();
+  kin.clear();
+  for (int n1 = -lim[0]; n1 <= lim[0]; ++n1)
+    for (int n2 = -lim[1]; n2 <= lim[1]; ++n2)
+      for (int n3 = -lim[2]; n3 <= lim[2]; ++n3) {
+        double q[3];
+        for (int x = 0; x < 3; ++x) q[x] = kc[x] + (n1 * B[x] + n2 * B[3 + x] + n3 * B[6 + x]);
+        const double e = 0.5 * (q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+        if (e <= ecut) {
+          mil.push_back(n1);
+          mil.push_back(n2);
+          mil.push_back(n3);
+          kin.push_back(e);
+        }
+      }
+}
+
+template <typename T>
+static int upload(Ctx* c, T** d, const std::vector<T>& h) {
+  PARO_CU(c, cudaMalloc(d, std::max<size_t>(h.size(), 1) * sizeof(T)));
+  if (!h.empty()) PARO_CU(c, cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return PARO_OK;
+}
+
+static int build_basis(Ctx* c, Basis& b) {
+  std::vector<int>& mil = b.miller;
+  sphere(c, b.kfrac, c->ecut, mil, b.kin);
+  b.npw = (int)b.kin.size();
+  std::vector<int> col_x, col_y, col_off, g_col(b.npw), g_z(b.npw);
+  for (int g = 0; g < b.npw; ++g) {
+    const int n1 = mil[3 * g], n2 = mil[3 * g + 1], n3 = mil[3 * g + 2];
+    if (g == 0 || n1 != mil[3 * (g - 1)] || n2 != mil[3 * (g - 1) + 1]) {
+      col_x.push_back(((n1 % c->N[0]) + c->N[0]) % c->N[0]);
+      col_y.push_back(((n2 % c->N[1]) + c->N[1]) % c->N[1]);
+      col_off.push_back(g);
+    }
+    g_col[g] = (int)col_x.size() - 1;
+    g_z[g] = ((n3 % c->N[2]) + c->N[2]) % c->N[2];
+  }
+  b.ncol = (int)col_x.size();
+  col_off.push_back(b.npw);
+  std::vector<int> xr(col_x);
+  std::sort(xr.begin(), xr.end());
+  xr.erase(std::unique(xr.begin(), xr.end()), xr.end());
+  b.nxr = (int)xr.size();
+  std::vector<float> kin32(b.kin.begin(), b.kin.end());
+  int st;
+  if ((st = upload(c, &b.d_miller, mil)) || (st = upload(c, &b.d_kin, b.kin)) || (st = upload(c, &b.d_kin32, kin32)) ||
+      (st = upload(c, &b.d_col_x, col_x)) || (st = upload(c, &b.d_col_y, col_y)) ||
+      (st = upload(c, &b.d_col_off, col_off)) || (st = upload(c, &b.d_g_col, g_col)) ||
+      (st = upload(c, &b.d_g_z, g_z)) || (st = upload(c, &b.d_xrows, xr)))
+    return st;
+  return PARO_OK;
+}
+
+static void update_sigma(Ctx* c) {
+  c->sigma_k.assign(c->nk, 0.0);
+  for (int ik = 0; ik < c->nk; ++ik) {
+    double lb = c->vmin;
+    if (c->have_kb)
+      for (int I = 0; I < c->nat; ++I) {
+        const double* m = &c->beta_norm2_max[((size_t)ik * c->nat + I) * 2];
+        if (c->D[2 * I] < 0) lb += c->D[2 * I] * m[0];
+        if (c->D[2 * I + 1] < 0) lb += c->D[2 * I + 1] * 3.0 * m[1];
+      }
+    c->sigma_k[ik] = lb - 0.5;
+  }
+}
+
+static int alloc_orbitals(Ctx* c, Basis& b) {
+  if (!b.d_psi) {
+    PARO_CU(c, cudaMalloc(&b.d_psi, (size_t)c->nb * b.npw * sizeof(double2)));
+    PARO_CU(c, cudaMalloc(&b.d_hpsi, (size_t)c->nb * b.npw * sizeof(double2)));
+  }
+  return PARO_OK;
+}
+
+__global__ void k_hermitize(int n, double2* __restrict__ a) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int i = idx / n, j = idx - i * n;
+  if (i < j) return;
+  const double2 lo = a[(size_t)i * n + j], up = a[(size_t)j * n + i];
+  const double2 h = make_double2(0.5 * (lo.x + up.x), 0.5 * (lo.y - up.y));
+  a[(size_t)i * n + j] = h;
+  a[(size_t)j * n + i] = make_double2(h.x, -h.y);
+}
+
+// Orthonormalise the nx rows of X (FP64, in place as Y = conj(L)^{-1} X) and take the Ritz pairs of
+// their span: H_sub = Y^H H Y, H_sub C = C diag(eps); psi = first nb rows of C^T Y, H psi = C^T (H Y).
+// Mixed precision applies H in FP32 (Y rounded to FP32) and keeps every reduction in FP64.
+static int project(Ctx* c, int ik, double2* X, int nx) {
+  Basis& b = c->bases[ik];
+  const int npw = b.npw, nb = c->nb;
+  double2* S = static_cast<double2*>(ws_get(c, "proj_S", (size_t)nx * nx * sizeof(double2)));
+  double2* G = static_cast<double2*>(ws_get(c, "proj_G", (size_t)nx * nx * sizeof(double2)));
+  double2* Y = static_cast<double2*>(ws_get(c, "proj_Y", (size_t)nx * npw * sizeof(double2)));
+  double2* HY = static_cast<double2*>(ws_get(c, "proj_HY", (size_t)nx * npw * sizeof(double2)));
+  double* w = static_cast<double*>(ws_get(c, "proj_w", (size_t)nx * sizeof(double)));
+  double* res = static_cast<double*>(ws_get(c, "proj_res", (size_t)nx * sizeof(double)));
+  if (!S || !G || !Y || !HY || !w || !res) return PARO_ERR_CUDA;
+  int st;
+  if ((st = gemm_cn<double, double, double>(c, nx, nx, npw, X, npw, X, npw, S, nx, true))) return st;
+  if ((st = chol_inv(c, nx, S, G))) return st;
+  if ((st = gemm_wx<double, double>(c, nx, npw, nx, G, nx, true, nullptr, X, npw, Y, npw, 0.0))) return st;
+  if (c->prec == PARO_MIXED) {
+    float2* Y32 = static_cast<float2*>(ws_get(c, "proj_Y32", (size_t)nx * npw * sizeof(float2)));
+    float2* HY32 = static_cast<float2*>(ws_get(c, "proj_HY32", (size_t)nx * npw * sizeof(float2)));
+    if (!Y32 || !HY32) return PARO_ERR_CUDA;
+    if ((st = convert<double, float>(c, (size_t)nx * npw, Y, Y32))) return st;
+    if ((st = apply_h<float>(c, ik, nx, Y32, HY32, 0.0, nullptr))) return st;
+    if ((st = convert<float, double>(c, (size_t)nx * npw, HY32, HY))) return st;
+  } else {
+    if ((st = apply_h<double>(c, ik, nx, Y, HY, 0.0, nullptr))) return st;
+  }
+  if ((st = gemm_cn<double, double, double>(c, nx, nx, npw, Y, npw, HY, npw, S, nx, false))) return st;
+  k_hermitize<<<(nx * nx + 255) / 256, 256, 0, c->stream>>>(nx, S);
+  PARO_LAUNCH(c, "k_hermitize");
+  if ((st = eigh(c, nx, S, w, G))) return st;  // G <- eigenvectors C
+  if ((st = gemm_wx<double, double>(c, nb, npw, nx, G, nx, false, nullptr, Y, npw, b.d_psi, npw, 0.0))) return st;
+  if ((st = gemm_wx<double, double>(c, nb, npw, nx, G, nx, false, nullptr, HY, npw, b.d_hpsi, npw, 0.0))) return st;
+  if ((st = residual_norms(c, nb, npw, b.d_psi, b.d_hpsi, w, res))) return st;
+  b.eps.resize(nb);
+  b.res.resize(nb);
+  PARO_CU(c, cudaMemcpyAsync(b.eps.data(), w, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PARO_CU(c, cudaMemcpyAsync(b.res.data(), res, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PARO_CU(c, cudaStreamSynchronize(c->stream));
+  b.have_psi = true;
+  return PARO_OK;
+}
+
+__global__ void k_axpy_rows(int npw, double2* __restrict__ y, const double2* __restrict__ x,
+                            const double* __restrict__ f, double sx) {
+  const int b = blockIdx.y;
+  const size_t o = (size_t)b * npw;
+  const double s = f ? f[b] : sx;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < npw; g += gridDim.x * blockDim.x)
+    y[o + g] = cadd(y[o + g], cscale(x[o + g], s));
+}
+
+// rhs_b = (eps_b - sigma) psi_b (Algorithm 1) or -(H psi_b - eps_b psi_b) (Algorithm 2), in T
+template <typename T>
+static int source_rhs(Ctx* c, int ik, bool alg2, cplx<T>* rhs) {
+  Basis& b = c->bases[ik];
+  const int nb = c->nb, npw = b.npw;
+  double* f = static_cast<double*>(ws_get(c, "rhs_f", (size_t)nb * sizeof(double)));
+  double2* tmp = static_cast<double2*>(ws_get(c, "rhs_tmp", (size_t)nb * npw * sizeof(double2)));
+  if (!f || !tmp) return PARO_ERR_CUDA;
+  std::vector<double> hf(nb);
+  for (int i = 0; i < nb; ++i) hf[i] = alg2 ? b.eps[i] : b.eps[i] - c->sigma_k[ik];
+  PARO_CU(c, cudaMemcpyAsync(f, hf.data(), nb * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  int st = scale_rows<double>(c, nb, npw, b.d_psi, f, tmp);
+  if (st) return st;
+  if (alg2) {
+    k_axpy_rows<<<dim3((npw + 255) / 256, nb), 256, 0, c->stream>>>(npw, tmp, b.d_hpsi, nullptr, -1.0);
+    PARO_LAUNCH(c, "k_axpy_rows");
+  }
+  if (sizeof(T) == 8) {
+    PARO_CU(c, cudaMemcpyAsync(rhs, tmp, (size_t)nb * npw * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+    return PARO_OK;
+  }
+  return convert<double, float>(c, (size_t)nb * npw, tmp, reinterpret_cast<float2*>(rhs));
+}
+
+// Source problems of all bands of k-point ik into X (FP64, rows 0..nb-1).
+template <typename T>
+static int solve_sources(Ctx* c, int ik, bool alg2, double rel_tol, int max_it, double2* X) {
+  Basis& b = c->bases[ik];
+  const int nb = c->nb, npw = b.npw;
+  const bool f64 = sizeof(T) == 8;
+  cplx<T>* rhs = static_cast<cplx<T>*>(ws_get(c, f64 ? "src_rhs64" : "src_rhs32", (size_t)nb * npw * sizeof(cplx<T>)));
+  cplx<T>* x = static_cast<cplx<T>*>(ws_get(c, f64 ? "src_x64" : "src_x32", (size_t)nb * npw * sizeof(cplx<T>)));
+  if (!rhs || !x) return PARO_ERR_CUDA;
+  int st = source_rhs<T>(c, ik, alg2, rhs);
+  if (st) return st;
+  if (!alg2) {
+    if (f64) {
+      PARO_CU(c, cudaMemcpyAsync(x, b.d_psi, (size_t)nb * npw * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+    } else if ((st = convert<double, float>(c, (size_t)nb * npw, b.d_psi, reinterpret_cast<float2*>(x)))) {
+      return st;
+    }
+  }
+  if ((st = pcg_run<T>(c, ik, nb, rhs, x, alg2, rel_tol, max_it, nullptr))) return st;
+  if (f64) {
+    PARO_CU(c, cudaMemcpyAsync(X, x, (size_t)nb * npw * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+    return PARO_OK;
+  }
+  return convert<float, double>(c, (size_t)nb * npw, reinterpret_cast<const float2*>(x), X);
+}
+
+__global__ void k_compact_rows(int npw, int nb, double2* __restrict__ dst, const double2* __restrict__ src,
+                               const int* __restrict__ map) {
+  const int r = blockIdx.y;
+  const int from = map[r];
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < npw; g += gridDim.x * blockDim.x)
+    dst[(size_t)(nb + r) * npw + g] = src[(size_t)from * npw + g];
+}
+
+// Algorithm 2: [psi, e] with e projected out of span{psi} and corrections of norm <= 1e-10 dropped.
+static int build_alg2_basis(Ctx* c, int ik, double2* E, double2* X, int* nx_out) {
+  Basis& b = c->bases[ik];
+  const int nb = c->nb, npw = b.npw;
+  double2* P = static_cast<double2*>(ws_get(c, "alg2_P", (size_t)nb * nb * sizeof(double2)));
+  double* nrm = static_cast<double*>(ws_get(c, "alg2_nrm", (size_t)nb * sizeof(double)));
+  int* map = static_cast<int*>(ws_get(c, "alg2_map", (size_t)nb * sizeof(int)));
+  if (!P || !nrm || !map) return PARO_ERR_CUDA;
+  int st;
+  // P[i][j] = <psi_i, e_j>;  e_j -= sum_i psi_i P[i][j]
+  if ((st = gemm_cn<double, double, double>(c, nb, nb, npw, b.d_psi, npw, E, npw, P, nb, false))) return st;
+  double2* tmp = static_cast<double2*>(ws_get(c, "alg2_tmp", (size_t)nb * npw * sizeof(double2)));
+  if (!tmp) return PARO_ERR_CUDA;
+  if ((st = gemm_wx<double, double>(c, nb, npw, nb, P, nb, false, nullptr, b.d_psi, npw, tmp, npw, 0.0))) return st;
+  k_axpy_rows<<<dim3((npw + 255) / 256, nb), 256, 0, c->stream>>>(npw, E, tmp, nullptr, -1.0);
+  PARO_LAUNCH(c, "k_axpy_rows");
+  if ((st = band_norms<double>(c, nb, npw, E, npw, nrm))) return st;
+  std::vector<double> h(nb);
+  PARO_CU(c, cudaMemcpyAsync(h.data(), nrm, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PARO_CU(c, cudaStreamSynchronize(c->stream));
+  std::vector<int> keep;
+  for (int i = 0; i < nb; ++i)
+    if (std::sqrt(h[i]) > 1e-10) keep.push_back(i);
+  PARO_CU(c, cudaMemcpyAsync(X, b.d_psi, (size_t)nb * npw * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+  if (!keep.empty()) {
+    PARO_CU(c, cudaMemcpyAsync(map, keep.data(), keep.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    k_compact_rows<<<dim3((npw + 255) / 256, (int)keep.size()), 256, 0, c->stream>>>(npw, nb, X, E, map);
+    PARO_LAUNCH(c, "k_compact_rows");
+  }
+  PARO_CU(c, cudaStreamSynchronize(c->stream));
+  *nx_out = nb + (int)keep.size();
+  return PARO_OK;
+}
+
+static double max_occ_resid(const Ctx* c) {
+  double m = 0;
+  for (const Basis& b : c->bases)
+    for (int i = 0; i < c->nocc && i < (int)b.res.size(); ++i) m = std::max(m, b.res[i]);
+  return m;
+}
+
+// step 3 of Algorithm 1/2 for k-point ik: the new basis rows in X (FP64), count in nx
+static int source_step(Ctx* c, int ik, int alg, double rel_tol, int max_it, double2* X, int* nx) {
+  const bool alg2 = alg == PARO_ALG2;
+  const int npw = c->bases[ik].npw;
+  double2* E = X;
+  if (alg2) {
+    E = static_cast<double2*>(ws_get(c, "alg2_E", (size_t)c->nb * npw * sizeof(double2)));
+    if (!E) return PARO_ERR_CUDA;
+  }
+  int st = c->prec == PARO_MIXED ? solve_sources<float>(c, ik, alg2, rel_tol, max_it, E)
+                                 : solve_sources<double>(c, ik, alg2, rel_tol, max_it, E);
+  if (st) return st;
+  if (!alg2) {
+    *nx = c->nb;
+    return PARO_OK;
+  }
+  return build_alg2_basis(c, ik, E, X, nx);
+}
+
+// Cholesky-orthonormalise the first nx rows of X in place (Y = conj(L)^{-1} X).
+static int orthonormalize(Ctx* c, int ik, double2* X, int nx) {
+  const int npw = c->bases[ik].npw;
+  double2* S = static_cast<double2*>(ws_get(c, "proj_S", (size_t)nx * nx * sizeof(double2)));
+  double2* G = static_cast<double2*>(ws_get(c, "proj_G", (size_t)nx * nx * sizeof(double2)));
+  double2* Y = static_cast<double2*>(ws_get(c, "proj_Y", (size_t)nx * npw * sizeof(double2)));
+  if (!S || !G || !Y) return PARO_ERR_CUDA;
+  int st;
+  if ((st = gemm_cn<double, double, double>(c, nx, nx, npw, X, npw, X, npw, S, nx, true))) return st;
+  if ((st = chol_inv(c, nx, S, G))) return st;
+  if ((st = gemm_wx<double, double>(c, nx, npw, nx, G, nx, true, nullptr, X, npw, Y, npw, 0.0))) return st;
+  PARO_CU(c, cudaMemcpyAsync(X, Y, (size_t)nx * npw * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+  return PARO_OK;
+}
+
+}  // namespace paro
+
+using namespace paro;
+
+// ================================================================================================
+// C ABI
+// ================================================================================================
+#define CTX_CHECK(ctx)                                       \
+  if (!(ctx)) return PARO_ERR_ARG;                           \
+  Ctx* c = &(ctx)->c;                                        \
+  c->err.clear();
+
+extern "C" {
+
+int paro_create(paro_ctx** out, const double lattice[9], int n_atoms, const double* pos, double ecut_ha, int n_k,
+                const double* k_frac, const double* k_w, int n_bands, int n_occ, int precision, void* stream) {
+  g_create_err.clear();
+  if (!out || !lattice || n_atoms < 0 || (n_atoms > 0 && !pos) || !(ecut_ha > 0) || n_k < 1 ||
+      (n_k > 1 && !k_frac) || n_bands < 1 || n_occ < 0 || n_occ > n_bands ||
+      (precision != PARO_FP64 && precision != PARO_MIXED)) {
+    g_create_err = "paro_create: invalid argument";
+    return PARO_ERR_ARG;
+  }
+  *out = nullptr;
+  paro_ctx* ctx = new paro_ctx;
+  Ctx* c = &ctx->c;
+  auto bail = [&](int code) {
+    g_create_err = c->err.empty() ? "paro_create failed" : c->err;
+    paro_destroy(ctx);
+    return code;
+  };
+  for (int i = 0; i < 9; ++i) c->lat[i] = lattice[i];
+  const double* L = c->lat;
+  const double det = L[0] * (L[4] * L[8] - L[5] * L[7]) - L[1] * (L[3] * L[8] - L[5] * L[6]) +
+                     L[2] * (L[3] * L[7] - L[4] * L[6]);
+  if (!(std::fabs(det) > 1e-12)) {
+    c->err = "paro_create: singular lattice";
+    return bail(PARO_ERR_ARG);
+  }
+  c->omega = std::fabs(det);
+  // b_i = 2 pi (a_j x a_k) / det
+  for (int i = 0; i < 3; ++i) {
+    const double* u = L + 3 * ((i + 1) % 3);
+    const double* v = L + 3 * ((i + 2) % 3);
+    c->bmat[3 * i + 0] = 2 * kPi * (u[1] * v[2] - u[2] * v[1]) / det;
+    c->bmat[3 * i + 1] = 2 * kPi * (u[2] * v[0] - u[0] * v[2]) / det;
+    c->bmat[3 * i + 2] = 2 * kPi * (u[0] * v[1] - u[1] * v[0]) / det;
+  }
+  c->nat = n_atoms;
+  c->pos.assign(pos, pos + 3 * n_atoms);
+  c->ecut = ecut_ha;
+  c->nk = n_k;
+  c->nb = n_bands;
+  c->nocc = n_occ;
+  c->prec = precision;
+  c->kw.resize(n_k);
+  double wsum = 0;
+  for (int i = 0; i < n_k; ++i) wsum += (c->kw[i] = k_w ? k_w[i] : 1.0 / n_k);
+  if (!(std::fabs(wsum - 1.0) < 1e-8)) {
+    c->err = "paro_create: k-point weights must sum to 1";
+    return bail(PARO_ERR_ARG);
+  }
+  if (stream) {
+    c->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      cuda_fail(c, e, "cudaStreamCreate");
+      return bail(PARO_ERR_CUDA);
+    }
+    c->own_stream = true;
+  }
+  // bases and the FFT grid: N_i = smallest 2^a 3^b above m_V,i + s_psi,i
+  c->bases.resize(n_k);
+  int span[3] = {0, 0, 0}, mv[3] = {0, 0, 0};
+  {
+    std::vector<int> mil;
+    std::vector<double> kin;
+    const double zero[3] = {0, 0, 0};
+    sphere(c, zero, 4.0 * ecut_ha, mil, kin);
+    for (size_t g = 0; g < kin.size(); ++g)
+      for (int i = 0; i < 3; ++i) mv[i] = std::max(mv[i], std::abs(mil[3 * g + i]));
+  }
+  for (int ik = 0; ik < n_k; ++ik) {
+    Basis& b = c->bases[ik];
+    for (int i = 0; i < 3; ++i) b.kfrac[i] = k_frac ? k_frac[3 * ik + i] : 0.0;
+    for (int x = 0; x < 3; ++x)
+      b.kcart[x] = b.kfrac[0] * c->bmat[x] + b.kfrac[1] * c->bmat[3 + x] + b.kfrac[2] * c->bmat[6 + x];
+    std::vector<int> mil;
+    std::vector<double> kin;
+    sphere(c, b.kfrac, ecut_ha, mil, kin);
+    if ((int)kin.size() < n_bands) {
+      c->err = "paro_create: fewer plane waves than bands";
+      return bail(PARO_ERR_ARG);
+    }
+    for (int i = 0; i < 3; ++i) {
+      int lo = 1 << 30, hi = -(1 << 30);
+      for (size_t g = 0; g < kin.size(); ++g) {
+        lo = std::min(lo, mil[3 * g + i]);
+        hi = std::max(hi, mil[3 * g + i]);
+      }
+      span[i] = std::max(span[i], hi - lo);
+    }
+  }
+  for (int i = 0; i < 3; ++i) {
+    c->N[i] = smooth23_above(mv[i] + span[i]);
+    c->plan[i] = make_plan(c->N[i]);
+  }
+  c->ngrid = c->N[0] * c->N[1] * c->N[2];
+  for (int ik = 0; ik < n_k; ++ik) {
+    if (build_basis(c, c->bases[ik])) return bail(PARO_ERR_CUDA);
+    c->max_npw = std::max(c->max_npw, c->bases[ik].npw);
+  }
+  if (build_twiddles(c)) return bail(PARO_ERR_CUDA);
+  if (check_fft_support(c, precision == PARO_MIXED ? 8 : 16)) return bail(PARO_ERR_ARG);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(PARO_ERR_CUDA);
+  *out = ctx;
+  return PARO_OK;
+}
+
+void paro_destroy(paro_ctx* ctx) {
+  if (!ctx) return;
+  Ctx* c = &ctx->c;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (Basis& b : c->bases) {
+    void* ps[] = {b.d_miller, b.d_kin, b.d_kin32, b.d_col_x, b.d_col_y, b.d_col_off, b.d_g_col, b.d_g_z,
+                  b.d_xrows, b.d_beta, b.d_beta32, b.d_prec_base, b.d_psi, b.d_hpsi};
+    for (void* p : ps)
+      if (p) cudaFree(p);
+  }
+  void* ps[] = {c->d_tw64[0], c->d_tw64[1], c->d_tw64[2], c->d_tw32[0], c->d_tw32[1], c->d_tw32[2],
+                c->d_vloc, c->d_dvec, c->d_dvec32, c->d_veff, c->d_vplane, c->d_vplane32,
+                c->d_rho_in, c->d_pulay_rho, c->d_pulay_res};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  for (auto& kv : c->ws) cudaFree(kv.second.first);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete ctx;
+}
+
+const char* paro_last_error(const paro_ctx* ctx) { return ctx ? ctx->c.err.c_str() : g_create_err.c_str(); }
+
+int paro_grid(const paro_ctx* ctx, int n[3]) {
+  if (!ctx || !n) return PARO_ERR_ARG;
+  for (int i = 0; i < 3; ++i) n[i] = ctx->c.N[i];
+  return PARO_OK;
+}
+
+int paro_npw(const paro_ctx* ctx, int ik, int* npw) {
+  if (!ctx || !npw || ik < 0 || ik >= ctx->c.nk) return PARO_ERR_ARG;
+  *npw = ctx->c.bases[ik].npw;
+  return PARO_OK;
+}
+
+int paro_miller(const paro_ctx* ctx, int ik, int* hkl) {
+  if (!ctx || !hkl || ik < 0 || ik >= ctx->c.nk) return PARO_ERR_ARG;
+  const Basis& b = ctx->c.bases[ik];
+  std::memcpy(hkl, b.miller.data(), b.miller.size() * sizeof(int));
+  return PARO_OK;
+}
+
+int paro_sigma(const paro_ctx* ctx, double* sigma) {
+  if (!ctx || !sigma) return PARO_ERR_ARG;
+  if (!ctx->c.have_veff) return PARO_ERR_STATE;
+  *sigma = ctx->c.sigma_k[0];
+  return PARO_OK;
+}
+
+int paro_set_local_pp(paro_ctx* ctx, double Z, double rc, double A, double a) {
+  CTX_CHECK(ctx);
+  if (!(rc > 0) || !(a > 0)) return fail(c, PARO_ERR_ARG, "rc and a must be positive");
+  c->Z = Z; c->rc = rc; c->A = A; c->a = a;
+  int st = build_vloc(c);
+  if (st) return st;
+  c->have_pp = true;
+  c->e_ewald = ewald(c);
+  if ((st = set_veff_device(c, c->d_vloc))) return st;
+  update_sigma(c);
+  return PARO_OK;
+}
+
+int paro_set_kb(paro_ctx* ctx, double rc, const double* D) {
+  CTX_CHECK(ctx);
+  if (!(rc > 0) || !D) return fail(c, PARO_ERR_ARG, "bad KB arguments");
+  c->kb_rc = rc;
+  c->D.assign(D, D + 2 * c->nat);
+  int st = build_beta(c);
+  if (st) return st;
+  std::vector<double> dv(c->nproj);
+  for (int I = 0; I < c->nat; ++I) {
+    dv[4 * I] = D[2 * I];
+    dv[4 * I + 1] = dv[4 * I + 2] = dv[4 * I + 3] = D[2 * I + 1];
+  }
+  if (!c->d_dvec) PARO_CU(c, cudaMalloc(&c->d_dvec, std::max(c->nproj, 1) * sizeof(double)));
+  PARO_CU(c, cudaMemcpy(c->d_dvec, dv.data(), c->nproj * sizeof(double), cudaMemcpyHostToDevice));
+  c->have_kb = c->nproj > 0;
+  update_sigma(c);
+  return PARO_OK;
+}
+
+int paro_set_veff(paro_ctx* ctx, const double* v_r, int on_device) {
+  CTX_CHECK(ctx);
+  if (!v_r) return fail(c, PARO_ERR_ARG, "null potential");
+  double* tmp = static_cast<double*>(ws_get(c, "grid_r1", (size_t)c->ngrid * sizeof(double)));
+  if (!tmp) return PARO_ERR_CUDA;
+  PARO_CU(c, cudaMemcpyAsync(tmp, v_r, (size_t)c->ngrid * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  int st = set_veff_device(c, tmp);
+  if (st) return st;
+  update_sigma(c);
+  return PARO_OK;
+}
+
+int paro_get_veff(paro_ctx* ctx, double* v_r) {
+  CTX_CHECK(ctx);
+  if (!v_r) return PARO_ERR_ARG;
+  if (!c->have_veff) return fail(c, PARO_ERR_STATE, "no potential");
+  PARO_CU(c, cudaMemcpyAsync(v_r, c->d_veff, (size_t)c->ngrid * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PARO_CU(c, cudaStreamSynchronize(c->stream));
+  return PARO_OK;
+}
+
+int paro_set_density(paro_ctx* ctx, const double* rho, int on_device) {
+  CTX_CHECK(ctx);
+  if (!rho) return PARO_ERR_ARG;
+  if (!c->d_rho_in) PARO_CU(c, cudaMalloc(&c->d_rho_in, (size_t)c->ngrid * sizeof(double)));
+  PARO_CU(c, cudaMemcpyAsync(c->d_rho_in, rho, (size_t)c->ngrid * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  int st = veff_from_density(c, c->d_rho_in, nullptr, nullptr);
+  if (st) return st;
+  c->have_rho = true;
+  update_sigma(c);
+  return PARO_OK;
+}
+
+int paro_apply_h(paro_ctx* ctx, int ik, int nb, int dtype, const void* psi, void* hpsi) {
+  CTX_CHECK(ctx);
+  if (ik < 0 || ik >= c->nk || nb < 1 || !psi || !hpsi || psi == hpsi ||
+      (dtype != PARO_C64 && dtype != PARO_C32))
+    return fail(c, PARO_ERR_ARG, "paro_apply_h: bad argument");
+  if (dtype == PARO_C64 && check_fft_support(c, 16)) return PARO_ERR_ARG;
+  return dtype == PARO_C64
+             ? apply_h<double>(c, ik, nb, static_cast<const double2*>(psi), static_cast<double2*>(hpsi), 0.0, nullptr)
+             : apply_h<float>(c, ik, nb, static_cast<const float2*>(psi), static_cast<float2*>(hpsi), 0.0, nullptr);
+}
+
+int paro_solve_source(paro_ctx* ctx, int ik, int nb, int dtype, const double* eps, const void* psi, void* x,
+                      double rel_tol, int max_it, int* iters_out) {
+  CTX_CHECK(ctx);
+  if (ik < 0 || ik >= c->nk || nb < 1 || !eps || !psi || !x || psi == x || max_it < 0 ||
+      (dtype != PARO_C64 && dtype != PARO_C32))
+    return fail(c, PARO_ERR_ARG, "paro_solve_source: bad argument");
+  if (!c->have_veff) return fail(c, PARO_ERR_STATE, "no effective potential set");
+  const int npw = c->bases[ik].npw;
+  double* f = static_cast<double*>(ws_get(c, "ss_f", (size_t)nb * sizeof(double)));
+  if (!f) return PARO_ERR_CUDA;
+  std::vector<double> hf(nb);
+  for (int i = 0; i < nb; ++i) hf[i] = eps[i] - c->sigma_k[ik];
+  PARO_CU(c, cudaMemcpyAsync(f, hf.data(), nb * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (dtype == PARO_C64) {
+    double2* rhs = static_cast<double2*>(ws_get(c, "src_rhs64", (size_t)nb * npw * sizeof(double2)));
+    if (!rhs) return PARO_ERR_CUDA;
+    int st = scale_rows<double>(c, nb, npw, static_cast<const double2*>(psi), f, rhs);
+    if (st) return st;
+    PARO_CU(c, cudaMemcpyAsync(x, psi, (size_t)nb * npw * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+    return pcg_run<double>(c, ik, nb, rhs, static_cast<double2*>(x), false, rel_tol, max_it, iters_out);
+  }
+  float2* rhs = static_cast<float2*>(ws_get(c, "src_rhs32", (size_t)nb * npw * sizeof(float2)));
+  if (!rhs) return PARO_ERR_CUDA;
+  int st = scale_rows<float>(c, nb, npw, static_cast<const float2*>(psi), f, rhs);
+  if (st) return st;
+  PARO_CU(c, cudaMemcpyAsync(x, psi, (size_t)nb * npw * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+  return pcg_run<float>(c, ik, nb, rhs, static_cast<float2*>(x), false, rel_tol, max_it, iters_out);
+}
+
+int paro_set_orbitals(paro_ctx* ctx, int ik, const void* psi, int on_device) {
+  CTX_CHECK(ctx);
+  if (ik < 0 || ik >= c->nk || !psi) return fail(c, PARO_ERR_ARG, "paro_set_orbitals: bad argument");
+  if (!c->have_veff) return fail(c, PARO_ERR_STATE, "no effective potential set");
+  Basis& b = c->bases[ik];
+  int st = alloc_orbitals(c, b);
+  if (st) return st;
+  double2* X = static_cast<double2*>(ws_get(c, "step_X", (size_t)2 * c->nb * b.npw * sizeof(double2)));
+  if (!X) return PARO_ERR_CUDA;
+  PARO_CU(c, cudaMemcpyAsync(X, psi, (size_t)c->nb * b.npw * sizeof(double2),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  return project(c, ik, X, c->nb);
+}
+
+int paro_get_orbitals(paro_ctx* ctx, int ik, void* psi, int on_device) {
+  CTX_CHECK(ctx);
+  if (ik < 0 || ik >= c->nk || !psi) return PARO_ERR_ARG;
+  Basis& b = c->bases[ik];
+  if (!b.have_psi) return fail(c, PARO_ERR_STATE, "no orbitals");
+  PARO_CU(c, cudaMemcpyAsync(psi, b.d_psi, (size_t)c->nb * b.npw * sizeof(double2),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  PARO_CU(c, cudaStreamSynchronize(c->stream));
+  return PARO_OK;
+}
+
+int paro_get_eigenvalues(paro_ctx* ctx, double* eps) {
+  CTX_CHECK(ctx);
+  if (!eps) return PARO_ERR_ARG;
+  for (int ik = 0; ik < c->nk; ++ik) {
+    if (!c->bases[ik].have_psi) return fail(c, PARO_ERR_STATE, "no orbitals");
+    std::copy(c->bases[ik].eps.begin(), c->bases[ik].eps.end(), eps + (size_t)ik * c->nb);
+  }
+  return PARO_OK;
+}
+
+int paro_get_residuals(paro_ctx* ctx, double* res) {
+  CTX_CHECK(ctx);
+  if (!res) return PARO_ERR_ARG;
+  for (int ik = 0; ik < c->nk; ++ik) {
+    if (!c->bases[ik].have_psi) return fail(c, PARO_ERR_STATE, "no orbitals");
+    std::copy(c->bases[ik].res.begin(), c->bases[ik].res.end(), res + (size_t)ik * c->nb);
+  }
+  return PARO_OK;
+}
+
+int paro_step(paro_ctx* ctx, int alg, double rel_tol, int max_it, double* max_resid_out) {
+  CTX_CHECK(ctx);
+  if ((alg != PARO_ALG1 && alg != PARO_ALG2) || max_it < 0) return fail(c, PARO_ERR_ARG, "paro_step: bad argument");
+  for (int ik = 0; ik < c->nk; ++ik) {
+    Basis& b = c->bases[ik];
+    if (!b.have_psi) return fail(c, PARO_ERR_STATE, "paro_step: orbitals not set");
+    double2* X = static_cast<double2*>(ws_get(c, "step_X", (size_t)2 * c->nb * b.npw * sizeof(double2)));
+    if (!X) return PARO_ERR_CUDA;
+    int nx = c->nb;
+    int st = source_step(c, ik, alg, rel_tol, max_it, X, &nx);
+    if (st) return st;
+    if ((st = project(c, ik, X, nx))) return st;
+  }
+  if (max_resid_out) *max_resid_out = max_occ_resid(c);
+  return PARO_OK;
+}
+
+int paro_eigh(paro_ctx* ctx, int n, const void* a, double* w, void* v) {
+  CTX_CHECK(ctx);
+  if (n < 1 || !a || !w || !v) return fail(c, PARO_ERR_ARG, "paro_eigh: bad argument");
+  return eigh(c, n, static_cast<const double2*>(a), w, static_cast<double2*>(v));
+}
+
+int paro_density(paro_ctx* ctx, double* rho_dev) {
+  CTX_CHECK(ctx);
+  if (!rho_dev) return PARO_ERR_ARG;
+  std::vector<const double2*> ps(c->nk);
+  for (int ik = 0; ik < c->nk; ++ik) {
+    if (!c->bases[ik].have_psi) return fail(c, PARO_ERR_STATE, "no orbitals");
+    ps[ik] = c->bases[ik].d_psi;
+  }
+  return density(c, ps.data(), rho_dev);
+}
+
+int paro_energy(paro_ctx* ctx, double terms[7]) {
+  CTX_CHECK(ctx);
+  if (!terms) return PARO_ERR_ARG;
+  if (!c->have_pp) return fail(c, PARO_ERR_STATE, "no local pseudopotential");
+  double* rho = static_cast<double*>(ws_get(c, "energy_rho", (size_t)c->ngrid * sizeof(double)));
+  if (!rho) return PARO_ERR_CUDA;
+  int st = paro_density(ctx, rho);
+  if (st) return st;
+  return energy_terms(c, rho, terms);
+}
+
+__global__ void k_fill(int n, double v, double* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = v;
+}
+
+int paro_scf_step(paro_ctx* ctx, const paro_scf_opts* o, double energy[7], double* max_resid_out) {
+  CTX_CHECK(ctx);
+  if (!o || (o->alg != PARO_ALG1 && o->alg != PARO_ALG2)) return fail(c, PARO_ERR_ARG, "paro_scf_step: bad options");
+  if (!c->have_pp) return fail(c, PARO_ERR_STATE, "no local pseudopotential");
+  for (int ik = 0; ik < c->nk; ++ik)
+    if (!c->bases[ik].have_psi) return fail(c, PARO_ERR_STATE, "orbitals not set");
+  int st;
+  if (!c->have_rho) {  // first iteration: uniform density, Ritz pairs of the start span under its potential
+    if (!c->d_rho_in) PARO_CU(c, cudaMalloc(&c->d_rho_in, (size_t)c->ngrid * sizeof(double)));
+    k_fill<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, 2.0 * c->nocc / c->omega, c->d_rho_in);
+    PARO_LAUNCH(c, "k_fill");
+    if ((st = veff_from_density(c, c->d_rho_in, nullptr, nullptr))) return st;
+    update_sigma(c);
+    for (int ik = 0; ik < c->nk; ++ik) {
+      Basis& b = c->bases[ik];
+      double2* X = static_cast<double2*>(ws_get(c, "step_X", (size_t)2 * c->nb * b.npw * sizeof(double2)));
+      if (!X) return PARO_ERR_CUDA;
+      PARO_CU(c, cudaMemcpyAsync(X, b.d_psi, (size_t)c->nb * b.npw * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                 c->stream));
+      if ((st = project(c, ik, X, c->nb))) return st;
+    }
+    c->have_rho = true;
+    c->scf_iter = 0;
+    c->scf_small = 0;
+    c->pulay_n = 0;
+    c->pulay_head = 0;
+  }
+  // step 3 with V(rho_in^n), then Cholesky
+  std::vector<double2*> xs(c->nk);
+  std::vector<int> nxs(c->nk);
+  for (int ik = 0; ik < c->nk; ++ik) {
+    Basis& b = c->bases[ik];
+    std::string name = "scf_X" + std::to_string(ik);
+    xs[ik] = static_cast<double2*>(ws_get(c, name.c_str(), (size_t)2 * c->nb * b.npw * sizeof(double2)));
+    if (!xs[ik]) return PARO_ERR_CUDA;
+    if ((st = source_step(c, ik, o->alg, o->inner_rel_tol, o->inner_max_it, xs[ik], &nxs[ik]))) return st;
+    if ((st = orthonormalize(c, ik, xs[ik], nxs[ik]))) return st;
+  }
+  // rho_in^{n+1/2} = Pulay(rho_in^n, rho[X]) (Algorithm 2: rho of the previous orbitals)
+  double* rho_out = static_cast<double*>(ws_get(c, "scf_rho_out", (size_t)c->ngrid * sizeof(double)));
+  if (!rho_out) return PARO_ERR_CUDA;
+  std::vector<const double2*> dens_src(c->nk);
+  for (int ik = 0; ik < c->nk; ++ik) dens_src[ik] = o->alg == PARO_ALG1 ? xs[ik] : c->bases[ik].d_psi;
+  if ((st = density(c, dens_src.data(), rho_out))) return st;
+  if ((st = pulay_mix(c, rho_out, o->pulay_depth, o->pulay_beta))) return st;
+  if ((st = veff_from_density(c, c->d_rho_in, nullptr, nullptr))) return st;
+  update_sigma(c);
+  // step 4: Rayleigh-Ritz with V(rho_in^{n+1/2})
+  for (int ik = 0; ik < c->nk; ++ik)
+    if ((st = project(c, ik, xs[ik], nxs[ik]))) return st;
+  double terms[7];
+  if ((st = paro_energy(ctx, terms))) return st;
+  if (energy) std::copy(terms, terms + 7, energy);
+  if (max_resid_out) *max_resid_out = max_occ_resid(c);
+  const double e = terms[PARO_E_TOTAL];
+  if (c->scf_iter > 0 && std::fabs(e - c->e_prev) / std::max(c->nat, 1) < o->tol_per_atom)
+    ++c->scf_small;
+  else
+    c->scf_small = 0;
+  c->e_prev = e;
+  ++c->scf_iter;
+  return PARO_OK;
+}
+
+int paro_scf(paro_ctx* ctx, const paro_scf_opts* o, paro_scf_result* r) {
+  CTX_CHECK(ctx);
+  if (!o || !r || o->max_iter < 1) return fail(c, PARO_ERR_ARG, "paro_scf: bad argument");
+  std::memset(r, 0, sizeof(*r));
+  for (int it = 0; it < o->max_iter; ++it) {
+    int st = paro_scf_step(ctx, o, r->energy, &r->max_resid);
+    if (st) return st;
+    r->n_iter = it + 1;
+    if (c->scf_small >= 2) {
+      r->converged = 1;
+      return PARO_OK;
+    }
+  }
+  return fail(c, PARO_ERR_NOT_CONVERGED, "SCF did not converge within max_iter");
+}
+
+}  // extern "C"

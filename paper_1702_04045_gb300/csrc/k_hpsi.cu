@@ -1,0 +1,232 @@
+// H psi for a batch of orbitals (Eq. e5 applied through the FFT), three passes over the FFT grid:
+//
+//   pass 1  scatter each z-column ("stick") of the cutoff sphere into a line of N3 points and
+//           inverse-FFT it along z; sticks of one band are written plane-major S[b][z][stick];
+//   pass 2  per (band, z-plane): place the plane's sticks on the N1 x N2 plane, inverse-FFT along y
+//           (only the rows that hold sticks) and along x, multiply by V_eff(r)/N_grid, forward-FFT
+//           along x and along y (rows with sticks only), and keep the stick positions;
+//   pass 3  forward-FFT each stick along z and gather the sphere coefficients, adding the kinetic
+//           term |k+G|^2/2 c_G (and an optional shift -sigma c_G for the PCG operator H - sigma).
+//
+// The nonlocal Kleinman-Bylander part (Section 2.2, V_nl) is added afterwards by two GEMMs:
+// P = beta^H psi (nproj x nb), then H psi += beta (D o P).
+#include "paro_ctx.h"
+
+namespace paro {
+
+// ------------------------------------------------------------------------------------------------
+// pass 1
+// ------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_zpass_inv(const cplx<T>* __restrict__ psi, int ldpsi,
+                                                   cplx<T>* __restrict__ S, const int* __restrict__ col_off,
+                                                   const int* __restrict__ g_col, const int* __restrict__ g_z,
+                                                   int ncol, FftPlan pz, const cplx<T>* __restrict__ twz,
+                                                   const int* __restrict__ active, int CB) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int N3 = pz.n, ls = N3 + 1;
+  cplx<T>* line = tw + N3;
+  const int b = blockIdx.y;
+  if (active != nullptr && active[b] == 0) return;
+  const int c0 = blockIdx.x * CB;
+  const int ncb = min(CB, ncol - c0);
+  for (int i = threadIdx.x; i < N3; i += blockDim.x) tw[i] = twz[i];
+  for (int i = threadIdx.x; i < ncb * ls; i += blockDim.x) line[i] = mk<T>(0, 0);
+  __syncthreads();
+  const int g0 = col_off[c0], g1 = col_off[c0 + ncb];
+  const cplx<T>* p = psi + (size_t)b * ldpsi;
+  for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) line[(g_col[g] - c0) * ls + g_z[g]] = p[g];
+  __syncthreads();
+  fft_lines<T, true, false>(line, pz, ncb, 1, LinesDirect{ls}, tw);
+  cplx<T>* Sb = S + (size_t)b * N3 * ncol;
+  for (int i = threadIdx.x; i < N3 * ncb; i += blockDim.x) {
+    const int z = i / ncb, cc = i - z * ncb;
+    Sb[(size_t)z * ncol + c0 + cc] = line[cc * ls + z];
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// pass 2
+// ------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(512, 1) k_plane(cplx<T>* __restrict__ S, int ncol, const int* __restrict__ col_x,
+                        const int* __restrict__ col_y, const int* __restrict__ xrows, int nxr, FftPlan px,
+                        FftPlan py, const cplx<T>* __restrict__ twx, const cplx<T>* __restrict__ twy,
+                        const T* __restrict__ vplane, const int* __restrict__ active) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N1 = px.n, N2 = py.n;
+  cplx<T>* tx = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* ty = tx + N1;
+  cplx<T>* P = ty + N2;
+  const int z = blockIdx.x, b = blockIdx.y, N3 = gridDim.x;
+  if (active != nullptr && active[b] == 0) return;
+  for (int i = threadIdx.x; i < N1; i += blockDim.x) tx[i] = twx[i];
+  for (int i = threadIdx.x; i < N2; i += blockDim.x) ty[i] = twy[i];
+  for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) P[i] = mk<T>(0, 0);
+  __syncthreads();
+  cplx<T>* Sz = S + ((size_t)b * N3 + z) * ncol;
+  for (int c = threadIdx.x; c < ncol; c += blockDim.x) P[col_x[c] * N2 + col_y[c]] = Sz[c];
+  __syncthreads();
+  fft_lines<T, true, false>(P, py, nxr, 1, LinesMapped{xrows, N2}, ty);
+  fft_lines<T, true, true>(P, px, N2, N2, LinesDirect{1}, tx);
+  const T* V = vplane + (size_t)z * N1 * N2;
+  for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) P[i] = cscale(P[i], V[i]);
+  __syncthreads();
+  fft_lines<T, false, true>(P, px, N2, N2, LinesDirect{1}, tx);
+  fft_lines<T, false, false>(P, py, nxr, 1, LinesMapped{xrows, N2}, ty);
+  for (int c = threadIdx.x; c < ncol; c += blockDim.x) Sz[c] = P[col_x[c] * N2 + col_y[c]];
+}
+
+// ------------------------------------------------------------------------------------------------
+// pass 3
+// ------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_zpass_fwd(const cplx<T>* __restrict__ S, const cplx<T>* __restrict__ psi,
+                                                   int ldpsi, cplx<T>* __restrict__ hpsi, int ldh,
+                                                   const T* __restrict__ kin, T shift,
+                                                   const int* __restrict__ col_off, const int* __restrict__ g_col,
+                                                   const int* __restrict__ g_z, int ncol, FftPlan pz,
+                                                   const cplx<T>* __restrict__ twz,
+                                                   const int* __restrict__ active, int CB) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int N3 = pz.n, ls = N3 + 1;
+  cplx<T>* line = tw + N3;
+  const int b = blockIdx.y;
+  if (active != nullptr && active[b] == 0) return;
+  const int c0 = blockIdx.x * CB;
+  const int ncb = min(CB, ncol - c0);
+  for (int i = threadIdx.x; i < N3; i += blockDim.x) tw[i] = twz[i];
+  const cplx<T>* Sb = S + (size_t)b * N3 * ncol;
+  for (int i = threadIdx.x; i < N3 * ncb; i += blockDim.x) {
+    const int z = i / ncb, cc = i - z * ncb;
+    line[cc * ls + z] = Sb[(size_t)z * ncol + c0 + cc];
+  }
+  __syncthreads();
+  fft_lines<T, false, false>(line, pz, ncb, 1, LinesDirect{ls}, tw);
+  const int g0 = col_off[c0], g1 = col_off[c0 + ncb];
+  const cplx<T>* p = psi + (size_t)b * ldpsi;
+  cplx<T>* h = hpsi + (size_t)b * ldh;
+  for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+    const cplx<T> v = line[(g_col[g] - c0) * ls + g_z[g]];
+    const cplx<T> c = p[g];
+    const T t = kin[g] - shift;
+    h[g] = mk<T>(v.x + t * c.x, v.y + t * c.y);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------------
+static const int kStickBatch = 32;
+static const int kZThreads = 256;
+
+static int plane_threads(const Ctx*) { return 512; }
+
+// every stage must hold at least one whole line (lines are processed in groups)
+static bool stages_fit(const FftPlan& p, int threads) {
+  for (int s = 0; s < p.nst; ++s) {
+    const int R = p.rad[s];
+    const int mu = R == 2 ? 4 : (R == 8 ? 1 : 2);
+    if (p.n / R > mu * threads) return false;
+  }
+  return true;
+}
+
+static size_t zpass_smem(const Ctx* c, int eb) { return (size_t)eb * (c->N[2] + kStickBatch * (c->N[2] + 1)); }
+static size_t plane_smem(const Ctx* c, int eb) { return (size_t)eb * (c->N[0] + c->N[1] + c->N[0] * c->N[1]); }
+
+int check_fft_support(Ctx* c, int eb) {
+  const int pt = plane_threads(c);
+  if (!stages_fit(c->plan[2], kZThreads) || !stages_fit(c->plan[1], pt) || !stages_fit(c->plan[0], pt))
+    return fail(c, PARO_ERR_ARG, "FFT grid too large for the register budget of the shared-memory FFT");
+  if (plane_smem(c, eb) > 227 * 1024 || zpass_smem(c, eb) > 227 * 1024)
+    return fail(c, PARO_ERR_ARG, "FFT plane does not fit in shared memory for this precision");
+  return PARO_OK;
+}
+
+template <typename T>
+static int configure(Ctx* c) {
+  const int eb = (int)sizeof(cplx<T>);
+  bool& d = c->fft_configured[sizeof(T) == 8];
+  if (!d) {
+    PARO_CU(c, cudaFuncSetAttribute(k_zpass_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    PARO_CU(c, cudaFuncSetAttribute(k_zpass_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    PARO_CU(c, cudaFuncSetAttribute(k_plane<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    d = true;
+  }
+  return check_fft_support(c, eb);
+}
+
+template <typename T> static const cplx<T>* tw_of(const Ctx* c, int ax);
+template <> const double2* tw_of<double>(const Ctx* c, int ax) { return c->d_tw64[ax]; }
+template <> const float2* tw_of<float>(const Ctx* c, int ax) { return c->d_tw32[ax]; }
+template <typename T> static const T* vplane_of(const Ctx* c);
+template <> const double* vplane_of<double>(const Ctx* c) { return c->d_vplane; }
+template <> const float* vplane_of<float>(const Ctx* c) { return c->d_vplane32; }
+template <typename T> static const T* kin_of(const Basis& b);
+template <> const double* kin_of<double>(const Basis& b) { return b.d_kin; }
+template <> const float* kin_of<float>(const Basis& b) { return b.d_kin32; }
+
+template <typename T>
+int apply_h(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* hpsi, double shift, const int* active) {
+  if (!c->have_veff) return fail(c, PARO_ERR_STATE, "no effective potential set");
+  int st = configure<T>(c);
+  if (st) return st;
+  const Basis& B = c->bases[ik];
+  const int eb = (int)sizeof(cplx<T>);
+  const size_t sbytes = (size_t)nb * c->N[2] * B.ncol * eb;
+  cplx<T>* S = static_cast<cplx<T>*>(ws_get(c, sizeof(T) == 8 ? "sticks64" : "sticks32", sbytes));
+  if (!S) return PARO_ERR_CUDA;
+  const dim3 gz((B.ncol + kStickBatch - 1) / kStickBatch, nb);
+  k_zpass_inv<T><<<gz, kZThreads, zpass_smem(c, eb), c->stream>>>(psi, B.npw, S, B.d_col_off, B.d_g_col, B.d_g_z,
+                                                                  B.ncol, c->plan[2], tw_of<T>(c, 2), active,
+                                                                  kStickBatch);
+  PARO_LAUNCH(c, "k_zpass_inv");
+  k_plane<T><<<dim3(c->N[2], nb), plane_threads(c), plane_smem(c, eb), c->stream>>>(
+      S, B.ncol, B.d_col_x, B.d_col_y, B.d_xrows, B.nxr, c->plan[0], c->plan[1], tw_of<T>(c, 0), tw_of<T>(c, 1),
+      vplane_of<T>(c), active);
+  PARO_LAUNCH(c, "k_plane");
+  k_zpass_fwd<T><<<gz, kZThreads, zpass_smem(c, eb), c->stream>>>(S, psi, B.npw, hpsi, B.npw, kin_of<T>(B),
+                                                                  (T)shift, B.d_col_off, B.d_g_col, B.d_g_z,
+                                                                  B.ncol, c->plan[2], tw_of<T>(c, 2), active,
+                                                                  kStickBatch);
+  PARO_LAUNCH(c, "k_zpass_fwd");
+  if (c->have_kb) return kb_apply<T>(c, ik, nb, psi, hpsi);
+  return PARO_OK;
+}
+
+int sticks_inverse(Ctx* c, int ik, int nb, const double2* psi, double2* S) {
+  int st = configure<double>(c);
+  if (st) return st;
+  const Basis& B = c->bases[ik];
+  const dim3 gz((B.ncol + kStickBatch - 1) / kStickBatch, nb);
+  k_zpass_inv<double><<<gz, kZThreads, zpass_smem(c, sizeof(double2)), c->stream>>>(
+      psi, B.npw, S, B.d_col_off, B.d_g_col, B.d_g_z, B.ncol, c->plan[2], c->d_tw64[2], nullptr, kStickBatch);
+  PARO_LAUNCH(c, "k_zpass_inv");
+  return PARO_OK;
+}
+
+template <typename T> static const cplx<T>* beta_of(const Basis& b);
+template <> const double2* beta_of<double>(const Basis& b) { return b.d_beta; }
+template <> const float2* beta_of<float>(const Basis& b) { return b.d_beta32; }
+
+// H psi += beta (D o (beta^H psi))
+template <typename T>
+int kb_apply(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* hpsi) {
+  const Basis& B = c->bases[ik];
+  double2* P = static_cast<double2*>(ws_get(c, "kb_proj", (size_t)c->nproj * nb * sizeof(double2)));
+  if (!P) return PARO_ERR_CUDA;
+  int st = gemm_cn<T, T, T>(c, c->nproj, nb, B.npw, beta_of<T>(B), B.npw, psi, B.npw, P, nb, false);
+  if (st) return st;
+  // W(k = p, m = b) = D_p P[p][b]
+  return gemm_wx<T, T>(c, nb, B.npw, c->nproj, P, nb, false, c->d_dvec, beta_of<T>(B), B.npw, hpsi, B.npw, 1.0);
+}
+
+template int apply_h<double>(Ctx*, int, int, const double2*, double2*, double, const int*);
+template int apply_h<float>(Ctx*, int, int, const float2*, float2*, double, const int*);
+template int kb_apply<double>(Ctx*, int, int, const double2*, double2*);
+template int kb_apply<float>(Ctx*, int, int, const float2*, float2*);
+
+}  // namespace paro

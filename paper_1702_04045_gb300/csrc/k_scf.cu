@@ -1,0 +1,810 @@
+// Setup and SCF kernels: twiddle tables, full-grid 3D FFT, structure factors, local pseudopotential,
+// Kleinman-Bylander projectors, effective potential (Hartree + LDA-PZ), density, Pulay mixing,
+// energy terms and the Ewald energy (Section 2.1, Section 2.2, Section 2.3).
+#include <cmath>
+#include <vector>
+
+#include "paro_ctx.h"
+
+namespace paro {
+
+static const double kPi = 3.14159265358979323846;
+
+__device__ __forceinline__ int signed_index(int j, int n) { return 2 * j < n ? j : j - n; }
+
+// ------------------------------------------------------------------------------------------------
+// twiddles exp(-2 pi i j / n)
+// ------------------------------------------------------------------------------------------------
+__global__ void k_twiddle(int n, double2* __restrict__ t64, float2* __restrict__ t32) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double s, c;
+  sincospi(2.0 * (double)j / (double)n, &s, &c);
+  t64[j] = make_double2(c, -s);
+  t32[j] = make_float2((float)c, (float)-s);
+}
+
+int build_twiddles(Ctx* c) {
+  for (int ax = 0; ax < 3; ++ax) {
+    const int n = c->N[ax];
+    PARO_CU(c, cudaMalloc(&c->d_tw64[ax], n * sizeof(double2)));
+    PARO_CU(c, cudaMalloc(&c->d_tw32[ax], n * sizeof(float2)));
+    k_twiddle<<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->d_tw64[ax], c->d_tw32[ax]);
+    PARO_LAUNCH(c, "k_twiddle");
+  }
+  return PARO_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// full-grid 3D FFT (FP64), in place, unnormalised; C order (x, y, z)
+// ------------------------------------------------------------------------------------------------
+static const int kLB = 16;  // lines per CTA
+
+template <bool INV>
+__global__ void __launch_bounds__(256) k_fft_z(double2* __restrict__ data, int nlines, FftPlan p,
+                                               const double2* __restrict__ twg) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = p.n, ls = n + 1;
+  double2* tw = reinterpret_cast<double2*>(smem_raw);
+  double2* lines = tw + n;
+  const int l0 = blockIdx.x * kLB, nl = min(kLB, nlines - l0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < nl * n; i += blockDim.x) {
+    const int l = i / n, j = i - l * n;
+    lines[l * ls + j] = data[(size_t)(l0 + l) * n + j];
+  }
+  __syncthreads();
+  fft_lines<double, INV, false>(lines, p, nl, 1, LinesDirect{ls}, tw);
+  for (int i = threadIdx.x; i < nl * n; i += blockDim.x) {
+    const int l = i / n, j = i - l * n;
+    data[(size_t)(l0 + l) * n + j] = lines[l * ls + j];
+  }
+}
+
+// lines along an axis of element stride es; a CTA takes 16 consecutive z positions of one outer index
+template <bool INV>
+__global__ void __launch_bounds__(256) k_fft_strided(double2* __restrict__ data, FftPlan p, int es, int os,
+                                                     int ninner, const double2* __restrict__ twg) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = p.n, ls = n + 1;
+  double2* tw = reinterpret_cast<double2*>(smem_raw);
+  double2* lines = tw + n;
+  const int z0 = blockIdx.x * kLB, nz = min(kLB, ninner - z0);
+  const size_t base = (size_t)blockIdx.y * os + z0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < nz * n; i += blockDim.x) {
+    const int l = i % nz, j = i / nz;
+    lines[l * ls + j] = data[base + (size_t)j * es + l];
+  }
+  __syncthreads();
+  fft_lines<double, INV, false>(lines, p, nz, 1, LinesDirect{ls}, tw);
+  for (int i = threadIdx.x; i < nz * n; i += blockDim.x) {
+    const int l = i % nz, j = i / nz;
+    data[base + (size_t)j * es + l] = lines[l * ls + j];
+  }
+}
+
+int fft3d(Ctx* c, double2* data, bool inverse) {
+  const int N1 = c->N[0], N2 = c->N[1], N3 = c->N[2];
+  const size_t smz = (size_t)(N3 + kLB * (N3 + 1)) * sizeof(double2);
+  const size_t smy = (size_t)(N2 + kLB * (N2 + 1)) * sizeof(double2);
+  const size_t smx = (size_t)(N1 + kLB * (N1 + 1)) * sizeof(double2);
+  if (inverse) {
+    PARO_CU(c, cudaFuncSetAttribute(k_fft_z<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+    PARO_CU(c, cudaFuncSetAttribute(k_fft_strided<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+    k_fft_z<true><<<(N1 * N2 + kLB - 1) / kLB, 256, smz, c->stream>>>(data, N1 * N2, c->plan[2], c->d_tw64[2]);
+    k_fft_strided<true><<<dim3((N3 + kLB - 1) / kLB, N1), 256, smy, c->stream>>>(data, c->plan[1], N3, N2 * N3, N3,
+                                                                               c->d_tw64[1]);
+    k_fft_strided<true><<<dim3((N3 + kLB - 1) / kLB, N2), 256, smx, c->stream>>>(data, c->plan[0], N2 * N3, N3, N3,
+                                                                               c->d_tw64[0]);
+  } else {
+    PARO_CU(c, cudaFuncSetAttribute(k_fft_z<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+    PARO_CU(c, cudaFuncSetAttribute(k_fft_strided<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+    k_fft_z<false><<<(N1 * N2 + kLB - 1) / kLB, 256, smz, c->stream>>>(data, N1 * N2, c->plan[2], c->d_tw64[2]);
+    k_fft_strided<false><<<dim3((N3 + kLB - 1) / kLB, N1), 256, smy, c->stream>>>(data, c->plan[1], N3, N2 * N3, N3,
+                                                                                c->d_tw64[1]);
+    k_fft_strided<false><<<dim3((N3 + kLB - 1) / kLB, N2), 256, smx, c->stream>>>(data, c->plan[0], N2 * N3, N3, N3,
+                                                                                c->d_tw64[0]);
+  }
+  PARO_LAUNCH(c, "fft3d");
+  return PARO_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// structure-factor phase tables: ph[a][I][j] = exp(-i 2 pi n f_{I,a}), n = signed grid index j
+// ------------------------------------------------------------------------------------------------
+__global__ void k_phase_tables(int nat, int N1, int N2, int N3, const double* __restrict__ frac,
+                               double2* __restrict__ ph) {
+  const int tot = N1 + N2 + N3;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nat * tot) return;
+  const int I = idx / tot;
+  int j = idx - I * tot, a = 0, n = N1;
+  if (j >= N1) { j -= N1; a = 1; n = N2; if (j >= N2) { j -= N2; a = 2; n = N3; } }
+  const int s = signed_index(j, n);
+  double sn, cs;
+  sincospi(2.0 * (double)s * frac[I * 3 + a], &sn, &cs);
+  ph[idx] = make_double2(cs, -sn);
+}
+
+static double2* phase_tables(Ctx* c) {
+  const int tot = c->N[0] + c->N[1] + c->N[2];
+  double2* ph = static_cast<double2*>(ws_get(c, "phase_tables", (size_t)c->nat * tot * sizeof(double2)));
+  double* dfrac = static_cast<double*>(ws_get(c, "frac", (size_t)c->nat * 3 * sizeof(double)));
+  if (!ph || !dfrac) return nullptr;
+  // fractional coordinates f_a = R . b_a / (2 pi)
+  std::vector<double> frac(c->nat * 3);
+  for (int I = 0; I < c->nat; ++I)
+    for (int a = 0; a < 3; ++a) {
+      double s = 0;
+      for (int x = 0; x < 3; ++x) s += c->pos[I * 3 + x] * c->bmat[a * 3 + x];
+      frac[I * 3 + a] = s / (2.0 * kPi);
+    }
+  if (cudaMemcpyAsync(dfrac, frac.data(), frac.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream) !=
+      cudaSuccess) {
+    fail(c, PARO_ERR_CUDA, "phase table copy failed");
+    return nullptr;
+  }
+  k_phase_tables<<<(c->nat * tot + 255) / 256, 256, 0, c->stream>>>(c->nat, c->N[0], c->N[1], c->N[2], dfrac, ph);
+  if (cudaGetLastError() != cudaSuccess) {
+    fail(c, PARO_ERR_CUDA, "k_phase_tables launch failed");
+    return nullptr;
+  }
+  return ph;
+}
+
+struct Mat3 {
+  double m[9];
+};
+
+// ------------------------------------------------------------------------------------------------
+// local pseudopotential V_loc(G) on the density sphere, then V_loc(r) by an inverse FFT
+// ------------------------------------------------------------------------------------------------
+__global__ void k_vloc_g(int N1, int N2, int N3, Mat3 B, double ecut4, double Z, double rc, double A, double a,
+                         double omega, int nat, const double2* __restrict__ ph, double2* __restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ng = N1 * N2 * N3;
+  if (idx >= ng) return;
+  const int j3 = idx % N3, j2 = (idx / N3) % N2, j1 = idx / (N2 * N3);
+  const int n1 = signed_index(j1, N1), n2 = signed_index(j2, N2), n3 = signed_index(j3, N3);
+  const double gx = n1 * B.m[0] + n2 * B.m[3] + n3 * B.m[6];
+  const double gy = n1 * B.m[1] + n2 * B.m[4] + n3 * B.m[7];
+  const double gz = n1 * B.m[2] + n2 * B.m[5] + n3 * B.m[8];
+  const double g2 = gx * gx + gy * gy + gz * gz;
+  double2 v = make_double2(0.0, 0.0);
+  if (0.5 * g2 <= ecut4 && 2 * abs(n1) < N1 && 2 * abs(n2) < N2 && 2 * abs(n3) < N3) {
+    const int tot = N1 + N2 + N3;
+    double2 sf = make_double2(0.0, 0.0);
+    for (int I = 0; I < nat; ++I) {
+      const double2* p = ph + (size_t)I * tot;
+      sf = cadd(sf, cmul(cmul(p[j1], p[N1 + j2]), p[N1 + N2 + j3]));
+    }
+    double form = A * pow(kPi, 1.5) * a * a * a * exp(-g2 * a * a / 4.0);
+    form += g2 > 0.0 ? -4.0 * kPi * Z * exp(-g2 * rc * rc / 4.0) / g2 : kPi * Z * rc * rc;
+    v = cscale(sf, form / omega);
+  }
+  out[idx] = v;
+}
+
+__global__ void k_real_part(int n, const double2* __restrict__ z, double* __restrict__ r) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) r[i] = z[i].x;
+}
+
+int build_vloc(Ctx* c) {
+  double2* ph = phase_tables(c);
+  if (!ph) return PARO_ERR_CUDA;
+  double2* vg = static_cast<double2*>(ws_get(c, "grid_c0", (size_t)c->ngrid * sizeof(double2)));
+  if (!vg) return PARO_ERR_CUDA;
+  Mat3 B;
+  for (int i = 0; i < 9; ++i) B.m[i] = c->bmat[i];
+  k_vloc_g<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->N[0], c->N[1], c->N[2], B, 4.0 * c->ecut, c->Z, c->rc,
+                                                          c->A, c->a, c->omega, c->nat, ph, vg);
+  PARO_LAUNCH(c, "k_vloc_g");
+  int st = fft3d(c, vg, true);
+  if (st) return st;
+  if (!c->d_vloc) PARO_CU(c, cudaMalloc(&c->d_vloc, (size_t)c->ngrid * sizeof(double)));
+  k_real_part<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, vg, c->d_vloc);
+  PARO_LAUNCH(c, "k_real_part");
+  return PARO_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Kleinman-Bylander projector table beta[4 I + j][g], j = s, px, py, pz
+// ------------------------------------------------------------------------------------------------
+__global__ void k_beta(int npw, int nat, int N1, int N2, int N3, Mat3 B, double kx, double ky, double kz,
+                       const int* __restrict__ miller, const double2* __restrict__ ph,
+                       const double2* __restrict__ kph, double rc, double omega, double2* __restrict__ beta,
+                       float2* __restrict__ beta32) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int I = blockIdx.y;
+  if (g >= npw) return;
+  const int n1 = miller[3 * g], n2 = miller[3 * g + 1], n3 = miller[3 * g + 2];
+  const double qx = kx + n1 * B.m[0] + n2 * B.m[3] + n3 * B.m[6];
+  const double qy = ky + n1 * B.m[1] + n2 * B.m[4] + n3 * B.m[7];
+  const double qz = kz + n1 * B.m[2] + n2 * B.m[5] + n3 * B.m[8];
+  const double q2 = qx * qx + qy * qy + qz * qz;
+  const double gauss = exp(-q2 * rc * rc / 4.0);
+  const double pi15 = pow(kPi, 1.5);
+  const double n0 = 1.0 / sqrt(pow(kPi / 2.0, 1.5) * rc * rc * rc);
+  const double nn1 = 1.0 / sqrt(pow(kPi / 2.0, 1.5) * pow(rc, 5.0) / 4.0);
+  const double fs = n0 * pi15 * rc * rc * rc * gauss;
+  const double fp = nn1 * pi15 * pow(rc, 5.0) / 2.0 * gauss;  // p~_a = -i fp q_a
+  const int tot = N1 + N2 + N3;
+  const double2* p = ph + (size_t)I * tot;
+  const int j1 = n1 < 0 ? n1 + N1 : n1, j2 = n2 < 0 ? n2 + N2 : n2, j3 = n3 < 0 ? n3 + N3 : n3;
+  double2 phase = cmul(cmul(cmul(p[j1], p[N1 + j2]), p[N1 + N2 + j3]), kph[I]);
+  phase = cscale(phase, 1.0 / sqrt(omega));
+  const double2 vs = cscale(phase, fs);
+  const double2 mi = make_double2(phase.y, -phase.x);  // -i * phase
+  const double2 vx = cscale(mi, fp * qx), vy = cscale(mi, fp * qy), vz = cscale(mi, fp * qz);
+  const size_t row = (size_t)4 * I;
+  beta[(row + 0) * npw + g] = vs;
+  beta[(row + 1) * npw + g] = vx;
+  beta[(row + 2) * npw + g] = vy;
+  beta[(row + 3) * npw + g] = vz;
+  beta32[(row + 0) * npw + g] = make_float2((float)vs.x, (float)vs.y);
+  beta32[(row + 1) * npw + g] = make_float2((float)vx.x, (float)vx.y);
+  beta32[(row + 2) * npw + g] = make_float2((float)vy.x, (float)vy.y);
+  beta32[(row + 3) * npw + g] = make_float2((float)vz.x, (float)vz.y);
+}
+
+int build_beta(Ctx* c) {
+  double2* ph = phase_tables(c);
+  if (!ph) return PARO_ERR_CUDA;
+  Mat3 B;
+  for (int i = 0; i < 9; ++i) B.m[i] = c->bmat[i];
+  c->nproj = 4 * c->nat;
+  double2* kph = static_cast<double2*>(ws_get(c, "kphase", (size_t)c->nat * sizeof(double2)));
+  double* norms = static_cast<double*>(ws_get(c, "beta_norms", (size_t)c->nproj * sizeof(double)));
+  if (!kph || !norms) return PARO_ERR_CUDA;
+  c->beta_norm2_max.assign((size_t)c->nk * c->nat * 2, 0.0);
+  for (int ik = 0; ik < c->nk; ++ik) {
+    Basis& b = c->bases[ik];
+    std::vector<double2> hk(c->nat);
+    for (int I = 0; I < c->nat; ++I) {
+      double kr = 0;
+      for (int x = 0; x < 3; ++x) kr += b.kcart[x] * c->pos[I * 3 + x];
+      hk[I] = make_double2(std::cos(kr), -std::sin(kr));
+    }
+    PARO_CU(c, cudaMemcpyAsync(kph, hk.data(), c->nat * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    if (!b.d_beta) {
+      PARO_CU(c, cudaMalloc(&b.d_beta, (size_t)c->nproj * b.npw * sizeof(double2)));
+      PARO_CU(c, cudaMalloc(&b.d_beta32, (size_t)c->nproj * b.npw * sizeof(float2)));
+    }
+    k_beta<<<dim3((b.npw + 127) / 128, c->nat), 128, 0, c->stream>>>(b.npw, c->nat, c->N[0], c->N[1], c->N[2], B,
+                                                                    b.kcart[0], b.kcart[1], b.kcart[2], b.d_miller,
+                                                                    ph, kph, c->kb_rc, c->omega, b.d_beta,
+                                                                    b.d_beta32);
+    PARO_LAUNCH(c, "k_beta");
+    int st = band_norms<double>(c, c->nproj, b.npw, b.d_beta, b.npw, norms);
+    if (st) return st;
+    std::vector<double> h(c->nproj);
+    PARO_CU(c, cudaMemcpyAsync(h.data(), norms, c->nproj * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    PARO_CU(c, cudaStreamSynchronize(c->stream));
+    for (int I = 0; I < c->nat; ++I) {
+      double* m = &c->beta_norm2_max[((size_t)ik * c->nat + I) * 2];
+      m[0] = h[4 * I];
+      m[1] = std::max(h[4 * I + 1], std::max(h[4 * I + 2], h[4 * I + 3]));
+    }
+  }
+  return PARO_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// effective potential on the grid: plane-major copies scaled by 1/N_grid, min and mean
+// ------------------------------------------------------------------------------------------------
+__global__ void k_vplane(int N1, int N2, int N3, const double* __restrict__ v, double* __restrict__ vp,
+                         float* __restrict__ vp32, double inv_n) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // over the plane-major output
+  if (idx >= N1 * N2 * N3) return;
+  const int y = idx % N2, x = (idx / N2) % N1, z = idx / (N1 * N2);
+  const double val = v[((size_t)x * N2 + y) * N3 + z] * inv_n;
+  vp[idx] = val;
+  vp32[idx] = (float)val;
+}
+
+__global__ void k_min_sum(int n, const double* __restrict__ v, double* __restrict__ out) {
+  __shared__ double red[32];
+  __shared__ double rmin[32];
+  double s = 0.0, mn = 1e300;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    s += v[i];
+    mn = fmin(mn, v[i]);
+  }
+  s = block_sum(s, red);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  if ((threadIdx.x & 31) == 0) rmin[threadIdx.x >> 5] = mn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mn = fmin(mn, rmin[w]);
+    out[0] = s;
+    out[1] = fmin(mn, rmin[0]);
+  }
+}
+
+int set_veff_device(Ctx* c, const double* v_dev) {
+  if (!c->d_veff) {
+    PARO_CU(c, cudaMalloc(&c->d_veff, (size_t)c->ngrid * sizeof(double)));
+    PARO_CU(c, cudaMalloc(&c->d_vplane, (size_t)c->ngrid * sizeof(double)));
+    PARO_CU(c, cudaMalloc(&c->d_vplane32, (size_t)c->ngrid * sizeof(float)));
+  }
+  if (v_dev != c->d_veff)
+    PARO_CU(c, cudaMemcpyAsync(c->d_veff, v_dev, (size_t)c->ngrid * sizeof(double), cudaMemcpyDeviceToDevice,
+                               c->stream));
+  k_vplane<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->N[0], c->N[1], c->N[2], c->d_veff, c->d_vplane,
+                                                          c->d_vplane32, 1.0 / c->ngrid);
+  PARO_LAUNCH(c, "k_vplane");
+  double* ms = static_cast<double*>(ws_get(c, "vminsum", 2 * sizeof(double)));
+  if (!ms) return PARO_ERR_CUDA;
+  k_min_sum<<<1, 1024, 0, c->stream>>>(c->ngrid, c->d_veff, ms);
+  PARO_LAUNCH(c, "k_min_sum");
+  double h[2];
+  PARO_CU(c, cudaMemcpyAsync(h, ms, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  PARO_CU(c, cudaStreamSynchronize(c->stream));
+  c->vmean = h[0] / c->ngrid;
+  c->vmin = h[1];
+  c->have_veff = true;
+  return PARO_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Hartree and LDA-PZ
+// ------------------------------------------------------------------------------------------------
+__global__ void k_to_complex(int n, const double* __restrict__ r, double2* __restrict__ z) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[i] = make_double2(r[i], 0.0);
+}
+
+// rho_g (unnormalised forward FFT of rho) -> V_H(G) = 4 pi rho(G)/G^2 with rho(G) = rho_g / N; partial
+// sums of |rho(G)|^2 / G^2 per block for E_H.
+__global__ void k_hartree_g(int N1, int N2, int N3, Mat3 B, double2* __restrict__ z, double* __restrict__ part) {
+  __shared__ double red[32];
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ng = N1 * N2 * N3;
+  double e = 0.0;
+  if (idx < ng) {
+    const int j3 = idx % N3, j2 = (idx / N3) % N2, j1 = idx / (N2 * N3);
+    const int n1 = signed_index(j1, N1), n2 = signed_index(j2, N2), n3 = signed_index(j3, N3);
+    const double gx = n1 * B.m[0] + n2 * B.m[3] + n3 * B.m[6];
+    const double gy = n1 * B.m[1] + n2 * B.m[4] + n3 * B.m[7];
+    const double gz = n1 * B.m[2] + n2 * B.m[5] + n3 * B.m[8];
+    const double g2 = gx * gx + gy * gy + gz * gz;
+    double2 r = cscale(z[idx], 1.0 / ng);
+    if (g2 > 0.0) {
+      e = (r.x * r.x + r.y * r.y) / g2;
+      z[idx] = cscale(r, 4.0 * kPi / g2);
+    } else {
+      z[idx] = make_double2(0.0, 0.0);
+    }
+  }
+  e = block_sum(e, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = e;
+}
+
+__device__ __forceinline__ void lda_pz(double rho, double* eps, double* v) {
+  if (!(rho >= 1e-30)) { *eps = 0.0; *v = 0.0; return; }
+  const double pi = kPi;
+  const double ex = -0.75 * cbrt(3.0 * rho / pi);
+  const double vx = 4.0 / 3.0 * ex;
+  const double rs = cbrt(3.0 / (4.0 * pi * rho));
+  double ec, vc;
+  if (rs >= 1.0) {
+    const double s = sqrt(rs);
+    const double den = 1.0 + 1.0529 * s + 0.3334 * rs;
+    ec = -0.1423 / den;
+    vc = ec * (1.0 + 7.0 / 6.0 * 1.0529 * s + 4.0 / 3.0 * 0.3334 * rs) / den;
+  } else {
+    const double lr = log(rs);
+    ec = 0.0311 * lr - 0.048 + 0.0020 * rs * lr - 0.0116 * rs;
+    vc = 0.0311 * lr + (-0.048 - 0.0311 / 3.0) + 2.0 / 3.0 * 0.0020 * rs * lr + (2.0 * -0.0116 - 0.0020) / 3.0 * rs;
+  }
+  *eps = ex + ec;
+  *v = vx + vc;
+}
+
+__global__ void k_veff_combine(int n, const double* __restrict__ vloc, const double2* __restrict__ vh,
+                               const double* __restrict__ rho, double* __restrict__ veff) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double e, v;
+  lda_pz(rho[i], &e, &v);
+  veff[i] = vloc[i] + vh[i].x + v;
+}
+
+static int sum_parts(Ctx* c, const double* part, int n, double* out) {
+  std::vector<double> h(n);
+  PARO_CU(c, cudaMemcpyAsync(h.data(), part, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PARO_CU(c, cudaStreamSynchronize(c->stream));
+  double s = 0;
+  for (int i = 0; i < n; ++i) s += h[i];
+  *out = s;
+  return PARO_OK;
+}
+
+static int hartree_energy_and_potential(Ctx* c, const double* rho_dev, double2* z, double* eh) {
+  Mat3 B;
+  for (int i = 0; i < 9; ++i) B.m[i] = c->bmat[i];
+  const int nblk = (c->ngrid + 255) / 256;
+  double* part = static_cast<double*>(ws_get(c, "hartree_part", (size_t)nblk * sizeof(double)));
+  if (!part) return PARO_ERR_CUDA;
+  k_to_complex<<<nblk, 256, 0, c->stream>>>(c->ngrid, rho_dev, z);
+  PARO_LAUNCH(c, "k_to_complex");
+  int st = fft3d(c, z, false);
+  if (st) return st;
+  k_hartree_g<<<nblk, 256, 0, c->stream>>>(c->N[0], c->N[1], c->N[2], B, z, part);
+  PARO_LAUNCH(c, "k_hartree_g");
+  st = fft3d(c, z, true);
+  if (st) return st;
+  double s = 0;
+  st = sum_parts(c, part, nblk, &s);
+  if (st) return st;
+  *eh = 0.5 * c->omega * 4.0 * kPi * s;
+  return PARO_OK;
+}
+
+int veff_from_density(Ctx* c, const double* rho_dev, double* eh_out, double* exc_out) {
+  (void)exc_out;
+  if (!c->have_pp) return fail(c, PARO_ERR_STATE, "no local pseudopotential set");
+  double2* z = static_cast<double2*>(ws_get(c, "grid_c0", (size_t)c->ngrid * sizeof(double2)));
+  double* v = static_cast<double*>(ws_get(c, "grid_r0", (size_t)c->ngrid * sizeof(double)));
+  if (!z || !v) return PARO_ERR_CUDA;
+  double eh = 0;
+  int st = hartree_energy_and_potential(c, rho_dev, z, &eh);
+  if (st) return st;
+  k_veff_combine<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, c->d_vloc, z, rho_dev, v);
+  PARO_LAUNCH(c, "k_veff_combine");
+  if (eh_out) *eh_out = eh;
+  return set_veff_device(c, v);
+}
+
+// ------------------------------------------------------------------------------------------------
+// density of occupied orbitals: pass 1 (z inverse) then, per (plane, band group), the inverse plane
+// FFT and sum of w |psi(r)|^2; partial planes per group are reduced in a fixed order.
+// ------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(512, 1) k_plane_density(const cplx<T>* __restrict__ S, int ncol, int nbands, int gsize,
+                                const int* __restrict__ col_x, const int* __restrict__ col_y,
+                                const int* __restrict__ xrows, int nxr, FftPlan px, FftPlan py,
+                                const cplx<T>* __restrict__ twx, const cplx<T>* __restrict__ twy, double wfac,
+                                double* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N1 = px.n, N2 = py.n;
+  double* acc = reinterpret_cast<double*>(smem_raw);
+  cplx<T>* tx = reinterpret_cast<cplx<T>*>(acc + N1 * N2);
+  cplx<T>* ty = tx + N1;
+  cplx<T>* P = ty + N2;
+  const int z = blockIdx.x, grp = blockIdx.y, N3 = gridDim.x;
+  for (int i = threadIdx.x; i < N1; i += blockDim.x) tx[i] = twx[i];
+  for (int i = threadIdx.x; i < N2; i += blockDim.x) ty[i] = twy[i];
+  for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) acc[i] = 0.0;
+  const int b0 = grp * gsize, b1 = min(nbands, b0 + gsize);
+  for (int b = b0; b < b1; ++b) {
+    for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) P[i] = mk<T>(0, 0);
+    __syncthreads();
+    const cplx<T>* Sz = S + ((size_t)b * N3 + z) * ncol;
+    for (int cc = threadIdx.x; cc < ncol; cc += blockDim.x) P[col_x[cc] * N2 + col_y[cc]] = Sz[cc];
+    __syncthreads();
+    fft_lines<T, true, false>(P, py, nxr, 1, LinesMapped{xrows, N2}, ty);
+    fft_lines<T, true, true>(P, px, N2, N2, LinesDirect{1}, tx);
+    for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) {
+      const double re = P[i].x, im = P[i].y;
+      acc[i] += re * re + im * im;
+    }
+    __syncthreads();
+  }
+  double* out = part + ((size_t)grp * N3 + z) * N1 * N2;
+  for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) out[i] = acc[i] * wfac;
+}
+
+// rho[x][y][z] += sum_g part[g][z][x][y]
+__global__ void k_density_reduce(int N1, int N2, int N3, int ngrp, const double* __restrict__ part,
+                                 double* __restrict__ rho, int accumulate) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // C order output
+  if (idx >= N1 * N2 * N3) return;
+  const int z = idx % N3, y = (idx / N3) % N2, x = idx / (N2 * N3);
+  const size_t pl = (size_t)z * N1 * N2 + (size_t)x * N2 + y;
+  double s = 0.0;
+  for (int g = 0; g < ngrp; ++g) s += part[(size_t)g * N1 * N2 * N3 + pl];
+  rho[idx] = accumulate ? rho[idx] + s : s;
+}
+
+int density(Ctx* c, const double2* const* psis, double* rho_dev) {
+  const int N1 = c->N[0], N2 = c->N[1], N3 = c->N[2];
+  const int gsize = 8;
+  const int ngrp = (c->nocc + gsize - 1) / gsize;
+  double* part = static_cast<double*>(ws_get(c, "dens_part", (size_t)ngrp * c->ngrid * sizeof(double)));
+  if (!part) return PARO_ERR_CUDA;
+  const size_t smem = (size_t)N1 * N2 * sizeof(double) + (size_t)(N1 + N2 + N1 * N2) * sizeof(double2);
+  if (smem > 227 * 1024) return fail(c, PARO_ERR_ARG, "density: plane too large for shared memory in FP64");
+  PARO_CU(c, cudaFuncSetAttribute(k_plane_density<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  const int threads = N1 * N2 > 96 * 96 ? 1024 : 512;
+  for (int ik = 0; ik < c->nk; ++ik) {
+    const Basis& B = c->bases[ik];
+    double2* S = static_cast<double2*>(ws_get(c, "sticks64", (size_t)c->nocc * N3 * B.ncol * sizeof(double2)));
+    if (!S) return PARO_ERR_CUDA;
+    int st = sticks_inverse(c, ik, c->nocc, psis[ik], S);
+    if (st) return st;
+    k_plane_density<double><<<dim3(N3, ngrp), threads, smem, c->stream>>>(
+        S, B.ncol, c->nocc, gsize, B.d_col_x, B.d_col_y, B.d_xrows, B.nxr, c->plan[0], c->plan[1], c->d_tw64[0],
+        c->d_tw64[1], 2.0 * c->kw[ik] / c->omega, part);
+    PARO_LAUNCH(c, "k_plane_density");
+    k_density_reduce<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(N1, N2, N3, ngrp, part, rho_dev, ik > 0);
+    PARO_LAUNCH(c, "k_density_reduce");
+  }
+  return PARO_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// energy terms
+// ------------------------------------------------------------------------------------------------
+// per block partial sums of w_b * sum_g kin_g |c_bg|^2 over blocks (band, chunk)
+__global__ void k_kinetic(int npw, const double2* __restrict__ psi, const double* __restrict__ kin, double* part) {
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  double s = 0.0;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+    const double2 v = psi[(size_t)b * npw + g];
+    s += kin[g] * (v.x * v.x + v.y * v.y);
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[b] = s;
+}
+
+// sum_p D_p |P[p][b]|^2 per band b
+__global__ void k_nonlocal(int nproj, int nb, const double2* __restrict__ P, const double* __restrict__ dvec,
+                           double* part) {
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  double s = 0.0;
+  for (int p = threadIdx.x; p < nproj; p += blockDim.x) {
+    const double2 v = P[(size_t)p * nb + b];
+    s += dvec[p] * (v.x * v.x + v.y * v.y);
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[b] = s;
+}
+
+// per block partials of sum V_loc rho and sum rho eps_xc(rho)
+__global__ void k_grid_energies(int n, const double* __restrict__ vloc, const double* __restrict__ rho,
+                                double* __restrict__ part) {
+  __shared__ double red[32];
+  double sl = 0.0, sx = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double e, v;
+    lda_pz(rho[i], &e, &v);
+    sl += vloc[i] * rho[i];
+    sx += rho[i] * e;
+  }
+  sl = block_sum(sl, red);
+  if (threadIdx.x == 0) part[2 * blockIdx.x] = sl;
+  sx = block_sum(sx, red);
+  if (threadIdx.x == 0) part[2 * blockIdx.x + 1] = sx;
+}
+
+int energy_terms(Ctx* c, const double* rho_dev, double terms[7]) {
+  for (int i = 0; i < 7; ++i) terms[i] = 0.0;
+  double* part = static_cast<double*>(ws_get(c, "energy_part", (size_t)std::max(c->nb, 512) * 2 * sizeof(double)));
+  if (!part) return PARO_ERR_CUDA;
+  for (int ik = 0; ik < c->nk; ++ik) {
+    const Basis& B = c->bases[ik];
+    k_kinetic<<<c->nocc, 256, 0, c->stream>>>(B.npw, B.d_psi, B.d_kin, part);
+    PARO_LAUNCH(c, "k_kinetic");
+    double s = 0;
+    int st = sum_parts(c, part, c->nocc, &s);
+    if (st) return st;
+    terms[PARO_E_KINETIC] += 2.0 * c->kw[ik] * s;
+    if (c->have_kb) {
+      double2* P = static_cast<double2*>(ws_get(c, "kb_proj", (size_t)c->nproj * c->nb * sizeof(double2)));
+      if (!P) return PARO_ERR_CUDA;
+      st = gemm_cn<double, double, double>(c, c->nproj, c->nocc, B.npw, B.d_beta, B.npw, B.d_psi, B.npw, P, c->nocc,
+                                          false);
+      if (st) return st;
+      k_nonlocal<<<c->nocc, 256, 0, c->stream>>>(c->nproj, c->nocc, P, c->d_dvec, part);
+      PARO_LAUNCH(c, "k_nonlocal");
+      st = sum_parts(c, part, c->nocc, &s);
+      if (st) return st;
+      terms[PARO_E_NONLOCAL] += 2.0 * c->kw[ik] * s;
+    }
+  }
+  const int nblk = 304;
+  k_grid_energies<<<nblk, 256, 0, c->stream>>>(c->ngrid, c->d_vloc, rho_dev, part);
+  PARO_LAUNCH(c, "k_grid_energies");
+  std::vector<double> h(2 * nblk);
+  PARO_CU(c, cudaMemcpyAsync(h.data(), part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PARO_CU(c, cudaStreamSynchronize(c->stream));
+  double sl = 0, sx = 0;
+  for (int i = 0; i < nblk; ++i) {
+    sl += h[2 * i];
+    sx += h[2 * i + 1];
+  }
+  const double dv = c->omega / c->ngrid;
+  terms[PARO_E_LOCAL] = dv * sl;
+  terms[PARO_E_XC] = dv * sx;
+  double2* z = static_cast<double2*>(ws_get(c, "grid_c0", (size_t)c->ngrid * sizeof(double2)));
+  if (!z) return PARO_ERR_CUDA;
+  double eh = 0;
+  int st = hartree_energy_and_potential(c, rho_dev, z, &eh);
+  if (st) return st;
+  terms[PARO_E_HARTREE] = eh;
+  terms[PARO_E_EWALD] = c->e_ewald;
+  terms[PARO_E_TOTAL] = terms[0] + terms[1] + terms[2] + terms[3] + terms[4] + terms[5];
+  return PARO_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Pulay (DIIS) mixing: rho_new = sum_i a_i (rho_in^i + beta R^i), a minimising ||sum a_i R^i|| with
+// sum a_i = 1 over the stored history (a ring buffer of depth <= pulay_cap).
+// ------------------------------------------------------------------------------------------------
+__global__ void k_pulay_push(int n, const double* __restrict__ rin, const double* __restrict__ rout,
+                             double* __restrict__ hr, double* __restrict__ hres) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  hr[i] = rin[i];
+  hres[i] = rout[i] - rin[i];
+}
+
+// part[blk][i*m + j] = block partial of <R_i, R_j> (i <= j)
+__global__ void k_pulay_dots(int n, int m, const double* __restrict__ hres, const int* __restrict__ slot,
+                             double* __restrict__ part) {
+  __shared__ double red[32];
+  for (int i = 0; i < m; ++i)
+    for (int j = i; j < m; ++j) {
+      const double* ri = hres + (size_t)slot[i] * n;
+      const double* rj = hres + (size_t)slot[j] * n;
+      double s = 0.0;
+      for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) s += ri[t] * rj[t];
+      s = block_sum(s, red);
+      if (threadIdx.x == 0) part[(size_t)blockIdx.x * m * m + i * m + j] = s;
+      __syncthreads();
+    }
+}
+
+// one thread: sum partials, build the bordered system, Gaussian elimination with partial pivoting
+__global__ void k_pulay_solve(int m, int nblk, const double* __restrict__ part, double* __restrict__ coef) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double a[17][18];
+  const int n = m + 1;
+  for (int i = 0; i < m; ++i)
+    for (int j = i; j < m; ++j) {
+      double s = 0.0;
+      for (int b = 0; b < nblk; ++b) s += part[(size_t)b * m * m + i * m + j];
+      a[i][j] = a[j][i] = s;
+    }
+  for (int i = 0; i < m; ++i) { a[i][m] = 1.0; a[m][i] = 1.0; a[i][n] = 0.0; }
+  a[m][m] = 0.0;
+  a[m][n] = 1.0;
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;
+    if (piv != col)
+      for (int k = 0; k <= n; ++k) { const double t = a[col][k]; a[col][k] = a[piv][k]; a[piv][k] = t; }
+    const double d = a[col][col];
+    for (int r = col + 1; r < n; ++r) {
+      const double f = a[r][col] / d;
+      for (int k = col; k <= n; ++k) a[r][k] -= f * a[col][k];
+    }
+  }
+  double x[17];
+  for (int r = n - 1; r >= 0; --r) {
+    double s = a[r][n];
+    for (int k = r + 1; k < n; ++k) s -= a[r][k] * x[k];
+    x[r] = s / a[r][r];
+  }
+  for (int i = 0; i < m; ++i) coef[i] = x[i];
+}
+
+__global__ void k_pulay_mix(int n, int m, const double* __restrict__ hr, const double* __restrict__ hres,
+                            const int* __restrict__ slot, const double* __restrict__ coef, double beta,
+                            double* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double s = 0.0;
+  for (int i = 0; i < m; ++i) {
+    const size_t o = (size_t)slot[i] * n + t;
+    s += coef[i] * (hr[o] + beta * hres[o]);
+  }
+  out[t] = s;
+}
+
+int pulay_mix(Ctx* c, const double* rho_out, int depth, double beta) {
+  if (depth < 1 || depth > 16) return fail(c, PARO_ERR_ARG, "pulay depth must be in [1, 16]");
+  const int n = c->ngrid;
+  if (!c->d_pulay_rho || c->pulay_cap != depth) {
+    if (c->d_pulay_rho) { cudaFree(c->d_pulay_rho); cudaFree(c->d_pulay_res); }
+    PARO_CU(c, cudaMalloc(&c->d_pulay_rho, (size_t)depth * n * sizeof(double)));
+    PARO_CU(c, cudaMalloc(&c->d_pulay_res, (size_t)depth * n * sizeof(double)));
+    c->pulay_cap = depth;
+    c->pulay_n = 0;
+    c->pulay_head = 0;
+  }
+  const int slot_new = c->pulay_head;
+  k_pulay_push<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->d_rho_in, rho_out, c->d_pulay_rho + (size_t)slot_new * n,
+                                                       c->d_pulay_res + (size_t)slot_new * n);
+  PARO_LAUNCH(c, "k_pulay_push");
+  c->pulay_head = (c->pulay_head + 1) % depth;
+  if (c->pulay_n < depth) ++c->pulay_n;
+  const int m = c->pulay_n;
+  std::vector<int> slots(m);
+  for (int i = 0; i < m; ++i) slots[i] = ((c->pulay_head - m + i) % depth + depth) % depth;  // oldest first
+  int* dslot = static_cast<int*>(ws_get(c, "pulay_slot", 16 * sizeof(int)));
+  const int nblk = 152;
+  double* part = static_cast<double*>(ws_get(c, "pulay_part", (size_t)nblk * 16 * 16 * sizeof(double)));
+  double* coef = static_cast<double*>(ws_get(c, "pulay_coef", 16 * sizeof(double)));
+  if (!dslot || !part || !coef) return PARO_ERR_CUDA;
+  PARO_CU(c, cudaMemcpyAsync(dslot, slots.data(), m * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  k_pulay_dots<<<nblk, 256, 0, c->stream>>>(n, m, c->d_pulay_res, dslot, part);
+  PARO_LAUNCH(c, "k_pulay_dots");
+  k_pulay_solve<<<1, 32, 0, c->stream>>>(m, nblk, part, coef);
+  PARO_LAUNCH(c, "k_pulay_solve");
+  k_pulay_mix<<<(n + 255) / 256, 256, 0, c->stream>>>(n, m, c->d_pulay_rho, c->d_pulay_res, dslot, coef, beta,
+                                                      c->d_rho_in);
+  PARO_LAUNCH(c, "k_pulay_mix");
+  // keep the host copy of slots alive until the copy above has been consumed
+  PARO_CU(c, cudaStreamSynchronize(c->stream));
+  return PARO_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Ewald energy of point ions Z in a neutralising background (host, FP64)
+// ------------------------------------------------------------------------------------------------
+double ewald(const Ctx* c) {
+  const double* L = c->lat;
+  const double omega = c->omega;
+  const double Z = c->Z;
+  const int nat = c->nat;
+  const double eta = std::sqrt(kPi) / std::cbrt(omega);
+  const double tol = 1e-16;
+  double rcut = 1.0;
+  while (std::erfc(eta * rcut) / rcut > tol) rcut *= 1.2;
+  int nmax[3];
+  for (int i = 0; i < 3; ++i) {
+    const double* u = L + 3 * ((i + 1) % 3);
+    const double* v = L + 3 * ((i + 2) % 3);
+    const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
+    const double h = omega / std::sqrt(cx * cx + cy * cy + cz * cz);  // layer spacing
+    nmax[i] = (int)std::ceil(rcut / h) + 1;
+  }
+  double ereal = 0;
+  for (int i = 0; i < nat; ++i)
+    for (int j = 0; j < nat; ++j)
+      for (int a = -nmax[0]; a <= nmax[0]; ++a)
+        for (int b = -nmax[1]; b <= nmax[1]; ++b)
+          for (int cc = -nmax[2]; cc <= nmax[2]; ++cc) {
+            double d[3];
+            for (int x = 0; x < 3; ++x)
+              d[x] = c->pos[i * 3 + x] - c->pos[j * 3 + x] + a * L[x] + b * L[3 + x] + cc * L[6 + x];
+            const double r = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            if (r > 1e-12 && r < rcut) ereal += 0.5 * Z * Z * std::erfc(eta * r) / r;
+          }
+  const double gcut = 2.0 * eta * std::sqrt(-std::log(tol));
+  int gm[3];
+  for (int i = 0; i < 3; ++i) {
+    const double len = std::sqrt(L[3 * i] * L[3 * i] + L[3 * i + 1] * L[3 * i + 1] + L[3 * i + 2] * L[3 * i + 2]);
+    gm[i] = (int)std::ceil(gcut * len / (2 * kPi)) + 1;
+  }
+  double erec = 0;
+  for (int a = -gm[0]; a <= gm[0]; ++a)
+    for (int b = -gm[1]; b <= gm[1]; ++b)
+      for (int cc = -gm[2]; cc <= gm[2]; ++cc) {
+        double g[3];
+        for (int x = 0; x < 3; ++x) g[x] = a * c->bmat[x] + b * c->bmat[3 + x] + cc * c->bmat[6 + x];
+        const double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+        if (g2 <= 0 || g2 >= gcut * gcut) continue;
+        double sr = 0, si = 0;
+        for (int I = 0; I < nat; ++I) {
+          const double ph = g[0] * c->pos[I * 3] + g[1] * c->pos[I * 3 + 1] + g[2] * c->pos[I * 3 + 2];
+          sr += Z * std::cos(ph);
+          si += Z * std::sin(ph);
+        }
+        erec += (sr * sr + si * si) * std::exp(-g2 / (4 * eta * eta)) / g2;
+      }
+  erec *= 2 * kPi / omega;
+  const double eself = -eta / std::sqrt(kPi) * nat * Z * Z;
+  const double ebg = -kPi * (nat * Z) * (nat * Z) / (2 * omega * eta * eta);
+  return ereal + erec + eself + ebg;
+}
+
+}  // namespace paro

@@ -1,0 +1,172 @@
+// Internal state of a libparo context and the host-side interfaces between its translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/paro.h"
+#include "paro_common.cuh"
+
+namespace paro {
+
+// Plane-wave basis of one k-point (Eq. e3) with the z-column ("stick") structure the FFT passes use.
+struct Basis {
+  int npw = 0;
+  double kfrac[3] = {0, 0, 0};
+  double kcart[3] = {0, 0, 0};
+  std::vector<int> miller;        // npw * 3, lexicographic (n1, n2, n3)
+  std::vector<double> kin;        // |k+G|^2 / 2
+  int ncol = 0;                   // sticks: distinct (n1, n2)
+  int nxr = 0;                    // distinct grid rows j1 holding sticks
+  int max_run = 0;
+  // device
+  int* d_miller = nullptr;
+  double* d_kin = nullptr;
+  float* d_kin32 = nullptr;
+  int* d_col_x = nullptr;         // grid row j1 of stick c
+  int* d_col_y = nullptr;         // grid column j2 of stick c
+  int* d_col_off = nullptr;       // first coefficient of stick c (ncol + 1 entries)
+  int* d_g_col = nullptr;         // stick of coefficient g
+  int* d_g_z = nullptr;           // grid index j3 of coefficient g
+  int* d_xrows = nullptr;         // the nxr rows j1 with sticks
+  double2* d_beta = nullptr;      // KB projectors, nproj x npw
+  float2* d_beta32 = nullptr;
+  double* d_prec_base = nullptr;  // |k+G|^2/2 (copy used by the preconditioner)
+  // orbitals
+  double2* d_psi = nullptr;       // n_bands x npw, orthonormal
+  double2* d_hpsi = nullptr;      // H psi of the current orbitals
+  std::vector<double> eps;        // Ritz values
+  std::vector<double> res;        // residual norms
+  bool have_psi = false;
+};
+
+struct Ctx {
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  // cell
+  double lat[9], bmat[9], omega = 0;
+  int nat = 0;
+  std::vector<double> pos;
+  double ecut = 0;
+  int nk = 1;
+  std::vector<double> kw;
+  int nb = 0, nocc = 0, prec = 0;
+  int N[3] = {0, 0, 0};
+  int ngrid = 0;
+  std::vector<Basis> bases;
+  int max_npw = 0;
+  FftPlan plan[3];
+  double2* d_tw64[3] = {nullptr, nullptr, nullptr};
+  float2* d_tw32[3] = {nullptr, nullptr, nullptr};
+  // pseudopotentials
+  bool have_pp = false;
+  double Z = 0, rc = 0, A = 0, a = 0;
+  double* d_vloc = nullptr;       // V_loc(r), C order
+  bool have_kb = false;
+  double kb_rc = 0;
+  std::vector<double> D;          // n_atoms * 2
+  int nproj = 0;
+  double* d_dvec = nullptr;       // D per projector
+  float* d_dvec32 = nullptr;
+  std::vector<double> beta_norm2_max;  // per (atom, l): max_j ||beta_Ij||^2 over k
+  // potential
+  bool have_veff = false;
+  double* d_veff = nullptr;       // V_eff(r), C order
+  double* d_vplane = nullptr;     // V_eff / N_grid, plane-major [z][x][y]
+  float* d_vplane32 = nullptr;
+  double vmean = 0, vmin = 0;
+  std::vector<double> sigma_k;    // PCG shift per k-point
+  double e_ewald = 0;
+  // SCF state
+  double* d_rho_in = nullptr;
+  bool have_rho = false;
+  int pulay_n = 0, pulay_head = 0, pulay_cap = 0;
+  double* d_pulay_rho = nullptr;  // pulay_cap x ngrid
+  double* d_pulay_res = nullptr;
+  double e_prev = 0;
+  int scf_iter = 0, scf_small = 0;
+  bool fft_configured[2] = {false, false};
+  // workspaces by name
+  std::map<std::string, std::pair<void*, size_t>> ws;
+};
+
+// Status helpers (api.cu)
+int fail(Ctx* c, int code, const std::string& msg);
+int cuda_fail(Ctx* c, cudaError_t e, const char* where);
+void* ws_get(Ctx* c, const char* name, size_t bytes);  // nullptr on failure (err set)
+
+#define PARO_CU(c, call)                                               \
+  do {                                                                 \
+    cudaError_t e__ = (call);                                          \
+    if (e__ != cudaSuccess) return ::paro::cuda_fail((c), e__, #call); \
+  } while (0)
+#define PARO_LAUNCH(c, what)                                                 \
+  do {                                                                       \
+    cudaError_t e__ = cudaGetLastError();                                    \
+    if (e__ != cudaSuccess) return ::paro::cuda_fail((c), e__, what);        \
+  } while (0)
+
+// ---- H psi (k_hpsi.cu) ----
+// hpsi = (H - shift) psi for nb bands, T = float or double; active: device int[nb] or nullptr.
+template <typename T>
+int apply_h(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* hpsi, double shift, const int* active);
+// Checks that the FFT passes support this grid / precision (register and shared-memory budgets).
+int check_fft_support(Ctx* c, int elem_bytes);
+
+// ---- dense complex linear algebra (k_linalg.cu) ----
+// C[m][n] = sum_k conj(A[m][k]) B[n][k]; A: M x K (lda), B: N x K (ldb); C: M x N (ldc) complex double.
+// Products accumulate in ACC inside a K-slice; slices are summed in double in a fixed order.
+// herm: A == B, only tiles with m-tile <= n-tile are computed, the rest mirrored.
+template <typename TA, typename TB, typename ACC>
+int gemm_cn(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb,
+            double2* C, int ldc, bool herm);
+// Y[m][n] = beta Y[m][n] + sum_k s_k W(k, m) X[k][n]; W: complex double, element (k, m) at W[k*ldw + m]
+// (or at W[m*ldw + k] when wt); s: device double[K] or nullptr (1); X: K x N (ldx) of TX;
+// Y: M x N (ldy) of TY; accumulation in TY.
+template <typename TX, typename TY>
+int gemm_wx(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, const double* s, const cplx<TX>* X,
+            int ldx, cplx<TY>* Y, int ldy, double beta);
+// Cholesky S = L L^H (n x n, row-major, device), then writes G = conj(L)^{-1} (lower) into g.
+int chol_inv(Ctx* c, int n, const double2* s, double2* g);
+// Hermitian eigensolver (one CTA): w ascending, v columns = eigenvectors.
+int eigh(Ctx* c, int n, const double2* a, double* w, double2* v);
+// Per-band partial sums: out[b] = sum_g Re conj(x[b][g]) y[b][g] (weights optional) — helpers.
+template <typename T>
+int band_norms(Ctx* c, int nb, int npw, const cplx<T>* x, int ldx, double* out_dev);
+// residual norms ||hpsi_b - eps_b psi_b||, eps device
+int residual_norms(Ctx* c, int nb, int npw, const double2* psi, const double2* hpsi, const double* eps_dev,
+                   double* out_dev);
+template <typename TS, typename TD>
+int convert(Ctx* c, size_t n, const cplx<TS>* src, cplx<TD>* dst);
+
+// ---- KB projectors (k_hpsi.cu) ----
+template <typename T>
+int kb_apply(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* hpsi);
+
+// ---- setup / SCF (k_scf.cu) ----
+int build_vloc(Ctx* c);                   // d_vloc from (Z, rc, A, a)
+int build_beta(Ctx* c);                   // d_beta per k
+int set_veff_device(Ctx* c, const double* v_dev);  // vplane, sigma, mean
+int veff_from_density(Ctx* c, const double* rho_dev, double* eh_out, double* exc_out);
+int density(Ctx* c, const double2* const* psis, double* rho_dev);  // from given orbitals (occupied)
+int energy_terms(Ctx* c, const double* rho_dev, double terms[7]);
+int pulay_mix(Ctx* c, const double* rho_out, int depth, double beta);
+int fft3d(Ctx* c, double2* data, bool inverse);  // in place, unnormalised, C order grid
+double ewald(const Ctx* c);
+
+int build_twiddles(Ctx* c);
+// pass 1 of H psi only (z-inverse FFT of the sticks), FP64, for the density
+int sticks_inverse(Ctx* c, int ik, int nb, const double2* psi, double2* S);
+
+// ---- batched PCG (k_pcg.cu) ----
+template <typename T>
+int pcg_run(Ctx* c, int ik, int nb, const cplx<T>* rhs, cplx<T>* x, bool x0_zero, double rel_tol, int max_it,
+            int* iters);
+template <typename T>
+int scale_rows(Ctx* c, int nb, int npw, const cplx<T>* x, const double* f_dev, cplx<T>* y);
+
+}  // namespace paro
