@@ -55,7 +55,7 @@ enum {
  *   precision PARO_FP64: every step in FP64. PARO_MIXED: FFTs, V.psi, the KB projector GEMMs and
  *             the inner PCG in FP32 (dot products accumulated in FP64); Gram, Cholesky, Rayleigh-Ritz,
  *             residual norms and energies in FP64.
- *   stream    cudaStream_t to enqueue on, or NULL for a stream owned by the context.
+ *   stream    cudaStream_t to enqueue all work on; NULL means the default stream.
  * The FFT grid is the smallest 2^a 3^b per axis with N_i > m_V,i + s_psi,i (m_V: largest |n_i| of the
  * density sphere |G|^2/2 <= 4 ecut; s_psi: span of n_i over every k's basis), so that V.psi is alias
  * free. Errors: PARO_ERR_ARG for non-positive sizes, singular lattice, n_occ > n_bands, n_bands > npw.
@@ -189,6 +189,28 @@ typedef struct {
  */
 int paro_scf_step(paro_ctx* ctx, const paro_scf_opts* opts, double energy[7], double* max_resid_out);
 int paro_scf(paro_ctx* ctx, const paro_scf_opts* opts, paro_scf_result* result);
+
+/*
+ * paro_set_state -- checkpoint restore: orbitals of k-point ik (n_bands x npw complex double, host or
+ * device) and their Ritz values (host double[n_bands]) taken verbatim, no orthonormalisation; H psi
+ * and the residual norms are recomputed under the current potential. The caller passes a state saved
+ * with paro_get_orbitals / paro_get_eigenvalues (orthonormal orbitals).
+ */
+int paro_set_state(paro_ctx* ctx, int ik, const void* psi, const double* eps, int on_device);
+
+/*
+ * Instrumentation (not part of the method). paro_profile(ctx, 1) starts recording a CUDA event pair
+ * on the context's stream around every launch of the named kernels (the three H psi passes, the KB
+ * apply, the GEMMs, Cholesky, eigensolver and the PCG vector kernels) and clears earlier records;
+ * paro_profile(ctx, 0) stops. paro_profile_read synchronises and returns the number of recorded
+ * launches of `name` ("*" for all) and their summed duration in ms; paro_profile_names writes the
+ * recorded names, comma separated, into buf[len]. paro_launch_count returns the number of kernels
+ * this context has launched since it was created.
+ */
+int paro_profile(paro_ctx* ctx, int enable);
+int paro_profile_read(paro_ctx* ctx, const char* name, int* count, double* total_ms);
+int paro_profile_names(paro_ctx* ctx, char* buf, int len);
+int paro_launch_count(const paro_ctx* ctx, long long* n);
 
 /* paro_last_error -- message of the last failed call on ctx (or of the last failed paro_create when
  * ctx is NULL); valid until the next call on the same context. */

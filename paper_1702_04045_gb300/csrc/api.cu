@@ -175,10 +175,11 @@ __global__ void k_hermitize(int n, double2* __restrict__ a) {
   a[(size_t)j * n + i] = make_double2(h.x, -h.y);
 }
 
-// Orthonormalise the nx rows of X (FP64, in place as Y = conj(L)^{-1} X) and take the Ritz pairs of
-// their span: H_sub = Y^H H Y, H_sub C = C diag(eps); psi = first nb rows of C^T Y, H psi = C^T (H Y).
-// Mixed precision applies H in FP32 (Y rounded to FP32) and keeps every reduction in FP64.
-static int project(Ctx* c, int ik, double2* X, int nx) {
+// Orthonormalise the nx rows of X (FP64, as Y = conj(L)^{-1} X; skipped when X is already
+// orthonormal) and take the Ritz pairs of their span: H_sub = Y^H H Y, H_sub C = C diag(eps);
+// psi = first nb rows of C^T Y, H psi = C^T (H Y). Mixed precision applies H in FP32 (Y rounded to
+// FP32) and keeps every reduction in FP64.
+static int project(Ctx* c, int ik, double2* X, int nx, bool orthonormal = false) {
   Basis& b = c->bases[ik];
   const int npw = b.npw, nb = c->nb;
   double2* S = static_cast<double2*>(ws_get(c, "proj_S", (size_t)nx * nx * sizeof(double2)));
@@ -189,23 +190,38 @@ static int project(Ctx* c, int ik, double2* X, int nx) {
   double* res = static_cast<double*>(ws_get(c, "proj_res", (size_t)nx * sizeof(double)));
   if (!S || !G || !Y || !HY || !w || !res) return PARO_ERR_CUDA;
   int st;
-  if ((st = gemm_cn<double, double, double>(c, nx, nx, npw, X, npw, X, npw, S, nx, true))) return st;
-  if ((st = chol_inv(c, nx, S, G))) return st;
-  if ((st = gemm_wx<double, double>(c, nx, npw, nx, G, nx, true, nullptr, X, npw, Y, npw, 0.0))) return st;
-  if (c->prec == PARO_MIXED) {
-    float2* Y32 = static_cast<float2*>(ws_get(c, "proj_Y32", (size_t)nx * npw * sizeof(float2)));
-    float2* HY32 = static_cast<float2*>(ws_get(c, "proj_HY32", (size_t)nx * npw * sizeof(float2)));
-    if (!Y32 || !HY32) return PARO_ERR_CUDA;
-    if ((st = convert<double, float>(c, (size_t)nx * npw, Y, Y32))) return st;
-    if ((st = apply_h<float>(c, ik, nx, Y32, HY32, 0.0, nullptr))) return st;
-    if ((st = convert<float, double>(c, (size_t)nx * npw, HY32, HY))) return st;
+  if (orthonormal) {
+    Y = X;
   } else {
-    if ((st = apply_h<double>(c, ik, nx, Y, HY, 0.0, nullptr))) return st;
+    {
+      ProfTag t(c, "gram");
+      if ((st = gemm_cn<double, double, double>(c, nx, nx, npw, X, npw, X, npw, S, nx, true))) return st;
+      if ((st = chol_inv(c, nx, S, G))) return st;
+    }
+    ProfTag t(c, "orth");
+    if ((st = gemm_wx<double, double>(c, nx, npw, nx, G, nx, true, nullptr, X, npw, Y, npw, 0.0))) return st;
   }
-  if ((st = gemm_cn<double, double, double>(c, nx, nx, npw, Y, npw, HY, npw, S, nx, false))) return st;
-  k_hermitize<<<(nx * nx + 255) / 256, 256, 0, c->stream>>>(nx, S);
-  PARO_LAUNCH(c, "k_hermitize");
-  if ((st = eigh(c, nx, S, w, G))) return st;  // G <- eigenvectors C
+  {
+    ProfTag t(c, "rr");
+    if (c->prec == PARO_MIXED) {
+      float2* Y32 = static_cast<float2*>(ws_get(c, "proj_Y32", (size_t)nx * npw * sizeof(float2)));
+      float2* HY32 = static_cast<float2*>(ws_get(c, "proj_HY32", (size_t)nx * npw * sizeof(float2)));
+      if (!Y32 || !HY32) return PARO_ERR_CUDA;
+      if ((st = convert<double, float>(c, (size_t)nx * npw, Y, Y32))) return st;
+      if ((st = apply_h<float>(c, ik, nx, Y32, HY32, 0.0, nullptr))) return st;
+      if ((st = convert<float, double>(c, (size_t)nx * npw, HY32, HY))) return st;
+    } else {
+      if ((st = apply_h<double>(c, ik, nx, Y, HY, 0.0, nullptr))) return st;
+    }
+  }
+  {
+    ProfTag t(c, "hsub");
+    if ((st = gemm_cn<double, double, double>(c, nx, nx, npw, Y, npw, HY, npw, S, nx, false))) return st;
+    k_hermitize<<<(nx * nx + 255) / 256, 256, 0, c->stream>>>(nx, S);
+    PARO_LAUNCH(c, "k_hermitize");
+    if ((st = eigh(c, nx, S, w, G))) return st;  // G <- eigenvectors C
+  }
+  ProfTag t(c, "rot");
   if ((st = gemm_wx<double, double>(c, nb, npw, nx, G, nx, false, nullptr, Y, npw, b.d_psi, npw, 0.0))) return st;
   if ((st = gemm_wx<double, double>(c, nb, npw, nx, G, nx, false, nullptr, HY, npw, b.d_hpsi, npw, 0.0))) return st;
   if ((st = residual_norms(c, nb, npw, b.d_psi, b.d_hpsi, w, res))) return st;
@@ -319,6 +335,25 @@ static int build_alg2_basis(Ctx* c, int ik, double2* E, double2* X, int* nx_out)
   return PARO_OK;
 }
 
+cudaEvent_t prof_begin(Ctx* c) {
+  if (!c->prof) return nullptr;
+  cudaEvent_t a = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess) return nullptr;
+  cudaEventRecord(a, c->stream);
+  return a;
+}
+
+void prof_end(Ctx* c, const char* name, cudaEvent_t a) {
+  if (!c->prof || !a) return;
+  cudaEvent_t b = nullptr;
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return;
+  }
+  cudaEventRecord(b, c->stream);
+  c->prof_ev.push_back({c->prof_tag ? std::string(c->prof_tag) + ":" + name : std::string(name), a, b});
+}
+
 static double max_occ_resid(const Ctx* c) {
   double m = 0;
   for (const Basis& b : c->bases)
@@ -353,8 +388,12 @@ static int orthonormalize(Ctx* c, int ik, double2* X, int nx) {
   double2* Y = static_cast<double2*>(ws_get(c, "proj_Y", (size_t)nx * npw * sizeof(double2)));
   if (!S || !G || !Y) return PARO_ERR_CUDA;
   int st;
-  if ((st = gemm_cn<double, double, double>(c, nx, nx, npw, X, npw, X, npw, S, nx, true))) return st;
-  if ((st = chol_inv(c, nx, S, G))) return st;
+  {
+    ProfTag t(c, "gram");
+    if ((st = gemm_cn<double, double, double>(c, nx, nx, npw, X, npw, X, npw, S, nx, true))) return st;
+    if ((st = chol_inv(c, nx, S, G))) return st;
+  }
+  ProfTag t(c, "orth");
   if ((st = gemm_wx<double, double>(c, nx, npw, nx, G, nx, true, nullptr, X, npw, Y, npw, 0.0))) return st;
   PARO_CU(c, cudaMemcpyAsync(X, Y, (size_t)nx * npw * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
   return PARO_OK;
@@ -422,16 +461,8 @@ int paro_create(paro_ctx** out, const double lattice[9], int n_atoms, const doub
     c->err = "paro_create: k-point weights must sum to 1";
     return bail(PARO_ERR_ARG);
   }
-  if (stream) {
-    c->stream = static_cast<cudaStream_t>(stream);
-  } else {
-    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) {
-      cuda_fail(c, e, "cudaStreamCreate");
-      return bail(PARO_ERR_CUDA);
-    }
-    c->own_stream = true;
-  }
+  c->stream = static_cast<cudaStream_t>(stream);  // NULL: the default stream
+  c->own_stream = false;
   // bases and the FFT grid: N_i = smallest 2^a 3^b above m_V,i + s_psi,i
   c->bases.resize(n_k);
   int span[3] = {0, 0, 0}, mv[3] = {0, 0, 0};
@@ -496,6 +527,10 @@ void paro_destroy(paro_ctx* ctx) {
   for (void* p : ps)
     if (p) cudaFree(p);
   for (auto& kv : c->ws) cudaFree(kv.second.first);
+  for (auto& e : c->prof_ev) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete ctx;
 }
@@ -773,15 +808,21 @@ int paro_scf_step(paro_ctx* ctx, const paro_scf_opts* o, double energy[7], doubl
   if (!rho_out) return PARO_ERR_CUDA;
   std::vector<const double2*> dens_src(c->nk);
   for (int ik = 0; ik < c->nk; ++ik) dens_src[ik] = o->alg == PARO_ALG1 ? xs[ik] : c->bases[ik].d_psi;
-  if ((st = density(c, dens_src.data(), rho_out))) return st;
-  if ((st = pulay_mix(c, rho_out, o->pulay_depth, o->pulay_beta))) return st;
-  if ((st = veff_from_density(c, c->d_rho_in, nullptr, nullptr))) return st;
+  {
+    ProfTag t(c, "mix");
+    if ((st = density(c, dens_src.data(), rho_out))) return st;
+    if ((st = pulay_mix(c, rho_out, o->pulay_depth, o->pulay_beta))) return st;
+    if ((st = veff_from_density(c, c->d_rho_in, nullptr, nullptr))) return st;
+  }
   update_sigma(c);
-  // step 4: Rayleigh-Ritz with V(rho_in^{n+1/2})
+  // step 4: Rayleigh-Ritz with V(rho_in^{n+1/2}) in the already orthonormal span
   for (int ik = 0; ik < c->nk; ++ik)
-    if ((st = project(c, ik, xs[ik], nxs[ik]))) return st;
+    if ((st = project(c, ik, xs[ik], nxs[ik], true))) return st;
   double terms[7];
-  if ((st = paro_energy(ctx, terms))) return st;
+  {
+    ProfTag t(c, "energy");
+    if ((st = paro_energy(ctx, terms))) return st;
+  }
   if (energy) std::copy(terms, terms + 7, energy);
   if (max_resid_out) *max_resid_out = max_occ_resid(c);
   const double e = terms[PARO_E_TOTAL];
@@ -791,6 +832,88 @@ int paro_scf_step(paro_ctx* ctx, const paro_scf_opts* o, double energy[7], doubl
     c->scf_small = 0;
   c->e_prev = e;
   ++c->scf_iter;
+  return PARO_OK;
+}
+
+int paro_set_state(paro_ctx* ctx, int ik, const void* psi, const double* eps, int on_device) {
+  CTX_CHECK(ctx);
+  if (ik < 0 || ik >= c->nk || !psi || !eps) return fail(c, PARO_ERR_ARG, "paro_set_state: bad argument");
+  if (!c->have_veff) return fail(c, PARO_ERR_STATE, "no effective potential set");
+  Basis& b = c->bases[ik];
+  int st = alloc_orbitals(c, b);
+  if (st) return st;
+  const size_t bytes = (size_t)c->nb * b.npw * sizeof(double2);
+  PARO_CU(c, cudaMemcpyAsync(b.d_psi, psi, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             c->stream));
+  b.eps.assign(eps, eps + c->nb);
+  double* w = static_cast<double*>(ws_get(c, "state_eps", (size_t)c->nb * sizeof(double)));
+  double* res = static_cast<double*>(ws_get(c, "state_res", (size_t)c->nb * sizeof(double)));
+  if (!w || !res) return PARO_ERR_CUDA;
+  PARO_CU(c, cudaMemcpyAsync(w, b.eps.data(), c->nb * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (c->prec == PARO_MIXED) {
+    float2* p32 = static_cast<float2*>(ws_get(c, "state_p32", (size_t)c->nb * b.npw * sizeof(float2)));
+    float2* h32 = static_cast<float2*>(ws_get(c, "state_h32", (size_t)c->nb * b.npw * sizeof(float2)));
+    if (!p32 || !h32) return PARO_ERR_CUDA;
+    if ((st = convert<double, float>(c, (size_t)c->nb * b.npw, b.d_psi, p32))) return st;
+    if ((st = apply_h<float>(c, ik, c->nb, p32, h32, 0.0, nullptr))) return st;
+    if ((st = convert<float, double>(c, (size_t)c->nb * b.npw, h32, b.d_hpsi))) return st;
+  } else if ((st = apply_h<double>(c, ik, c->nb, b.d_psi, b.d_hpsi, 0.0, nullptr))) {
+    return st;
+  }
+  if ((st = residual_norms(c, c->nb, b.npw, b.d_psi, b.d_hpsi, w, res))) return st;
+  b.res.resize(c->nb);
+  PARO_CU(c, cudaMemcpyAsync(b.res.data(), res, c->nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PARO_CU(c, cudaStreamSynchronize(c->stream));
+  b.have_psi = true;
+  return PARO_OK;
+}
+
+int paro_profile(paro_ctx* ctx, int enable) {
+  CTX_CHECK(ctx);
+  cudaStreamSynchronize(c->stream);
+  for (auto& e : c->prof_ev) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  c->prof_ev.clear();
+  c->prof = enable != 0;
+  return PARO_OK;
+}
+
+int paro_profile_read(paro_ctx* ctx, const char* name, int* count, double* total_ms) {
+  CTX_CHECK(ctx);
+  if (!name || !count || !total_ms) return PARO_ERR_ARG;
+  PARO_CU(c, cudaStreamSynchronize(c->stream));
+  int n = 0;
+  double t = 0;
+  for (auto& e : c->prof_ev) {
+    if (e.name != name && std::strcmp(name, "*") != 0) continue;
+    float ms = 0;
+    PARO_CU(c, cudaEventElapsedTime(&ms, e.a, e.b));
+    ++n;
+    t += ms;
+  }
+  *count = n;
+  *total_ms = t;
+  return PARO_OK;
+}
+
+int paro_profile_names(paro_ctx* ctx, char* buf, int len) {
+  CTX_CHECK(ctx);
+  if (!buf || len < 1) return PARO_ERR_ARG;
+  std::vector<std::string> names;
+  for (auto& e : c->prof_ev)
+    if (std::find(names.begin(), names.end(), e.name) == names.end()) names.push_back(e.name);
+  std::string s;
+  for (auto& n : names) s += (s.empty() ? "" : ",") + n;
+  std::strncpy(buf, s.c_str(), len - 1);
+  buf[len - 1] = 0;
+  return PARO_OK;
+}
+
+int paro_launch_count(const paro_ctx* ctx, long long* n) {
+  if (!ctx || !n) return PARO_ERR_ARG;
+  *n = ctx->c.launches;
   return PARO_OK;
 }
 

@@ -180,20 +180,32 @@ int apply_h(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* hpsi, double sh
   cplx<T>* S = static_cast<cplx<T>*>(ws_get(c, sizeof(T) == 8 ? "sticks64" : "sticks32", sbytes));
   if (!S) return PARO_ERR_CUDA;
   const dim3 gz((B.ncol + kStickBatch - 1) / kStickBatch, nb);
+  const bool f64 = sizeof(T) == 8;
+  cudaEvent_t ev = prof_begin(c);
   k_zpass_inv<T><<<gz, kZThreads, zpass_smem(c, eb), c->stream>>>(psi, B.npw, S, B.d_col_off, B.d_g_col, B.d_g_z,
                                                                   B.ncol, c->plan[2], tw_of<T>(c, 2), active,
                                                                   kStickBatch);
   PARO_LAUNCH(c, "k_zpass_inv");
+  prof_end(c, f64 ? "k_zpass_inv<f64>" : "k_zpass_inv<f32>", ev);
+  ev = prof_begin(c);
   k_plane<T><<<dim3(c->N[2], nb), plane_threads(c), plane_smem(c, eb), c->stream>>>(
       S, B.ncol, B.d_col_x, B.d_col_y, B.d_xrows, B.nxr, c->plan[0], c->plan[1], tw_of<T>(c, 0), tw_of<T>(c, 1),
       vplane_of<T>(c), active);
   PARO_LAUNCH(c, "k_plane");
+  prof_end(c, f64 ? "k_plane<f64>" : "k_plane<f32>", ev);
+  ev = prof_begin(c);
   k_zpass_fwd<T><<<gz, kZThreads, zpass_smem(c, eb), c->stream>>>(S, psi, B.npw, hpsi, B.npw, kin_of<T>(B),
                                                                   (T)shift, B.d_col_off, B.d_g_col, B.d_g_z,
                                                                   B.ncol, c->plan[2], tw_of<T>(c, 2), active,
                                                                   kStickBatch);
   PARO_LAUNCH(c, "k_zpass_fwd");
-  if (c->have_kb) return kb_apply<T>(c, ik, nb, psi, hpsi);
+  prof_end(c, f64 ? "k_zpass_fwd<f64>" : "k_zpass_fwd<f32>", ev);
+  if (c->have_kb) {
+    ev = prof_begin(c);
+    int st2 = kb_apply<T>(c, ik, nb, psi, hpsi);
+    prof_end(c, f64 ? "kb_apply<f64>" : "kb_apply<f32>", ev);
+    return st2;
+  }
   return PARO_OK;
 }
 

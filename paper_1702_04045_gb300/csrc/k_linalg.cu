@@ -93,9 +93,11 @@ int gemm_cn(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, const cplx<
   if (K == 0) {
     PARO_CU(c, cudaMemsetAsync(part, 0, (size_t)M * N * sizeof(double2), c->stream));
   } else {
+    cudaEvent_t ev = prof_begin(c);
     k_gemm_cn<TA, TB, ACC><<<dim3(tiles_n, tiles_m, nz), 256, 0, c->stream>>>(M, N, K, kslice, A, lda, B, ldb, part,
                                                                               herm ? 1 : 0);
     PARO_LAUNCH(c, "k_gemm_cn");
+    prof_end(c, sizeof(ACC) == 8 ? "k_gemm_cn<f64>" : "k_gemm_cn<f32>", ev);
   }
   k_reduce_parts<<<(M * N + 255) / 256, 256, 0, c->stream>>>(M, N, K == 0 ? 1 : nz, part, C, ldc, herm ? 1 : 0);
   PARO_LAUNCH(c, "k_reduce_parts");
@@ -162,9 +164,11 @@ template <typename TX, typename TY>
 int gemm_wx(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, const double* s, const cplx<TX>* X,
             int ldx, cplx<TY>* Y, int ldy, double beta) {
   if (M <= 0 || N <= 0) return PARO_OK;
+  cudaEvent_t ev = prof_begin(c);
   k_gemm_wx<TX, TY><<<dim3((N + 63) / 64, (M + 31) / 32), 256, 0, c->stream>>>(M, N, K, W, ldw, wt ? 1 : 0, s, X,
                                                                                ldx, Y, ldy, beta);
   PARO_LAUNCH(c, "k_gemm_wx");
+  prof_end(c, sizeof(TY) == 8 ? "k_gemm_wx<f64>" : "k_gemm_wx<f32>", ev);
   return PARO_OK;
 }
 
@@ -224,8 +228,10 @@ int chol_inv(Ctx* c, int n, const double2* s, double2* g) {
   double2* L = static_cast<double2*>(ws_get(c, "chol_L", (size_t)n * n * sizeof(double2)));
   int* info = static_cast<int*>(ws_get(c, "chol_info", sizeof(int)));
   if (!L || !info) return PARO_ERR_CUDA;
+  cudaEvent_t ev = prof_begin(c);
   k_chol_inv<<<1, 1024, 0, c->stream>>>(n, s, L, g, info);
   PARO_LAUNCH(c, "k_chol_inv");
+  prof_end(c, "k_chol_inv", ev);
   int h = 0;
   PARO_CU(c, cudaMemcpyAsync(&h, info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   PARO_CU(c, cudaStreamSynchronize(c->stream));
@@ -458,8 +464,10 @@ int eigh(Ctx* c, int n, const double2* a, double* w, double2* v) {
   int threads = ((n + 31) / 32) * 32;
   if (threads < 256) threads = 256;
   if (threads > 1024) threads = 1024;
+  cudaEvent_t ev = prof_begin(c);
   k_eigh<<<1, threads, smem, c->stream>>>(n, a, A, Z, w, v, dw, info);
   PARO_LAUNCH(c, "k_eigh");
+  prof_end(c, "k_eigh", ev);
   int h = 0;
   PARO_CU(c, cudaMemcpyAsync(&h, info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   PARO_CU(c, cudaStreamSynchronize(c->stream));

@@ -192,6 +192,7 @@ template <> const float* kin_ptr<float>(const Basis& b) { return b.d_kin32; }
 template <typename T>
 int pcg_run(Ctx* c, int ik, int nb, const cplx<T>* rhs, cplx<T>* x, bool x0_zero, double rel_tol, int max_it,
             int* iters) {
+  ProfTag tag(c, "pcg");
   const Basis& B = c->bases[ik];
   const int npw = B.npw;
   const int nchunk = (npw + kChunk - 1) / kChunk;
@@ -230,6 +231,7 @@ int pcg_run(Ctx* c, int ik, int nb, const cplx<T>* rhs, cplx<T>* x, bool x0_zero
   for (int it = 0; it < max_it && hflags[0] > 0; ++it) {
     st = apply_h<T>(c, ik, nb, p, ap, sigma, active);
     if (st) return st;
+    cudaEvent_t ev = prof_begin(c);
     k_pcg_dot<T><<<gv, kVT, 0, c->stream>>>(npw, nchunk, p, ap, active, prz);
     PARO_LAUNCH(c, "k_pcg_dot");
     k_pcg_band_alpha<<<tb, 128, 0, c->stream>>>(nb, nchunk, prz, rz, active, alpha, flags + 1);
@@ -243,6 +245,7 @@ int pcg_run(Ctx* c, int ik, int nb, const cplx<T>* rhs, cplx<T>* x, bool x0_zero
     PARO_LAUNCH(c, "k_pcg_band_beta");
     k_pcg_pupdate<T><<<gv, kVT, 0, c->stream>>>(npw, p, r, kin_ptr<T>(B), pshift, beta, still);
     PARO_LAUNCH(c, "k_pcg_pupdate");
+    prof_end(c, f64 ? "pcg_vector<f64>" : "pcg_vector<f32>", ev);
     PARO_CU(c, cudaMemcpyAsync(active, still, nb * sizeof(int), cudaMemcpyDeviceToDevice, c->stream));
     PARO_CU(c, cudaMemcpyAsync(hflags, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     PARO_CU(c, cudaStreamSynchronize(c->stream));

@@ -471,10 +471,10 @@ __global__ void __launch_bounds__(512, 1) k_plane_density(const cplx<T>* __restr
                                 double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N1 = px.n, N2 = py.n;
-  double* acc = reinterpret_cast<double*>(smem_raw);
-  cplx<T>* tx = reinterpret_cast<cplx<T>*>(acc + N1 * N2);
+  cplx<T>* tx = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* ty = tx + N1;
   cplx<T>* P = ty + N2;
+  double* acc = reinterpret_cast<double*>(P + N1 * N2);
   const int z = blockIdx.x, grp = blockIdx.y, N3 = gridDim.x;
   for (int i = threadIdx.x; i < N1; i += blockDim.x) tx[i] = twx[i];
   for (int i = threadIdx.x; i < N2; i += blockDim.x) ty[i] = twy[i];

@@ -90,6 +90,15 @@ struct Ctx {
   double e_prev = 0;
   int scf_iter = 0, scf_small = 0;
   bool fft_configured[2] = {false, false};
+  // instrumentation: kernels launched, and CUDA-event pairs around named kernels while profiling
+  long long launches = 0;
+  bool prof = false;
+  struct ProfEv {
+    std::string name;
+    cudaEvent_t a, b;
+  };
+  std::vector<ProfEv> prof_ev;
+  const char* prof_tag = nullptr;  // phase prefix of recorded names ("pcg", "rr", ...)
   // workspaces by name
   std::map<std::string, std::pair<void*, size_t>> ws;
 };
@@ -108,7 +117,19 @@ void* ws_get(Ctx* c, const char* name, size_t bytes);  // nullptr on failure (er
   do {                                                                       \
     cudaError_t e__ = cudaGetLastError();                                    \
     if (e__ != cudaSuccess) return ::paro::cuda_fail((c), e__, what);        \
+    ++(c)->launches;                                                         \
   } while (0)
+
+// CUDA events around a named kernel launch on the context's stream (no-ops unless profiling).
+cudaEvent_t prof_begin(Ctx* c);
+void prof_end(Ctx* c, const char* name, cudaEvent_t a);
+// Scoped phase tag: names recorded inside become "tag:name".
+struct ProfTag {
+  Ctx* c;
+  const char* old;
+  ProfTag(Ctx* ctx, const char* tag) : c(ctx), old(ctx->prof_tag) { ctx->prof_tag = tag; }
+  ~ProfTag() { c->prof_tag = old; }
+};
 
 // ---- H psi (k_hpsi.cu) ----
 // hpsi = (H - shift) psi for nb bands, T = float or double; active: device int[nb] or nullptr.

@@ -26,7 +26,8 @@ EXPORTS = (
     "paro_create", "paro_set_local_pp", "paro_set_kb", "paro_set_veff", "paro_get_veff", "paro_set_density",
     "paro_grid", "paro_npw", "paro_miller", "paro_sigma", "paro_apply_h", "paro_solve_source",
     "paro_set_orbitals", "paro_get_orbitals", "paro_get_eigenvalues", "paro_get_residuals", "paro_step",
-    "paro_eigh", "paro_density", "paro_energy", "paro_scf_step", "paro_scf", "paro_last_error", "paro_destroy",
+    "paro_eigh", "paro_density", "paro_energy", "paro_scf_step", "paro_scf", "paro_set_state", "paro_profile",
+    "paro_profile_read", "paro_profile_names", "paro_launch_count", "paro_last_error", "paro_destroy",
 )
 
 _c_int_p = ctypes.POINTER(ctypes.c_int)
@@ -71,6 +72,11 @@ _SIGS = {
     "paro_energy": (ctypes.c_int, [_vp, _c_dbl_p]),
     "paro_scf_step": (ctypes.c_int, [_vp, ctypes.POINTER(ScfOpts), _c_dbl_p, _c_dbl_p]),
     "paro_scf": (ctypes.c_int, [_vp, ctypes.POINTER(ScfOpts), ctypes.POINTER(ScfResult)]),
+    "paro_set_state": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _c_dbl_p, ctypes.c_int]),
+    "paro_profile": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "paro_profile_read": (ctypes.c_int, [_vp, ctypes.c_char_p, _c_int_p, _c_dbl_p]),
+    "paro_profile_names": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.c_int]),
+    "paro_launch_count": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
     "paro_last_error": (ctypes.c_char_p, [_vp]),
     "paro_destroy": (None, [_vp]),
 }
@@ -286,6 +292,34 @@ class Context:
         r = ctypes.c_double()
         self._check(self.lib.paro_scf_step(self.h, ctypes.byref(o), _dptr(t), ctypes.byref(r)))
         return dict(zip(ENERGY_TERMS, t.tolist())), r.value
+
+    def set_state(self, psi, eps, ik=0):
+        """Restore orthonormal orbitals and their Ritz values verbatim (host array or CUDA tensor)."""
+        e = np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
+        if hasattr(psi, "is_cuda") and psi.is_cuda:
+            self._check(self.lib.paro_set_state(self.h, ik, _vp(psi.data_ptr()), _dptr(e), 1))
+        else:
+            a = np.ascontiguousarray(np.asarray(psi, dtype=np.complex128))
+            self._check(self.lib.paro_set_state(self.h, ik, _vp(a.ctypes.data), _dptr(e), 0))
+
+    def profile(self, enable=True):
+        self._check(self.lib.paro_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self, name="*"):
+        n = ctypes.c_int()
+        t = ctypes.c_double()
+        self._check(self.lib.paro_profile_read(self.h, name.encode(), ctypes.byref(n), ctypes.byref(t)))
+        return n.value, t.value
+
+    def profile_names(self):
+        buf = ctypes.create_string_buffer(4096)
+        self._check(self.lib.paro_profile_names(self.h, buf, 4096))
+        return [s for s in buf.value.decode().split(",") if s]
+
+    def launch_count(self):
+        n = ctypes.c_longlong()
+        self._check(self.lib.paro_launch_count(self.h, ctypes.byref(n)))
+        return n.value
 
     def scf(self, opts: ScfOptions | None = None):
         o = (opts or ScfOptions()).s
