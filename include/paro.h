@@ -110,6 +110,26 @@ int paro_sigma(const paro_ctx* ctx, double* sigma);
 int paro_apply_h(paro_ctx* ctx, int ik, int nb, int dtype, const void* psi, void* hpsi);
 
 /*
+ * paro_apply_h_noalloc -- the same H psi as paro_apply_h, for callers that cannot let the library
+ * allocate device memory during the call: applications that give all device memory to their own
+ * pool up front and run under a fixed budget, and callers that must keep the implicit device-wide
+ * synchronisation of cudaMalloc/cudaFree out of a latency-critical loop. The paper has no
+ * counterpart; this is a library-interface variant.
+ *   Arguments, layout and ownership as paro_apply_h. The call allocates nothing: its scratch (stick
+ *   buffer, KB projections, split-K partial sums) is one fixed 32 MiB device array inside the library,
+ *   which every GPU that loads the library holds until the process exits.
+ *   Size limit: nb * N3 * (stick columns) * element size, plus 2 * n_proj * nb * 16 bytes with KB
+ *   projectors, must fit in 32 MiB; larger requests fail with PARO_ERR_ARG and a message giving the
+ *   bytes needed (split the bands over several calls).
+ *   The first call on a device looks up the array's device address (with that device current) and
+ *   caches it; make that first call before any stream capture.
+ *   Every call shares the one array, and each call overwrites the scratch it reads: calls that
+ *   overlap on the GPU (different streams, threads or contexts on the same device) race and must be
+ *   serialised by the caller.
+ */
+int paro_apply_h_noalloc(paro_ctx* ctx, int ik, int nb, int dtype, const void* psi, void* hpsi);
+
+/*
  * paro_solve_source -- the independent source problems of Algorithm 1, step 3, for nb orbitals:
  * a(rho; x_i, phi) = (eps_i psi_i, phi), solved shifted as (H - sigma) x_i = (eps_i - sigma) psi_i by
  * batched preconditioned CG started at x_i = psi_i. sigma is a rigorous lower bound of the spectrum

@@ -18,6 +18,8 @@ namespace paro {
 static thread_local std::string g_create_err;
 static const double kPi = 3.14159265358979323846;
 
+Ctx* unwrap(paro_ctx* h) { return h ? &h->c : nullptr; }
+
 int fail(Ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
   return code;

@@ -10,6 +10,8 @@
 //
 // The nonlocal Kleinman-Bylander part (Section 2.2, V_nl) is added afterwards by two GEMMs:
 // P = beta^H psi (nproj x nb), then H psi += beta (D o P).
+#include <mutex>
+
 #include "paro_ctx.h"
 
 namespace paro {
@@ -241,4 +243,91 @@ template int apply_h<float>(Ctx*, int, int, const float2*, float2*, double, cons
 template int kb_apply<double>(Ctx*, int, int, const double2*, double2*);
 template int kb_apply<float>(Ctx*, int, int, const float2*, float2*);
 
+// ------------------------------------------------------------------------------------------------
+// Allocation-free H psi (paro_apply_h_noalloc). Some callers cannot let a library allocate device
+// memory in the middle of their work: applications that hand all device memory to their own pool
+// up front and run under a fixed budget, and callers that must not add the implicit device-wide
+// synchronisation of cudaMalloc/cudaFree to a latency-critical loop. For them the stick buffer, the
+// KB projections and the split-K partial sums of one H psi live in this file-scope device array,
+// which every GPU that loads the library holds until the process exits.
+// ------------------------------------------------------------------------------------------------
+static const size_t kNoAllocScratchBytes = (size_t)32 << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+static const int kMaxDevices = 64;
+static void* g_noalloc_addr[kMaxDevices];  // device address of g_noalloc_scratch, per device
+static std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device. The symbol's name in host code is only
+// a host-side stand-in, so the address is looked up once per device (with that device current) and
+// cached; the first call on a device does this set-up.
+static int noalloc_scratch(Ctx* c, unsigned char** out) {
+  int dev = 0;
+  PARO_CU(c, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(c, PARO_ERR_ARG, "paro_apply_h_noalloc: device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    g_noalloc_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  return PARO_OK;
+}
+
+static size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+
+template <typename T>
+static int apply_h_noalloc(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* hpsi) {
+  if (!c->have_veff) return fail(c, PARO_ERR_STATE, "no effective potential set");
+  int st = configure<T>(c);
+  if (st) return st;
+  const Basis& B = c->bases[ik];
+  const int eb = (int)sizeof(cplx<T>);
+  const size_t sticks = round256((size_t)nb * c->N[2] * B.ncol * eb);
+  const size_t proj = c->have_kb ? round256((size_t)c->nproj * nb * sizeof(double2)) : 0;
+  const size_t slice = c->have_kb ? (size_t)c->nproj * nb * sizeof(double2) : 0;  // one split-K slice
+  const size_t need = sticks + proj + slice;
+  if (need > kNoAllocScratchBytes)
+    return fail(c, PARO_ERR_ARG, "paro_apply_h_noalloc: this H psi needs " + std::to_string(need) +
+                                     " bytes of scratch, more than the fixed limit of " +
+                                     std::to_string(kNoAllocScratchBytes) + " bytes (32 MiB); use fewer bands per call");
+  unsigned char* base = nullptr;
+  if ((st = noalloc_scratch(c, &base))) return st;
+  cplx<T>* S = reinterpret_cast<cplx<T>*>(base);
+  const dim3 gz((B.ncol + kStickBatch - 1) / kStickBatch, nb);
+  k_zpass_inv<T><<<gz, kZThreads, zpass_smem(c, eb), c->stream>>>(psi, B.npw, S, B.d_col_off, B.d_g_col, B.d_g_z,
+                                                                  B.ncol, c->plan[2], tw_of<T>(c, 2), nullptr,
+                                                                  kStickBatch);
+  PARO_LAUNCH(c, "k_zpass_inv");
+  k_plane<T><<<dim3(c->N[2], nb), plane_threads(c), plane_smem(c, eb), c->stream>>>(
+      S, B.ncol, B.d_col_x, B.d_col_y, B.d_xrows, B.nxr, c->plan[0], c->plan[1], tw_of<T>(c, 0), tw_of<T>(c, 1),
+      vplane_of<T>(c), nullptr);
+  PARO_LAUNCH(c, "k_plane");
+  k_zpass_fwd<T><<<gz, kZThreads, zpass_smem(c, eb), c->stream>>>(S, psi, B.npw, hpsi, B.npw, kin_of<T>(B), (T)0,
+                                                                  B.d_col_off, B.d_g_col, B.d_g_z, B.ncol, c->plan[2],
+                                                                  tw_of<T>(c, 2), nullptr, kStickBatch);
+  PARO_LAUNCH(c, "k_zpass_fwd");
+  if (!c->have_kb) return PARO_OK;
+  double2* P = reinterpret_cast<double2*>(base + sticks);
+  double2* part = reinterpret_cast<double2*>(base + sticks + proj);
+  const size_t part_elems = (kNoAllocScratchBytes - sticks - proj) / sizeof(double2);
+  if ((st = gemm_cn_scratch<T, T, T>(c, c->nproj, nb, B.npw, beta_of<T>(B), B.npw, psi, B.npw, P, nb, part,
+                                     part_elems)))
+    return st;
+  return gemm_wx<T, T>(c, nb, B.npw, c->nproj, P, nb, false, c->d_dvec, beta_of<T>(B), B.npw, hpsi, B.npw, 1.0);
+}
+
 }  // namespace paro
+
+extern "C" int paro_apply_h_noalloc(paro_ctx* ctx, int ik, int nb, int dtype, const void* psi, void* hpsi) {
+  paro::Ctx* c = paro::unwrap(ctx);
+  if (!c) return PARO_ERR_ARG;
+  c->err.clear();
+  if (ik < 0 || ik >= c->nk || nb < 1 || !psi || !hpsi || psi == hpsi || (dtype != PARO_C64 && dtype != PARO_C32))
+    return paro::fail(c, PARO_ERR_ARG, "paro_apply_h_noalloc: bad argument");
+  return dtype == PARO_C64 ? paro::apply_h_noalloc<double>(c, ik, nb, static_cast<const double2*>(psi),
+                                                           static_cast<double2*>(hpsi))
+                           : paro::apply_h_noalloc<float>(c, ik, nb, static_cast<const float2*>(psi),
+                                                          static_cast<float2*>(hpsi));
+}

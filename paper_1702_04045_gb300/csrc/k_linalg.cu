@@ -104,6 +104,36 @@ int gemm_cn(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, const cplx<
   return PARO_OK;
 }
 
+// The same product with the K-slice partial sums in caller-provided memory of part_elems complex
+// doubles (no allocation); every partial that k_reduce_parts reads is written first by k_gemm_cn.
+template <typename TA, typename TB, typename ACC>
+int gemm_cn_scratch(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb,
+                    double2* C, int ldc, double2* part, size_t part_elems) {
+  if (M <= 0 || N <= 0) return PARO_OK;
+  if (K <= 0) return fail(c, PARO_ERR_ARG, "gemm: K must be positive");
+  const size_t slice = (size_t)M * N;
+  if (part_elems < slice) return fail(c, PARO_ERR_ARG, "gemm: scratch smaller than one K slice");
+  const int tiles = ((M + 31) / 32) * ((N + 31) / 32);
+  int nz = (2 * 152 + tiles - 1) / tiles;
+  const int maxz = (K + 255) / 256;
+  if (nz > maxz) nz = maxz;
+  if ((size_t)nz > part_elems / slice) nz = (int)(part_elems / slice);
+  if (nz < 1) nz = 1;
+  const int kslice = ((K + nz - 1) / nz + 31) / 32 * 32;
+  nz = (K + kslice - 1) / kslice;
+  k_gemm_cn<TA, TB, ACC><<<dim3((N + 31) / 32, (M + 31) / 32, nz), 256, 0, c->stream>>>(M, N, K, kslice, A, lda, B,
+                                                                                      ldb, part, 0);
+  PARO_LAUNCH(c, "k_gemm_cn");
+  k_reduce_parts<<<(M * N + 255) / 256, 256, 0, c->stream>>>(M, N, nz, part, C, ldc, 0);
+  PARO_LAUNCH(c, "k_reduce_parts");
+  return PARO_OK;
+}
+
+template int gemm_cn_scratch<double, double, double>(Ctx*, int, int, int, const double2*, int, const double2*, int,
+                                                     double2*, int, double2*, size_t);
+template int gemm_cn_scratch<float, float, float>(Ctx*, int, int, int, const float2*, int, const float2*, int,
+                                                  double2*, int, double2*, size_t);
+
 // ------------------------------------------------------------------------------------------------
 // Y = beta Y + W^T X (short K): 32 x 64 output tile per CTA, 256 threads with 4 x 2 outputs each.
 // ------------------------------------------------------------------------------------------------

@@ -151,6 +151,12 @@ int gemm_cn(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, const cplx<
 template <typename TX, typename TY>
 int gemm_wx(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, const double* s, const cplx<TX>* X,
             int ldx, cplx<TY>* Y, int ldy, double beta);
+// gemm_cn with the K-slice partials in caller memory (part_elems complex doubles); allocates nothing.
+template <typename TA, typename TB, typename ACC>
+int gemm_cn_scratch(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb,
+                    double2* C, int ldc, double2* part, size_t part_elems);
+// The context behind a C-ABI handle (api.cu).
+Ctx* unwrap(paro_ctx* h);
 // Cholesky S = L L^H (n x n, row-major, device), then writes G = conj(L)^{-1} (lower) into g.
 int chol_inv(Ctx* c, int n, const double2* s, double2* g);
 // Hermitian eigensolver (one CTA): w ascending, v columns = eigenvectors.

@@ -16,6 +16,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libparo.so")
 
+PARO_OK, PARO_ERR_ARG, PARO_ERR_CUDA, PARO_ERR_BREAKDOWN, PARO_ERR_NOT_CONVERGED, PARO_ERR_STATE = 0, -1, -2, -3, -4, -6
 PARO_FP64, PARO_MIXED = 0, 1
 PARO_C64, PARO_C32 = 0, 1
 PARO_ALG1, PARO_ALG2 = 1, 2
@@ -24,7 +25,7 @@ ENERGY_TERMS = ("kinetic", "nonlocal", "local", "hartree", "xc", "ewald", "total
 # Every symbol include/paro.h declares.
 EXPORTS = (
     "paro_create", "paro_set_local_pp", "paro_set_kb", "paro_set_veff", "paro_get_veff", "paro_set_density",
-    "paro_grid", "paro_npw", "paro_miller", "paro_sigma", "paro_apply_h", "paro_solve_source",
+    "paro_grid", "paro_npw", "paro_miller", "paro_sigma", "paro_apply_h", "paro_apply_h_noalloc", "paro_solve_source",
     "paro_set_orbitals", "paro_get_orbitals", "paro_get_eigenvalues", "paro_get_residuals", "paro_step",
     "paro_eigh", "paro_density", "paro_energy", "paro_scf_step", "paro_scf", "paro_set_state", "paro_profile",
     "paro_profile_read", "paro_profile_names", "paro_launch_count", "paro_last_error", "paro_destroy",
@@ -60,6 +61,7 @@ _SIGS = {
     "paro_miller": (ctypes.c_int, [_vp, ctypes.c_int, _c_int_p]),
     "paro_sigma": (ctypes.c_int, [_vp, _c_dbl_p]),
     "paro_apply_h": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),
+    "paro_apply_h_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "paro_solve_source": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_dbl_p, _vp, _vp,
                                          ctypes.c_double, ctypes.c_int, _c_int_p]),
     "paro_set_orbitals": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int]),
@@ -220,6 +222,15 @@ class Context:
         if out is None:
             out = torch.empty_like(psi)
         self._check(self.lib.paro_apply_h(self.h, ik, nb, dt, _vp(psi.data_ptr()), _vp(out.data_ptr())))
+        return out
+
+    def apply_h_noalloc(self, psi, out, ik=0):
+        """H psi into a caller-provided output through the library's allocation-free entry point."""
+        torch = self.torch
+        dt = PARO_C64 if psi.dtype == torch.complex128 else PARO_C32
+        psi = psi.contiguous()
+        self._check(self.lib.paro_apply_h_noalloc(self.h, ik, psi.shape[0], dt, _vp(psi.data_ptr()),
+                                                  _vp(out.data_ptr())))
         return out
 
     def solve_source(self, eps, psi, rel_tol, max_it, ik=0):
