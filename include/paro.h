@@ -30,6 +30,7 @@ typedef enum {
   PARO_ERR_CUDA = -2,          /* a CUDA call failed; the message holds cudaGetErrorString */
   PARO_ERR_BREAKDOWN = -3,     /* PCG p^H A p <= 0 or NaN, or a Cholesky pivot <= 0 */
   PARO_ERR_NOT_CONVERGED = -4, /* SCF / ParO iteration limit reached; the last state is kept */
+  PARO_ERR_TIMEOUT = -5,       /* a bounded device-side wait (grid barrier) gave up */
   PARO_ERR_STATE = -6          /* call out of order (e.g. no potential or orbitals set yet) */
 } paro_status;
 

@@ -163,6 +163,10 @@ static int alloc_orbitals(Ctx* c, Basis& b) {
     PARO_CU(c, cudaMalloc(&b.d_psi, (size_t)c->nb * b.npw * sizeof(double2)));
     PARO_CU(c, cudaMalloc(&b.d_hpsi, (size_t)c->nb * b.npw * sizeof(double2)));
   }
+  if (c->prec == PARO_MIXED && !b.d_psi32) {
+    PARO_CU(c, cudaMalloc(&b.d_psi32, (size_t)c->nb * b.npw * sizeof(float2)));
+    PARO_CU(c, cudaMalloc(&b.d_hpsi32, (size_t)c->nb * b.npw * sizeof(float2)));
+  }
   return PARO_OK;
 }
 
@@ -177,17 +181,31 @@ __global__ void k_hermitize(int n, double2* __restrict__ a) {
   a[(size_t)j * n + i] = make_double2(h.x, -h.y);
 }
 
-// Orthonormalise the nx rows of X (FP64, as Y = conj(L)^{-1} X; skipped when X is already
-// orthonormal) and take the Ritz pairs of their span: H_sub = Y^H H Y, H_sub C = C diag(eps);
-// psi = first nb rows of C^T Y, H psi = C^T (H Y). Mixed precision applies H in FP32 (Y rounded to
-// FP32) and keeps every reduction in FP64.
-static int project(Ctx* c, int ik, double2* X, int nx, bool orthonormal = false) {
+// Orbitals in the working precision: FP64 path d_psi / d_hpsi, mixed path d_psi32 / d_hpsi32.
+template <typename T> static cplx<T>* psi_of(Basis& b);
+template <> double2* psi_of<double>(Basis& b) { return b.d_psi; }
+template <> float2* psi_of<float>(Basis& b) { return b.d_psi32; }
+template <typename T> static cplx<T>* hpsi_of(Basis& b);
+template <> double2* hpsi_of<double>(Basis& b) { return b.d_hpsi; }
+template <> float2* hpsi_of<float>(Basis& b) { return b.d_hpsi32; }
+
+static const char* wsn(bool f64, const char* a, const char* b) { return f64 ? a : b; }
+
+// Rayleigh-Ritz in the span of the nx rows of X (Algorithm 1 step 4): Cholesky-orthonormalise
+// (Y = conj(L)^{-1} X, skipped when X is already orthonormal), H_sub = Y^H H Y, H_sub C = C diag(eps),
+// psi = first nb rows of C^T Y, H psi = C^T (H Y), residual norms. T = double: every step in FP64.
+// T = float (mixed): the Cholesky apply, H Y and the rotations in FP32; the Gram and H_sub products
+// accumulated in FP64 (upper halves, mirrored); Cholesky, eigensolver and residual norms in FP64.
+template <typename T>
+static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal) {
   Basis& b = c->bases[ik];
   const int npw = b.npw, nb = c->nb;
+  const bool f64 = sizeof(T) == 8;
   double2* S = static_cast<double2*>(ws_get(c, "proj_S", (size_t)nx * nx * sizeof(double2)));
   double2* G = static_cast<double2*>(ws_get(c, "proj_G", (size_t)nx * nx * sizeof(double2)));
-  double2* Y = static_cast<double2*>(ws_get(c, "proj_Y", (size_t)nx * npw * sizeof(double2)));
-  double2* HY = static_cast<double2*>(ws_get(c, "proj_HY", (size_t)nx * npw * sizeof(double2)));
+  cplx<T>* Y = static_cast<cplx<T>*>(ws_get(c, wsn(f64, "proj_Y64", "proj_Y32"), (size_t)nx * npw * sizeof(cplx<T>)));
+  cplx<T>* HY =
+      static_cast<cplx<T>*>(ws_get(c, wsn(f64, "proj_HY64", "proj_HY32"), (size_t)nx * npw * sizeof(cplx<T>)));
   double* w = static_cast<double*>(ws_get(c, "proj_w", (size_t)nx * sizeof(double)));
   double* res = static_cast<double*>(ws_get(c, "proj_res", (size_t)nx * sizeof(double)));
   if (!S || !G || !Y || !HY || !w || !res) return PARO_ERR_CUDA;
@@ -197,35 +215,32 @@ static int project(Ctx* c, int ik, double2* X, int nx, bool orthonormal = false)
   } else {
     {
       ProfTag t(c, "gram");
-      if ((st = gemm_cn<double, double, double>(c, nx, nx, npw, X, npw, X, npw, S, nx, true))) return st;
+      if ((st = gemm_cn<T, T, double>(c, nx, nx, npw, X, npw, X, npw, S, nx, true))) return st;
       if ((st = chol_inv(c, nx, S, G))) return st;
     }
     ProfTag t(c, "orth");
-    if ((st = gemm_wx<double, double>(c, nx, npw, nx, G, nx, true, nullptr, X, npw, Y, npw, 0.0))) return st;
+    if ((st = gemm_wx<T, T>(c, nx, npw, nx, G, nx, true, nullptr, X, npw, Y, npw, 0.0))) return st;
   }
   {
     ProfTag t(c, "rr");
-    if (c->prec == PARO_MIXED) {
-      float2* Y32 = static_cast<float2*>(ws_get(c, "proj_Y32", (size_t)nx * npw * sizeof(float2)));
-      float2* HY32 = static_cast<float2*>(ws_get(c, "proj_HY32", (size_t)nx * npw * sizeof(float2)));
-      if (!Y32 || !HY32) return PARO_ERR_CUDA;
-      if ((st = convert<double, float>(c, (size_t)nx * npw, Y, Y32))) return st;
-      if ((st = apply_h<float>(c, ik, nx, Y32, HY32, 0.0, nullptr))) return st;
-      if ((st = convert<float, double>(c, (size_t)nx * npw, HY32, HY))) return st;
-    } else {
-      if ((st = apply_h<double>(c, ik, nx, Y, HY, 0.0, nullptr))) return st;
-    }
+    if ((st = apply_h<T>(c, ik, nx, Y, HY, 0.0, nullptr))) return st;
   }
   {
     ProfTag t(c, "hsub");
-    if ((st = gemm_cn<double, double, double>(c, nx, nx, npw, Y, npw, HY, npw, S, nx, false))) return st;
+    if ((st = gemm_cn<T, T, double>(c, nx, nx, npw, Y, npw, HY, npw, S, nx, true))) return st;
     k_hermitize<<<(nx * nx + 255) / 256, 256, 0, c->stream>>>(nx, S);
     PARO_LAUNCH(c, "k_hermitize");
     if ((st = eigh(c, nx, S, w, G))) return st;  // G <- eigenvectors C
   }
-  ProfTag t(c, "rot");
-  if ((st = gemm_wx<double, double>(c, nb, npw, nx, G, nx, false, nullptr, Y, npw, b.d_psi, npw, 0.0))) return st;
-  if ((st = gemm_wx<double, double>(c, nb, npw, nx, G, nx, false, nullptr, HY, npw, b.d_hpsi, npw, 0.0))) return st;
+  {
+    ProfTag t(c, "rot");
+    if ((st = gemm_wx<T, T>(c, nb, npw, nx, G, nx, false, nullptr, Y, npw, psi_of<T>(b), npw, 0.0))) return st;
+    if ((st = gemm_wx<T, T>(c, nb, npw, nx, G, nx, false, nullptr, HY, npw, hpsi_of<T>(b), npw, 0.0))) return st;
+  }
+  if (!f64) {
+    if ((st = convert<float, double>(c, (size_t)nb * npw, b.d_psi32, b.d_psi))) return st;
+    if ((st = convert<float, double>(c, (size_t)nb * npw, b.d_hpsi32, b.d_hpsi))) return st;
+  }
   if ((st = residual_norms(c, nb, npw, b.d_psi, b.d_hpsi, w, res))) return st;
   b.eps.resize(nb);
   b.res.resize(nb);
@@ -236,16 +251,16 @@ static int project(Ctx* c, int ik, double2* X, int nx, bool orthonormal = false)
   return PARO_OK;
 }
 
-__global__ void k_axpy_rows(int npw, double2* __restrict__ y, const double2* __restrict__ x,
-                            const double* __restrict__ f, double sx) {
+template <typename T>
+__global__ void k_axpy_rows(int npw, cplx<T>* __restrict__ y, const cplx<T>* __restrict__ x, T sx) {
   const int b = blockIdx.y;
   const size_t o = (size_t)b * npw;
-  const double s = f ? f[b] : sx;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < npw; g += gridDim.x * blockDim.x)
-    y[o + g] = cadd(y[o + g], cscale(x[o + g], s));
+    y[o + g] = cadd(y[o + g], cscale(x[o + g], sx));
 }
 
-// rhs_b = (eps_b - sigma) psi_b (Algorithm 1) or -(H psi_b - eps_b psi_b) (Algorithm 2), in T
+// rhs_b = (eps_b - sigma) psi_b (Algorithm 1) or -(H psi_b - eps_b psi_b) (Algorithm 2), formed in
+// FP64 from the current orbitals and stored in T
 template <typename T>
 static int source_rhs(Ctx* c, int ik, bool alg2, cplx<T>* rhs) {
   Basis& b = c->bases[ik];
@@ -259,7 +274,7 @@ static int source_rhs(Ctx* c, int ik, bool alg2, cplx<T>* rhs) {
   int st = scale_rows<double>(c, nb, npw, b.d_psi, f, tmp);
   if (st) return st;
   if (alg2) {
-    k_axpy_rows<<<dim3((npw + 255) / 256, nb), 256, 0, c->stream>>>(npw, tmp, b.d_hpsi, nullptr, -1.0);
+    k_axpy_rows<double><<<dim3((npw + 255) / 256, nb), 256, 0, c->stream>>>(npw, tmp, b.d_hpsi, -1.0);
     PARO_LAUNCH(c, "k_axpy_rows");
   }
   if (sizeof(T) == 8) {
@@ -269,33 +284,24 @@ static int source_rhs(Ctx* c, int ik, bool alg2, cplx<T>* rhs) {
   return convert<double, float>(c, (size_t)nb * npw, tmp, reinterpret_cast<float2*>(rhs));
 }
 
-// Source problems of all bands of k-point ik into X (FP64, rows 0..nb-1).
+// Source problems of all bands of k-point ik; solutions in x (T), started at psi (Algorithm 1) or 0.
 template <typename T>
-static int solve_sources(Ctx* c, int ik, bool alg2, double rel_tol, int max_it, double2* X) {
+static int solve_sources(Ctx* c, int ik, bool alg2, double rel_tol, int max_it, cplx<T>* x) {
   Basis& b = c->bases[ik];
   const int nb = c->nb, npw = b.npw;
   const bool f64 = sizeof(T) == 8;
-  cplx<T>* rhs = static_cast<cplx<T>*>(ws_get(c, f64 ? "src_rhs64" : "src_rhs32", (size_t)nb * npw * sizeof(cplx<T>)));
-  cplx<T>* x = static_cast<cplx<T>*>(ws_get(c, f64 ? "src_x64" : "src_x32", (size_t)nb * npw * sizeof(cplx<T>)));
-  if (!rhs || !x) return PARO_ERR_CUDA;
+  cplx<T>* rhs = static_cast<cplx<T>*>(ws_get(c, wsn(f64, "src_rhs64", "src_rhs32"), (size_t)nb * npw * sizeof(cplx<T>)));
+  if (!rhs) return PARO_ERR_CUDA;
   int st = source_rhs<T>(c, ik, alg2, rhs);
   if (st) return st;
-  if (!alg2) {
-    if (f64) {
-      PARO_CU(c, cudaMemcpyAsync(x, b.d_psi, (size_t)nb * npw * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
-    } else if ((st = convert<double, float>(c, (size_t)nb * npw, b.d_psi, reinterpret_cast<float2*>(x)))) {
-      return st;
-    }
-  }
-  if ((st = pcg_run<T>(c, ik, nb, rhs, x, alg2, rel_tol, max_it, nullptr))) return st;
-  if (f64) {
-    PARO_CU(c, cudaMemcpyAsync(X, x, (size_t)nb * npw * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
-    return PARO_OK;
-  }
-  return convert<float, double>(c, (size_t)nb * npw, reinterpret_cast<const float2*>(x), X);
+  if (!alg2)
+    PARO_CU(c, cudaMemcpyAsync(x, psi_of<T>(b), (size_t)nb * npw * sizeof(cplx<T>), cudaMemcpyDeviceToDevice,
+                               c->stream));
+  return pcg_run<T>(c, ik, nb, rhs, x, alg2, rel_tol, max_it, nullptr);
 }
 
-__global__ void k_compact_rows(int npw, int nb, double2* __restrict__ dst, const double2* __restrict__ src,
+template <typename T>
+__global__ void k_compact_rows(int npw, int nb, cplx<T>* __restrict__ dst, const cplx<T>* __restrict__ src,
                                const int* __restrict__ map) {
   const int r = blockIdx.y;
   const int from = map[r];
@@ -303,33 +309,36 @@ __global__ void k_compact_rows(int npw, int nb, double2* __restrict__ dst, const
     dst[(size_t)(nb + r) * npw + g] = src[(size_t)from * npw + g];
 }
 
-// Algorithm 2: [psi, e] with e projected out of span{psi} and corrections of norm <= 1e-10 dropped.
-static int build_alg2_basis(Ctx* c, int ik, double2* E, double2* X, int* nx_out) {
+// Algorithm 2: rows [psi, e] of X with e projected out of span{psi}; corrections whose remaining
+// norm is at most 1e-10 are left out (they add nothing to the span).
+template <typename T>
+static int build_alg2_basis(Ctx* c, int ik, cplx<T>* E, cplx<T>* X, int* nx_out) {
   Basis& b = c->bases[ik];
   const int nb = c->nb, npw = b.npw;
+  const bool f64 = sizeof(T) == 8;
   double2* P = static_cast<double2*>(ws_get(c, "alg2_P", (size_t)nb * nb * sizeof(double2)));
   double* nrm = static_cast<double*>(ws_get(c, "alg2_nrm", (size_t)nb * sizeof(double)));
   int* map = static_cast<int*>(ws_get(c, "alg2_map", (size_t)nb * sizeof(int)));
-  if (!P || !nrm || !map) return PARO_ERR_CUDA;
+  cplx<T>* tmp = static_cast<cplx<T>*>(ws_get(c, wsn(f64, "alg2_tmp64", "alg2_tmp32"), (size_t)nb * npw * sizeof(cplx<T>)));
+  if (!P || !nrm || !map || !tmp) return PARO_ERR_CUDA;
+  cplx<T>* psi = psi_of<T>(b);
   int st;
   // P[i][j] = <psi_i, e_j>;  e_j -= sum_i psi_i P[i][j]
-  if ((st = gemm_cn<double, double, double>(c, nb, nb, npw, b.d_psi, npw, E, npw, P, nb, false))) return st;
-  double2* tmp = static_cast<double2*>(ws_get(c, "alg2_tmp", (size_t)nb * npw * sizeof(double2)));
-  if (!tmp) return PARO_ERR_CUDA;
-  if ((st = gemm_wx<double, double>(c, nb, npw, nb, P, nb, false, nullptr, b.d_psi, npw, tmp, npw, 0.0))) return st;
-  k_axpy_rows<<<dim3((npw + 255) / 256, nb), 256, 0, c->stream>>>(npw, E, tmp, nullptr, -1.0);
+  if ((st = gemm_cn<T, T, double>(c, nb, nb, npw, psi, npw, E, npw, P, nb, false))) return st;
+  if ((st = gemm_wx<T, T>(c, nb, npw, nb, P, nb, false, nullptr, psi, npw, tmp, npw, 0.0))) return st;
+  k_axpy_rows<T><<<dim3((npw + 255) / 256, nb), 256, 0, c->stream>>>(npw, E, tmp, (T)-1);
   PARO_LAUNCH(c, "k_axpy_rows");
-  if ((st = band_norms<double>(c, nb, npw, E, npw, nrm))) return st;
+  if ((st = band_norms<T>(c, nb, npw, E, npw, nrm))) return st;
   std::vector<double> h(nb);
   PARO_CU(c, cudaMemcpyAsync(h.data(), nrm, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   PARO_CU(c, cudaStreamSynchronize(c->stream));
   std::vector<int> keep;
   for (int i = 0; i < nb; ++i)
     if (std::sqrt(h[i]) > 1e-10) keep.push_back(i);
-  PARO_CU(c, cudaMemcpyAsync(X, b.d_psi, (size_t)nb * npw * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+  PARO_CU(c, cudaMemcpyAsync(X, psi, (size_t)nb * npw * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, c->stream));
   if (!keep.empty()) {
     PARO_CU(c, cudaMemcpyAsync(map, keep.data(), keep.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    k_compact_rows<<<dim3((npw + 255) / 256, (int)keep.size()), 256, 0, c->stream>>>(npw, nb, X, E, map);
+    k_compact_rows<T><<<dim3((npw + 255) / 256, (int)keep.size()), 256, 0, c->stream>>>(npw, nb, X, E, map);
     PARO_LAUNCH(c, "k_compact_rows");
   }
   PARO_CU(c, cudaStreamSynchronize(c->stream));
@@ -363,42 +372,119 @@ static double max_occ_resid(const Ctx* c) {
   return m;
 }
 
-// step 3 of Algorithm 1/2 for k-point ik: the new basis rows in X (FP64), count in nx
-static int source_step(Ctx* c, int ik, int alg, double rel_tol, int max_it, double2* X, int* nx) {
+// step 3 of Algorithm 1/2 for k-point ik: the new basis rows in X (T), count in nx
+template <typename T>
+static int source_step(Ctx* c, int ik, int alg, double rel_tol, int max_it, cplx<T>* X, int* nx) {
   const bool alg2 = alg == PARO_ALG2;
   const int npw = c->bases[ik].npw;
-  double2* E = X;
+  cplx<T>* E = X;
   if (alg2) {
-    E = static_cast<double2*>(ws_get(c, "alg2_E", (size_t)c->nb * npw * sizeof(double2)));
+    E = static_cast<cplx<T>*>(ws_get(c, wsn(sizeof(T) == 8, "alg2_E64", "alg2_E32"), (size_t)c->nb * npw * sizeof(cplx<T>)));
     if (!E) return PARO_ERR_CUDA;
   }
-  int st = c->prec == PARO_MIXED ? solve_sources<float>(c, ik, alg2, rel_tol, max_it, E)
-                                 : solve_sources<double>(c, ik, alg2, rel_tol, max_it, E);
+  int st = solve_sources<T>(c, ik, alg2, rel_tol, max_it, E);
   if (st) return st;
   if (!alg2) {
     *nx = c->nb;
     return PARO_OK;
   }
-  return build_alg2_basis(c, ik, E, X, nx);
+  return build_alg2_basis<T>(c, ik, E, X, nx);
 }
 
-// Cholesky-orthonormalise the first nx rows of X in place (Y = conj(L)^{-1} X).
-static int orthonormalize(Ctx* c, int ik, double2* X, int nx) {
+// Cholesky-orthonormalise the first nx rows of X in place (Y = conj(L)^{-1} X); Gram in FP64.
+template <typename T>
+static int orthonormalize(Ctx* c, int ik, cplx<T>* X, int nx) {
   const int npw = c->bases[ik].npw;
+  const bool f64 = sizeof(T) == 8;
   double2* S = static_cast<double2*>(ws_get(c, "proj_S", (size_t)nx * nx * sizeof(double2)));
   double2* G = static_cast<double2*>(ws_get(c, "proj_G", (size_t)nx * nx * sizeof(double2)));
-  double2* Y = static_cast<double2*>(ws_get(c, "proj_Y", (size_t)nx * npw * sizeof(double2)));
+  cplx<T>* Y = static_cast<cplx<T>*>(ws_get(c, wsn(f64, "proj_Y64", "proj_Y32"), (size_t)nx * npw * sizeof(cplx<T>)));
   if (!S || !G || !Y) return PARO_ERR_CUDA;
   int st;
   {
     ProfTag t(c, "gram");
-    if ((st = gemm_cn<double, double, double>(c, nx, nx, npw, X, npw, X, npw, S, nx, true))) return st;
+    if ((st = gemm_cn<T, T, double>(c, nx, nx, npw, X, npw, X, npw, S, nx, true))) return st;
     if ((st = chol_inv(c, nx, S, G))) return st;
   }
   ProfTag t(c, "orth");
-  if ((st = gemm_wx<double, double>(c, nx, npw, nx, G, nx, true, nullptr, X, npw, Y, npw, 0.0))) return st;
-  PARO_CU(c, cudaMemcpyAsync(X, Y, (size_t)nx * npw * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+  if ((st = gemm_wx<T, T>(c, nx, npw, nx, G, nx, true, nullptr, X, npw, Y, npw, 0.0))) return st;
+  PARO_CU(c, cudaMemcpyAsync(X, Y, (size_t)nx * npw * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, c->stream));
   return PARO_OK;
+}
+
+// Workspace for 2 n_bands rows of k-point ik in T
+template <typename T>
+static cplx<T>* rows_ws(Ctx* c, const char* base, int ik) {
+  std::string name = std::string(base) + (sizeof(T) == 8 ? "64_" : "32_") + std::to_string(ik);
+  return static_cast<cplx<T>*>(ws_get(c, name.c_str(), (size_t)2 * c->nb * c->bases[ik].npw * sizeof(cplx<T>)));
+}
+
+// Rayleigh-Ritz of the span of the current orbitals (after a change of potential or a restart)
+static int reproject(Ctx* c, int ik) {
+  Basis& b = c->bases[ik];
+  const size_t n = (size_t)c->nb * b.npw;
+  if (c->prec == PARO_MIXED) {
+    float2* X = rows_ws<float>(c, "X", ik);
+    if (!X) return PARO_ERR_CUDA;
+    int st = convert<double, float>(c, n, b.d_psi, X);
+    return st ? st : project<float>(c, ik, X, c->nb, false);
+  }
+  double2* X = rows_ws<double>(c, "X", ik);
+  if (!X) return PARO_ERR_CUDA;
+  PARO_CU(c, cudaMemcpyAsync(X, b.d_psi, n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+  return project<double>(c, ik, X, c->nb, false);
+}
+
+// One ParO step (Algorithm 1 or 2) of k-point ik at the current potential.
+template <typename T>
+static int paro_step_k(Ctx* c, int ik, int alg, double rel_tol, int max_it) {
+  cplx<T>* X = rows_ws<T>(c, "X", ik);
+  if (!X) return PARO_ERR_CUDA;
+  int nx = c->nb;
+  int st = source_step<T>(c, ik, alg, rel_tol, max_it, X, &nx);
+  return st ? st : project<T>(c, ik, X, nx, false);
+}
+
+// The merged SCF iteration in precision T (see paro_scf_step).
+template <typename T>
+static int scf_iteration(Ctx* c, const paro_scf_opts* o) {
+  std::vector<cplx<T>*> xs(c->nk);
+  std::vector<int> nxs(c->nk);
+  int st;
+  for (int ik = 0; ik < c->nk; ++ik) {
+    xs[ik] = rows_ws<T>(c, "X", ik);
+    if (!xs[ik]) return PARO_ERR_CUDA;
+    if ((st = source_step<T>(c, ik, o->alg, o->inner_rel_tol, o->inner_max_it, xs[ik], &nxs[ik]))) return st;
+    if ((st = orthonormalize<T>(c, ik, xs[ik], nxs[ik]))) return st;
+  }
+  // rho_in^{n+1/2} = Pulay(rho_in^n, rho[X]) (Algorithm 2: rho of the previous orbitals)
+  double* rho_out = static_cast<double*>(ws_get(c, "scf_rho_out", (size_t)c->ngrid * sizeof(double)));
+  if (!rho_out) return PARO_ERR_CUDA;
+  std::vector<const cplx<T>*> dens_src(c->nk);
+  for (int ik = 0; ik < c->nk; ++ik) dens_src[ik] = o->alg == PARO_ALG1 ? xs[ik] : psi_of<T>(c->bases[ik]);
+  {
+    ProfTag t(c, "mix");
+    if ((st = density<T>(c, dens_src.data(), rho_out))) return st;
+    if ((st = pulay_mix(c, rho_out, o->pulay_depth, o->pulay_beta))) return st;
+    if ((st = veff_from_density(c, c->d_rho_in, nullptr, nullptr))) return st;
+  }
+  update_sigma(c);
+  // step 4: Rayleigh-Ritz with V(rho_in^{n+1/2}) in the already orthonormal span
+  for (int ik = 0; ik < c->nk; ++ik)
+    if ((st = project<T>(c, ik, xs[ik], nxs[ik], true))) return st;
+  return PARO_OK;
+}
+
+// density of the current orbitals, in the working precision
+static int current_density(Ctx* c, double* rho) {
+  if (c->prec == PARO_MIXED) {
+    std::vector<const float2*> ps(c->nk);
+    for (int ik = 0; ik < c->nk; ++ik) ps[ik] = c->bases[ik].d_psi32;
+    return density<float>(c, ps.data(), rho);
+  }
+  std::vector<const double2*> ps(c->nk);
+  for (int ik = 0; ik < c->nk; ++ik) ps[ik] = c->bases[ik].d_psi;
+  return density<double>(c, ps.data(), rho);
 }
 
 }  // namespace paro
@@ -519,7 +605,7 @@ void paro_destroy(paro_ctx* ctx) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (Basis& b : c->bases) {
     void* ps[] = {b.d_miller, b.d_kin, b.d_kin32, b.d_col_x, b.d_col_y, b.d_col_off, b.d_g_col, b.d_g_z,
-                  b.d_xrows, b.d_beta, b.d_beta32, b.d_prec_base, b.d_psi, b.d_hpsi};
+                  b.d_xrows, b.d_beta, b.d_beta32, b.d_prec_base, b.d_psi, b.d_hpsi, b.d_psi32, b.d_hpsi32};
     for (void* p : ps)
       if (p) cudaFree(p);
   }
@@ -679,11 +765,9 @@ int paro_set_orbitals(paro_ctx* ctx, int ik, const void* psi, int on_device) {
   Basis& b = c->bases[ik];
   int st = alloc_orbitals(c, b);
   if (st) return st;
-  double2* X = static_cast<double2*>(ws_get(c, "step_X", (size_t)2 * c->nb * b.npw * sizeof(double2)));
-  if (!X) return PARO_ERR_CUDA;
-  PARO_CU(c, cudaMemcpyAsync(X, psi, (size_t)c->nb * b.npw * sizeof(double2),
+  PARO_CU(c, cudaMemcpyAsync(b.d_psi, psi, (size_t)c->nb * b.npw * sizeof(double2),
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
-  return project(c, ik, X, c->nb);
+  return reproject(c, ik);
 }
 
 int paro_get_orbitals(paro_ctx* ctx, int ik, void* psi, int on_device) {
@@ -721,14 +805,10 @@ int paro_step(paro_ctx* ctx, int alg, double rel_tol, int max_it, double* max_re
   CTX_CHECK(ctx);
   if ((alg != PARO_ALG1 && alg != PARO_ALG2) || max_it < 0) return fail(c, PARO_ERR_ARG, "paro_step: bad argument");
   for (int ik = 0; ik < c->nk; ++ik) {
-    Basis& b = c->bases[ik];
-    if (!b.have_psi) return fail(c, PARO_ERR_STATE, "paro_step: orbitals not set");
-    double2* X = static_cast<double2*>(ws_get(c, "step_X", (size_t)2 * c->nb * b.npw * sizeof(double2)));
-    if (!X) return PARO_ERR_CUDA;
-    int nx = c->nb;
-    int st = source_step(c, ik, alg, rel_tol, max_it, X, &nx);
+    if (!c->bases[ik].have_psi) return fail(c, PARO_ERR_STATE, "paro_step: orbitals not set");
+    int st = c->prec == PARO_MIXED ? paro_step_k<float>(c, ik, alg, rel_tol, max_it)
+                                   : paro_step_k<double>(c, ik, alg, rel_tol, max_it);
     if (st) return st;
-    if ((st = project(c, ik, X, nx))) return st;
   }
   if (max_resid_out) *max_resid_out = max_occ_resid(c);
   return PARO_OK;
@@ -743,12 +823,9 @@ int paro_eigh(paro_ctx* ctx, int n, const void* a, double* w, void* v) {
 int paro_density(paro_ctx* ctx, double* rho_dev) {
   CTX_CHECK(ctx);
   if (!rho_dev) return PARO_ERR_ARG;
-  std::vector<const double2*> ps(c->nk);
-  for (int ik = 0; ik < c->nk; ++ik) {
+  for (int ik = 0; ik < c->nk; ++ik)
     if (!c->bases[ik].have_psi) return fail(c, PARO_ERR_STATE, "no orbitals");
-    ps[ik] = c->bases[ik].d_psi;
-  }
-  return density(c, ps.data(), rho_dev);
+  return current_density(c, rho_dev);
 }
 
 int paro_energy(paro_ctx* ctx, double terms[7]) {
@@ -780,46 +857,16 @@ int paro_scf_step(paro_ctx* ctx, const paro_scf_opts* o, double energy[7], doubl
     PARO_LAUNCH(c, "k_fill");
     if ((st = veff_from_density(c, c->d_rho_in, nullptr, nullptr))) return st;
     update_sigma(c);
-    for (int ik = 0; ik < c->nk; ++ik) {
-      Basis& b = c->bases[ik];
-      double2* X = static_cast<double2*>(ws_get(c, "step_X", (size_t)2 * c->nb * b.npw * sizeof(double2)));
-      if (!X) return PARO_ERR_CUDA;
-      PARO_CU(c, cudaMemcpyAsync(X, b.d_psi, (size_t)c->nb * b.npw * sizeof(double2), cudaMemcpyDeviceToDevice,
-                                 c->stream));
-      if ((st = project(c, ik, X, c->nb))) return st;
-    }
+    for (int ik = 0; ik < c->nk; ++ik)
+      if ((st = reproject(c, ik))) return st;
     c->have_rho = true;
     c->scf_iter = 0;
     c->scf_small = 0;
     c->pulay_n = 0;
     c->pulay_head = 0;
   }
-  // step 3 with V(rho_in^n), then Cholesky
-  std::vector<double2*> xs(c->nk);
-  std::vector<int> nxs(c->nk);
-  for (int ik = 0; ik < c->nk; ++ik) {
-    Basis& b = c->bases[ik];
-    std::string name = "scf_X" + std::to_string(ik);
-    xs[ik] = static_cast<double2*>(ws_get(c, name.c_str(), (size_t)2 * c->nb * b.npw * sizeof(double2)));
-    if (!xs[ik]) return PARO_ERR_CUDA;
-    if ((st = source_step(c, ik, o->alg, o->inner_rel_tol, o->inner_max_it, xs[ik], &nxs[ik]))) return st;
-    if ((st = orthonormalize(c, ik, xs[ik], nxs[ik]))) return st;
-  }
-  // rho_in^{n+1/2} = Pulay(rho_in^n, rho[X]) (Algorithm 2: rho of the previous orbitals)
-  double* rho_out = static_cast<double*>(ws_get(c, "scf_rho_out", (size_t)c->ngrid * sizeof(double)));
-  if (!rho_out) return PARO_ERR_CUDA;
-  std::vector<const double2*> dens_src(c->nk);
-  for (int ik = 0; ik < c->nk; ++ik) dens_src[ik] = o->alg == PARO_ALG1 ? xs[ik] : c->bases[ik].d_psi;
-  {
-    ProfTag t(c, "mix");
-    if ((st = density(c, dens_src.data(), rho_out))) return st;
-    if ((st = pulay_mix(c, rho_out, o->pulay_depth, o->pulay_beta))) return st;
-    if ((st = veff_from_density(c, c->d_rho_in, nullptr, nullptr))) return st;
-  }
-  update_sigma(c);
-  // step 4: Rayleigh-Ritz with V(rho_in^{n+1/2}) in the already orthonormal span
-  for (int ik = 0; ik < c->nk; ++ik)
-    if ((st = project(c, ik, xs[ik], nxs[ik], true))) return st;
+  st = c->prec == PARO_MIXED ? scf_iteration<float>(c, o) : scf_iteration<double>(c, o);
+  if (st) return st;
   double terms[7];
   {
     ProfTag t(c, "energy");
@@ -853,12 +900,9 @@ int paro_set_state(paro_ctx* ctx, int ik, const void* psi, const double* eps, in
   if (!w || !res) return PARO_ERR_CUDA;
   PARO_CU(c, cudaMemcpyAsync(w, b.eps.data(), c->nb * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   if (c->prec == PARO_MIXED) {
-    float2* p32 = static_cast<float2*>(ws_get(c, "state_p32", (size_t)c->nb * b.npw * sizeof(float2)));
-    float2* h32 = static_cast<float2*>(ws_get(c, "state_h32", (size_t)c->nb * b.npw * sizeof(float2)));
-    if (!p32 || !h32) return PARO_ERR_CUDA;
-    if ((st = convert<double, float>(c, (size_t)c->nb * b.npw, b.d_psi, p32))) return st;
-    if ((st = apply_h<float>(c, ik, c->nb, p32, h32, 0.0, nullptr))) return st;
-    if ((st = convert<float, double>(c, (size_t)c->nb * b.npw, h32, b.d_hpsi))) return st;
+    if ((st = convert<double, float>(c, (size_t)c->nb * b.npw, b.d_psi, b.d_psi32))) return st;
+    if ((st = apply_h<float>(c, ik, c->nb, b.d_psi32, b.d_hpsi32, 0.0, nullptr))) return st;
+    if ((st = convert<float, double>(c, (size_t)c->nb * b.npw, b.d_hpsi32, b.d_hpsi))) return st;
   } else if ((st = apply_h<double>(c, ik, c->nb, b.d_psi, b.d_hpsi, 0.0, nullptr))) {
     return st;
   }

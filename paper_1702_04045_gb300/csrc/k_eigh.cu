@@ -1,0 +1,419 @@
+// Hermitian eigensolver of the Rayleigh-Ritz step (Algorithm 1 step 4; Algorithm 2 step 4), FP64.
+// GB300 runs FP64 at about 2 FMA per clock per SM, so every O(n^3) part is spread over many SMs:
+//
+//  1. k_tridiag (cooperative, many CTAs): Householder reduction A <- H_j A H_j, H_j = I - tau u u^H,
+//     to a Hermitian tridiagonal matrix; step j's matrix-vector product and rank-2 update are shared
+//     by all CTAs, separated by grid barriers. A diagonal unitary D (D_0 = 1,
+//     D_{j+1} = D_j conj(e_j)/|e_j|) turns the complex off-diagonals e_j into |e_j|: a real symmetric
+//     tridiagonal T'.
+//  2. k_bisect (warp per eigenvalue): the k-th eigenvalue of T' by multisection on the Sturm count
+//     (the number of negative pivots of the LDL^T factorisation of T' - x), 32 points per step.
+//  3. k_invit (one CTA): eigenvectors of T' by inverse iteration, one thread per eigenvalue, with the
+//     LU factorisation of T' - lambda (partial pivoting); after each of three iterations the vectors of
+//     a cluster (eigenvalues closer than 1e-3 ||T'||_1) are orthogonalised in eigenvalue order by one
+//     warp (the standard remedy for close eigenvalues, as in LAPACK's xSTEIN).
+//  4. k_backtransform (warp per column, many CTAs): eigenvectors of A = Q D^H z, Q = H_0 H_1 ...
+#include <cfloat>
+#include <cmath>
+
+#include "paro_ctx.h"
+
+namespace paro {
+
+__global__ void k_herm_full(int n, const double2* __restrict__ Ain, double2* __restrict__ A) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int i = idx / n, j = idx - i * n;
+  A[idx] = (i >= j) ? Ain[idx] : cconj(Ain[(size_t)j * n + i]);
+}
+
+// -------------------------------------------------------------------------------------------------
+// 1. tridiagonalisation. A: n x n full Hermitian work copy; u_j ends up below the diagonal of column
+// j. ub, pb: n complex of scratch; sc: scalars; bar: grid barrier; err: barrier time-out flag.
+// -------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_tridiag(int n, double2* __restrict__ A, double* __restrict__ d,
+                                                 double* __restrict__ e, double2* __restrict__ ph,
+                                                 double* __restrict__ tau, double2* __restrict__ ecx,
+                                                 double2* __restrict__ ub, double2* __restrict__ pb,
+                                                 double* __restrict__ sc, unsigned* bar, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* us = reinterpret_cast<double2*>(smem_raw);  // u
+  double2* ws = us + n;                                 // w
+  __shared__ double red[32];
+  __shared__ double s_K;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int gwarp = blockIdx.x * (blockDim.x >> 5) + (tid >> 5), nwarp = gridDim.x * (blockDim.x >> 5);
+  const int gth = blockIdx.x * blockDim.x + tid, nth = gridDim.x * blockDim.x;
+  for (int j = 0; j + 1 < n; ++j) {
+    const int m = n - j - 1;
+    if (blockIdx.x == 0) {  // the reflector of column j
+      double nrm2 = 0.0;
+      for (int i = tid; i < m; i += blockDim.x) {
+        const double2 x = __ldcg(&A[(size_t)(j + 1 + i) * n + j]);
+        us[i] = x;
+        nrm2 += x.x * x.x + x.y * x.y;
+      }
+      nrm2 = block_sum(nrm2, red);
+      if (tid == 0) {
+        const double2 x0 = us[0];
+        const double ax0 = hypot(x0.x, x0.y);
+        const double nx = sqrt(nrm2);
+        double2 alpha = x0;
+        double t = 0.0;
+        if (m > 1 && nx > 0.0 && nrm2 - ax0 * ax0 > 0.0) {
+          const double2 phs = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+          alpha = make_double2(-phs.x * nx, -phs.y * nx);
+          us[0] = csub(x0, alpha);  // u = x - alpha e_1
+          __stcg(&A[(size_t)(j + 1) * n + j], us[0]);
+          t = 1.0 / (nrm2 + nx * ax0);  // 2 / ||u||^2
+        }
+        sc[0] = t;
+        tau[j] = t;
+        ecx[j] = alpha;
+        d[j] = __ldcg(&A[(size_t)j * n + j]).x;
+      }
+      __syncthreads();
+      for (int i = tid; i < m; i += blockDim.x) __stcg(&ub[i], us[i]);
+    }
+    if (!grid_barrier(bar, err)) return;
+    const double t = __ldcg(&sc[0]);
+    if (t == 0.0) continue;
+    for (int i = tid; i < m; i += blockDim.x) us[i] = __ldcg(&ub[i]);
+    __syncthreads();
+    // p_i = t sum_k B[i][k] u_k, B = A[j+1.., j+1..]: one warp per row
+    for (int i = gwarp; i < m; i += nwarp) {
+      const double2* row = A + (size_t)(j + 1 + i) * n + (j + 1);
+      double2 acc = make_double2(0.0, 0.0);
+      for (int k = lane; k < m; k += 32) {
+        const double2 b = __ldcg(&row[k]), u = us[k];
+        acc.x = fma(b.x, u.x, fma(-b.y, u.y, acc.x));
+        acc.y = fma(b.x, u.y, fma(b.y, u.x, acc.y));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      }
+      if (lane == 0) __stcg(&pb[i], cscale(acc, t));
+    }
+    if (!grid_barrier(bar, err)) return;
+    double kre = 0.0;  // u^H p is real; every CTA forms it
+    for (int i = tid; i < m; i += blockDim.x) {
+      const double2 p = __ldcg(&pb[i]);
+      ws[i] = p;
+      kre += us[i].x * p.x + us[i].y * p.y;
+    }
+    kre = block_sum(kre, red);
+    if (tid == 0) s_K = 0.5 * t * kre;
+    __syncthreads();
+    for (int i = tid; i < m; i += blockDim.x) ws[i] = csub(ws[i], cscale(us[i], s_K));  // w = p - K u
+    __syncthreads();
+    for (size_t idx = gth; idx < (size_t)m * m; idx += nth) {  // B -= u w^H + w u^H
+      const int i = (int)(idx / m), k = (int)(idx - (size_t)i * m);
+      double2* bp = &A[(size_t)(j + 1 + i) * n + (j + 1 + k)];
+      const double2 ui = us[i], wi = ws[i], uk = us[k], wk = ws[k];
+      double2 b = __ldcg(bp);
+      b.x -= ui.x * wk.x + ui.y * wk.y + wi.x * uk.x + wi.y * uk.y;
+      b.y -= ui.y * wk.x - ui.x * wk.y + wi.y * uk.x - wi.x * uk.y;
+      __stcg(bp, b);
+    }
+    if (!grid_barrier(bar, err)) return;
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    d[n - 1] = __ldcg(&A[(size_t)(n - 1) * n + (n - 1)]).x;
+    ph[0] = make_double2(1.0, 0.0);
+    for (int j = 0; j + 1 < n; ++j) {
+      const double a = hypot(ecx[j].x, ecx[j].y);
+      e[j] = a;
+      ph[j + 1] = a > 0.0 ? cmul(ph[j], make_double2(ecx[j].x / a, -ecx[j].y / a)) : ph[j];
+    }
+    e[n - 1] = 0.0;
+  }
+}
+
+// -------------------------------------------------------------------------------------------------
+// 2. multisection: w[k] = k-th smallest eigenvalue of T' (d, e); one warp per eigenvalue
+// -------------------------------------------------------------------------------------------------
+__device__ __forceinline__ int sturm_count(int n, const double* d, const double* e2, double x, double pivmin) {
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  int c = q < 0.0;
+  for (int i = 1; i < n; ++i) {
+    q = d[i] - x - e2[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    c += q < 0.0;
+  }
+  return c;
+}
+
+__global__ void __launch_bounds__(128) k_bisect(int n, const double* __restrict__ dg, const double* __restrict__ eg,
+                                                double* __restrict__ w) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* d = reinterpret_cast<double*>(smem_raw);
+  double* e2 = d + n;
+  __shared__ double s_lo, s_hi, s_pivmin;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    d[i] = dg[i];
+    e2[i] = eg[i] * eg[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double lo = 1e300, hi = -1e300, emax = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double r = (i > 0 ? fabs(eg[i - 1]) : 0.0) + (i + 1 < n ? fabs(eg[i]) : 0.0);
+      lo = fmin(lo, d[i] - r);
+      hi = fmax(hi, d[i] + r);
+      emax = fmax(emax, e2[i]);
+    }
+    const double tn = fmax(fabs(lo), fabs(hi));
+    s_lo = lo - 2.0 * DBL_EPSILON * tn * n - DBL_MIN;
+    s_hi = hi + 2.0 * DBL_EPSILON * tn * n + DBL_MIN;
+    s_pivmin = DBL_MIN * fmax(1.0, emax);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (k >= n) return;
+  double lo = s_lo, hi = s_hi;
+  for (int it = 0; it < 64; ++it) {
+    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + s_pivmin) break;
+    const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+    const int cnt = sturm_count(n, d, e2, x, s_pivmin);
+    const unsigned above = __ballot_sync(0xffffffffu, cnt > k);
+    const int l = above ? __ffs(above) - 1 : 32;  // first point with more than k eigenvalues below it
+    const double xl = __shfl_sync(0xffffffffu, x, l < 32 ? l : 31);
+    const double xm = __shfl_sync(0xffffffffu, x, l > 0 ? l - 1 : 0);
+    const double nlo = l == 0 ? lo : xm;
+    const double nhi = l == 32 ? hi : xl;
+    if (!(nhi - nlo < hi - lo)) break;
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane == 0) w[k] = 0.5 * (lo + hi);
+}
+
+// -------------------------------------------------------------------------------------------------
+// 3. block inverse iteration (one CTA, n <= blockDim.x). Z: column j = eigenvector j of T'
+// (row-major n x n). lu: 5 n^2 doubles (U rows, reciprocal pivot, multipliers, interchange flags).
+// -------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_invit(int n, const double* __restrict__ d, const double* __restrict__ e,
+                                                const double* __restrict__ w, double* __restrict__ Z,
+                                                double* __restrict__ lu, int* __restrict__ info) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* lam = reinterpret_cast<double*>(smem_raw);   // n shifts
+  int* cstart = reinterpret_cast<int*>(lam + n);        // n + 1
+  __shared__ int s_nclu;
+  __shared__ double s_tiny;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const double eps = DBL_EPSILON;
+  if (tid == 0) {
+    double t1 = 0.0;
+    for (int i = 0; i < n; ++i)
+      t1 = fmax(t1, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0));
+    t1 = fmax(t1, DBL_MIN);
+    const double ortol = 1e-3 * t1, tiny = eps * t1;
+    s_tiny = tiny;
+    int nc = 0;
+    for (int j = 0; j < n; ++j) {
+      double l = w[j];
+      if (j == 0 || w[j] - w[j - 1] > ortol) {
+        cstart[nc++] = j;
+      } else if (l - lam[j - 1] < 10.0 * eps * fabs(l) + tiny) {
+        l = lam[j - 1] + 10.0 * eps * fabs(l) + tiny;  // distinct shifts inside a cluster
+      }
+      lam[j] = l;
+    }
+    cstart[nc] = n;
+    s_nclu = nc;
+  }
+  __syncthreads();
+  const double tiny = s_tiny;
+  const size_t nn = (size_t)n * n;
+  double* U1 = lu;
+  double* U2 = lu + nn;
+  double* R0 = lu + 2 * nn;  // 1 / (guarded pivot)
+  double* L = lu + 3 * nn;
+  double* SW = lu + 4 * nn;
+  if (tid < n) {  // LU of T' - lam_j with partial pivoting; element i of column j at [i*n + j]
+    const int j = tid;
+    const double l = lam[j];
+    double p = d[0] - l, q = n > 1 ? e[0] : 0.0, r = 0.0;
+    for (int i = 0; i + 1 < n; ++i) {
+      const double b = e[i];
+      const double a1 = d[i + 1] - l, c1 = (i + 2 < n) ? e[i + 1] : 0.0;
+      double u0, u1, u2, mlt, sw;
+      if (fabs(p) >= fabs(b)) {
+        mlt = (p != 0.0) ? b / p : 0.0;
+        u0 = p; u1 = q; u2 = r; sw = 0.0;
+        p = a1 - mlt * q;
+        q = c1 - mlt * r;
+      } else {
+        mlt = p / b;
+        u0 = b; u1 = a1; u2 = c1; sw = 1.0;
+        p = q - mlt * a1;
+        q = r - mlt * c1;
+      }
+      r = 0.0;
+      if (fabs(u0) < tiny) u0 = u0 < 0.0 ? -tiny : tiny;
+      const size_t o = (size_t)i * n + j;
+      R0[o] = 1.0 / u0; U1[o] = u1; U2[o] = u2; L[o] = mlt; SW[o] = sw;
+    }
+    if (fabs(p) < tiny) p = p < 0.0 ? -tiny : tiny;
+    const size_t o = (size_t)(n - 1) * n + j;
+    R0[o] = 1.0 / p; U1[o] = 0.0; U2[o] = 0.0; L[o] = 0.0; SW[o] = 0.0;
+    for (int i = 0; i < n; ++i) Z[(size_t)i * n + j] = (double)(((i * 7919 + j * 104729) % 1999) + 1) / 1999.0 - 0.5;
+  }
+  __syncthreads();
+  for (int it = 0; it < 3; ++it) {
+    if (tid < n) {  // solve (T' - lam_j) z = z in place
+      const int j = tid;
+      for (int i = 0; i + 1 < n; ++i) {
+        const size_t o = (size_t)i * n + j;
+        double zi = Z[o], zi1 = Z[o + n];
+        if (SW[o] != 0.0) { const double t = zi; zi = zi1; zi1 = t; }
+        Z[o] = zi;
+        Z[o + n] = zi1 - L[o] * zi;
+      }
+      for (int i = n - 1; i >= 0; --i) {
+        const size_t o = (size_t)i * n + j;
+        double s = Z[o];
+        if (i + 1 < n) s -= U1[o] * Z[o + n];
+        if (i + 2 < n) s -= U2[o] * Z[o + 2 * n];
+        Z[o] = s * R0[o];
+      }
+    }
+    __syncthreads();
+    for (int cl = warp; cl < s_nclu; cl += nw) {  // orthonormalise each cluster in eigenvalue order
+      const int c0 = cstart[cl], c1 = cstart[cl + 1];
+      for (int j = c0; j < c1; ++j) {
+        for (int q = c0; q < j; ++q) {
+          double s = 0.0;
+          for (int i = lane; i < n; i += 32) s += Z[(size_t)i * n + j] * Z[(size_t)i * n + q];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          for (int i = lane; i < n; i += 32) Z[(size_t)i * n + j] -= s * Z[(size_t)i * n + q];
+          __syncwarp();
+        }
+        double nrm = 0.0;
+        for (int i = lane; i < n; i += 32) nrm += Z[(size_t)i * n + j] * Z[(size_t)i * n + j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+        if (!(nrm > 0.0) || !isfinite(nrm)) {
+          if (lane == 0) atomicExch(info, 1);
+          nrm = 1.0;
+        }
+        const double inv = 1.0 / sqrt(nrm);
+        for (int i = lane; i < n; i += 32) Z[(size_t)i * n + j] *= inv;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// -------------------------------------------------------------------------------------------------
+// 4. back-transformation: V[:, c] = H_0 H_1 ... H_{n-2} D^H Z[:, c]; one warp per column
+// -------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_backtransform(int n, const double2* __restrict__ A,
+                                                       const double* __restrict__ tau,
+                                                       const double2* __restrict__ ph,
+                                                       const double* __restrict__ Z, double2* __restrict__ V) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int cpb = blockDim.x >> 5;  // columns per CTA
+  double2* vc = reinterpret_cast<double2*>(smem_raw);  // n x cpb
+  const int lane = threadIdx.x & 31, wc = threadIdx.x >> 5;
+  const int col = blockIdx.x * cpb + wc;
+  if (col >= n) return;
+  for (int i = lane; i < n; i += 32) vc[(size_t)i * cpb + wc] = cscale(cconj(ph[i]), Z[(size_t)i * n + col]);
+  __syncwarp();
+  for (int j = n - 2; j >= 0; --j) {
+    const double t = tau[j];
+    if (t == 0.0) continue;
+    const int m = n - j - 1;
+    double2 s = make_double2(0.0, 0.0);
+    for (int i = lane; i < m; i += 32)
+      s = cadd(s, cmul(cconj(A[(size_t)(j + 1 + i) * n + j]), vc[(size_t)(j + 1 + i) * cpb + wc]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+      s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+    }
+    s = cscale(s, t);
+    for (int i = lane; i < m; i += 32) {
+      double2& v = vc[(size_t)(j + 1 + i) * cpb + wc];
+      v = csub(v, cmul(A[(size_t)(j + 1 + i) * n + j], s));
+    }
+    __syncwarp();
+  }
+  for (int i = lane; i < n; i += 32) V[(size_t)i * n + col] = vc[(size_t)i * cpb + wc];
+}
+
+// CTAs of a cooperative launch of `kernel` with `threads` threads and `smem` bytes: at most `cap`,
+// and no more than can be co-resident.
+int coop_grid(Ctx* c, const void* kernel, int threads, size_t smem, int cap, int* grid) {
+  int dev = 0, sms = 0, per_sm = 0;
+  PARO_CU(c, cudaGetDevice(&dev));
+  PARO_CU(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  PARO_CU(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem));
+  int g = per_sm * sms;
+  if (g > cap) g = cap;
+  if (g < 1) return fail(c, PARO_ERR_ARG, "cooperative kernel cannot be resident");
+  *grid = g;
+  return PARO_OK;
+}
+
+int eigh(Ctx* c, int n, const double2* a, double* w, double2* v) {
+  if (n < 1 || n > 1024) return fail(c, PARO_ERR_ARG, "eigh: n must be in [1, 1024]");
+  double2* A = static_cast<double2*>(ws_get(c, "eigh_A", (size_t)n * n * sizeof(double2)));
+  double* Z = static_cast<double*>(ws_get(c, "eigh_Z", (size_t)n * n * sizeof(double)));
+  double* dt = static_cast<double*>(ws_get(c, "eigh_dt", (size_t)n * 4 * sizeof(double)));
+  double2* cw = static_cast<double2*>(ws_get(c, "eigh_cw", (size_t)n * 4 * sizeof(double2)));
+  double* lu = static_cast<double*>(ws_get(c, "eigh_lu", (size_t)5 * n * n * sizeof(double)));
+  int* flags = static_cast<int*>(ws_get(c, "eigh_flags", 16 * sizeof(int)));
+  if (!A || !Z || !dt || !cw || !lu || !flags) return PARO_ERR_CUDA;
+  double *d = dt, *e = dt + n, *tau = dt + 2 * n, *sc = dt + 3 * n;
+  double2 *ph = cw, *ecx = cw + n, *ub = cw + 2 * n, *pb = cw + 3 * n;
+  unsigned* bar = reinterpret_cast<unsigned*>(flags);
+  int* err = flags + 2;
+  int* info = flags + 3;
+  PARO_CU(c, cudaMemsetAsync(flags, 0, 16 * sizeof(int), c->stream));
+  k_herm_full<<<(n * n + 255) / 256, 256, 0, c->stream>>>(n, a, A);
+  PARO_LAUNCH(c, "k_herm_full");
+  cudaEvent_t ev = prof_begin(c);
+  const size_t sm1 = (size_t)2 * n * sizeof(double2);
+  int grid = 1;
+  int st = coop_grid(c, (const void*)k_tridiag, 256, sm1, 64, &grid);
+  if (st) return st;
+  {
+    int nn = n;
+    void* args[] = {&nn, &A, &d, &e, &ph, &tau, &ecx, &ub, &pb, &sc, &bar, &err};
+    PARO_CU(c, cudaLaunchCooperativeKernel((const void*)k_tridiag, dim3(grid), dim3(256), args, sm1, c->stream));
+    ++c->launches;
+  }
+  prof_end(c, "k_tridiag", ev);
+  ev = prof_begin(c);
+  k_bisect<<<(n + 3) / 4, 128, (size_t)2 * n * sizeof(double), c->stream>>>(n, d, e, w);
+  PARO_LAUNCH(c, "k_bisect");
+  prof_end(c, "k_bisect", ev);
+  ev = prof_begin(c);
+  const size_t sm3 = (size_t)n * sizeof(double) + (size_t)(n + 1) * sizeof(int);
+  const int t3 = ((n + 31) / 32) * 32 < 256 ? 256 : ((n + 31) / 32) * 32;
+  k_invit<<<1, t3, sm3, c->stream>>>(n, d, e, w, Z, lu, info);
+  PARO_LAUNCH(c, "k_invit");
+  prof_end(c, "k_invit", ev);
+  ev = prof_begin(c);
+  const int cpb = 8;
+  const size_t sm4 = (size_t)n * cpb * sizeof(double2);
+  PARO_CU(c, cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4));
+  k_backtransform<<<(n + cpb - 1) / cpb, 32 * cpb, sm4, c->stream>>>(n, A, tau, ph, Z, v);
+  PARO_LAUNCH(c, "k_backtransform");
+  prof_end(c, "k_backtransform", ev);
+  int h[2] = {0, 0};
+  PARO_CU(c, cudaMemcpyAsync(h, flags + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  PARO_CU(c, cudaStreamSynchronize(c->stream));
+  if (h[0]) return fail(c, PARO_ERR_TIMEOUT, "eigh: grid barrier wait gave up");
+  if (h[1]) return fail(c, PARO_ERR_NOT_CONVERGED, "eigh: inverse iteration produced a zero or non-finite vector");
+  return PARO_OK;
+}
+
+}  // namespace paro

@@ -211,16 +211,20 @@ int apply_h(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* hpsi, double sh
   return PARO_OK;
 }
 
-int sticks_inverse(Ctx* c, int ik, int nb, const double2* psi, double2* S) {
-  int st = configure<double>(c);
+template <typename T>
+int sticks_inverse(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* S) {
+  int st = configure<T>(c);
   if (st) return st;
   const Basis& B = c->bases[ik];
   const dim3 gz((B.ncol + kStickBatch - 1) / kStickBatch, nb);
-  k_zpass_inv<double><<<gz, kZThreads, zpass_smem(c, sizeof(double2)), c->stream>>>(
-      psi, B.npw, S, B.d_col_off, B.d_g_col, B.d_g_z, B.ncol, c->plan[2], c->d_tw64[2], nullptr, kStickBatch);
+  k_zpass_inv<T><<<gz, kZThreads, zpass_smem(c, sizeof(cplx<T>)), c->stream>>>(
+      psi, B.npw, S, B.d_col_off, B.d_g_col, B.d_g_z, B.ncol, c->plan[2], tw_of<T>(c, 2), nullptr, kStickBatch);
   PARO_LAUNCH(c, "k_zpass_inv");
   return PARO_OK;
 }
+
+template int sticks_inverse<double>(Ctx*, int, int, const double2*, double2*);
+template int sticks_inverse<float>(Ctx*, int, int, const float2*, float2*);
 
 template <typename T> static const cplx<T>* beta_of(const Basis& b);
 template <> const double2* beta_of<double>(const Basis& b) { return b.d_beta; }

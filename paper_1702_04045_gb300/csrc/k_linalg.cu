@@ -44,12 +44,17 @@ __global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kslice
     __syncthreads();
 #pragma unroll 8
     for (int kx = 0; kx < 32; ++kx) {
-      const cplx<ACC> a0 = As[2 * ty][kx], a1 = As[2 * ty + 1][kx];
-      const cplx<ACC> b0 = Bs[2 * tx][kx], b1 = Bs[2 * tx + 1][kx];
-      acc[0][0] = cadd(acc[0][0], cmul(a0, b0));
-      acc[0][1] = cadd(acc[0][1], cmul(a0, b1));
-      acc[1][0] = cadd(acc[1][0], cmul(a1, b0));
-      acc[1][1] = cadd(acc[1][1], cmul(a1, b1));
+      const cplx<ACC> a[2] = {As[2 * ty][kx], As[2 * ty + 1][kx]};
+      const cplx<ACC> b[2] = {Bs[2 * tx][kx], Bs[2 * tx + 1][kx]};
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {  // acc += a b, four fused multiply-adds
+          acc[i][j].x = fma(a[i].x, b[j].x, acc[i][j].x);
+          acc[i][j].x = fma(-a[i].y, b[j].y, acc[i][j].x);
+          acc[i][j].y = fma(a[i].x, b[j].y, acc[i][j].y);
+          acc[i][j].y = fma(a[i].y, b[j].x, acc[i][j].y);
+        }
     }
     __syncthreads();
   }
@@ -203,305 +208,96 @@ int gemm_wx(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, con
 }
 
 // ------------------------------------------------------------------------------------------------
-// Cholesky S = L L^H (left-looking, one CTA), then G = conj(L)^{-1} by forward substitution,
-// one column of G per thread. info[0] = 0 or (1 + index of the first non-positive pivot).
-// ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_chol_inv(int n, const double2* __restrict__ S, double2* __restrict__ L,
-                                                   double2* __restrict__ G, int* __restrict__ info) {
-  __shared__ double red[32];
-  __shared__ double s_diag;
-  __shared__ int s_bad;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) s_bad = 0;
-  for (int i = tid; i < n * n; i += nt) L[i] = make_double2(0.0, 0.0);
-  __syncthreads();
+// Cholesky S = L L^H and G = conj(L)^{-1} (cooperative, many CTAs). Right-looking: at step j every CTA
+// reads the pivot S_jj of the updated matrix W, stores column j of L and applies the rank-1 update
+// W_ik -= W_ij conj(W_kj) / W_jj to its share of the trailing lower triangle; a grid barrier closes
+// each step. Then G's columns are independent forward substitutions conj(L) g_j = e_j, one warp per
+// column. info[0] = 0, or 1 + the first column whose pivot is not positive.
+__global__ void __launch_bounds__(256) k_chol(int n, const double2* __restrict__ S, double2* __restrict__ W,
+                                              double2* __restrict__ Lm, double2* __restrict__ G, unsigned* bar,
+                                              int* err, int* info) {
+  const int gth = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const int gwarp = gth >> 5, nwarp = nth >> 5;
+  for (size_t idx = gth; idx < (size_t)n * n; idx += nth) {
+    __stcg(&W[idx], S[idx]);
+    __stcg(&Lm[idx], make_double2(0.0, 0.0));
+  }
+  if (!grid_barrier(bar, err)) return;
   for (int j = 0; j < n; ++j) {
-    double acc = 0.0;
-    for (int k = tid; k < j; k += nt) {
-      const double2 l = L[(size_t)j * n + k];
-      acc += l.x * l.x + l.y * l.y;
+    double djj = __ldcg(&W[(size_t)j * n + j]).x;
+    if (!(djj > 0.0) || !isfinite(djj)) {
+      if (gth == 0) atomicCAS(info, 0, j + 1);
+      djj = 1.0;
     }
-    acc = block_sum(acc, red);
-    if (tid == 0) {
-      const double d = S[(size_t)j * n + j].x - acc;
-      if (!(d > 0.0) || !isfinite(d)) {
-        if (!s_bad) s_bad = j + 1;
-        s_diag = 1.0;
-      } else {
-        s_diag = sqrt(d);
-      }
-      L[(size_t)j * n + j] = make_double2(s_diag, 0.0);
+    const double ljj = sqrt(djj);
+    const int m = n - j - 1;
+    for (int i = gth; i < m; i += nth)
+      __stcg(&Lm[(size_t)(j + 1 + i) * n + j], cscale(__ldcg(&W[(size_t)(j + 1 + i) * n + j]), 1.0 / ljj));
+    if (gth == 0) __stcg(&Lm[(size_t)j * n + j], make_double2(ljj, 0.0));
+    // trailing lower triangle (i >= k > j), element count m (m + 1) / 2
+    const size_t tot = (size_t)m * (m + 1) / 2;
+    const double inv = 1.0 / djj;
+    for (size_t t = gth; t < tot; t += nth) {
+      // t -> (i, k) with 0 <= k <= i < m, row-major over the lower triangle
+      int i = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+      while ((size_t)i * (i + 1) / 2 > t) --i;
+      while ((size_t)(i + 1) * (i + 2) / 2 <= t) ++i;
+      const int k = (int)(t - (size_t)i * (i + 1) / 2);
+      const double2 wi = __ldcg(&W[(size_t)(j + 1 + i) * n + j]);
+      const double2 wk = __ldcg(&W[(size_t)(j + 1 + k) * n + j]);
+      double2* p = &W[(size_t)(j + 1 + i) * n + (j + 1 + k)];
+      double2 v = __ldcg(p);
+      v.x -= (wi.x * wk.x + wi.y * wk.y) * inv;
+      v.y -= (wi.y * wk.x - wi.x * wk.y) * inv;
+      __stcg(p, v);
     }
-    __syncthreads();
-    const double ljj = s_diag;
-    for (int i = j + 1 + tid; i < n; i += nt) {
-      double2 v = S[(size_t)i * n + j];
-      for (int k = 0; k < j; ++k) v = csub(v, cmul(L[(size_t)i * n + k], cconj(L[(size_t)j * n + k])));
-      L[(size_t)i * n + j] = cscale(v, 1.0 / ljj);
-    }
-    __syncthreads();
+    if (!grid_barrier(bar, err)) return;
   }
-  // G = conj(L)^{-1}: column j solves conj(L) g = e_j.
-  for (int j = tid; j < n; j += nt) {
-    for (int i = 0; i < j; ++i) G[(size_t)i * n + j] = make_double2(0.0, 0.0);
-    G[(size_t)j * n + j] = make_double2(1.0 / L[(size_t)j * n + j].x, 0.0);
+  // G = conj(L)^{-1}: column j solves conj(L) g = e_j; lanes share the inner sums
+  for (int j = gwarp; j < n; j += nwarp) {
+    for (int i = lane; i < j; i += 32) G[(size_t)i * n + j] = make_double2(0.0, 0.0);
+    if (lane == 0) G[(size_t)j * n + j] = make_double2(1.0 / __ldcg(&Lm[(size_t)j * n + j]).x, 0.0);
+    __syncwarp();
     for (int i = j + 1; i < n; ++i) {
-      double2 acc2 = make_double2(0.0, 0.0);
-      for (int k = j; k < i; ++k) acc2 = cadd(acc2, cmul(cconj(L[(size_t)i * n + k]), G[(size_t)k * n + j]));
-      G[(size_t)i * n + j] = cscale(acc2, -1.0 / L[(size_t)i * n + i].x);
+      double2 s = make_double2(0.0, 0.0);
+      for (int k = j + lane; k < i; k += 32) s = cadd(s, cmul(cconj(__ldcg(&Lm[(size_t)i * n + k])), G[(size_t)k * n + j]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+      }
+      if (lane == 0) G[(size_t)i * n + j] = cscale(s, -1.0 / __ldcg(&Lm[(size_t)i * n + i]).x);
+      __syncwarp();
     }
   }
-  if (tid == 0) info[0] = s_bad;
 }
+
+int coop_grid(Ctx* c, const void* kernel, int threads, size_t smem, int cap, int* grid);  // k_eigh.cu
 
 int chol_inv(Ctx* c, int n, const double2* s, double2* g) {
+  double2* W = static_cast<double2*>(ws_get(c, "chol_W", (size_t)n * n * sizeof(double2)));
   double2* L = static_cast<double2*>(ws_get(c, "chol_L", (size_t)n * n * sizeof(double2)));
-  int* info = static_cast<int*>(ws_get(c, "chol_info", sizeof(int)));
-  if (!L || !info) return PARO_ERR_CUDA;
+  int* flags = static_cast<int*>(ws_get(c, "chol_flags", 8 * sizeof(int)));
+  if (!W || !L || !flags) return PARO_ERR_CUDA;
+  PARO_CU(c, cudaMemsetAsync(flags, 0, 8 * sizeof(int), c->stream));
+  int grid = 1;
+  int st = coop_grid(c, (const void*)k_chol, 256, 0, 64, &grid);
+  if (st) return st;
+  unsigned* bar = reinterpret_cast<unsigned*>(flags);
+  int* err = flags + 2;
+  int* info = flags + 3;
   cudaEvent_t ev = prof_begin(c);
-  k_chol_inv<<<1, 1024, 0, c->stream>>>(n, s, L, g, info);
-  PARO_LAUNCH(c, "k_chol_inv");
-  prof_end(c, "k_chol_inv", ev);
-  int h = 0;
-  PARO_CU(c, cudaMemcpyAsync(&h, info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  int nn = n;
+  void* args[] = {&nn, (void*)&s, &W, &L, &g, &bar, &err, &info};
+  PARO_CU(c, cudaLaunchCooperativeKernel((const void*)k_chol, dim3(grid), dim3(256), args, 0, c->stream));
+  ++c->launches;
+  prof_end(c, "k_chol", ev);
+  int h[2] = {0, 0};
+  PARO_CU(c, cudaMemcpyAsync(h, flags + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   PARO_CU(c, cudaStreamSynchronize(c->stream));
-  if (h) return fail(c, PARO_ERR_BREAKDOWN, "Cholesky pivot <= 0 at column " + std::to_string(h - 1));
-  return PARO_OK;
-}
-
-// ------------------------------------------------------------------------------------------------
-// Hermitian eigensolver, one CTA, FP64:
-//  1. Householder reduction to tridiagonal form, A <- H_j A H_j with H_j = I - tau u u^H;
-//  2. a diagonal unitary D makes the complex off-diagonals real and non-negative;
-//  3. implicit-shift QL on the real tridiagonal matrix; thread 0 chases each bulge and records its
-//     plane rotations, then every thread applies them to its own row of Z;
-//  4. eigenvectors of A: Q D^H z, with Q = H_0 H_1 ..., sorted by ascending eigenvalue.
-// work: n*n complex (A copy), n*n double (Z, column-major), info[0] = 0 or 1 if QL failed.
-// ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_eigh(int n, const double2* __restrict__ Ain, double2* __restrict__ A,
-                                               double* __restrict__ Z, double* __restrict__ w,
-                                               double2* __restrict__ V, double* __restrict__ dwork,
-                                               int* __restrict__ info) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* ph = reinterpret_cast<double2*>(smem_raw);  // n phases D_j
-  double2* ecx = ph + n;                                // n complex off-diagonals
-  double* d = reinterpret_cast<double*>(ecx + n);       // n
-  double* e = d + n;                                    // n
-  double* tau = e + n;                                  // n
-  double* rs = tau + n;                                 // n rotation sines
-  double* rcs = rs + n;                                 // n rotation cosines
-  int* ri = reinterpret_cast<int*>(rcs + n);            // n rotation indices
-  __shared__ double red[32];
-  __shared__ double2 s_alpha;
-  __shared__ double s_tau, s_K;
-  __shared__ int s_cnt, s_go, s_bad;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  double2* p = reinterpret_cast<double2*>(dwork);     // n complex scratch (p, then w)
-
-  // full Hermitian copy from the lower triangle
-  for (int idx = tid; idx < n * n; idx += nt) {
-    const int i = idx / n, j = idx - i * n;
-    A[idx] = (i >= j) ? Ain[idx] : cconj(Ain[(size_t)j * n + i]);
-  }
-  if (tid == 0) s_bad = 0;
-  __syncthreads();
-
-  // 1. tridiagonalisation
-  for (int j = 0; j + 1 < n; ++j) {
-    const int m = n - j - 1;             // length of x = A[j+1.., j]
-    double nrm2 = 0.0;
-    for (int i = tid; i < m; i += nt) {
-      const double2 x = A[(size_t)(j + 1 + i) * n + j];
-      nrm2 += x.x * x.x + x.y * x.y;
-    }
-    nrm2 = block_sum(nrm2, red);
-    if (tid == 0) {
-      const double2 x0 = A[(size_t)(j + 1) * n + j];
-      const double ax0 = hypot(x0.x, x0.y);
-      const double nx = sqrt(nrm2);
-      if (m == 1 || nx == 0.0 || nrm2 - ax0 * ax0 <= 0.0) {
-        s_tau = 0.0;                     // nothing to annihilate
-        s_alpha = x0;
-      } else {
-        const double2 phase = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
-        s_alpha = make_double2(-phase.x * nx, -phase.y * nx);
-        A[(size_t)(j + 1) * n + j] = csub(x0, s_alpha);  // u_0 = x_0 - alpha, u_i = x_i
-        s_tau = 1.0 / (nrm2 + nx * ax0);                 // 2 / ||u||^2
-      }
-      tau[j] = s_tau;
-      ecx[j] = s_alpha;
-      d[j] = A[(size_t)j * n + j].x;
-    }
-    __syncthreads();
-    const double t = s_tau;
-    if (t != 0.0) {
-      // u_i = A[(j+1+i)*n + j];  p = t * B u, B = A[j+1.., j+1..]; p_i = t * sum_k conj(B[k][i]) u_k (B Hermitian)
-      for (int i = tid; i < m; i += nt) {
-        double2 acc = make_double2(0.0, 0.0);
-        for (int k = 0; k < m; ++k)
-          acc = cadd(acc, cmul(cconj(A[(size_t)(j + 1 + k) * n + (j + 1 + i)]), A[(size_t)(j + 1 + k) * n + j]));
-        p[i] = cscale(acc, t);
-      }
-      __syncthreads();
-      double kre = 0.0;  // u^H p is real
-      for (int i = tid; i < m; i += nt) {
-        const double2 ui = A[(size_t)(j + 1 + i) * n + j];
-        const double2 pi = p[i];
-        kre += ui.x * pi.x + ui.y * pi.y;
-      }
-      kre = block_sum(kre, red);
-      if (tid == 0) s_K = 0.5 * t * kre;
-      __syncthreads();
-      for (int i = tid; i < m; i += nt) p[i] = csub(p[i], cscale(A[(size_t)(j + 1 + i) * n + j], s_K));  // w
-      __syncthreads();
-      // B -= u w^H + w u^H
-      for (int idx = tid; idx < m * m; idx += nt) {
-        const int i = idx / m, k = idx - i * m;
-        const double2 ui = A[(size_t)(j + 1 + i) * n + j], uk = A[(size_t)(j + 1 + k) * n + j];
-        const double2 wi = p[i], wk = p[k];
-        double2& b = A[(size_t)(j + 1 + i) * n + (j + 1 + k)];
-        b = csub(b, cadd(cmul(ui, cconj(wk)), cmul(wi, cconj(uk))));
-      }
-      __syncthreads();
-    }
-  }
-  if (tid == 0) d[n - 1] = A[(size_t)(n - 1) * n + (n - 1)].x;
-  __syncthreads();
-
-  // 2. phases: D_0 = 1, D_{j+1} = D_j conj(e_j)/|e_j|; real off-diagonals |e_j|
-  if (tid == 0) {
-    ph[0] = make_double2(1.0, 0.0);
-    for (int j = 0; j + 1 < n; ++j) {
-      const double a = hypot(ecx[j].x, ecx[j].y);
-      e[j] = a;
-      ph[j + 1] = a > 0.0 ? cmul(ph[j], make_double2(ecx[j].x / a, -ecx[j].y / a)) : ph[j];
-    }
-    e[n - 1] = 0.0;
-  }
-  for (int idx = tid; idx < n * n; idx += nt) Z[idx] = 0.0;
-  __syncthreads();
-  for (int k = tid; k < n; k += nt) Z[(size_t)k * n + k] = 1.0;  // Z column-major: Z[col*n + row]
-  __syncthreads();
-
-  // 3. implicit QL; rotation (i, s, c) acts on columns i, i+1 of Z
-  for (int l = 0; l < n; ++l) {
-    int iter = 0;
-    while (true) {
-      if (tid == 0) {
-        int m = l;
-        for (; m < n - 1; ++m) {
-          const double dd = fabs(d[m]) + fabs(d[m + 1]);
-          if (fabs(e[m]) <= DBL_EPSILON * dd) break;
-        }
-        if (m == l) {
-          s_go = 0;
-        } else if (iter >= 60) {
-          s_bad = 1;
-          s_go = 0;
-        } else {
-          ++iter;
-          double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-          double r = hypot(g, 1.0);
-          g = d[m] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
-          double s = 1.0, cs = 1.0, pp = 0.0;
-          int cnt = 0;
-          bool early = false;
-          for (int i = m - 1; i >= l; --i) {
-            const double f = s * e[i], b = cs * e[i];
-            r = hypot(f, g);
-            e[i + 1] = r;
-            if (r == 0.0) {
-              d[i + 1] -= pp;
-              e[m] = 0.0;
-              early = true;
-              break;
-            }
-            s = f / r;
-            cs = g / r;
-            g = d[i + 1] - pp;
-            r = (d[i] - g) * s + 2.0 * cs * b;
-            pp = s * r;
-            d[i + 1] = g + pp;
-            g = cs * r - b;
-            ri[cnt] = i;
-            rs[cnt] = s;
-            rcs[cnt] = cs;
-            ++cnt;
-          }
-          if (!early) {
-            d[l] -= pp;
-            e[l] = g;
-            e[m] = 0.0;
-          }
-          s_cnt = cnt;
-          s_go = 1;
-        }
-      }
-      __syncthreads();
-      if (!s_go) break;
-      const int cnt = s_cnt;
-      for (int k = tid; k < n; k += nt) {
-        for (int t = 0; t < cnt; ++t) {
-          const int i = ri[t];
-          const double s = rs[t], cs = rcs[t];
-          const double zi = Z[(size_t)i * n + k], zi1 = Z[(size_t)(i + 1) * n + k];
-          Z[(size_t)(i + 1) * n + k] = s * zi + cs * zi1;
-          Z[(size_t)i * n + k] = cs * zi - s * zi1;
-        }
-      }
-      __syncthreads();
-    }
-  }
-  __syncthreads();
-
-  // 4. sort and back-transform: column r(k) of V = Q D^H z_k
-  for (int k = tid; k < n; k += nt) {
-    int r = 0;
-    const double dk = d[k];
-    for (int j = 0; j < n; ++j) r += (d[j] < dk) || (d[j] == dk && j < k);
-    w[r] = dk;
-    for (int i = 0; i < n; ++i) V[(size_t)i * n + r] = cscale(cconj(ph[i]), Z[(size_t)k * n + i]);
-  }
-  __syncthreads();
-  for (int j = n - 2; j >= 0; --j) {
-    const double t = tau[j];
-    if (t == 0.0) continue;
-    const int m = n - j - 1;
-    for (int col = tid; col < n; col += nt) {
-      double2 s = make_double2(0.0, 0.0);
-      for (int i = 0; i < m; ++i) s = cadd(s, cmul(cconj(A[(size_t)(j + 1 + i) * n + j]), V[(size_t)(j + 1 + i) * n + col]));
-      s = cscale(s, t);
-      for (int i = 0; i < m; ++i) {
-        double2& v = V[(size_t)(j + 1 + i) * n + col];
-        v = csub(v, cmul(A[(size_t)(j + 1 + i) * n + j], s));
-      }
-    }
-    __syncthreads();
-  }
-  if (tid == 0) info[0] = s_bad;
-}
-
-int eigh(Ctx* c, int n, const double2* a, double* w, double2* v) {
-  if (n < 1 || n > 4096) return fail(c, PARO_ERR_ARG, "eigh: n out of range");
-  double2* A = static_cast<double2*>(ws_get(c, "eigh_A", (size_t)n * n * sizeof(double2)));
-  double* Z = static_cast<double*>(ws_get(c, "eigh_Z", (size_t)n * n * sizeof(double)));
-  double* dw = static_cast<double*>(ws_get(c, "eigh_p", (size_t)n * sizeof(double2)));
-  int* info = static_cast<int*>(ws_get(c, "eigh_info", sizeof(int)));
-  if (!A || !Z || !dw || !info) return PARO_ERR_CUDA;
-  const size_t smem = (size_t)n * (5 * sizeof(double) + 2 * sizeof(double2) + sizeof(int));
-  if (smem > 227 * 1024) return fail(c, PARO_ERR_ARG, "eigh: n too large for shared memory");
-  PARO_CU(c, cudaFuncSetAttribute(k_eigh, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int threads = ((n + 31) / 32) * 32;
-  if (threads < 256) threads = 256;
-  if (threads > 1024) threads = 1024;
-  cudaEvent_t ev = prof_begin(c);
-  k_eigh<<<1, threads, smem, c->stream>>>(n, a, A, Z, w, v, dw, info);
-  PARO_LAUNCH(c, "k_eigh");
-  prof_end(c, "k_eigh", ev);
-  int h = 0;
-  PARO_CU(c, cudaMemcpyAsync(&h, info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  PARO_CU(c, cudaStreamSynchronize(c->stream));
-  if (h) return fail(c, PARO_ERR_NOT_CONVERGED, "eigh: QL iteration limit reached");
+  if (h[0]) return fail(c, PARO_ERR_TIMEOUT, "Cholesky: grid barrier wait gave up");
+  if (h[1]) return fail(c, PARO_ERR_BREAKDOWN, "Cholesky pivot <= 0 at column " + std::to_string(h[1] - 1));
   return PARO_OK;
 }
 

@@ -510,31 +510,43 @@ __global__ void k_density_reduce(int N1, int N2, int N3, int ngrp, const double*
   rho[idx] = accumulate ? rho[idx] + s : s;
 }
 
-int density(Ctx* c, const double2* const* psis, double* rho_dev) {
+template <typename T> static const cplx<T>* twid(const Ctx* c, int ax);
+template <> const double2* twid<double>(const Ctx* c, int ax) { return c->d_tw64[ax]; }
+template <> const float2* twid<float>(const Ctx* c, int ax) { return c->d_tw32[ax]; }
+
+// rho(r) from orbitals in precision T (the FFTs in T, |psi(r)|^2 summed in FP64)
+template <typename T>
+int density(Ctx* c, const cplx<T>* const* psis, double* rho_dev) {
   const int N1 = c->N[0], N2 = c->N[1], N3 = c->N[2];
   const int gsize = 8;
   const int ngrp = (c->nocc + gsize - 1) / gsize;
   double* part = static_cast<double*>(ws_get(c, "dens_part", (size_t)ngrp * c->ngrid * sizeof(double)));
   if (!part) return PARO_ERR_CUDA;
-  const size_t smem = (size_t)N1 * N2 * sizeof(double) + (size_t)(N1 + N2 + N1 * N2) * sizeof(double2);
-  if (smem > 227 * 1024) return fail(c, PARO_ERR_ARG, "density: plane too large for shared memory in FP64");
-  PARO_CU(c, cudaFuncSetAttribute(k_plane_density<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-  const int threads = N1 * N2 > 96 * 96 ? 1024 : 512;
+  const size_t smem = (size_t)N1 * N2 * sizeof(double) + (size_t)(N1 + N2 + N1 * N2) * sizeof(cplx<T>);
+  if (smem > 227 * 1024) return fail(c, PARO_ERR_ARG, "density: plane too large for shared memory");
+  PARO_CU(c, cudaFuncSetAttribute(k_plane_density<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  const int threads = 512;
   for (int ik = 0; ik < c->nk; ++ik) {
     const Basis& B = c->bases[ik];
-    double2* S = static_cast<double2*>(ws_get(c, "sticks64", (size_t)c->nocc * N3 * B.ncol * sizeof(double2)));
+    cplx<T>* S = static_cast<cplx<T>*>(
+        ws_get(c, sizeof(T) == 8 ? "sticks64" : "sticks32", (size_t)c->nocc * N3 * B.ncol * sizeof(cplx<T>)));
     if (!S) return PARO_ERR_CUDA;
-    int st = sticks_inverse(c, ik, c->nocc, psis[ik], S);
+    int st = sticks_inverse<T>(c, ik, c->nocc, psis[ik], S);
     if (st) return st;
-    k_plane_density<double><<<dim3(N3, ngrp), threads, smem, c->stream>>>(
-        S, B.ncol, c->nocc, gsize, B.d_col_x, B.d_col_y, B.d_xrows, B.nxr, c->plan[0], c->plan[1], c->d_tw64[0],
-        c->d_tw64[1], 2.0 * c->kw[ik] / c->omega, part);
+    cudaEvent_t ev = prof_begin(c);
+    k_plane_density<T><<<dim3(N3, ngrp), threads, smem, c->stream>>>(
+        S, B.ncol, c->nocc, gsize, B.d_col_x, B.d_col_y, B.d_xrows, B.nxr, c->plan[0], c->plan[1], twid<T>(c, 0),
+        twid<T>(c, 1), 2.0 * c->kw[ik] / c->omega, part);
     PARO_LAUNCH(c, "k_plane_density");
+    prof_end(c, sizeof(T) == 8 ? "k_plane_density<f64>" : "k_plane_density<f32>", ev);
     k_density_reduce<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(N1, N2, N3, ngrp, part, rho_dev, ik > 0);
     PARO_LAUNCH(c, "k_density_reduce");
   }
   return PARO_OK;
 }
+
+template int density<double>(Ctx*, const double2* const*, double*);
+template int density<float>(Ctx*, const float2* const*, double*);
 
 // ------------------------------------------------------------------------------------------------
 // energy terms
@@ -598,8 +610,13 @@ int energy_terms(Ctx* c, const double* rho_dev, double terms[7]) {
     if (c->have_kb) {
       double2* P = static_cast<double2*>(ws_get(c, "kb_proj", (size_t)c->nproj * c->nb * sizeof(double2)));
       if (!P) return PARO_ERR_CUDA;
-      st = gemm_cn<double, double, double>(c, c->nproj, c->nocc, B.npw, B.d_beta, B.npw, B.d_psi, B.npw, P, c->nocc,
-                                          false);
+      // <beta|psi>: FP64 on the FP64 path; the mixed path projects its FP32 orbitals in FP32 (the
+      // energy sum itself stays FP64)
+      st = c->prec == PARO_MIXED && B.d_psi32
+               ? gemm_cn<float, float, float>(c, c->nproj, c->nocc, B.npw, B.d_beta32, B.npw, B.d_psi32, B.npw, P,
+                                              c->nocc, false)
+               : gemm_cn<double, double, double>(c, c->nproj, c->nocc, B.npw, B.d_beta, B.npw, B.d_psi, B.npw, P,
+                                                 c->nocc, false);
       if (st) return st;
       k_nonlocal<<<c->nocc, 256, 0, c->stream>>>(c->nproj, c->nocc, P, c->d_dvec, part);
       PARO_LAUNCH(c, "k_nonlocal");

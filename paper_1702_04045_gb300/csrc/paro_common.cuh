@@ -178,6 +178,39 @@ __device__ void fft_lines(cplx<T>* s, const FftPlan& p, int nlines, int es, LB l
   }
 }
 
+// Grid-wide barrier for kernels started with cudaLaunchCooperativeKernel (all CTAs co-resident).
+// bar[0] counts arrivals, bar[1] is the generation. The wait is bounded: after ~2^24 polls (about a
+// second) the CTA sets *err and the barrier returns false, so a kernel can leave instead of hanging.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(bar, 1u) == gridDim.x * gridDim.y * gridDim.z - 1) {
+      bar[0] = 0;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned polls = 0;
+      while (*gen == g) {
+        if (++polls > (1u << 24) || *(volatile int*)err) {
+          atomicExch(err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 // Block-wide sum of one double per thread (blockDim.x a multiple of 32, <= 1024).
 __device__ __forceinline__ double block_sum(double v, double* red) {
 #pragma unroll

@@ -38,6 +38,8 @@ struct Basis {
   // orbitals
   double2* d_psi = nullptr;       // n_bands x npw, orthonormal
   double2* d_hpsi = nullptr;      // H psi of the current orbitals
+  float2* d_psi32 = nullptr;      // mixed precision: the same orbitals and H psi in FP32
+  float2* d_hpsi32 = nullptr;
   std::vector<double> eps;        // Ritz values
   std::vector<double> res;        // residual norms
   bool have_psi = false;
@@ -179,7 +181,8 @@ int build_vloc(Ctx* c);                   // d_vloc from (Z, rc, A, a)
 int build_beta(Ctx* c);                   // d_beta per k
 int set_veff_device(Ctx* c, const double* v_dev);  // vplane, sigma, mean
 int veff_from_density(Ctx* c, const double* rho_dev, double* eh_out, double* exc_out);
-int density(Ctx* c, const double2* const* psis, double* rho_dev);  // from given orbitals (occupied)
+template <typename T>
+int density(Ctx* c, const cplx<T>* const* psis, double* rho_dev);  // from given orbitals (occupied)
 int energy_terms(Ctx* c, const double* rho_dev, double terms[7]);
 int pulay_mix(Ctx* c, const double* rho_out, int depth, double beta);
 int fft3d(Ctx* c, double2* data, bool inverse);  // in place, unnormalised, C order grid
@@ -187,7 +190,8 @@ double ewald(const Ctx* c);
 
 int build_twiddles(Ctx* c);
 // pass 1 of H psi only (z-inverse FFT of the sticks), FP64, for the density
-int sticks_inverse(Ctx* c, int ik, int nb, const double2* psi, double2* S);
+template <typename T>
+int sticks_inverse(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* S);
 
 // ---- batched PCG (k_pcg.cu) ----
 template <typename T>
