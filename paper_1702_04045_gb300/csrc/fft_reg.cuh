@@ -1,0 +1,148 @@
+// Register-resident line FFTs for the H psi passes.
+//
+// A line of N = Q * P points is held by a group of P consecutive lanes of a warp, Q values each. In
+// the natural layout D_in lane p holds v[q] = x[P q + p]. The unnormalised inverse transform
+// (sign +) is the two-factor Cooley-Tukey split n = P q + p, k = k1 + Q k2:
+//   A  Q-point DFT over q inside each lane;
+//   B  twiddle W_N^{p k1};
+//   C  P-point DFT over the lanes by decimation in frequency with warp shuffles, after which lane p
+//      holds k2 = bitrev(p): layout D_out, v[k1] = X[k1 + Q bitrev(p)].
+// The forward transform (sign -) runs the mirror image, C' (the stages of C in reverse order with the
+// decimation-in-time butterfly and conjugate twiddles), B' (W_N^{-k1 p}) and A' (Q-point DFT), and
+// maps D_out back to D_in. So an inverse transform, a pointwise product and a forward transform
+// need no data movement between lanes beyond the shuffles.
+//
+// Twiddles come from the table tw[j] = exp(-2 pi i j / N), j < N, in shared memory.
+#pragma once
+
+#include "paro_common.cuh"
+
+namespace paro {
+
+template <typename T, bool INV>
+__device__ __forceinline__ cplx<T> tw_get(const cplx<T>* tw, int j) {  // exp(-+ 2 pi i j / N)
+  const cplx<T> w = tw[j];
+  return INV ? cconj(w) : w;
+}
+
+template <typename T> __device__ __forceinline__ cplx<T> shfl_xor_c(cplx<T> v, int m) {
+  cplx<T> r;
+  r.x = __shfl_xor_sync(0xffffffffu, v.x, m);
+  r.y = __shfl_xor_sync(0xffffffffu, v.y, m);
+  return r;
+}
+
+template <int P> __device__ __forceinline__ int bitrev_lane(int p) {
+  if (P == 1) return 0;
+  constexpr int bits = P == 2 ? 1 : P == 4 ? 2 : P == 8 ? 3 : P == 16 ? 4 : 5;
+  return (int)(__brev((unsigned)p) >> (32 - bits));
+}
+
+// ---- Q-point DFT in registers, sign by INV; `stride` = N / Q indexes the N-point table ----
+template <typename T, int Q, bool INV> struct RegDft;
+
+template <typename T, bool INV> struct RegDft<T, 1, INV> {
+  static __device__ __forceinline__ void run(cplx<T>*, const cplx<T>*, int) {}
+};
+template <typename T, bool INV> struct RegDft<T, 2, INV> {
+  static __device__ __forceinline__ void run(cplx<T>* v, const cplx<T>*, int) { dft2<T, INV>(v); }
+};
+template <typename T, bool INV> struct RegDft<T, 3, INV> {
+  static __device__ __forceinline__ void run(cplx<T>* v, const cplx<T>*, int) { dft3<T, INV>(v); }
+};
+template <typename T, bool INV> struct RegDft<T, 4, INV> {
+  static __device__ __forceinline__ void run(cplx<T>* v, const cplx<T>*, int) { dft4<T, INV>(v); }
+};
+template <typename T, bool INV> struct RegDft<T, 8, INV> {
+  static __device__ __forceinline__ void run(cplx<T>* v, const cplx<T>*, int) { dft8<T, INV>(v); }
+};
+
+// Q = Q1 Q2: input index q = Q2 q1 + q2, output k = k1 + Q1 k2
+template <typename T, int Q1, int Q2, bool INV>
+__device__ __forceinline__ void reg_dft_2f(cplx<T>* v, const cplx<T>* tw, int stride) {
+  constexpr int Q = Q1 * Q2;
+  cplx<T> a[Q];
+#pragma unroll
+  for (int q2 = 0; q2 < Q2; ++q2) {
+    cplx<T> t[Q1];
+#pragma unroll
+    for (int q1 = 0; q1 < Q1; ++q1) t[q1] = v[Q2 * q1 + q2];
+    RegDft<T, Q1, INV>::run(t, tw, stride * Q2);
+#pragma unroll
+    for (int k1 = 0; k1 < Q1; ++k1)
+      a[k1 * Q2 + q2] = (q2 * k1 == 0) ? t[k1] : cmul(t[k1], tw_get<T, INV>(tw, stride * q2 * k1));
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < Q1; ++k1) {
+    cplx<T> u[Q2];
+#pragma unroll
+    for (int q2 = 0; q2 < Q2; ++q2) u[q2] = a[k1 * Q2 + q2];
+    RegDft<T, Q2, INV>::run(u, tw, stride * Q1);
+#pragma unroll
+    for (int k2 = 0; k2 < Q2; ++k2) v[k1 + Q1 * k2] = u[k2];
+  }
+}
+
+template <typename T, bool INV> struct RegDft<T, 6, INV> {
+  static __device__ __forceinline__ void run(cplx<T>* v, const cplx<T>* tw, int s) { reg_dft_2f<T, 2, 3, INV>(v, tw, s); }
+};
+template <typename T, bool INV> struct RegDft<T, 9, INV> {
+  static __device__ __forceinline__ void run(cplx<T>* v, const cplx<T>* tw, int s) { reg_dft_2f<T, 3, 3, INV>(v, tw, s); }
+};
+template <typename T, bool INV> struct RegDft<T, 12, INV> {
+  static __device__ __forceinline__ void run(cplx<T>* v, const cplx<T>* tw, int s) { reg_dft_2f<T, 4, 3, INV>(v, tw, s); }
+};
+template <typename T, bool INV> struct RegDft<T, 16, INV> {
+  static __device__ __forceinline__ void run(cplx<T>* v, const cplx<T>* tw, int s) { reg_dft_2f<T, 4, 4, INV>(v, tw, s); }
+};
+
+// ---- inverse line transform, D_in -> D_out (sign +, unnormalised) ----
+template <typename T, int Q, int P>
+__device__ __forceinline__ void line_inv(cplx<T>* v, int p, const cplx<T>* tw) {
+  constexpr int N = Q * P;
+  RegDft<T, Q, true>::run(v, tw, P);
+#pragma unroll
+  for (int k1 = 1; k1 < Q; ++k1)
+    if (p) v[k1] = cmul(v[k1], tw_get<T, true>(tw, p * k1));
+#pragma unroll
+  for (int h = P / 2; h >= 1; h >>= 1) {
+    const bool up = (p & h) != 0;
+    const cplx<T> w = tw_get<T, true>(tw, (p & (h - 1)) * (N / (2 * h)));
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const cplx<T> b = shfl_xor_c<T>(v[q], h);
+      v[q] = up ? cmul(csub(b, v[q]), w) : cadd(v[q], b);
+    }
+  }
+}
+
+// ---- forward line transform, D_out -> D_in (sign -) ----
+template <typename T, int Q, int P>
+__device__ __forceinline__ void line_fwd(cplx<T>* v, int p, const cplx<T>* tw) {
+  constexpr int N = Q * P;
+#pragma unroll
+  for (int h = 1; h < P; h <<= 1) {
+    const bool up = (p & h) != 0;
+    const cplx<T> wc = tw_get<T, false>(tw, (p & (h - 1)) * (N / (2 * h)));
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const cplx<T> t = up ? cmul(v[q], wc) : v[q];
+      const cplx<T> o = shfl_xor_c<T>(t, h);
+      v[q] = up ? csub(o, t) : cadd(t, o);
+    }
+  }
+#pragma unroll
+  for (int k1 = 1; k1 < Q; ++k1)
+    if (p) v[k1] = cmul(v[k1], tw_get<T, false>(tw, p * k1));
+  RegDft<T, Q, false>::run(v, tw, P);
+}
+
+// Factorisations N = Q * P used by the register kernels (P lanes per line, Q values per lane).
+template <int N> struct LineShape;
+template <> struct LineShape<32> { static constexpr int Q = 4, P = 8; };
+template <> struct LineShape<36> { static constexpr int Q = 9, P = 4; };
+template <> struct LineShape<48> { static constexpr int Q = 6, P = 8; };
+template <> struct LineShape<72> { static constexpr int Q = 9, P = 8; };
+template <> struct LineShape<128> { static constexpr int Q = 8, P = 16; };
+
+}  // namespace paro

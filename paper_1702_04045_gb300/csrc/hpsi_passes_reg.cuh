@@ -1,0 +1,388 @@
+// Register-FFT H psi passes; included by k_hpsi.cu after its helpers (kStickBatch, tw_of, vplane_of,
+// kin_of), inside namespace paro.
+#pragma once
+
+// ------------------------------------------------------------------------------------------------
+// Register-FFT versions of the three passes for cubic grids N^3 with N in {32, 36, 48, 72, 128}
+// (line FFTs of fft_reg.cuh: one group of P lanes per line, Q values per lane).
+// ------------------------------------------------------------------------------------------------
+template <typename T, int N3>
+__global__ void __launch_bounds__(256) k_zpass_inv_reg(const cplx<T>* __restrict__ psi, int ldpsi,
+                                                       cplx<T>* __restrict__ S, const int* __restrict__ col_off,
+                                                       const int* __restrict__ g_col, const int* __restrict__ g_z,
+                                                       int ncol, const cplx<T>* __restrict__ twz,
+                                                       const int* __restrict__ active, int CB) {
+  using SH = LineShape<N3>;
+  constexpr int Q = SH::Q, P = SH::P, LS = N3 + 1, G = 32 / P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* line = tw + N3;
+  const int b = blockIdx.y;
+  if (active != nullptr && active[b] == 0) return;
+  const int c0 = blockIdx.x * CB;
+  const int ncb = min(CB, ncol - c0);
+  for (int i = threadIdx.x; i < N3; i += blockDim.x) tw[i] = twz[i];
+  for (int i = threadIdx.x; i < ncb * LS; i += blockDim.x) line[i] = mk<T>(0, 0);
+  __syncthreads();
+  const int g0 = col_off[c0], g1 = col_off[c0 + ncb];
+  const cplx<T>* pp = psi + (size_t)b * ldpsi;
+  for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) line[(g_col[g] - c0) * LS + g_z[g]] = pp[g];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int grp = lane / P, p = lane % P, pr = bitrev_lane<P>(p);
+  for (int l0 = warp * G; l0 < ncb; l0 += nw * G) {
+    const int l = l0 + grp;
+    const bool ok = l < ncb;
+    cplx<T>* ln = line + (ok ? l : 0) * LS;
+    cplx<T> v[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) v[q] = ok ? ln[P * q + p] : mk<T>(0, 0);
+    line_inv<T, Q, P>(v, p, tw);
+    __syncwarp();
+    if (ok)
+#pragma unroll
+      for (int k = 0; k < Q; ++k) ln[k + Q * pr] = v[k];
+    __syncwarp();
+  }
+  __syncthreads();
+  cplx<T>* Sb = S + (size_t)b * N3 * ncol;
+  for (int i = threadIdx.x; i < N3 * ncb; i += blockDim.x) {
+    const int z = i / ncb, cc = i - z * ncb;
+    Sb[(size_t)z * ncol + c0 + cc] = line[cc * LS + z];
+  }
+}
+
+template <typename T, int N1, int N2>
+__global__ void __launch_bounds__(256) k_plane_reg(cplx<T>* __restrict__ S, int ncol, const int* __restrict__ col_x,
+                                                   const int* __restrict__ col_y, const int* __restrict__ xrows,
+                                                   int nxr, const cplx<T>* __restrict__ twx,
+                                                   const cplx<T>* __restrict__ twy, const T* __restrict__ vplane,
+                                                   const int* __restrict__ active) {
+  using SX = LineShape<N1>;
+  using SY = LineShape<N2>;
+  constexpr int LS = N2 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* tx = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* ty = tx + N1;
+  cplx<T>* Pl = ty + N2;
+  const int z = blockIdx.x, b = blockIdx.y, N3 = gridDim.x;
+  if (active != nullptr && active[b] == 0) return;
+  for (int i = threadIdx.x; i < N1; i += blockDim.x) tx[i] = twx[i];
+  for (int i = threadIdx.x; i < N2; i += blockDim.x) ty[i] = twy[i];
+  for (int i = threadIdx.x; i < N1 * LS; i += blockDim.x) Pl[i] = mk<T>(0, 0);
+  __syncthreads();
+  cplx<T>* Sz = S + ((size_t)b * N3 + z) * ncol;
+  for (int c = threadIdx.x; c < ncol; c += blockDim.x) Pl[col_x[c] * LS + col_y[c]] = Sz[c];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  {  // inverse along y, rows that hold sticks
+    constexpr int Q = SY::Q, P = SY::P, G = 32 / P;
+    const int grp = lane / P, p = lane % P, pr = bitrev_lane<P>(p);
+    for (int r0 = warp * G; r0 < nxr; r0 += nw * G) {
+      const int r = r0 + grp;
+      const bool ok = r < nxr;
+      cplx<T>* row = Pl + (ok ? xrows[r] : 0) * LS;
+      cplx<T> v[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) v[q] = ok ? row[P * q + p] : mk<T>(0, 0);
+      line_inv<T, Q, P>(v, p, ty);
+      __syncwarp();
+      if (ok)
+#pragma unroll
+        for (int k = 0; k < Q; ++k) row[k + Q * pr] = v[k];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  {  // along x for every column: inverse, times V / N_grid, forward (all in registers)
+    constexpr int Q = SX::Q, P = SX::P, G = 32 / P;
+    const int grp = lane / P, p = lane % P, pr = bitrev_lane<P>(p);
+    const T* V = vplane + (size_t)z * N1 * N2;
+    for (int c0 = warp * G; c0 < N2; c0 += nw * G) {
+      const int y = c0 + grp;
+      const bool ok = y < N2;
+      cplx<T> v[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) v[q] = ok ? Pl[(P * q + p) * LS + y] : mk<T>(0, 0);
+      line_inv<T, Q, P>(v, p, tx);
+#pragma unroll
+      for (int k = 0; k < Q; ++k) v[k] = cscale(v[k], ok ? V[(k + Q * pr) * N2 + y] : (T)0);
+      line_fwd<T, Q, P>(v, p, tx);
+      if (ok)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) Pl[(P * q + p) * LS + y] = v[q];
+    }
+  }
+  __syncthreads();
+  {  // forward along y, rows that hold sticks
+    constexpr int Q = SY::Q, P = SY::P, G = 32 / P;
+    const int grp = lane / P, p = lane % P, pr = bitrev_lane<P>(p);
+    for (int r0 = warp * G; r0 < nxr; r0 += nw * G) {
+      const int r = r0 + grp;
+      const bool ok = r < nxr;
+      cplx<T>* row = Pl + (ok ? xrows[r] : 0) * LS;
+      cplx<T> v[Q];
+#pragma unroll
+      for (int k = 0; k < Q; ++k) v[k] = ok ? row[k + Q * pr] : mk<T>(0, 0);
+      line_fwd<T, Q, P>(v, p, ty);
+      __syncwarp();
+      if (ok)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) row[P * q + p] = v[q];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncol; c += blockDim.x) Sz[c] = Pl[col_x[c] * LS + col_y[c]];
+}
+
+template <typename T, int N3>
+__global__ void __launch_bounds__(256) k_zpass_fwd_reg(const cplx<T>* __restrict__ S, const cplx<T>* __restrict__ psi,
+                                                       int ldpsi, cplx<T>* __restrict__ hpsi, int ldh,
+                                                       const T* __restrict__ kin, T shift,
+                                                       const int* __restrict__ col_off, const int* __restrict__ g_col,
+                                                       const int* __restrict__ g_z, int ncol,
+                                                       const cplx<T>* __restrict__ twz,
+                                                       const int* __restrict__ active, int CB) {
+  using SH = LineShape<N3>;
+  constexpr int Q = SH::Q, P = SH::P, LS = N3 + 1, G = 32 / P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* line = tw + N3;
+  const int b = blockIdx.y;
+  if (active != nullptr && active[b] == 0) return;
+  const int c0 = blockIdx.x * CB;
+  const int ncb = min(CB, ncol - c0);
+  for (int i = threadIdx.x; i < N3; i += blockDim.x) tw[i] = twz[i];
+  const cplx<T>* Sb = S + (size_t)b * N3 * ncol;
+  for (int i = threadIdx.x; i < N3 * ncb; i += blockDim.x) {
+    const int z = i / ncb, cc = i - z * ncb;
+    line[cc * LS + z] = Sb[(size_t)z * ncol + c0 + cc];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int grp = lane / P, p = lane % P, pr = bitrev_lane<P>(p);
+  for (int l0 = warp * G; l0 < ncb; l0 += nw * G) {
+    const int l = l0 + grp;
+    const bool ok = l < ncb;
+    cplx<T>* ln = line + (ok ? l : 0) * LS;
+    cplx<T> v[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) v[k] = ok ? ln[k + Q * pr] : mk<T>(0, 0);
+    line_fwd<T, Q, P>(v, p, tw);
+    __syncwarp();
+    if (ok)
+#pragma unroll
+      for (int q = 0; q < Q; ++q) ln[P * q + p] = v[q];
+    __syncwarp();
+  }
+  __syncthreads();
+  const int g0 = col_off[c0], g1 = col_off[c0 + ncb];
+  const cplx<T>* pp = psi + (size_t)b * ldpsi;
+  cplx<T>* h = hpsi + (size_t)b * ldh;
+  for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+    const cplx<T> v = line[(g_col[g] - c0) * LS + g_z[g]];
+    const cplx<T> cc = pp[g];
+    const T t = kin[g] - shift;
+    h[g] = mk<T>(v.x + t * cc.x, v.y + t * cc.y);
+  }
+}
+
+// dynamic shared memory limit, set once per kernel instantiation and device
+template <typename K> static int set_smem_once(Ctx* c, K kernel, int* done) {
+  int dev = 0;
+  PARO_CU(c, cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64 && done[dev]) return PARO_OK;
+  PARO_CU(c, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  if (dev >= 0 && dev < 64) done[dev] = 1;
+  return PARO_OK;
+}
+
+template <typename T, int N>
+static int passes_reg(Ctx* c, const Basis& B, int nb, const cplx<T>* psi, cplx<T>* S, cplx<T>* hpsi, double shift,
+                      const int* active) {
+  static int done[3][64];
+  const int eb = (int)sizeof(cplx<T>);
+  const bool f64 = sizeof(T) == 8;
+  const size_t smz = (size_t)eb * (N + kStickBatch * (N + 1));
+  const size_t smp = (size_t)eb * (2 * N + N * (N + 1));
+  int st;
+  if ((st = set_smem_once(c, k_zpass_inv_reg<T, N>, done[0])) || (st = set_smem_once(c, k_plane_reg<T, N, N>, done[1])) ||
+      (st = set_smem_once(c, k_zpass_fwd_reg<T, N>, done[2])))
+    return st;
+  const dim3 gz((B.ncol + kStickBatch - 1) / kStickBatch, nb);
+  cudaEvent_t ev = prof_begin(c);
+  k_zpass_inv_reg<T, N><<<gz, 256, smz, c->stream>>>(psi, B.npw, S, B.d_col_off, B.d_g_col, B.d_g_z, B.ncol,
+                                                     tw_of<T>(c, 2), active, kStickBatch);
+  PARO_LAUNCH(c, "k_zpass_inv_reg");
+  prof_end(c, f64 ? "k_zpass_inv<f64>" : "k_zpass_inv<f32>", ev);
+  ev = prof_begin(c);
+  k_plane_reg<T, N, N><<<dim3(c->N[2], nb), 256, smp, c->stream>>>(S, B.ncol, B.d_col_x, B.d_col_y, B.d_xrows, B.nxr,
+                                                                   tw_of<T>(c, 0), tw_of<T>(c, 1), vplane_of<T>(c),
+                                                                   active);
+  PARO_LAUNCH(c, "k_plane_reg");
+  prof_end(c, f64 ? "k_plane<f64>" : "k_plane<f32>", ev);
+  ev = prof_begin(c);
+  k_zpass_fwd_reg<T, N><<<gz, 256, smz, c->stream>>>(S, psi, B.npw, hpsi, B.npw, kin_of<T>(B), (T)shift,
+                                                     B.d_col_off, B.d_g_col, B.d_g_z, B.ncol, tw_of<T>(c, 2), active,
+                                                     kStickBatch);
+  PARO_LAUNCH(c, "k_zpass_fwd_reg");
+  prof_end(c, f64 ? "k_zpass_fwd<f64>" : "k_zpass_fwd<f32>", ev);
+  return PARO_OK;
+}
+
+// Register kernels when the grid is N^3 with a supported N and the plane fits in shared memory.
+template <typename T>
+static int passes_reg_dispatch(Ctx* c, const Basis& B, int nb, const cplx<T>* psi, cplx<T>* S, cplx<T>* hpsi,
+                               double shift, const int* active, bool* used) {
+  *used = false;
+  const int n = c->N[0];
+  if (c->N[1] != n || c->N[2] != n) return PARO_OK;
+  if ((size_t)sizeof(cplx<T>) * (2 * n + n * (n + 1)) > 227 * 1024) return PARO_OK;
+  *used = true;
+  switch (n) {
+    case 32: return passes_reg<T, 32>(c, B, nb, psi, S, hpsi, shift, active);
+    case 36: return passes_reg<T, 36>(c, B, nb, psi, S, hpsi, shift, active);
+    case 48: return passes_reg<T, 48>(c, B, nb, psi, S, hpsi, shift, active);
+    case 72: return passes_reg<T, 72>(c, B, nb, psi, S, hpsi, shift, active);
+    case 128: return passes_reg<T, 128>(c, B, nb, psi, S, hpsi, shift, active);
+    default: *used = false; return PARO_OK;
+  }
+}
+
+// Density planes with the register FFT: per (z-plane, band group) the inverse transforms along y and
+// x of each band, |psi(r)|^2 summed in FP64 in shared memory, the group's plane written to part.
+template <typename T, int N1, int N2>
+__global__ void __launch_bounds__(256) k_plane_density_reg(const cplx<T>* __restrict__ S, int ncol, int nbands,
+                                                           int gsize, const int* __restrict__ col_x,
+                                                           const int* __restrict__ col_y,
+                                                           const int* __restrict__ xrows, int nxr,
+                                                           const cplx<T>* __restrict__ twx,
+                                                           const cplx<T>* __restrict__ twy, double wfac,
+                                                           double* __restrict__ part) {
+  using SX = LineShape<N1>;
+  using SY = LineShape<N2>;
+  constexpr int LS = N2 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* tx = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* ty = tx + N1;
+  cplx<T>* Pl = ty + N2;
+  double* acc = reinterpret_cast<double*>(Pl + N1 * LS);
+  const int z = blockIdx.x, grp_b = blockIdx.y, N3 = gridDim.x;
+  for (int i = threadIdx.x; i < N1; i += blockDim.x) tx[i] = twx[i];
+  for (int i = threadIdx.x; i < N2; i += blockDim.x) ty[i] = twy[i];
+  for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) acc[i] = 0.0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int b0 = grp_b * gsize, b1 = min(nbands, b0 + gsize);
+  for (int b = b0; b < b1; ++b) {
+    for (int i = threadIdx.x; i < N1 * LS; i += blockDim.x) Pl[i] = mk<T>(0, 0);
+    __syncthreads();
+    const cplx<T>* Sz = S + ((size_t)b * N3 + z) * ncol;
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) Pl[col_x[c] * LS + col_y[c]] = Sz[c];
+    __syncthreads();
+    {
+      constexpr int Q = SY::Q, P = SY::P, G = 32 / P;
+      const int grp = lane / P, p = lane % P, pr = bitrev_lane<P>(p);
+      for (int r0 = warp * G; r0 < nxr; r0 += nw * G) {
+        const int r = r0 + grp;
+        const bool ok = r < nxr;
+        cplx<T>* row = Pl + (ok ? xrows[r] : 0) * LS;
+        cplx<T> v[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) v[q] = ok ? row[P * q + p] : mk<T>(0, 0);
+        line_inv<T, Q, P>(v, p, ty);
+        __syncwarp();
+        if (ok)
+#pragma unroll
+          for (int k = 0; k < Q; ++k) row[k + Q * pr] = v[k];
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    {
+      constexpr int Q = SX::Q, P = SX::P, G = 32 / P;
+      const int grp = lane / P, p = lane % P, pr = bitrev_lane<P>(p);
+      for (int c0 = warp * G; c0 < N2; c0 += nw * G) {
+        const int y = c0 + grp;
+        const bool ok = y < N2;
+        cplx<T> v[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) v[q] = ok ? Pl[(P * q + p) * LS + y] : mk<T>(0, 0);
+        line_inv<T, Q, P>(v, p, tx);
+        if (ok)
+#pragma unroll
+          for (int k = 0; k < Q; ++k) {
+            const double re = v[k].x, im = v[k].y;
+            acc[(k + Q * pr) * N2 + y] += re * re + im * im;
+          }
+      }
+    }
+    __syncthreads();
+  }
+  double* out = part + ((size_t)grp_b * N3 + z) * N1 * N2;
+  for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) out[i] = acc[i] * wfac;
+}
+
+template <typename T, int N>
+static int density_planes_reg_n(Ctx* c, const Basis& B, const cplx<T>* S, int ngrp, int gsize, double wfac,
+                                double* part) {
+  static int done[64];
+  int st;
+  if ((st = set_smem_once(c, k_plane_density_reg<T, N, N>, done))) return st;
+  const size_t smem = (size_t)sizeof(cplx<T>) * (2 * N + N * (N + 1)) + (size_t)N * N * sizeof(double);
+  k_plane_density_reg<T, N, N><<<dim3(N, ngrp), 256, smem, c->stream>>>(S, B.ncol, c->nocc, gsize, B.d_col_x,
+                                                                       B.d_col_y, B.d_xrows, B.nxr, tw_of<T>(c, 0),
+                                                                       tw_of<T>(c, 1), wfac, part);
+  PARO_LAUNCH(c, "k_plane_density_reg");
+  return PARO_OK;
+}
+
+template <typename T>
+int density_planes_reg(Ctx* c, int ik, const cplx<T>* S, int ngrp, int gsize, double wfac, double* part, bool* used) {
+  *used = false;
+  const int n = c->N[0];
+  if (c->N[1] != n || c->N[2] != n) return PARO_OK;
+  if ((size_t)sizeof(cplx<T>) * (2 * n + n * (n + 1)) + (size_t)n * n * sizeof(double) > 227 * 1024) return PARO_OK;
+  const Basis& B = c->bases[ik];
+  *used = true;
+  switch (n) {
+    case 32: return density_planes_reg_n<T, 32>(c, B, S, ngrp, gsize, wfac, part);
+    case 36: return density_planes_reg_n<T, 36>(c, B, S, ngrp, gsize, wfac, part);
+    case 48: return density_planes_reg_n<T, 48>(c, B, S, ngrp, gsize, wfac, part);
+    case 72: return density_planes_reg_n<T, 72>(c, B, S, ngrp, gsize, wfac, part);
+    case 128: return density_planes_reg_n<T, 128>(c, B, S, ngrp, gsize, wfac, part);
+    default: *used = false; return PARO_OK;
+  }
+}
+
+// pass 1 alone (z-inverse of the sticks) with the register FFT; false in *used for other grids
+template <typename T>
+static int sticks_inverse_reg(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* S, bool* used) {
+  *used = false;
+  const int n = c->N[2];
+  if (c->N[0] != n || c->N[1] != n) return PARO_OK;
+  const Basis& B = c->bases[ik];
+  const dim3 gz((B.ncol + kStickBatch - 1) / kStickBatch, nb);
+  const size_t smz = (size_t)sizeof(cplx<T>) * (n + kStickBatch * (n + 1));
+  static int done[5][64];
+  int st = PARO_OK;
+  *used = true;
+  switch (n) {
+#define PARO_ZINV_CASE(NN, I)                                                                                    \
+  case NN:                                                                                                      \
+    if ((st = set_smem_once(c, k_zpass_inv_reg<T, NN>, done[I]))) return st;                                    \
+    k_zpass_inv_reg<T, NN><<<gz, 256, smz, c->stream>>>(psi, B.npw, S, B.d_col_off, B.d_g_col, B.d_g_z, B.ncol, \
+                                                        tw_of<T>(c, 2), nullptr, kStickBatch);                  \
+    PARO_LAUNCH(c, "k_zpass_inv_reg");                                                                          \
+    return PARO_OK;
+    PARO_ZINV_CASE(32, 0)
+    PARO_ZINV_CASE(36, 1)
+    PARO_ZINV_CASE(48, 2)
+    PARO_ZINV_CASE(72, 3)
+    PARO_ZINV_CASE(128, 4)
+#undef PARO_ZINV_CASE
+    default:
+      *used = false;
+      return st;
+  }
+}

@@ -12,6 +12,7 @@
 // P = beta^H psi (nproj x nb), then H psi += beta (D o P).
 #include <mutex>
 
+#include "fft_reg.cuh"
 #include "paro_ctx.h"
 
 namespace paro {
@@ -171,6 +172,8 @@ template <typename T> static const T* kin_of(const Basis& b);
 template <> const double* kin_of<double>(const Basis& b) { return b.d_kin; }
 template <> const float* kin_of<float>(const Basis& b) { return b.d_kin32; }
 
+#include "hpsi_passes_reg.cuh"
+
 template <typename T>
 int apply_h(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* hpsi, double shift, const int* active) {
   if (!c->have_veff) return fail(c, PARO_ERR_STATE, "no effective potential set");
@@ -181,6 +184,16 @@ int apply_h(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* hpsi, double sh
   const size_t sbytes = (size_t)nb * c->N[2] * B.ncol * eb;
   cplx<T>* S = static_cast<cplx<T>*>(ws_get(c, sizeof(T) == 8 ? "sticks64" : "sticks32", sbytes));
   if (!S) return PARO_ERR_CUDA;
+  bool used = false;
+  if ((st = passes_reg_dispatch<T>(c, B, nb, psi, S, hpsi, shift, active, &used))) return st;
+  if (used) {
+    if (!c->have_kb) return PARO_OK;
+    cudaEvent_t ev = prof_begin(c);
+    st = kb_apply<T>(c, ik, nb, psi, hpsi);
+    prof_end(c, sizeof(T) == 8 ? "kb_apply<f64>" : "kb_apply<f32>", ev);
+    return st;
+  }
+  // shared-memory Stockham passes for the other grids
   const dim3 gz((B.ncol + kStickBatch - 1) / kStickBatch, nb);
   const bool f64 = sizeof(T) == 8;
   cudaEvent_t ev = prof_begin(c);
@@ -215,6 +228,8 @@ template <typename T>
 int sticks_inverse(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* S) {
   int st = configure<T>(c);
   if (st) return st;
+  bool used = false;
+  if ((st = sticks_inverse_reg<T>(c, ik, nb, psi, S, &used)) || used) return st;
   const Basis& B = c->bases[ik];
   const dim3 gz((B.ncol + kStickBatch - 1) / kStickBatch, nb);
   k_zpass_inv<T><<<gz, kZThreads, zpass_smem(c, sizeof(cplx<T>)), c->stream>>>(
@@ -225,6 +240,8 @@ int sticks_inverse(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* S) {
 
 template int sticks_inverse<double>(Ctx*, int, int, const double2*, double2*);
 template int sticks_inverse<float>(Ctx*, int, int, const float2*, float2*);
+template int density_planes_reg<double>(Ctx*, int, const double2*, int, int, double, double*, bool*);
+template int density_planes_reg<float>(Ctx*, int, const float2*, int, int, double, double*, bool*);
 
 template <typename T> static const cplx<T>* beta_of(const Basis& b);
 template <> const double2* beta_of<double>(const Basis& b) { return b.d_beta; }

@@ -17,39 +17,48 @@ template <typename TO, typename TI> __device__ __forceinline__ cplx<TO> cvt(cplx
 }
 
 // ------------------------------------------------------------------------------------------------
-// C = conj(A) B^T, 32 x 32 output tile per CTA, K split over gridDim.z into fixed slices.
+// C = conj(A) B^T, 64 x 64 output tile per CTA (256 threads, 4 x 4 complex accumulators each, rows
+// ty + 16 i and columns tx + 16 j), K split over gridDim.z into fixed slices of 16-wide steps.
 // part[z][m][n] receives the slice sums (complex double).
 // ------------------------------------------------------------------------------------------------
+static const int kCnTile = 64;
+
 template <typename TA, typename TB, typename ACC>
 __global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kslice, const cplx<TA>* __restrict__ A,
                                                  int lda, const cplx<TB>* __restrict__ B, int ldb,
                                                  double2* __restrict__ part, int herm) {
-  const int tm = blockIdx.y * 32, tn = blockIdx.x * 32;
+  const int tm = blockIdx.y * kCnTile, tn = blockIdx.x * kCnTile;
   if (herm && tm > tn) return;
   const int k0 = blockIdx.z * kslice, k1 = min(K, k0 + kslice);
-  __shared__ cplx<ACC> As[32][33], Bs[32][33];
+  __shared__ cplx<ACC> As[16][kCnTile + 1], Bs[16][kCnTile + 1];
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  cplx<ACC> acc[2][2];
+  cplx<ACC> acc[4][4];
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) acc[i][j] = mk<ACC>(0, 0);
-  for (int kk = k0; kk < k1; kk += 32) {
-    for (int i = tid; i < 1024; i += 256) {
-      const int r = i >> 5, kx = i & 31, gk = kk + kx;
+    for (int j = 0; j < 4; ++j) acc[i][j] = mk<ACC>(0, 0);
+  for (int kk = k0; kk < k1; kk += 16) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int i = tid + 256 * t;
+      const int r = i >> 4, kx = i & 15, gk = kk + kx;
       const int gm = tm + r, gn = tn + r;
-      As[r][kx] = (gm < M && gk < k1) ? cconj(cvt<ACC, TA>(A[(size_t)gm * lda + gk])) : mk<ACC>(0, 0);
-      Bs[r][kx] = (gn < N && gk < k1) ? cvt<ACC, TB>(B[(size_t)gn * ldb + gk]) : mk<ACC>(0, 0);
+      As[kx][r] = (gm < M && gk < k1) ? cconj(cvt<ACC, TA>(A[(size_t)gm * lda + gk])) : mk<ACC>(0, 0);
+      Bs[kx][r] = (gn < N && gk < k1) ? cvt<ACC, TB>(B[(size_t)gn * ldb + gk]) : mk<ACC>(0, 0);
     }
     __syncthreads();
-#pragma unroll 8
-    for (int kx = 0; kx < 32; ++kx) {
-      const cplx<ACC> a[2] = {As[2 * ty][kx], As[2 * ty + 1][kx]};
-      const cplx<ACC> b[2] = {Bs[2 * tx][kx], Bs[2 * tx + 1][kx]};
+#pragma unroll 4
+    for (int kx = 0; kx < 16; ++kx) {
+      cplx<ACC> a[4], b[4];
 #pragma unroll
-      for (int i = 0; i < 2; ++i)
+      for (int i = 0; i < 4; ++i) {
+        a[i] = As[kx][ty + 16 * i];
+        b[i] = Bs[kx][tx + 16 * i];
+      }
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {  // acc += a b, four fused multiply-adds
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {  // acc += a b, four fused multiply-adds
           acc[i][j].x = fma(a[i].x, b[j].x, acc[i][j].x);
           acc[i][j].x = fma(-a[i].y, b[j].y, acc[i][j].x);
           acc[i][j].y = fma(a[i].x, b[j].y, acc[i][j].y);
@@ -60,10 +69,10 @@ __global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kslice
   }
   double2* pz = part + (size_t)blockIdx.z * M * N;
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int m = tm + 2 * ty + i, n = tn + 2 * tx + j;
+    for (int j = 0; j < 4; ++j) {
+      const int m = tm + ty + 16 * i, n = tn + tx + 16 * j;
       if (m < M && n < N) pz[(size_t)m * N + n] = make_double2((double)acc[i][j].x, (double)acc[i][j].y);
     }
 }
@@ -73,26 +82,34 @@ __global__ void k_reduce_parts(int M, int N, int nz, const double2* __restrict__
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= M * N) return;
   const int m = idx / N, n = idx - m * N;
-  const bool mirror = herm && (m / 32) > (n / 32);
+  const bool mirror = herm && (m / kCnTile) > (n / kCnTile);
   const size_t off = mirror ? (size_t)n * N + m : (size_t)m * N + n;
   double2 s = make_double2(0.0, 0.0);
   for (int z = 0; z < nz; ++z) s = cadd(s, part[(size_t)z * M * N + off]);
   C[(size_t)m * ldc + n] = mirror ? cconj(s) : s;
 }
 
+// K slices: enough CTAs for two waves of the 152 SMs, slices of at least 256 and a multiple of 16
+static void split_k(int tiles, int K, size_t max_slices, int* nz_out, int* kslice_out) {
+  int nz = (2 * 152 + tiles - 1) / tiles;
+  const int maxz = (K + 255) / 256;
+  if (nz > maxz) nz = maxz;
+  if ((size_t)nz > max_slices) nz = (int)max_slices;
+  if (nz < 1) nz = 1;
+  const int kslice = ((K + nz - 1) / nz + 15) / 16 * 16;
+  nz = (K + kslice - 1) / kslice;
+  *nz_out = nz < 1 ? 1 : nz;
+  *kslice_out = kslice;
+}
+
 template <typename TA, typename TB, typename ACC>
 int gemm_cn(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb, double2* C,
             int ldc, bool herm) {
   if (M <= 0 || N <= 0) return PARO_OK;
-  const int tiles_m = (M + 31) / 32, tiles_n = (N + 31) / 32;
+  const int tiles_m = (M + kCnTile - 1) / kCnTile, tiles_n = (N + kCnTile - 1) / kCnTile;
   const int tiles = herm ? tiles_m * (tiles_m + 1) / 2 : tiles_m * tiles_n;
-  int nz = (2 * 152 + tiles - 1) / tiles;
-  const int maxz = (K + 255) / 256;
-  if (nz > maxz) nz = maxz;
-  if (nz < 1) nz = 1;
-  const int kslice = ((K + nz - 1) / nz + 31) / 32 * 32;
-  nz = (K + kslice - 1) / kslice;
-  if (nz < 1) nz = 1;
+  int nz = 1, kslice = 16;
+  split_k(tiles, K, (size_t)1 << 20, &nz, &kslice);
   double2* part = static_cast<double2*>(ws_get(c, "gemm_parts", (size_t)nz * M * N * sizeof(double2)));
   if (!part) return PARO_ERR_CUDA;
   if (K == 0) {
@@ -118,16 +135,11 @@ int gemm_cn_scratch(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, con
   if (K <= 0) return fail(c, PARO_ERR_ARG, "gemm: K must be positive");
   const size_t slice = (size_t)M * N;
   if (part_elems < slice) return fail(c, PARO_ERR_ARG, "gemm: scratch smaller than one K slice");
-  const int tiles = ((M + 31) / 32) * ((N + 31) / 32);
-  int nz = (2 * 152 + tiles - 1) / tiles;
-  const int maxz = (K + 255) / 256;
-  if (nz > maxz) nz = maxz;
-  if ((size_t)nz > part_elems / slice) nz = (int)(part_elems / slice);
-  if (nz < 1) nz = 1;
-  const int kslice = ((K + nz - 1) / nz + 31) / 32 * 32;
-  nz = (K + kslice - 1) / kslice;
-  k_gemm_cn<TA, TB, ACC><<<dim3((N + 31) / 32, (M + 31) / 32, nz), 256, 0, c->stream>>>(M, N, K, kslice, A, lda, B,
-                                                                                      ldb, part, 0);
+  const int tiles = ((M + kCnTile - 1) / kCnTile) * ((N + kCnTile - 1) / kCnTile);
+  int nz = 1, kslice = 16;
+  split_k(tiles, K, part_elems / slice, &nz, &kslice);
+  k_gemm_cn<TA, TB, ACC><<<dim3((N + kCnTile - 1) / kCnTile, (M + kCnTile - 1) / kCnTile, nz), 256, 0, c->stream>>>(
+      M, N, K, kslice, A, lda, B, ldb, part, 0);
   PARO_LAUNCH(c, "k_gemm_cn");
   k_reduce_parts<<<(M * N + 255) / 256, 256, 0, c->stream>>>(M, N, nz, part, C, ldc, 0);
   PARO_LAUNCH(c, "k_reduce_parts");

@@ -534,10 +534,14 @@ int density(Ctx* c, const cplx<T>* const* psis, double* rho_dev) {
     int st = sticks_inverse<T>(c, ik, c->nocc, psis[ik], S);
     if (st) return st;
     cudaEvent_t ev = prof_begin(c);
-    k_plane_density<T><<<dim3(N3, ngrp), threads, smem, c->stream>>>(
-        S, B.ncol, c->nocc, gsize, B.d_col_x, B.d_col_y, B.d_xrows, B.nxr, c->plan[0], c->plan[1], twid<T>(c, 0),
-        twid<T>(c, 1), 2.0 * c->kw[ik] / c->omega, part);
-    PARO_LAUNCH(c, "k_plane_density");
+    bool used = false;
+    if ((st = density_planes_reg<T>(c, ik, S, ngrp, gsize, 2.0 * c->kw[ik] / c->omega, part, &used))) return st;
+    if (!used) {
+      k_plane_density<T><<<dim3(N3, ngrp), threads, smem, c->stream>>>(
+          S, B.ncol, c->nocc, gsize, B.d_col_x, B.d_col_y, B.d_xrows, B.nxr, c->plan[0], c->plan[1], twid<T>(c, 0),
+          twid<T>(c, 1), 2.0 * c->kw[ik] / c->omega, part);
+      PARO_LAUNCH(c, "k_plane_density");
+    }
     prof_end(c, sizeof(T) == 8 ? "k_plane_density<f64>" : "k_plane_density<f32>", ev);
     k_density_reduce<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(N1, N2, N3, ngrp, part, rho_dev, ik > 0);
     PARO_LAUNCH(c, "k_density_reduce");

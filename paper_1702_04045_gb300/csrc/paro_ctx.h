@@ -192,6 +192,9 @@ int build_twiddles(Ctx* c);
 // pass 1 of H psi only (z-inverse FFT of the sticks), FP64, for the density
 template <typename T>
 int sticks_inverse(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* S);
+// density planes with the register FFT (cubic grids it supports); *used = false otherwise
+template <typename T>
+int density_planes_reg(Ctx* c, int ik, const cplx<T>* S, int ngrp, int gsize, double wfac, double* part, bool* used);
 
 // ---- batched PCG (k_pcg.cu) ----
 template <typename T>

@@ -73,6 +73,32 @@ def test_apply_h_matches_oracle(kb, kfrac):
     assert _rel(got32, ref) < 2e-6
 
 
+@pytest.mark.parametrize("ecut", [10.0, 14.0, 20.0])
+@pytest.mark.parametrize("kfrac", [(0, 0, 0), (0.25, -1 / 3, 1 / 3)])
+def test_apply_h_register_fft_grids(ecut, kfrac):
+    # cutoffs whose grids (32^3, 36^3, 48^3) take the register-resident line FFTs
+    ctx, prob, _ = _small(kfrac, ecut=ecut, kb=True)
+    assert ctx.grid[0] in (32, 36, 48) and len(set(ctx.grid)) == 1
+    rng = np.random.default_rng(int(ecut))
+    nb = 5
+    psi = rng.standard_normal((nb, prob.basis.npw)) + 1j * rng.standard_normal((nb, prob.basis.npw))
+    ref = prob.h(psi)
+    got = ctx.apply_h(torch.from_numpy(psi).cuda()).cpu().numpy()
+    assert _rel(got, ref) < 1e-12
+    got32 = ctx.apply_h(torch.from_numpy(psi.astype(np.complex64)).cuda()).cpu().numpy()
+    assert _rel(got32, ref) < 2e-6
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 2e-6)])
+def test_density_register_grid_matches_oracle(precision, tol):
+    ctx, prob, (lat, pos, d) = _small(ecut=10.0, nb=20, nocc=16, precision=precision)
+    assert ctx.grid == (32, 32, 32)
+    ctx.set_orbitals(inputs.start_vectors(20, prob.basis.npw, 12))
+    psi = ctx.get_orbitals()
+    sys_ = scf.ScfSystem(lat, pos, 10.0, 20, 16, inputs.LOCAL_PP, d, inputs.KB_RC)
+    assert _rel(ctx.density().cpu().numpy(), sys_.density([psi])) < tol
+
+
 @pytest.mark.parametrize("name", ["si8_local", "si64_scf"])
 def test_apply_h_full_size_sampled_bands(name):
     ctx = _ctx(name)
