@@ -146,9 +146,8 @@ def launch_work(name: str, s):
         if kern.startswith("kb_apply"):
             return "flop", 2 * 8 * npj * nb * npw
     if kern.startswith("k_gemm_cn") and tag in ("gram", "hsub"):
-        t = (nb + 31) // 32
-        frac = (t * (t + 1) / 2) / (t * t) if tag == "gram" else 1.0
-        return "flop", 8 * nb * nb * npw * frac
+        # Hermitian products: the nb (nb + 1) / 2 distinct entries are the algorithmic work
+        return "flop", 8 * nb * (nb + 1) // 2 * npw
     if kern.startswith("k_gemm_wx") and tag in ("orth", "rot"):
         return "flop", 8 * nb * nb * npw
     return None, None

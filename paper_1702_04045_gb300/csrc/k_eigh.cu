@@ -13,10 +13,14 @@
 //     a cluster (eigenvalues closer than 1e-3 ||T'||_1) are orthogonalised in eigenvalue order by one
 //     warp (the standard remedy for close eigenvalues, as in LAPACK's xSTEIN).
 //  4. k_backtransform (warp per column, many CTAs): eigenvectors of A = Q D^H z, Q = H_0 H_1 ...
+#include <cooperative_groups.h>
+
 #include <cfloat>
 #include <cmath>
 
 #include "paro_ctx.h"
+
+namespace cg = cooperative_groups;
 
 namespace paro {
 
@@ -126,6 +130,138 @@ __global__ void __launch_bounds__(256) k_tridiag(int n, double2* __restrict__ A,
       const double a = hypot(ecx[j].x, ecx[j].y);
       e[j] = a;
       ph[j + 1] = a > 0.0 ? cmul(ph[j], make_double2(ecx[j].x / a, -ecx[j].y / a)) : ph[j];
+    }
+    e[n - 1] = 0.0;
+  }
+}
+
+// -------------------------------------------------------------------------------------------------
+// 1'. the same reduction on one thread-block cluster of C CTAs, for matrices that fit in the cluster's
+// shared memory: row g of the full Hermitian matrix lives in CTA g mod C (local row g / C), so the
+// active rows stay spread evenly as the matrix shrinks. Step j: the owner of row j forms u_j from it
+// (column j below the diagonal is the conjugate of row j right of it); cluster barrier; every CTA reads
+// u_j from the owner's shared memory and forms p_i = tau sum_k B_ik u_k for its rows; cluster barrier;
+// every CTA gathers all of p, forms w = p - (tau/2)(u^H p) u in the same order, and updates its rows
+// B -= u w^H + w u^H. u_j is written to U[j][0..m) for the back-transformation. Buffers shared with
+// other CTAs alternate with the step parity; a barrier separates every write from the reads of the
+// step before that used the same buffer.
+// -------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_tridiag_cluster(int n, const double2* __restrict__ a,
+                                                          double2* __restrict__ U, double* __restrict__ d,
+                                                          double* __restrict__ e, double2* __restrict__ ph,
+                                                          double* __restrict__ tau, double2* __restrict__ ecx) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), q = (int)cl.block_rank();
+  const int R = (n + C - 1) / C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* rows = reinterpret_cast<double2*>(smem_raw);  // R x n
+  double2* ubuf = rows + (size_t)R * n;                  // 2 x n: u_j of the steps this CTA owns
+  double2* pl = ubuf + 2 * n;                            // 2 x n: p_i of this CTA's rows, i = g - j - 1
+  double2* ul = pl + 2 * n;                              // u_j (local copy)
+  double2* wl = ul + n;                                  // p, then w
+  double* tb = reinterpret_cast<double*>(wl + n);        // 2: tau_j of owned steps
+  __shared__ double red[32];
+  __shared__ double s_K;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  for (size_t idx = tid; idx < (size_t)R * n; idx += blockDim.x) {
+    const int r = (int)(idx / n), k = (int)(idx - (size_t)r * n), g = q + C * r;
+    rows[idx] = g >= n ? make_double2(0.0, 0.0) : (g >= k ? a[(size_t)g * n + k] : cconj(a[(size_t)k * n + g]));
+  }
+  __syncthreads();
+  for (int j = 0; j + 1 < n; ++j) {
+    const int m = n - j - 1, par = j & 1, owner = j % C;
+    double2* ub = ubuf + par * n;
+    if (q == owner) {
+      const double2* rj = rows + (size_t)(j / C) * n;
+      double nrm2 = 0.0;
+      for (int i = tid; i < m; i += blockDim.x) {
+        const double2 x = cconj(rj[j + 1 + i]);
+        ub[i] = x;
+        nrm2 += x.x * x.x + x.y * x.y;
+      }
+      nrm2 = block_sum(nrm2, red);
+      if (tid == 0) {
+        const double2 x0 = ub[0];
+        const double ax0 = hypot(x0.x, x0.y);
+        const double nx = sqrt(nrm2);
+        double2 alpha = x0;
+        double t = 0.0;
+        if (m > 1 && nx > 0.0 && nrm2 - ax0 * ax0 > 0.0) {
+          const double2 phs = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+          alpha = make_double2(-phs.x * nx, -phs.y * nx);
+          ub[0] = csub(x0, alpha);  // u = x - alpha e_1
+          t = 1.0 / (nrm2 + nx * ax0);  // 2 / ||u||^2
+        }
+        tb[par] = t;
+        tau[j] = t;
+        ecx[j] = alpha;
+        d[j] = rj[j].x;
+      }
+      __syncthreads();
+      for (int i = tid; i < m; i += blockDim.x) U[(size_t)j * n + i] = ub[i];
+    }
+    cl.sync();
+    const double t = *cl.map_shared_rank(tb + par, owner);
+    if (t == 0.0) continue;  // the same t in every CTA: all skip the step together
+    const double2* uo = cl.map_shared_rank(ub, owner);
+    for (int i = tid; i < m; i += blockDim.x) ul[i] = uo[i];
+    __syncthreads();
+    const int r0 = (j + 1 > q) ? (j + 1 - q + C - 1) / C : 0;  // first local row with g > j
+    for (int r = r0 + warp; r < R; r += nwarp) {
+      const int g = q + C * r;
+      if (g >= n) break;
+      const double2* row = rows + (size_t)r * n + (j + 1);
+      double2 acc = make_double2(0.0, 0.0);
+      for (int k = lane; k < m; k += 32) {
+        const double2 b = row[k], u = ul[k];
+        acc.x = fma(b.x, u.x, fma(-b.y, u.y, acc.x));
+        acc.y = fma(b.x, u.y, fma(b.y, u.x, acc.y));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      }
+      if (lane == 0) pl[par * n + (g - j - 1)] = cscale(acc, t);
+    }
+    cl.sync();
+    double kre = 0.0;  // u^H p is real
+    for (int i = tid; i < m; i += blockDim.x) {
+      const double2 p = *cl.map_shared_rank(pl + par * n + i, (j + 1 + i) % C);
+      wl[i] = p;
+      kre += ul[i].x * p.x + ul[i].y * p.y;
+    }
+    kre = block_sum(kre, red);
+    if (tid == 0) s_K = 0.5 * t * kre;
+    __syncthreads();
+    const double K = s_K;
+    for (int i = tid; i < m; i += blockDim.x) wl[i] = csub(wl[i], cscale(ul[i], K));  // w = p - K u
+    __syncthreads();
+    for (int r = r0 + warp; r < R; r += nwarp) {  // B -= u w^H + w u^H on this CTA's rows
+      const int g = q + C * r;
+      if (g >= n) break;
+      const int i = g - j - 1;
+      const double2 ui = ul[i], wi = wl[i];
+      double2* row = rows + (size_t)r * n + (j + 1);
+      for (int k = lane; k < m; k += 32) {
+        const double2 uk = ul[k], wk = wl[k];
+        double2 b = row[k];
+        b.x -= ui.x * wk.x + ui.y * wk.y + wi.x * uk.x + wi.y * uk.y;
+        b.y -= ui.y * wk.x - ui.x * wk.y + wi.y * uk.x - wi.x * uk.y;
+        row[k] = b;
+      }
+    }
+    __syncthreads();
+  }
+  if (q == (n - 1) % C && tid == 0) d[n - 1] = rows[(size_t)((n - 1) / C) * n + (n - 1)].x;
+  __threadfence();
+  cl.sync();  // no CTA leaves while another may still read its shared memory; d and ecx complete
+  if (q == 0 && tid == 0) {
+    ph[0] = make_double2(1.0, 0.0);
+    for (int j = 0; j + 1 < n; ++j) {
+      const double v = hypot(ecx[j].x, ecx[j].y);
+      e[j] = v;
+      ph[j + 1] = v > 0.0 ? cmul(ph[j], make_double2(ecx[j].x / v, -ecx[j].y / v)) : ph[j];
     }
     e[n - 1] = 0.0;
   }
@@ -312,9 +448,10 @@ __global__ void __launch_bounds__(1024) k_invit(int n, const double* __restrict_
 }
 
 // -------------------------------------------------------------------------------------------------
-// 4. back-transformation: V[:, c] = H_0 H_1 ... H_{n-2} D^H Z[:, c]; one warp per column
+// 4. back-transformation: V[:, c] = H_0 H_1 ... H_{n-2} D^H Z[:, c]; one warp per column. Element i of
+// u_j is at U[j sj + i si].
 // -------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_backtransform(int n, const double2* __restrict__ A,
+__global__ void __launch_bounds__(256) k_backtransform(int n, const double2* __restrict__ U, size_t sj, size_t si,
                                                        const double* __restrict__ tau,
                                                        const double2* __restrict__ ph,
                                                        const double* __restrict__ Z, double2* __restrict__ V) {
@@ -331,8 +468,8 @@ __global__ void __launch_bounds__(256) k_backtransform(int n, const double2* __r
     if (t == 0.0) continue;
     const int m = n - j - 1;
     double2 s = make_double2(0.0, 0.0);
-    for (int i = lane; i < m; i += 32)
-      s = cadd(s, cmul(cconj(A[(size_t)(j + 1 + i) * n + j]), vc[(size_t)(j + 1 + i) * cpb + wc]));
+    const double2* u = U + (size_t)j * sj;
+    for (int i = lane; i < m; i += 32) s = cadd(s, cmul(cconj(u[i * si]), vc[(size_t)(j + 1 + i) * cpb + wc]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
@@ -341,7 +478,7 @@ __global__ void __launch_bounds__(256) k_backtransform(int n, const double2* __r
     s = cscale(s, t);
     for (int i = lane; i < m; i += 32) {
       double2& v = vc[(size_t)(j + 1 + i) * cpb + wc];
-      v = csub(v, cmul(A[(size_t)(j + 1 + i) * n + j], s));
+      v = csub(v, cmul(u[i * si], s));
     }
     __syncwarp();
   }
@@ -362,6 +499,43 @@ int coop_grid(Ctx* c, const void* kernel, int threads, size_t smem, int cap, int
   return PARO_OK;
 }
 
+// Cluster shape for k_tridiag_cluster: 16 CTAs where the device allows a cluster of that size with the
+// needed shared memory, else 8; *cls = 0 when neither fits (the grid-barrier kernel is used).
+static int tridiag_cluster_shape(Ctx* c, int n, int* cls, int* thr, size_t* smem) {
+  *cls = 0;
+  PARO_CU(c, cudaFuncSetAttribute(k_tridiag_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  PARO_CU(c, cudaFuncSetAttribute(k_tridiag_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  for (int C : {16, 8}) {
+    const int R = (n + C - 1) / C;
+    const size_t sm = ((size_t)R * n + 6 * (size_t)n) * sizeof(double2) + 2 * sizeof(double);
+    if (sm > 200 * 1024) continue;
+    const int warps = R < 4 ? 4 : (R > 32 ? 32 : R);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(32 * warps);
+    cfg.dynamicSmemBytes = sm;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_tridiag_cluster, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (nclusters >= 1) {
+      *cls = C;
+      *thr = 32 * warps;
+      *smem = sm;
+      return PARO_OK;
+    }
+  }
+  return PARO_OK;
+}
+
 int eigh(Ctx* c, int n, const double2* a, double* w, double2* v) {
   if (n < 1 || n > 1024) return fail(c, PARO_ERR_ARG, "eigh: n must be in [1, 1024]");
   double2* A = static_cast<double2*>(ws_get(c, "eigh_A", (size_t)n * n * sizeof(double2)));
@@ -377,20 +551,44 @@ int eigh(Ctx* c, int n, const double2* a, double* w, double2* v) {
   int* err = flags + 2;
   int* info = flags + 3;
   PARO_CU(c, cudaMemsetAsync(flags, 0, 16 * sizeof(int), c->stream));
-  k_herm_full<<<(n * n + 255) / 256, 256, 0, c->stream>>>(n, a, A);
-  PARO_LAUNCH(c, "k_herm_full");
+  // Householder vectors: row j of A (cluster path) or column j of the work copy (grid path)
+  const double2* Uh = A + n;
+  size_t usj = (size_t)n + 1, usi = (size_t)n;
+  int cls = 0, thr = 0, st;
+  size_t smc = 0;
+  if ((st = tridiag_cluster_shape(c, n, &cls, &thr, &smc))) return st;
   cudaEvent_t ev = prof_begin(c);
-  const size_t sm1 = (size_t)2 * n * sizeof(double2);
-  int grid = 1;
-  int st = coop_grid(c, (const void*)k_tridiag, 256, sm1, 64, &grid);
-  if (st) return st;
-  {
+  if (cls > 0) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cls;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cls);
+    cfg.blockDim = dim3(thr);
+    cfg.dynamicSmemBytes = smc;
+    cfg.stream = c->stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    PARO_CU(c, cudaLaunchKernelEx(&cfg, k_tridiag_cluster, n, a, A, d, e, ph, tau, ecx));
+    ++c->launches;
+    Uh = A;
+    usj = (size_t)n;
+    usi = 1;
+    prof_end(c, "k_tridiag_cluster", ev);
+  } else {
+    k_herm_full<<<(n * n + 255) / 256, 256, 0, c->stream>>>(n, a, A);
+    PARO_LAUNCH(c, "k_herm_full");
+    const size_t sm1 = (size_t)2 * n * sizeof(double2);
+    int grid = 1;
+    if ((st = coop_grid(c, (const void*)k_tridiag, 256, sm1, 64, &grid))) return st;
     int nn = n;
     void* args[] = {&nn, &A, &d, &e, &ph, &tau, &ecx, &ub, &pb, &sc, &bar, &err};
     PARO_CU(c, cudaLaunchCooperativeKernel((const void*)k_tridiag, dim3(grid), dim3(256), args, sm1, c->stream));
     ++c->launches;
+    prof_end(c, "k_tridiag", ev);
   }
-  prof_end(c, "k_tridiag", ev);
   ev = prof_begin(c);
   k_bisect<<<(n + 3) / 4, 128, (size_t)2 * n * sizeof(double), c->stream>>>(n, d, e, w);
   PARO_LAUNCH(c, "k_bisect");
@@ -402,10 +600,10 @@ int eigh(Ctx* c, int n, const double2* a, double* w, double2* v) {
   PARO_LAUNCH(c, "k_invit");
   prof_end(c, "k_invit", ev);
   ev = prof_begin(c);
-  const int cpb = 8;
+  const int cpb = 2;
   const size_t sm4 = (size_t)n * cpb * sizeof(double2);
   PARO_CU(c, cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4));
-  k_backtransform<<<(n + cpb - 1) / cpb, 32 * cpb, sm4, c->stream>>>(n, A, tau, ph, Z, v);
+  k_backtransform<<<(n + cpb - 1) / cpb, 32 * cpb, sm4, c->stream>>>(n, Uh, usj, usi, tau, ph, Z, v);
   PARO_LAUNCH(c, "k_backtransform");
   prof_end(c, "k_backtransform", ev);
   int h[2] = {0, 0};

@@ -17,29 +17,37 @@ template <typename TO, typename TI> __device__ __forceinline__ cplx<TO> cvt(cplx
 }
 
 // ------------------------------------------------------------------------------------------------
-// C = conj(A) B^T, 64 x 64 output tile per CTA (256 threads, 4 x 4 complex accumulators each, rows
-// ty + 16 i and columns tx + 16 j), K split over gridDim.z into fixed slices of 16-wide steps.
-// part[z][m][n] receives the slice sums (complex double).
+// C = conj(A) B^T, (16 R) x (16 R) output tile per CTA (256 threads, R x R complex accumulators each,
+// rows ty + 16 i and columns tx + 16 j), K split over gridDim.z into fixed slices of 16-wide steps.
+// part[z][m][n] receives the slice sums (complex double). R is chosen per call to minimise padding.
+// ACC = double: every product and sum in FP64. ACC = float: FP32 sums over the K slice, or with CARRY the
+// 16 products of one K step are summed in FP32 and that partial sum is carried into FP64 registers, so
+// the FP32 rounding is that of a 16-term sum (the size of the rounding already in FP32 operands) and
+// does not grow with K.
 // ------------------------------------------------------------------------------------------------
-static const int kCnTile = 64;
-
-template <typename TA, typename TB, typename ACC>
+template <typename TA, typename TB, typename ACC, int R, bool CARRY>
 __global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kslice, const cplx<TA>* __restrict__ A,
                                                  int lda, const cplx<TB>* __restrict__ B, int ldb,
                                                  double2* __restrict__ part, int herm) {
-  const int tm = blockIdx.y * kCnTile, tn = blockIdx.x * kCnTile;
+  constexpr int TILE = 16 * R;
+  const int tm = blockIdx.y * TILE, tn = blockIdx.x * TILE;
   if (herm && tm > tn) return;
   const int k0 = blockIdx.z * kslice, k1 = min(K, k0 + kslice);
-  __shared__ cplx<ACC> As[16][kCnTile + 1], Bs[16][kCnTile + 1];
+  __shared__ cplx<ACC> As[16][TILE + 1], Bs[16][TILE + 1];
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  cplx<ACC> acc[4][4];
+  constexpr bool kCarry = CARRY && sizeof(ACC) == 4;
+  cplx<ACC> acc[R][R];
+  double2 carry[R][R];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = mk<ACC>(0, 0);
+    for (int j = 0; j < R; ++j) {
+      acc[i][j] = mk<ACC>(0, 0);
+      carry[i][j] = make_double2(0.0, 0.0);
+    }
   for (int kk = k0; kk < k1; kk += 16) {
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
+    for (int t = 0; t < R; ++t) {
       const int i = tid + 256 * t;
       const int r = i >> 4, kx = i & 15, gk = kk + kx;
       const int gm = tm + r, gn = tn + r;
@@ -49,64 +57,125 @@ __global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kslice
     __syncthreads();
 #pragma unroll 4
     for (int kx = 0; kx < 16; ++kx) {
-      cplx<ACC> a[4], b[4];
+      cplx<ACC> a[R], b[R];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < R; ++i) {
         a[i] = As[kx][ty + 16 * i];
         b[i] = Bs[kx][tx + 16 * i];
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {  // acc += a b, four fused multiply-adds
+        for (int j = 0; j < R; ++j) {  // acc += a b, four fused multiply-adds
           acc[i][j].x = fma(a[i].x, b[j].x, acc[i][j].x);
           acc[i][j].x = fma(-a[i].y, b[j].y, acc[i][j].x);
           acc[i][j].y = fma(a[i].x, b[j].y, acc[i][j].y);
           acc[i][j].y = fma(a[i].y, b[j].x, acc[i][j].y);
         }
     }
+    if (kCarry) {
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          carry[i][j].x += (double)acc[i][j].x;
+          carry[i][j].y += (double)acc[i][j].y;
+          acc[i][j] = mk<ACC>(0, 0);
+        }
+    }
     __syncthreads();
   }
   double2* pz = part + (size_t)blockIdx.z * M * N;
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < R; ++j) {
       const int m = tm + ty + 16 * i, n = tn + tx + 16 * j;
-      if (m < M && n < N) pz[(size_t)m * N + n] = make_double2((double)acc[i][j].x, (double)acc[i][j].y);
+      if (m < M && n < N)
+        pz[(size_t)m * N + n] =
+            kCarry ? carry[i][j] : make_double2((double)acc[i][j].x, (double)acc[i][j].y);
     }
 }
 
 __global__ void k_reduce_parts(int M, int N, int nz, const double2* __restrict__ part, double2* __restrict__ C,
-                               int ldc, int herm) {
+                               int ldc, int herm, int tile) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= M * N) return;
   const int m = idx / N, n = idx - m * N;
-  const bool mirror = herm && (m / kCnTile) > (n / kCnTile);
+  const bool mirror = herm && (m / tile) > (n / tile);
   const size_t off = mirror ? (size_t)n * N + m : (size_t)m * N + n;
   double2 s = make_double2(0.0, 0.0);
   for (int z = 0; z < nz; ++z) s = cadd(s, part[(size_t)z * M * N + off]);
   C[(size_t)m * ldc + n] = mirror ? cconj(s) : s;
 }
 
-// K slices: enough CTAs for two waves of the 152 SMs, slices of at least 256 and a multiple of 16
+// micro-tile R (tile 16 R) with the least padded work for an M x N product; ties go to larger R
+static int pick_r(int M, int N, bool herm) {
+  int best = 4;
+  double best_work = 1e300;
+  for (int r = 4; r >= 2; --r) {
+    const int t = 16 * r, tm = (M + t - 1) / t, tn = (N + t - 1) / t;
+    const double tiles = herm ? tm * (tm + 1) / 2.0 : (double)tm * tn;
+    const double work = tiles * t * t;
+    if (work < best_work * 0.999) {
+      best_work = work;
+      best = r;
+    }
+  }
+  return best;
+}
+
+// K slices: the count nz (at most one per 256 of K, at most max_slices) that minimises the modelled
+// makespan, ceil(tiles nz / 152) waves of CTAs sharing an SM times the 16-wide steps of one slice;
+// ties go to fewer slices (less partial-sum traffic).
 static void split_k(int tiles, int K, size_t max_slices, int* nz_out, int* kslice_out) {
-  int nz = (2 * 152 + tiles - 1) / tiles;
-  const int maxz = (K + 255) / 256;
-  if (nz > maxz) nz = maxz;
-  if ((size_t)nz > max_slices) nz = (int)max_slices;
-  if (nz < 1) nz = 1;
-  const int kslice = ((K + nz - 1) / nz + 15) / 16 * 16;
-  nz = (K + kslice - 1) / kslice;
-  *nz_out = nz < 1 ? 1 : nz;
-  *kslice_out = kslice;
+  const int steps = (K + 15) / 16;
+  int maxz = (K + 255) / 256;
+  if ((size_t)maxz > max_slices) maxz = (int)max_slices;
+  if (maxz < 1) maxz = 1;
+  long long best = -1;
+  int best_nz = 1, best_steps = steps;
+  for (int nz = 1; nz <= maxz; ++nz) {
+    const int s = (steps + nz - 1) / nz;
+    const int z = (steps + s - 1) / s;
+    const long long waves = ((long long)tiles * z + 151) / 152;
+    const long long cost = waves * s;
+    if (best < 0 || cost < best) {
+      best = cost;
+      best_nz = z;
+      best_steps = s;
+    }
+  }
+  *nz_out = best_nz;
+  *kslice_out = best_steps * 16;
+}
+
+template <typename TA, typename TB, typename ACC, bool CARRY>
+static void launch_cn_r(int r, dim3 grid, cudaStream_t st, int M, int N, int K, int kslice, const cplx<TA>* A,
+                        int lda, const cplx<TB>* B, int ldb, double2* part, int herm) {
+  if (r == 2)
+    k_gemm_cn<TA, TB, ACC, 2, CARRY><<<grid, 256, 0, st>>>(M, N, K, kslice, A, lda, B, ldb, part, herm);
+  else if (r == 3)
+    k_gemm_cn<TA, TB, ACC, 3, CARRY><<<grid, 256, 0, st>>>(M, N, K, kslice, A, lda, B, ldb, part, herm);
+  else
+    k_gemm_cn<TA, TB, ACC, 4, CARRY><<<grid, 256, 0, st>>>(M, N, K, kslice, A, lda, B, ldb, part, herm);
+}
+
+template <typename TA, typename TB, typename ACC>
+static void launch_cn(int r, bool carry, dim3 grid, cudaStream_t st, int M, int N, int K, int kslice,
+                      const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb, double2* part, int herm) {
+  if (carry && sizeof(ACC) == 4)
+    launch_cn_r<TA, TB, ACC, true>(r, grid, st, M, N, K, kslice, A, lda, B, ldb, part, herm);
+  else
+    launch_cn_r<TA, TB, ACC, false>(r, grid, st, M, N, K, kslice, A, lda, B, ldb, part, herm);
 }
 
 template <typename TA, typename TB, typename ACC>
 int gemm_cn(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb, double2* C,
-            int ldc, bool herm) {
+            int ldc, bool herm, bool carry) {
   if (M <= 0 || N <= 0) return PARO_OK;
-  const int tiles_m = (M + kCnTile - 1) / kCnTile, tiles_n = (N + kCnTile - 1) / kCnTile;
+  const int r = pick_r(M, N, herm), tile = 16 * r;
+  const int tiles_m = (M + tile - 1) / tile, tiles_n = (N + tile - 1) / tile;
   const int tiles = herm ? tiles_m * (tiles_m + 1) / 2 : tiles_m * tiles_n;
   int nz = 1, kslice = 16;
   split_k(tiles, K, (size_t)1 << 20, &nz, &kslice);
@@ -116,12 +185,13 @@ int gemm_cn(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, const cplx<
     PARO_CU(c, cudaMemsetAsync(part, 0, (size_t)M * N * sizeof(double2), c->stream));
   } else {
     cudaEvent_t ev = prof_begin(c);
-    k_gemm_cn<TA, TB, ACC><<<dim3(tiles_n, tiles_m, nz), 256, 0, c->stream>>>(M, N, K, kslice, A, lda, B, ldb, part,
-                                                                              herm ? 1 : 0);
+    launch_cn<TA, TB, ACC>(r, carry, dim3(tiles_n, tiles_m, nz), c->stream, M, N, K, kslice, A, lda, B, ldb,
+                           part, herm ? 1 : 0);
     PARO_LAUNCH(c, "k_gemm_cn");
     prof_end(c, sizeof(ACC) == 8 ? "k_gemm_cn<f64>" : "k_gemm_cn<f32>", ev);
   }
-  k_reduce_parts<<<(M * N + 255) / 256, 256, 0, c->stream>>>(M, N, K == 0 ? 1 : nz, part, C, ldc, herm ? 1 : 0);
+  k_reduce_parts<<<(M * N + 255) / 256, 256, 0, c->stream>>>(M, N, K == 0 ? 1 : nz, part, C, ldc, herm ? 1 : 0,
+                                                             tile);
   PARO_LAUNCH(c, "k_reduce_parts");
   return PARO_OK;
 }
@@ -135,13 +205,14 @@ int gemm_cn_scratch(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, con
   if (K <= 0) return fail(c, PARO_ERR_ARG, "gemm: K must be positive");
   const size_t slice = (size_t)M * N;
   if (part_elems < slice) return fail(c, PARO_ERR_ARG, "gemm: scratch smaller than one K slice");
-  const int tiles = ((M + kCnTile - 1) / kCnTile) * ((N + kCnTile - 1) / kCnTile);
+  const int r = pick_r(M, N, false), tile = 16 * r;
+  const int tiles_m = (M + tile - 1) / tile, tiles_n = (N + tile - 1) / tile;
   int nz = 1, kslice = 16;
-  split_k(tiles, K, part_elems / slice, &nz, &kslice);
-  k_gemm_cn<TA, TB, ACC><<<dim3((N + kCnTile - 1) / kCnTile, (M + kCnTile - 1) / kCnTile, nz), 256, 0, c->stream>>>(
-      M, N, K, kslice, A, lda, B, ldb, part, 0);
+  split_k(tiles_m * tiles_n, K, part_elems / slice, &nz, &kslice);
+  launch_cn<TA, TB, ACC>(r, false, dim3(tiles_n, tiles_m, nz), c->stream, M, N, K, kslice, A, lda, B, ldb, part,
+                         0);
   PARO_LAUNCH(c, "k_gemm_cn");
-  k_reduce_parts<<<(M * N + 255) / 256, 256, 0, c->stream>>>(M, N, nz, part, C, ldc, 0);
+  k_reduce_parts<<<(M * N + 255) / 256, 256, 0, c->stream>>>(M, N, nz, part, C, ldc, 0, tile);
   PARO_LAUNCH(c, "k_reduce_parts");
   return PARO_OK;
 }
@@ -377,13 +448,9 @@ int convert(Ctx* c, size_t n, const cplx<TS>* src, cplx<TD>* dst) {
 
 // instantiations
 template int gemm_cn<double, double, double>(Ctx*, int, int, int, const double2*, int, const double2*, int, double2*,
-                                             int, bool);
+                                             int, bool, bool);
 template int gemm_cn<float, float, float>(Ctx*, int, int, int, const float2*, int, const float2*, int, double2*, int,
-                                          bool);
-template int gemm_cn<float, float, double>(Ctx*, int, int, int, const float2*, int, const float2*, int, double2*,
-                                           int, bool);
-template int gemm_cn<double, float, double>(Ctx*, int, int, int, const double2*, int, const float2*, int, double2*,
-                                            int, bool);
+                                          bool, bool);
 template int gemm_wx<double, double>(Ctx*, int, int, int, const double2*, int, bool, const double*, const double2*,
                                      int, double2*, int, double);
 template int gemm_wx<float, float>(Ctx*, int, int, int, const double2*, int, bool, const double*, const float2*, int,

@@ -142,11 +142,12 @@ int check_fft_support(Ctx* c, int elem_bytes);
 
 // ---- dense complex linear algebra (k_linalg.cu) ----
 // C[m][n] = sum_k conj(A[m][k]) B[n][k]; A: M x K (lda), B: N x K (ldb); C: M x N (ldc) complex double.
-// Products accumulate in ACC inside a K-slice; slices are summed in double in a fixed order.
+// ACC = double: FP64 throughout. ACC = float: FP32 sums over each K slice, or with carry sums of 16
+// consecutive products in FP32 carried into FP64. K-slice partials are summed in double in a fixed order.
 // herm: A == B, only tiles with m-tile <= n-tile are computed, the rest mirrored.
 template <typename TA, typename TB, typename ACC>
 int gemm_cn(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb,
-            double2* C, int ldc, bool herm);
+            double2* C, int ldc, bool herm, bool carry = false);
 // Y[m][n] = beta Y[m][n] + sum_k s_k W(k, m) X[k][n]; W: complex double, element (k, m) at W[k*ldw + m]
 // (or at W[m*ldw + k] when wt); s: device double[K] or nullptr (1); X: K x N (ldx) of TX;
 // Y: M x N (ldy) of TY; accumulation in TY.
@@ -194,7 +195,17 @@ template <typename T>
 int sticks_inverse(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* S);
 // density planes with the register FFT (cubic grids it supports); *used = false otherwise
 template <typename T>
-int density_planes_reg(Ctx* c, int ik, const cplx<T>* S, int ngrp, int gsize, double wfac, double* part, bool* used);
+int density_planes_reg(Ctx* c, int ik, const cplx<T>* S, int nbands, int ngrp, int gsize, double wfac, double* part,
+                       bool* used);
+// rho(r) (+)= wfac sum_b |psi~_b(r)|^2 over nbands rows of psi at k-point ik (psi~: unnormalised inverse DFT)
+template <typename T>
+int density_bands(Ctx* c, int ik, int nbands, const cplx<T>* psi, double wfac, double* rho_dev, bool accumulate);
+
+// ---- adjoint of H psi (k_adjoint.cu, k_scf.cu) ----
+int apply_h_adjoint(Ctx* c, int ik, int nb, int dtype, const void* psi, const void* w, void* gpsi, double* gv,
+                    double* gpos);
+// gpos[I][a] = dL/dR_Ia through V_loc, from gv = dL/dV(r) (device; overwrites gpos)
+int vloc_position_grad(Ctx* c, const double* gv, double* gpos);
 
 // ---- batched PCG (k_pcg.cu) ----
 template <typename T>
