@@ -83,11 +83,22 @@ int paro_set_local_pp(paro_ctx* ctx, double Z, double rc, double A, double a);
  */
 int paro_set_kb(paro_ctx* ctx, double rc, const double* D);
 
+/*
+ * paro_set_positions -- move the atoms to pos (host double[n_atoms*3], Cartesian Bohr): rebuilds
+ * V_loc(r) and the KB projectors from the new structure factors and the Ewald energy; keeps
+ * V_eff - V_loc (the Hartree and exchange-correlation part, or whatever part of a set V_eff is not
+ * V_loc) and re-takes the Ritz pairs of the current orbitals under the new H.
+ */
+int paro_set_positions(paro_ctx* ctx, const double* pos);
+
 /* paro_set_veff -- fixed effective potential V_eff(r) (Ha) on the grid, C order (N1, N2, N3);
  * host (on_device = 0) or device (on_device = 1) double[N1*N2*N3]. */
 int paro_set_veff(paro_ctx* ctx, const double* v_r, int on_device);
 /* paro_get_veff -- copy the current V_eff(r) to a host double[N1*N2*N3]. */
 int paro_get_veff(paro_ctx* ctx, double* v_r);
+/* paro_get_vloc -- copy the local pseudopotential V_loc(r) of the current positions (Section 2.2,
+ * V_loc) to a host double[N1*N2*N3], C order. PARO_ERR_STATE before paro_set_local_pp. */
+int paro_get_vloc(paro_ctx* ctx, double* v_r);
 
 /* paro_set_density -- V_eff = V_loc + V_H[rho] + V_xc[rho] from a density rho(r) (electrons/Bohr^3,
  * C order, host or device double[N1*N2*N3]): Hartree V_H(G) = 4 pi rho(G)/G^2 (G != 0), LDA
@@ -129,6 +140,24 @@ int paro_apply_h(paro_ctx* ctx, int ik, int nb, int dtype, const void* psi, void
  *   serialised by the caller.
  */
 int paro_apply_h_noalloc(paro_ctx* ctx, int ik, int nb, int dtype, const void* psi, void* hpsi);
+
+/*
+ * paro_apply_h_adjoint -- vector-Jacobian product of Y = H Psi (Eq. e5 with V_loc and the KB projectors
+ * of Section 2.2). The paper applies H but never differentiates it; this is the derivative of that
+ * operator, for gradient-based use of the same Hamiltonian (forces, potential optimisation).
+ * For a real loss L with cotangent W = dL/dRe(Y) + i dL/dIm(Y) (so dL = Re sum conj(W) dY):
+ *   g_psi = dL/dPsi = H W (same convention);
+ *   g_v(r) = dL/dV_eff(r) = N^{-1} Re sum_b conj(W~_b(r)) psi~_b(r), psi~ and W~ the unnormalised
+ *            inverse DFTs of the coefficients on the N = N1 N2 N3 grid;
+ *   g_pos[I][a] = dL/dR_Ia through the structure factors exp(-i G.R_I) of V_loc (with V_eff - V_loc
+ *            held fixed) and exp(-i (k+G).R_I) of the projectors.
+ *   psi, w, g_psi: device nb x npw complex of dtype (row = band); g_v: device double[N1*N2*N3]
+ *   (C order, overwritten); g_pos: device double[n_atoms*3] (overwritten). g_psi, g_v or g_pos may be
+ *   NULL to skip that output. Work runs in the precision of dtype (FP32 FFTs and FP64-carried FP32
+ *   projections for PARO_C32), accumulated in FP64. Enqueued on the context stream, no synchronisation.
+ */
+int paro_apply_h_adjoint(paro_ctx* ctx, int ik, int nb, int dtype, const void* psi, const void* w, void* g_psi,
+                         double* g_v, double* g_pos);
 
 /*
  * paro_solve_source -- the independent source problems of Algorithm 1, step 3, for nb orbitals:

@@ -72,9 +72,10 @@ def grad_pos_local(basis: pw.Basis, pos, pp, g_v) -> np.ndarray:
     return out
 
 
-def grad_pos_kb(basis: pw.Basis, pos, kb, psi, w) -> np.ndarray:
+def grad_pos_kb(basis: pw.Basis, pos, kb, psi, w, atoms=None) -> np.ndarray:
     """dL/dR_I through the projectors, by the product rule on Y_b += sum_p beta_p D_p (beta_p^H psi_b)
-    with d beta_p / dR_Ia = -i (k+G)_a beta_p for the projectors p of atom I."""
+    with d beta_p / dR_Ia = -i (k+G)_a beta_p for the projectors p of atom I (rows of the atoms listed
+    in `atoms` only, the others left zero, when given)."""
     rc, dstr = kb
     beta = pw.kb_beta(basis.lat, pos, basis.q, rc)
     dvec = pw.kb_dvec(dstr)
@@ -83,7 +84,7 @@ def grad_pos_kb(basis: pw.Basis, pos, kb, psi, w) -> np.ndarray:
     pos = np.asarray(pos, dtype=np.float64)
     out = np.zeros_like(pos)
     proj = np.conj(beta) @ psi.T
-    for i_at in range(pos.shape[0]):
+    for i_at in (range(pos.shape[0]) if atoms is None else atoms):
         sel = np.zeros(beta.shape[0], dtype=bool)
         sel[4 * i_at:4 * i_at + 4] = True
         for al in range(3):

@@ -215,7 +215,7 @@ static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal) {
   } else {
     {
       ProfTag t(c, "gram");
-      if ((st = gemm_cn<T, T, double>(c, nx, nx, npw, X, npw, X, npw, S, nx, true))) return st;
+      if ((st = gemm_cn<T, T, T>(c, nx, nx, npw, X, npw, X, npw, S, nx, true, true))) return st;
       if ((st = chol_inv(c, nx, S, G))) return st;
     }
     ProfTag t(c, "orth");
@@ -227,7 +227,7 @@ static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal) {
   }
   {
     ProfTag t(c, "hsub");
-    if ((st = gemm_cn<T, T, double>(c, nx, nx, npw, Y, npw, HY, npw, S, nx, true))) return st;
+    if ((st = gemm_cn<T, T, T>(c, nx, nx, npw, Y, npw, HY, npw, S, nx, true, true))) return st;
     k_hermitize<<<(nx * nx + 255) / 256, 256, 0, c->stream>>>(nx, S);
     PARO_LAUNCH(c, "k_hermitize");
     if ((st = eigh(c, nx, S, w, G))) return st;  // G <- eigenvectors C
@@ -324,7 +324,7 @@ static int build_alg2_basis(Ctx* c, int ik, cplx<T>* E, cplx<T>* X, int* nx_out)
   cplx<T>* psi = psi_of<T>(b);
   int st;
   // P[i][j] = <psi_i, e_j>;  e_j -= sum_i psi_i P[i][j]
-  if ((st = gemm_cn<T, T, double>(c, nb, nb, npw, psi, npw, E, npw, P, nb, false))) return st;
+  if ((st = gemm_cn<T, T, T>(c, nb, nb, npw, psi, npw, E, npw, P, nb, false, true))) return st;
   if ((st = gemm_wx<T, T>(c, nb, npw, nb, P, nb, false, nullptr, psi, npw, tmp, npw, 0.0))) return st;
   k_axpy_rows<T><<<dim3((npw + 255) / 256, nb), 256, 0, c->stream>>>(npw, E, tmp, (T)-1);
   PARO_LAUNCH(c, "k_axpy_rows");
@@ -403,7 +403,7 @@ static int orthonormalize(Ctx* c, int ik, cplx<T>* X, int nx) {
   int st;
   {
     ProfTag t(c, "gram");
-    if ((st = gemm_cn<T, T, double>(c, nx, nx, npw, X, npw, X, npw, S, nx, true))) return st;
+    if ((st = gemm_cn<T, T, T>(c, nx, nx, npw, X, npw, X, npw, S, nx, true, true))) return st;
     if ((st = chol_inv(c, nx, S, G))) return st;
   }
   ProfTag t(c, "orth");
@@ -490,6 +490,12 @@ static int current_density(Ctx* c, double* rho) {
 }  // namespace paro
 
 using namespace paro;
+
+// y += a x on the grid
+__global__ void k_axpy_grid(int n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] += a * x[i];
+}
 
 // ================================================================================================
 // C ABI
@@ -683,6 +689,40 @@ int paro_set_kb(paro_ctx* ctx, double rc, const double* D) {
   return PARO_OK;
 }
 
+int paro_set_positions(paro_ctx* ctx, const double* pos) {
+  CTX_CHECK(ctx);
+  if (c->nat > 0 && !pos) return fail(c, PARO_ERR_ARG, "paro_set_positions: null positions");
+  int st;
+  double* v = nullptr;
+  if (c->have_veff) {  // keep V_eff - V_loc
+    v = static_cast<double*>(ws_get(c, "grid_r1", (size_t)c->ngrid * sizeof(double)));
+    if (!v) return PARO_ERR_CUDA;
+    PARO_CU(c, cudaMemcpyAsync(v, c->d_veff, (size_t)c->ngrid * sizeof(double), cudaMemcpyDeviceToDevice,
+                               c->stream));
+    if (c->have_pp) {
+      k_axpy_grid<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, -1.0, c->d_vloc, v);
+      PARO_LAUNCH(c, "k_axpy_grid");
+    }
+  }
+  c->pos.assign(pos, pos + 3 * c->nat);
+  if (c->have_pp) {
+    if ((st = build_vloc(c))) return st;
+    c->e_ewald = ewald(c);
+  }
+  if (c->have_kb && (st = build_beta(c))) return st;
+  if (v) {
+    if (c->have_pp) {
+      k_axpy_grid<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, 1.0, c->d_vloc, v);
+      PARO_LAUNCH(c, "k_axpy_grid");
+    }
+    if ((st = set_veff_device(c, v))) return st;
+  }
+  update_sigma(c);
+  for (int ik = 0; ik < c->nk; ++ik)
+    if (c->bases[ik].have_psi && (st = reproject(c, ik))) return st;
+  return PARO_OK;
+}
+
 int paro_set_veff(paro_ctx* ctx, const double* v_r, int on_device) {
   CTX_CHECK(ctx);
   if (!v_r) return fail(c, PARO_ERR_ARG, "null potential");
@@ -701,6 +741,15 @@ int paro_get_veff(paro_ctx* ctx, double* v_r) {
   if (!v_r) return PARO_ERR_ARG;
   if (!c->have_veff) return fail(c, PARO_ERR_STATE, "no potential");
   PARO_CU(c, cudaMemcpyAsync(v_r, c->d_veff, (size_t)c->ngrid * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PARO_CU(c, cudaStreamSynchronize(c->stream));
+  return PARO_OK;
+}
+
+int paro_get_vloc(paro_ctx* ctx, double* v_r) {
+  CTX_CHECK(ctx);
+  if (!v_r) return PARO_ERR_ARG;
+  if (!c->have_pp) return fail(c, PARO_ERR_STATE, "no local pseudopotential");
+  PARO_CU(c, cudaMemcpyAsync(v_r, c->d_vloc, (size_t)c->ngrid * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   PARO_CU(c, cudaStreamSynchronize(c->stream));
   return PARO_OK;
 }
@@ -727,6 +776,17 @@ int paro_apply_h(paro_ctx* ctx, int ik, int nb, int dtype, const void* psi, void
   return dtype == PARO_C64
              ? apply_h<double>(c, ik, nb, static_cast<const double2*>(psi), static_cast<double2*>(hpsi), 0.0, nullptr)
              : apply_h<float>(c, ik, nb, static_cast<const float2*>(psi), static_cast<float2*>(hpsi), 0.0, nullptr);
+}
+
+int paro_apply_h_adjoint(paro_ctx* ctx, int ik, int nb, int dtype, const void* psi, const void* w, void* g_psi,
+                         double* g_v, double* g_pos) {
+  CTX_CHECK(ctx);
+  if (ik < 0 || ik >= c->nk || nb < 1 || !psi || !w || (dtype != PARO_C64 && dtype != PARO_C32) ||
+      g_psi == psi || g_psi == w)
+    return fail(c, PARO_ERR_ARG, "paro_apply_h_adjoint: bad argument");
+  if (!c->have_veff) return fail(c, PARO_ERR_STATE, "no effective potential set");
+  if (dtype == PARO_C64 && check_fft_support(c, 16)) return PARO_ERR_ARG;
+  return apply_h_adjoint(c, ik, nb, dtype, psi, w, g_psi, g_v, g_pos);
 }
 
 int paro_solve_source(paro_ctx* ctx, int ik, int nb, int dtype, const double* eps, const void* psi, void* x,

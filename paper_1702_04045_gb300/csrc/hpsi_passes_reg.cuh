@@ -324,13 +324,13 @@ __global__ void __launch_bounds__(256) k_plane_density_reg(const cplx<T>* __rest
 }
 
 template <typename T, int N>
-static int density_planes_reg_n(Ctx* c, const Basis& B, const cplx<T>* S, int ngrp, int gsize, double wfac,
-                                double* part) {
+static int density_planes_reg_n(Ctx* c, const Basis& B, const cplx<T>* S, int nbands, int ngrp, int gsize,
+                                double wfac, double* part) {
   static int done[64];
   int st;
   if ((st = set_smem_once(c, k_plane_density_reg<T, N, N>, done))) return st;
   const size_t smem = (size_t)sizeof(cplx<T>) * (2 * N + N * (N + 1)) + (size_t)N * N * sizeof(double);
-  k_plane_density_reg<T, N, N><<<dim3(N, ngrp), 256, smem, c->stream>>>(S, B.ncol, c->nocc, gsize, B.d_col_x,
+  k_plane_density_reg<T, N, N><<<dim3(N, ngrp), 256, smem, c->stream>>>(S, B.ncol, nbands, gsize, B.d_col_x,
                                                                        B.d_col_y, B.d_xrows, B.nxr, tw_of<T>(c, 0),
                                                                        tw_of<T>(c, 1), wfac, part);
   PARO_LAUNCH(c, "k_plane_density_reg");
@@ -338,7 +338,8 @@ static int density_planes_reg_n(Ctx* c, const Basis& B, const cplx<T>* S, int ng
 }
 
 template <typename T>
-int density_planes_reg(Ctx* c, int ik, const cplx<T>* S, int ngrp, int gsize, double wfac, double* part, bool* used) {
+int density_planes_reg(Ctx* c, int ik, const cplx<T>* S, int nbands, int ngrp, int gsize, double wfac, double* part,
+                       bool* used) {
   *used = false;
   const int n = c->N[0];
   if (c->N[1] != n || c->N[2] != n) return PARO_OK;
@@ -346,11 +347,11 @@ int density_planes_reg(Ctx* c, int ik, const cplx<T>* S, int ngrp, int gsize, do
   const Basis& B = c->bases[ik];
   *used = true;
   switch (n) {
-    case 32: return density_planes_reg_n<T, 32>(c, B, S, ngrp, gsize, wfac, part);
-    case 36: return density_planes_reg_n<T, 36>(c, B, S, ngrp, gsize, wfac, part);
-    case 48: return density_planes_reg_n<T, 48>(c, B, S, ngrp, gsize, wfac, part);
-    case 72: return density_planes_reg_n<T, 72>(c, B, S, ngrp, gsize, wfac, part);
-    case 128: return density_planes_reg_n<T, 128>(c, B, S, ngrp, gsize, wfac, part);
+    case 32: return density_planes_reg_n<T, 32>(c, B, S, nbands, ngrp, gsize, wfac, part);
+    case 36: return density_planes_reg_n<T, 36>(c, B, S, nbands, ngrp, gsize, wfac, part);
+    case 48: return density_planes_reg_n<T, 48>(c, B, S, nbands, ngrp, gsize, wfac, part);
+    case 72: return density_planes_reg_n<T, 72>(c, B, S, nbands, ngrp, gsize, wfac, part);
+    case 128: return density_planes_reg_n<T, 128>(c, B, S, nbands, ngrp, gsize, wfac, part);
     default: *used = false; return PARO_OK;
   }
 }

@@ -210,6 +210,90 @@ int build_vloc(Ctx* c) {
 }
 
 // ------------------------------------------------------------------------------------------------
+// dL/dR_I through V_loc (adjoint of H psi): with V_loc(r) = sum_G V_loc(G) exp(i G.r) and
+// dV_loc(G)/dR_Ia = -i G_a Omega^{-1} exp(-i G.R_I) v(G),
+//   dL/dR_Ia = Re sum_G (-i G_a) Omega^{-1} v(G) exp(-i G.R_I) conj(g^(G)),  g^ = forward DFT of dL/dV(r).
+// k_vloc_weight: wg(G) = Omega^{-1} v(G) conj(g^(G)) on the V_loc support, 0 elsewhere (in place).
+// k_vloc_force: one CTA per (atom, grid chunk), partial sums per chunk; k_vloc_force_reduce sums the
+// chunks in a fixed order.
+// ------------------------------------------------------------------------------------------------
+__global__ void k_to_complex(int n, const double* __restrict__ r, double2* __restrict__ z);
+
+__global__ void k_vloc_weight(int N1, int N2, int N3, Mat3 B, double ecut4, double Z, double rc, double A, double a,
+                              double omega, double2* __restrict__ g) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N1 * N2 * N3) return;
+  const int j3 = idx % N3, j2 = (idx / N3) % N2, j1 = idx / (N2 * N3);
+  const int n1 = signed_index(j1, N1), n2 = signed_index(j2, N2), n3 = signed_index(j3, N3);
+  const double gx = n1 * B.m[0] + n2 * B.m[3] + n3 * B.m[6];
+  const double gy = n1 * B.m[1] + n2 * B.m[4] + n3 * B.m[7];
+  const double gz = n1 * B.m[2] + n2 * B.m[5] + n3 * B.m[8];
+  const double g2 = gx * gx + gy * gy + gz * gz;
+  double2 out = make_double2(0.0, 0.0);
+  if (0.5 * g2 <= ecut4 && 2 * abs(n1) < N1 && 2 * abs(n2) < N2 && 2 * abs(n3) < N3) {
+    double form = A * pow(kPi, 1.5) * a * a * a * exp(-g2 * a * a / 4.0);
+    form += g2 > 0.0 ? -4.0 * kPi * Z * exp(-g2 * rc * rc / 4.0) / g2 : kPi * Z * rc * rc;
+    out = cscale(cconj(g[idx]), form / omega);
+  }
+  g[idx] = out;
+}
+
+__global__ void __launch_bounds__(256) k_vloc_force(int N1, int N2, int N3, Mat3 B, int chunk,
+                                                    const double2* __restrict__ ph, const double2* __restrict__ wg,
+                                                    double* __restrict__ part) {
+  __shared__ double red[32];
+  const int I = blockIdx.y, tot = N1 + N2 + N3, ng = N1 * N2 * N3;
+  const double2* p = ph + (size_t)I * tot;
+  const int i0 = blockIdx.x * chunk, i1 = min(ng, i0 + chunk);
+  double f[3] = {0.0, 0.0, 0.0};
+  for (int idx = i0 + threadIdx.x; idx < i1; idx += blockDim.x) {
+    const double2 w = wg[idx];
+    if (w.x == 0.0 && w.y == 0.0) continue;
+    const int j3 = idx % N3, j2 = (idx / N3) % N2, j1 = idx / (N2 * N3);
+    const int n1 = signed_index(j1, N1), n2 = signed_index(j2, N2), n3 = signed_index(j3, N3);
+    const double2 sw = cmul(cmul(cmul(p[j1], p[N1 + j2]), p[N1 + N2 + j3]), w);  // exp(-i G.R_I) wg
+    // Re[(-i G_a) sw] = G_a Im(sw)
+    for (int al = 0; al < 3; ++al) f[al] += (n1 * B.m[al] + n2 * B.m[3 + al] + n3 * B.m[6 + al]) * sw.y;
+  }
+  for (int al = 0; al < 3; ++al) {
+    const double v = block_sum(f[al], red);
+    if (threadIdx.x == 0) part[((size_t)I * gridDim.x + blockIdx.x) * 3 + al] = v;
+  }
+}
+
+__global__ void k_vloc_force_reduce(int nat, int nchunk, const double* __restrict__ part, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nat * 3) return;
+  const int I = i / 3, al = i - 3 * I;
+  double s = 0.0;
+  for (int ch = 0; ch < nchunk; ++ch) s += part[((size_t)I * nchunk + ch) * 3 + al];
+  out[i] = s;
+}
+
+int vloc_position_grad(Ctx* c, const double* gv, double* gpos) {
+  if (c->nat == 0) return PARO_OK;
+  double2* ph = phase_tables(c);
+  double2* g = static_cast<double2*>(ws_get(c, "grid_c1", (size_t)c->ngrid * sizeof(double2)));
+  const int chunk = 4096, nchunk = (c->ngrid + chunk - 1) / chunk;
+  double* part = static_cast<double*>(ws_get(c, "vforce_part", (size_t)c->nat * nchunk * 3 * sizeof(double)));
+  if (!ph || !g || !part) return PARO_ERR_CUDA;
+  k_to_complex<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, gv, g);
+  PARO_LAUNCH(c, "k_to_complex");
+  int st = fft3d(c, g, false);
+  if (st) return st;
+  Mat3 B;
+  for (int i = 0; i < 9; ++i) B.m[i] = c->bmat[i];
+  k_vloc_weight<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->N[0], c->N[1], c->N[2], B, 4.0 * c->ecut, c->Z,
+                                                               c->rc, c->A, c->a, c->omega, g);
+  PARO_LAUNCH(c, "k_vloc_weight");
+  k_vloc_force<<<dim3(nchunk, c->nat), 256, 0, c->stream>>>(c->N[0], c->N[1], c->N[2], B, chunk, ph, g, part);
+  PARO_LAUNCH(c, "k_vloc_force");
+  k_vloc_force_reduce<<<(c->nat * 3 + 127) / 128, 128, 0, c->stream>>>(c->nat, nchunk, part, gpos);
+  PARO_LAUNCH(c, "k_vloc_force_reduce");
+  return PARO_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
 // Kleinman-Bylander projector table beta[4 I + j][g], j = s, px, py, pz
 // ------------------------------------------------------------------------------------------------
 __global__ void k_beta(int npw, int nat, int N1, int N2, int N3, Mat3 B, double kx, double ky, double kz,
@@ -514,41 +598,52 @@ template <typename T> static const cplx<T>* twid(const Ctx* c, int ax);
 template <> const double2* twid<double>(const Ctx* c, int ax) { return c->d_tw64[ax]; }
 template <> const float2* twid<float>(const Ctx* c, int ax) { return c->d_tw32[ax]; }
 
-// rho(r) from orbitals in precision T (the FFTs in T, |psi(r)|^2 summed in FP64)
+// rho(r) (+)= wfac sum_b |psi~_b(r)|^2 for nbands orbitals of k-point ik (the FFTs in T, sums in FP64)
 template <typename T>
-int density(Ctx* c, const cplx<T>* const* psis, double* rho_dev) {
+int density_bands(Ctx* c, int ik, int nbands, const cplx<T>* psi, double wfac, double* rho_dev, bool accumulate) {
   const int N1 = c->N[0], N2 = c->N[1], N3 = c->N[2];
   const int gsize = 8;
-  const int ngrp = (c->nocc + gsize - 1) / gsize;
+  const int ngrp = (nbands + gsize - 1) / gsize;
+  if (nbands < 1) return fail(c, PARO_ERR_ARG, "density: no bands");
   double* part = static_cast<double*>(ws_get(c, "dens_part", (size_t)ngrp * c->ngrid * sizeof(double)));
   if (!part) return PARO_ERR_CUDA;
   const size_t smem = (size_t)N1 * N2 * sizeof(double) + (size_t)(N1 + N2 + N1 * N2) * sizeof(cplx<T>);
   if (smem > 227 * 1024) return fail(c, PARO_ERR_ARG, "density: plane too large for shared memory");
   PARO_CU(c, cudaFuncSetAttribute(k_plane_density<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
   const int threads = 512;
+  const Basis& B = c->bases[ik];
+  cplx<T>* S = static_cast<cplx<T>*>(
+      ws_get(c, sizeof(T) == 8 ? "sticks64" : "sticks32", (size_t)nbands * N3 * B.ncol * sizeof(cplx<T>)));
+  if (!S) return PARO_ERR_CUDA;
+  int st = sticks_inverse<T>(c, ik, nbands, psi, S);
+  if (st) return st;
+  cudaEvent_t ev = prof_begin(c);
+  bool used = false;
+  if ((st = density_planes_reg<T>(c, ik, S, nbands, ngrp, gsize, wfac, part, &used))) return st;
+  if (!used) {
+    k_plane_density<T><<<dim3(N3, ngrp), threads, smem, c->stream>>>(
+        S, B.ncol, nbands, gsize, B.d_col_x, B.d_col_y, B.d_xrows, B.nxr, c->plan[0], c->plan[1], twid<T>(c, 0),
+        twid<T>(c, 1), wfac, part);
+    PARO_LAUNCH(c, "k_plane_density");
+  }
+  prof_end(c, sizeof(T) == 8 ? "k_plane_density<f64>" : "k_plane_density<f32>", ev);
+  k_density_reduce<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(N1, N2, N3, ngrp, part, rho_dev, accumulate);
+  PARO_LAUNCH(c, "k_density_reduce");
+  return PARO_OK;
+}
+
+// rho(r) = sum_k w_k 2 sum_{occupied b} |psi_kb(r)|^2 / Omega from orbitals in precision T
+template <typename T>
+int density(Ctx* c, const cplx<T>* const* psis, double* rho_dev) {
   for (int ik = 0; ik < c->nk; ++ik) {
-    const Basis& B = c->bases[ik];
-    cplx<T>* S = static_cast<cplx<T>*>(
-        ws_get(c, sizeof(T) == 8 ? "sticks64" : "sticks32", (size_t)c->nocc * N3 * B.ncol * sizeof(cplx<T>)));
-    if (!S) return PARO_ERR_CUDA;
-    int st = sticks_inverse<T>(c, ik, c->nocc, psis[ik], S);
+    const int st = density_bands<T>(c, ik, c->nocc, psis[ik], 2.0 * c->kw[ik] / c->omega, rho_dev, ik > 0);
     if (st) return st;
-    cudaEvent_t ev = prof_begin(c);
-    bool used = false;
-    if ((st = density_planes_reg<T>(c, ik, S, ngrp, gsize, 2.0 * c->kw[ik] / c->omega, part, &used))) return st;
-    if (!used) {
-      k_plane_density<T><<<dim3(N3, ngrp), threads, smem, c->stream>>>(
-          S, B.ncol, c->nocc, gsize, B.d_col_x, B.d_col_y, B.d_xrows, B.nxr, c->plan[0], c->plan[1], twid<T>(c, 0),
-          twid<T>(c, 1), 2.0 * c->kw[ik] / c->omega, part);
-      PARO_LAUNCH(c, "k_plane_density");
-    }
-    prof_end(c, sizeof(T) == 8 ? "k_plane_density<f64>" : "k_plane_density<f32>", ev);
-    k_density_reduce<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(N1, N2, N3, ngrp, part, rho_dev, ik > 0);
-    PARO_LAUNCH(c, "k_density_reduce");
   }
   return PARO_OK;
 }
 
+template int density_bands<double>(Ctx*, int, int, const double2*, double, double*, bool);
+template int density_bands<float>(Ctx*, int, int, const float2*, double, double*, bool);
 template int density<double>(Ctx*, const double2* const*, double*);
 template int density<float>(Ctx*, const float2* const*, double*);
 

@@ -24,8 +24,9 @@ ENERGY_TERMS = ("kinetic", "nonlocal", "local", "hartree", "xc", "ewald", "total
 
 # Every symbol include/paro.h declares.
 EXPORTS = (
-    "paro_create", "paro_set_local_pp", "paro_set_kb", "paro_set_veff", "paro_get_veff", "paro_set_density",
-    "paro_grid", "paro_npw", "paro_miller", "paro_sigma", "paro_apply_h", "paro_apply_h_noalloc", "paro_solve_source",
+    "paro_create", "paro_set_local_pp", "paro_set_kb", "paro_set_positions", "paro_set_veff", "paro_get_veff",
+    "paro_get_vloc", "paro_set_density", "paro_grid", "paro_npw", "paro_miller", "paro_sigma", "paro_apply_h",
+    "paro_apply_h_noalloc", "paro_apply_h_adjoint", "paro_solve_source",
     "paro_set_orbitals", "paro_get_orbitals", "paro_get_eigenvalues", "paro_get_residuals", "paro_step",
     "paro_eigh", "paro_density", "paro_energy", "paro_scf_step", "paro_scf", "paro_set_state", "paro_profile",
     "paro_profile_read", "paro_profile_names", "paro_launch_count", "paro_last_error", "paro_destroy",
@@ -62,6 +63,10 @@ _SIGS = {
     "paro_sigma": (ctypes.c_int, [_vp, _c_dbl_p]),
     "paro_apply_h": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "paro_apply_h_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),
+    "paro_apply_h_adjoint": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp,
+                                            _vp]),
+    "paro_set_positions": (ctypes.c_int, [_vp, _c_dbl_p]),
+    "paro_get_vloc": (ctypes.c_int, [_vp, _c_dbl_p]),
     "paro_solve_source": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_dbl_p, _vp, _vp,
                                          ctypes.c_double, ctypes.c_int, _c_int_p]),
     "paro_set_orbitals": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int]),
@@ -233,6 +238,36 @@ class Context:
                                                   _vp(out.data_ptr())))
         return out
 
+    def apply_h_adjoint(self, psi, w, ik=0, grads=("psi", "v", "pos")):
+        """Vector-Jacobian product of Y = H Psi for cotangent W: (dL/dPsi, dL/dV_eff(r), dL/dR) as device
+        tensors (None where not asked for); dL/dV has the grid's shape, dL/dR is (n_atoms, 3)."""
+        torch = self.torch
+        dt = PARO_C64 if psi.dtype == torch.complex128 else PARO_C32
+        psi = psi.contiguous()
+        w = w.to(psi.dtype).contiguous()
+        dev = psi.device
+        g_psi = torch.empty_like(psi) if "psi" in grads else None
+        g_v = torch.empty(self.grid, dtype=torch.float64, device=dev) if "v" in grads else None
+        g_pos = torch.empty((self.n_atoms, 3), dtype=torch.float64, device=dev) if "pos" in grads else None
+
+        def p(t):
+            return _vp(t.data_ptr()) if t is not None else None
+
+        self._check(self.lib.paro_apply_h_adjoint(self.h, ik, psi.shape[0], dt, p(psi), p(w), p(g_psi), p(g_v),
+                                                  p(g_pos)))
+        return g_psi, g_v, g_pos
+
+    def set_positions(self, pos):
+        pos = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1))
+        if pos.size != 3 * self.n_atoms:
+            raise ValueError("positions must be n_atoms x 3")
+        self._check(self.lib.paro_set_positions(self.h, _dptr(pos)))
+
+    def get_vloc(self):
+        v = np.empty(self.grid, dtype=np.float64)
+        self._check(self.lib.paro_get_vloc(self.h, _dptr(v)))
+        return v
+
     def solve_source(self, eps, psi, rel_tol, max_it, ik=0):
         torch = self.torch
         dt = PARO_C64 if psi.dtype == torch.complex128 else PARO_C32
@@ -343,6 +378,37 @@ class Context:
             err.result = out
             raise err
         return out
+
+
+_HPSI_FN = None
+
+
+def hpsi(ctx: Context, psi, v_rest, pos, ik=0):
+    """Differentiable Y = H Psi with H built from V_eff = V_loc(pos) + v_rest and the KB projectors at
+    pos (torch.autograd): the backward pass is the library's adjoint (dL/dPsi, dL/dv_rest, dL/dpos).
+    psi: device complex (nb, npw); v_rest: float64 tensor of the grid's shape; pos: float64 (n_atoms, 3)."""
+    global _HPSI_FN
+    torch = ctx.torch
+    if _HPSI_FN is None:
+        class _HPsi(torch.autograd.Function):
+            @staticmethod
+            def forward(fctx, psi_, v_rest_, pos_, c, k):
+                c.set_positions(pos_.detach().cpu().numpy())
+                v = torch.from_numpy(c.get_vloc()).to(v_rest_.device) + v_rest_.detach().to(torch.float64)
+                c.set_veff(v.contiguous())
+                y = c.apply_h(psi_.detach(), ik=k)
+                fctx.save_for_backward(psi_.detach())
+                fctx.c, fctx.k = c, k
+                return y
+
+            @staticmethod
+            def backward(fctx, gy):
+                (psi_,) = fctx.saved_tensors
+                g_psi, g_v, g_pos = fctx.c.apply_h_adjoint(psi_, gy, ik=fctx.k)
+                return g_psi, g_v, g_pos, None, None
+
+        _HPSI_FN = _HPsi
+    return _HPSI_FN.apply(psi, v_rest, pos, ctx, ik)
 
 
 def context_from_config(name: str, precision: str = "fp64", **kw) -> Context:
