@@ -280,6 +280,37 @@ def run_ours(args, rank, world, local, pg):
     return out
 
 
+def run_adjoint(nb=1088, calls=2):
+    """Adjoint of H psi on the 512-atom cell (137059 plane waves, 128^3 grid, 2048 KB projectors), FP32
+    inputs: ms per call over all three outputs (dL/dpsi, dL/dV, dL/dR) with CUDA events."""
+    import torch
+    from paper_1702_04045_gb300 import paro
+    ctx = paro.context_from_config("si512", "mixed")
+    npw = ctx.npw()
+    g = torch.Generator(device="cuda").manual_seed(5124)
+    psi = torch.randn((nb, npw), dtype=torch.complex64, device="cuda", generator=g)
+    w = torch.randn((nb, npw), dtype=torch.complex64, device="cuda", generator=g)
+    ctx.apply_h_adjoint(psi, w)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(calls):
+        ctx.apply_h_adjoint(psi, w)
+    e1.record()
+    torch.cuda.synchronize()
+    prof = {n: ctx.profile_read(n) for n in ctx.profile_names()}
+    ctx.profile(False)
+    ms = e0.elapsed_time(e1) / calls
+    top = sorted(prof.items(), key=lambda kv: -kv[1][1])[:6]
+    out = {"workload": "512-atom diamond cell a=41.04 Bohr, Ecut 12 Ha (137059 PW, 128^3 grid), 2048 KB "
+                       "projectors, FP32 inputs", "bands": nb, "ms_per_call": ms,
+           "outputs": "dL/dpsi, dL/dV_eff(r), dL/dR (512 atoms)",
+           "kernel_ms_per_call": {k: round(v[1] / calls, 3) for k, v in top}}
+    ctx.close()
+    return out
+
+
 def cpu_sample(args, steps=1, warmup=0):
     """The FP64 CPU oracle on this host: seconds per ParO-SCF iteration of the same cell."""
     from oracle import scf
@@ -326,6 +357,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -336,6 +368,8 @@ def main():
             print(json.dumps(out))
         return
     out = run_ours(args, rank, world, local, pg)
+    if rank == 0 and world == 1 and not args.no_adjoint:
+        out["adjoint_512"] = run_adjoint()
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             times, cores = cpu_sample(args)

@@ -252,7 +252,10 @@ static int passes_reg_dispatch(Ctx* c, const Basis& B, int nb, const cplx<T>* ps
 
 // Density planes with the register FFT: per (z-plane, band group) the inverse transforms along y and
 // x of each band, |psi(r)|^2 summed in FP64 in shared memory, the group's plane written to part.
-template <typename T, int N1, int N2>
+// TACC: accumulator of the |psi|^2 sum over the group's bands (at most gsize = 8). double where the
+// plane's N1 x N2 FP64 accumulator fits next to the plane in shared memory; float otherwise (FP32
+// orbitals on large planes: an 8-term FP32 sum, the groups then summed in FP64 by the caller).
+template <typename T, int N1, int N2, typename TACC>
 __global__ void __launch_bounds__(256) k_plane_density_reg(const cplx<T>* __restrict__ S, int ncol, int nbands,
                                                            int gsize, const int* __restrict__ col_x,
                                                            const int* __restrict__ col_y,
@@ -267,11 +270,11 @@ __global__ void __launch_bounds__(256) k_plane_density_reg(const cplx<T>* __rest
   cplx<T>* tx = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* ty = tx + N1;
   cplx<T>* Pl = ty + N2;
-  double* acc = reinterpret_cast<double*>(Pl + N1 * LS);
+  TACC* acc = reinterpret_cast<TACC*>(Pl + N1 * LS);
   const int z = blockIdx.x, grp_b = blockIdx.y, N3 = gridDim.x;
   for (int i = threadIdx.x; i < N1; i += blockDim.x) tx[i] = twx[i];
   for (int i = threadIdx.x; i < N2; i += blockDim.x) ty[i] = twy[i];
-  for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) acc[i] = 0.0;
+  for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) acc[i] = (TACC)0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int b0 = grp_b * gsize, b1 = min(nbands, b0 + gsize);
   for (int b = b0; b < b1; ++b) {
@@ -312,7 +315,7 @@ __global__ void __launch_bounds__(256) k_plane_density_reg(const cplx<T>* __rest
         if (ok)
 #pragma unroll
           for (int k = 0; k < Q; ++k) {
-            const double re = v[k].x, im = v[k].y;
+            const TACC re = v[k].x, im = v[k].y;
             acc[(k + Q * pr) * N2 + y] += re * re + im * im;
           }
       }
@@ -320,21 +323,34 @@ __global__ void __launch_bounds__(256) k_plane_density_reg(const cplx<T>* __rest
     __syncthreads();
   }
   double* out = part + ((size_t)grp_b * N3 + z) * N1 * N2;
-  for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) out[i] = acc[i] * wfac;
+  for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) out[i] = (double)acc[i] * wfac;
+}
+
+template <typename T, int N, typename TACC>
+static size_t density_reg_smem() {
+  return (size_t)sizeof(cplx<T>) * (2 * N + N * (N + 1)) + (size_t)N * N * sizeof(TACC);
+}
+
+template <typename T, int N, typename TACC>
+static int density_planes_reg_acc(Ctx* c, const Basis& B, const cplx<T>* S, int nbands, int ngrp, int gsize,
+                                  double wfac, double* part) {
+  static int done[64];
+  int st;
+  if ((st = set_smem_once(c, k_plane_density_reg<T, N, N, TACC>, done))) return st;
+  const size_t smem = density_reg_smem<T, N, TACC>();
+  k_plane_density_reg<T, N, N, TACC><<<dim3(N, ngrp), 256, smem, c->stream>>>(
+      S, B.ncol, nbands, gsize, B.d_col_x, B.d_col_y, B.d_xrows, B.nxr, tw_of<T>(c, 0), tw_of<T>(c, 1), wfac, part);
+  PARO_LAUNCH(c, "k_plane_density_reg");
+  return PARO_OK;
 }
 
 template <typename T, int N>
 static int density_planes_reg_n(Ctx* c, const Basis& B, const cplx<T>* S, int nbands, int ngrp, int gsize,
                                 double wfac, double* part) {
-  static int done[64];
-  int st;
-  if ((st = set_smem_once(c, k_plane_density_reg<T, N, N>, done))) return st;
-  const size_t smem = (size_t)sizeof(cplx<T>) * (2 * N + N * (N + 1)) + (size_t)N * N * sizeof(double);
-  k_plane_density_reg<T, N, N><<<dim3(N, ngrp), 256, smem, c->stream>>>(S, B.ncol, nbands, gsize, B.d_col_x,
-                                                                       B.d_col_y, B.d_xrows, B.nxr, tw_of<T>(c, 0),
-                                                                       tw_of<T>(c, 1), wfac, part);
-  PARO_LAUNCH(c, "k_plane_density_reg");
-  return PARO_OK;
+  if (density_reg_smem<T, N, double>() <= 227 * 1024)
+    return density_planes_reg_acc<T, N, double>(c, B, S, nbands, ngrp, gsize, wfac, part);
+  if constexpr (sizeof(T) == 4) return density_planes_reg_acc<T, N, float>(c, B, S, nbands, ngrp, gsize, wfac, part);
+  return fail(c, PARO_ERR_ARG, "density: plane too large for shared memory");
 }
 
 template <typename T>
@@ -343,7 +359,8 @@ int density_planes_reg(Ctx* c, int ik, const cplx<T>* S, int nbands, int ngrp, i
   *used = false;
   const int n = c->N[0];
   if (c->N[1] != n || c->N[2] != n) return PARO_OK;
-  if ((size_t)sizeof(cplx<T>) * (2 * n + n * (n + 1)) + (size_t)n * n * sizeof(double) > 227 * 1024) return PARO_OK;
+  const size_t acc_bytes = (sizeof(T) == 4 && gsize <= 8) ? sizeof(float) : sizeof(double);
+  if ((size_t)sizeof(cplx<T>) * (2 * n + n * (n + 1)) + (size_t)n * n * acc_bytes > 227 * 1024) return PARO_OK;
   const Basis& B = c->bases[ik];
   *used = true;
   switch (n) {

@@ -608,8 +608,6 @@ int density_bands(Ctx* c, int ik, int nbands, const cplx<T>* psi, double wfac, d
   double* part = static_cast<double*>(ws_get(c, "dens_part", (size_t)ngrp * c->ngrid * sizeof(double)));
   if (!part) return PARO_ERR_CUDA;
   const size_t smem = (size_t)N1 * N2 * sizeof(double) + (size_t)(N1 + N2 + N1 * N2) * sizeof(cplx<T>);
-  if (smem > 227 * 1024) return fail(c, PARO_ERR_ARG, "density: plane too large for shared memory");
-  PARO_CU(c, cudaFuncSetAttribute(k_plane_density<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
   const int threads = 512;
   const Basis& B = c->bases[ik];
   cplx<T>* S = static_cast<cplx<T>*>(
@@ -621,6 +619,8 @@ int density_bands(Ctx* c, int ik, int nbands, const cplx<T>* psi, double wfac, d
   bool used = false;
   if ((st = density_planes_reg<T>(c, ik, S, nbands, ngrp, gsize, wfac, part, &used))) return st;
   if (!used) {
+    if (smem > 227 * 1024) return fail(c, PARO_ERR_ARG, "density: plane too large for shared memory");
+    PARO_CU(c, cudaFuncSetAttribute(k_plane_density<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     k_plane_density<T><<<dim3(N3, ngrp), threads, smem, c->stream>>>(
         S, B.ncol, nbands, gsize, B.d_col_x, B.d_col_y, B.d_xrows, B.nxr, c->plan[0], c->plan[1], twid<T>(c, 0),
         twid<T>(c, 1), wfac, part);

@@ -166,7 +166,7 @@ __device__ __forceinline__ void fft_stage_all(cplx<T>* s, int n, int Ns, int nli
 // Full FFT of `nlines` lines (all stages of plan p). tw: twiddles exp(-2 pi i j / n), j < n.
 // Requires n/R <= MaxUnits<R> * blockDim.x for every radix R of the plan.
 template <typename T, bool INV, bool LFAST, class LB>
-__device__ void fft_lines(cplx<T>* s, const FftPlan& p, int nlines, int es, LB lb, const cplx<T>* tw) {
+__device__ __forceinline__ void fft_lines(cplx<T>* s, const FftPlan& p, int nlines, int es, LB lb, const cplx<T>* tw) {
   int Ns = 1;
   for (int st = 0; st < p.nst; ++st) {
     const int R = p.rad[st];

@@ -91,3 +91,34 @@ def config_inputs(name: str):
     lat, pos = diamond_cell(c["n_rep"], c["a"], c["seed_pos"])
     d = kb_strengths(len(pos), c["seed_kb"]) if c["kb"] else None
     return lat, pos, d, c
+
+
+# Batched workloads of uneven problems: the 8-atom cell on a 3x3x3 Monkhorst-Pack mesh (27 k-points,
+# plane-wave counts differing per k) and 64 independent 8-atom cells with seeded lattice constants and
+# cutoffs (uneven plane-wave counts and FFT grids). 20 orbitals (16 occupied) per problem, local
+# pseudopotential as in the 8-atom fixed-potential workload.
+BATCHES = {
+    "si8_mp27": dict(kind="kmesh", a=10.26, ecut=10.0, q=3, n_bands=20, n_occ=16, seed_pos=1001, seed_psi=4002),
+    "cells64": dict(kind="cells", n_cells=64, seed_cells=4101, seed_pos=4102, seed_psi=4103, n_bands=20,
+                    n_occ=16),
+}
+
+
+def batch_inputs(name: str, limit: int | None = None):
+    """Problems of a batched workload: one dict per cell with lattice, positions, cutoff, k-points
+    (reduced), k-weights, bands, occupied bands and the start-vector seed of each k-point."""
+    c = BATCHES[name]
+    out = []
+    if c["kind"] == "kmesh":
+        lat, pos = diamond_cell(1, c["a"], c["seed_pos"])
+        k, w = monkhorst_pack(c["q"])
+        out.append(dict(lat=lat, pos=pos, ecut=c["ecut"], kpts=k, kweights=w, n_bands=c["n_bands"],
+                        n_occ=c["n_occ"], seeds=[c["seed_psi"] + i for i in range(len(k))]))
+    else:
+        a, ecut = random_cells(c["n_cells"], c["seed_cells"])
+        for i in range(c["n_cells"]):
+            lat, pos = diamond_cell(1, float(a[i]), c["seed_pos"] + i)
+            out.append(dict(lat=lat, pos=pos, ecut=float(ecut[i]), kpts=np.zeros((1, 3)), kweights=np.ones(1),
+                            n_bands=c["n_bands"], n_occ=c["n_occ"], seeds=[c["seed_psi"] + i]))
+    return out[:limit] if limit else out
+

@@ -26,7 +26,8 @@ ENERGY_TERMS = ("kinetic", "nonlocal", "local", "hartree", "xc", "ewald", "total
 EXPORTS = (
     "paro_create", "paro_set_local_pp", "paro_set_kb", "paro_set_positions", "paro_set_veff", "paro_get_veff",
     "paro_get_vloc", "paro_set_density", "paro_grid", "paro_npw", "paro_miller", "paro_sigma", "paro_apply_h",
-    "paro_apply_h_noalloc", "paro_apply_h_adjoint", "paro_solve_source",
+    "paro_apply_h_noalloc", "paro_apply_h_adjoint", "paro_solve_source", "paro_batch_create", "paro_batch_apply_h",
+    "paro_batch_step", "paro_batch_info", "paro_batch_destroy",
     "paro_set_orbitals", "paro_get_orbitals", "paro_get_eigenvalues", "paro_get_residuals", "paro_step",
     "paro_eigh", "paro_density", "paro_energy", "paro_scf_step", "paro_scf", "paro_set_state", "paro_profile",
     "paro_profile_read", "paro_profile_names", "paro_launch_count", "paro_last_error", "paro_destroy",
@@ -66,6 +67,12 @@ _SIGS = {
     "paro_apply_h_adjoint": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp,
                                             _vp]),
     "paro_set_positions": (ctypes.c_int, [_vp, _c_dbl_p]),
+    "paro_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int]),
+    "paro_batch_apply_h": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
+    "paro_batch_step": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, _c_dbl_p]),
+    "paro_batch_info": (ctypes.c_int, [_vp, _c_int_p, _c_int_p, _c_int_p, _c_int_p,
+                                       ctypes.POINTER(ctypes.c_longlong)]),
+    "paro_batch_destroy": (None, [_vp]),
     "paro_get_vloc": (ctypes.c_int, [_vp, _c_dbl_p]),
     "paro_solve_source": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_dbl_p, _vp, _vp,
                                          ctypes.c_double, ctypes.c_int, _c_int_p]),
@@ -378,6 +385,60 @@ class Context:
             err.result = out
             raise err
         return out
+
+
+class Batch:
+    """Batched ParO over the k-points of several contexts (uneven plane-wave counts and grids): one
+    persistent H psi launch over all orbitals, one CUDA graph per ParO step."""
+
+    def __init__(self, ctxs):
+        self.ctxs = list(ctxs)
+        self.lib = self.ctxs[0].lib
+        arr = (_vp * len(self.ctxs))(*[c.h for c in self.ctxs])
+        h = _vp()
+        st = self.lib.paro_batch_create(ctypes.byref(h), arr, len(self.ctxs))
+        if st != 0:
+            raise ParoError(st, self.lib.paro_last_error(self.ctxs[0].h).decode())
+        self.h = h
+        self.problems = [(i, k) for i, c in enumerate(self.ctxs) for k in range(c.nk)]
+
+    def _check(self, st):
+        if st != 0:
+            raise ParoError(st, self.lib.paro_last_error(self.ctxs[0].h).decode())
+
+    def apply_h(self, psis):
+        """H psi of every problem; psis: one device tensor (n_bands, npw) per problem, context-major."""
+        torch = self.ctxs[0].torch
+        psis = [p.contiguous() for p in psis]
+        outs = [torch.empty_like(p) for p in psis]
+        dt = PARO_C64 if psis[0].dtype == torch.complex128 else PARO_C32
+        a = (_vp * len(psis))(*[_vp(p.data_ptr()) for p in psis])
+        o = (_vp * len(outs))(*[_vp(p.data_ptr()) for p in outs])
+        self._check(self.lib.paro_batch_apply_h(self.h, dt, a, o))
+        return outs
+
+    def step(self, rel_tol=0.25, max_it=8):
+        r = ctypes.c_double()
+        self._check(self.lib.paro_batch_step(self.h, float(rel_tol), int(max_it), ctypes.byref(r)))
+        return r.value
+
+    def info(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        k = ctypes.c_longlong()
+        self._check(self.lib.paro_batch_info(self.h, *[ctypes.byref(x) for x in v], ctypes.byref(k)))
+        return dict(problems=v[0].value, items=v[1].value, threads=v[2].value, grid=v[3].value,
+                    kernels_per_step=k.value)
+
+    def close(self):
+        if self.h:
+            self.lib.paro_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 _HPSI_FN = None

@@ -149,3 +149,63 @@ def test_adjoint_full_size_64_atoms(precision_dtype, tol):
         hq = ctx.apply_h(q[:, al][None, :] * tp)
         want = torch.real(torch.sum(torch.conj(tw) * (-1j * q[:, al][None, :] * hp + 1j * hq))).item()
         assert g_pos[:, al].sum() == pytest.approx(want, rel=max(tol, 1e-9), abs=tol * np.abs(g_pos).max())
+
+
+def test_hellmann_feynman_density_8_atoms():
+    # For orbitals of the 8-atom workload after ParO steps, W = 2 Psi_occ gives L = E_band and
+    # dE_band/dV(r) = rho(r) Omega / N: the adjoint's dL/dV against the library's density pass.
+    from paper_1702_04045_gb300 import paro
+    name = "si8_local"
+    lat, pos, _, c = inputs.config_inputs(name)
+    ctx = paro.context_from_config(name, "fp64")
+    ctx.set_orbitals(inputs.start_vectors(c["n_bands"], ctx.npw(), c["seed_psi"]))
+    for _ in range(30):
+        ctx.step(1, 0.25, 8)
+    psi = ctx.get_orbitals(device=True)[: c["n_occ"]].contiguous()
+    _, g_v, _ = ctx.apply_h_adjoint(psi, 2.0 * psi, grads=("v",))
+    omega = abs(np.linalg.det(lat))
+    n = int(np.prod(ctx.grid))
+    rho = ctx.density().cpu().numpy()
+    assert _rel(g_v.cpu().numpy() * n / omega, rho) < 1e-12
+
+
+def test_adjoint_512_atoms_forces_central_differences():
+    # 512-atom cell (137059 plane waves, 128^3 grid, 2048 KB projectors), FP32 adjoint: forces on 8 seeded
+    # atoms against central differences (h = 1e-4 Bohr) of the FP64 oracle's L. Only the moved atom's
+    # terms of L change: sum_r V_loc,I(r) dL/dV(r) with its single-atom local potential, and
+    # Re sum_b sum_{p in I} D_p conj(A_pb) P_pb with its four projectors.
+    from paper_1702_04045_gb300 import paro
+    name = "si512"
+    lat, pos, d, c = inputs.config_inputs(name)
+    ctx = paro.context_from_config(name, "mixed")
+    grid = ctx.grid
+    basis = pw.Basis(lat, c["ecut"], grid)
+    assert basis.npw == 137059 and grid == (128, 128, 128)
+    nb = 16
+    psi = inputs.start_vectors(nb, basis.npw, 5121)
+    w = inputs.start_vectors(nb, basis.npw, 5122)
+    _, g_v_gpu, g_pos = ctx.apply_h_adjoint(torch.from_numpy(psi.astype(np.complex64)).cuda(),
+                                            torch.from_numpy(w.astype(np.complex64)).cuda(), grads=("v", "pos"))
+    g_pos = g_pos.cpu().numpy()
+    g_v = adjoint.grad_v(basis, psi, w)
+    assert _rel(g_v_gpu.cpu().numpy(), g_v) < 2e-5
+    dvec = pw.kb_dvec(d)
+    rng = np.random.default_rng(5123)
+    atoms = rng.choice(len(pos), 8, replace=False)
+    axes = rng.integers(0, 3, 8)
+
+    def l_atom(i_at, r):
+        v_i = pw.vloc_real(lat, r[None], grid, c["ecut"], **inputs.LOCAL_PP)
+        beta = pw.kb_beta(lat, r[None], basis.q, inputs.KB_RC)
+        proj, aproj = np.conj(beta) @ psi.T, np.conj(beta) @ w.T
+        dv = dvec[4 * i_at:4 * i_at + 4]
+        return float(np.sum(v_i * g_v)) + float(np.real(np.sum(dv[:, None] * np.conj(aproj) * proj)))
+
+    h = 1e-4
+    scale = np.abs(g_pos).max()
+    for i_at, al in zip(atoms, axes):
+        rp, rm = pos[i_at].copy(), pos[i_at].copy()
+        rp[al] += h
+        rm[al] -= h
+        fd = (l_atom(i_at, rp) - l_atom(i_at, rm)) / (2 * h)
+        assert abs(fd - g_pos[i_at, al]) < 2e-5 * scale

@@ -108,3 +108,27 @@ def test_grad_pos_is_hellmann_feynman_force(case):
         pm[i_at, al] -= h
         fd = (lowest(pp)[0][0] - lowest(pm)[0][0]) / (2 * h)
         assert abs(fd - g_pos[i_at, al]) <= 1e-6 * max(1.0, np.abs(g_pos).max())
+
+
+def test_grad_v_is_hellmann_feynman_density(case):
+    # W = Psi = a normalised non-degenerate eigenvector: dL/dV(r) = d(eps)/dV(r) = |psi~(r)|^2 / N,
+    # checked against central differences of the dense eigenvalue in V at single grid points.
+    basis, pos, _, _, v_rest, kb = case
+
+    def lowest(v):
+        v_r, beta, dvec = adjoint.hamiltonian_parts(basis, v, pos, inputs.LOCAL_PP, kb)
+        e, vec = np.linalg.eigh(pw.dense_h(basis, v_r, beta, dvec))
+        return e[0], vec[:, 0]
+
+    _, c0 = lowest(v_rest)
+    _, g_v, _ = adjoint.hpsi_vjp(basis, v_rest, pos, inputs.LOCAL_PP, c0[None], c0[None], kb)
+    dens = np.abs(pw.to_real_space(basis, c0[None])[0]) ** 2 / basis.ngrid
+    assert np.allclose(g_v, dens, rtol=0, atol=1e-14)
+    h = 1e-4
+    flat = v_rest.reshape(-1)
+    for j in [0, 777, flat.size // 2 + 13]:
+        vp, vm = flat.copy(), flat.copy()
+        vp[j] += h
+        vm[j] -= h
+        fd = (lowest(vp.reshape(v_rest.shape))[0] - lowest(vm.reshape(v_rest.shape))[0]) / (2 * h)
+        assert abs(fd - g_v.reshape(-1)[j]) <= 1e-8 * g_v.max()
