@@ -311,6 +311,61 @@ def run_adjoint(nb=1088, calls=2):
     return out
 
 
+def run_batched(name, steps=10, warmup=3, ref_steps=3):
+    """Batched ParO (one persistent H psi launch over all orbitals, one CUDA graph per step) on a workload
+    of uneven problems, mixed precision, against the per-context calls on the same problems. Each step
+    synchronises, so host wall time brackets it."""
+    import torch
+    from paper_1702_04045_gb300 import inputs, paro
+    cells = inputs.batch_inputs(name)
+    ctxs = []
+    for c in cells:
+        ctx = paro.Context(c["lat"], c["pos"], c["ecut"], c["n_bands"], c["n_occ"], "mixed", kpts=c["kpts"],
+                           kweights=c["kweights"])
+        ctx.set_local_pp(**inputs.LOCAL_PP)
+        for ik in range(len(c["kpts"])):
+            ctx.set_orbitals(inputs.start_vectors(c["n_bands"], ctx.npw(ik), c["seeds"][ik]), ik)
+        ctxs.append(ctx)
+    b = paro.Batch(ctxs)
+    for _ in range(warmup):
+        b.step(0.25, 8)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        r = b.step(0.25, 8)
+    t_b = (time.perf_counter() - t0) / steps
+    # one fused H psi over every orbital of every problem
+    psis = [ctxs[i].get_orbitals(k, device=True).to(torch.complex64) for i, k in b.problems]
+    b.apply_h(psis)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        b.apply_h(psis)
+    e1.record()
+    torch.cuda.synchronize()
+    t_h = e0.elapsed_time(e1) / 5
+    info = b.info()
+    for c in ctxs:
+        c.step(1, 0.25, 8)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ref_steps):
+        for c in ctxs:
+            c.step(1, 0.25, 8)
+    t_c = (time.perf_counter() - t0) / ref_steps
+    npw = [ctxs[i].npw(k) for i, k in b.problems]
+    out = {"workload": name, "problems": info["problems"], "orbitals": info["items"],
+           "npw_range": [min(npw), max(npw)], "precision": "mixed",
+           "ms_per_step_batched": t_b * 1e3, "ms_per_step_per_context": t_c * 1e3, "speedup": t_c / t_b,
+           "fused_hpsi_ms_all_orbitals": t_h, "fused_kernel": {"threads": info["threads"], "grid": info["grid"]},
+           "kernels_per_step": info["kernels_per_step"], "max_resid_after": r}
+    b.close()
+    for c in ctxs:
+        c.close()
+    return out
+
+
 def cpu_sample(args, steps=1, warmup=0):
     """The FP64 CPU oracle on this host: seconds per ParO-SCF iteration of the same cell."""
     from oracle import scf
@@ -358,6 +413,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -370,6 +426,8 @@ def main():
     out = run_ours(args, rank, world, local, pg)
     if rank == 0 and world == 1 and not args.no_adjoint:
         out["adjoint_512"] = run_adjoint()
+    if rank == 0 and world == 1 and not args.no_batched:
+        out["batched"] = [run_batched("si8_mp27"), run_batched("cells64")]
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             times, cores = cpu_sample(args)
