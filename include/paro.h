@@ -153,7 +153,7 @@ int paro_apply_h_noalloc(paro_ctx* ctx, int ik, int nb, int dtype, const void* p
  *            held fixed) and exp(-i (k+G).R_I) of the projectors.
  *   psi, w, g_psi: device nb x npw complex of dtype (row = band); g_v: device double[N1*N2*N3]
  *   (C order, overwritten); g_pos: device double[n_atoms*3] (overwritten). g_psi, g_v or g_pos may be
- *   NULL to skip that output. Work runs in the precision of dtype (FP32 FFTs and FP64-carried FP32
+ *   NULL to skip that output. Work runs in the precision of dtype (FP32 FFTs and 3xTF32 tensor-core
  *   projections for PARO_C32), accumulated in FP64. Enqueued on the context stream, no synchronisation.
  */
 int paro_apply_h_adjoint(paro_ctx* ctx, int ik, int nb, int dtype, const void* psi, const void* w, void* g_psi,

@@ -247,6 +247,7 @@ static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal) {
   PARO_CU(c, cudaMemcpyAsync(b.eps.data(), w, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   PARO_CU(c, cudaMemcpyAsync(b.res.data(), res, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   PARO_CU(c, cudaStreamSynchronize(c->stream));
+  if ((st = tc_check(c))) return st;
   b.have_psi = true;
   return PARO_OK;
 }
@@ -617,7 +618,7 @@ void paro_destroy(paro_ctx* ctx) {
   }
   void* ps[] = {c->d_tw64[0], c->d_tw64[1], c->d_tw64[2], c->d_tw32[0], c->d_tw32[1], c->d_tw32[2],
                 c->d_vloc, c->d_dvec, c->d_dvec32, c->d_veff, c->d_vplane, c->d_vplane32,
-                c->d_rho_in, c->d_pulay_rho, c->d_pulay_res};
+                c->d_rho_in, c->d_pulay_rho, c->d_pulay_res, c->d_tc_err};
   for (void* p : ps)
     if (p) cudaFree(p);
   for (auto& kv : c->ws) cudaFree(kv.second.first);

@@ -118,17 +118,17 @@ static int hpsi_adjoint(Ctx* c, int ik, int nb, const cplx<T>* psi, const cplx<T
   if (!M || !Y) return PARO_ERR_CUDA;
   double2 *P = M, *A = M + mat, *Pa = M + 2 * mat, *Aa = M + 5 * mat;
   const cplx<T>* beta = projectors<T>(B);
-  if ((st = gemm_cn<T, T, T>(c, np, nb, npw, beta, npw, psi, npw, P, nb, false, true))) return st;
-  if ((st = gemm_cn<T, T, T>(c, np, nb, npw, beta, npw, w, npw, A, nb, false, true))) return st;
+  if ((st = gemm_cn<T, T, T>(c, np, nb, npw, beta, npw, psi, npw, P, nb, false, false))) return st;
+  if ((st = gemm_cn<T, T, T>(c, np, nb, npw, beta, npw, w, npw, A, nb, false, false))) return st;
   Rec3 R;
   for (int i = 0; i < 9; ++i) R.m[i] = c->bmat[i];
   for (int al = 0; al < 3; ++al) {
     k_scale_q<T><<<dim3((npw + 255) / 256, nb), 256, 0, c->stream>>>(npw, B.d_miller, R, B.kcart[al], al, psi, Y);
     PARO_LAUNCH(c, "k_scale_q");
-    if ((st = gemm_cn<T, T, T>(c, np, nb, npw, beta, npw, Y, npw, Pa + al * mat, nb, false, true))) return st;
+    if ((st = gemm_cn<T, T, T>(c, np, nb, npw, beta, npw, Y, npw, Pa + al * mat, nb, false, false))) return st;
     k_scale_q<T><<<dim3((npw + 255) / 256, nb), 256, 0, c->stream>>>(npw, B.d_miller, R, B.kcart[al], al, w, Y);
     PARO_LAUNCH(c, "k_scale_q");
-    if ((st = gemm_cn<T, T, T>(c, np, nb, npw, beta, npw, Y, npw, Aa + al * mat, nb, false, true))) return st;
+    if ((st = gemm_cn<T, T, T>(c, np, nb, npw, beta, npw, Y, npw, Aa + al * mat, nb, false, false))) return st;
   }
   k_kb_force<<<c->nat, 256, 0, c->stream>>>(nb, P, A, Pa, Aa, mat, c->d_dvec, gpos);
   PARO_LAUNCH(c, "k_kb_force");

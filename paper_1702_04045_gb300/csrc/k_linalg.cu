@@ -2,8 +2,11 @@
 // Gram and Rayleigh-Ritz matrices (long-K "conj(A) B^T" GEMM, split over K with a fixed-order
 // reduction), subspace rotations (short-K update GEMM), Cholesky orthonormalisation and the
 // Hermitian eigensolver of the small Rayleigh-Ritz problem.
+#include <cooperative_groups.h>
+
 #include <cfloat>
 #include <cmath>
+#include <cstdlib>
 
 #include "paro_ctx.h"
 
@@ -170,10 +173,51 @@ static void launch_cn(int r, bool carry, dim3 grid, cudaStream_t st, int M, int 
     launch_cn_r<TA, TB, ACC, false>(r, grid, st, M, N, K, kslice, A, lda, B, ldb, part, herm);
 }
 
+bool tc_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("PARO_NO_TC");
+    return !(e && e[0] && e[0] != '0');
+  }();
+  return on;
+}
+
+int* tc_err_flag(Ctx* c) {
+  if (!c->d_tc_err) {
+    if (cudaMalloc(&c->d_tc_err, sizeof(int)) != cudaSuccess) return nullptr;
+    if (cudaMemsetAsync(c->d_tc_err, 0, sizeof(int), c->stream) != cudaSuccess) return nullptr;
+  }
+  return c->d_tc_err;
+}
+
+int tc_check(Ctx* c) {
+  if (!c->d_tc_err) return PARO_OK;
+  int h = 0;
+  PARO_CU(c, cudaMemcpyAsync(&h, c->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  PARO_CU(c, cudaStreamSynchronize(c->stream));
+  if (h) return fail(c, PARO_ERR_TIMEOUT, "tensor-core product: mbarrier wait gave up");
+  return PARO_OK;
+}
+
 template <typename TA, typename TB, typename ACC>
 int gemm_cn(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb, double2* C,
             int ldc, bool herm, bool carry) {
   if (M <= 0 || N <= 0) return PARO_OK;
+  if constexpr (sizeof(TA) == 4 && sizeof(TB) == 4 && sizeof(ACC) == 4) {
+    if (!herm && !carry && K > 0 && tc_enabled()) {
+      int nz = 1, kslice = 16;
+      gemm_cn_tc_plan(M, N, K, &nz, &kslice);
+      double2* part = static_cast<double2*>(ws_get(c, "gemm_parts", (size_t)nz * M * N * sizeof(double2)));
+      int* err = tc_err_flag(c);
+      if (!part || !err) return PARO_ERR_CUDA;
+      cudaEvent_t ev = prof_begin(c);
+      int st = gemm_cn_tc(c, M, N, K, A, lda, B, ldb, part, kslice, nz, err);
+      if (st) return st;
+      prof_end(c, "k_gemm_cn_tc", ev);
+      k_reduce_parts<<<(M * N + 255) / 256, 256, 0, c->stream>>>(M, N, nz, part, C, ldc, 0, 64);
+      PARO_LAUNCH(c, "k_reduce_parts");
+      return PARO_OK;
+    }
+  }
   const int r = pick_r(M, N, herm), tile = 16 * r;
   const int tiles_m = (M + tile - 1) / tile, tiles_n = (N + tile - 1) / tile;
   const int tiles = herm ? tiles_m * (tiles_m + 1) / 2 : tiles_m * tiles_n;
@@ -282,6 +326,17 @@ template <typename TX, typename TY>
 int gemm_wx(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, const double* s, const cplx<TX>* X,
             int ldx, cplx<TY>* Y, int ldy, double beta) {
   if (M <= 0 || N <= 0) return PARO_OK;
+  if constexpr (sizeof(TX) == 4 && sizeof(TY) == 4) {
+    if (tc_enabled()) {
+      int* err = tc_err_flag(c);
+      if (!err) return PARO_ERR_CUDA;
+      cudaEvent_t ev = prof_begin(c);
+      int st = gemm_wx_tc(c, M, N, K, W, ldw, wt, s, X, ldx, Y, ldy, beta, err);
+      if (st) return st;
+      prof_end(c, "k_gemm_wx_tc", ev);
+      return PARO_OK;
+    }
+  }
   cudaEvent_t ev = prof_begin(c);
   k_gemm_wx<TX, TY><<<dim3((N + 63) / 64, (M + 31) / 32), 256, 0, c->stream>>>(M, N, K, W, ldw, wt ? 1 : 0, s, X,
                                                                                ldx, Y, ldy, beta);
@@ -358,7 +413,132 @@ __global__ void __launch_bounds__(256) k_chol(int n, const double2* __restrict__
 
 int coop_grid(Ctx* c, const void* kernel, int threads, size_t smem, int cap, int* grid);  // k_eigh.cu
 
+// Cholesky S = L L^H and G = conj(L)^{-1} on one thread-block cluster of C CTAs, row g of [S | I] in
+// CTA g mod C. Gaussian elimination without pivoting (stable for Hermitian positive definite S): step j
+// subtracts m_ij = a_ij / a_jj times pivot row j from every row i > j, in both halves. That leaves
+// D L_u^H on the left and L_u^{-1} on the right (S = L_u D L_u^H, L_u unit lower triangular), so
+// L^{-1} = D^{-1/2} L_u^{-1}. Row j is final once step j-1 is done and is never written again; every CTA
+// copies it from its owner's shared memory, and one cluster barrier per column orders the steps.
+// info: first column + 1 with a_jj <= 0 (the elimination then continues with a_jj = 1).
+__global__ void __launch_bounds__(1024) k_chol_cluster(int n, const double2* __restrict__ s, double2* __restrict__ g,
+                                                       int* __restrict__ info) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), q = (int)cl.block_rank();
+  const int R = (n + C - 1) / C, W2 = 2 * n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* rows = reinterpret_cast<double2*>(smem_raw);  // R x 2n: [a_i | b_i]
+  double2* piv = rows + (size_t)R * W2;                  // this step's pivot row
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  if (tid == 0) s_bad = 0;
+  for (size_t idx = tid; idx < (size_t)R * W2; idx += blockDim.x) {
+    const int r = (int)(idx / W2), k = (int)(idx - (size_t)r * W2), gi = q + C * r;
+    double2 v = make_double2(0.0, 0.0);
+    if (gi < n) v = k < n ? s[(size_t)gi * n + k] : make_double2(k - n == gi ? 1.0 : 0.0, 0.0);
+    rows[idx] = v;
+  }
+  cl.sync();
+  for (int j = 0; j < n; ++j) {
+    const double2* pr = cl.map_shared_rank(rows + (size_t)(j / C) * W2, j % C);
+    for (int k = tid; k < W2; k += blockDim.x)
+      if ((k >= j && k < n) || (k >= n && k - n <= j)) piv[k] = pr[k];
+    __syncthreads();
+    double ajj = piv[j].x;
+    if (!(ajj > 0.0) || !isfinite(ajj)) {
+      if (tid == 0 && s_bad == 0) s_bad = j + 1;
+      ajj = 1.0;
+    }
+    const double inv = 1.0 / ajj;
+    const int r0 = (j + 1 > q) ? (j + 1 - q + C - 1) / C : 0;  // first local row with g > j
+    for (int r = r0 + warp; r < R; r += nwarp) {
+      const int gi = q + C * r;
+      if (gi >= n) break;
+      double2* row = rows + (size_t)r * W2;
+      const double2 m = cscale(row[j], inv);
+      for (int k = j + 1 + lane; k < n; k += 32) row[k] = csub(row[k], cmul(m, piv[k]));
+      for (int k = lane; k <= j; k += 32) row[n + k] = csub(row[n + k], cmul(m, piv[n + k]));
+    }
+    cl.sync();
+  }
+  for (size_t idx = tid; idx < (size_t)R * n; idx += blockDim.x) {
+    const int r = (int)(idx / n), k = (int)(idx - (size_t)r * n), gi = q + C * r;
+    if (gi >= n) continue;
+    const double d = rows[(size_t)r * W2 + gi].x;
+    const double2 b = rows[(size_t)r * W2 + n + k];
+    g[(size_t)gi * n + k] = (k <= gi && d > 0.0) ? cscale(cconj(b), 1.0 / sqrt(d)) : make_double2(0.0, 0.0);
+  }
+  if (q == 0 && tid == 0) *info = s_bad;
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+// cluster size (16, else 8; 0 = neither fits) and threads for k_chol_cluster
+static int chol_cluster_shape(Ctx* c, int n, int* cls, int* thr, size_t* smem) {
+  *cls = 0;
+  PARO_CU(c, cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  PARO_CU(c, cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  for (int C : {16, 8}) {
+    const int R = (n + C - 1) / C;
+    const size_t sm = ((size_t)R * 2 * n + 2 * (size_t)n) * sizeof(double2);
+    if (sm > 200 * 1024) continue;
+    const int warps = R < 4 ? 4 : (R > 32 ? 32 : R);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(32 * warps);
+    cfg.dynamicSmemBytes = sm;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_chol_cluster, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (nclusters >= 1) {
+      *cls = C;
+      *thr = 32 * warps;
+      *smem = sm;
+      return PARO_OK;
+    }
+  }
+  return PARO_OK;
+}
+
 int chol_inv(Ctx* c, int n, const double2* s, double2* g) {
+  {
+    int cls = 0, thr = 0, st;
+    size_t sm = 0;
+    if ((st = chol_cluster_shape(c, n, &cls, &thr, &sm))) return st;
+    if (cls > 0) {
+      int* flags = static_cast<int*>(ws_get(c, "chol_flags", 8 * sizeof(int)));
+      if (!flags) return PARO_ERR_CUDA;
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cls;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(cls);
+      cfg.blockDim = dim3(thr);
+      cfg.dynamicSmemBytes = sm;
+      cfg.stream = c->stream;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      cudaEvent_t ev = prof_begin(c);
+      PARO_CU(c, cudaLaunchKernelEx(&cfg, k_chol_cluster, n, s, g, flags));
+      ++c->launches;
+      prof_end(c, "k_chol_cluster", ev);
+      int h = 0;
+      PARO_CU(c, cudaMemcpyAsync(&h, flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+      PARO_CU(c, cudaStreamSynchronize(c->stream));
+      if (h) return fail(c, PARO_ERR_BREAKDOWN, "Cholesky pivot <= 0 at column " + std::to_string(h - 1));
+      return PARO_OK;
+    }
+  }
   double2* W = static_cast<double2*>(ws_get(c, "chol_W", (size_t)n * n * sizeof(double2)));
   double2* L = static_cast<double2*>(ws_get(c, "chol_L", (size_t)n * n * sizeof(double2)));
   int* flags = static_cast<int*>(ws_get(c, "chol_flags", 8 * sizeof(int)));

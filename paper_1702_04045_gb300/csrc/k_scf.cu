@@ -388,11 +388,13 @@ __global__ void k_vplane(int N1, int N2, int N3, const double* __restrict__ v, d
   vp32[idx] = (float)val;
 }
 
-__global__ void k_min_sum(int n, const double* __restrict__ v, double* __restrict__ out) {
+// sum and minimum of V over the grid: per-CTA partials over fixed chunks, then one CTA combines them
+// in order (deterministic)
+__global__ void k_min_sum(int n, const double* __restrict__ v, double* __restrict__ part) {
   __shared__ double red[32];
   __shared__ double rmin[32];
   double s = 0.0, mn = 1e300;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     s += v[i];
     mn = fmin(mn, v[i]);
   }
@@ -403,9 +405,20 @@ __global__ void k_min_sum(int n, const double* __restrict__ v, double* __restric
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mn = fmin(mn, rmin[w]);
-    out[0] = s;
-    out[1] = fmin(mn, rmin[0]);
+    part[2 * blockIdx.x] = s;
+    part[2 * blockIdx.x + 1] = fmin(mn, rmin[0]);
   }
+}
+
+__global__ void k_min_sum_final(int nblk, const double* __restrict__ part, double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double s = 0.0, mn = 1e300;
+  for (int b = 0; b < nblk; ++b) {
+    s += part[2 * b];
+    mn = fmin(mn, part[2 * b + 1]);
+  }
+  out[0] = s;
+  out[1] = mn;
 }
 
 int set_veff_device(Ctx* c, const double* v_dev) {
@@ -420,10 +433,13 @@ int set_veff_device(Ctx* c, const double* v_dev) {
   k_vplane<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->N[0], c->N[1], c->N[2], c->d_veff, c->d_vplane,
                                                           c->d_vplane32, 1.0 / c->ngrid);
   PARO_LAUNCH(c, "k_vplane");
-  double* ms = static_cast<double*>(ws_get(c, "vminsum", 2 * sizeof(double)));
+  const int nblk = 304;
+  double* ms = static_cast<double*>(ws_get(c, "vminsum", (2 + 2 * nblk) * sizeof(double)));
   if (!ms) return PARO_ERR_CUDA;
-  k_min_sum<<<1, 1024, 0, c->stream>>>(c->ngrid, c->d_veff, ms);
+  k_min_sum<<<nblk, 256, 0, c->stream>>>(c->ngrid, c->d_veff, ms + 2);
   PARO_LAUNCH(c, "k_min_sum");
+  k_min_sum_final<<<1, 32, 0, c->stream>>>(nblk, ms + 2, ms);
+  PARO_LAUNCH(c, "k_min_sum_final");
   double h[2];
   PARO_CU(c, cudaMemcpyAsync(h, ms, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   PARO_CU(c, cudaStreamSynchronize(c->stream));

@@ -2,7 +2,7 @@
 wrapper) against the FP64 CPU oracle (oracle/adjoint.py) on the same seeded inputs.
 
 Tolerances: FP64 (complex128 inputs) to rounding, 1e-11 relative to the largest entry of each
-output; FP32 (complex64 inputs) 2e-5 relative (FP32 FFTs and FP64-carried FP32 projections)."""
+output; FP32 (complex64 inputs) 2e-5 relative (FP32 FFTs and 3xTF32 tensor-core projections)."""
 import numpy as np
 import pytest
 
