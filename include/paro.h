@@ -230,8 +230,11 @@ int paro_get_residuals(paro_ctx* ctx, double* res);
 int paro_step(paro_ctx* ctx, int alg, double rel_tol, int max_it, double* max_resid_out);
 
 /*
- * paro_eigh -- Hermitian eigensolver used by the Rayleigh-Ritz step (one CTA, FP64): Householder
- * tridiagonalisation, implicit-shift QL, back-transformation.
+ * paro_eigh -- Hermitian eigensolver used by the Rayleigh-Ritz step (Algorithm 1 step 4). FP64 contexts:
+ * Householder tridiagonalisation, multisection, inverse iteration, back-transformation, all in FP64.
+ * Mixed contexts (n <= 160): the same steps in FP32, then two FP64 refinement steps of the eigenvector
+ * matrix (Ogita-Aishima) and a Rayleigh-Ritz inside each cluster of close eigenvalues; the result has
+ * FP64 accuracy.
  *   a  device n x n complex double, row-major, Hermitian (the lower triangle is read); w device double[n]
  *   ascending eigenvalues; v device n x n complex double, column j = eigenvector j (row-major storage).
  */

@@ -83,6 +83,7 @@ static int hpsi_adjoint(Ctx* c, int ik, int nb, const cplx<T>* psi, const cplx<T
   const Basis& B = c->bases[ik];
   const int npw = B.npw;
   const bool f64 = sizeof(T) == 8;
+  TcScope tcs(c);  // gradients in FP32 use the 3xTF32 products
   int st;
   if (gpsi && (st = apply_h<T>(c, ik, nb, w, gpsi, 0.0, nullptr))) return st;
   double* gvv = gv;

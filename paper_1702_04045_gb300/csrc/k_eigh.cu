@@ -1,20 +1,22 @@
 // Hermitian eigensolver of the Rayleigh-Ritz step (Algorithm 1 step 4; Algorithm 2 step 4), FP64.
 // GB300 runs FP64 at about 2 FMA per clock per SM, so every O(n^3) part is spread over many SMs:
 //
-//  1. k_tridiag (cooperative, many CTAs): Householder reduction A <- H_j A H_j, H_j = I - tau u u^H,
-//     to a Hermitian tridiagonal matrix; step j's matrix-vector product and rank-2 update are shared
-//     by all CTAs, separated by grid barriers. A diagonal unitary D (D_0 = 1,
-//     D_{j+1} = D_j conj(e_j)/|e_j|) turns the complex off-diagonals e_j into |e_j|: a real symmetric
-//     tridiagonal T'.
+//  1. k_tridiag_cluster (one thread-block cluster of 16 or 8 CTAs, the matrix in their distributed shared
+//     memory) or, when it does not fit, k_tridiag (cooperative, many CTAs, grid barriers): Householder
+//     reduction A <- H_j A H_j, H_j = I - tau u u^H, to a Hermitian tridiagonal matrix. A diagonal
+//     unitary D (D_0 = 1, D_{j+1} = D_j conj(e_j)/|e_j|) turns the complex off-diagonals e_j into |e_j|:
+//     a real symmetric tridiagonal T'.
 //  2. k_bisect (warp per eigenvalue): the k-th eigenvalue of T' by multisection on the Sturm count
 //     (the number of negative pivots of the LDL^T factorisation of T' - x), 32 points per step.
-//  3. k_invit (one CTA): eigenvectors of T' by inverse iteration, one thread per eigenvalue, with the
-//     LU factorisation of T' - lambda (partial pivoting); after each of three iterations the vectors of
-//     a cluster (eigenvalues closer than 1e-3 ||T'||_1) are orthogonalised in eigenvalue order by one
-//     warp (the standard remedy for close eigenvalues, as in LAPACK's xSTEIN).
+//  3. k_invit_solve / k_invit_mgs: eigenvectors of T' by inverse iteration, one thread per eigenvalue
+//     with its LU factorisation of T' - lambda (partial pivoting) and its vector in shared memory; after
+//     each of three solves the vectors of a cluster (eigenvalues closer than 1e-3 ||T'||_1) are
+//     orthogonalised in eigenvalue order by one warp (the standard remedy for close eigenvalues, as in
+//     LAPACK's xSTEIN).
 //  4. k_backtransform (warp per column, many CTAs): eigenvectors of A = Q D^H z, Q = H_0 H_1 ...
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 
@@ -268,182 +270,204 @@ __global__ void __launch_bounds__(1024) k_tridiag_cluster(int n, const double2* 
 }
 
 // -------------------------------------------------------------------------------------------------
-// 2. multisection: w[k] = k-th smallest eigenvalue of T' (d, e); one warp per eigenvalue
+// 2. multisection: w[k] = k-th smallest eigenvalue of T' (d, e); one warp per eigenvalue. R = double,
+// or float for the first stage of the mixed-precision solver (refined afterwards in FP64).
 // -------------------------------------------------------------------------------------------------
-__device__ __forceinline__ int sturm_count(int n, const double* d, const double* e2, double x, double pivmin) {
-  double q = d[0] - x;
+template <typename R> struct RealLimits;
+template <> struct RealLimits<double> {
+  static __device__ __forceinline__ double eps() { return DBL_EPSILON; }
+  static __device__ __forceinline__ double tiny() { return DBL_MIN; }
+  static __device__ __forceinline__ double huge() { return 1e300; }
+};
+template <> struct RealLimits<float> {
+  static __device__ __forceinline__ float eps() { return FLT_EPSILON; }
+  static __device__ __forceinline__ float tiny() { return FLT_MIN; }
+  static __device__ __forceinline__ float huge() { return 1e30f; }
+};
+
+template <typename R>
+__device__ __forceinline__ int sturm_count(int n, const R* d, const R* e2, R x, R pivmin) {
+  R q = d[0] - x;
   if (fabs(q) < pivmin) q = -pivmin;
-  int c = q < 0.0;
+  int c = q < (R)0;
   for (int i = 1; i < n; ++i) {
     q = d[i] - x - e2[i - 1] / q;
     if (fabs(q) < pivmin) q = -pivmin;
-    c += q < 0.0;
+    c += q < (R)0;
   }
   return c;
 }
 
-__global__ void __launch_bounds__(128) k_bisect(int n, const double* __restrict__ dg, const double* __restrict__ eg,
-                                                double* __restrict__ w) {
+template <typename R>
+__global__ void __launch_bounds__(128) k_bisect(int n, const R* __restrict__ dg, const R* __restrict__ eg,
+                                                R* __restrict__ w) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* d = reinterpret_cast<double*>(smem_raw);
-  double* e2 = d + n;
-  __shared__ double s_lo, s_hi, s_pivmin;
+  R* d = reinterpret_cast<R*>(smem_raw);
+  R* e2 = d + n;
+  __shared__ R s_lo, s_hi, s_pivmin;
+  using L = RealLimits<R>;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     d[i] = dg[i];
     e2[i] = eg[i] * eg[i];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double lo = 1e300, hi = -1e300, emax = 0.0;
+    R lo = L::huge(), hi = -L::huge(), emax = 0;
     for (int i = 0; i < n; ++i) {
-      const double r = (i > 0 ? fabs(eg[i - 1]) : 0.0) + (i + 1 < n ? fabs(eg[i]) : 0.0);
+      const R r = (i > 0 ? fabs(eg[i - 1]) : (R)0) + (i + 1 < n ? fabs(eg[i]) : (R)0);
       lo = fmin(lo, d[i] - r);
       hi = fmax(hi, d[i] + r);
       emax = fmax(emax, e2[i]);
     }
-    const double tn = fmax(fabs(lo), fabs(hi));
-    s_lo = lo - 2.0 * DBL_EPSILON * tn * n - DBL_MIN;
-    s_hi = hi + 2.0 * DBL_EPSILON * tn * n + DBL_MIN;
-    s_pivmin = DBL_MIN * fmax(1.0, emax);
+    const R tn = fmax(fabs(lo), fabs(hi));
+    s_lo = lo - (R)2 * L::eps() * tn * n - L::tiny();
+    s_hi = hi + (R)2 * L::eps() * tn * n + L::tiny();
+    s_pivmin = L::tiny() * fmax((R)1, emax);
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (k >= n) return;
-  double lo = s_lo, hi = s_hi;
+  R lo = s_lo, hi = s_hi;
   for (int it = 0; it < 64; ++it) {
-    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + s_pivmin) break;
-    const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-    const int cnt = sturm_count(n, d, e2, x, s_pivmin);
+    if (hi - lo <= (R)2 * L::eps() * fmax(fabs(lo), fabs(hi)) + s_pivmin) break;
+    const R x = lo + (hi - lo) * (R)(lane + 1) / (R)33;
+    const int cnt = sturm_count<R>(n, d, e2, x, s_pivmin);
     const unsigned above = __ballot_sync(0xffffffffu, cnt > k);
     const int l = above ? __ffs(above) - 1 : 32;  // first point with more than k eigenvalues below it
-    const double xl = __shfl_sync(0xffffffffu, x, l < 32 ? l : 31);
-    const double xm = __shfl_sync(0xffffffffu, x, l > 0 ? l - 1 : 0);
-    const double nlo = l == 0 ? lo : xm;
-    const double nhi = l == 32 ? hi : xl;
+    const R xl = __shfl_sync(0xffffffffu, x, l < 32 ? l : 31);
+    const R xm = __shfl_sync(0xffffffffu, x, l > 0 ? l - 1 : 0);
+    const R nlo = l == 0 ? lo : xm;
+    const R nhi = l == 32 ? hi : xl;
     if (!(nhi - nlo < hi - lo)) break;
     lo = nlo;
     hi = nhi;
   }
-  if (lane == 0) w[k] = 0.5 * (lo + hi);
+  if (lane == 0) w[k] = (R)0.5 * (lo + hi);
 }
 
 // -------------------------------------------------------------------------------------------------
-// 3. block inverse iteration (one CTA, n <= blockDim.x). Z: column j = eigenvector j of T'
-// (row-major n x n). lu: 5 n^2 doubles (U rows, reciprocal pivot, multipliers, interchange flags).
+// 3. inverse iteration. Shifts: eigenvalues closer than ortol = 1e-3 ||T'||_1 form a cluster, and shifts
+// inside a cluster are kept at least 10 eps |lambda| + eps ||T'||_1 apart (k_invit_prep, one thread).
+// k_invit_solve: one thread per eigenvalue, EPB per CTA, the LU factorisation of T' - lambda_j (partial
+// pivoting) and the vector in shared memory ([row][thread], conflict free); solves (T' - lambda_j) z = z
+// from the stored vector (or a fixed start vector) and writes it back. k_invit_mgs: the vectors of each
+// cluster are orthonormalised in eigenvalue order by one warp (the standard remedy for close eigenvalues,
+// as in LAPACK's xSTEIN). Three rounds of solve + orthonormalisation. Z: column j = vector j (n x n).
 // -------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_invit(int n, const double* __restrict__ d, const double* __restrict__ e,
-                                                const double* __restrict__ w, double* __restrict__ Z,
-                                                double* __restrict__ lu, int* __restrict__ info) {
+template <typename R>
+__global__ void k_invit_prep(int n, const R* __restrict__ d, const R* __restrict__ e, const R* __restrict__ w,
+                             R* __restrict__ lam, int* __restrict__ cstart, int* __restrict__ nclu,
+                             R* __restrict__ tiny_out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  using L = RealLimits<R>;
+  const R eps = L::eps();
+  R t1 = 0;
+  for (int i = 0; i < n; ++i)
+    t1 = fmax(t1, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : (R)0) + (i + 1 < n ? fabs(e[i]) : (R)0));
+  t1 = fmax(t1, L::tiny());
+  const R ortol = (R)1e-3 * t1, tiny = eps * t1;
+  int nc = 0;
+  for (int j = 0; j < n; ++j) {
+    R l = w[j];
+    if (j == 0 || w[j] - w[j - 1] > ortol) {
+      cstart[nc++] = j;
+    } else if (l - lam[j - 1] < (R)10 * eps * fabs(l) + tiny) {
+      l = lam[j - 1] + (R)10 * eps * fabs(l) + tiny;
+    }
+    lam[j] = l;
+  }
+  cstart[nc] = n;
+  *nclu = nc;
+  *tiny_out = tiny;
+}
+
+template <typename R>
+__global__ void k_invit_solve(int n, const R* __restrict__ d, const R* __restrict__ e, const R* __restrict__ lam,
+                              const R* __restrict__ tinyp, R* __restrict__ Z, int first) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* lam = reinterpret_cast<double*>(smem_raw);   // n shifts
-  int* cstart = reinterpret_cast<int*>(lam + n);        // n + 1
-  __shared__ int s_nclu;
-  __shared__ double s_tiny;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const double eps = DBL_EPSILON;
-  if (tid == 0) {
-    double t1 = 0.0;
-    for (int i = 0; i < n; ++i)
-      t1 = fmax(t1, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0));
-    t1 = fmax(t1, DBL_MIN);
-    const double ortol = 1e-3 * t1, tiny = eps * t1;
-    s_tiny = tiny;
-    int nc = 0;
-    for (int j = 0; j < n; ++j) {
-      double l = w[j];
-      if (j == 0 || w[j] - w[j - 1] > ortol) {
-        cstart[nc++] = j;
-      } else if (l - lam[j - 1] < 10.0 * eps * fabs(l) + tiny) {
-        l = lam[j - 1] + 10.0 * eps * fabs(l) + tiny;  // distinct shifts inside a cluster
-      }
-      lam[j] = l;
+  const int E = blockDim.x, t = threadIdx.x, j = blockIdx.x * E + t;
+  R* R0 = reinterpret_cast<R*>(smem_raw);  // 1 / (guarded pivot)
+  R* U1 = R0 + (size_t)n * E;
+  R* U2 = U1 + (size_t)n * E;
+  R* Lm = U2 + (size_t)n * E;
+  R* z = Lm + (size_t)n * E;
+  unsigned char* SW = reinterpret_cast<unsigned char*>(z + (size_t)n * E);
+  if (j >= n) return;  // no barriers below
+  const R tiny = *tinyp, l = lam[j];
+  R p = d[0] - l, q = n > 1 ? e[0] : (R)0, r = 0;
+  for (int i = 0; i + 1 < n; ++i) {  // LU of T' - l with partial pivoting, row i at [i * E + t]
+    const R b = e[i];
+    const R a1 = d[i + 1] - l, c1 = (i + 2 < n) ? e[i + 1] : (R)0;
+    R u0, u1, u2, mlt;
+    unsigned char sw;
+    if (fabs(p) >= fabs(b)) {
+      mlt = (p != (R)0) ? b / p : (R)0;
+      u0 = p; u1 = q; u2 = r; sw = 0;
+      p = a1 - mlt * q;
+      q = c1 - mlt * r;
+    } else {
+      mlt = p / b;
+      u0 = b; u1 = a1; u2 = c1; sw = 1;
+      p = q - mlt * a1;
+      q = r - mlt * c1;
     }
-    cstart[nc] = n;
-    s_nclu = nc;
+    r = 0;
+    if (fabs(u0) < tiny) u0 = u0 < (R)0 ? -tiny : tiny;
+    const size_t o = (size_t)i * E + t;
+    R0[o] = (R)1 / u0; U1[o] = u1; U2[o] = u2; Lm[o] = mlt; SW[o] = sw;
   }
-  __syncthreads();
-  const double tiny = s_tiny;
-  const size_t nn = (size_t)n * n;
-  double* U1 = lu;
-  double* U2 = lu + nn;
-  double* R0 = lu + 2 * nn;  // 1 / (guarded pivot)
-  double* L = lu + 3 * nn;
-  double* SW = lu + 4 * nn;
-  if (tid < n) {  // LU of T' - lam_j with partial pivoting; element i of column j at [i*n + j]
-    const int j = tid;
-    const double l = lam[j];
-    double p = d[0] - l, q = n > 1 ? e[0] : 0.0, r = 0.0;
-    for (int i = 0; i + 1 < n; ++i) {
-      const double b = e[i];
-      const double a1 = d[i + 1] - l, c1 = (i + 2 < n) ? e[i + 1] : 0.0;
-      double u0, u1, u2, mlt, sw;
-      if (fabs(p) >= fabs(b)) {
-        mlt = (p != 0.0) ? b / p : 0.0;
-        u0 = p; u1 = q; u2 = r; sw = 0.0;
-        p = a1 - mlt * q;
-        q = c1 - mlt * r;
-      } else {
-        mlt = p / b;
-        u0 = b; u1 = a1; u2 = c1; sw = 1.0;
-        p = q - mlt * a1;
-        q = r - mlt * c1;
-      }
-      r = 0.0;
-      if (fabs(u0) < tiny) u0 = u0 < 0.0 ? -tiny : tiny;
-      const size_t o = (size_t)i * n + j;
-      R0[o] = 1.0 / u0; U1[o] = u1; U2[o] = u2; L[o] = mlt; SW[o] = sw;
-    }
-    if (fabs(p) < tiny) p = p < 0.0 ? -tiny : tiny;
-    const size_t o = (size_t)(n - 1) * n + j;
-    R0[o] = 1.0 / p; U1[o] = 0.0; U2[o] = 0.0; L[o] = 0.0; SW[o] = 0.0;
-    for (int i = 0; i < n; ++i) Z[(size_t)i * n + j] = (double)(((i * 7919 + j * 104729) % 1999) + 1) / 1999.0 - 0.5;
+  if (fabs(p) < tiny) p = p < (R)0 ? -tiny : tiny;
+  {
+    const size_t o = (size_t)(n - 1) * E + t;
+    R0[o] = (R)1 / p; U1[o] = 0; U2[o] = 0; Lm[o] = 0; SW[o] = 0;
   }
-  __syncthreads();
-  for (int it = 0; it < 3; ++it) {
-    if (tid < n) {  // solve (T' - lam_j) z = z in place
-      const int j = tid;
-      for (int i = 0; i + 1 < n; ++i) {
-        const size_t o = (size_t)i * n + j;
-        double zi = Z[o], zi1 = Z[o + n];
-        if (SW[o] != 0.0) { const double t = zi; zi = zi1; zi1 = t; }
-        Z[o] = zi;
-        Z[o + n] = zi1 - L[o] * zi;
-      }
-      for (int i = n - 1; i >= 0; --i) {
-        const size_t o = (size_t)i * n + j;
-        double s = Z[o];
-        if (i + 1 < n) s -= U1[o] * Z[o + n];
-        if (i + 2 < n) s -= U2[o] * Z[o + 2 * n];
-        Z[o] = s * R0[o];
-      }
-    }
-    __syncthreads();
-    for (int cl = warp; cl < s_nclu; cl += nw) {  // orthonormalise each cluster in eigenvalue order
-      const int c0 = cstart[cl], c1 = cstart[cl + 1];
-      for (int j = c0; j < c1; ++j) {
-        for (int q = c0; q < j; ++q) {
-          double s = 0.0;
-          for (int i = lane; i < n; i += 32) s += Z[(size_t)i * n + j] * Z[(size_t)i * n + q];
+  for (int i = 0; i < n; ++i)
+    z[(size_t)i * E + t] = first ? (R)(((i * 7919 + j * 104729) % 1999) + 1) / (R)1999 - (R)0.5 : Z[(size_t)i * n + j];
+  for (int i = 0; i + 1 < n; ++i) {  // forward: row interchanges and multipliers
+    const size_t o = (size_t)i * E + t;
+    R zi = z[o], zi1 = z[o + E];
+    if (SW[o]) { const R tmp = zi; zi = zi1; zi1 = tmp; }
+    z[o] = zi;
+    z[o + E] = zi1 - Lm[o] * zi;
+  }
+  for (int i = n - 1; i >= 0; --i) {  // back substitution with U (bandwidth 3)
+    const size_t o = (size_t)i * E + t;
+    R sv = z[o];
+    if (i + 1 < n) sv -= U1[o] * z[o + E];
+    if (i + 2 < n) sv -= U2[o] * z[o + 2 * E];
+    z[o] = sv * R0[o];
+  }
+  for (int i = 0; i < n; ++i) Z[(size_t)i * n + j] = z[(size_t)i * E + t];
+}
+
+template <typename R>
+__global__ void k_invit_mgs(int n, R* __restrict__ Z, const int* __restrict__ cstart, const int* __restrict__ nclu,
+                            int* __restrict__ info) {
+  const int lane = threadIdx.x & 31;
+  const int cl = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (cl >= *nclu) return;
+  const int c0 = cstart[cl], c1 = cstart[cl + 1];
+  for (int j = c0; j < c1; ++j) {
+    for (int q = c0; q < j; ++q) {
+      R s = 0;
+      for (int i = lane; i < n; i += 32) s += Z[(size_t)i * n + j] * Z[(size_t)i * n + q];
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-          for (int i = lane; i < n; i += 32) Z[(size_t)i * n + j] -= s * Z[(size_t)i * n + q];
-          __syncwarp();
-        }
-        double nrm = 0.0;
-        for (int i = lane; i < n; i += 32) nrm += Z[(size_t)i * n + j] * Z[(size_t)i * n + j];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-        if (!(nrm > 0.0) || !isfinite(nrm)) {
-          if (lane == 0) atomicExch(info, 1);
-          nrm = 1.0;
-        }
-        const double inv = 1.0 / sqrt(nrm);
-        for (int i = lane; i < n; i += 32) Z[(size_t)i * n + j] *= inv;
-        __syncwarp();
-      }
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      for (int i = lane; i < n; i += 32) Z[(size_t)i * n + j] -= s * Z[(size_t)i * n + q];
+      __syncwarp();
     }
-    __syncthreads();
+    R nrm = 0;
+    for (int i = lane; i < n; i += 32) nrm += Z[(size_t)i * n + j] * Z[(size_t)i * n + j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+    if (!(nrm > (R)0) || !isfinite(nrm)) {
+      if (lane == 0) atomicExch(info, 1);
+      nrm = 1;
+    }
+    const R inv = (R)1 / sqrt(nrm);
+    for (int i = lane; i < n; i += 32) Z[(size_t)i * n + j] *= inv;
+    __syncwarp();
   }
 }
 
@@ -451,24 +475,24 @@ __global__ void __launch_bounds__(1024) k_invit(int n, const double* __restrict_
 // 4. back-transformation: V[:, c] = H_0 H_1 ... H_{n-2} D^H Z[:, c]; one warp per column. Element i of
 // u_j is at U[j sj + i si].
 // -------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_backtransform(int n, const double2* __restrict__ U, size_t sj, size_t si,
-                                                       const double* __restrict__ tau,
-                                                       const double2* __restrict__ ph,
-                                                       const double* __restrict__ Z, double2* __restrict__ V) {
+template <typename R>
+__global__ void __launch_bounds__(256) k_backtransform(int n, const cplx<R>* __restrict__ U, size_t sj, size_t si,
+                                                       const R* __restrict__ tau, const cplx<R>* __restrict__ ph,
+                                                       const R* __restrict__ Z, cplx<R>* __restrict__ V) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int cpb = blockDim.x >> 5;  // columns per CTA
-  double2* vc = reinterpret_cast<double2*>(smem_raw);  // n x cpb
+  cplx<R>* vc = reinterpret_cast<cplx<R>*>(smem_raw);  // n x cpb
   const int lane = threadIdx.x & 31, wc = threadIdx.x >> 5;
   const int col = blockIdx.x * cpb + wc;
   if (col >= n) return;
   for (int i = lane; i < n; i += 32) vc[(size_t)i * cpb + wc] = cscale(cconj(ph[i]), Z[(size_t)i * n + col]);
   __syncwarp();
   for (int j = n - 2; j >= 0; --j) {
-    const double t = tau[j];
-    if (t == 0.0) continue;
+    const R t = tau[j];
+    if (t == (R)0) continue;
     const int m = n - j - 1;
-    double2 s = make_double2(0.0, 0.0);
-    const double2* u = U + (size_t)j * sj;
+    cplx<R> s = mk<R>(0, 0);
+    const cplx<R>* u = U + (size_t)j * sj;
     for (int i = lane; i < m; i += 32) s = cadd(s, cmul(cconj(u[i * si]), vc[(size_t)(j + 1 + i) * cpb + wc]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -477,7 +501,7 @@ __global__ void __launch_bounds__(256) k_backtransform(int n, const double2* __r
     }
     s = cscale(s, t);
     for (int i = lane; i < m; i += 32) {
-      double2& v = vc[(size_t)(j + 1 + i) * cpb + wc];
+      cplx<R>& v = vc[(size_t)(j + 1 + i) * cpb + wc];
       v = csub(v, cmul(u[i * si], s));
     }
     __syncwarp();
@@ -536,15 +560,59 @@ static int tridiag_cluster_shape(Ctx* c, int n, int* cls, int* thr, size_t* smem
   return PARO_OK;
 }
 
+// Inverse iteration for the n eigenvectors of the tridiagonal (d, e) at the ascending eigenvalues w
+// into Z (column j = vector j); info set if a vector vanished.
+template <typename R>
+int invit(Ctx* c, int n, const R* d, const R* e, const R* w, R* Z, int* info) {
+  const bool f64 = sizeof(R) == 8;
+  R* lam = static_cast<R*>(ws_get(c, f64 ? "invit_lam64" : "invit_lam32", (size_t)(n + 1) * sizeof(R)));
+  int* cst = static_cast<int*>(ws_get(c, "invit_cst", (size_t)(n + 2) * sizeof(int)));
+  if (!lam || !cst) return PARO_ERR_CUDA;
+  int* nclu = cst + n + 1;
+  R* tiny = lam + n;
+  k_invit_prep<R><<<1, 32, 0, c->stream>>>(n, d, e, w, lam, cst, nclu, tiny);
+  PARO_LAUNCH(c, "k_invit_prep");
+  const size_t per = (size_t)n * (5 * sizeof(R) + 1);
+  int E = (int)std::min<size_t>(32, (200 * 1024) / per);
+  if (E < 1) return fail(c, PARO_ERR_ARG, "inverse iteration: n too large");
+  const size_t sm = per * E;
+  PARO_CU(c, cudaFuncSetAttribute(k_invit_solve<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  for (int it = 0; it < 3; ++it) {
+    k_invit_solve<R><<<(n + E - 1) / E, E, sm, c->stream>>>(n, d, e, lam, tiny, Z, it == 0 ? 1 : 0);
+    PARO_LAUNCH(c, "k_invit_solve");
+    k_invit_mgs<R><<<(n + 3) / 4, 128, 0, c->stream>>>(n, Z, cst, nclu, info);
+    PARO_LAUNCH(c, "k_invit_mgs");
+  }
+  return PARO_OK;
+}
+template int invit<double>(Ctx*, int, const double*, const double*, const double*, double*, int*);
+template int invit<float>(Ctx*, int, const float*, const float*, const float*, float*, int*);
+
+// FP32 multisection, inverse iteration and back-transformation of the mixed-precision solver
+// (k_eigh_mixed.cu): w ascending eigenvalues of (d, e), V[:, j] the eigenvector of the Hermitian matrix
+// whose reflectors are the rows of U.
+int eigh_fp32_pieces(Ctx* c, int n, const float* d, const float* e, float* w, const float2* U, const float* tau,
+                     const float2* ph, float* Z, float2* V, int* info) {
+  k_bisect<float><<<(n + 3) / 4, 128, (size_t)2 * n * sizeof(float), c->stream>>>(n, d, e, w);
+  PARO_LAUNCH(c, "k_bisect");
+  int st = invit<float>(c, n, d, e, w, Z, info);
+  if (st) return st;
+  const int cpb = 2;
+  const size_t sm4 = (size_t)n * cpb * sizeof(float2);
+  PARO_CU(c, cudaFuncSetAttribute(k_backtransform<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4));
+  k_backtransform<float><<<(n + cpb - 1) / cpb, 32 * cpb, sm4, c->stream>>>(n, U, (size_t)n, 1, tau, ph, Z, V);
+  PARO_LAUNCH(c, "k_backtransform");
+  return PARO_OK;
+}
+
 int eigh(Ctx* c, int n, const double2* a, double* w, double2* v) {
   if (n < 1 || n > 1024) return fail(c, PARO_ERR_ARG, "eigh: n must be in [1, 1024]");
   double2* A = static_cast<double2*>(ws_get(c, "eigh_A", (size_t)n * n * sizeof(double2)));
   double* Z = static_cast<double*>(ws_get(c, "eigh_Z", (size_t)n * n * sizeof(double)));
   double* dt = static_cast<double*>(ws_get(c, "eigh_dt", (size_t)n * 4 * sizeof(double)));
   double2* cw = static_cast<double2*>(ws_get(c, "eigh_cw", (size_t)n * 4 * sizeof(double2)));
-  double* lu = static_cast<double*>(ws_get(c, "eigh_lu", (size_t)5 * n * n * sizeof(double)));
   int* flags = static_cast<int*>(ws_get(c, "eigh_flags", 16 * sizeof(int)));
-  if (!A || !Z || !dt || !cw || !lu || !flags) return PARO_ERR_CUDA;
+  if (!A || !Z || !dt || !cw || !flags) return PARO_ERR_CUDA;
   double *d = dt, *e = dt + n, *tau = dt + 2 * n, *sc = dt + 3 * n;
   double2 *ph = cw, *ecx = cw + n, *ub = cw + 2 * n, *pb = cw + 3 * n;
   unsigned* bar = reinterpret_cast<unsigned*>(flags);
@@ -590,20 +658,17 @@ int eigh(Ctx* c, int n, const double2* a, double* w, double2* v) {
     prof_end(c, "k_tridiag", ev);
   }
   ev = prof_begin(c);
-  k_bisect<<<(n + 3) / 4, 128, (size_t)2 * n * sizeof(double), c->stream>>>(n, d, e, w);
+  k_bisect<double><<<(n + 3) / 4, 128, (size_t)2 * n * sizeof(double), c->stream>>>(n, d, e, w);
   PARO_LAUNCH(c, "k_bisect");
   prof_end(c, "k_bisect", ev);
   ev = prof_begin(c);
-  const size_t sm3 = (size_t)n * sizeof(double) + (size_t)(n + 1) * sizeof(int);
-  const int t3 = ((n + 31) / 32) * 32 < 256 ? 256 : ((n + 31) / 32) * 32;
-  k_invit<<<1, t3, sm3, c->stream>>>(n, d, e, w, Z, lu, info);
-  PARO_LAUNCH(c, "k_invit");
+  if ((st = invit<double>(c, n, d, e, w, Z, info))) return st;
   prof_end(c, "k_invit", ev);
   ev = prof_begin(c);
   const int cpb = 2;
   const size_t sm4 = (size_t)n * cpb * sizeof(double2);
-  PARO_CU(c, cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4));
-  k_backtransform<<<(n + cpb - 1) / cpb, 32 * cpb, sm4, c->stream>>>(n, Uh, usj, usi, tau, ph, Z, v);
+  PARO_CU(c, cudaFuncSetAttribute(k_backtransform<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4));
+  k_backtransform<double><<<(n + cpb - 1) / cpb, 32 * cpb, sm4, c->stream>>>(n, Uh, usj, usi, tau, ph, Z, v);
   PARO_LAUNCH(c, "k_backtransform");
   prof_end(c, "k_backtransform", ev);
   int h[2] = {0, 0};

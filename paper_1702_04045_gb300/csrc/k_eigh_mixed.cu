@@ -1,0 +1,405 @@
+// Hermitian eigensolver of the mixed-precision Rayleigh-Ritz step (Algorithm 1 step 4 on the mixed path):
+// an FP32 solve refined in FP64.
+//
+//  1. FP32: Householder tridiagonalisation in one CTA with the whole matrix in shared memory
+//     (k_tridiag_cta), multisection, inverse iteration and back-transformation (the FP64 solver's kernels
+//     instantiated for float). GB300 runs FP32 at 64x its FP64 rate, and the one-CTA reduction needs no
+//     cluster or grid barriers.
+//  2. FP64 refinement of the eigenvector matrix X by the iteration of Ogita and Aishima (Japan J. Indust.
+//     Appl. Math. 35, 2018, "Iterative refinement for symmetric eigenvalue decomposition"), written for
+//     the Hermitian case: R = I - X^H X, S = X^H A X, lambda_i = S_ii / (1 - R_ii),
+//     delta = 2 (||S - diag(lambda)|| + ||A|| ||R||); E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i)
+//     when lambda_i and lambda_j lie in different clusters (runs of eigenvalues closer than
+//     max(delta, 1e-3 ||A||): no closer than the clusters of the FP32 inverse iteration, inside which the
+//     vectors are only orthogonalised), E_ij = R_ij / 2 inside a cluster; X <- X + X E. Each step squares
+//     the error of X across clusters.
+//  3. Clusters of close eigenvalues are only orthonormalised by step 2; a Rayleigh-Ritz inside each
+//     cluster (FP64 Jacobi on X_c^H A X_c) resolves them.
+// The products are FP64 n x n complex GEMMs spread over many CTAs (k_zgemm16).
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+
+#include "jacobi_small.cuh"
+#include "paro_ctx.h"
+
+namespace paro {
+
+// pieces of the FP64 solver instantiated for float (k_eigh.cu)
+template <typename R>
+int invit(Ctx* c, int n, const R* d, const R* e, const R* w, R* Z, int* info);
+int eigh_fp32_pieces(Ctx* c, int n, const float* d, const float* e, float* w, const float2* U, const float* tau,
+                     const float2* ph, float* Z, float2* V, int* info);
+
+static const int kMixMaxN = 160;  // largest n whose FP32 matrix fits one CTA's shared memory
+
+// ------------------------------------------------------------------------------------------------
+// Householder tridiagonalisation, one CTA, matrix (FP32) in shared memory. The same reflectors and outputs
+// as the FP64 kernels: u_j in U[j][0..m), tau, the complex off-diagonals ecx, d; then the phase diagonal D
+// (D_0 = 1, D_{j+1} = D_j conj(e_j)/|e_j|) and the real off-diagonals |e_j|. Input a: full Hermitian FP64.
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_tridiag_cta(int n, const double2* __restrict__ a, float2* __restrict__ U,
+                                                      float* __restrict__ d, float* __restrict__ e,
+                                                      float2* __restrict__ ph, float* __restrict__ tau,
+                                                      float2* __restrict__ ecx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ld = n + 1;
+  float2* A = reinterpret_cast<float2*>(smem_raw);  // n x ld
+  float2* u = A + (size_t)n * ld;
+  float2* w = u + n;
+  __shared__ double red[32];
+  __shared__ float s_t, s_K;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  for (int idx = tid; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, k = idx - i * n;
+    const double2 v = a[idx];
+    A[i * ld + k] = make_float2((float)v.x, (float)v.y);
+  }
+  __syncthreads();
+  for (int j = 0; j + 1 < n; ++j) {
+    const int m = n - j - 1;
+    double nrm2 = 0.0;
+    for (int i = tid; i < m; i += blockDim.x) {
+      const float2 x = A[(j + 1 + i) * ld + j];
+      u[i] = x;
+      nrm2 += (double)x.x * x.x + (double)x.y * x.y;
+    }
+    nrm2 = block_sum(nrm2, red);
+    if (tid == 0) {
+      const float2 x0 = u[0];
+      const float ax0 = hypotf(x0.x, x0.y);
+      const float nx = (float)sqrt(nrm2);
+      float2 alpha = x0;
+      float t = 0.f;
+      if (m > 1 && nx > 0.f && nrm2 - (double)ax0 * ax0 > 0.0) {
+        const float2 phs = ax0 > 0.f ? make_float2(x0.x / ax0, x0.y / ax0) : make_float2(1.f, 0.f);
+        alpha = make_float2(-phs.x * nx, -phs.y * nx);
+        u[0] = csub(x0, alpha);
+        t = (float)(1.0 / (nrm2 + (double)nx * ax0));
+      }
+      s_t = t;
+      tau[j] = t;
+      ecx[j] = alpha;
+      d[j] = A[j * ld + j].x;
+    }
+    __syncthreads();
+    for (int i = tid; i < m; i += blockDim.x) U[(size_t)j * n + i] = u[i];
+    const float t = s_t;
+    if (t == 0.f) continue;
+    for (int i = warp; i < m; i += nwarp) {  // p_i = t sum_k B_ik u_k
+      const float2* row = A + (j + 1 + i) * ld + (j + 1);
+      float2 acc = make_float2(0.f, 0.f);
+      for (int k = lane; k < m; k += 32) {
+        const float2 b = row[k], uk = u[k];
+        acc.x = fmaf(b.x, uk.x, fmaf(-b.y, uk.y, acc.x));
+        acc.y = fmaf(b.x, uk.y, fmaf(b.y, uk.x, acc.y));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      }
+      if (lane == 0) w[i] = make_float2(t * acc.x, t * acc.y);
+    }
+    __syncthreads();
+    double kre = 0.0;
+    for (int i = tid; i < m; i += blockDim.x) kre += (double)u[i].x * w[i].x + (double)u[i].y * w[i].y;
+    kre = block_sum(kre, red);
+    if (tid == 0) s_K = (float)(0.5 * t * kre);
+    __syncthreads();
+    const float K = s_K;
+    for (int i = tid; i < m; i += blockDim.x) w[i] = make_float2(w[i].x - K * u[i].x, w[i].y - K * u[i].y);
+    __syncthreads();
+    for (int idx = tid; idx < m * m; idx += blockDim.x) {  // B -= u w^H + w u^H
+      const int i = idx / m, k = idx - i * m;
+      float2& b = A[(j + 1 + i) * ld + (j + 1 + k)];
+      const float2 ui = u[i], wi = w[i], uk = u[k], wk = w[k];
+      b.x -= ui.x * wk.x + ui.y * wk.y + wi.x * uk.x + wi.y * uk.y;
+      b.y -= ui.y * wk.x - ui.x * wk.y + wi.y * uk.x - wi.x * uk.y;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    d[n - 1] = A[(n - 1) * ld + (n - 1)].x;
+    ph[0] = make_float2(1.f, 0.f);
+    for (int j = 0; j + 1 < n; ++j) {
+      const float v = hypotf(ecx[j].x, ecx[j].y);
+      e[j] = v;
+      ph[j + 1] = v > 0.f ? cmul(ph[j], make_float2(ecx[j].x / v, -ecx[j].y / v)) : ph[j];
+    }
+    e[n - 1] = 0.f;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// FP64 n x n complex products: part[z] = op(A) B over the K slice z (op = identity, or conjugate transpose
+// when ah); 16 x 16 outputs per CTA. k_zreduce sums the slices in order: C = sum (+ C when add).
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_zgemm16(int n, const double2* __restrict__ A, int ah,
+                                                 const double2* __restrict__ B, double2* __restrict__ part,
+                                                 int kslice) {
+  __shared__ double2 As[16][17], Bs[16][17];
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  const int i0 = blockIdx.y * 16, j0 = blockIdx.x * 16;
+  const int k0 = blockIdx.z * kslice, k1 = min(n, k0 + kslice);
+  double2 acc = make_double2(0.0, 0.0);
+  for (int kk = k0; kk < k1; kk += 16) {
+    const int ia = i0 + ty, ka = kk + tx;
+    double2 av = make_double2(0.0, 0.0);
+    if (ia < n && ka < k1) av = ah ? cconj(A[(size_t)ka * n + ia]) : A[(size_t)ia * n + ka];
+    As[ty][tx] = av;
+    const int kb = kk + ty, jb = j0 + tx;
+    Bs[ty][tx] = (kb < k1 && jb < n) ? B[(size_t)kb * n + jb] : make_double2(0.0, 0.0);
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < 16; ++k) {
+      const double2 x = As[ty][k], y = Bs[k][tx];
+      acc.x = fma(x.x, y.x, fma(-x.y, y.y, acc.x));
+      acc.y = fma(x.x, y.y, fma(x.y, y.x, acc.y));
+    }
+    __syncthreads();
+  }
+  const int i = i0 + ty, jj = j0 + tx;
+  if (i < n && jj < n) part[(size_t)blockIdx.z * n * n + (size_t)i * n + jj] = acc;
+}
+
+__global__ void k_zreduce(int n, int nz, const double2* __restrict__ part, double2* __restrict__ C, int add) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  double2 s = add ? C[idx] : make_double2(0.0, 0.0);
+  for (int z = 0; z < nz; ++z) s = cadd(s, part[(size_t)z * n * n + idx]);
+  C[idx] = s;
+}
+
+// ------------------------------------------------------------------------------------------------
+// One refinement step's small quantities (one CTA): from G = X^H X and S = X^H A X form lambda, delta,
+// the clusters (cl: cluster index per column; cst: first column of each cluster; ncl) and E.
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_refine_e(int n, const double2* __restrict__ G, const double2* __restrict__ S,
+                                                   double* __restrict__ lam, int* __restrict__ cl,
+                                                   int* __restrict__ cst, int* __restrict__ ncl,
+                                                   double2* __restrict__ E) {
+  __shared__ double red[32];
+  __shared__ double s_delta;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < n; i += blockDim.x) lam[i] = S[(size_t)i * n + i].x / G[(size_t)i * n + i].x;
+  __syncthreads();
+  double ns = 0.0, nr = 0.0, na = 0.0;
+  for (int idx = tid; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx - i * n;
+    double2 sv = S[idx];
+    if (i == j) sv.x -= lam[i];
+    ns += sv.x * sv.x + sv.y * sv.y;
+    double2 rv = cscale(G[idx], -1.0);
+    if (i == j) rv.x += 1.0;
+    nr += rv.x * rv.x + rv.y * rv.y;
+  }
+  for (int i = tid; i < n; i += blockDim.x) na = fmax(na, fabs(lam[i]));
+  ns = block_sum(ns, red);
+  __syncthreads();
+  nr = block_sum(nr, red);
+  __syncthreads();
+  // max of na over the CTA
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) na = fmax(na, __shfl_xor_sync(0xffffffffu, na, o));
+  if ((tid & 31) == 0) red[tid >> 5] = na;
+  __syncthreads();
+  if (tid == 0) {
+    double mx = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+    // clusters: at least the FP32 solver's own (eigenvalues closer than 1e-3 ||A||, whose vectors inverse
+    // iteration only orthogonalised), so that every pair corrected below is already accurate to first order
+    s_delta = fmax(2.0 * (sqrt(ns) + mx * sqrt(nr)), 1e-3 * mx);
+    int c = 0;
+    cst[0] = 0;
+    cl[0] = 0;
+    for (int i = 1; i < n; ++i) {
+      if (lam[i] - lam[i - 1] > s_delta) cst[++c] = i;
+      cl[i] = c;
+    }
+    cst[c + 1] = n;
+    *ncl = c + 1;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx - i * n;
+    double2 rv = cscale(G[idx], -1.0);
+    if (i == j) rv.x += 1.0;
+    if (cl[i] == cl[j]) {
+      E[idx] = cscale(rv, 0.5);
+    } else {
+      const double2 num = cadd(S[idx], cscale(rv, lam[j]));
+      E[idx] = cscale(num, 1.0 / (lam[j] - lam[i]));
+    }
+  }
+}
+
+// Rayleigh-Ritz inside each cluster of two or more columns: S_c = (X^H A X)_cc (k x k, k <= 64)
+// diagonalised by Jacobi, X_c <- X_c Q, lam_c = its eigenvalues; one CTA per cluster. Singleton
+// clusters take lam_i = S_ii. info |= 4 for a cluster larger than 64, |= 8 if Jacobi did not converge.
+__global__ void __launch_bounds__(256) k_cluster_rr(int n, const double2* __restrict__ S, const int* __restrict__ cst,
+                                                    const int* __restrict__ ncl, double2* __restrict__ X,
+                                                    double* __restrict__ lam, int* __restrict__ info) {
+  constexpr int KM = 64, LD = KM + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* Am = reinterpret_cast<double2*>(smem_raw);
+  double2* Vm = Am + KM * LD;
+  __shared__ int pos[KM];
+  __shared__ double rc[KM / 2], rs[KM / 2];
+  __shared__ double2 rph[KM / 2];
+  __shared__ int rp[KM / 2], rq[KM / 2];
+  __shared__ double red[32];
+  __shared__ double s_off, s_tot;
+  const int c = blockIdx.x;
+  if (c >= *ncl) return;
+  const int c0 = cst[c], k = cst[c + 1] - c0;
+  if (k == 1) {
+    if (threadIdx.x == 0) lam[c0] = S[(size_t)c0 * n + c0].x;
+    return;
+  }
+  if (k > KM) {
+    if (threadIdx.x == 0) atomicOr(info, 4);
+    return;
+  }
+  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+    const int i = idx / k, j = idx - i * k;
+    Am[i * LD + j] = S[(size_t)(c0 + i) * n + (c0 + j)];
+    Vm[i * LD + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  JacobiScratch sc{pos, rc, rs, rph, rp, rq, red, &s_off, &s_tot};
+  const int ok = jacobi_herm(k, LD, Am, Vm, sc);
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x) lam[c0 + j] = Am[j * LD + j].x;
+  // X_c <- X_c Q: each thread one row at a time (k <= 64 values in registers)
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double2 row[KM];
+    for (int l = 0; l < k; ++l) row[l] = X[(size_t)i * n + c0 + l];
+    for (int j = 0; j < k; ++j) {
+      double2 s = make_double2(0.0, 0.0);
+      for (int l = 0; l < k; ++l) s = cadd(s, cmul(row[l], Vm[l * LD + j]));
+      X[(size_t)i * n + c0 + j] = s;
+    }
+  }
+  if (threadIdx.x == 0 && !ok) atomicOr(info, 8);
+}
+
+// ascending order (ties by index): w[j] = lam[perm j], V[:, j] = X[:, perm j]
+__global__ void k_eig_sort(int n, const double* __restrict__ lam, const double2* __restrict__ X, double* __restrict__ w,
+                           double2* __restrict__ V, int* __restrict__ perm) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid < n) {
+    const double a = lam[tid];
+    int r = 0;
+    for (int j = 0; j < n; ++j) {
+      const double b = lam[j];
+      r += (b < a) || (b == a && j < tid);
+    }
+    perm[r] = tid;
+  }
+}
+
+__global__ void k_eig_permute(int n, const double* __restrict__ lam, const double2* __restrict__ X,
+                              const int* __restrict__ perm, double* __restrict__ w, double2* __restrict__ V) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int i = idx / n, j = idx - i * n;
+  V[idx] = X[(size_t)i * n + perm[j]];
+  if (i == 0) w[j] = lam[perm[j]];
+}
+
+__global__ void k_f2d(int n, const float2* __restrict__ a, double2* __restrict__ b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = make_double2((double)a[i].x, (double)a[i].y);
+}
+
+__global__ void k_herm_full_mixed(int n, const double2* __restrict__ Ain, double2* __restrict__ A) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int i = idx / n, j = idx - i * n;
+  A[idx] = (i >= j) ? Ain[idx] : cconj(Ain[(size_t)j * n + i]);
+}
+
+// C = op(A) B (+ C), n x n FP64
+static int zgemm(Ctx* c, int n, const double2* A, bool ah, const double2* B, double2* C, bool add, double2* part) {
+  const int nz = std::max(1, std::min(8, (n + 47) / 48));
+  const int kslice = ((n + nz - 1) / nz + 15) / 16 * 16;
+  const int z = (n + kslice - 1) / kslice;
+  const int t = (n + 15) / 16;
+  k_zgemm16<<<dim3(t, t, z), 256, 0, c->stream>>>(n, A, ah ? 1 : 0, B, part, kslice);
+  PARO_LAUNCH(c, "k_zgemm16");
+  k_zreduce<<<(n * n + 255) / 256, 256, 0, c->stream>>>(n, z, part, C, add ? 1 : 0);
+  PARO_LAUNCH(c, "k_zreduce");
+  return PARO_OK;
+}
+
+int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v) {
+  if (n < 2 || n > kMixMaxN) return eigh(c, n, a, w, v);
+  const size_t nn = (size_t)n * n;
+  double2* Af = static_cast<double2*>(ws_get(c, "em_A", nn * sizeof(double2)));
+  double2* X = static_cast<double2*>(ws_get(c, "em_X", nn * sizeof(double2)));
+  double2* T1 = static_cast<double2*>(ws_get(c, "em_T1", nn * sizeof(double2)));
+  double2* G = static_cast<double2*>(ws_get(c, "em_G", nn * sizeof(double2)));
+  double2* S = static_cast<double2*>(ws_get(c, "em_S", nn * sizeof(double2)));
+  double2* part = static_cast<double2*>(ws_get(c, "em_part", 8 * nn * sizeof(double2)));
+  float2* U32 = static_cast<float2*>(ws_get(c, "em_U32", nn * sizeof(float2)));
+  float2* V32 = static_cast<float2*>(ws_get(c, "em_V32", nn * sizeof(float2)));
+  float* Z32 = static_cast<float*>(ws_get(c, "em_Z32", nn * sizeof(float)));
+  float* r32 = static_cast<float*>(ws_get(c, "em_r32", (size_t)6 * n * sizeof(float)));
+  double* lam = static_cast<double*>(ws_get(c, "em_lam", (size_t)n * sizeof(double)));
+  int* ib = static_cast<int*>(ws_get(c, "em_int", (size_t)(3 * n + 8) * sizeof(int)));
+  if (!Af || !X || !T1 || !G || !S || !part || !U32 || !V32 || !Z32 || !r32 || !lam || !ib) return PARO_ERR_CUDA;
+  float *d32 = r32, *e32 = r32 + n, *tau32 = r32 + 2 * n, *w32 = r32 + 3 * n;
+  float2* c32 = reinterpret_cast<float2*>(r32 + 4 * n);  // ph (n) then ecx: 2n floats each
+  float2* ph32 = c32;
+  int *cl = ib, *cst = ib + n, *perm = ib + 2 * n + 1, *flags = ib + 3 * n + 2;
+  int* ncl = flags + 1;
+  int* info = flags + 2;
+  float2* ecx32 = static_cast<float2*>(ws_get(c, "em_ecx32", (size_t)n * sizeof(float2)));
+  if (!ecx32) return PARO_ERR_CUDA;
+  PARO_CU(c, cudaMemsetAsync(flags, 0, 6 * sizeof(int), c->stream));
+  k_herm_full_mixed<<<(int)((nn + 255) / 256), 256, 0, c->stream>>>(n, a, Af);
+  PARO_LAUNCH(c, "k_herm_full");
+  // 1. FP32 solve
+  cudaEvent_t ev = prof_begin(c);
+  const size_t sm1 = ((size_t)n * (n + 1) + 2 * (size_t)n) * sizeof(float2);
+  PARO_CU(c, cudaFuncSetAttribute(k_tridiag_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+  k_tridiag_cta<<<1, 1024, sm1, c->stream>>>(n, Af, U32, d32, e32, ph32, tau32, ecx32);
+  PARO_LAUNCH(c, "k_tridiag_cta");
+  prof_end(c, "k_tridiag_cta", ev);
+  ev = prof_begin(c);
+  int st = eigh_fp32_pieces(c, n, d32, e32, w32, U32, tau32, ph32, Z32, V32, info);
+  if (st) return st;
+  prof_end(c, "eigh_fp32_rest", ev);
+  // 2. FP64 refinement (two steps), 3. Rayleigh-Ritz in the clusters
+  ev = prof_begin(c);
+  k_f2d<<<(int)((nn + 255) / 256), 256, 0, c->stream>>>((int)nn, V32, X);
+  PARO_LAUNCH(c, "k_f2d");
+  for (int it = 0; it < 2; ++it) {
+    if ((st = zgemm(c, n, X, true, X, G, false, part))) return st;    // G = X^H X
+    if ((st = zgemm(c, n, Af, false, X, T1, false, part))) return st;  // T1 = A X
+    if ((st = zgemm(c, n, X, true, T1, S, false, part))) return st;    // S = X^H A X
+    k_refine_e<<<1, 1024, 0, c->stream>>>(n, G, S, lam, cl, cst, ncl, T1);  // T1 = E
+    PARO_LAUNCH(c, "k_refine_e");
+    if ((st = zgemm(c, n, X, false, T1, X, true, part))) return st;    // X += X E
+  }
+  if ((st = zgemm(c, n, Af, false, X, T1, false, part))) return st;    // T1 = A X
+  if ((st = zgemm(c, n, X, true, T1, S, false, part))) return st;      // S = X^H A X
+  const size_t sm3 = (size_t)2 * 64 * 65 * sizeof(double2);
+  PARO_CU(c, cudaFuncSetAttribute(k_cluster_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+  k_cluster_rr<<<n, 256, sm3, c->stream>>>(n, S, cst, ncl, X, lam, info);
+  PARO_LAUNCH(c, "k_cluster_rr");
+  k_eig_sort<<<(n + 127) / 128, 128, 0, c->stream>>>(n, lam, X, w, v, perm);
+  PARO_LAUNCH(c, "k_eig_sort");
+  k_eig_permute<<<(int)((nn + 255) / 256), 256, 0, c->stream>>>(n, lam, X, perm, w, v);
+  PARO_LAUNCH(c, "k_eig_permute");
+  prof_end(c, "eigh_refine", ev);
+  int h = 0;
+  PARO_CU(c, cudaMemcpyAsync(&h, info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  PARO_CU(c, cudaStreamSynchronize(c->stream));
+  if (h & 1) return fail(c, PARO_ERR_NOT_CONVERGED, "eigh (mixed): inverse iteration produced a zero vector");
+  if (h & (4 | 8)) return eigh(c, n, a, w, v);  // a cluster the refinement cannot resolve: FP64 solver
+  return PARO_OK;
+}
+
+}  // namespace paro

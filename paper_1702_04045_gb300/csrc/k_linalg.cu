@@ -203,7 +203,7 @@ int gemm_cn(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, const cplx<
             int ldc, bool herm, bool carry) {
   if (M <= 0 || N <= 0) return PARO_OK;
   if constexpr (sizeof(TA) == 4 && sizeof(TB) == 4 && sizeof(ACC) == 4) {
-    if (!herm && !carry && K > 0 && tc_enabled()) {
+    if (!herm && !carry && K > 0 && c->tc_scope && tc_enabled()) {
       int nz = 1, kslice = 16;
       gemm_cn_tc_plan(M, N, K, &nz, &kslice);
       double2* part = static_cast<double2*>(ws_get(c, "gemm_parts", (size_t)nz * M * N * sizeof(double2)));
@@ -327,7 +327,7 @@ int gemm_wx(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, con
             int ldx, cplx<TY>* Y, int ldy, double beta) {
   if (M <= 0 || N <= 0) return PARO_OK;
   if constexpr (sizeof(TX) == 4 && sizeof(TY) == 4) {
-    if (tc_enabled()) {
+    if (c->tc_scope && tc_enabled()) {
       int* err = tc_err_flag(c);
       if (!err) return PARO_ERR_CUDA;
       cudaEvent_t ev = prof_begin(c);

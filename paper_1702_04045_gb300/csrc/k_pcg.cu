@@ -193,6 +193,7 @@ template <typename T>
 int pcg_run(Ctx* c, int ik, int nb, const cplx<T>* rhs, cplx<T>* x, bool x0_zero, double rel_tol, int max_it,
             int* iters) {
   ProfTag tag(c, "pcg");
+  TcScope tcs(c);  // the inner solves tolerate the 3xTF32 products
   const Basis& B = c->bases[ik];
   const int npw = B.npw;
   const int nchunk = (npw + kChunk - 1) / kChunk;

@@ -21,13 +21,12 @@
 namespace paro {
 
 static const int kTcM = 128;       // rows of A per CTA = TMEM lanes
-static const int kTcKc = 16;       // complex K elements per stage (32 reals = 4 MMAs of 8)
-static const int kTcCh = kTcKc * 2 * 4 / 16;  // 16-byte chunks per row per stage (8)
 static const int kTcThreads = 256;
 static const uint32_t kTcPolls = 1u << 24;
 
-__device__ __forceinline__ uint32_t tc_off(int row, int chunk) {
-  return (uint32_t)(((row >> 3) * kTcCh + chunk) * 128 + (row & 7) * 16);
+// byte offset of (row, 16-byte chunk) in a no-swizzle K-major tile with ch chunks per row
+__device__ __forceinline__ uint32_t tc_off(int row, int chunk, int ch) {
+  return (uint32_t)(((row >> 3) * ch + chunk) * 128 + (row & 7) * 16);
 }
 
 // split (v0, v1) into hi and lo TF32 quadruples (re0, im0, re1, im1)
@@ -37,21 +36,32 @@ __device__ __forceinline__ void tc_split(float2 v0, float2 v1, float4& h, float4
   l.z = tc::tf32_round(v1.x - h.z); l.w = tc::tf32_round(v1.y - h.w);
 }
 
+// Pipeline of the tensor-core kernels: two shared-memory buffers, one mbarrier each. Stage s is staged into
+// buffer s & 1 while the MMAs of stage s - 1 run on the other; before a buffer is overwritten, the MMAs of
+// stage s - 2 (its previous use) must have completed. Every wait is bounded; on a time-out the kernel
+// waits once more for the MMAs in flight, reports, and still releases tensor memory.
+struct TcPipe {
+  uint64_t* bar;      // [2]
+  uint32_t uses[2];   // completed uses waited for, per buffer
+  int ok;
+  __device__ __forceinline__ bool wait_buffer(int b) {  // all threads; uniform result
+    const int done = tc::mbar_wait(&bar[b], uses[b] & 1u, kTcPolls) ? 1 : 0;
+    ok = __syncthreads_and(done && ok);
+    if (ok) ++uses[b];
+    return ok;
+  }
+};
+
 // part[z][m][n] = sum over K slice z of conj(A[m][k]) B[n][k] (complex double). NT: N tile (multiple of
-// 16, at most 256). err: set when an mbarrier wait gives up.
-__global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int K, int kslice, int NT,
+// 16, at most 256); KC complex K elements per stage (16 or 8). err: set when an mbarrier wait gives up.
+__global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int K, int kslice, int NT, int KC,
                                                               const float2* __restrict__ A, int lda,
                                                               const float2* __restrict__ B, int ldb,
                                                               double2* __restrict__ part, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const int A_BYTES = kTcM * kTcCh * 16, B_BYTES = NT * kTcCh * 16;
-  unsigned char* sAh = smem;
-  unsigned char* sAl = smem + A_BYTES;
-  unsigned char* sAph = smem + 2 * A_BYTES;
-  unsigned char* sApl = smem + 3 * A_BYTES;
-  unsigned char* sBh = smem + 4 * A_BYTES;
-  unsigned char* sBl = sBh + B_BYTES;
-  __shared__ uint64_t mbar;
+  const int ch = KC / 2;  // 16-byte chunks per row per stage
+  const int A_BYTES = kTcM * ch * 16, B_BYTES = NT * ch * 16, STAGE = 4 * A_BYTES + 2 * B_BYTES;
+  __shared__ uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * kTcM, n0 = blockIdx.y * NT;
@@ -62,7 +72,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int 
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    tc::mbar_init(&mbar, 1);
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
     tc::fence_mbar_init();
   }
   tc::tc_fence_before();
@@ -70,14 +81,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int 
   tc::tc_fence_after();
   const uint32_t dR = tmem_base, dI = tmem_base + ncols / 2;
   const uint32_t idesc = tc::idesc_tf32(128, (uint32_t)NT);
-  const uint32_t aH = tc::smem_addr(sAh), aL = tc::smem_addr(sAl), apH = tc::smem_addr(sAph),
-                 apL = tc::smem_addr(sApl), bH = tc::smem_addr(sBh), bL = tc::smem_addr(sBl);
-  uint32_t phase = 0;
-  int ok = 1, nst = 0;
-  for (int kk = k0; kk < k1; kk += kTcKc, ++nst) {
-    for (int i = tid; i < kTcM * kTcCh; i += kTcThreads) {
-      const int r = i / kTcCh, ch = i - r * kTcCh;
-      const int gm = m0 + r, g0 = kk + 2 * ch;
+  TcPipe pipe{mbar, {0u, 0u}, 1};
+  int nst = 0, issued[2] = {0, 0};
+  for (int kk = k0; kk < k1; kk += KC, ++nst) {
+    const int b = nst & 1;
+    if (issued[b] && !pipe.wait_buffer(b)) break;  // the MMAs of stage nst - 2 read this buffer
+    issued[b] = 0;
+    unsigned char* sAh = smem + b * STAGE;
+    unsigned char* sAl = sAh + A_BYTES;
+    unsigned char* sAph = sAl + A_BYTES;
+    unsigned char* sApl = sAph + A_BYTES;
+    unsigned char* sBh = sApl + A_BYTES;
+    unsigned char* sBl = sBh + B_BYTES;
+    for (int i = tid; i < kTcM * ch; i += kTcThreads) {
+      const int r = i / ch, c = i - r * ch;
+      const int gm = m0 + r, g0 = kk + 2 * c;
       float2 v0 = make_float2(0.f, 0.f), v1 = v0;
       if (gm < M) {
         const float2* row = A + (size_t)gm * lda;
@@ -86,15 +104,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int 
       }
       float4 h, l;
       tc_split(v0, v1, h, l);
-      const uint32_t o = tc_off(r, ch);
+      const uint32_t o = tc_off(r, c, ch);
       *reinterpret_cast<float4*>(sAh + o) = h;
       *reinterpret_cast<float4*>(sAl + o) = l;
       *reinterpret_cast<float4*>(sAph + o) = make_float4(-h.y, h.x, -h.w, h.z);
       *reinterpret_cast<float4*>(sApl + o) = make_float4(-l.y, l.x, -l.w, l.z);
     }
-    for (int i = tid; i < NT * kTcCh; i += kTcThreads) {
-      const int r = i / kTcCh, ch = i - r * kTcCh;
-      const int gn = n0 + r, g0 = kk + 2 * ch;
+    for (int i = tid; i < NT * ch; i += kTcThreads) {
+      const int r = i / ch, c = i - r * ch;
+      const int gn = n0 + r, g0 = kk + 2 * c;
       float2 v0 = make_float2(0.f, 0.f), v1 = v0;
       if (gn < N) {
         const float2* row = B + (size_t)gn * ldb;
@@ -103,7 +121,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int 
       }
       float4 h, l;
       tc_split(v0, v1, h, l);
-      const uint32_t o = tc_off(r, ch);
+      const uint32_t o = tc_off(r, c, ch);
       *reinterpret_cast<float4*>(sBh + o) = h;
       *reinterpret_cast<float4*>(sBl + o) = l;
     }
@@ -111,14 +129,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int 
     __syncthreads();
     if (tid == 0) {
       tc::tc_fence_after();
-#pragma unroll
-      for (int s = 0; s < kTcCh / 2; ++s) {
-        const uint32_t off = (uint32_t)s * 256u;  // two 16-byte chunks (8 TF32) per MMA
-        const uint32_t lbo = 128u, sbo = kTcCh * 128u;
+      const uint32_t aH = tc::smem_addr(sAh), aL = tc::smem_addr(sAl), apH = tc::smem_addr(sAph),
+                     apL = tc::smem_addr(sApl), bH = tc::smem_addr(sBh), bL = tc::smem_addr(sBl);
+      const uint32_t lbo = 128u, sbo = (uint32_t)ch * 128u;
+      for (int s2 = 0; s2 < ch / 2; ++s2) {
+        const uint32_t off = (uint32_t)s2 * 256u;  // two 16-byte chunks (8 TF32) per MMA
         const uint64_t dAh = tc::smem_desc(aH + off, lbo, sbo), dAl = tc::smem_desc(aL + off, lbo, sbo);
         const uint64_t dApH = tc::smem_desc(apH + off, lbo, sbo), dApL = tc::smem_desc(apL + off, lbo, sbo);
         const uint64_t dBh = tc::smem_desc(bH + off, lbo, sbo), dBl = tc::smem_desc(bL + off, lbo, sbo);
-        const uint32_t acc = (nst > 0 || s > 0) ? 1u : 0u;
+        const uint32_t acc = (nst > 0 || s2 > 0) ? 1u : 0u;
         tc::mma_tf32(dR, dAh, dBh, idesc, acc);
         tc::mma_tf32(dR, dAh, dBl, idesc, 1u);
         tc::mma_tf32(dR, dAl, dBh, idesc, 1u);
@@ -126,16 +145,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int 
         tc::mma_tf32(dI, dApH, dBl, idesc, 1u);
         tc::mma_tf32(dI, dApL, dBh, idesc, 1u);
       }
-      tc::mma_commit(&mbar);
+      tc::mma_commit(&mbar[b]);
     }
-    const int done = tc::mbar_wait(&mbar, phase, kTcPolls) ? 1 : 0;
-    ok = __syncthreads_and(done);
-    if (!ok) {  // give the MMAs in flight one more bounded wait before tensor memory is released
-      tc::mbar_wait(&mbar, phase, kTcPolls);
-      break;
-    }
-    phase ^= 1u;
+    issued[b] = 1;
   }
+  // drain: the last one or two stages
+  for (int b = 0; b < 2; ++b)
+    if (issued[b] && pipe.ok && !pipe.wait_buffer(b)) break;
+  if (!pipe.ok) {  // one more bounded wait for MMAs in flight before tensor memory is released
+    for (int b = 0; b < 2; ++b)
+      if (issued[b]) tc::mbar_wait(&mbar[b], pipe.uses[b] & 1u, kTcPolls);
+  }
+  const int ok = pipe.ok;
   tc::tc_fence_after();
   // accumulators: warp w reads TMEM lanes 32 (w % 4) ..; warps w and w + 4 split the columns
   const int lq = warp & 3, half = warp >> 2;
@@ -168,31 +189,63 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int 
 // W[k ldw + m], or W[m ldw + k] when wt; s: per-k scale or null). The MMA tile is D[n][m] = sum_k A[n][k]
 // B[m][k] with A = X^T (the long N_pw dimension on the 128 TMEM lanes, transposed while staged) and
 // B[m][k] = s_k W(k, m):  Re D = A' . (Br, -Bi)',  Im D = A' . (Bi, Br)'  on the interleaved rows.
-__global__ void __launch_bounds__(kTcThreads, 1) k_gemm_wx_tc(int M, int N, int K, int NT,
-                                                              const double2* __restrict__ W, int ldw, int wt,
-                                                              const double* __restrict__ sc,
+// The four B tiles of every stage are split once per call by k_wx_presplit (Wp) and copied with 16-byte
+// loads.
+__global__ void k_wx_presplit(int M, int K, int NT, int KC, const double2* __restrict__ W, int ldw, int wt,
+                              const double* __restrict__ sc, float4* __restrict__ Wp) {
+  const int ch = KC / 2, nstage = (K + KC - 1) / KC;
+  const int mt = blockIdx.y;  // M tile
+  const size_t tile = (size_t)NT * ch;  // float4 per variant per stage
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)nstage * tile;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int st = (int)(i / tile);
+    const int rem = (int)(i - (size_t)st * tile);
+    const int r = rem / ch, c = rem - r * ch;
+    const int gm = mt * NT + r, k0 = st * KC + 2 * c;
+    float2 b0 = make_float2(0.f, 0.f), b1 = b0;
+    if (gm < M) {
+      if (k0 < K) {
+        const double2 w = wt ? W[(size_t)gm * ldw + k0] : W[(size_t)k0 * ldw + gm];
+        const double f = sc ? sc[k0] : 1.0;
+        b0 = make_float2((float)(f * w.x), (float)(f * w.y));
+      }
+      if (k0 + 1 < K) {
+        const double2 w = wt ? W[(size_t)gm * ldw + k0 + 1] : W[(size_t)(k0 + 1) * ldw + gm];
+        const double f = sc ? sc[k0 + 1] : 1.0;
+        b1 = make_float2((float)(f * w.x), (float)(f * w.y));
+      }
+    }
+    float4 h, l;
+    tc_split(b0, b1, h, l);
+    const size_t base = (((size_t)mt * nstage + st) * 4) * tile;
+    const uint32_t o = tc_off(r, c, ch) / 16;  // float4 index within a variant tile
+    Wp[base + 0 * tile + o] = make_float4(h.x, -h.y, h.z, -h.w);  // Re, hi
+    Wp[base + 1 * tile + o] = make_float4(l.x, -l.y, l.z, -l.w);  // Re, lo
+    Wp[base + 2 * tile + o] = make_float4(h.y, h.x, h.w, h.z);    // Im, hi
+    Wp[base + 3 * tile + o] = make_float4(l.y, l.x, l.w, l.z);    // Im, lo
+  }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_gemm_wx_tc(int M, int N, int K, int NT, int KC,
+                                                              const float4* __restrict__ Wp,
                                                               const float2* __restrict__ X, int ldx,
                                                               float2* __restrict__ Y, int ldy, float beta,
                                                               int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const int A_BYTES = kTcM * kTcCh * 16, B_BYTES = NT * kTcCh * 16;
-  unsigned char* sAh = smem;
-  unsigned char* sAl = smem + A_BYTES;
-  unsigned char* sRh = smem + 2 * A_BYTES;  // B for Re: (Br, -Bi)
-  unsigned char* sRl = sRh + B_BYTES;
-  unsigned char* sIh = sRl + B_BYTES;       // B for Im: (Bi, Br)
-  unsigned char* sIl = sIh + B_BYTES;
-  __shared__ uint64_t mbar;
+  const int ch = KC / 2, nstage = (K + KC - 1) / KC;
+  const int A_BYTES = kTcM * ch * 16, B_BYTES = NT * ch * 16, STAGE = 2 * A_BYTES + 4 * B_BYTES;
+  __shared__ uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int n0 = blockIdx.x * kTcM, m0 = blockIdx.y * NT;
+  const int n0 = blockIdx.x * kTcM, mt = blockIdx.y, m0 = mt * NT;
   const uint32_t ncols = NT <= 128 ? 256u : 512u;
   if (warp == 0) {
     tc::tmem_alloc(&tmem_base, ncols);
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    tc::mbar_init(&mbar, 1);
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
     tc::fence_mbar_init();
   }
   tc::tc_fence_before();
@@ -200,14 +253,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_wx_tc(int M, int N, int 
   tc::tc_fence_after();
   const uint32_t dR = tmem_base, dI = tmem_base + ncols / 2;
   const uint32_t idesc = tc::idesc_tf32(128, (uint32_t)NT);
-  const uint32_t aH = tc::smem_addr(sAh), aL = tc::smem_addr(sAl), rH = tc::smem_addr(sRh), rL = tc::smem_addr(sRl),
-                 iH = tc::smem_addr(sIh), iL = tc::smem_addr(sIl);
-  uint32_t phase = 0;
-  int ok = 1, nst = 0;
-  for (int kk = 0; kk < K; kk += kTcKc, ++nst) {
-    for (int i = tid; i < kTcM * kTcCh; i += kTcThreads) {  // consecutive threads: consecutive n (rows)
-      const int r = i % kTcM, ch = i / kTcM;
-      const int gn = n0 + r, k0 = kk + 2 * ch;
+  const size_t tile4 = (size_t)NT * ch;  // float4 per B variant per stage
+  TcPipe pipe{mbar, {0u, 0u}, 1};
+  int issued[2] = {0, 0};
+  int nst = 0;
+  for (; nst < nstage; ++nst) {
+    const int b = nst & 1, kk = nst * KC;
+    if (issued[b] && !pipe.wait_buffer(b)) break;
+    issued[b] = 0;
+    unsigned char* sAh = smem + b * STAGE;
+    unsigned char* sAl = sAh + A_BYTES;
+    unsigned char* sB = sAl + A_BYTES;  // 4 variant tiles: Re hi, Re lo, Im hi, Im lo
+    for (int i = tid; i < kTcM * ch; i += kTcThreads) {  // consecutive threads: consecutive n (rows)
+      const int r = i % kTcM, c = i / kTcM;
+      const int gn = n0 + r, k0 = kk + 2 * c;
       float2 v0 = make_float2(0.f, 0.f), v1 = v0;
       if (gn < N) {
         if (k0 < K) v0 = X[(size_t)k0 * ldx + gn];
@@ -215,46 +274,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_wx_tc(int M, int N, int 
       }
       float4 h, l;
       tc_split(v0, v1, h, l);
-      const uint32_t o = tc_off(r, ch);
+      const uint32_t o = tc_off(r, c, ch);
       *reinterpret_cast<float4*>(sAh + o) = h;
       *reinterpret_cast<float4*>(sAl + o) = l;
     }
-    for (int i = tid; i < NT * kTcCh; i += kTcThreads) {
-      const int r = i / kTcCh, ch = i - r * kTcCh;
-      const int gm = m0 + r, k0 = kk + 2 * ch;
-      float2 b0 = make_float2(0.f, 0.f), b1 = b0;
-      if (gm < M) {
-        if (k0 < K) {
-          const double2 w = wt ? W[(size_t)gm * ldw + k0] : W[(size_t)k0 * ldw + gm];
-          const double f = sc ? sc[k0] : 1.0;
-          b0 = make_float2((float)(f * w.x), (float)(f * w.y));
-        }
-        if (k0 + 1 < K) {
-          const double2 w = wt ? W[(size_t)gm * ldw + k0 + 1] : W[(size_t)(k0 + 1) * ldw + gm];
-          const double f = sc ? sc[k0 + 1] : 1.0;
-          b1 = make_float2((float)(f * w.x), (float)(f * w.y));
-        }
-      }
-      float4 h, l;
-      tc_split(b0, b1, h, l);
-      const uint32_t o = tc_off(r, ch);
-      *reinterpret_cast<float4*>(sRh + o) = make_float4(h.x, -h.y, h.z, -h.w);
-      *reinterpret_cast<float4*>(sRl + o) = make_float4(l.x, -l.y, l.z, -l.w);
-      *reinterpret_cast<float4*>(sIh + o) = make_float4(h.y, h.x, h.w, h.z);
-      *reinterpret_cast<float4*>(sIl + o) = make_float4(l.y, l.x, l.w, l.z);
-    }
+    const float4* src = Wp + (((size_t)mt * nstage + nst) * 4) * tile4;
+    float4* dst = reinterpret_cast<float4*>(sB);
+    for (size_t i = tid; i < 4 * tile4; i += kTcThreads) dst[i] = src[i];
     tc::fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
       tc::tc_fence_after();
-#pragma unroll
-      for (int s = 0; s < kTcCh / 2; ++s) {
-        const uint32_t off = (uint32_t)s * 256u;
-        const uint32_t lbo = 128u, sbo = kTcCh * 128u;
+      const uint32_t aH = tc::smem_addr(sAh), aL = tc::smem_addr(sAl), bb = tc::smem_addr(sB);
+      const uint32_t rH = bb, rL = bb + B_BYTES, iH = bb + 2 * B_BYTES, iL = bb + 3 * B_BYTES;
+      const uint32_t lbo = 128u, sbo = (uint32_t)ch * 128u;
+      for (int s2 = 0; s2 < ch / 2; ++s2) {
+        const uint32_t off = (uint32_t)s2 * 256u;
         const uint64_t dAh = tc::smem_desc(aH + off, lbo, sbo), dAl = tc::smem_desc(aL + off, lbo, sbo);
         const uint64_t dRh = tc::smem_desc(rH + off, lbo, sbo), dRl = tc::smem_desc(rL + off, lbo, sbo);
         const uint64_t dIh = tc::smem_desc(iH + off, lbo, sbo), dIl = tc::smem_desc(iL + off, lbo, sbo);
-        const uint32_t acc = (nst > 0 || s > 0) ? 1u : 0u;
+        const uint32_t acc = (nst > 0 || s2 > 0) ? 1u : 0u;
         tc::mma_tf32(dR, dAh, dRh, idesc, acc);
         tc::mma_tf32(dR, dAh, dRl, idesc, 1u);
         tc::mma_tf32(dR, dAl, dRh, idesc, 1u);
@@ -262,16 +301,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_wx_tc(int M, int N, int 
         tc::mma_tf32(dI, dAh, dIl, idesc, 1u);
         tc::mma_tf32(dI, dAl, dIh, idesc, 1u);
       }
-      tc::mma_commit(&mbar);
+      tc::mma_commit(&mbar[b]);
     }
-    const int done = tc::mbar_wait(&mbar, phase, kTcPolls) ? 1 : 0;
-    ok = __syncthreads_and(done);
-    if (!ok) {
-      tc::mbar_wait(&mbar, phase, kTcPolls);
-      break;
-    }
-    phase ^= 1u;
+    issued[b] = 1;
   }
+  for (int b = 0; b < 2; ++b)
+    if (issued[b] && pipe.ok && !pipe.wait_buffer(b)) break;
+  if (!pipe.ok) {
+    for (int b = 0; b < 2; ++b)
+      if (issued[b]) tc::mbar_wait(&mbar[b], pipe.uses[b] & 1u, kTcPolls);
+  }
+  const int ok = pipe.ok;
   tc::tc_fence_after();
   const int lq = warp & 3, half = warp >> 2;
   const int gn = n0 + 32 * lq + lane;
@@ -306,37 +346,58 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_wx_tc(int M, int N, int 
   if (!ok && tid == 0) atomicExch(err, 1);
 }
 
-static size_t tc_smem_wx(int NT) { return (size_t)2 * kTcM * kTcCh * 16 + (size_t)4 * NT * kTcCh * 16; }
+// dynamic shared memory of the two-buffer pipelines; KC = 16 complex per stage where both buffers fit,
+// else 8
+static size_t cn_stage_bytes(int NT, int KC) { return (size_t)(4 * kTcM + 2 * NT) * (KC / 2) * 16; }
+static size_t wx_stage_bytes(int NT, int KC) { return (size_t)(2 * kTcM + 4 * NT) * (KC / 2) * 16; }
+static const size_t kTcSmemMax = 220 * 1024;
+static int cn_kc(int NT) { return 2 * cn_stage_bytes(NT, 16) <= kTcSmemMax ? 16 : 8; }
+static int wx_kc(int NT) { return 2 * wx_stage_bytes(NT, 16) <= kTcSmemMax ? 16 : 8; }
+
+static int set_smem_attr(Ctx* c, const void* k, int* dev_done) {
+  int dev = 0;
+  PARO_CU(c, cudaGetDevice(&dev));
+  if (*dev_done != dev) {
+    PARO_CU(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax));
+    *dev_done = dev;
+  }
+  return PARO_OK;
+}
 
 int gemm_wx_tc(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, const double* s, const float2* X,
                int ldx, float2* Y, int ldy, double beta, int* err) {
   const int mtiles = (M + 255) / 256;
   const int nt = ((M + mtiles - 1) / mtiles + 15) / 16 * 16;
+  const int kc = wx_kc(nt);
+  const int nstage = std::max(1, (K + kc - 1) / kc);
+  const size_t tile4 = (size_t)nt * (kc / 2);
+  float4* Wp = static_cast<float4*>(ws_get(c, "tc_wx_split", (size_t)mtiles * nstage * 4 * tile4 * sizeof(float4)));
+  if (!Wp) return PARO_ERR_CUDA;
   static int attr_dev = -1;
-  int dev = 0;
-  PARO_CU(c, cudaGetDevice(&dev));
-  if (attr_dev != dev) {
-    PARO_CU(c, cudaFuncSetAttribute(k_gemm_wx_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_wx(256)));
-    attr_dev = dev;
+  int st;
+  if ((st = set_smem_attr(c, (const void*)k_gemm_wx_tc, &attr_dev))) return st;
+  if (K > 0) {
+    k_wx_presplit<<<dim3(64, mtiles), 256, 0, c->stream>>>(M, K, nt, kc, W, ldw, wt ? 1 : 0, s, Wp);
+    PARO_LAUNCH(c, "k_wx_presplit");
   }
-  k_gemm_wx_tc<<<dim3((N + kTcM - 1) / kTcM, mtiles), kTcThreads, tc_smem_wx(nt), c->stream>>>(
-      M, N, K, nt, W, ldw, wt ? 1 : 0, s, X, ldx, Y, ldy, (float)beta, err);
+  k_gemm_wx_tc<<<dim3((N + kTcM - 1) / kTcM, mtiles), kTcThreads, 2 * wx_stage_bytes(nt, kc), c->stream>>>(
+      M, N, K, nt, kc, Wp, X, ldx, Y, ldy, (float)beta, err);
   PARO_LAUNCH(c, "k_gemm_wx_tc");
   return PARO_OK;
 }
-
-static size_t tc_smem(int NT) { return (size_t)4 * kTcM * kTcCh * 16 + (size_t)2 * NT * kTcCh * 16; }
 
 // K split of the tensor-core product: one CTA per SM, the slice count minimising waves x stages per
 // slice (at least 4 stages per slice), and no slice longer than 8192 complex terms, so the FP32 sum in
 // tensor memory stays short (slices are added in FP64).
 void gemm_cn_tc_plan(int M, int N, int K, int* nz_out, int* kslice_out) {
   const int ntiles = (N + 255) / 256;
+  const int nt = ((N + ntiles - 1) / ntiles + 15) / 16 * 16;
+  const int kc = cn_kc(nt);
   const int mtiles = (M + kTcM - 1) / kTcM;
   const int tiles = mtiles * ntiles;
-  const int steps = (K + kTcKc - 1) / kTcKc;
+  const int steps = (K + kc - 1) / kc;
   const int maxz = std::max(1, steps / 4);
-  const int minz = (steps + 8192 / kTcKc - 1) / (8192 / kTcKc);
+  const int minz = (steps + 8192 / kc - 1) / (8192 / kc);
   int best_nz = minz;
   long long best = -1;
   for (int z = std::min(minz, maxz); z <= std::min(std::max(maxz, minz), 1024); ++z) {
@@ -348,7 +409,7 @@ void gemm_cn_tc_plan(int M, int N, int K, int* nz_out, int* kslice_out) {
       best_nz = zz;
     }
   }
-  const int kslice = ((steps + best_nz - 1) / best_nz) * kTcKc;
+  const int kslice = ((steps + best_nz - 1) / best_nz) * kc;
   *kslice_out = kslice;
   *nz_out = std::max(1, (K + kslice - 1) / kslice);
 }
@@ -359,16 +420,13 @@ int gemm_cn_tc(Ctx* c, int M, int N, int K, const float2* A, int lda, const floa
                int kslice, int nz, int* err) {
   const int ntiles = (N + 255) / 256;
   const int nt = ((N + ntiles - 1) / ntiles + 15) / 16 * 16;
+  const int kc = cn_kc(nt);
   const int mtiles = (M + kTcM - 1) / kTcM;
   static int attr_dev = -1;
-  int dev = 0;
-  PARO_CU(c, cudaGetDevice(&dev));
-  if (attr_dev != dev) {
-    PARO_CU(c, cudaFuncSetAttribute(k_gemm_cn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(256)));
-    attr_dev = dev;
-  }
-  k_gemm_cn_tc<<<dim3(mtiles, ntiles, nz), kTcThreads, tc_smem(nt), c->stream>>>(M, N, K, kslice, nt, A, lda, B, ldb,
-                                                                                 part, err);
+  int st;
+  if ((st = set_smem_attr(c, (const void*)k_gemm_cn_tc, &attr_dev))) return st;
+  k_gemm_cn_tc<<<dim3(mtiles, ntiles, nz), kTcThreads, 2 * cn_stage_bytes(nt, kc), c->stream>>>(
+      M, N, K, kslice, nt, kc, A, lda, B, ldb, part, err);
   PARO_LAUNCH(c, "k_gemm_cn_tc");
   return PARO_OK;
 }

@@ -104,6 +104,9 @@ struct Ctx {
   // workspaces by name
   std::map<std::string, std::pair<void*, size_t>> ws;
   int* d_tc_err = nullptr;  // set by a tensor-core kernel whose mbarrier wait gave up
+  // FP32 products may run on the tensor cores (3xTF32): inside the inexact inner solves and the adjoint,
+  // not in the Rayleigh-Ritz step, the rotations or the energy, which fix the self-consistent result
+  bool tc_scope = false;
 };
 
 // Status helpers (api.cu)
@@ -126,6 +129,13 @@ void* ws_get(Ctx* c, const char* name, size_t bytes);  // nullptr on failure (er
 // CUDA events around a named kernel launch on the context's stream (no-ops unless profiling).
 cudaEvent_t prof_begin(Ctx* c);
 void prof_end(Ctx* c, const char* name, cudaEvent_t a);
+// Scoped permission for tensor-core FP32 products (Ctx::tc_scope).
+struct TcScope {
+  Ctx* c;
+  bool old;
+  explicit TcScope(Ctx* ctx) : c(ctx), old(ctx->tc_scope) { ctx->tc_scope = true; }
+  ~TcScope() { c->tc_scope = old; }
+};
 // Scoped phase tag: names recorded inside become "tag:name".
 struct ProfTag {
   Ctx* c;
@@ -174,8 +184,10 @@ int tc_check(Ctx* c);  // PARO_ERR_TIMEOUT once a tensor-core kernel gave up wai
 Ctx* unwrap(paro_ctx* h);
 // Cholesky S = L L^H (n x n, row-major, device), then writes G = conj(L)^{-1} (lower) into g.
 int chol_inv(Ctx* c, int n, const double2* s, double2* g);
-// Hermitian eigensolver (one CTA): w ascending, v columns = eigenvectors.
+// Hermitian eigensolver, FP64 (k_eigh.cu): w ascending, v columns = eigenvectors (row-major n x n).
 int eigh(Ctx* c, int n, const double2* a, double* w, double2* v);
+// The same result from an FP32 solve refined in FP64 (k_eigh_mixed.cu); FP64 solver for n > 160.
+int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v);
 // Per-band partial sums: out[b] = sum_g Re conj(x[b][g]) y[b][g] (weights optional) — helpers.
 template <typename T>
 int band_norms(Ctx* c, int nb, int npw, const cplx<T>* x, int ldx, double* out_dev);

@@ -142,7 +142,8 @@ def test_adjoint_full_size_64_atoms(precision_dtype, tol):
     ref = adjoint.grad_pos_local(basis, pos, inputs.LOCAL_PP, adjoint.grad_v(basis, psi, w))
     ref = ref + adjoint.grad_pos_kb(basis, pos, (inputs.KB_RC, d), psi, w, atoms=atoms)
     assert _rel(g_pos[atoms], ref[atoms]) < max(tol, 1e-10) * np.abs(ref).max() / np.abs(ref[atoms]).max()
-    assert _rel(g_psi.cpu().numpy(), ctx.apply_h(tw).cpu().numpy()) < 1e-13
+    # dL/dpsi = H W: bit for bit in FP64; in FP32 the adjoint's projector products run on the tensor cores
+    assert _rel(g_psi.cpu().numpy(), ctx.apply_h(tw).cpu().numpy()) < (1e-13 if precision_dtype == np.complex128 else tol)
     q = torch.from_numpy(basis.q).cuda().to(tp.real.dtype)
     hp = ctx.apply_h(tp)
     for al in range(3):

@@ -131,6 +131,24 @@ def test_solve_source_matches_oracle_fixed_iterations():
     assert _rel(x32.cpu().numpy(), x_ref) < 1e-4
 
 
+def test_solve_source_fp32_full_size_64_atoms():
+    # inner solves of the 64-atom cell in FP32: the projector products run on the tensor cores (3xTF32,
+    # K = 23847 plane waves); 4 fixed steps against the FP64 oracle's PCG
+    ctx = _ctx("si64_scf", "mixed")
+    lat, pos, d, c = inputs.config_inputs("si64_scf")
+    b = pw.Basis(lat, c["ecut"], ctx.grid)
+    v = pw.vloc_real(lat, pos, ctx.grid, c["ecut"], **inputs.LOCAL_PP)
+    beta = pw.kb_beta(lat, pos, b.q, inputs.KB_RC)
+    prob = opar.ParoProblem(b, v, beta, d)
+    assert abs(prob.sigma - ctx.sigma()) < 1e-9
+    nb = 8
+    psi = np.linalg.qr(inputs.start_vectors(nb, b.npw, 31).T)[0].T
+    eps = np.linspace(-0.5, 0.3, nb)
+    x_ref, _ = opar.pcg(prob.a, (eps - prob.sigma)[:, None] * psi, psi, prob.precond, 0.0, 4)
+    x32, _ = ctx.solve_source(eps, torch.from_numpy(psi.astype(np.complex64)).cuda(), 0.0, 4)
+    assert _rel(x32.cpu().numpy(), x_ref) < 1e-4
+
+
 def test_solve_source_tolerance_stops_each_orbital():
     ctx, prob, _ = _small(ecut=4.0)
     c0 = inputs.start_vectors(12, prob.basis.npw, 6)
@@ -141,9 +159,11 @@ def test_solve_source_tolerance_stops_each_orbital():
     assert _rel(x.cpu().numpy(), x_ref) < 1e-10
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("n", [1, 5, 20, 144, 288])
-def test_eigh_matches_lapack(n):
-    ctx, _, _ = _small()
+def test_eigh_matches_lapack(n, precision):
+    # mixed: FP32 solve refined to FP64 accuracy (n <= 160; larger n uses the FP64 solver)
+    ctx, _, _ = _small(precision=precision)
     rng = np.random.default_rng(n)
     a = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
     a = a + a.conj().T
