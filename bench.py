@@ -132,25 +132,61 @@ def shapes(ctx):
 
 
 def launch_work(name: str, s):
-    """Algorithmic work of one launch of a profiled kernel with a fixed shape: (kind, amount)."""
+    """Algorithmic work of one launch of a profiled kernel with a fixed shape: (kind, amount).
+    kind: "hbm" (bytes), "alu32"/"alu64" (FP32 / FP64 CUDA-core flops), "tensor" (complex products on the
+    tensor cores: 8 M N K real flops of the product; the 3xTF32 split issues three TF32 MMAs for each)."""
     b = 16 if "<f64>" in name else 8
     nb, npw, ncol, n3, ng, npj = s["nb"], s["npw"], s["ncol"], s["n3"], s["ngrid"], s["nproj"]
     tag, _, kern = name.partition(":")
-    if tag in ("rr",):
+    if tag == "rr":
         if kern.startswith("k_zpass_inv"):
             return "hbm", nb * npw * b + nb * n3 * ncol * b
         if kern.startswith("k_plane"):
             return "hbm", 2 * nb * n3 * ncol * b + ng * b // 2
         if kern.startswith("k_zpass_fwd"):
             return "hbm", nb * n3 * ncol * b + 2 * nb * npw * b
-        if kern.startswith("kb_apply"):
-            return "flop", 2 * 8 * npj * nb * npw
+        if kern in ("k_gemm_cn_tc", "k_gemm_wx_tc"):
+            return "tensor", 8 * npj * nb * npw
     if kern.startswith("k_gemm_cn") and tag in ("gram", "hsub"):
         # Hermitian products: the nb (nb + 1) / 2 distinct entries are the algorithmic work
-        return "flop", 8 * nb * (nb + 1) // 2 * npw
-    if kern.startswith("k_gemm_wx") and tag in ("orth", "rot"):
-        return "flop", 8 * nb * nb * npw
+        return "alu32", 8 * nb * (nb + 1) // 2 * npw
+    if kern == "k_gemm_wx_tc" and tag in ("orth",):
+        return "tensor", 8 * nb * nb * npw
+    if kern.startswith("k_tridiag"):
+        return "alu64", 16.0 / 3.0 * nb ** 3
+    if kern.startswith("k_chol"):
+        return "alu64", 4.0 / 3.0 * nb ** 3 * 2
     return None, None
+
+
+# DRAM bytes per launch from one ncu capture, valid only for the kernel source it was taken on
+# (sha256 prefix of the file defining the kernel); otherwise the roofline's traffic is null.
+TRAFFIC = {
+    "k_tridiag_cluster": (224768, "paper_1702_04045_gb300/csrc/k_eigh.cu", "4037f1d18cc884a1"),
+}
+
+
+def traffic_of(kernel: str):
+    import hashlib
+    ent = TRAFFIC.get(kernel.partition(":")[2])
+    if not ent:
+        return None
+    nbytes, path, digest = ent
+    try:
+        with open(os.path.join(ROOT, path), "rb") as f:
+            cur = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return nbytes if cur == digest else None
+
+
+def tensor_peak():
+    """Dense TF32 tensor peak: the measured bf16 GEMM rate times the nominal TF32/bf16 ratio (1.1/2.25)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)["bf16_tflops"] * 1.1 / 2.25, "measured bf16 x 1.1/2.25"
+    except (OSError, KeyError):
+        return 1900.0 * 1.1 / 2.25, "fallback bf16 x 1.1/2.25"
 
 
 def hpsi_bytes(s, b):
@@ -225,28 +261,37 @@ def run_ours(args, rank, world, local, pg):
     totals = {n: t for n, (k, t) in prof.items()}
     dom = max(totals, key=totals.get) if totals else None
     hbm, hbm_src = peaks()
-    roof = None
-    for cand in sorted(totals, key=totals.get, reverse=True):
+    def roof_of(cand):
         kind, work = launch_work(cand, s)
         if kind is None:
-            continue
+            return None
         cnt, tot = prof[cand]
         avg_s = tot / cnt / 1e3
+        common = {"kernel": cand, "avg_launch_ms": avg_s * 1e3, "share_of_step": tot / ms,
+                  "traffic": traffic_of(cand)}
         if kind == "hbm":
             ach = work / avg_s / 1e9
-            roof = {"kernel": cand, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                    "frac": ach / hbm, "traffic": None, "peak_source": hbm_src,
-                    "bytes_per_launch": work, "avg_launch_ms": avg_s * 1e3,
-                    "share_of_step": tot / ms}
-        else:
-            ach = work / avg_s / 1e12
-            peak = FP64_TFLOPS if "<f64>" in cand else 67.0
-            roof = {"kernel": cand, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": None,
-                    "peak_source": "FP64 1.25 TFLOP/s (recipe table, reproduced by a probe)" if "<f64>" in cand
-                    else "FP32 FMA 67 TFLOP/s (probe)",
-                    "flops_per_launch": work, "avg_launch_ms": avg_s * 1e3, "share_of_step": tot / ms}
-        break
+            return dict(common, bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
+                        peak_source=hbm_src, bytes_per_launch=work)
+        if kind == "tensor":
+            tp, tsrc = tensor_peak()
+            ach = 3 * work / avg_s / 1e12
+            return dict(common, bound="tensor", achieved=ach, peak=tp, unit="TFLOP/s", frac=ach / tp,
+                        peak_source=tsrc, flops_per_launch=work,
+                        note="3xTF32: three TF32 MMAs per real product; achieved counts all three")
+        peak = FP64_TFLOPS if kind == "alu64" else 67.0
+        ach = work / avg_s / 1e12
+        return dict(common, bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                    peak_source="FP64 1.25 TFLOP/s (recipe table, reproduced by a probe)" if kind == "alu64"
+                    else "FP32 FMA 67 TFLOP/s (probe)", flops_per_launch=work)
+
+    # the dominant kernel (largest share of the step) with a fixed per-launch shape
+    roof = None
+    for cand in sorted(totals, key=totals.get, reverse=True):
+        roof = roof_of(cand)
+        if roof:
+            break
+    roof_tensor = roof_of("rr:k_gemm_cn_tc") if "rr:k_gemm_cn_tc" in prof else None
     # H psi GB/s over the three full-batch passes of the Rayleigh-Ritz apply
     bsz = 16 if args.precision == "fp64" else 8
     pas = [f"rr:k_zpass_inv<{'f64' if bsz == 16 else 'f32'}>", f"rr:k_plane<{'f64' if bsz == 16 else 'f32'}>",
@@ -268,6 +313,7 @@ def run_ours(args, rank, world, local, pg):
                 "h2d_bytes_per_step": nb * npw * 16 + nb * 8, "d2h_bytes_per_step": 8 * 8},
         "gpu_launches": launches,
         "roofline": roof,
+        "roofline_tensor_projector": roof_tensor,
         "hpsi": hpsi,
         "fp64_ms_per_step": fp64,
         "speedup_vs_fp64": (fp64 / (ms_max / args.steps)) if fp64 else None,
@@ -358,7 +404,8 @@ def run_batched(name, steps=10, warmup=3, ref_steps=3):
     out = {"workload": name, "problems": info["problems"], "orbitals": info["items"],
            "npw_range": [min(npw), max(npw)], "precision": "mixed",
            "ms_per_step_batched": t_b * 1e3, "ms_per_step_per_context": t_c * 1e3, "speedup": t_c / t_b,
-           "fused_hpsi_ms_all_orbitals": t_h, "fused_kernel": {"threads": info["threads"], "grid": info["grid"]},
+           "hpsi_ms_all_orbitals": t_h,
+           "hpsi_kernel": {"launches_per_apply": info["launches_per_apply"], "grid": info["grid"]},
            "kernels_per_step": info["kernels_per_step"], "max_resid_after": r}
     b.close()
     for c in ctxs:

@@ -165,30 +165,32 @@ int paro_apply_h_adjoint(paro_ctx* ctx, int ik, int nb, int dtype, const void* p
  * of parallelism: orbitals within a problem, problems within the batch). The paper has no batching
  * interface; these calls run Algorithm 1 on all problems at once.
  * paro_batch_create -- groups n_ctx contexts (same precision, same stream, n_bands <= 64 each, a
- *   potential set, at most 64 KB projectors per k-point). Problems are (context, k-point) pairs in
- *   context-major order. Every problem must fit the fused H psi kernel: (sticks x N3 + N1 x N2 + N_pw +
- *   N1 + N2 + N3 + n_proj) complex elements of the working precision within 227 KB of shared memory;
- *   otherwise PARO_ERR_ARG (use the per-context calls). The call times candidate launch shapes of the
- *   fused kernel on the batch's own problems and keeps the fastest. The batch refers to the contexts,
- *   which must outlive it.
- * paro_batch_apply_h -- H psi of every problem in one persistent launch: psi[i], hpsi[i] device
- *   n_bands x npw arrays of dtype (the contexts' precision: PARO_C64 for FP64, PARO_C32 for mixed) of
- *   problem i. Enqueued on the contexts' stream.
+ *   potential set). Problems are (context, k-point) pairs in context-major order. H psi runs as one
+ *   persistent kernel over flat work lists of all problems' orbitals (z-FFTs of stick groups, one unit
+ *   per (orbital, z-plane), z-FFTs back), so a plane of every problem must fit one CTA's shared memory
+ *   (N1 x N2 complex elements of the working precision within 227 KB; otherwise PARO_ERR_ARG). The call
+ *   times the candidate forms (one cooperative launch with grid barriers between the phases, or one
+ *   launch per phase) and grids on the batch's own problems and keeps the fastest. The batch refers to
+ *   the contexts, which must outlive it.
+ * paro_batch_apply_h -- H psi of every problem: psi[i], hpsi[i] device n_bands x npw arrays of dtype
+ *   (the contexts' precision: PARO_C64 for FP64, PARO_C32 for mixed) of problem i. Enqueued on the
+ *   contexts' stream.
  * paro_batch_step -- one ParO iteration (Algorithm 1, fixed potential) of every problem: source
  *   problems by PCG with a fixed number max_it of steps (each orbital frozen once ||r|| <= rel_tol ||r0||),
  *   Cholesky orthonormalisation, Rayleigh-Ritz with a Jacobi eigensolver per problem, all captured once
  *   into a CUDA graph (re-captured when rel_tol or max_it change) and replayed. The new orbitals,
  *   eigenvalues and residuals are stored in the contexts (paro_get_orbitals etc.); max_resid_out
  *   receives the largest occupied residual. Every context needs orbitals (paro_set_orbitals) first.
- *   Errors: PARO_ERR_BREAKDOWN (PCG or Cholesky), PARO_ERR_NOT_CONVERGED (Jacobi).
- * paro_batch_info -- problems, (problem, band) items, chosen block size and persistent grid of the
- *   fused kernel, and kernels launched per captured step (0 before the first step).
+ *   Errors: PARO_ERR_BREAKDOWN (PCG or Cholesky), PARO_ERR_NOT_CONVERGED (Jacobi), PARO_ERR_TIMEOUT (a
+ *   bounded grid-barrier wait gave up).
+ * paro_batch_info -- problems, (problem, band) items, H psi launches per apply (1 or 3), its grid, and
+ *   kernels launched per captured step (0 before the first step).
  */
 typedef struct paro_batch paro_batch;
 int paro_batch_create(paro_batch** out, paro_ctx* const* ctxs, int n_ctx);
 int paro_batch_apply_h(paro_batch* b, int dtype, const void* const* psi, void* const* hpsi);
 int paro_batch_step(paro_batch* b, double rel_tol, int max_it, double* max_resid_out);
-int paro_batch_info(const paro_batch* b, int* n_problems, int* n_items, int* threads, int* grid,
+int paro_batch_info(const paro_batch* b, int* n_problems, int* n_items, int* launches_per_apply, int* grid,
                     long long* kernels_per_step);
 void paro_batch_destroy(paro_batch* b);
 

@@ -3,18 +3,19 @@
 // problem is an independent source problem, Algorithm 1 step 3, and the projection step 4 is local to
 // its problem).
 //
-//  * H psi: one persistent kernel per apply over all (problem, band) items. Each CTA takes one item at a
-//    time and does the whole apply in shared memory: the item's coefficients, its z-columns ("sticks",
-//    plane-major), one z-plane at a time for the 2D FFTs and V_eff(r), and the Kleinman-Bylander
-//    projections (warp per projector). Items are ordered largest first and dealt round-robin.
+//  * H psi: one persistent kernel per apply over flat work lists of every problem's orbitals, in three
+//    phases: z-FFTs of stick groups (and the projections per orbital), one unit per (orbital, z-plane)
+//    for the 2D FFTs and V_eff(r), and z-FFTs back with the gather, kinetic and projector terms. The
+//    phases are separated by bounded grid barriers of a cooperative launch, or by kernel boundaries
+//    (three launches) when that is faster; the stick buffers stay in L2.
 //  * PCG: the batched kernels of the per-context solver, over a ragged list of bands (per-band plane-wave
 //    count and offset), with per-band convergence masks on the device and a fixed number of steps.
 //  * projection: per problem (n_bands <= 64) Gram and H_sub by split-K products, Cholesky and
 //    triangular inverse in one CTA, a cyclic Jacobi eigensolver (parallel round-robin ordering) in one CTA,
 //    and the rotations.
 //  * one ParO step is captured once into a CUDA graph and replayed; nothing in it waits on the host.
-//  * the fused kernel's block size and persistent grid are picked by timing candidates on the batch's
-//    own problems when the batch is created.
+//  * the H psi form (one cooperative launch or three) and its persistent grid are picked by timing the
+//    candidates on the batch's own problems when the batch is created.
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
@@ -34,11 +35,13 @@ static const int kBSlice = 512;   // K slice of the batched Gram / H_sub product
 // Per problem (one k-point of one context), device-visible.
 struct ProbDev {
   int npw, ncol, nxr, nb, N1, N2, N3, nproj;
-  long long off;  // first element of the problem's rows in the batch vectors
-  int band0;      // first band of the problem in the flat band list
+  long long off;   // first element of the problem's rows in the batch vectors
+  long long soff;  // first element of the problem's stick buffers (nb x N3 x ncol)
+  long long dpoff; // first element of the problem's scaled projections (nb x nproj)
+  int band0;       // first band of the problem in the flat band list
   int pad;
   FftPlan plan[3];
-  const int *col_x, *col_y, *g_col, *g_z, *xrows;
+  const int *col_x, *col_y, *col_off, *g_col, *g_z, *xrows;
   const double* kin;
   const float* kin32;
   const double* vplane;
@@ -63,53 +66,66 @@ template <typename T> __device__ __forceinline__ const cplx<T>* pd_beta(const Pr
 template <> __device__ __forceinline__ const double2* pd_beta<double>(const ProbDev& p) { return p.beta; }
 template <> __device__ __forceinline__ const float2* pd_beta<float>(const ProbDev& p) { return p.beta32; }
 
-// shared memory of one item (in elements of cplx<T>): sticks, plane, coefficients, twiddles, D P
-static size_t fused_elems(const ProbDev& p) {
-  return (size_t)p.ncol * p.N3 + (size_t)p.N1 * p.N2 + p.npw + p.N1 + p.N2 + p.N3 + p.nproj;
+static const int kSG = 32;  // sticks per z-FFT work unit
+
+// shared memory of one work unit (in elements of cplx<T>): the larger of a stick group's lines and a
+// plane, plus the three twiddle tables
+static size_t unit_elems(const ProbDev& p) {
+  const size_t lines = (size_t)kSG * (p.N3 + 1), plane = (size_t)p.N1 * p.N2;
+  return (lines > plane ? lines : plane) + p.N1 + p.N2 + p.N3;
 }
 
 // ------------------------------------------------------------------------------------------------
-// fused H psi: Y = (H - shift_p) X for every item (p, b); shift_p = sigma_p when `shifted`
+// H psi of every (problem, band) item in one persistent cooperative launch: Y = (H - shift_p) X,
+// shift_p = sigma_p when `shifted`. Three phases over flat work lists, separated by bounded grid
+// barriers; the stick buffers S (plane-major per item) and the scaled projections DP stay in L2.
+//   phase 1: (item, stick group) - scatter the group's coefficients on lines of N3 points and
+//            inverse-FFT them along z into S; (item, -1) - D_j (beta_j^H c) for the item's projectors
+//   phase 2: (item, z) - the plane: inverse FFT along y (rows with sticks) and x, times V(z)/N, forward
+//            FFT along x and y, back into S
+//   phase 3: (item, stick group) - forward FFT along z, gather, add (|k+G|^2/2 - shift) c_G and the
+//            projector term sum_j beta_j(G) DP_j
 // ------------------------------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(512, 1) k_hpsi_fused(const ProbDev* __restrict__ probs, const int2* __restrict__ items,
-                                                    int nitems, const cplx<T>* __restrict__ X, cplx<T>* __restrict__ Y,
+struct HpsiLists {
+  const int2* u1; int n1;  // (item, group or -1)
+  const int2* u2; int n2;  // (item, z)
+  const int2* u3; int n3;  // (item, group)
+};
+
+// PH = 0: all three phases in one cooperative launch (grid barriers between them); PH = 1, 2, 3: one
+// phase per launch (the kernel boundary orders them).
+template <typename T, int PH>
+__global__ void __launch_bounds__(256, PH == 0 ? 1 : 2) k_hpsi_batch(const ProbDev* __restrict__ probs, const int2* __restrict__ items,
+                                                    HpsiLists L, const cplx<T>* __restrict__ X, cplx<T>* __restrict__ Y,
+                                                    cplx<T>* __restrict__ S, cplx<T>* __restrict__ DP,
                                                     const int* __restrict__ active, const double* __restrict__ sigma,
-                                                    int shifted) {
+                                                    int shifted, unsigned* bar, int* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ ProbDev pd;
-  cplx<T>* St = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    __syncthreads();  // the previous item is done with shared memory
-    const int2 ib = items[it];
-    if (threadIdx.x == 0) pd = probs[ib.x];
+  // returns false when the unit's item is inactive (the whole CTA skips it)
+  auto begin_unit = [&](int2 u) -> bool {
     __syncthreads();
-    const int b = ib.y, gb = pd.band0 + b;
-    if (active != nullptr && active[gb] == 0) continue;
-    const int N1 = pd.N1, N2 = pd.N2, N3 = pd.N3, ncol = pd.ncol, npw = pd.npw, np = pd.nproj;
-    cplx<T>* P = St + (size_t)N3 * ncol;
-    cplx<T>* cb = P + N1 * N2;
-    cplx<T>* tx = cb + npw;
-    cplx<T>* ty = tx + N1;
-    cplx<T>* tz = ty + N2;
-    cplx<T>* dp = tz + N3;
+    if (threadIdx.x == 0) pd = probs[items[u.x].x];
+    __syncthreads();
+    return active == nullptr || active[pd.band0 + items[u.x].y] != 0;
+  };
+  // ---- phase 1
+  if (PH == 0 || PH == 1)
+  for (int ui = blockIdx.x; ui < L.n1; ui += gridDim.x) {
+    const int2 u = L.u1[ui];
+    if (!begin_unit(u)) continue;
+    const int b = items[u.x].y, npw = pd.npw, ncol = pd.ncol, N3 = pd.N3;
     const cplx<T>* x = X + pd.off + (size_t)b * npw;
-    cplx<T>* y = Y + pd.off + (size_t)b * npw;
-    for (int i = threadIdx.x; i < N1; i += blockDim.x) tx[i] = pd_tw<T>(pd, 0)[i];
-    for (int i = threadIdx.x; i < N2; i += blockDim.x) ty[i] = pd_tw<T>(pd, 1)[i];
-    for (int i = threadIdx.x; i < N3; i += blockDim.x) tz[i] = pd_tw<T>(pd, 2)[i];
-    for (int i = threadIdx.x; i < N3 * ncol; i += blockDim.x) St[i] = mk<T>(0, 0);
-    for (int g = threadIdx.x; g < npw; g += blockDim.x) cb[g] = x[g];
-    __syncthreads();
-    for (int g = threadIdx.x; g < npw; g += blockDim.x) St[pd.g_z[g] * ncol + pd.g_col[g]] = cb[g];
-    if (np > 0) {  // D_j (beta_j^H c), warp per projector
+    if (u.y < 0) {  // projections
       const cplx<T>* beta = pd_beta<T>(pd);
-      for (int j = warp; j < np; j += nwarp) {
+      cplx<T>* dp = DP + pd.dpoff + (size_t)b * pd.nproj;
+      for (int j = warp; j < pd.nproj; j += nwarp) {
         const cplx<T>* bj = beta + (size_t)j * npw;
         T sx = 0, sy = 0;
         for (int g = lane; g < npw; g += 32) {
-          const cplx<T> bv = bj[g], c = cb[g];
+          const cplx<T> bv = bj[g], c = x[g];
           sx += bv.x * c.x + bv.y * c.y;  // conj(beta) c
           sy += bv.x * c.y - bv.y * c.x;
         }
@@ -120,31 +136,77 @@ __global__ void __launch_bounds__(512, 1) k_hpsi_fused(const ProbDev* __restrict
         }
         if (lane == 0) dp[j] = mk<T>((T)(pd.dvec[j] * sx), (T)(pd.dvec[j] * sy));
       }
+      continue;
+    }
+    const int c0 = u.y * kSG, ncb = min(kSG, ncol - c0), ls = N3 + 1;
+    cplx<T>* tz = buf;
+    cplx<T>* line = tz + N3;
+    for (int i = threadIdx.x; i < N3; i += blockDim.x) tz[i] = pd_tw<T>(pd, 2)[i];
+    for (int i = threadIdx.x; i < ncb * ls; i += blockDim.x) line[i] = mk<T>(0, 0);
+    __syncthreads();
+    const int g0 = pd.col_off[c0], g1 = pd.col_off[c0 + ncb];
+    for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) line[(pd.g_col[g] - c0) * ls + pd.g_z[g]] = x[g];
+    __syncthreads();
+    fft_lines<T, true, false>(line, pd.plan[2], ncb, 1, LinesDirect{ls}, tz);
+    cplx<T>* Sb = S + pd.soff + (size_t)b * N3 * ncol;
+    for (int i = threadIdx.x; i < N3 * ncb; i += blockDim.x) {
+      const int z = i / ncb, cc = i - z * ncb;
+      Sb[(size_t)z * ncol + c0 + cc] = line[cc * ls + z];
+    }
+  }
+  if (PH == 0 && !grid_barrier(bar, err)) return;
+  // ---- phase 2
+  if (PH == 0 || PH == 2)
+  for (int ui = blockIdx.x; ui < L.n2; ui += gridDim.x) {
+    const int2 u = L.u2[ui];
+    if (!begin_unit(u)) continue;
+    const int b = items[u.x].y, z = u.y, N1 = pd.N1, N2 = pd.N2, ncol = pd.ncol;
+    cplx<T>* tx = buf;
+    cplx<T>* ty = tx + N1;
+    cplx<T>* P = ty + N2;
+    for (int i = threadIdx.x; i < N1; i += blockDim.x) tx[i] = pd_tw<T>(pd, 0)[i];
+    for (int i = threadIdx.x; i < N2; i += blockDim.x) ty[i] = pd_tw<T>(pd, 1)[i];
+    for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) P[i] = mk<T>(0, 0);
+    __syncthreads();
+    cplx<T>* Sz = S + pd.soff + ((size_t)b * pd.N3 + z) * ncol;
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) P[pd.col_x[c] * N2 + pd.col_y[c]] = Sz[c];
+    __syncthreads();
+    fft_lines<T, true, false>(P, pd.plan[1], pd.nxr, 1, LinesMapped{pd.xrows, N2}, ty);
+    fft_lines<T, true, true>(P, pd.plan[0], N2, N2, LinesDirect{1}, tx);
+    const T* Vz = pd_v<T>(pd) + (size_t)z * N1 * N2;
+    for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) P[i] = cscale(P[i], Vz[i]);
+    __syncthreads();
+    fft_lines<T, false, true>(P, pd.plan[0], N2, N2, LinesDirect{1}, tx);
+    fft_lines<T, false, false>(P, pd.plan[1], pd.nxr, 1, LinesMapped{pd.xrows, N2}, ty);
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) Sz[c] = P[pd.col_x[c] * N2 + pd.col_y[c]];
+  }
+  if (PH == 0 && !grid_barrier(bar, err)) return;
+  // ---- phase 3
+  if (PH == 0 || PH == 3)
+  for (int ui = blockIdx.x; ui < L.n3; ui += gridDim.x) {
+    const int2 u = L.u3[ui];
+    if (!begin_unit(u)) continue;
+    const int b = items[u.x].y, npw = pd.npw, ncol = pd.ncol, N3 = pd.N3, np = pd.nproj;
+    const int c0 = u.y * kSG, ncb = min(kSG, ncol - c0), ls = N3 + 1;
+    cplx<T>* tz = buf;
+    cplx<T>* line = tz + N3;
+    for (int i = threadIdx.x; i < N3; i += blockDim.x) tz[i] = pd_tw<T>(pd, 2)[i];
+    const cplx<T>* Sb = S + pd.soff + (size_t)b * N3 * ncol;
+    for (int i = threadIdx.x; i < N3 * ncb; i += blockDim.x) {
+      const int z = i / ncb, cc = i - z * ncb;
+      line[cc * ls + z] = Sb[(size_t)z * ncol + c0 + cc];
     }
     __syncthreads();
-    fft_lines<T, true, true>(St, pd.plan[2], ncol, ncol, LinesDirect{1}, tz);  // z inverse of every stick
-    const T* V = pd_v<T>(pd);
-    for (int z = 0; z < N3; ++z) {
-      for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) P[i] = mk<T>(0, 0);
-      __syncthreads();
-      for (int c = threadIdx.x; c < ncol; c += blockDim.x) P[pd.col_x[c] * N2 + pd.col_y[c]] = St[z * ncol + c];
-      __syncthreads();
-      fft_lines<T, true, false>(P, pd.plan[1], pd.nxr, 1, LinesMapped{pd.xrows, N2}, ty);
-      fft_lines<T, true, true>(P, pd.plan[0], N2, N2, LinesDirect{1}, tx);
-      const T* Vz = V + (size_t)z * N1 * N2;
-      for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) P[i] = cscale(P[i], Vz[i]);
-      __syncthreads();
-      fft_lines<T, false, true>(P, pd.plan[0], N2, N2, LinesDirect{1}, tx);
-      fft_lines<T, false, false>(P, pd.plan[1], pd.nxr, 1, LinesMapped{pd.xrows, N2}, ty);
-      for (int c = threadIdx.x; c < ncol; c += blockDim.x) St[z * ncol + c] = P[pd.col_x[c] * N2 + pd.col_y[c]];
-      __syncthreads();
-    }
-    fft_lines<T, false, true>(St, pd.plan[2], ncol, ncol, LinesDirect{1}, tz);  // z forward
-    const T sh = shifted ? (T)sigma[ib.x] : (T)0;
-    const T* kin = pd_kin<T>(pd);
+    fft_lines<T, false, false>(line, pd.plan[2], ncb, 1, LinesDirect{ls}, tz);
+    const cplx<T>* x = X + pd.off + (size_t)b * npw;
+    cplx<T>* y = Y + pd.off + (size_t)b * npw;
+    const cplx<T>* dp = DP + pd.dpoff + (size_t)b * np;
     const cplx<T>* beta = pd_beta<T>(pd);
-    for (int g = threadIdx.x; g < npw; g += blockDim.x) {
-      const cplx<T> v = St[pd.g_z[g] * ncol + pd.g_col[g]], c = cb[g];
+    const T sh = shifted ? (T)sigma[items[u.x].x] : (T)0;
+    const T* kin = pd_kin<T>(pd);
+    const int g0 = pd.col_off[c0], g1 = pd.col_off[c0 + ncb];
+    for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+      const cplx<T> v = line[(pd.g_col[g] - c0) * ls + pd.g_z[g]], c = x[g];
       const T t = kin[g] - sh;
       T hx = v.x + t * c.x, hy = v.y + t * c.y;
       for (int j = 0; j < np; ++j) {
@@ -623,7 +685,11 @@ struct paro_batch {
   int nprob = 0, nbt = 0, nitems = 0, nch = 1, nslice = 1;
   size_t nelem = 0;      // complex elements of one batch vector
   size_t smem = 0;       // bytes of the fused kernel's dynamic shared memory
-  int threads = 256, grid = 152;  // chosen by the autotuner
+  int threads = 1, grid = 152;  // autotuner's choice: launches per H psi (1 cooperative or 3) and grid
+  void *sbuf = nullptr, *dpbuf = nullptr;  // stick buffers and scaled projections of the H psi phases
+  int2 *d_u1 = nullptr, *d_u2 = nullptr, *d_u3 = nullptr;
+  int n1 = 0, n2 = 0, n3 = 0;
+  unsigned* d_bar = nullptr;  // grid barrier (count, generation) and its time-out flag
   int ldm = 1;                     // largest n_bands + 1 (leading dimension of the per-problem matrices in
   size_t small_smem = 0;           // shared memory); bytes of the Jacobi kernel's two ldm x ldm matrices
   std::vector<ProbDev> hprob;
@@ -668,12 +734,39 @@ int berr(paro_batch* b, int code, const std::string& msg) {
 
 BandMap bandmap(const paro_batch* b) { return BandMap{b->d_bprob, b->d_brow, b->d_prob}; }
 
+// One H psi over every item: mode 0 = one cooperative launch of the three phases, mode 1 = three launches.
 template <typename T>
 int launch_fused(paro_batch* b, cudaStream_t s, const cplx<T>* X, cplx<T>* Y, const int* active, int shifted,
-                 int threads, int grid) {
-  k_hpsi_fused<T><<<grid, threads, b->smem, s>>>(b->d_prob, b->d_items, b->nitems, X, Y, active, b->sigma,
-                                                     shifted);
-  BLAUNCH(b, "k_hpsi_fused");
+                 int mode, int grid) {
+  const HpsiLists L{b->d_u1, b->n1, b->d_u2, b->n2, b->d_u3, b->n3};
+  cplx<T>* S = static_cast<cplx<T>*>(b->sbuf);
+  cplx<T>* DP = static_cast<cplx<T>*>(b->dpbuf);
+  int* err = reinterpret_cast<int*>(b->d_bar + 2);
+  if (mode == 0) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = b->smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    BCU(b, cudaLaunchKernelEx(&cfg, k_hpsi_batch<T, 0>, (const ProbDev*)b->d_prob, (const int2*)b->d_items, L, X, Y, S,
+                              DP, active, (const double*)b->sigma, shifted, b->d_bar, err));
+    ++b->graph_kernels;
+    return PARO_OK;
+  }
+  k_hpsi_batch<T, 1><<<std::min(grid, b->n1), 256, b->smem, s>>>(b->d_prob, b->d_items, L, X, Y, S, DP, active,
+                                                                  b->sigma, shifted, b->d_bar, err);
+  BLAUNCH(b, "k_hpsi_batch<1>");
+  k_hpsi_batch<T, 2><<<std::min(grid, b->n2), 256, b->smem, s>>>(b->d_prob, b->d_items, L, X, Y, S, DP, active,
+                                                                  b->sigma, shifted, b->d_bar, err);
+  BLAUNCH(b, "k_hpsi_batch<2>");
+  k_hpsi_batch<T, 3><<<std::min(grid, b->n3), 256, b->smem, s>>>(b->d_prob, b->d_items, L, X, Y, S, DP, active,
+                                                                  b->sigma, shifted, b->d_bar, err);
+  BLAUNCH(b, "k_hpsi_batch<3>");
   return PARO_OK;
 }
 
@@ -703,13 +796,13 @@ int enqueue_step(paro_batch* b, double tol, int maxit) {
   // step 3: (H - sigma) x = (eps - sigma) psi, x0 = psi
   k_brhs<T><<<dim3(4, b->nbt), 256, 0, s_>>>(bm, b->psi64, b->eps, b->sigma, rhs, x);
   BLAUNCH(b, "k_brhs");
-  if ((st = launch_fused<T>(b, s_, x, ap, nullptr, 1, b->threads, b->grid))) return st;
+  if ((st = launch_fused<T>(b, s_, x, ap, nullptr, 1, b->threads == 1 ? 0 : 1, b->grid))) return st;
   k_bpcg_init<T><<<gv, 256, 0, s_>>>(bm, b->nch, rhs, ap, r, p, b->pshift, b->prz, b->prr);
   BLAUNCH(b, "k_bpcg_init");
   k_bpcg_band_init<<<tb, 128, 0, s_>>>(b->nbt, b->nch, b->prz, b->prr, b->rz, b->r0n, b->active);
   BLAUNCH(b, "k_bpcg_band_init");
   for (int it = 0; it < maxit; ++it) {
-    if ((st = launch_fused<T>(b, s_, p, ap, b->active, 1, b->threads, b->grid))) return st;
+    if ((st = launch_fused<T>(b, s_, p, ap, b->active, 1, b->threads == 1 ? 0 : 1, b->grid))) return st;
     k_bpcg_dot<T><<<gv, 256, 0, s_>>>(bm, b->nch, p, ap, b->active, b->prz);
     BLAUNCH(b, "k_bpcg_dot");
     k_bpcg_alpha<<<tb, 128, 0, s_>>>(b->nbt, b->nch, b->prz, b->rz, b->active, b->alpha, b->flags);
@@ -738,7 +831,7 @@ int enqueue_step(paro_batch* b, double tol, int maxit) {
   const dim3 gw((b->nch * kBChunk + 255) / 256, b->nprob);
   k_bwx<T><<<gw, 256, 0, s_>>>(b->d_prob, b->G, 1, x, y);
   BLAUNCH(b, "k_bwx");
-  if ((st = launch_fused<T>(b, s_, y, hy, nullptr, 0, b->threads, b->grid))) return st;
+  if ((st = launch_fused<T>(b, s_, y, hy, nullptr, 0, b->threads == 1 ? 0 : 1, b->grid))) return st;
   if (carry)
     k_bgram<T, true><<<gg, 256, 0, s_>>>(b->d_prob, b->nslice, y, hy, b->part);
   else
@@ -789,7 +882,10 @@ int autotune(paro_batch* b) {
   int dev = 0, sms = 0;
   BCU(b, cudaGetDevice(&dev));
   BCU(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  BCU(b, cudaFuncSetAttribute(k_hpsi_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+  BCU(b, cudaFuncSetAttribute(k_hpsi_batch<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+  BCU(b, cudaFuncSetAttribute(k_hpsi_batch<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+  BCU(b, cudaFuncSetAttribute(k_hpsi_batch<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+  BCU(b, cudaFuncSetAttribute(k_hpsi_batch<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
   BCU(b, cudaFuncSetAttribute(k_bjacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->small_smem));
   BCU(b, cudaFuncSetAttribute(k_bchol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->small_smem));
   cplx<T>* X = static_cast<cplx<T>*>(b->p);
@@ -799,32 +895,37 @@ int autotune(paro_batch* b) {
   BCU(b, cudaEventCreate(&e0));
   BCU(b, cudaEventCreate(&e1));
   float best = 1e30f;
-  for (int threads : {256, 512}) {
+  for (int mode : {0, 1}) {
     int per_sm = 0;
-    BCU(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hpsi_fused<T>, threads, b->smem));
-    if (per_sm < 1) continue;
-    for (int mult : {1, 2, 4}) {
+    if (mode == 0)
+      BCU(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hpsi_batch<T, 0>, 256, b->smem));
+    else
+      BCU(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hpsi_batch<T, 2>, 256, b->smem));
+    for (int mult : {1, 2, 4, 8}) {  // mode 0: co-resident CTAs only
       if (mult > per_sm) break;
-      const int grid = std::min(b->nitems, mult * sms);
+      const int grid = mult * sms;
       int st;
-      if ((st = launch_fused<T>(b, b->st, X, Y, nullptr, 0, threads, grid))) return st;
+      if ((st = launch_fused<T>(b, b->st, X, Y, nullptr, 0, mode, grid))) return st;
       BCU(b, cudaEventRecord(e0, b->st));
       for (int rep = 0; rep < 3; ++rep)
-        if ((st = launch_fused<T>(b, b->st, X, Y, nullptr, 0, threads, grid))) return st;
+        if ((st = launch_fused<T>(b, b->st, X, Y, nullptr, 0, mode, grid))) return st;
       BCU(b, cudaEventRecord(e1, b->st));
       BCU(b, cudaEventSynchronize(e1));
       float ms = 0.f;
       BCU(b, cudaEventElapsedTime(&ms, e0, e1));
       if (ms < best) {
         best = ms;
-        b->threads = threads;
+        b->threads = mode == 0 ? 1 : 3;  // launches per H psi
         b->grid = grid;
       }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (best >= 1e30f) return berr(b, PARO_ERR_ARG, "batch: fused H psi kernel cannot be resident");
+  if (best >= 1e30f) return berr(b, PARO_ERR_ARG, "batch: H psi kernel cannot be resident");
+  unsigned h[3] = {0, 0, 0};
+  BCU(b, cudaMemcpy(h, b->d_bar, sizeof(h), cudaMemcpyDeviceToHost));
+  if (h[2]) return berr(b, PARO_ERR_TIMEOUT, "batch: grid barrier wait gave up");
   b->graph_kernels = 0;
   return PARO_OK;
 }
@@ -834,6 +935,7 @@ void free_batch(paro_batch* b) {
   if (b->ev) cudaEventDestroy(b->ev);
   if (b->gst) cudaStreamDestroy(b->gst);
   void* bufs[] = {b->d_prob, b->d_items, b->d_bprob, b->d_brow, b->x, b->r, b->p, b->ap, b->rhs, b->y, b->hy,
+                  b->sbuf, b->dpbuf, b->d_u1, b->d_u2, b->d_u3, b->d_bar,
                   b->psi64, b->hpsi64, b->prz, b->prr, b->rz, b->r0n, b->alpha, b->beta, b->active, b->still,
                   b->flags, b->part, b->S, b->G, b->eps, b->res, b->sigma, b->pshift};
   for (void* q : bufs)
@@ -885,7 +987,7 @@ int paro_batch_create(paro_batch** out, paro_ctx* const* ctxs, int n_ctx) {
     free_batch(b);
     return code;
   };
-  size_t off = 0, max_el = 0;
+  size_t off = 0, max_el = 0, soff = 0, dpoff = 0;
   int band0 = 0, max_npw = 0;
   for (int ci = 0; ci < n_ctx; ++ci) {
     Ctx& c = *unwrap(ctxs[ci]);
@@ -913,6 +1015,7 @@ int paro_batch_create(paro_batch** out, paro_ctx* const* ctxs, int n_ctx) {
       }
       P.col_x = B.d_col_x;
       P.col_y = B.d_col_y;
+      P.col_off = B.d_col_off;
       P.g_col = B.d_g_col;
       P.g_z = B.d_g_z;
       P.xrows = B.d_xrows;
@@ -923,8 +1026,11 @@ int paro_batch_create(paro_batch** out, paro_ctx* const* ctxs, int n_ctx) {
       P.beta = B.d_beta;
       P.beta32 = B.d_beta32;
       P.dvec = c.d_dvec;
-      if (P.nproj > 64) return bail(PARO_ERR_ARG, "batch: at most 64 KB projectors per problem");
-      max_el = std::max(max_el, fused_elems(P));
+      P.soff = (long long)soff;
+      P.dpoff = (long long)dpoff;
+      soff += (size_t)c.nb * P.N3 * P.ncol;
+      dpoff += (size_t)c.nb * P.nproj;
+      max_el = std::max(max_el, unit_elems(P));
       b->hprob.push_back(P);
       b->pk.push_back({ci, ik});
       off += (size_t)c.nb * B.npw;
@@ -937,8 +1043,8 @@ int paro_batch_create(paro_batch** out, paro_ctx* const* ctxs, int n_ctx) {
   b->nelem = off;
   b->smem = max_el * es;
   if (b->smem > 227 * 1024)
-    return bail(PARO_ERR_ARG, "batch: a problem does not fit the fused kernel's shared memory (" +
-                                  std::to_string(b->smem) + " bytes)");
+    return bail(PARO_ERR_ARG, "batch: a plane does not fit one CTA's shared memory (" + std::to_string(b->smem) +
+                                  " bytes)");
   int max_nb = 1;
   for (const ProbDev& P : b->hprob) max_nb = std::max(max_nb, P.nb);
   b->ldm = max_nb + 1;
@@ -956,6 +1062,20 @@ int paro_batch_create(paro_batch** out, paro_ctx* const* ctxs, int n_ctx) {
   for (int pi : order)
     for (int j = 0; j < b->hprob[pi].nb; ++j) items.push_back(make_int2(pi, j));
   b->nitems = (int)items.size();
+  std::vector<int2> u1, u2, u3;
+  for (int it = 0; it < b->nitems; ++it) {
+    const ProbDev& P = b->hprob[items[it].x];
+    const int ng = (P.ncol + kSG - 1) / kSG;
+    if (P.nproj > 0) u1.push_back(make_int2(it, -1));
+    for (int g = 0; g < ng; ++g) {
+      u1.push_back(make_int2(it, g));
+      u3.push_back(make_int2(it, g));
+    }
+    for (int z = 0; z < P.N3; ++z) u2.push_back(make_int2(it, z));
+  }
+  b->n1 = (int)u1.size();
+  b->n2 = (int)u2.size();
+  b->n3 = (int)u3.size();
   std::vector<int> bprob(b->nbt), brow(b->nbt);
   for (int pi = 0; pi < b->nprob; ++pi)
     for (int j = 0; j < b->hprob[pi].nb; ++j) {
@@ -984,6 +1104,12 @@ int paro_batch_create(paro_batch** out, paro_ctx* const* ctxs, int n_ctx) {
   al((void**)&b->still, b->nbt * sizeof(int));
   al((void**)&b->flags, (1 + b->nprob) * sizeof(int));
   al((void**)&b->part, (size_t)b->nprob * b->nslice * 4096 * sizeof(double2));
+  al(&b->sbuf, soff * es);
+  al(&b->dpbuf, std::max<size_t>(dpoff, 1) * es);
+  al((void**)&b->d_u1, u1.size() * sizeof(int2));
+  al((void**)&b->d_u2, u2.size() * sizeof(int2));
+  al((void**)&b->d_u3, u3.size() * sizeof(int2));
+  al((void**)&b->d_bar, 4 * sizeof(unsigned));
   al((void**)&b->S, mat);
   al((void**)&b->G, mat);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->gst, cudaStreamNonBlocking);
@@ -995,6 +1121,10 @@ int paro_batch_create(paro_batch** out, paro_ctx* const* ctxs, int n_ctx) {
   if (e == cudaSuccess) e = cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_bprob, bprob.data(), b->nbt * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_brow, brow.data(), b->nbt * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_u1, u1.data(), u1.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_u2, u2.data(), u2.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_u3, u3.data(), u3.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(b->d_bar, 0, 4 * sizeof(unsigned));
   if (e != cudaSuccess) return bail(PARO_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e));
   const int st = b->f64 ? autotune<double>(b) : autotune<float>(b);
   if (st) {
@@ -1016,10 +1146,11 @@ int paro_batch_apply_h(paro_batch* b, int dtype, const void* const* psi, void* c
     BCU(b, cudaMemcpyAsync(static_cast<char*>(b->p) + P.off * es, psi[i], (size_t)P.nb * P.npw * es,
                            cudaMemcpyDeviceToDevice, b->st));
   }
-  int st = b->f64 ? launch_fused<double>(b, b->st, static_cast<const double2*>(b->p), static_cast<double2*>(b->ap), nullptr,
-                                         0, b->threads, b->grid)
-                  : launch_fused<float>(b, b->st, static_cast<const float2*>(b->p), static_cast<float2*>(b->ap), nullptr, 0,
-                                        b->threads, b->grid);
+  const int mode = b->threads == 1 ? 0 : 1;
+  int st = b->f64 ? launch_fused<double>(b, b->st, static_cast<const double2*>(b->p), static_cast<double2*>(b->ap),
+                                         nullptr, 0, mode, b->grid)
+                  : launch_fused<float>(b, b->st, static_cast<const float2*>(b->p), static_cast<float2*>(b->ap),
+                                        nullptr, 0, mode, b->grid);
   if (st) return st;
   b->lead->launches += 1;
   for (int i = 0; i < b->nprob; ++i) {
@@ -1042,14 +1173,20 @@ int paro_batch_step(paro_batch* b, double rel_tol, int max_it, double* max_resid
       b->exec = nullptr;
     }
     cudaGraph_t g = nullptr;
-    BCU(b, cudaStreamBeginCapture(b->gst, cudaStreamCaptureModeThreadLocal));
-    b->graph_kernels = 0;
-    st = b->f64 ? enqueue_step<double>(b, rel_tol, max_it) : enqueue_step<float>(b, rel_tol, max_it);
-    const cudaError_t ec = cudaStreamEndCapture(b->gst, &g);
-    if (st) {
+    cudaError_t ec = cudaSuccess;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      BCU(b, cudaStreamBeginCapture(b->gst, cudaStreamCaptureModeThreadLocal));
+      b->graph_kernels = 0;
+      st = b->f64 ? enqueue_step<double>(b, rel_tol, max_it) : enqueue_step<float>(b, rel_tol, max_it);
+      ec = cudaStreamEndCapture(b->gst, &g);
+      if (st == PARO_OK && ec == cudaSuccess) break;
       if (g) cudaGraphDestroy(g);
-      return st;
+      g = nullptr;
+      cudaGetLastError();
+      if (b->threads != 1) break;
+      b->threads = 3;  // capture the three-launch form of H psi instead of the cooperative one
     }
+    if (st) return st;
     if (ec != cudaSuccess) return berr(b, PARO_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
     const cudaError_t ei = cudaGraphInstantiate(&b->exec, g, 0);
     cudaGraphDestroy(g);
@@ -1060,6 +1197,9 @@ int paro_batch_step(paro_batch* b, double rel_tol, int max_it, double* max_resid
   BCU(b, cudaGraphLaunch(b->exec, b->gst));
   BCU(b, cudaStreamSynchronize(b->gst));
   b->lead->launches += b->graph_kernels;
+  unsigned hb[3] = {0, 0, 0};
+  BCU(b, cudaMemcpy(hb, b->d_bar, sizeof(hb), cudaMemcpyDeviceToHost));
+  if (hb[2]) return berr(b, PARO_ERR_TIMEOUT, "batch: grid barrier wait gave up");
   if (b->h_flags[0])
     return berr(b, PARO_ERR_BREAKDOWN, "batch PCG breakdown in band " + std::to_string(b->h_flags[0] - 1));
   double mx = 0.0;
@@ -1078,12 +1218,12 @@ int paro_batch_step(paro_batch* b, double rel_tol, int max_it, double* max_resid
   return PARO_OK;
 }
 
-int paro_batch_info(const paro_batch* b, int* n_problems, int* n_items, int* threads, int* grid,
+int paro_batch_info(const paro_batch* b, int* n_problems, int* n_items, int* launches_per_apply, int* grid,
                     long long* kernels_per_step) {
   if (!b) return PARO_ERR_ARG;
   if (n_problems) *n_problems = b->nprob;
   if (n_items) *n_items = b->nitems;
-  if (threads) *threads = b->threads;
+  if (launches_per_apply) *launches_per_apply = b->threads;
   if (grid) *grid = b->grid;
   if (kernels_per_step) *kernels_per_step = b->exec ? b->graph_kernels : 0;
   return PARO_OK;

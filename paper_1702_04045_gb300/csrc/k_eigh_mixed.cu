@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(1024) k_tridiag_cta(int n, const double2* __re
   float2* A = reinterpret_cast<float2*>(smem_raw);  // n x ld
   float2* u = A + (size_t)n * ld;
   float2* w = u + n;
-  __shared__ double red[32];
+  __shared__ float red[32];
   __shared__ float s_t, s_K;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   for (int idx = tid; idx < n * n; idx += blockDim.x) {
@@ -58,24 +58,24 @@ __global__ void __launch_bounds__(1024) k_tridiag_cta(int n, const double2* __re
   __syncthreads();
   for (int j = 0; j + 1 < n; ++j) {
     const int m = n - j - 1;
-    double nrm2 = 0.0;
+    float nrm2 = 0.f;  // FP32 throughout: GB300's FP64 pipe would make these reductions the bottleneck
     for (int i = tid; i < m; i += blockDim.x) {
       const float2 x = A[(j + 1 + i) * ld + j];
       u[i] = x;
-      nrm2 += (double)x.x * x.x + (double)x.y * x.y;
+      nrm2 += x.x * x.x + x.y * x.y;
     }
-    nrm2 = block_sum(nrm2, red);
+    nrm2 = block_sumf(nrm2, red);
     if (tid == 0) {
       const float2 x0 = u[0];
       const float ax0 = hypotf(x0.x, x0.y);
-      const float nx = (float)sqrt(nrm2);
+      const float nx = sqrtf(nrm2);
       float2 alpha = x0;
       float t = 0.f;
-      if (m > 1 && nx > 0.f && nrm2 - (double)ax0 * ax0 > 0.0) {
+      if (m > 1 && nx > 0.f && nrm2 - ax0 * ax0 > 0.f) {
         const float2 phs = ax0 > 0.f ? make_float2(x0.x / ax0, x0.y / ax0) : make_float2(1.f, 0.f);
         alpha = make_float2(-phs.x * nx, -phs.y * nx);
         u[0] = csub(x0, alpha);
-        t = (float)(1.0 / (nrm2 + (double)nx * ax0));
+        t = 1.f / (nrm2 + nx * ax0);
       }
       s_t = t;
       tau[j] = t;
@@ -102,10 +102,10 @@ __global__ void __launch_bounds__(1024) k_tridiag_cta(int n, const double2* __re
       if (lane == 0) w[i] = make_float2(t * acc.x, t * acc.y);
     }
     __syncthreads();
-    double kre = 0.0;
-    for (int i = tid; i < m; i += blockDim.x) kre += (double)u[i].x * w[i].x + (double)u[i].y * w[i].y;
-    kre = block_sum(kre, red);
-    if (tid == 0) s_K = (float)(0.5 * t * kre);
+    float kre = 0.f;
+    for (int i = tid; i < m; i += blockDim.x) kre += u[i].x * w[i].x + u[i].y * w[i].y;
+    kre = block_sumf(kre, red);
+    if (tid == 0) s_K = 0.5f * t * kre;
     __syncthreads();
     const float K = s_K;
     for (int i = tid; i < m; i += blockDim.x) w[i] = make_float2(w[i].x - K * u[i].x, w[i].y - K * u[i].y);

@@ -93,37 +93,67 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int 
     unsigned char* sApl = sAph + A_BYTES;
     unsigned char* sBh = sApl + A_BYTES;
     unsigned char* sBl = sBh + B_BYTES;
-    for (int i = tid; i < kTcM * ch; i += kTcThreads) {
-      const int r = i / ch, c = i - r * ch;
-      const int gm = m0 + r, g0 = kk + 2 * c;
-      float2 v0 = make_float2(0.f, 0.f), v1 = v0;
-      if (gm < M) {
-        const float2* row = A + (size_t)gm * lda;
-        if (g0 < k1) v0 = row[g0];
-        if (g0 + 1 < k1) v1 = row[g0 + 1];
+    // unit i -> (row, chunk): each group of 8 consecutive threads covers the 8 rows of one core matrix at
+    // one chunk, so its 16-byte stores hit 8 distinct bank groups (a warp still reads whole 64-byte runs
+    // of 8 rows). All of a thread's loads are issued before any split or store.
+    {
+      constexpr int UA = kTcM * 8 / kTcThreads;  // units per thread at 8 chunks per row
+      float2 va[UA][2];
+#pragma unroll
+      for (int t = 0; t < UA; ++t) {
+        const int i = tid + t * kTcThreads;
+        va[t][0] = va[t][1] = make_float2(0.f, 0.f);
+        if (i < kTcM * ch) {
+          const int r = (i & 7) + 8 * (i / (8 * ch)), c = (i >> 3) % ch;
+          const int gm = m0 + r, g0 = kk + 2 * c;
+          if (gm < M) {
+            const float2* row = A + (size_t)gm * lda;
+            if (g0 < k1) va[t][0] = row[g0];
+            if (g0 + 1 < k1) va[t][1] = row[g0 + 1];
+          }
+        }
       }
-      float4 h, l;
-      tc_split(v0, v1, h, l);
-      const uint32_t o = tc_off(r, c, ch);
-      *reinterpret_cast<float4*>(sAh + o) = h;
-      *reinterpret_cast<float4*>(sAl + o) = l;
-      *reinterpret_cast<float4*>(sAph + o) = make_float4(-h.y, h.x, -h.w, h.z);
-      *reinterpret_cast<float4*>(sApl + o) = make_float4(-l.y, l.x, -l.w, l.z);
+#pragma unroll
+      for (int t = 0; t < UA; ++t) {
+        const int i = tid + t * kTcThreads;
+        if (i >= kTcM * ch) continue;
+        const int r = (i & 7) + 8 * (i / (8 * ch)), c = (i >> 3) % ch;
+        float4 h, l;
+        tc_split(va[t][0], va[t][1], h, l);
+        const uint32_t o = tc_off(r, c, ch);
+        *reinterpret_cast<float4*>(sAh + o) = h;
+        *reinterpret_cast<float4*>(sAl + o) = l;
+        *reinterpret_cast<float4*>(sAph + o) = make_float4(-h.y, h.x, -h.w, h.z);
+        *reinterpret_cast<float4*>(sApl + o) = make_float4(-l.y, l.x, -l.w, l.z);
+      }
     }
-    for (int i = tid; i < NT * ch; i += kTcThreads) {
-      const int r = i / ch, c = i - r * ch;
-      const int gn = n0 + r, g0 = kk + 2 * c;
-      float2 v0 = make_float2(0.f, 0.f), v1 = v0;
-      if (gn < N) {
-        const float2* row = B + (size_t)gn * ldb;
-        if (g0 < k1) v0 = row[g0];
-        if (g0 + 1 < k1) v1 = row[g0 + 1];
+    for (int i0 = 0; i0 < NT * ch; i0 += 4 * kTcThreads) {
+      float2 vb[4][2];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int i = i0 + tid + t * kTcThreads;
+        vb[t][0] = vb[t][1] = make_float2(0.f, 0.f);
+        if (i < NT * ch) {
+          const int r = (i & 7) + 8 * (i / (8 * ch)), c = (i >> 3) % ch;
+          const int gn = n0 + r, g0 = kk + 2 * c;
+          if (gn < N) {
+            const float2* row = B + (size_t)gn * ldb;
+            if (g0 < k1) vb[t][0] = row[g0];
+            if (g0 + 1 < k1) vb[t][1] = row[g0 + 1];
+          }
+        }
       }
-      float4 h, l;
-      tc_split(v0, v1, h, l);
-      const uint32_t o = tc_off(r, c, ch);
-      *reinterpret_cast<float4*>(sBh + o) = h;
-      *reinterpret_cast<float4*>(sBl + o) = l;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int i = i0 + tid + t * kTcThreads;
+        if (i >= NT * ch) continue;
+        const int r = (i & 7) + 8 * (i / (8 * ch)), c = (i >> 3) % ch;
+        float4 h, l;
+        tc_split(vb[t][0], vb[t][1], h, l);
+        const uint32_t o = tc_off(r, c, ch);
+        *reinterpret_cast<float4*>(sBh + o) = h;
+        *reinterpret_cast<float4*>(sBl + o) = l;
+      }
     }
     tc::fence_proxy_async_smem();
     __syncthreads();

@@ -426,7 +426,7 @@ class Batch:
         v = [ctypes.c_int() for _ in range(4)]
         k = ctypes.c_longlong()
         self._check(self.lib.paro_batch_info(self.h, *[ctypes.byref(x) for x in v], ctypes.byref(k)))
-        return dict(problems=v[0].value, items=v[1].value, threads=v[2].value, grid=v[3].value,
+        return dict(problems=v[0].value, items=v[1].value, launches_per_apply=v[2].value, grid=v[3].value,
                     kernels_per_step=k.value)
 
     def close(self):
