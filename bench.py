@@ -128,7 +128,8 @@ def shapes(ctx):
     mil = ctx.miller()
     ncol = len({(int(a), int(b)) for a, b, _ in mil})
     n1, n2, n3 = ctx.grid
-    return dict(nb=ctx.n_bands, npw=ctx.npw(), ncol=ncol, n3=n3, ngrid=n1 * n2 * n3, nproj=4 * ctx.n_atoms)
+    return dict(nb=ctx.n_bands, npw=ctx.npw(), ncol=ncol, n3=n3, ngrid=n1 * n2 * n3, nproj=4 * ctx.n_atoms,
+                nocc=ctx.n_occ)
 
 
 def launch_work(name: str, s):
@@ -152,8 +153,16 @@ def launch_work(name: str, s):
         return "alu32", 8 * nb * (nb + 1) // 2 * npw
     if kern == "k_gemm_wx_tc" and tag in ("orth",):
         return "tensor", 8 * nb * nb * npw
+    if kern == "k_tridiag_cta":  # FP32 one-CTA reduction of the mixed eigensolver
+        return "alu32", 16.0 / 3.0 * nb ** 3
     if kern.startswith("k_tridiag"):
         return "alu64", 16.0 / 3.0 * nb ** 3
+    if kern == "eigh_refine":  # two refinement steps + the cluster Rayleigh-Ritz: 10 FP64 n x n complex GEMMs
+        return "alu64", 10 * 8.0 * nb ** 3
+    if kern.startswith("k_plane_density") and tag in ("energy", "mix"):
+        # inverse plane FFTs of the occupied orbitals: stick buffer read once, FP64 partial planes written
+        nocc = s["nocc"]
+        return "hbm", nocc * n3 * ncol * b + (nocc + 7) // 8 * ng * 8
     if kern.startswith("k_chol"):
         return "alu64", 4.0 / 3.0 * nb ** 3 * 2
     return None, None
@@ -279,7 +288,7 @@ def run_ours(args, rank, world, local, pg):
             return dict(common, bound="tensor", achieved=ach, peak=tp, unit="TFLOP/s", frac=ach / tp,
                         peak_source=tsrc, flops_per_launch=work,
                         note="3xTF32: three TF32 MMAs per real product; achieved counts all three")
-        peak = FP64_TFLOPS if kind == "alu64" else 67.0
+        peak = FP64_TFLOPS if kind == "alu64" else 67.0  # alu32: FP32 FMA rate of the probe
         ach = work / avg_s / 1e12
         return dict(common, bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
                     peak_source="FP64 1.25 TFLOP/s (recipe table, reproduced by a probe)" if kind == "alu64"

@@ -252,9 +252,8 @@ static int passes_reg_dispatch(Ctx* c, const Basis& B, int nb, const cplx<T>* ps
 
 // Density planes with the register FFT: per (z-plane, band group) the inverse transforms along y and
 // x of each band, |psi(r)|^2 summed in FP64 in shared memory, the group's plane written to part.
-// TACC: accumulator of the |psi|^2 sum over the group's bands (at most gsize = 8). double where the
-// plane's N1 x N2 FP64 accumulator fits next to the plane in shared memory; float otherwise (FP32
-// orbitals on large planes: an 8-term FP32 sum, the groups then summed in FP64 by the caller).
+// TACC: accumulator of the |psi|^2 sum over the group's bands (at most gsize = 8): float for FP32 orbitals
+// (an 8-term FP32 sum, the groups then summed in FP64 by the caller), double for FP64 orbitals.
 template <typename T, int N1, int N2, typename TACC>
 __global__ void __launch_bounds__(256) k_plane_density_reg(const cplx<T>* __restrict__ S, int ncol, int nbands,
                                                            int gsize, const int* __restrict__ col_x,
@@ -347,9 +346,11 @@ static int density_planes_reg_acc(Ctx* c, const Basis& B, const cplx<T>* S, int 
 template <typename T, int N>
 static int density_planes_reg_n(Ctx* c, const Basis& B, const cplx<T>* S, int nbands, int ngrp, int gsize,
                                 double wfac, double* part) {
+  // FP32 orbitals: the group's |psi|^2 sum in FP32 (an 8-term sum, rounding of the FP32 FFT's own size) keeps
+  // the per-point accumulation off GB300's slow FP64 pipe; the groups are summed in FP64 by the caller
+  if constexpr (sizeof(T) == 4) return density_planes_reg_acc<T, N, float>(c, B, S, nbands, ngrp, gsize, wfac, part);
   if (density_reg_smem<T, N, double>() <= 227 * 1024)
     return density_planes_reg_acc<T, N, double>(c, B, S, nbands, ngrp, gsize, wfac, part);
-  if constexpr (sizeof(T) == 4) return density_planes_reg_acc<T, N, float>(c, B, S, nbands, ngrp, gsize, wfac, part);
   return fail(c, PARO_ERR_ARG, "density: plane too large for shared memory");
 }
 

@@ -66,12 +66,18 @@ template <typename T> __device__ __forceinline__ const cplx<T>* pd_beta(const Pr
 template <> __device__ __forceinline__ const double2* pd_beta<double>(const ProbDev& p) { return p.beta; }
 template <> __device__ __forceinline__ const float2* pd_beta<float>(const ProbDev& p) { return p.beta32; }
 
-static const int kSG = 32;  // sticks per z-FFT work unit
+static const int kSG = 64;  // sticks per z-FFT work unit
+
+// z-planes per plane work unit: enough that one unit's FFT stages cover ~4096 points
+__host__ __device__ __forceinline__ int planes_per_unit(int N1, int N2) {
+  const int pb = 4096 / (N1 * N2);
+  return pb < 1 ? 1 : (pb > 4 ? 4 : pb);
+}
 
 // shared memory of one work unit (in elements of cplx<T>): the larger of a stick group's lines and a
 // plane, plus the three twiddle tables
 static size_t unit_elems(const ProbDev& p) {
-  const size_t lines = (size_t)kSG * (p.N3 + 1), plane = (size_t)p.N1 * p.N2;
+  const size_t lines = (size_t)kSG * (p.N3 + 1), plane = (size_t)p.N1 * p.N2 * planes_per_unit(p.N1, p.N2);
   return (lines > plane ? lines : plane) + p.N1 + p.N2 + p.N3;
 }
 
@@ -160,25 +166,32 @@ __global__ void __launch_bounds__(256, PH == 0 ? 1 : 2) k_hpsi_batch(const ProbD
   for (int ui = blockIdx.x; ui < L.n2; ui += gridDim.x) {
     const int2 u = L.u2[ui];
     if (!begin_unit(u)) continue;
-    const int b = items[u.x].y, z = u.y, N1 = pd.N1, N2 = pd.N2, ncol = pd.ncol;
+    const int b = items[u.x].y, N1 = pd.N1, N2 = pd.N2, ncol = pd.ncol, PS = N1 * N2;
+    const int z0 = u.y, np = min(planes_per_unit(N1, N2), pd.N3 - z0);
     cplx<T>* tx = buf;
     cplx<T>* ty = tx + N1;
-    cplx<T>* P = ty + N2;
+    cplx<T>* P = ty + N2;  // np planes
     for (int i = threadIdx.x; i < N1; i += blockDim.x) tx[i] = pd_tw<T>(pd, 0)[i];
     for (int i = threadIdx.x; i < N2; i += blockDim.x) ty[i] = pd_tw<T>(pd, 1)[i];
-    for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) P[i] = mk<T>(0, 0);
+    for (int i = threadIdx.x; i < np * PS; i += blockDim.x) P[i] = mk<T>(0, 0);
     __syncthreads();
-    cplx<T>* Sz = S + pd.soff + ((size_t)b * pd.N3 + z) * ncol;
-    for (int c = threadIdx.x; c < ncol; c += blockDim.x) P[pd.col_x[c] * N2 + pd.col_y[c]] = Sz[c];
+    cplx<T>* Sz = S + pd.soff + ((size_t)b * pd.N3 + z0) * ncol;
+    for (int i = threadIdx.x; i < np * ncol; i += blockDim.x) {
+      const int q = i / ncol, c = i - q * ncol;
+      P[q * PS + pd.col_x[c] * N2 + pd.col_y[c]] = Sz[(size_t)q * ncol + c];
+    }
     __syncthreads();
-    fft_lines<T, true, false>(P, pd.plan[1], pd.nxr, 1, LinesMapped{pd.xrows, N2}, ty);
-    fft_lines<T, true, true>(P, pd.plan[0], N2, N2, LinesDirect{1}, tx);
-    const T* Vz = pd_v<T>(pd) + (size_t)z * N1 * N2;
-    for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) P[i] = cscale(P[i], Vz[i]);
+    fft_lines<T, true, false>(P, pd.plan[1], np * pd.nxr, 1, LinesPlanes{pd.xrows, pd.nxr, N2, PS}, ty);
+    fft_lines<T, true, true>(P, pd.plan[0], np * N2, N2, LinesPlanes{nullptr, N2, 1, PS}, tx);
+    const T* Vz = pd_v<T>(pd) + (size_t)z0 * PS;
+    for (int i = threadIdx.x; i < np * PS; i += blockDim.x) P[i] = cscale(P[i], Vz[i]);
     __syncthreads();
-    fft_lines<T, false, true>(P, pd.plan[0], N2, N2, LinesDirect{1}, tx);
-    fft_lines<T, false, false>(P, pd.plan[1], pd.nxr, 1, LinesMapped{pd.xrows, N2}, ty);
-    for (int c = threadIdx.x; c < ncol; c += blockDim.x) Sz[c] = P[pd.col_x[c] * N2 + pd.col_y[c]];
+    fft_lines<T, false, true>(P, pd.plan[0], np * N2, N2, LinesPlanes{nullptr, N2, 1, PS}, tx);
+    fft_lines<T, false, false>(P, pd.plan[1], np * pd.nxr, 1, LinesPlanes{pd.xrows, pd.nxr, N2, PS}, ty);
+    for (int i = threadIdx.x; i < np * ncol; i += blockDim.x) {
+      const int q = i / ncol, c = i - q * ncol;
+      Sz[(size_t)q * ncol + c] = P[q * PS + pd.col_x[c] * N2 + pd.col_y[c]];
+    }
   }
   if (PH == 0 && !grid_barrier(bar, err)) return;
   // ---- phase 3
@@ -1071,7 +1084,7 @@ int paro_batch_create(paro_batch** out, paro_ctx* const* ctxs, int n_ctx) {
       u1.push_back(make_int2(it, g));
       u3.push_back(make_int2(it, g));
     }
-    for (int z = 0; z < P.N3; ++z) u2.push_back(make_int2(it, z));
+    for (int z = 0; z < P.N3; z += planes_per_unit(P.N1, P.N2)) u2.push_back(make_int2(it, z));
   }
   b->n1 = (int)u1.size();
   b->n2 = (int)u2.size();

@@ -106,6 +106,15 @@ struct LinesMapped {  // base = map[l] * ls
   __device__ __forceinline__ int operator()(int l) const { return map[l] * ls; }
 };
 
+struct LinesPlanes {  // lines of several planes: base = (l / nper) * pstride + (map ? map[l % nper] : l % nper) * ls
+  const int* map;
+  int nper, ls, pstride;
+  __device__ __forceinline__ int operator()(int l) const {
+    const int p = l / nper, r = l - p * nper;
+    return p * pstride + (map ? map[r] : r) * ls;
+  }
+};
+
 // One Stockham stage over lines l0 .. l0+nlines-1 of length n in shared memory s; the caller keeps
 // nlines * n/R <= MaxUnits<R> * blockDim.x. LFAST: consecutive threads take consecutive lines (for
 // strided lines), else consecutive butterflies of one line.
