@@ -151,6 +151,9 @@ def launch_work(name: str, s):
     if kern.startswith("k_gemm_cn") and tag in ("gram", "hsub"):
         # Hermitian products: the nb (nb + 1) / 2 distinct entries are the algorithmic work
         return "alu32", 8 * nb * (nb + 1) // 2 * npw
+    if kern in ("k_gemm_cn_tc", "k_gemm_wx_tc") and tag == "pcg":
+        # projector products of the inner solves: every source column, whatever the active set
+        return "tensor", 8 * npj * nb * npw
     if kern == "k_gemm_wx_tc" and tag in ("orth",):
         return "tensor", 8 * nb * nb * npw
     if kern == "k_tridiag_cta":  # FP32 one-CTA reduction of the mixed eigensolver
@@ -328,6 +331,7 @@ def run_ours(args, rank, world, local, pg):
         "speedup_vs_fp64": (fp64 / (ms_max / args.steps)) if fp64 else None,
         "dominant_kernel": dom,
         "kernel_ms": {k: round(v[1], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+        "kernel_calls": {k: v[0] for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
         "clocks": clk,
         "energy_last_step": energy["total"] if energy else None,
     }

@@ -230,7 +230,8 @@ static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal) {
     if ((st = gemm_cn<T, T, T>(c, nx, nx, npw, Y, npw, HY, npw, S, nx, true, true))) return st;
     k_hermitize<<<(nx * nx + 255) / 256, 256, 0, c->stream>>>(nx, S);
     PARO_LAUNCH(c, "k_hermitize");
-    if ((st = f64 ? eigh(c, nx, S, w, G) : eigh_mixed(c, nx, S, w, G))) return st;  // G <- eigenvectors C
+    // mixed: one refinement step (FP64 Ritz values, vectors well below the FP32 level of the orbitals)
+    if ((st = f64 ? eigh(c, nx, S, w, G) : eigh_mixed(c, nx, S, w, G, 1))) return st;  // G <- eigenvectors C
   }
   {
     ProfTag t(c, "rot");
@@ -878,7 +879,7 @@ int paro_step(paro_ctx* ctx, int alg, double rel_tol, int max_it, double* max_re
 int paro_eigh(paro_ctx* ctx, int n, const void* a, double* w, void* v) {
   CTX_CHECK(ctx);
   if (n < 1 || !a || !w || !v) return fail(c, PARO_ERR_ARG, "paro_eigh: bad argument");
-  return c->prec == PARO_MIXED ? eigh_mixed(c, n, static_cast<const double2*>(a), w, static_cast<double2*>(v))
+  return c->prec == PARO_MIXED ? eigh_mixed(c, n, static_cast<const double2*>(a), w, static_cast<double2*>(v), 2)
                                : eigh(c, n, static_cast<const double2*>(a), w, static_cast<double2*>(v));
 }
 

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256) k_tridiag(int n, double2* __restrict__ A,
           __stcg(&A[(size_t)(j + 1) * n + j], us[0]);
           t = 1.0 / (nrm2 + nx * ax0);  // 2 / ||u||^2
         }
-        sc[0] = t;
+        sc[j & 1] = t;  // by parity: a CTA still reading step j's t while block 0 starts j + 1
         tau[j] = t;
         ecx[j] = alpha;
         d[j] = __ldcg(&A[(size_t)j * n + j]).x;
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256) k_tridiag(int n, double2* __restrict__ A,
       for (int i = tid; i < m; i += blockDim.x) __stcg(&ub[i], us[i]);
     }
     if (!grid_barrier(bar, err)) return;
-    const double t = __ldcg(&sc[0]);
+    const double t = __ldcg(&sc[j & 1]);
     if (t == 0.0) continue;
     for (int i = tid; i < m; i += blockDim.x) us[i] = __ldcg(&ub[i]);
     __syncthreads();
@@ -509,6 +509,47 @@ __global__ void __launch_bounds__(256) k_backtransform(int n, const cplx<R>* __r
   for (int i = lane; i < n; i += 32) V[(size_t)i * n + col] = vc[(size_t)i * cpb + wc];
 }
 
+// The same with every reflector in shared memory (when n^2 values of cplx<R> fit): U rows u_j at
+// Us[j * n + i]; one warp per column, blockDim / 32 columns per CTA.
+template <typename R>
+__global__ void __launch_bounds__(512) k_backtransform_s(int n, const cplx<R>* __restrict__ U, const R* __restrict__ tau,
+                                                         const cplx<R>* __restrict__ ph, const R* __restrict__ Z,
+                                                         cplx<R>* __restrict__ V) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int cpb = blockDim.x >> 5;
+  cplx<R>* Us = reinterpret_cast<cplx<R>*>(smem_raw);  // n x n (row j = u_j, m = n - j - 1 entries used)
+  cplx<R>* vc = Us + (size_t)n * n;                   // cpb x n: column wc of this CTA contiguous
+  R* ts = reinterpret_cast<R*>(vc + (size_t)n * cpb);
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) Us[i] = U[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) ts[i] = tau[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wc = threadIdx.x >> 5;
+  const int col = blockIdx.x * cpb + wc;
+  if (col >= n) return;
+  for (int i = lane; i < n; i += 32) vc[(size_t)wc * n + i] = cscale(cconj(ph[i]), Z[(size_t)i * n + col]);
+  __syncwarp();
+  for (int j = n - 2; j >= 0; --j) {
+    const R t = ts[j];
+    if (t == (R)0) continue;
+    const int m = n - j - 1;
+    cplx<R> sv = mk<R>(0, 0);
+    const cplx<R>* u = Us + (size_t)j * n;
+    for (int i = lane; i < m; i += 32) sv = cadd(sv, cmul(cconj(u[i]), vc[(size_t)wc * n + j + 1 + i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sv.x += __shfl_xor_sync(0xffffffffu, sv.x, o);
+      sv.y += __shfl_xor_sync(0xffffffffu, sv.y, o);
+    }
+    sv = cscale(sv, t);
+    for (int i = lane; i < m; i += 32) {
+      cplx<R>& vv = vc[(size_t)wc * n + j + 1 + i];
+      vv = csub(vv, cmul(u[i], sv));
+    }
+    __syncwarp();
+  }
+  for (int i = lane; i < n; i += 32) V[(size_t)i * n + col] = vc[(size_t)wc * n + i];
+}
+
 // CTAs of a cooperative launch of `kernel` with `threads` threads and `smem` bytes: at most `cap`,
 // and no more than can be co-resident.
 int coop_grid(Ctx* c, const void* kernel, int threads, size_t smem, int cap, int* grid) {
@@ -593,15 +634,30 @@ template int invit<float>(Ctx*, int, const float*, const float*, const float*, f
 // whose reflectors are the rows of U.
 int eigh_fp32_pieces(Ctx* c, int n, const float* d, const float* e, float* w, const float2* U, const float* tau,
                      const float2* ph, float* Z, float2* V, int* info) {
+  cudaEvent_t ev = prof_begin(c);
   k_bisect<float><<<(n + 3) / 4, 128, (size_t)2 * n * sizeof(float), c->stream>>>(n, d, e, w);
   PARO_LAUNCH(c, "k_bisect");
+  prof_end(c, "eigh32_bisect", ev);
+  ev = prof_begin(c);
   int st = invit<float>(c, n, d, e, w, Z, info);
   if (st) return st;
-  const int cpb = 2;
-  const size_t sm4 = (size_t)n * cpb * sizeof(float2);
+  prof_end(c, "eigh32_invit", ev);
+  ev = prof_begin(c);
+  const int cpb = 4;
+  const size_t sms = ((size_t)n * n + (size_t)n * cpb) * sizeof(float2) + (size_t)n * sizeof(float);
+  if (sms <= 220 * 1024) {  // reflectors in shared memory
+    PARO_CU(c, cudaFuncSetAttribute(k_backtransform_s<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms));
+    k_backtransform_s<float><<<(n + cpb - 1) / cpb, 32 * cpb, sms, c->stream>>>(n, U, tau, ph, Z, V);
+    PARO_LAUNCH(c, "k_backtransform_s");
+    prof_end(c, "eigh32_backtransform", ev);
+    return PARO_OK;
+  }
+  const int cpb2 = 2;
+  const size_t sm4 = (size_t)n * cpb2 * sizeof(float2);
   PARO_CU(c, cudaFuncSetAttribute(k_backtransform<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4));
-  k_backtransform<float><<<(n + cpb - 1) / cpb, 32 * cpb, sm4, c->stream>>>(n, U, (size_t)n, 1, tau, ph, Z, V);
+  k_backtransform<float><<<(n + cpb2 - 1) / cpb2, 32 * cpb2, sm4, c->stream>>>(n, U, (size_t)n, 1, tau, ph, Z, V);
   PARO_LAUNCH(c, "k_backtransform");
+  prof_end(c, "eigh32_backtransform", ev);
   return PARO_OK;
 }
 

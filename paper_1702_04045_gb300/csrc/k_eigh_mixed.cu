@@ -5,7 +5,7 @@
 //     (k_tridiag_cta), multisection, inverse iteration and back-transformation (the FP64 solver's kernels
 //     instantiated for float). GB300 runs FP32 at 64x its FP64 rate, and the one-CTA reduction needs no
 //     cluster or grid barriers.
-//  2. FP64 refinement of the eigenvector matrix X by the iteration of Ogita and Aishima (Japan J. Indust.
+//  2. FP64 refinement (one or two steps) of the eigenvector matrix X by the iteration of Ogita and Aishima (Japan J. Indust.
 //     Appl. Math. 35, 2018, "Iterative refinement for symmetric eigenvalue decomposition"), written for
 //     the Hermitian case: R = I - X^H X, S = X^H A X, lambda_i = S_ii / (1 - R_ii),
 //     delta = 2 (||S - diag(lambda)|| + ||A|| ||R||); E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i)
@@ -47,8 +47,7 @@ __global__ void __launch_bounds__(1024) k_tridiag_cta(int n, const double2* __re
   float2* A = reinterpret_cast<float2*>(smem_raw);  // n x ld
   float2* u = A + (size_t)n * ld;
   float2* w = u + n;
-  __shared__ float red[32];
-  __shared__ float s_t, s_K;
+  __shared__ float s_t[2];  // by parity of j: a CTA that skips column j (t = 0) still reads it safely
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   for (int idx = tid; idx < n * n; idx += blockDim.x) {
     const int i = idx / n, k = idx - i * n;
@@ -58,41 +57,46 @@ __global__ void __launch_bounds__(1024) k_tridiag_cta(int n, const double2* __re
   __syncthreads();
   for (int j = 0; j + 1 < n; ++j) {
     const int m = n - j - 1;
-    float nrm2 = 0.f;  // FP32 throughout: GB300's FP64 pipe would make these reductions the bottleneck
-    for (int i = tid; i < m; i += blockDim.x) {
-      const float2 x = A[(j + 1 + i) * ld + j];
-      u[i] = x;
-      nrm2 += x.x * x.x + x.y * x.y;
-    }
-    nrm2 = block_sumf(nrm2, red);
-    if (tid == 0) {
-      const float2 x0 = u[0];
-      const float ax0 = hypotf(x0.x, x0.y);
-      const float nx = sqrtf(nrm2);
-      float2 alpha = x0;
-      float t = 0.f;
-      if (m > 1 && nx > 0.f && nrm2 - ax0 * ax0 > 0.f) {
-        const float2 phs = ax0 > 0.f ? make_float2(x0.x / ax0, x0.y / ax0) : make_float2(1.f, 0.f);
-        alpha = make_float2(-phs.x * nx, -phs.y * nx);
-        u[0] = csub(x0, alpha);
-        t = 1.f / (nrm2 + nx * ax0);
+    if (warp == 0) {  // the reflector of column j, by one warp (FP32: the FP64 refinement follows)
+      float nrm2 = 0.f;
+      for (int i = lane; i < m; i += 32) {
+        const float2 x = A[(j + 1 + i) * ld + j];
+        u[i] = x;
+        nrm2 += x.x * x.x + x.y * x.y;
       }
-      s_t = t;
-      tau[j] = t;
-      ecx[j] = alpha;
-      d[j] = A[j * ld + j].x;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) nrm2 += __shfl_xor_sync(0xffffffffu, nrm2, o);
+      __syncwarp();
+      if (lane == 0) {
+        const float2 x0 = u[0];
+        const float ax0 = hypotf(x0.x, x0.y);
+        const float nx = sqrtf(nrm2);
+        float2 alpha = x0;
+        float t = 0.f;
+        if (m > 1 && nx > 0.f && nrm2 - ax0 * ax0 > 0.f) {
+          const float2 phs = ax0 > 0.f ? make_float2(x0.x / ax0, x0.y / ax0) : make_float2(1.f, 0.f);
+          alpha = make_float2(-phs.x * nx, -phs.y * nx);
+          u[0] = csub(x0, alpha);
+          t = 1.f / (nrm2 + nx * ax0);
+        }
+        s_t[j & 1] = t;
+        tau[j] = t;
+        ecx[j] = alpha;
+        d[j] = A[j * ld + j].x;
+      }
+      __syncwarp();
+      for (int i = lane; i < m; i += 32) U[(size_t)j * n + i] = u[i];
     }
     __syncthreads();
-    for (int i = tid; i < m; i += blockDim.x) U[(size_t)j * n + i] = u[i];
-    const float t = s_t;
+    const float t = s_t[j & 1];
     if (t == 0.f) continue;
     for (int i = warp; i < m; i += nwarp) {  // p_i = t sum_k B_ik u_k
       const float2* row = A + (j + 1 + i) * ld + (j + 1);
       float2 acc = make_float2(0.f, 0.f);
       for (int k = lane; k < m; k += 32) {
-        const float2 b = row[k], uk = u[k];
-        acc.x = fmaf(b.x, uk.x, fmaf(-b.y, uk.y, acc.x));
-        acc.y = fmaf(b.x, uk.y, fmaf(b.y, uk.x, acc.y));
+        const float2 bv = row[k], uk = u[k];
+        acc.x = fmaf(bv.x, uk.x, fmaf(-bv.y, uk.y, acc.x));
+        acc.y = fmaf(bv.x, uk.y, fmaf(bv.y, uk.x, acc.y));
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -102,20 +106,25 @@ __global__ void __launch_bounds__(1024) k_tridiag_cta(int n, const double2* __re
       if (lane == 0) w[i] = make_float2(t * acc.x, t * acc.y);
     }
     __syncthreads();
-    float kre = 0.f;
-    for (int i = tid; i < m; i += blockDim.x) kre += u[i].x * w[i].x + u[i].y * w[i].y;
-    kre = block_sumf(kre, red);
-    if (tid == 0) s_K = 0.5f * t * kre;
+    if (warp == 0) {  // K = (t/2) u^H p (real), w = p - K u
+      float kre = 0.f;
+      for (int i = lane; i < m; i += 32) kre += u[i].x * w[i].x + u[i].y * w[i].y;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) kre += __shfl_xor_sync(0xffffffffu, kre, o);
+      const float K = 0.5f * t * kre;
+      for (int i = lane; i < m; i += 32) w[i] = make_float2(w[i].x - K * u[i].x, w[i].y - K * u[i].y);
+    }
     __syncthreads();
-    const float K = s_K;
-    for (int i = tid; i < m; i += blockDim.x) w[i] = make_float2(w[i].x - K * u[i].x, w[i].y - K * u[i].y);
-    __syncthreads();
-    for (int idx = tid; idx < m * m; idx += blockDim.x) {  // B -= u w^H + w u^H
-      const int i = idx / m, k = idx - i * m;
-      float2& b = A[(j + 1 + i) * ld + (j + 1 + k)];
-      const float2 ui = u[i], wi = w[i], uk = u[k], wk = w[k];
-      b.x -= ui.x * wk.x + ui.y * wk.y + wi.x * uk.x + wi.y * uk.y;
-      b.y -= ui.y * wk.x - ui.x * wk.y + wi.y * uk.x - wi.x * uk.y;
+    for (int i = warp; i < m; i += nwarp) {  // B -= u w^H + w u^H, one row per warp
+      const float2 ui = u[i], wi = w[i];
+      float2* row = A + (j + 1 + i) * ld + (j + 1);
+      for (int k = lane; k < m; k += 32) {
+        const float2 uk = u[k], wk = w[k];
+        float2 bv = row[k];
+        bv.x -= ui.x * wk.x + ui.y * wk.y + wi.x * uk.x + wi.y * uk.y;
+        bv.y -= ui.y * wk.x - ui.x * wk.y + wi.y * uk.x - wi.x * uk.y;
+        row[k] = bv;
+      }
     }
     __syncthreads();
   }
@@ -333,7 +342,7 @@ static int zgemm(Ctx* c, int n, const double2* A, bool ah, const double2* B, dou
   return PARO_OK;
 }
 
-int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v) {
+int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refine_steps) {
   if (n < 2 || n > kMixMaxN) return eigh(c, n, a, w, v);
   const size_t nn = (size_t)n * n;
   double2* Af = static_cast<double2*>(ws_get(c, "em_A", nn * sizeof(double2)));
@@ -367,15 +376,13 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v) {
   k_tridiag_cta<<<1, 1024, sm1, c->stream>>>(n, Af, U32, d32, e32, ph32, tau32, ecx32);
   PARO_LAUNCH(c, "k_tridiag_cta");
   prof_end(c, "k_tridiag_cta", ev);
-  ev = prof_begin(c);
   int st = eigh_fp32_pieces(c, n, d32, e32, w32, U32, tau32, ph32, Z32, V32, info);
   if (st) return st;
-  prof_end(c, "eigh_fp32_rest", ev);
-  // 2. FP64 refinement (two steps), 3. Rayleigh-Ritz in the clusters
+  // 2. FP64 refinement (refine_steps steps), 3. Rayleigh-Ritz in the clusters
   ev = prof_begin(c);
   k_f2d<<<(int)((nn + 255) / 256), 256, 0, c->stream>>>((int)nn, V32, X);
   PARO_LAUNCH(c, "k_f2d");
-  for (int it = 0; it < 2; ++it) {
+  for (int it = 0; it < refine_steps; ++it) {
     if ((st = zgemm(c, n, X, true, X, G, false, part))) return st;    // G = X^H X
     if ((st = zgemm(c, n, Af, false, X, T1, false, part))) return st;  // T1 = A X
     if ((st = zgemm(c, n, X, true, T1, S, false, part))) return st;    // S = X^H A X
