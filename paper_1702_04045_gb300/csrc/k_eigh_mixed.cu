@@ -36,7 +36,8 @@ static const int kMixMaxN = 160;  // largest n whose FP32 matrix fits one CTA's 
 // ------------------------------------------------------------------------------------------------
 // Householder tridiagonalisation, one CTA, matrix (FP32) in shared memory. The same reflectors and outputs
 // as the FP64 kernels: u_j in U[j][0..m), tau, the complex off-diagonals ecx, d; then the phase diagonal D
-// (D_0 = 1, D_{j+1} = D_j conj(e_j)/|e_j|) and the real off-diagonals |e_j|. Input a: full Hermitian FP64.
+// (D_0 = 1, D_{j+1} = D_j conj(e_j)/|e_j|) and the real off-diagonals |e_j|. Input a: full Hermitian FP64;
+// only the lower triangle of the trailing matrix is kept current (the upper part is read as its conjugate).
 // ------------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_tridiag_cta(int n, const double2* __restrict__ a, float2* __restrict__ U,
                                                       float* __restrict__ d, float* __restrict__ e,
@@ -90,11 +91,19 @@ __global__ void __launch_bounds__(1024) k_tridiag_cta(int n, const double2* __re
     __syncthreads();
     const float t = s_t[j & 1];
     if (t == 0.f) continue;
-    for (int i = warp; i < m; i += nwarp) {  // p_i = t sum_k B_ik u_k
+    for (int i = warp; i < m; i += nwarp) {  // p_i = t sum_k B_ik u_k, B_ik = conj(B_ki) above the diagonal
       const float2* row = A + (j + 1 + i) * ld + (j + 1);
+      const float2* col = A + (j + 1) * ld + (j + 1 + i);
       float2 acc = make_float2(0.f, 0.f);
       for (int k = lane; k < m; k += 32) {
-        const float2 bv = row[k], uk = u[k];
+        float2 bv;
+        if (k <= i) {
+          bv = row[k];
+        } else {
+          bv = col[k * ld];
+          bv.y = -bv.y;
+        }
+        const float2 uk = u[k];
         acc.x = fmaf(bv.x, uk.x, fmaf(-bv.y, uk.y, acc.x));
         acc.y = fmaf(bv.x, uk.y, fmaf(bv.y, uk.x, acc.y));
       }
@@ -115,10 +124,10 @@ __global__ void __launch_bounds__(1024) k_tridiag_cta(int n, const double2* __re
       for (int i = lane; i < m; i += 32) w[i] = make_float2(w[i].x - K * u[i].x, w[i].y - K * u[i].y);
     }
     __syncthreads();
-    for (int i = warp; i < m; i += nwarp) {  // B -= u w^H + w u^H, one row per warp
+    for (int i = warp; i < m; i += nwarp) {  // B -= u w^H + w u^H on and below the diagonal, one row per warp
       const float2 ui = u[i], wi = w[i];
       float2* row = A + (j + 1 + i) * ld + (j + 1);
-      for (int k = lane; k < m; k += 32) {
+      for (int k = lane; k <= i; k += 32) {
         const float2 uk = u[k], wk = w[k];
         float2 bv = row[k];
         bv.x -= ui.x * wk.x + ui.y * wk.y + wi.x * uk.x + wi.y * uk.y;

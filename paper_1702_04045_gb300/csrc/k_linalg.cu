@@ -24,10 +24,20 @@ template <typename TO, typename TI> __device__ __forceinline__ cplx<TO> cvt(cplx
 // rows ty + 16 i and columns tx + 16 j), K split over gridDim.z into fixed slices of 16-wide steps.
 // part[z][m][n] receives the slice sums (complex double). R is chosen per call to minimise padding.
 // ACC = double: every product and sum in FP64. ACC = float: FP32 sums over the K slice, or with CARRY the
-// 16 products of one K step are summed in FP32 and that partial sum is carried into FP64 registers, so
-// the FP32 rounding is that of a 16-term sum (the size of the rounding already in FP32 operands) and
-// does not grow with K.
+// 16 products of one K step are summed in FP32 and the step sums are added into an unevaluated pair
+// hi + lo of FP32 values (error-free two-sum, Knuth; lo gathers the rounding error of every addition),
+// so the FP32 rounding is that of a 16-term sum (the size of the rounding already in FP32 operands) and
+// does not grow with K, without FP64 instructions in the loop (FP64 issues at 1/64 of the FP32 rate here).
 // ------------------------------------------------------------------------------------------------
+// hi + lo += x with the rounding error of hi + x kept exactly (two-sum: six FP32 operations, no branch)
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float ap = s - bp;
+  lo += (hi - ap) + (x - bp);
+  hi = s;
+}
+
 template <typename TA, typename TB, typename ACC, int R, bool CARRY>
 __global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kslice, const cplx<TA>* __restrict__ A,
                                                  int lda, const cplx<TB>* __restrict__ B, int ldb,
@@ -40,13 +50,13 @@ __global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kslice
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   constexpr bool kCarry = CARRY && sizeof(ACC) == 4;
   cplx<ACC> acc[R][R];
-  double2 carry[R][R];
+  float2 chi[R][R], clo[R][R];  // CARRY: running sum hi + lo
 #pragma unroll
   for (int i = 0; i < R; ++i)
 #pragma unroll
     for (int j = 0; j < R; ++j) {
       acc[i][j] = mk<ACC>(0, 0);
-      carry[i][j] = make_double2(0.0, 0.0);
+      chi[i][j] = clo[i][j] = make_float2(0.f, 0.f);
     }
   for (int kk = k0; kk < k1; kk += 16) {
 #pragma unroll
@@ -81,8 +91,8 @@ __global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kslice
       for (int i = 0; i < R; ++i)
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-          carry[i][j].x += (double)acc[i][j].x;
-          carry[i][j].y += (double)acc[i][j].y;
+          two_sum_acc(chi[i][j].x, clo[i][j].x, (float)acc[i][j].x);
+          two_sum_acc(chi[i][j].y, clo[i][j].y, (float)acc[i][j].y);
           acc[i][j] = mk<ACC>(0, 0);
         }
     }
@@ -96,7 +106,8 @@ __global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kslice
       const int m = tm + ty + 16 * i, n = tn + tx + 16 * j;
       if (m < M && n < N)
         pz[(size_t)m * N + n] =
-            kCarry ? carry[i][j] : make_double2((double)acc[i][j].x, (double)acc[i][j].y);
+            kCarry ? make_double2((double)chi[i][j].x + (double)clo[i][j].x, (double)chi[i][j].y + (double)clo[i][j].y)
+                   : make_double2((double)acc[i][j].x, (double)acc[i][j].y);
     }
 }
 
@@ -322,6 +333,109 @@ __global__ void __launch_bounds__(256) k_gemm_wx(int M, int N, int K, const doub
   }
 }
 
+// FP32 form: Y = beta Y + W^T X with every output row of a (16 RM)-row block in one CTA, so the long X
+// (K x N_pw) is read once per row block. 256 threads = 16 x 16, thread (ty, tx) holds rows ty + 16 i
+// (i < RM) and columns tx + 16 j (j < RN): RM + RN shared-memory loads per RM RN complex products.
+template <int RM, int RN>
+__global__ void __launch_bounds__(256) k_gemm_wx32(int M, int N, int K, const double2* __restrict__ W, int ldw,
+                                                   int wt, const double* __restrict__ s,
+                                                   const float2* __restrict__ X, int ldx, float2* __restrict__ Y,
+                                                   int ldy, float beta) {
+  constexpr int TM = 16 * RM, TN = 16 * RN;
+  const int tm = blockIdx.y * TM, tn = blockIdx.x * TN;
+  __shared__ float2 Ws[16][TM];
+  __shared__ float2 Xs[16][TN];
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  float2 acc[RM][RN];
+#pragma unroll
+  for (int i = 0; i < RM; ++i)
+#pragma unroll
+    for (int j = 0; j < RN; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int i = tid; i < 16 * TM; i += 256) {
+      int kx, r;
+      if (wt) {  // W[m][k]: consecutive threads along k
+        r = i >> 4;
+        kx = i & 15;
+      } else {   // W[k][m]: consecutive threads along m
+        kx = i / TM;
+        r = i - kx * TM;
+      }
+      const int gk = k0 + kx, gm = tm + r;
+      double2 w = make_double2(0.0, 0.0);
+      if (gk < K && gm < M) {
+        w = wt ? W[(size_t)gm * ldw + gk] : W[(size_t)gk * ldw + gm];
+        if (s) w = cscale(w, s[gk]);
+      }
+      Ws[kx][r] = make_float2((float)w.x, (float)w.y);
+    }
+    for (int i = tid; i < 16 * TN; i += 256) {
+      const int kx = i / TN, cc = i - kx * TN, gk = k0 + kx, gn = tn + cc;
+      Xs[kx][cc] = (gk < K && gn < N) ? X[(size_t)gk * ldx + gn] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kx = 0; kx < 16; ++kx) {
+      float2 x[RN], w[RM];
+#pragma unroll
+      for (int j = 0; j < RN; ++j) x[j] = Xs[kx][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < RM; ++i) w[i] = Ws[kx][ty + 16 * i];
+#pragma unroll
+      for (int i = 0; i < RM; ++i)
+#pragma unroll
+        for (int j = 0; j < RN; ++j) {
+          acc[i][j].x = fmaf(w[i].x, x[j].x, acc[i][j].x);
+          acc[i][j].x = fmaf(-w[i].y, x[j].y, acc[i][j].x);
+          acc[i][j].y = fmaf(w[i].x, x[j].y, acc[i][j].y);
+          acc[i][j].y = fmaf(w[i].y, x[j].x, acc[i][j].y);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < RM; ++i) {
+    const int m = tm + ty + 16 * i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < RN; ++j) {
+      const int n = tn + tx + 16 * j;
+      if (n >= N) continue;
+      float2 v = acc[i][j];
+      if (beta != 0.f) {
+        const float2 o = Y[(size_t)m * ldy + n];
+        v = make_float2(fmaf(beta, o.x, v.x), fmaf(beta, o.y, v.y));
+      }
+      Y[(size_t)m * ldy + n] = v;
+    }
+  }
+}
+
+// launch of k_gemm_wx32: RM = 9 (144-row blocks) unless M fits 64 rows; RN (32 or 64 columns) with the
+// smaller makespan in waves of 152 SMs x resident CTAs
+static int launch_wx32(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, const double* s,
+                       const float2* X, int ldx, float2* Y, int ldy, double beta) {
+  const bool big = M > 64;
+  const int tm = big ? 144 : 64;
+  const int mt = (M + tm - 1) / tm;
+  const long long s2 = (long long)mt * ((N + 31) / 32), s4 = (long long)mt * ((N + 63) / 64);
+  // resident CTAs per SM by register use: about 3 (RN = 2) and 2 (RN = 4) at RM = 9
+  const long long w2 = (s2 + 3 * 152 - 1) / (3 * 152) * 2, w4 = (s4 + 2 * 152 - 1) / (2 * 152) * 4;
+  const bool rn4 = w4 < w2;
+  const dim3 grid((N + (rn4 ? 63 : 31)) / (rn4 ? 64 : 32), mt);
+  const int iwt = wt ? 1 : 0;
+  const float fb = (float)beta;
+  if (big) {
+    if (rn4) k_gemm_wx32<9, 4><<<grid, 256, 0, c->stream>>>(M, N, K, W, ldw, iwt, s, X, ldx, Y, ldy, fb);
+    else k_gemm_wx32<9, 2><<<grid, 256, 0, c->stream>>>(M, N, K, W, ldw, iwt, s, X, ldx, Y, ldy, fb);
+  } else {
+    if (rn4) k_gemm_wx32<4, 4><<<grid, 256, 0, c->stream>>>(M, N, K, W, ldw, iwt, s, X, ldx, Y, ldy, fb);
+    else k_gemm_wx32<4, 2><<<grid, 256, 0, c->stream>>>(M, N, K, W, ldw, iwt, s, X, ldx, Y, ldy, fb);
+  }
+  PARO_LAUNCH(c, "k_gemm_wx32");
+  return PARO_OK;
+}
+
 template <typename TX, typename TY>
 int gemm_wx(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, const double* s, const cplx<TX>* X,
             int ldx, cplx<TY>* Y, int ldy, double beta) {
@@ -336,6 +450,11 @@ int gemm_wx(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, con
       prof_end(c, "k_gemm_wx_tc", ev);
       return PARO_OK;
     }
+    cudaEvent_t ev = prof_begin(c);
+    int st = launch_wx32(c, M, N, K, W, ldw, wt, s, X, ldx, Y, ldy, beta);
+    if (st) return st;
+    prof_end(c, "k_gemm_wx<f32>", ev);
+    return PARO_OK;
   }
   cudaEvent_t ev = prof_begin(c);
   k_gemm_wx<TX, TY><<<dim3((N + 63) / 64, (M + 31) / 32), 256, 0, c->stream>>>(M, N, K, W, ldw, wt ? 1 : 0, s, X,
