@@ -24,9 +24,24 @@ static const int kTcM = 128;       // rows of A per CTA = TMEM lanes
 static const int kTcThreads = 256;
 static const uint32_t kTcPolls = 1u << 24;
 
-// byte offset of (row, 16-byte chunk) in a no-swizzle K-major tile with ch chunks per row
+// byte offset of (row, 16-byte chunk) in a K-major tile with ch chunks per row: 128-byte swizzle when a
+// row is exactly 128 bytes (ch = 8: 8-row atoms of 1024 bytes, chunk c of row r at c ^ (r % 8)), else the
+// no-swizzle core-matrix layout (8 rows x 16 bytes contiguous)
 __device__ __forceinline__ uint32_t tc_off(int row, int chunk, int ch) {
+  if (ch == 8) return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
   return (uint32_t)(((row >> 3) * ch + chunk) * 128 + (row & 7) * 16);
+}
+
+// descriptor of the K step s2 (8 TF32 values) of a tile at shared address base, layout as in tc_off
+__device__ __forceinline__ uint64_t tc_desc(uint32_t base, int s2, int ch) {
+  if (ch == 8) return tc::smem_desc_sw128(base + (uint32_t)s2 * 32u);
+  return tc::smem_desc(base + (uint32_t)s2 * 256u, 128u, (uint32_t)ch * 128u);
+}
+
+// dynamic shared memory rounded up to the 1024-byte alignment of the swizzle atoms (1 KB extra allocated)
+__device__ __forceinline__ unsigned char* tc_align1024(unsigned char* p) {
+  const uint32_t a = tc::smem_addr(p);
+  return p + ((1024u - (a & 1023u)) & 1023u);
 }
 
 // split (v0, v1) into hi and lo TF32 quadruples (re0, im0, re1, im1)
@@ -44,9 +59,10 @@ struct TcPipe {
   uint64_t* bar;      // [2]
   uint32_t uses[2];   // completed uses waited for, per buffer
   int ok;
+  const int* fail;    // shared flag set by the MMA-issuing thread (its own copy wait gave up), or null
   __device__ __forceinline__ bool wait_buffer(int b) {  // all threads; uniform result
     const int done = tc::mbar_wait(&bar[b], uses[b] & 1u, kTcPolls) ? 1 : 0;
-    ok = __syncthreads_and(done && ok);
+    ok = __syncthreads_and(done && ok && !(fail && *fail));
     if (ok) ++uses[b];
     return ok;
   }
@@ -58,7 +74,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int 
                                                               const float2* __restrict__ A, int lda,
                                                               const float2* __restrict__ B, int ldb,
                                                               double2* __restrict__ part, int* __restrict__ err) {
-  extern __shared__ __align__(128) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
+  unsigned char* smem = tc_align1024(smem_dyn);
   const int ch = KC / 2;  // 16-byte chunks per row per stage
   const int A_BYTES = kTcM * ch * 16, B_BYTES = NT * ch * 16, STAGE = 4 * A_BYTES + 2 * B_BYTES;
   __shared__ uint64_t mbar[2];
@@ -81,7 +98,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int 
   tc::tc_fence_after();
   const uint32_t dR = tmem_base, dI = tmem_base + ncols / 2;
   const uint32_t idesc = tc::idesc_tf32(128, (uint32_t)NT);
-  TcPipe pipe{mbar, {0u, 0u}, 1};
+  TcPipe pipe{mbar, {0u, 0u}, 1, nullptr};
   int nst = 0, issued[2] = {0, 0};
   for (int kk = k0; kk < k1; kk += KC, ++nst) {
     const int b = nst & 1;
@@ -161,12 +178,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int 
       tc::tc_fence_after();
       const uint32_t aH = tc::smem_addr(sAh), aL = tc::smem_addr(sAl), apH = tc::smem_addr(sAph),
                      apL = tc::smem_addr(sApl), bH = tc::smem_addr(sBh), bL = tc::smem_addr(sBl);
-      const uint32_t lbo = 128u, sbo = (uint32_t)ch * 128u;
-      for (int s2 = 0; s2 < ch / 2; ++s2) {
-        const uint32_t off = (uint32_t)s2 * 256u;  // two 16-byte chunks (8 TF32) per MMA
-        const uint64_t dAh = tc::smem_desc(aH + off, lbo, sbo), dAl = tc::smem_desc(aL + off, lbo, sbo);
-        const uint64_t dApH = tc::smem_desc(apH + off, lbo, sbo), dApL = tc::smem_desc(apL + off, lbo, sbo);
-        const uint64_t dBh = tc::smem_desc(bH + off, lbo, sbo), dBl = tc::smem_desc(bL + off, lbo, sbo);
+      for (int s2 = 0; s2 < ch / 2; ++s2) {  // two 16-byte chunks (8 TF32) per MMA
+        const uint64_t dAh = tc_desc(aH, s2, ch), dAl = tc_desc(aL, s2, ch);
+        const uint64_t dApH = tc_desc(apH, s2, ch), dApL = tc_desc(apL, s2, ch);
+        const uint64_t dBh = tc_desc(bH, s2, ch), dBl = tc_desc(bL, s2, ch);
         const uint32_t acc = (nst > 0 || s2 > 0) ? 1u : 0u;
         tc::mma_tf32(dR, dAh, dBh, idesc, acc);
         tc::mma_tf32(dR, dAh, dBl, idesc, 1u);
@@ -261,11 +276,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_wx_tc(int M, int N, int 
                                                               const float2* __restrict__ X, int ldx,
                                                               float2* __restrict__ Y, int ldy, float beta,
                                                               int* __restrict__ err) {
-  extern __shared__ __align__(128) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
+  unsigned char* smem = tc_align1024(smem_dyn);
   const int ch = KC / 2, nstage = (K + KC - 1) / KC;
   const int A_BYTES = kTcM * ch * 16, B_BYTES = NT * ch * 16, STAGE = 2 * A_BYTES + 4 * B_BYTES;
-  __shared__ uint64_t mbar[2];
+  __shared__ uint64_t mbar[2], fbar[2];  // MMAs done / B tiles landed, per buffer
   __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n0 = blockIdx.x * kTcM, mt = blockIdx.y, m0 = mt * NT;
   const uint32_t ncols = NT <= 128 ? 256u : 512u;
@@ -276,6 +293,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_wx_tc(int M, int N, int 
   if (tid == 0) {
     tc::mbar_init(&mbar[0], 1);
     tc::mbar_init(&mbar[1], 1);
+    tc::mbar_init(&fbar[0], 1);
+    tc::mbar_init(&fbar[1], 1);
+    s_fail = 0;
     tc::fence_mbar_init();
   }
   tc::tc_fence_before();
@@ -284,8 +304,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_wx_tc(int M, int N, int 
   const uint32_t dR = tmem_base, dI = tmem_base + ncols / 2;
   const uint32_t idesc = tc::idesc_tf32(128, (uint32_t)NT);
   const size_t tile4 = (size_t)NT * ch;  // float4 per B variant per stage
-  TcPipe pipe{mbar, {0u, 0u}, 1};
+  TcPipe pipe{mbar, {0u, 0u}, 1, &s_fail};
   int issued[2] = {0, 0};
+  uint32_t fuses[2] = {0u, 0u};  // thread 0: completed phases of fbar
+  int pend[2] = {0, 0};           // thread 0: a bulk copy into this buffer not yet seen complete
+  const uint32_t bbytes = (uint32_t)(4 * B_BYTES);
   int nst = 0;
   for (; nst < nstage; ++nst) {
     const int b = nst & 1, kk = nst * KC;
@@ -294,35 +317,56 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_wx_tc(int M, int N, int 
     unsigned char* sAh = smem + b * STAGE;
     unsigned char* sAl = sAh + A_BYTES;
     unsigned char* sB = sAl + A_BYTES;  // 4 variant tiles: Re hi, Re lo, Im hi, Im lo
-    for (int i = tid; i < kTcM * ch; i += kTcThreads) {  // consecutive threads: consecutive n (rows)
-      const int r = i % kTcM, c = i / kTcM;
-      const int gn = n0 + r, k0 = kk + 2 * c;
-      float2 v0 = make_float2(0.f, 0.f), v1 = v0;
-      if (gn < N) {
-        if (k0 < K) v0 = X[(size_t)k0 * ldx + gn];
-        if (k0 + 1 < K) v1 = X[(size_t)(k0 + 1) * ldx + gn];
-      }
-      float4 h, l;
-      tc_split(v0, v1, h, l);
-      const uint32_t o = tc_off(r, c, ch);
-      *reinterpret_cast<float4*>(sAh + o) = h;
-      *reinterpret_cast<float4*>(sAl + o) = l;
+    if (tid == 0) {  // the presplit B tiles of this stage: one bulk copy (contiguous in Wp)
+      tc::mbar_arrive_expect_tx(&fbar[b], bbytes);
+      tc::bulk_g2s(sB, Wp + (((size_t)mt * nstage + nst) * 4) * tile4, bbytes, &fbar[b]);
+      pend[b] = 1;
     }
-    const float4* src = Wp + (((size_t)mt * nstage + nst) * 4) * tile4;
-    float4* dst = reinterpret_cast<float4*>(sB);
-    for (size_t i = tid; i < 4 * tile4; i += kTcThreads) dst[i] = src[i];
+    {  // consecutive threads: consecutive n (rows); all loads before any split or store
+      constexpr int UA = kTcM * 8 / kTcThreads;
+      float2 va[UA][2];
+#pragma unroll
+      for (int t = 0; t < UA; ++t) {
+        const int i = tid + t * kTcThreads;
+        va[t][0] = va[t][1] = make_float2(0.f, 0.f);
+        if (i < kTcM * ch) {
+          const int r = i % kTcM, c = i / kTcM;
+          const int gn = n0 + r, k0 = kk + 2 * c;
+          if (gn < N) {
+            if (k0 < K) va[t][0] = X[(size_t)k0 * ldx + gn];
+            if (k0 + 1 < K) va[t][1] = X[(size_t)(k0 + 1) * ldx + gn];
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < UA; ++t) {
+        const int i = tid + t * kTcThreads;
+        if (i >= kTcM * ch) continue;
+        const int r = i % kTcM, c = i / kTcM;
+        float4 h, l;
+        tc_split(va[t][0], va[t][1], h, l);
+        const uint32_t o = tc_off(r, c, ch);
+        *reinterpret_cast<float4*>(sAh + o) = h;
+        *reinterpret_cast<float4*>(sAl + o) = l;
+      }
+    }
     tc::fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
+      const bool landed = tc::mbar_wait(&fbar[b], fuses[b] & 1u, kTcPolls);
+      if (landed) {
+        ++fuses[b];
+        pend[b] = 0;
+      } else {
+        s_fail = 1;  // no MMAs for this stage; the commit below still arrives
+      }
       tc::tc_fence_after();
       const uint32_t aH = tc::smem_addr(sAh), aL = tc::smem_addr(sAl), bb = tc::smem_addr(sB);
       const uint32_t rH = bb, rL = bb + B_BYTES, iH = bb + 2 * B_BYTES, iL = bb + 3 * B_BYTES;
-      const uint32_t lbo = 128u, sbo = (uint32_t)ch * 128u;
-      for (int s2 = 0; s2 < ch / 2; ++s2) {
-        const uint32_t off = (uint32_t)s2 * 256u;
-        const uint64_t dAh = tc::smem_desc(aH + off, lbo, sbo), dAl = tc::smem_desc(aL + off, lbo, sbo);
-        const uint64_t dRh = tc::smem_desc(rH + off, lbo, sbo), dRl = tc::smem_desc(rL + off, lbo, sbo);
-        const uint64_t dIh = tc::smem_desc(iH + off, lbo, sbo), dIl = tc::smem_desc(iL + off, lbo, sbo);
+      for (int s2 = 0; landed && s2 < ch / 2; ++s2) {
+        const uint64_t dAh = tc_desc(aH, s2, ch), dAl = tc_desc(aL, s2, ch);
+        const uint64_t dRh = tc_desc(rH, s2, ch), dRl = tc_desc(rL, s2, ch);
+        const uint64_t dIh = tc_desc(iH, s2, ch), dIl = tc_desc(iL, s2, ch);
         const uint32_t acc = (nst > 0 || s2 > 0) ? 1u : 0u;
         tc::mma_tf32(dR, dAh, dRh, idesc, acc);
         tc::mma_tf32(dR, dAh, dRl, idesc, 1u);
@@ -341,6 +385,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_wx_tc(int M, int N, int 
     for (int b = 0; b < 2; ++b)
       if (issued[b]) tc::mbar_wait(&mbar[b], pipe.uses[b] & 1u, kTcPolls);
   }
+  if (tid == 0)  // a bulk copy still in flight after a time-out lands before the CTA leaves
+    for (int b = 0; b < 2; ++b)
+      if (pend[b]) tc::mbar_wait(&fbar[b], fuses[b] & 1u, kTcPolls);
   const int ok = pipe.ok;
   tc::tc_fence_after();
   const int lq = warp & 3, half = warp >> 2;
@@ -381,8 +428,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_wx_tc(int M, int N, int 
 static size_t cn_stage_bytes(int NT, int KC) { return (size_t)(4 * kTcM + 2 * NT) * (KC / 2) * 16; }
 static size_t wx_stage_bytes(int NT, int KC) { return (size_t)(2 * kTcM + 4 * NT) * (KC / 2) * 16; }
 static const size_t kTcSmemMax = 220 * 1024;
-static int cn_kc(int NT) { return 2 * cn_stage_bytes(NT, 16) <= kTcSmemMax ? 16 : 8; }
-static int wx_kc(int NT) { return 2 * wx_stage_bytes(NT, 16) <= kTcSmemMax ? 16 : 8; }
+static const size_t kTcAlignPad = 1024;  // room to align the stage buffers to 1024 bytes
+static int cn_kc(int NT) { return 2 * cn_stage_bytes(NT, 16) + kTcAlignPad <= kTcSmemMax ? 16 : 8; }
+static int wx_kc(int NT) { return 2 * wx_stage_bytes(NT, 16) + kTcAlignPad <= kTcSmemMax ? 16 : 8; }
 
 static int set_smem_attr(Ctx* c, const void* k, int* dev_done) {
   int dev = 0;
@@ -410,7 +458,7 @@ int gemm_wx_tc(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, 
     k_wx_presplit<<<dim3(64, mtiles), 256, 0, c->stream>>>(M, K, nt, kc, W, ldw, wt ? 1 : 0, s, Wp);
     PARO_LAUNCH(c, "k_wx_presplit");
   }
-  k_gemm_wx_tc<<<dim3((N + kTcM - 1) / kTcM, mtiles), kTcThreads, 2 * wx_stage_bytes(nt, kc), c->stream>>>(
+  k_gemm_wx_tc<<<dim3((N + kTcM - 1) / kTcM, mtiles), kTcThreads, 2 * wx_stage_bytes(nt, kc) + kTcAlignPad, c->stream>>>(
       M, N, K, nt, kc, Wp, X, ldx, Y, ldy, (float)beta, err);
   PARO_LAUNCH(c, "k_gemm_wx_tc");
   return PARO_OK;
@@ -455,7 +503,7 @@ int gemm_cn_tc(Ctx* c, int M, int N, int K, const float2* A, int lda, const floa
   static int attr_dev = -1;
   int st;
   if ((st = set_smem_attr(c, (const void*)k_gemm_cn_tc, &attr_dev))) return st;
-  k_gemm_cn_tc<<<dim3(mtiles, ntiles, nz), kTcThreads, 2 * cn_stage_bytes(nt, kc), c->stream>>>(
+  k_gemm_cn_tc<<<dim3(mtiles, ntiles, nz), kTcThreads, 2 * cn_stage_bytes(nt, kc) + kTcAlignPad, c->stream>>>(
       M, N, K, kslice, nt, kc, A, lda, B, ldb, part, err);
   PARO_LAUNCH(c, "k_gemm_cn_tc");
   return PARO_OK;

@@ -43,6 +43,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
   return false;
 }
 
+// one arrival that also expects `bytes` of asynchronous copies on the current phase
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+// bulk copy global -> shared (this CTA) of `bytes` (multiple of 16, both addresses 16-byte aligned),
+// completing as transaction bytes on `bar`
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
 // ---- fences ----
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
@@ -70,6 +84,19 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
   d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// The same for the 128-byte swizzled K-major layout: rows of 128 bytes (32 TF32 values), 8-row atoms of
+// 1024 bytes (stride-dimension offset), the 16-byte chunk c of row r stored at chunk c ^ (r % 8); atoms
+// 1024-byte aligned. A K step inside the row advances the start address by its byte width.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;            // leading-dimension offset (unused inside a 128-byte swizzle row)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride between 8-row atoms
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
   return d;
 }
 
