@@ -336,9 +336,20 @@ __global__ void __launch_bounds__(256) k_gemm_wx(int M, int N, int K, const doub
 // FP32 form: Y = beta Y + W^T X with every output row of a (16 RM)-row block in one CTA, so the long X
 // (K x N_pw) is read once per row block. 256 threads = 16 x 16, thread (ty, tx) holds rows ty + 16 i
 // (i < RM) and columns tx + 16 j (j < RN): RM + RN shared-memory loads per RM RN complex products.
+// Wf[k][m] = (float)(s_k W(k, m)), K x M: the small matrix converted once per call, because a conversion
+// or product in FP64 per staged element would occupy GB300's FP64 pipe longer than the product's FMAs
+__global__ void k_w_to_f32(int M, int K, const double2* __restrict__ W, int ldw, int wt,
+                           const double* __restrict__ s, float2* __restrict__ Wf) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M * K; i += gridDim.x * blockDim.x) {
+    const int k = i / M, m = i - k * M;
+    double2 w = wt ? W[(size_t)m * ldw + k] : W[(size_t)k * ldw + m];
+    if (s) w = cscale(w, s[k]);
+    Wf[i] = make_float2((float)w.x, (float)w.y);
+  }
+}
+
 template <int RM, int RN>
-__global__ void __launch_bounds__(256) k_gemm_wx32(int M, int N, int K, const double2* __restrict__ W, int ldw,
-                                                   int wt, const double* __restrict__ s,
+__global__ void __launch_bounds__(256) k_gemm_wx32(int M, int N, int K, const float2* __restrict__ Wf,
                                                    const float2* __restrict__ X, int ldx, float2* __restrict__ Y,
                                                    int ldy, float beta) {
   constexpr int TM = 16 * RM, TN = 16 * RN;
@@ -353,21 +364,8 @@ __global__ void __launch_bounds__(256) k_gemm_wx32(int M, int N, int K, const do
     for (int j = 0; j < RN; ++j) acc[i][j] = make_float2(0.f, 0.f);
   for (int k0 = 0; k0 < K; k0 += 16) {
     for (int i = tid; i < 16 * TM; i += 256) {
-      int kx, r;
-      if (wt) {  // W[m][k]: consecutive threads along k
-        r = i >> 4;
-        kx = i & 15;
-      } else {   // W[k][m]: consecutive threads along m
-        kx = i / TM;
-        r = i - kx * TM;
-      }
-      const int gk = k0 + kx, gm = tm + r;
-      double2 w = make_double2(0.0, 0.0);
-      if (gk < K && gm < M) {
-        w = wt ? W[(size_t)gm * ldw + gk] : W[(size_t)gk * ldw + gm];
-        if (s) w = cscale(w, s[gk]);
-      }
-      Ws[kx][r] = make_float2((float)w.x, (float)w.y);
+      const int kx = i / TM, r = i - kx * TM, gk = k0 + kx, gm = tm + r;
+      Ws[kx][r] = (gk < K && gm < M) ? Wf[(size_t)gk * M + gm] : make_float2(0.f, 0.f);
     }
     for (int i = tid; i < 16 * TN; i += 256) {
       const int kx = i / TN, cc = i - kx * TN, gk = k0 + kx, gn = tn + cc;
@@ -414,7 +412,7 @@ __global__ void __launch_bounds__(256) k_gemm_wx32(int M, int N, int K, const do
 // launch of k_gemm_wx32: RM = 9 (144-row blocks) unless M fits 64 rows; RN (32 or 64 columns) with the
 // smaller makespan in waves of 152 SMs x resident CTAs
 static int launch_wx32(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, const double* s,
-                       const float2* X, int ldx, float2* Y, int ldy, double beta) {
+                       const float2* X, int ldx, float2* Y, int ldy, double beta, float2* Wf) {
   const bool big = M > 64;
   const int tm = big ? 144 : 64;
   const int mt = (M + tm - 1) / tm;
@@ -423,14 +421,19 @@ static int launch_wx32(Ctx* c, int M, int N, int K, const double2* W, int ldw, b
   const long long w2 = (s2 + 3 * 152 - 1) / (3 * 152) * 2, w4 = (s4 + 2 * 152 - 1) / (2 * 152) * 4;
   const bool rn4 = w4 < w2;
   const dim3 grid((N + (rn4 ? 63 : 31)) / (rn4 ? 64 : 32), mt);
-  const int iwt = wt ? 1 : 0;
   const float fb = (float)beta;
+  if (!Wf) Wf = static_cast<float2*>(ws_get(c, "wx32_w", (size_t)M * K * sizeof(float2)));
+  if (!Wf) return PARO_ERR_CUDA;
+  if (K > 0) {
+    k_w_to_f32<<<std::min((M * K + 255) / 256, 304), 256, 0, c->stream>>>(M, K, W, ldw, wt ? 1 : 0, s, Wf);
+    PARO_LAUNCH(c, "k_w_to_f32");
+  }
   if (big) {
-    if (rn4) k_gemm_wx32<9, 4><<<grid, 256, 0, c->stream>>>(M, N, K, W, ldw, iwt, s, X, ldx, Y, ldy, fb);
-    else k_gemm_wx32<9, 2><<<grid, 256, 0, c->stream>>>(M, N, K, W, ldw, iwt, s, X, ldx, Y, ldy, fb);
+    if (rn4) k_gemm_wx32<9, 4><<<grid, 256, 0, c->stream>>>(M, N, K, Wf, X, ldx, Y, ldy, fb);
+    else k_gemm_wx32<9, 2><<<grid, 256, 0, c->stream>>>(M, N, K, Wf, X, ldx, Y, ldy, fb);
   } else {
-    if (rn4) k_gemm_wx32<4, 4><<<grid, 256, 0, c->stream>>>(M, N, K, W, ldw, iwt, s, X, ldx, Y, ldy, fb);
-    else k_gemm_wx32<4, 2><<<grid, 256, 0, c->stream>>>(M, N, K, W, ldw, iwt, s, X, ldx, Y, ldy, fb);
+    if (rn4) k_gemm_wx32<4, 4><<<grid, 256, 0, c->stream>>>(M, N, K, Wf, X, ldx, Y, ldy, fb);
+    else k_gemm_wx32<4, 2><<<grid, 256, 0, c->stream>>>(M, N, K, Wf, X, ldx, Y, ldy, fb);
   }
   PARO_LAUNCH(c, "k_gemm_wx32");
   return PARO_OK;
@@ -438,7 +441,7 @@ static int launch_wx32(Ctx* c, int M, int N, int K, const double2* W, int ldw, b
 
 template <typename TX, typename TY>
 int gemm_wx(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, const double* s, const cplx<TX>* X,
-            int ldx, cplx<TY>* Y, int ldy, double beta) {
+            int ldx, cplx<TY>* Y, int ldy, double beta, float2* wf) {
   if (M <= 0 || N <= 0) return PARO_OK;
   if constexpr (sizeof(TX) == 4 && sizeof(TY) == 4) {
     if (c->tc_scope && tc_enabled()) {
@@ -451,7 +454,7 @@ int gemm_wx(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, con
       return PARO_OK;
     }
     cudaEvent_t ev = prof_begin(c);
-    int st = launch_wx32(c, M, N, K, W, ldw, wt, s, X, ldx, Y, ldy, beta);
+    int st = launch_wx32(c, M, N, K, W, ldw, wt, s, X, ldx, Y, ldy, beta, wf);
     if (st) return st;
     prof_end(c, "k_gemm_wx<f32>", ev);
     return PARO_OK;
@@ -751,11 +754,11 @@ template int gemm_cn<double, double, double>(Ctx*, int, int, int, const double2*
 template int gemm_cn<float, float, float>(Ctx*, int, int, int, const float2*, int, const float2*, int, double2*, int,
                                           bool, bool);
 template int gemm_wx<double, double>(Ctx*, int, int, int, const double2*, int, bool, const double*, const double2*,
-                                     int, double2*, int, double);
+                                     int, double2*, int, double, float2*);
 template int gemm_wx<float, float>(Ctx*, int, int, int, const double2*, int, bool, const double*, const float2*, int,
-                                   float2*, int, double);
+                                   float2*, int, double, float2*);
 template int gemm_wx<float, double>(Ctx*, int, int, int, const double2*, int, bool, const double*, const float2*,
-                                    int, double2*, int, double);
+                                    int, double2*, int, double, float2*);
 template int band_norms<double>(Ctx*, int, int, const double2*, int, double*);
 template int band_norms<float>(Ctx*, int, int, const float2*, int, double*);
 template int convert<double, float>(Ctx*, size_t, const double2*, float2*);

@@ -161,10 +161,11 @@ int gemm_cn(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, const cplx<
             double2* C, int ldc, bool herm, bool carry = false);
 // Y[m][n] = beta Y[m][n] + sum_k s_k W(k, m) X[k][n]; W: complex double, element (k, m) at W[k*ldw + m]
 // (or at W[m*ldw + k] when wt); s: device double[K] or nullptr (1); X: K x N (ldx) of TX;
-// Y: M x N (ldy) of TY; accumulation in TY.
+// Y: M x N (ldy) of TY; accumulation in TY. wf: device scratch of M K float2 for the FP32 form's converted
+// W (nullptr: a workspace of the context, allocated on first use).
 template <typename TX, typename TY>
 int gemm_wx(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, const double* s, const cplx<TX>* X,
-            int ldx, cplx<TY>* Y, int ldy, double beta);
+            int ldx, cplx<TY>* Y, int ldy, double beta, float2* wf = nullptr);
 // gemm_cn with the K-slice partials in caller memory (part_elems complex doubles); allocates nothing.
 template <typename TA, typename TB, typename ACC>
 int gemm_cn_scratch(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb,
