@@ -42,13 +42,38 @@ template <typename TA, typename TB, typename ACC, int R, bool CARRY>
 __global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kslice, const cplx<TA>* __restrict__ A,
                                                  int lda, const cplx<TB>* __restrict__ B, int ldb,
                                                  double2* __restrict__ part, int herm) {
-  constexpr int TILE = 16 * R;
+  constexpr int TILE = 16 * R, LD = TILE + 1, STG = 2 * 16 * LD;  // elements per stage (A then B)
   const int tm = blockIdx.y * TILE, tn = blockIdx.x * TILE;
   if (herm && tm > tn) return;
   const int k0 = blockIdx.z * kslice, k1 = min(K, k0 + kslice);
-  __shared__ cplx<ACC> As[16][TILE + 1], Bs[16][TILE + 1];
+  extern __shared__ __align__(16) unsigned char cn_smem_raw[];
+  cplx<ACC>* cn_smem = reinterpret_cast<cplx<ACC>*>(cn_smem_raw);  // two stages of As[16][LD], Bs[16][LD]
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   constexpr bool kCarry = CARRY && sizeof(ACC) == 4;
+  static_assert(sizeof(TA) == sizeof(ACC) && sizeof(TB) == sizeof(ACC), "operands are staged as stored");
+  constexpr int EB = (int)sizeof(cplx<ACC>);
+  // K step kk into stage buffer st by asynchronous copies (zero-filled outside); A is kept unconjugated
+  auto stage = [&](int kk, int st) {
+    cplx<ACC>* As = cn_smem + st * STG;
+    cplx<ACC>* Bs = As + 16 * LD;
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const int i = tid + 256 * t;
+      const int r = i >> 4, kx = i & 15, gk = kk + kx;
+      const int gm = tm + r, gn = tn + r;
+      const bool ia = gm < M && gk < k1, ib = gn < N && gk < k1;
+      const cplx<TA>* sa = ia ? A + (size_t)gm * lda + gk : A;
+      const cplx<TB>* sb = ib ? B + (size_t)gn * ldb + gk : B;
+      if constexpr (EB == 8) {
+        cp_async8(As + kx * LD + r, sa, ia ? 8 : 0);
+        cp_async8(Bs + kx * LD + r, sb, ib ? 8 : 0);
+      } else {
+        cp_async16(As + kx * LD + r, sa, ia ? 16 : 0);
+        cp_async16(Bs + kx * LD + r, sb, ib ? 16 : 0);
+      }
+    }
+    cp_async_commit();
+  };
   cplx<ACC> acc[R][R];
   float2 chi[R][R], clo[R][R];  // CARRY: running sum hi + lo
 #pragma unroll
@@ -58,32 +83,34 @@ __global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kslice
       acc[i][j] = mk<ACC>(0, 0);
       chi[i][j] = clo[i][j] = make_float2(0.f, 0.f);
     }
-  for (int kk = k0; kk < k1; kk += 16) {
-#pragma unroll
-    for (int t = 0; t < R; ++t) {
-      const int i = tid + 256 * t;
-      const int r = i >> 4, kx = i & 15, gk = kk + kx;
-      const int gm = tm + r, gn = tn + r;
-      As[kx][r] = (gm < M && gk < k1) ? cconj(cvt<ACC, TA>(A[(size_t)gm * lda + gk])) : mk<ACC>(0, 0);
-      Bs[kx][r] = (gn < N && gk < k1) ? cvt<ACC, TB>(B[(size_t)gn * ldb + gk]) : mk<ACC>(0, 0);
+  const int nk = k1 > k0 ? (k1 - k0 + 15) / 16 : 0;
+  if (nk > 0) stage(k0, 0);
+  for (int kt = 0; kt < nk; ++kt) {
+    if (kt + 1 < nk) {
+      stage(k0 + 16 * (kt + 1), (kt + 1) & 1);  // the other buffer: its readers passed the last barrier
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
+    const cplx<ACC>* As = cn_smem + (kt & 1) * STG;
+    const cplx<ACC>* Bs = As + 16 * LD;
 #pragma unroll 4
     for (int kx = 0; kx < 16; ++kx) {
       cplx<ACC> a[R], b[R];
 #pragma unroll
       for (int i = 0; i < R; ++i) {
-        a[i] = As[kx][ty + 16 * i];
-        b[i] = Bs[kx][tx + 16 * i];
+        a[i] = As[kx * LD + ty + 16 * i];
+        b[i] = Bs[kx * LD + tx + 16 * i];
       }
 #pragma unroll
       for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < R; ++j) {  // acc += a b, four fused multiply-adds
+        for (int j = 0; j < R; ++j) {  // acc += conj(a) b, four fused multiply-adds
           acc[i][j].x = fma(a[i].x, b[j].x, acc[i][j].x);
-          acc[i][j].x = fma(-a[i].y, b[j].y, acc[i][j].x);
+          acc[i][j].x = fma(a[i].y, b[j].y, acc[i][j].x);
           acc[i][j].y = fma(a[i].x, b[j].y, acc[i][j].y);
-          acc[i][j].y = fma(a[i].y, b[j].x, acc[i][j].y);
+          acc[i][j].y = fma(-a[i].y, b[j].x, acc[i][j].y);
         }
     }
     if (kCarry) {
@@ -164,15 +191,31 @@ static void split_k(int tiles, int K, size_t max_slices, int* nz_out, int* kslic
   *kslice_out = best_steps * 16;
 }
 
+// dynamic shared memory above the 48 KB default (the FP64 forms with R >= 3), set once per device
+template <typename TA, typename TB, typename ACC, int R, bool CARRY>
+static void cn_smem_attr(size_t sm) {
+  static int dev_done = -1;
+  int dev = 0;
+  if (sm <= 48 * 1024 || cudaGetDevice(&dev) != cudaSuccess || dev == dev_done) return;
+  if (cudaFuncSetAttribute(k_gemm_cn<TA, TB, ACC, R, CARRY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) ==
+      cudaSuccess)
+    dev_done = dev;
+}
+
 template <typename TA, typename TB, typename ACC, bool CARRY>
 static void launch_cn_r(int r, dim3 grid, cudaStream_t st, int M, int N, int K, int kslice, const cplx<TA>* A,
                         int lda, const cplx<TB>* B, int ldb, double2* part, int herm) {
-  if (r == 2)
-    k_gemm_cn<TA, TB, ACC, 2, CARRY><<<grid, 256, 0, st>>>(M, N, K, kslice, A, lda, B, ldb, part, herm);
-  else if (r == 3)
-    k_gemm_cn<TA, TB, ACC, 3, CARRY><<<grid, 256, 0, st>>>(M, N, K, kslice, A, lda, B, ldb, part, herm);
-  else
-    k_gemm_cn<TA, TB, ACC, 4, CARRY><<<grid, 256, 0, st>>>(M, N, K, kslice, A, lda, B, ldb, part, herm);
+  const size_t sm = (size_t)2 * 2 * 16 * (16 * r + 1) * sizeof(cplx<ACC>);  // two stages of A and B
+  if (r == 2) {
+    cn_smem_attr<TA, TB, ACC, 2, CARRY>(sm);
+    k_gemm_cn<TA, TB, ACC, 2, CARRY><<<grid, 256, sm, st>>>(M, N, K, kslice, A, lda, B, ldb, part, herm);
+  } else if (r == 3) {
+    cn_smem_attr<TA, TB, ACC, 3, CARRY>(sm);
+    k_gemm_cn<TA, TB, ACC, 3, CARRY><<<grid, 256, sm, st>>>(M, N, K, kslice, A, lda, B, ldb, part, herm);
+  } else {
+    cn_smem_attr<TA, TB, ACC, 4, CARRY>(sm);
+    k_gemm_cn<TA, TB, ACC, 4, CARRY><<<grid, 256, sm, st>>>(M, N, K, kslice, A, lda, B, ldb, part, herm);
+  }
 }
 
 template <typename TA, typename TB, typename ACC>
@@ -352,33 +395,50 @@ template <int RM, int RN>
 __global__ void __launch_bounds__(256) k_gemm_wx32(int M, int N, int K, const float2* __restrict__ Wf,
                                                    const float2* __restrict__ X, int ldx, float2* __restrict__ Y,
                                                    int ldy, float beta) {
-  constexpr int TM = 16 * RM, TN = 16 * RN;
+  constexpr int TM = 16 * RM, TN = 16 * RN, STG = 16 * (TM + TN);  // float2 per stage buffer
+  extern __shared__ __align__(16) float2 wx_smem[];                // two stages: Ws[16][TM], Xs[16][TN]
   const int tm = blockIdx.y * TM, tn = blockIdx.x * TN;
-  __shared__ float2 Ws[16][TM];
-  __shared__ float2 Xs[16][TN];
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  // the K step k0 into stage buffer st by asynchronous 8-byte copies (zero-filled outside the matrices)
+  auto stage = [&](int k0, int st) {
+    float2* Ws = wx_smem + st * STG;
+    float2* Xs = Ws + 16 * TM;
+    for (int i = tid; i < 16 * TM; i += 256) {
+      const int kx = i / TM, r = i - kx * TM, gk = k0 + kx, gm = tm + r;
+      const bool in = gk < K && gm < M;
+      cp_async8(Ws + i, in ? Wf + (size_t)gk * M + gm : Wf, in ? 8 : 0);
+    }
+    for (int i = tid; i < 16 * TN; i += 256) {
+      const int kx = i / TN, cc = i - kx * TN, gk = k0 + kx, gn = tn + cc;
+      const bool in = gk < K && gn < N;
+      cp_async8(Xs + i, in ? X + (size_t)gk * ldx + gn : X, in ? 8 : 0);
+    }
+    cp_async_commit();
+  };
   float2 acc[RM][RN];
 #pragma unroll
   for (int i = 0; i < RM; ++i)
 #pragma unroll
     for (int j = 0; j < RN; ++j) acc[i][j] = make_float2(0.f, 0.f);
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    for (int i = tid; i < 16 * TM; i += 256) {
-      const int kx = i / TM, r = i - kx * TM, gk = k0 + kx, gm = tm + r;
-      Ws[kx][r] = (gk < K && gm < M) ? Wf[(size_t)gk * M + gm] : make_float2(0.f, 0.f);
-    }
-    for (int i = tid; i < 16 * TN; i += 256) {
-      const int kx = i / TN, cc = i - kx * TN, gk = k0 + kx, gn = tn + cc;
-      Xs[kx][cc] = (gk < K && gn < N) ? X[(size_t)gk * ldx + gn] : make_float2(0.f, 0.f);
+  const int nk = (K + 15) / 16;
+  if (nk > 0) stage(0, 0);
+  for (int kt = 0; kt < nk; ++kt) {
+    if (kt + 1 < nk) {
+      stage(16 * (kt + 1), (kt + 1) & 1);  // the other buffer: its readers passed the barrier below
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
+    const float2* Ws = wx_smem + (kt & 1) * STG;
+    const float2* Xs = Ws + 16 * TM;
 #pragma unroll 4
     for (int kx = 0; kx < 16; ++kx) {
       float2 x[RN], w[RM];
 #pragma unroll
-      for (int j = 0; j < RN; ++j) x[j] = Xs[kx][tx + 16 * j];
+      for (int j = 0; j < RN; ++j) x[j] = Xs[kx * TN + tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < RM; ++i) w[i] = Ws[kx][ty + 16 * i];
+      for (int i = 0; i < RM; ++i) w[i] = Ws[kx * TM + ty + 16 * i];
 #pragma unroll
       for (int i = 0; i < RM; ++i)
 #pragma unroll
@@ -428,12 +488,21 @@ static int launch_wx32(Ctx* c, int M, int N, int K, const double2* W, int ldw, b
     k_w_to_f32<<<std::min((M * K + 255) / 256, 304), 256, 0, c->stream>>>(M, K, W, ldw, wt ? 1 : 0, s, Wf);
     PARO_LAUNCH(c, "k_w_to_f32");
   }
+  const int rm = big ? 9 : 4, rn = rn4 ? 4 : 2;
+  const size_t sm = (size_t)2 * 16 * 16 * (rm + rn) * sizeof(float2);  // two stages
+  static int attr_dev = -1;  // dynamic shared memory above 48 KB for the 9 x 4 form, set per device
+  int dev = 0;
+  PARO_CU(c, cudaGetDevice(&dev));
+  if (attr_dev != dev) {
+    PARO_CU(c, cudaFuncSetAttribute(k_gemm_wx32<9, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+    attr_dev = dev;
+  }
   if (big) {
-    if (rn4) k_gemm_wx32<9, 4><<<grid, 256, 0, c->stream>>>(M, N, K, Wf, X, ldx, Y, ldy, fb);
-    else k_gemm_wx32<9, 2><<<grid, 256, 0, c->stream>>>(M, N, K, Wf, X, ldx, Y, ldy, fb);
+    if (rn4) k_gemm_wx32<9, 4><<<grid, 256, sm, c->stream>>>(M, N, K, Wf, X, ldx, Y, ldy, fb);
+    else k_gemm_wx32<9, 2><<<grid, 256, sm, c->stream>>>(M, N, K, Wf, X, ldx, Y, ldy, fb);
   } else {
-    if (rn4) k_gemm_wx32<4, 4><<<grid, 256, 0, c->stream>>>(M, N, K, Wf, X, ldx, Y, ldy, fb);
-    else k_gemm_wx32<4, 2><<<grid, 256, 0, c->stream>>>(M, N, K, Wf, X, ldx, Y, ldy, fb);
+    if (rn4) k_gemm_wx32<4, 4><<<grid, 256, sm, c->stream>>>(M, N, K, Wf, X, ldx, Y, ldy, fb);
+    else k_gemm_wx32<4, 2><<<grid, 256, sm, c->stream>>>(M, N, K, Wf, X, ldx, Y, ldy, fb);
   }
   PARO_LAUNCH(c, "k_gemm_wx32");
   return PARO_OK;
