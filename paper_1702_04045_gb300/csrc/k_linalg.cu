@@ -29,15 +29,6 @@ template <typename TO, typename TI> __device__ __forceinline__ cplx<TO> cvt(cplx
 // so the FP32 rounding is that of a 16-term sum (the size of the rounding already in FP32 operands) and
 // does not grow with K, without FP64 instructions in the loop (FP64 issues at 1/64 of the FP32 rate here).
 // ------------------------------------------------------------------------------------------------
-// hi + lo += x with the rounding error of hi + x kept exactly (two-sum: six FP32 operations, no branch)
-__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
-  const float s = hi + x;
-  const float bp = s - hi;
-  const float ap = s - bp;
-  lo += (hi - ap) + (x - bp);
-  hi = s;
-}
-
 template <typename TA, typename TB, typename ACC, int R, bool CARRY>
 __global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kslice, const cplx<TA>* __restrict__ A,
                                                  int lda, const cplx<TB>* __restrict__ B, int ldb,
@@ -258,17 +249,12 @@ int gemm_cn(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, const cplx<
   if (M <= 0 || N <= 0) return PARO_OK;
   if constexpr (sizeof(TA) == 4 && sizeof(TB) == 4 && sizeof(ACC) == 4) {
     if (!herm && !carry && K > 0 && c->tc_scope && tc_enabled()) {
-      int nz = 1, kslice = 16;
-      gemm_cn_tc_plan(M, N, K, &nz, &kslice);
-      double2* part = static_cast<double2*>(ws_get(c, "gemm_parts", (size_t)nz * M * N * sizeof(double2)));
       int* err = tc_err_flag(c);
-      if (!part || !err) return PARO_ERR_CUDA;
+      if (!err) return PARO_ERR_CUDA;
       cudaEvent_t ev = prof_begin(c);
-      int st = gemm_cn_tc(c, M, N, K, A, lda, B, ldb, part, kslice, nz, err);
+      int st = gemm_cn_tc(c, M, N, K, A, lda, B, ldb, C, ldc, err);
       if (st) return st;
       prof_end(c, "k_gemm_cn_tc", ev);
-      k_reduce_parts<<<(M * N + 255) / 256, 256, 0, c->stream>>>(M, N, nz, part, C, ldc, 0, 64);
-      PARO_LAUNCH(c, "k_reduce_parts");
       return PARO_OK;
     }
   }

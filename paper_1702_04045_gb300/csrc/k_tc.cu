@@ -68,21 +68,32 @@ struct TcPipe {
   }
 };
 
-// part[z][m][n] = sum over K slice z of conj(A[m][k]) B[n][k] (complex double). NT: N tile (multiple of
-// 16, at most 256); KC complex K elements per stage (16 or 8). err: set when an mbarrier wait gives up.
-__global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int K, int kslice, int NT, int KC,
+// part[z][m][n] = sum over K slice z of conj(A[m][k]) B[n][k] (complex, FP32 as the tensor memory holds
+// it). NT: N tile (multiple of 16, at most 256). Stages of KC = 8 complex K values. err: set when an
+// mbarrier wait gives up.
+//
+// Pipeline: NR raw stages of plain FP32 rows (A rows m0.., then B rows n0..; 80-byte row pitch so that the
+// split's 16-byte reads are conflict-free) are filled by cp.async NR - 1 stages ahead; each iteration splits
+// one raw stage into the six operand tiles of one of two operand buffers (hi, lo of A' and A'', hi, lo of
+// B') while the MMAs of the previous stage run, then one thread issues the stage's 12 MMAs.
+static const int kCnKC = 8, kCnCh = 4, kRawPitch = 80;
+template <int NR>
+__global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int K, int kslice, int NT,
                                                               const float2* __restrict__ A, int lda,
                                                               const float2* __restrict__ B, int ldb,
-                                                              double2* __restrict__ part, int* __restrict__ err) {
+                                                              float2* __restrict__ part, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   unsigned char* smem = tc_align1024(smem_dyn);
-  const int ch = KC / 2;  // 16-byte chunks per row per stage
+  constexpr int ch = kCnCh;
   const int A_BYTES = kTcM * ch * 16, B_BYTES = NT * ch * 16, STAGE = 4 * A_BYTES + 2 * B_BYTES;
+  const int RROWS = kTcM + NT, RAW = RROWS * kRawPitch;
+  unsigned char* raw0 = smem + 2 * STAGE;
   __shared__ uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * kTcM, n0 = blockIdx.y * NT;
   const int k0 = blockIdx.z * kslice, k1 = min(K, k0 + kslice);
+  const int nst = k1 > k0 ? (k1 - k0 + kCnKC - 1) / kCnKC : 0;
   const uint32_t ncols = NT <= 128 ? 256u : 512u;  // Re and Im accumulators, NT columns each
   if (warp == 0) {
     tc::tmem_alloc(&tmem_base, ncols);
@@ -98,11 +109,42 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int 
   tc::tc_fence_after();
   const uint32_t dR = tmem_base, dI = tmem_base + ncols / 2;
   const uint32_t idesc = tc::idesc_tf32(128, (uint32_t)NT);
+  // raw stage s: row r (A rows, then B rows) x 8 complex; one 8-byte copy per element, zero-filled outside
+  auto issue = [&](int st) {
+    unsigned char* raw = raw0 + (st % NR) * RAW;
+    const int kk = k0 + st * kCnKC;
+    for (int i = tid; i < RROWS * kCnKC; i += kTcThreads) {
+      const int r = i >> 3, kx = i & 7, gk = kk + kx;
+      const float2* src;
+      bool in;
+      if (r < kTcM) {
+        in = m0 + r < M && gk < k1;
+        src = in ? A + (size_t)(m0 + r) * lda + gk : A;
+      } else {
+        in = n0 + r - kTcM < N && gk < k1;
+        src = in ? B + (size_t)(n0 + r - kTcM) * ldb + gk : B;
+      }
+      cp_async8(raw + r * kRawPitch + kx * 8, src, in ? 8 : 0);
+    }
+  };
   TcPipe pipe{mbar, {0u, 0u}, 1, nullptr};
-  int nst = 0, issued[2] = {0, 0};
-  for (int kk = k0; kk < k1; kk += KC, ++nst) {
-    const int b = nst & 1;
-    if (issued[b] && !pipe.wait_buffer(b)) break;  // the MMAs of stage nst - 2 read this buffer
+  int issued[2] = {0, 0};
+#pragma unroll
+  for (int p = 0; p < NR - 1; ++p) {
+    if (p < nst) issue(p);
+    cp_async_commit();
+  }
+  int s = 0;
+  for (; s < nst; ++s) {
+    if (s + NR - 1 < nst) issue(s + NR - 1);  // into the slot read in iteration s - 1 (past its barrier)
+    cp_async_commit();
+    cp_async_wait<NR - 1>();  // this thread's copies of raw stage s have landed
+    const int b = s & 1;
+    if (issued[b]) {
+      if (!pipe.wait_buffer(b)) break;  // barrier: raw stage s visible, operand buffer b free
+    } else {
+      __syncthreads();
+    }
     issued[b] = 0;
     unsigned char* sAh = smem + b * STAGE;
     unsigned char* sAl = sAh + A_BYTES;
@@ -110,67 +152,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int 
     unsigned char* sApl = sAph + A_BYTES;
     unsigned char* sBh = sApl + A_BYTES;
     unsigned char* sBl = sBh + B_BYTES;
-    // unit i -> (row, chunk): each group of 8 consecutive threads covers the 8 rows of one core matrix at
-    // one chunk, so its 16-byte stores hit 8 distinct bank groups (a warp still reads whole 64-byte runs
-    // of 8 rows). All of a thread's loads are issued before any split or store.
-    {
-      constexpr int UA = kTcM * 8 / kTcThreads;  // units per thread at 8 chunks per row
-      float2 va[UA][2];
-#pragma unroll
-      for (int t = 0; t < UA; ++t) {
-        const int i = tid + t * kTcThreads;
-        va[t][0] = va[t][1] = make_float2(0.f, 0.f);
-        if (i < kTcM * ch) {
-          const int r = (i & 7) + 8 * (i / (8 * ch)), c = (i >> 3) % ch;
-          const int gm = m0 + r, g0 = kk + 2 * c;
-          if (gm < M) {
-            const float2* row = A + (size_t)gm * lda;
-            if (g0 < k1) va[t][0] = row[g0];
-            if (g0 + 1 < k1) va[t][1] = row[g0 + 1];
-          }
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < UA; ++t) {
-        const int i = tid + t * kTcThreads;
-        if (i >= kTcM * ch) continue;
-        const int r = (i & 7) + 8 * (i / (8 * ch)), c = (i >> 3) % ch;
-        float4 h, l;
-        tc_split(va[t][0], va[t][1], h, l);
-        const uint32_t o = tc_off(r, c, ch);
-        *reinterpret_cast<float4*>(sAh + o) = h;
-        *reinterpret_cast<float4*>(sAl + o) = l;
-        *reinterpret_cast<float4*>(sAph + o) = make_float4(-h.y, h.x, -h.w, h.z);
-        *reinterpret_cast<float4*>(sApl + o) = make_float4(-l.y, l.x, -l.w, l.z);
-      }
+    const unsigned char* raw = raw0 + (s % NR) * RAW;
+    // unit i -> (row, chunk): 8 consecutive threads take the 8 rows of one core matrix at one chunk
+    for (int i = tid; i < kTcM * ch; i += kTcThreads) {
+      const int r = (i & 7) + 8 * (i / (8 * ch)), c = (i >> 3) % ch;
+      const float4 v = *reinterpret_cast<const float4*>(raw + r * kRawPitch + c * 16);
+      float4 h, l;
+      tc_split(make_float2(v.x, v.y), make_float2(v.z, v.w), h, l);
+      const uint32_t o = tc_off(r, c, ch);
+      *reinterpret_cast<float4*>(sAh + o) = h;
+      *reinterpret_cast<float4*>(sAl + o) = l;
+      *reinterpret_cast<float4*>(sAph + o) = make_float4(-h.y, h.x, -h.w, h.z);
+      *reinterpret_cast<float4*>(sApl + o) = make_float4(-l.y, l.x, -l.w, l.z);
     }
-    for (int i0 = 0; i0 < NT * ch; i0 += 4 * kTcThreads) {
-      float2 vb[4][2];
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int i = i0 + tid + t * kTcThreads;
-        vb[t][0] = vb[t][1] = make_float2(0.f, 0.f);
-        if (i < NT * ch) {
-          const int r = (i & 7) + 8 * (i / (8 * ch)), c = (i >> 3) % ch;
-          const int gn = n0 + r, g0 = kk + 2 * c;
-          if (gn < N) {
-            const float2* row = B + (size_t)gn * ldb;
-            if (g0 < k1) vb[t][0] = row[g0];
-            if (g0 + 1 < k1) vb[t][1] = row[g0 + 1];
-          }
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int i = i0 + tid + t * kTcThreads;
-        if (i >= NT * ch) continue;
-        const int r = (i & 7) + 8 * (i / (8 * ch)), c = (i >> 3) % ch;
-        float4 h, l;
-        tc_split(vb[t][0], vb[t][1], h, l);
-        const uint32_t o = tc_off(r, c, ch);
-        *reinterpret_cast<float4*>(sBh + o) = h;
-        *reinterpret_cast<float4*>(sBl + o) = l;
-      }
+    for (int i = tid; i < NT * ch; i += kTcThreads) {
+      const int r = (i & 7) + 8 * (i / (8 * ch)), c = (i >> 3) % ch;
+      const float4 v = *reinterpret_cast<const float4*>(raw + (kTcM + r) * kRawPitch + c * 16);
+      float4 h, l;
+      tc_split(make_float2(v.x, v.y), make_float2(v.z, v.w), h, l);
+      const uint32_t o = tc_off(r, c, ch);
+      *reinterpret_cast<float4*>(sBh + o) = h;
+      *reinterpret_cast<float4*>(sBl + o) = l;
     }
     tc::fence_proxy_async_smem();
     __syncthreads();
@@ -182,7 +184,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int 
         const uint64_t dAh = tc_desc(aH, s2, ch), dAl = tc_desc(aL, s2, ch);
         const uint64_t dApH = tc_desc(apH, s2, ch), dApL = tc_desc(apL, s2, ch);
         const uint64_t dBh = tc_desc(bH, s2, ch), dBl = tc_desc(bL, s2, ch);
-        const uint32_t acc = (nst > 0 || s2 > 0) ? 1u : 0u;
+        const uint32_t acc = (s > 0 || s2 > 0) ? 1u : 0u;
         tc::mma_tf32(dR, dAh, dBh, idesc, acc);
         tc::mma_tf32(dR, dAh, dBl, idesc, 1u);
         tc::mma_tf32(dR, dAl, dBh, idesc, 1u);
@@ -194,6 +196,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int 
     }
     issued[b] = 1;
   }
+  cp_async_wait<0>();  // no copy into shared memory outlives the CTA
   // drain: the last one or two stages
   for (int b = 0; b < 2; ++b)
     if (issued[b] && pipe.ok && !pipe.wait_buffer(b)) break;
@@ -207,7 +210,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int 
   const int lq = warp & 3, half = warp >> 2;
   const int row = m0 + 32 * lq + lane;
   const uint32_t lane_off = (uint32_t)(32 * lq) << 16;
-  double2* pz = part + (size_t)blockIdx.z * M * N;
+  float2* pz = part + (size_t)blockIdx.z * M * N;
+  const bool have = ok && nst > 0;
   for (int cb = 8 * half; cb < NT; cb += 16) {
     float re[8], im[8];
     tc::tmem_ld_x8(dR + lane_off + (uint32_t)cb, re);
@@ -216,8 +220,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int 
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int n = n0 + cb + j;
-        if (n < N)
-          pz[(size_t)row * N + n] = (ok && nst > 0) ? make_double2((double)re[j], (double)im[j]) : make_double2(0.0, 0.0);
+        if (n < N) pz[(size_t)row * N + n] = have ? make_float2(re[j], im[j]) : make_float2(0.f, 0.f);
       }
     }
   }
@@ -228,6 +231,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_cn_tc(int M, int N, int 
     tc::tmem_dealloc(tmem_base, ncols);
   }
   if (!ok && tid == 0) atomicExch(err, 1);
+}
+
+// C[m][n] = sum over z of part[z][m][n] in a fixed order, added into an FP32 two-sum pair (no FP64 pipe)
+__global__ void k_reduce_parts32(int M, int N, int nz, const float2* __restrict__ part, double2* __restrict__ C,
+                                 int ldc) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= M * N) return;
+  float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
+  for (int z = 0; z < nz; ++z) {
+    const float2 v = part[(size_t)z * M * N + idx];
+    two_sum_acc(hx, lx, v.x);
+    two_sum_acc(hy, ly, v.y);
+  }
+  const int m = idx / N, n = idx - m * N;
+  C[(size_t)m * ldc + n] = make_double2((double)hx + (double)lx, (double)hy + (double)ly);
 }
 
 // Y[m][n] = beta Y[m][n] + sum_k s_k W(k, m) X[k][n] (complex FP32 X, Y; complex double W, W(k, m) at
@@ -425,11 +443,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_wx_tc(int M, int N, int 
 
 // dynamic shared memory of the two-buffer pipelines; KC = 16 complex per stage where both buffers fit,
 // else 8
-static size_t cn_stage_bytes(int NT, int KC) { return (size_t)(4 * kTcM + 2 * NT) * (KC / 2) * 16; }
 static size_t wx_stage_bytes(int NT, int KC) { return (size_t)(2 * kTcM + 4 * NT) * (KC / 2) * 16; }
 static const size_t kTcSmemMax = 220 * 1024;
 static const size_t kTcAlignPad = 1024;  // room to align the stage buffers to 1024 bytes
-static int cn_kc(int NT) { return 2 * cn_stage_bytes(NT, 16) + kTcAlignPad <= kTcSmemMax ? 16 : 8; }
 static int wx_kc(int NT) { return 2 * wx_stage_bytes(NT, 16) + kTcAlignPad <= kTcSmemMax ? 16 : 8; }
 
 static int set_smem_attr(Ctx* c, const void* k, int* dev_done) {
@@ -464,15 +480,19 @@ int gemm_wx_tc(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, 
   return PARO_OK;
 }
 
+// shared memory of the projection pipeline: two operand buffers, NR raw stages, 1 KB of alignment room
+static size_t cn_smem_bytes(int NT, int NR) {
+  return (size_t)2 * (4 * kTcM + 2 * NT) * kCnCh * 16 + (size_t)NR * (kTcM + NT) * kRawPitch + kTcAlignPad;
+}
+
 // K split of the tensor-core product: one CTA per SM, the slice count minimising waves x stages per
 // slice (at least 4 stages per slice), and no slice longer than 8192 complex terms, so the FP32 sum in
-// tensor memory stays short (slices are added in FP64).
-void gemm_cn_tc_plan(int M, int N, int K, int* nz_out, int* kslice_out) {
+// tensor memory stays short (slices are added in an FP32 two-sum pair).
+static void gemm_cn_tc_plan(int M, int N, int K, int* nz_out, int* kslice_out) {
   const int ntiles = (N + 255) / 256;
-  const int nt = ((N + ntiles - 1) / ntiles + 15) / 16 * 16;
-  const int kc = cn_kc(nt);
   const int mtiles = (M + kTcM - 1) / kTcM;
   const int tiles = mtiles * ntiles;
+  const int kc = kCnKC;
   const int steps = (K + kc - 1) / kc;
   const int maxz = std::max(1, steps / 4);
   const int minz = (steps + 8192 / kc - 1) / (8192 / kc);
@@ -492,20 +512,40 @@ void gemm_cn_tc_plan(int M, int N, int K, int* nz_out, int* kslice_out) {
   *nz_out = std::max(1, (K + kslice - 1) / kslice);
 }
 
-// Tensor-core path of gemm_cn<float, float, float> (no Hermitian half, no carry): the same partial-sum
-// layout as the CUDA-core kernel, reduced by k_reduce_parts; part holds nz x M x N (gemm_cn_tc_plan).
-int gemm_cn_tc(Ctx* c, int M, int N, int K, const float2* A, int lda, const float2* B, int ldb, double2* part,
-               int kslice, int nz, int* err) {
+// Tensor-core path of gemm_cn<float, float, float> (no Hermitian half, no carry): C = conj(A) B^T, the
+// K-slice partials in FP32 (a workspace of the context) reduced in a fixed order.
+int gemm_cn_tc(Ctx* c, int M, int N, int K, const float2* A, int lda, const float2* B, int ldb, double2* C,
+               int ldc, int* err) {
   const int ntiles = (N + 255) / 256;
   const int nt = ((N + ntiles - 1) / ntiles + 15) / 16 * 16;
-  const int kc = cn_kc(nt);
   const int mtiles = (M + kTcM - 1) / kTcM;
-  static int attr_dev = -1;
-  int st;
-  if ((st = set_smem_attr(c, (const void*)k_gemm_cn_tc, &attr_dev))) return st;
-  k_gemm_cn_tc<<<dim3(mtiles, ntiles, nz), kTcThreads, 2 * cn_stage_bytes(nt, kc) + kTcAlignPad, c->stream>>>(
-      M, N, K, kslice, nt, kc, A, lda, B, ldb, part, err);
+  int nz = 1, kslice = kCnKC;
+  gemm_cn_tc_plan(M, N, K, &nz, &kslice);
+  float2* part = static_cast<float2*>(ws_get(c, "tc_parts32", (size_t)nz * M * N * sizeof(float2)));
+  if (!part) return PARO_ERR_CUDA;
+  int nr = 5;
+  while (nr > 3 && cn_smem_bytes(nt, nr) > kTcSmemMax) --nr;
+  if (cn_smem_bytes(nt, nr) > kTcSmemMax) return fail(c, PARO_ERR_ARG, "tensor-core product: N tile too wide");
+  static int attr_dev[3] = {-1, -1, -1};
+  int dev = 0;
+  PARO_CU(c, cudaGetDevice(&dev));
+  const void* kf = nr == 5 ? (const void*)k_gemm_cn_tc<5> : nr == 4 ? (const void*)k_gemm_cn_tc<4>
+                                                                    : (const void*)k_gemm_cn_tc<3>;
+  if (attr_dev[nr - 3] != dev) {
+    PARO_CU(c, cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax));
+    attr_dev[nr - 3] = dev;
+  }
+  const dim3 grid(mtiles, ntiles, nz);
+  const size_t sm = cn_smem_bytes(nt, nr);
+  if (nr == 5)
+    k_gemm_cn_tc<5><<<grid, kTcThreads, sm, c->stream>>>(M, N, K, kslice, nt, A, lda, B, ldb, part, err);
+  else if (nr == 4)
+    k_gemm_cn_tc<4><<<grid, kTcThreads, sm, c->stream>>>(M, N, K, kslice, nt, A, lda, B, ldb, part, err);
+  else
+    k_gemm_cn_tc<3><<<grid, kTcThreads, sm, c->stream>>>(M, N, K, kslice, nt, A, lda, B, ldb, part, err);
   PARO_LAUNCH(c, "k_gemm_cn_tc");
+  k_reduce_parts32<<<(M * N + 255) / 256, 256, 0, c->stream>>>(M, N, nz, part, C, ldc);
+  PARO_LAUNCH(c, "k_reduce_parts32");
   return PARO_OK;
 }
 

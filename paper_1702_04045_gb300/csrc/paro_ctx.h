@@ -170,10 +170,9 @@ int gemm_wx(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, con
 template <typename TA, typename TB, typename ACC>
 int gemm_cn_scratch(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb,
                     double2* C, int ldc, double2* part, size_t part_elems);
-// Tensor-core (tcgen05, 3xTF32) C = conj(A) B^T partials for gemm_cn<float, float, float> (k_tc.cu).
-void gemm_cn_tc_plan(int M, int N, int K, int* nz, int* kslice);
-int gemm_cn_tc(Ctx* c, int M, int N, int K, const float2* A, int lda, const float2* B, int ldb, double2* part,
-               int kslice, int nz, int* err);
+// Tensor-core (tcgen05, 3xTF32) C = conj(A) B^T for gemm_cn<float, float, float> (k_tc.cu); err: time-out flag.
+int gemm_cn_tc(Ctx* c, int M, int N, int K, const float2* A, int lda, const float2* B, int ldb, double2* C,
+               int ldc, int* err);
 // Tensor-core gemm_wx<float, float> (k_tc.cu): Y = beta Y + sum_k s_k W(k, m) X[k].
 int gemm_wx_tc(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, const double* s, const float2* X,
                int ldx, float2* Y, int ldy, double beta, int* err);
