@@ -303,7 +303,8 @@ def run_ours(args, rank, world, local, pg):
         roof = roof_of(cand)
         if roof:
             break
-    roof_tensor = roof_of("rr:k_gemm_cn_tc") if "rr:k_gemm_cn_tc" in prof else None
+    # the tensor-core projector products of the inner solves (every source column, fixed shape)
+    roof_tensor = {k: roof_of(k) for k in ("pcg:k_gemm_cn_tc", "pcg:k_gemm_wx_tc") if k in prof} or None
     # H psi GB/s over the three full-batch passes of the Rayleigh-Ritz apply
     bsz = 16 if args.precision == "fp64" else 8
     pas = [f"rr:k_zpass_inv<{'f64' if bsz == 16 else 'f32'}>", f"rr:k_plane<{'f64' if bsz == 16 else 'f32'}>",
