@@ -190,65 +190,76 @@ __global__ void k_zreduce(int n, int nz, const double2* __restrict__ part, doubl
 }
 
 // ------------------------------------------------------------------------------------------------
-// One refinement step's small quantities (one CTA): from G = X^H X and S = X^H A X form lambda, delta,
-// the clusters (cl: cluster index per column; cst: first column of each cluster; ncl) and E.
+// One refinement step's small quantities. k_refine_lam (one CTA): lambda_i = S_ii / G_ii, delta and the
+// clusters (cl: cluster index per column; cst: first column of each cluster; ncl). delta only sets the
+// cluster threshold, so its norms are summed in FP32 (no FP64 pipe on the n^2 sweep).
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_refine_e(int n, const double2* __restrict__ G, const double2* __restrict__ S,
-                                                   double* __restrict__ lam, int* __restrict__ cl,
-                                                   int* __restrict__ cst, int* __restrict__ ncl,
-                                                   double2* __restrict__ E) {
-  __shared__ double red[32];
-  __shared__ double s_delta;
+__global__ void __launch_bounds__(1024) k_refine_lam(int n, const double2* __restrict__ G,
+                                                     const double2* __restrict__ S, double* __restrict__ lam,
+                                                     int* __restrict__ cl, int* __restrict__ cst,
+                                                     int* __restrict__ ncl) {
+  __shared__ float red[32];
+  __shared__ double s_lam[kMixMaxN];
   const int tid = threadIdx.x;
-  for (int i = tid; i < n; i += blockDim.x) lam[i] = S[(size_t)i * n + i].x / G[(size_t)i * n + i].x;
+  for (int i = tid; i < n; i += blockDim.x) {
+    const double l = S[(size_t)i * n + i].x / G[(size_t)i * n + i].x;
+    lam[i] = l;
+    s_lam[i] = l;
+  }
   __syncthreads();
-  double ns = 0.0, nr = 0.0, na = 0.0;
+  float ns = 0.f, nr = 0.f, na = 0.f;
   for (int idx = tid; idx < n * n; idx += blockDim.x) {
     const int i = idx / n, j = idx - i * n;
-    double2 sv = S[idx];
-    if (i == j) sv.x -= lam[i];
-    ns += sv.x * sv.x + sv.y * sv.y;
-    double2 rv = cscale(G[idx], -1.0);
-    if (i == j) rv.x += 1.0;
-    nr += rv.x * rv.x + rv.y * rv.y;
+    const double2 sv = S[idx], gv = G[idx];
+    const float sx = (float)(i == j ? sv.x - s_lam[i] : sv.x), sy = (float)sv.y;
+    const float rx = (float)(i == j ? 1.0 - gv.x : -gv.x), ry = (float)(-gv.y);
+    ns = fmaf(sx, sx, fmaf(sy, sy, ns));
+    nr = fmaf(rx, rx, fmaf(ry, ry, nr));
   }
-  for (int i = tid; i < n; i += blockDim.x) na = fmax(na, fabs(lam[i]));
-  ns = block_sum(ns, red);
+  for (int i = tid; i < n; i += blockDim.x) na = fmaxf(na, (float)fabs(s_lam[i]));
+  ns = block_sumf(ns, red);
   __syncthreads();
-  nr = block_sum(nr, red);
+  nr = block_sumf(nr, red);
   __syncthreads();
-  // max of na over the CTA
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) na = fmax(na, __shfl_xor_sync(0xffffffffu, na, o));
+  for (int o = 16; o > 0; o >>= 1) na = fmaxf(na, __shfl_xor_sync(0xffffffffu, na, o));
   if ((tid & 31) == 0) red[tid >> 5] = na;
   __syncthreads();
   if (tid == 0) {
-    double mx = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+    float mx = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w]);
     // clusters: at least the FP32 solver's own (eigenvalues closer than 1e-3 ||A||, whose vectors inverse
     // iteration only orthogonalised), so that every pair corrected below is already accurate to first order
-    s_delta = fmax(2.0 * (sqrt(ns) + mx * sqrt(nr)), 1e-3 * mx);
+    const double delta = fmax(2.0 * ((double)sqrtf(ns) + (double)mx * (double)sqrtf(nr)), 1e-3 * (double)mx);
     int c = 0;
     cst[0] = 0;
     cl[0] = 0;
     for (int i = 1; i < n; ++i) {
-      if (lam[i] - lam[i - 1] > s_delta) cst[++c] = i;
+      if (s_lam[i] - s_lam[i - 1] > delta) cst[++c] = i;
       cl[i] = c;
     }
     cst[c + 1] = n;
     *ncl = c + 1;
   }
-  __syncthreads();
-  for (int idx = tid; idx < n * n; idx += blockDim.x) {
-    const int i = idx / n, j = idx - i * n;
-    double2 rv = cscale(G[idx], -1.0);
-    if (i == j) rv.x += 1.0;
-    if (cl[i] == cl[j]) {
-      E[idx] = cscale(rv, 0.5);
-    } else {
-      const double2 num = cadd(S[idx], cscale(rv, lam[j]));
-      E[idx] = cscale(num, 1.0 / (lam[j] - lam[i]));
-    }
+}
+
+// E (many CTAs): R = I - G; E_ij = R_ij / 2 inside a cluster, else (S_ij + lambda_j R_ij) / (lambda_j -
+// lambda_i). E is a correction of size ~ the FP32 solver's error, so the quotient is formed in FP32 from
+// an FP64 numerator and difference: its relative FP32 rounding is far below what the step needs.
+__global__ void k_refine_e(int n, const double2* __restrict__ G, const double2* __restrict__ S,
+                           const double* __restrict__ lam, const int* __restrict__ cl, double2* __restrict__ E) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int i = idx / n, j = idx - i * n;
+  double2 rv = cscale(G[idx], -1.0);
+  if (i == j) rv.x += 1.0;
+  if (cl[i] == cl[j]) {
+    E[idx] = cscale(rv, 0.5);
+  } else {
+    const double lj = lam[j];
+    const double2 num = make_double2(fma(lj, rv.x, S[idx].x), fma(lj, rv.y, S[idx].y));
+    const float inv = 1.0f / (float)(lj - lam[i]);
+    E[idx] = make_double2((double)((float)num.x * inv), (double)((float)num.y * inv));
   }
 }
 
@@ -395,7 +406,9 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
     if ((st = zgemm(c, n, X, true, X, G, false, part))) return st;    // G = X^H X
     if ((st = zgemm(c, n, Af, false, X, T1, false, part))) return st;  // T1 = A X
     if ((st = zgemm(c, n, X, true, T1, S, false, part))) return st;    // S = X^H A X
-    k_refine_e<<<1, 1024, 0, c->stream>>>(n, G, S, lam, cl, cst, ncl, T1);  // T1 = E
+    k_refine_lam<<<1, 1024, 0, c->stream>>>(n, G, S, lam, cl, cst, ncl);
+    PARO_LAUNCH(c, "k_refine_lam");
+    k_refine_e<<<(n * n + 255) / 256, 256, 0, c->stream>>>(n, G, S, lam, cl, T1);  // T1 = E
     PARO_LAUNCH(c, "k_refine_e");
     if ((st = zgemm(c, n, X, false, T1, X, true, part))) return st;    // X += X E
   }

@@ -592,10 +592,13 @@ int coop_grid(Ctx* c, const void* kernel, int threads, size_t smem, int cap, int
 
 // Cholesky S = L L^H and G = conj(L)^{-1} on one thread-block cluster of C CTAs, row g of [S | I] in
 // CTA g mod C. Gaussian elimination without pivoting (stable for Hermitian positive definite S): step j
-// subtracts m_ij = a_ij / a_jj times pivot row j from every row i > j, in both halves. That leaves
-// D L_u^H on the left and L_u^{-1} on the right (S = L_u D L_u^H, L_u unit lower triangular), so
-// L^{-1} = D^{-1/2} L_u^{-1}. Row j is final once step j-1 is done and is never written again; every CTA
-// copies it from its owner's shared memory, and one cluster barrier per column orders the steps.
+// subtracts m_ij = a_ij / a_jj times pivot row j from every row i > j, in both halves. That leaves the
+// diagonal D of S = L_u D L_u^H on the left and L_u^{-1} on the right (L_u unit lower triangular), so
+// L^{-1} = D^{-1/2} L_u^{-1}. The trailing left block stays Hermitian, so only its lower triangle is kept
+// (a third less FP64 work than the full rows): the pivot row's left part a_jk (k > j) is read as
+// conj(a_kj), column j of the rows below. After step j - 1 each CTA pushes column j of its rows, and
+// the owner of row j the right half of row j, into every CTA's shared memory (double-buffered by the
+// parity of j), so each step reads its pivot locally; one cluster barrier per column orders the steps.
 // info: first column + 1 with a_jj <= 0 (the elimination then continues with a_jj = 1).
 __global__ void __launch_bounds__(1024) k_chol_cluster(int n, const double2* __restrict__ s, double2* __restrict__ g,
                                                        int* __restrict__ info) {
@@ -605,7 +608,7 @@ __global__ void __launch_bounds__(1024) k_chol_cluster(int n, const double2* __r
   const int R = (n + C - 1) / C, W2 = 2 * n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* rows = reinterpret_cast<double2*>(smem_raw);  // R x 2n: [a_i | b_i]
-  double2* piv = rows + (size_t)R * W2;                  // this step's pivot row
+  double2* pivb = rows + (size_t)R * W2;                 // 2 x 2n: pivot row of step j in pivb[j & 1]
   __shared__ int s_bad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   if (tid == 0) s_bad = 0;
@@ -615,12 +618,32 @@ __global__ void __launch_bounds__(1024) k_chol_cluster(int n, const double2* __r
     if (gi < n) v = k < n ? s[(size_t)gi * n + k] : make_double2(k - n == gi ? 1.0 : 0.0, 0.0);
     rows[idx] = v;
   }
+  // pivot data of step c into every CTA: conj(a_kc) of this CTA's rows k >= c (left part, at index k),
+  // and, from the owner of row c, its right half b_ck (k <= c, at index n + k)
+  auto push = [&](int c) {
+    double2* dst = pivb + (c & 1) * W2;
+    const int rc0 = (c > q) ? (c - q + C - 1) / C : 0;  // first local row with g >= c
+    const int nl = R - rc0;
+    for (int t = tid; t < nl * C; t += blockDim.x) {
+      const int r = rc0 + t / C, tgt = t - (t / C) * C, gi = q + C * r;
+      if (gi >= n) continue;
+      double2* rd = cl.map_shared_rank(dst, tgt);
+      rd[gi] = cconj(rows[(size_t)r * W2 + c]);
+    }
+    if (c % C == q) {
+      const double2* rowc = rows + (size_t)(c / C) * W2 + n;
+      for (int t = tid; t < (c + 1) * C; t += blockDim.x) {
+        const int k = t / C, tgt = t - k * C;
+        double2* rd = cl.map_shared_rank(dst, tgt);
+        rd[n + k] = rowc[k];
+      }
+    }
+  };
+  cl.sync();  // every CTA of the cluster is running (and has its rows) before shared memory is written remotely
+  push(0);
   cl.sync();
   for (int j = 0; j < n; ++j) {
-    const double2* pr = cl.map_shared_rank(rows + (size_t)(j / C) * W2, j % C);
-    for (int k = tid; k < W2; k += blockDim.x)
-      if ((k >= j && k < n) || (k >= n && k - n <= j)) piv[k] = pr[k];
-    __syncthreads();
+    const double2* piv = pivb + (j & 1) * W2;
     double ajj = piv[j].x;
     if (!(ajj > 0.0) || !isfinite(ajj)) {
       if (tid == 0 && s_bad == 0) s_bad = j + 1;
@@ -633,8 +656,12 @@ __global__ void __launch_bounds__(1024) k_chol_cluster(int n, const double2* __r
       if (gi >= n) break;
       double2* row = rows + (size_t)r * W2;
       const double2 m = cscale(row[j], inv);
-      for (int k = j + 1 + lane; k < n; k += 32) row[k] = csub(row[k], cmul(m, piv[k]));
+      for (int k = j + 1 + lane; k <= gi; k += 32) row[k] = csub(row[k], cmul(m, piv[k]));
       for (int k = lane; k <= j; k += 32) row[n + k] = csub(row[n + k], cmul(m, piv[n + k]));
+    }
+    if (j + 1 < n) {
+      __syncthreads();  // this CTA's rows are updated for step j
+      push(j + 1);
     }
     cl.sync();
   }
@@ -646,7 +673,7 @@ __global__ void __launch_bounds__(1024) k_chol_cluster(int n, const double2* __r
     g[(size_t)gi * n + k] = (k <= gi && d > 0.0) ? cscale(cconj(b), 1.0 / sqrt(d)) : make_double2(0.0, 0.0);
   }
   if (q == 0 && tid == 0) *info = s_bad;
-  cl.sync();  // no CTA leaves while another may still read its shared memory
+  cl.sync();  // no CTA leaves while another may still write into its shared memory
 }
 
 // cluster size (16, else 8; 0 = neither fits) and threads for k_chol_cluster
@@ -656,7 +683,7 @@ static int chol_cluster_shape(Ctx* c, int n, int* cls, int* thr, size_t* smem) {
   PARO_CU(c, cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   for (int C : {16, 8}) {
     const int R = (n + C - 1) / C;
-    const size_t sm = ((size_t)R * 2 * n + 2 * (size_t)n) * sizeof(double2);
+    const size_t sm = ((size_t)R * 2 * n + 4 * (size_t)n) * sizeof(double2);  // rows, two pivot buffers
     if (sm > 200 * 1024) continue;
     const int warps = R < 4 ? 4 : (R > 32 ? 32 : R);
     cudaLaunchConfig_t cfg = {};
