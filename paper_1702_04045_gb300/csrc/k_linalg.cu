@@ -792,16 +792,29 @@ int band_norms(Ctx* c, int nb, int npw, const cplx<T>* x, int ldx, double* out_d
   return PARO_OK;
 }
 
+// ||H psi_b - eps_b psi_b||. f32sq (mixed precision, whose orbitals carry FP32 rounding anyway): the
+// difference in FP64 (it cancels), its square summed in an FP32 two-sum pair, a third of the FP64
+// instructions and the norm to a relative 1e-7; otherwise all in FP64.
 __global__ void k_resid(int npw, const double2* __restrict__ psi, const double2* __restrict__ hpsi,
-                        const double* __restrict__ eps, double* __restrict__ out) {
+                        const double* __restrict__ eps, double* __restrict__ out, int f32sq) {
   __shared__ double red[32];
   const int b = blockIdx.x;
   const double e = eps[b];
   double acc = 0.0;
-  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
-    const double2 p = psi[(size_t)b * npw + g], h = hpsi[(size_t)b * npw + g];
-    const double re = h.x - e * p.x, im = h.y - e * p.y;
-    acc += re * re + im * im;
+  if (f32sq) {
+    float hi = 0.f, lo = 0.f;
+    for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+      const double2 p = psi[(size_t)b * npw + g], h = hpsi[(size_t)b * npw + g];
+      const float re = (float)fma(-e, p.x, h.x), im = (float)fma(-e, p.y, h.y);
+      two_sum_acc(hi, lo, fmaf(re, re, im * im));
+    }
+    acc = (double)hi + (double)lo;
+  } else {
+    for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+      const double2 p = psi[(size_t)b * npw + g], h = hpsi[(size_t)b * npw + g];
+      const double re = h.x - e * p.x, im = h.y - e * p.y;
+      acc += re * re + im * im;
+    }
   }
   acc = block_sum(acc, red);
   if (threadIdx.x == 0) out[b] = sqrt(acc);
@@ -809,7 +822,7 @@ __global__ void k_resid(int npw, const double2* __restrict__ psi, const double2*
 
 int residual_norms(Ctx* c, int nb, int npw, const double2* psi, const double2* hpsi, const double* eps_dev,
                    double* out_dev) {
-  k_resid<<<nb, 256, 0, c->stream>>>(npw, psi, hpsi, eps_dev, out_dev);
+  k_resid<<<nb, 256, 0, c->stream>>>(npw, psi, hpsi, eps_dev, out_dev, c->prec == PARO_MIXED ? 1 : 0);
   PARO_LAUNCH(c, "k_resid");
   return PARO_OK;
 }

@@ -410,15 +410,24 @@ __global__ void k_min_sum(int n, const double* __restrict__ v, double* __restric
   }
 }
 
+// one warp: lane-strided partial sums and minima, then a fixed-order shuffle tree (a single thread's
+// chain of dependent FP64 adds would cost ~100 cycles per block here)
 __global__ void k_min_sum_final(int nblk, const double* __restrict__ part, double* __restrict__ out) {
-  if (threadIdx.x != 0) return;
+  const int lane = threadIdx.x;
   double s = 0.0, mn = 1e300;
-  for (int b = 0; b < nblk; ++b) {
+  for (int b = lane; b < nblk; b += 32) {
     s += part[2 * b];
     mn = fmin(mn, part[2 * b + 1]);
   }
-  out[0] = s;
-  out[1] = mn;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  }
+  if (lane == 0) {
+    out[0] = s;
+    out[1] = mn;
+  }
 }
 
 int set_veff_device(Ctx* c, const double* v_dev) {
@@ -523,7 +532,8 @@ static int sum_parts(Ctx* c, const double* part, int n, double* out) {
   return PARO_OK;
 }
 
-static int hartree_energy_and_potential(Ctx* c, const double* rho_dev, double2* z, double* eh) {
+// E_H of rho and, when potential, V_H(r) in z (real parts); the energy alone needs only the forward FFT
+static int hartree_energy_and_potential(Ctx* c, const double* rho_dev, double2* z, double* eh, bool potential) {
   Mat3 B;
   for (int i = 0; i < 9; ++i) B.m[i] = c->bmat[i];
   const int nblk = (c->ngrid + 255) / 256;
@@ -535,8 +545,7 @@ static int hartree_energy_and_potential(Ctx* c, const double* rho_dev, double2* 
   if (st) return st;
   k_hartree_g<<<nblk, 256, 0, c->stream>>>(c->N[0], c->N[1], c->N[2], B, z, part);
   PARO_LAUNCH(c, "k_hartree_g");
-  st = fft3d(c, z, true);
-  if (st) return st;
+  if (potential && (st = fft3d(c, z, true))) return st;
   double s = 0;
   st = sum_parts(c, part, nblk, &s);
   if (st) return st;
@@ -551,7 +560,7 @@ int veff_from_density(Ctx* c, const double* rho_dev, double* eh_out, double* exc
   double* v = static_cast<double*>(ws_get(c, "grid_r0", (size_t)c->ngrid * sizeof(double)));
   if (!z || !v) return PARO_ERR_CUDA;
   double eh = 0;
-  int st = hartree_energy_and_potential(c, rho_dev, z, &eh);
+  int st = hartree_energy_and_potential(c, rho_dev, z, &eh, true);
   if (st) return st;
   k_veff_combine<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, c->d_vloc, z, rho_dev, v);
   PARO_LAUNCH(c, "k_veff_combine");
@@ -757,7 +766,7 @@ int energy_terms(Ctx* c, const double* rho_dev, double terms[7]) {
   double2* z = static_cast<double2*>(ws_get(c, "grid_c0", (size_t)c->ngrid * sizeof(double2)));
   if (!z) return PARO_ERR_CUDA;
   double eh = 0;
-  int st = hartree_energy_and_potential(c, rho_dev, z, &eh);
+  int st = hartree_energy_and_potential(c, rho_dev, z, &eh, false);
   if (st) return st;
   terms[PARO_E_HARTREE] = eh;
   terms[PARO_E_EWALD] = c->e_ewald;
@@ -794,16 +803,27 @@ __global__ void k_pulay_dots(int n, int m, const double* __restrict__ hres, cons
 }
 
 // one thread: sum partials, build the bordered system, Gaussian elimination with partial pivoting
-__global__ void k_pulay_solve(int m, int nblk, const double* __restrict__ part, double* __restrict__ coef) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void __launch_bounds__(256) k_pulay_solve(int m, int nblk, const double* __restrict__ part,
+                                                     double* __restrict__ coef) {
+  __shared__ double sa[16 * 16];
+  {  // the block partials of each (i, j) summed by one warp (lane-strided, then a shuffle tree)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int ij = warp; ij < m * m; ij += nw) {
+      const int i = ij / m, j = ij - i * m;
+      double s = 0.0;
+      if (j >= i)
+        for (int b = lane; b < nblk; b += 32) s += part[(size_t)b * m * m + ij];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) sa[ij] = s;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   double a[17][18];
   const int n = m + 1;
   for (int i = 0; i < m; ++i)
-    for (int j = i; j < m; ++j) {
-      double s = 0.0;
-      for (int b = 0; b < nblk; ++b) s += part[(size_t)b * m * m + i * m + j];
-      a[i][j] = a[j][i] = s;
-    }
+    for (int j = i; j < m; ++j) a[i][j] = a[j][i] = sa[i * m + j];
   for (int i = 0; i < m; ++i) { a[i][m] = 1.0; a[m][i] = 1.0; a[i][n] = 0.0; }
   a[m][m] = 0.0;
   a[m][n] = 1.0;
@@ -869,7 +889,7 @@ int pulay_mix(Ctx* c, const double* rho_out, int depth, double beta) {
   PARO_CU(c, cudaMemcpyAsync(dslot, slots.data(), m * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   k_pulay_dots<<<nblk, 256, 0, c->stream>>>(n, m, c->d_pulay_res, dslot, part);
   PARO_LAUNCH(c, "k_pulay_dots");
-  k_pulay_solve<<<1, 32, 0, c->stream>>>(m, nblk, part, coef);
+  k_pulay_solve<<<1, 256, 0, c->stream>>>(m, nblk, part, coef);
   PARO_LAUNCH(c, "k_pulay_solve");
   k_pulay_mix<<<(n + 255) / 256, 256, 0, c->stream>>>(n, m, c->d_pulay_rho, c->d_pulay_res, dslot, coef, beta,
                                                       c->d_rho_in);
