@@ -532,13 +532,14 @@ static int sum_parts(Ctx* c, const double* part, int n, double* out) {
   return PARO_OK;
 }
 
-// E_H of rho and, when potential, V_H(r) in z (real parts); the energy alone needs only the forward FFT
-static int hartree_energy_and_potential(Ctx* c, const double* rho_dev, double2* z, double* eh, bool potential) {
+// Partial sums of E_H of rho (hartree_blocks(c) doubles in part; E_H = 2 pi Omega times their sum) and,
+// when potential, V_H(r) in z (real parts). Launches only: the energy alone needs only the forward FFT
+// and no host synchronisation until the caller reads the partials.
+static int hartree_blocks(const Ctx* c) { return (c->ngrid + 255) / 256; }
+static int hartree_g(Ctx* c, const double* rho_dev, double2* z, double* part, bool potential) {
   Mat3 B;
   for (int i = 0; i < 9; ++i) B.m[i] = c->bmat[i];
-  const int nblk = (c->ngrid + 255) / 256;
-  double* part = static_cast<double*>(ws_get(c, "hartree_part", (size_t)nblk * sizeof(double)));
-  if (!part) return PARO_ERR_CUDA;
+  const int nblk = hartree_blocks(c);
   k_to_complex<<<nblk, 256, 0, c->stream>>>(c->ngrid, rho_dev, z);
   PARO_LAUNCH(c, "k_to_complex");
   int st = fft3d(c, z, false);
@@ -546,12 +547,9 @@ static int hartree_energy_and_potential(Ctx* c, const double* rho_dev, double2* 
   k_hartree_g<<<nblk, 256, 0, c->stream>>>(c->N[0], c->N[1], c->N[2], B, z, part);
   PARO_LAUNCH(c, "k_hartree_g");
   if (potential && (st = fft3d(c, z, true))) return st;
-  double s = 0;
-  st = sum_parts(c, part, nblk, &s);
-  if (st) return st;
-  *eh = 0.5 * c->omega * 4.0 * kPi * s;
   return PARO_OK;
 }
+static double hartree_energy(const Ctx* c, double part_sum) { return 0.5 * c->omega * 4.0 * kPi * part_sum; }
 
 int veff_from_density(Ctx* c, const double* rho_dev, double* eh_out, double* exc_out) {
   (void)exc_out;
@@ -559,12 +557,17 @@ int veff_from_density(Ctx* c, const double* rho_dev, double* eh_out, double* exc
   double2* z = static_cast<double2*>(ws_get(c, "grid_c0", (size_t)c->ngrid * sizeof(double2)));
   double* v = static_cast<double*>(ws_get(c, "grid_r0", (size_t)c->ngrid * sizeof(double)));
   if (!z || !v) return PARO_ERR_CUDA;
-  double eh = 0;
-  int st = hartree_energy_and_potential(c, rho_dev, z, &eh, true);
+  double* part = static_cast<double*>(ws_get(c, "hartree_part", (size_t)hartree_blocks(c) * sizeof(double)));
+  if (!part) return PARO_ERR_CUDA;
+  int st = hartree_g(c, rho_dev, z, part, true);
   if (st) return st;
   k_veff_combine<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, c->d_vloc, z, rho_dev, v);
   PARO_LAUNCH(c, "k_veff_combine");
-  if (eh_out) *eh_out = eh;
+  if (eh_out) {
+    double sp = 0;
+    if ((st = sum_parts(c, part, hartree_blocks(c), &sp))) return st;
+    *eh_out = hartree_energy(c, sp);
+  }
   return set_veff_device(c, v);
 }
 
@@ -721,16 +724,19 @@ __global__ void k_grid_energies(int n, const double* __restrict__ vloc, const do
 
 int energy_terms(Ctx* c, const double* rho_dev, double terms[7]) {
   for (int i = 0; i < 7; ++i) terms[i] = 0.0;
-  double* part = static_cast<double*>(ws_get(c, "energy_part", (size_t)std::max(c->nb, 512) * 2 * sizeof(double)));
-  if (!part) return PARO_ERR_CUDA;
+  // every partial sum lands in one buffer, read back with a single synchronisation:
+  // [kinetic: nk x nocc][nonlocal: nk x nocc][V_loc rho, rho eps_xc: 2 x 304][Hartree blocks]
+  const int nblk = 304, nh = hartree_blocks(c), nkb = c->nk * c->nocc;
+  const size_t ntot = (size_t)2 * nkb + 2 * nblk + nh;
+  double* part = static_cast<double*>(ws_get(c, "energy_part", ntot * sizeof(double)));
+  double2* z = static_cast<double2*>(ws_get(c, "grid_c0", (size_t)c->ngrid * sizeof(double2)));
+  if (!part || !z) return PARO_ERR_CUDA;
+  double *pk = part, *pn = part + nkb, *pg = part + 2 * nkb, *ph = pg + 2 * nblk;
+  int st;
   for (int ik = 0; ik < c->nk; ++ik) {
     const Basis& B = c->bases[ik];
-    k_kinetic<<<c->nocc, 256, 0, c->stream>>>(B.npw, B.d_psi, B.d_kin, part);
+    k_kinetic<<<c->nocc, 256, 0, c->stream>>>(B.npw, B.d_psi, B.d_kin, pk + (size_t)ik * c->nocc);
     PARO_LAUNCH(c, "k_kinetic");
-    double s = 0;
-    int st = sum_parts(c, part, c->nocc, &s);
-    if (st) return st;
-    terms[PARO_E_KINETIC] += 2.0 * c->kw[ik] * s;
     if (c->have_kb) {
       double2* P = static_cast<double2*>(ws_get(c, "kb_proj", (size_t)c->nproj * c->nb * sizeof(double2)));
       if (!P) return PARO_ERR_CUDA;
@@ -742,33 +748,35 @@ int energy_terms(Ctx* c, const double* rho_dev, double terms[7]) {
                : gemm_cn<double, double, double>(c, c->nproj, c->nocc, B.npw, B.d_beta, B.npw, B.d_psi, B.npw, P,
                                                  c->nocc, false);
       if (st) return st;
-      k_nonlocal<<<c->nocc, 256, 0, c->stream>>>(c->nproj, c->nocc, P, c->d_dvec, part);
+      k_nonlocal<<<c->nocc, 256, 0, c->stream>>>(c->nproj, c->nocc, P, c->d_dvec, pn + (size_t)ik * c->nocc);
       PARO_LAUNCH(c, "k_nonlocal");
-      st = sum_parts(c, part, c->nocc, &s);
-      if (st) return st;
-      terms[PARO_E_NONLOCAL] += 2.0 * c->kw[ik] * s;
     }
   }
-  const int nblk = 304;
-  k_grid_energies<<<nblk, 256, 0, c->stream>>>(c->ngrid, c->d_vloc, rho_dev, part);
+  k_grid_energies<<<nblk, 256, 0, c->stream>>>(c->ngrid, c->d_vloc, rho_dev, pg);
   PARO_LAUNCH(c, "k_grid_energies");
-  std::vector<double> h(2 * nblk);
-  PARO_CU(c, cudaMemcpyAsync(h.data(), part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if ((st = hartree_g(c, rho_dev, z, ph, false))) return st;
+  std::vector<double> h(ntot);
+  PARO_CU(c, cudaMemcpyAsync(h.data(), part, ntot * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   PARO_CU(c, cudaStreamSynchronize(c->stream));
-  double sl = 0, sx = 0;
-  for (int i = 0; i < nblk; ++i) {
-    sl += h[2 * i];
-    sx += h[2 * i + 1];
+  for (int ik = 0; ik < c->nk; ++ik) {
+    double sk = 0, sn = 0;
+    for (int b = 0; b < c->nocc; ++b) {
+      sk += h[(size_t)ik * c->nocc + b];
+      sn += h[nkb + (size_t)ik * c->nocc + b];
+    }
+    terms[PARO_E_KINETIC] += 2.0 * c->kw[ik] * sk;
+    if (c->have_kb) terms[PARO_E_NONLOCAL] += 2.0 * c->kw[ik] * sn;
   }
+  double sl = 0, sx = 0, sh = 0;
+  for (int i = 0; i < nblk; ++i) {
+    sl += h[2 * nkb + 2 * i];
+    sx += h[2 * nkb + 2 * i + 1];
+  }
+  for (int i = 0; i < nh; ++i) sh += h[2 * nkb + 2 * nblk + i];
   const double dv = c->omega / c->ngrid;
   terms[PARO_E_LOCAL] = dv * sl;
   terms[PARO_E_XC] = dv * sx;
-  double2* z = static_cast<double2*>(ws_get(c, "grid_c0", (size_t)c->ngrid * sizeof(double2)));
-  if (!z) return PARO_ERR_CUDA;
-  double eh = 0;
-  int st = hartree_energy_and_potential(c, rho_dev, z, &eh, false);
-  if (st) return st;
-  terms[PARO_E_HARTREE] = eh;
+  terms[PARO_E_HARTREE] = hartree_energy(c, sh);
   terms[PARO_E_EWALD] = c->e_ewald;
   terms[PARO_E_TOTAL] = terms[0] + terms[1] + terms[2] + terms[3] + terms[4] + terms[5];
   return PARO_OK;
