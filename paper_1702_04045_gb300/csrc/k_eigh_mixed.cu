@@ -91,21 +91,32 @@ __global__ void __launch_bounds__(1024) k_tridiag_cta(int n, const double2* __re
     __syncthreads();
     const float t = s_t[j & 1];
     if (t == 0.f) continue;
+    // u cached in registers: lane holds u_k for k = lane + 32 c (c < KC)
+    constexpr int KC = (kMixMaxN + 31) / 32;
+    float2 ur[KC];
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      const int k = lane + 32 * c;
+      ur[c] = k < m ? u[k] : make_float2(0.f, 0.f);
+    }
     for (int i = warp; i < m; i += nwarp) {  // p_i = t sum_k B_ik u_k, B_ik = conj(B_ki) above the diagonal
       const float2* row = A + (j + 1 + i) * ld + (j + 1);
       const float2* col = A + (j + 1) * ld + (j + 1 + i);
       float2 acc = make_float2(0.f, 0.f);
-      for (int k = lane; k < m; k += 32) {
-        float2 bv;
-        if (k <= i) {
-          bv = row[k];
-        } else {
-          bv = col[k * ld];
-          bv.y = -bv.y;
+#pragma unroll
+      for (int c = 0; c < KC; ++c) {
+        const int k = lane + 32 * c;
+        if (k < m) {
+          float2 bv;
+          if (k <= i) {
+            bv = row[k];
+          } else {
+            bv = col[k * ld];
+            bv.y = -bv.y;
+          }
+          acc.x = fmaf(bv.x, ur[c].x, fmaf(-bv.y, ur[c].y, acc.x));
+          acc.y = fmaf(bv.x, ur[c].y, fmaf(bv.y, ur[c].x, acc.y));
         }
-        const float2 uk = u[k];
-        acc.x = fmaf(bv.x, uk.x, fmaf(-bv.y, uk.y, acc.x));
-        acc.y = fmaf(bv.x, uk.y, fmaf(bv.y, uk.x, acc.y));
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -115,24 +126,34 @@ __global__ void __launch_bounds__(1024) k_tridiag_cta(int n, const double2* __re
       if (lane == 0) w[i] = make_float2(t * acc.x, t * acc.y);
     }
     __syncthreads();
-    if (warp == 0) {  // K = (t/2) u^H p (real), w = p - K u
-      float kre = 0.f;
-      for (int i = lane; i < m; i += 32) kre += u[i].x * w[i].x + u[i].y * w[i].y;
+    // every warp: K = (t/2) u^H p (real), w = p - K u in registers (no second barrier for w)
+    float2 wr[KC];
+    float kre = 0.f;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) kre += __shfl_xor_sync(0xffffffffu, kre, o);
-      const float K = 0.5f * t * kre;
-      for (int i = lane; i < m; i += 32) w[i] = make_float2(w[i].x - K * u[i].x, w[i].y - K * u[i].y);
+    for (int c = 0; c < KC; ++c) {
+      const int k = lane + 32 * c;
+      wr[c] = k < m ? w[k] : make_float2(0.f, 0.f);
+      kre += ur[c].x * wr[c].x + ur[c].y * wr[c].y;
     }
-    __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) kre += __shfl_xor_sync(0xffffffffu, kre, o);
+    const float K = 0.5f * t * kre;
+#pragma unroll
+    for (int c = 0; c < KC; ++c) wr[c] = make_float2(wr[c].x - K * ur[c].x, wr[c].y - K * ur[c].y);
     for (int i = warp; i < m; i += nwarp) {  // B -= u w^H + w u^H on and below the diagonal, one row per warp
-      const float2 ui = u[i], wi = w[i];
+      const float2 ui = u[i], pi = w[i];
+      const float2 wi = make_float2(pi.x - K * ui.x, pi.y - K * ui.y);
       float2* row = A + (j + 1 + i) * ld + (j + 1);
-      for (int k = lane; k <= i; k += 32) {
-        const float2 uk = u[k], wk = w[k];
-        float2 bv = row[k];
-        bv.x -= ui.x * wk.x + ui.y * wk.y + wi.x * uk.x + wi.y * uk.y;
-        bv.y -= ui.y * wk.x - ui.x * wk.y + wi.y * uk.x - wi.x * uk.y;
-        row[k] = bv;
+#pragma unroll
+      for (int c = 0; c < KC; ++c) {
+        const int k = lane + 32 * c;
+        if (k <= i) {
+          const float2 uk = ur[c], wk = wr[c];
+          float2 bv = row[k];
+          bv.x -= ui.x * wk.x + ui.y * wk.y + wi.x * uk.x + wi.y * uk.y;
+          bv.y -= ui.y * wk.x - ui.x * wk.y + wi.y * uk.x - wi.x * uk.y;
+          row[k] = bv;
+        }
       }
     }
     __syncthreads();
