@@ -550,6 +550,111 @@ __global__ void __launch_bounds__(512) k_backtransform_s(int n, const cplx<R>* _
   for (int i = lane; i < n; i += 32) V[(size_t)i * n + col] = vc[(size_t)wc * n + i];
 }
 
+// Blocked back-transformation (compact WY form, forward accumulation): the reflectors in blocks of
+// kWY, H_j0 ... H_j0+k-1 = I - V T V^H with T upper triangular, T_ii = tau_i and
+// T(0:i, i) = -tau_i T(0:i, 0:i) V(:, 0:i)^H v_i; then V_eig = Q_0 Q_1 ... (D^H Z), each block applied as
+// Z -= V (T (V^H Z)), three small products instead of k dependent reflector steps per column.
+static const int kWY = 16;
+
+// T of every block (one CTA of 256 threads per block): Tb[b] is kWY x kWY, row-major
+template <typename R>
+__global__ void __launch_bounds__(256) k_wy_t(int n, const cplx<R>* __restrict__ U, const R* __restrict__ tau,
+                                              cplx<R>* __restrict__ Tb) {
+  __shared__ cplx<R> Gm[kWY][kWY + 1];  // G(i, l) = v_i^H v_l, i < l
+  __shared__ cplx<R> T[kWY][kWY + 1];
+  const int b = blockIdx.x, j0 = b * kWY, nbk = min(kWY, n - 1 - j0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  // v_j[r] = U[j n + r - j - 1] for r > j: the overlap of v_i and v_l (i < l) is r > j0 + l
+  for (int pr = warp; pr < kWY * kWY; pr += nwarp) {
+    const int i = pr / kWY, l = pr - i * kWY;
+    if (i >= l || l >= nbk) continue;
+    const int ji = j0 + i, jl = j0 + l;
+    cplx<R> acc = mk<R>(0, 0);
+    for (int r = jl + 1 + lane; r < n; r += 32)
+      acc = cadd(acc, cmul(cconj(U[(size_t)ji * n + (r - ji - 1)]), U[(size_t)jl * n + (r - jl - 1)]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) Gm[i][l] = acc;
+  }
+  for (int idx = threadIdx.x; idx < kWY * kWY; idx += blockDim.x) {
+    const int i = idx / kWY, l = idx - i * kWY;
+    T[i][l] = mk<R>(i == l && i < nbk ? tau[j0 + i] : (R)0, 0);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int l = 1; l < nbk; ++l) {  // T(i, l) = -tau_l sum_{k = i}^{l-1} T(i, k) G(k, l), lane i < l
+      cplx<R> acc = mk<R>(0, 0);
+      if (lane < l)
+        for (int k = lane; k < l; ++k) acc = cadd(acc, cmul(T[lane][k], Gm[k][l]));
+      __syncwarp();
+      if (lane < l) T[lane][l] = cscale(acc, -tau[j0 + l]);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < kWY * kWY; idx += blockDim.x)
+    Tb[(size_t)b * kWY * kWY + idx] = T[idx / kWY][idx % kWY];
+}
+
+// V[:, c] for the CG columns c0.. of this CTA: Zc = D^H Z[:, c], then every block from the last to the
+// first: W = V_b^H Zc (kWY x CG), W = T_b W, Zc -= V_b W. V_b staged in shared memory per block.
+template <typename R, int CG>
+__global__ void __launch_bounds__(256) k_wy_apply(int n, const cplx<R>* __restrict__ U, const cplx<R>* __restrict__ Tb,
+                                                  const cplx<R>* __restrict__ ph, const R* __restrict__ Z,
+                                                  cplx<R>* __restrict__ V) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* Zc = reinterpret_cast<cplx<R>*>(smem_raw);  // n x CG
+  cplx<R>* Vs = Zc + (size_t)n * CG;                   // kWY x n: Vs[i][r] = v_{j0+i}[r] (0 for r <= j0 + i)
+  __shared__ cplx<R> W[kWY][CG], W2[kWY][CG], Ts[kWY][kWY];
+  const int c0 = blockIdx.x * CG, nc = min(CG, n - c0);
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < n * CG; idx += blockDim.x) {
+    const int r = idx / CG, cc = idx - r * CG;
+    Zc[idx] = cc < nc ? cscale(cconj(ph[r]), Z[(size_t)r * n + c0 + cc]) : mk<R>(0, 0);
+  }
+  const int nblk = (n - 1 + kWY - 1) / kWY;
+  for (int b = nblk - 1; b >= 0; --b) {
+    const int j0 = b * kWY, nbk = min(kWY, n - 1 - j0);
+    __syncthreads();  // Zc complete; the previous block's Vs, W2 no longer read
+    for (int idx = tid; idx < kWY * n; idx += blockDim.x) {
+      const int i = idx / n, r = idx - i * n, j = j0 + i;
+      Vs[idx] = (i < nbk && r > j) ? U[(size_t)j * n + (r - j - 1)] : mk<R>(0, 0);
+    }
+    for (int idx = tid; idx < kWY * kWY; idx += blockDim.x)
+      Ts[idx / kWY][idx % kWY] = Tb[(size_t)b * kWY * kWY + idx];
+    __syncthreads();
+    for (int idx = tid; idx < kWY * CG; idx += blockDim.x) {  // W = V_b^H Zc
+      const int i = idx / CG, cc = idx - i * CG;
+      cplx<R> acc = mk<R>(0, 0);
+      for (int r = j0 + i + 1; r < n; ++r) acc = cadd(acc, cmul(cconj(Vs[i * n + r]), Zc[r * CG + cc]));
+      W[i][cc] = acc;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < kWY * CG; idx += blockDim.x) {  // W2 = T W (T upper triangular)
+      const int i = idx / CG, cc = idx - i * CG;
+      cplx<R> acc = mk<R>(0, 0);
+      for (int k = i; k < kWY; ++k) acc = cadd(acc, cmul(Ts[i][k], W[k][cc]));
+      W2[i][cc] = acc;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < (n - j0 - 1) * CG; idx += blockDim.x) {  // Zc -= V_b W2 (rows r > j0)
+      const int r = j0 + 1 + idx / CG, cc = idx % CG;
+      cplx<R> acc = mk<R>(0, 0);
+#pragma unroll 4
+      for (int i = 0; i < kWY; ++i) acc = cadd(acc, cmul(Vs[i * n + r], W2[i][cc]));
+      Zc[r * CG + cc] = csub(Zc[r * CG + cc], acc);
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < n * CG; idx += blockDim.x) {
+    const int r = idx / CG, cc = idx - r * CG;
+    if (cc < nc) V[(size_t)r * n + c0 + cc] = Zc[idx];
+  }
+}
+
 // CTAs of a cooperative launch of `kernel` with `threads` threads and `smem` bytes: at most `cap`,
 // and no more than can be co-resident.
 int coop_grid(Ctx* c, const void* kernel, int threads, size_t smem, int cap, int* grid) {
@@ -643,6 +748,22 @@ int eigh_fp32_pieces(Ctx* c, int n, const float* d, const float* e, float* w, co
   if (st) return st;
   prof_end(c, "eigh32_invit", ev);
   ev = prof_begin(c);
+  {  // blocked (compact WY) back-transformation
+    const int nblk = (n - 1 + kWY - 1) / kWY;
+    constexpr int CG = 8;
+    const size_t smw = ((size_t)n * CG + (size_t)kWY * n) * sizeof(float2);
+    float2* Tb = static_cast<float2*>(ws_get(c, "wy_T32", (size_t)std::max(nblk, 1) * kWY * kWY * sizeof(float2)));
+    if (!Tb) return PARO_ERR_CUDA;
+    if (smw <= 200 * 1024 && n >= 2) {
+      k_wy_t<float><<<nblk, 256, 0, c->stream>>>(n, U, tau, Tb);
+      PARO_LAUNCH(c, "k_wy_t");
+      PARO_CU(c, cudaFuncSetAttribute(k_wy_apply<float, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw));
+      k_wy_apply<float, CG><<<(n + CG - 1) / CG, 256, smw, c->stream>>>(n, U, Tb, ph, Z, V);
+      PARO_LAUNCH(c, "k_wy_apply");
+      prof_end(c, "eigh32_backtransform", ev);
+      return PARO_OK;
+    }
+  }
   const int cpb = 4;
   const size_t sms = ((size_t)n * n + (size_t)n * cpb) * sizeof(float2) + (size_t)n * sizeof(float);
   if (sms <= 220 * 1024) {  // reflectors in shared memory
