@@ -382,9 +382,12 @@ __global__ void k_invit_prep(int n, const R* __restrict__ d, const R* __restrict
   *tiny_out = tiny;
 }
 
+// The factors depend only on lambda_j: the first round stores them in fac (4 n x n values, [i][j]) and
+// sw (n x n), later rounds read them back instead of factorising again.
 template <typename R>
 __global__ void k_invit_solve(int n, const R* __restrict__ d, const R* __restrict__ e, const R* __restrict__ lam,
-                              const R* __restrict__ tinyp, R* __restrict__ Z, int first) {
+                              const R* __restrict__ tinyp, R* __restrict__ Z, int first, R* __restrict__ fac,
+                              unsigned char* __restrict__ swg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int E = blockDim.x, t = threadIdx.x, j = blockIdx.x * E + t;
   R* R0 = reinterpret_cast<R*>(smem_raw);  // 1 / (guarded pivot)
@@ -394,6 +397,13 @@ __global__ void k_invit_solve(int n, const R* __restrict__ d, const R* __restric
   R* z = Lm + (size_t)n * E;
   unsigned char* SW = reinterpret_cast<unsigned char*>(z + (size_t)n * E);
   if (j >= n) return;  // no barriers below
+  const size_t nn = (size_t)n * n;
+  if (!first) {
+    for (int i = 0; i < n; ++i) {
+      const size_t o = (size_t)i * E + t, g = (size_t)i * n + j;
+      R0[o] = fac[g]; U1[o] = fac[nn + g]; U2[o] = fac[2 * nn + g]; Lm[o] = fac[3 * nn + g]; SW[o] = swg[g];
+    }
+  } else {
   const R tiny = *tinyp, l = lam[j];
   R p = d[0] - l, q = n > 1 ? e[0] : (R)0, r = 0;
   for (int i = 0; i + 1 < n; ++i) {  // LU of T' - l with partial pivoting, row i at [i * E + t]
@@ -421,6 +431,11 @@ __global__ void k_invit_solve(int n, const R* __restrict__ d, const R* __restric
   {
     const size_t o = (size_t)(n - 1) * E + t;
     R0[o] = (R)1 / p; U1[o] = 0; U2[o] = 0; Lm[o] = 0; SW[o] = 0;
+  }
+  for (int i = 0; i < n; ++i) {
+    const size_t o = (size_t)i * E + t, g = (size_t)i * n + j;
+    fac[g] = R0[o]; fac[nn + g] = U1[o]; fac[2 * nn + g] = U2[o]; fac[3 * nn + g] = Lm[o]; swg[g] = SW[o];
+  }
   }
   for (int i = 0; i < n; ++i)
     z[(size_t)i * E + t] = first ? (R)(((i * 7919 + j * 104729) % 1999) + 1) / (R)1999 - (R)0.5 : Z[(size_t)i * n + j];
@@ -723,8 +738,11 @@ int invit(Ctx* c, int n, const R* d, const R* e, const R* w, R* Z, int* info) {
   if (E < 1) return fail(c, PARO_ERR_ARG, "inverse iteration: n too large");
   const size_t sm = per * E;
   PARO_CU(c, cudaFuncSetAttribute(k_invit_solve<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  R* fac = static_cast<R*>(ws_get(c, f64 ? "invit_fac64" : "invit_fac32", (size_t)4 * n * n * sizeof(R)));
+  unsigned char* swg = static_cast<unsigned char*>(ws_get(c, "invit_sw", (size_t)n * n));
+  if (!fac || !swg) return PARO_ERR_CUDA;
   for (int it = 0; it < 3; ++it) {
-    k_invit_solve<R><<<(n + E - 1) / E, E, sm, c->stream>>>(n, d, e, lam, tiny, Z, it == 0 ? 1 : 0);
+    k_invit_solve<R><<<(n + E - 1) / E, E, sm, c->stream>>>(n, d, e, lam, tiny, Z, it == 0 ? 1 : 0, fac, swg);
     PARO_LAUNCH(c, "k_invit_solve");
     k_invit_mgs<R><<<(n + 3) / 4, 128, 0, c->stream>>>(n, Z, cst, nclu, info);
     PARO_LAUNCH(c, "k_invit_mgs");
