@@ -299,7 +299,8 @@ static int solve_sources(Ctx* c, int ik, bool alg2, double rel_tol, int max_it, 
   if (!alg2)
     PARO_CU(c, cudaMemcpyAsync(x, psi_of<T>(b), (size_t)nb * npw * sizeof(cplx<T>), cudaMemcpyDeviceToDevice,
                                c->stream));
-  return pcg_run<T>(c, ik, nb, rhs, x, alg2, rel_tol, max_it, nullptr);
+  // Algorithm 1 starts from the orbitals, whose H psi the last Rayleigh-Ritz step left in hpsi
+  return pcg_run<T>(c, ik, nb, rhs, x, alg2, rel_tol, max_it, nullptr, alg2 ? nullptr : hpsi_of<T>(b));
 }
 
 template <typename T>

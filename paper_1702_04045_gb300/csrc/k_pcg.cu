@@ -186,12 +186,25 @@ template <typename T> static const T* kin_ptr(const Basis& b);
 template <> const double* kin_ptr<double>(const Basis& b) { return b.d_kin; }
 template <> const float* kin_ptr<float>(const Basis& b) { return b.d_kin32; }
 
+// ap_b = hx_b - sigma x_b: (H - sigma) x from a known H x
+template <typename T>
+__global__ void k_shift_known(int npw, const cplx<T>* __restrict__ hx, const cplx<T>* __restrict__ x, T sigma,
+                              cplx<T>* __restrict__ ap) {
+  const size_t o = (size_t)blockIdx.y * npw;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < npw; g += gridDim.x * blockDim.x) {
+    const cplx<T> h = hx[o + g], v = x[o + g];
+    ap[o + g] = mk<T>(h.x - sigma * v.x, h.y - sigma * v.y);
+  }
+}
+
 // Solves (H - sigma_k) x_b = rhs_b for b < nb. On entry x holds the start vectors (ignored when
 // x0_zero), on exit the approximate solutions. Every orbital stops once ||r_b|| <= rel_tol ||r_b^0||
-// or after max_it steps; iters (host, may be null) receives the steps taken.
+// or after max_it steps; iters (host, may be null) receives the steps taken. hx0 (may be null): H x
+// of the start vectors when the caller already has it (the orbitals' H psi from the last
+// Rayleigh-Ritz step), which saves the first H application.
 template <typename T>
 int pcg_run(Ctx* c, int ik, int nb, const cplx<T>* rhs, cplx<T>* x, bool x0_zero, double rel_tol, int max_it,
-            int* iters) {
+            int* iters, const cplx<T>* hx0) {
   ProfTag tag(c, "pcg");
   TcScope tcs(c);  // the inner solves tolerate the 3xTF32 products
   const Basis& B = c->bases[ik];
@@ -215,7 +228,10 @@ int pcg_run(Ctx* c, int ik, int nb, const cplx<T>* rhs, cplx<T>* x, bool x0_zero
   const int tb = (nb + 127) / 128;
   PARO_CU(c, cudaMemsetAsync(flags, 0, 2 * sizeof(int), c->stream));
   int st;
-  if (!x0_zero) {
+  if (!x0_zero && hx0) {
+    k_shift_known<T><<<dim3((npw + 255) / 256, nb), 256, 0, c->stream>>>(npw, hx0, x, (T)sigma, ap);
+    PARO_LAUNCH(c, "k_shift_known");
+  } else if (!x0_zero) {
     st = apply_h<T>(c, ik, nb, x, ap, sigma, nullptr);
     if (st) return st;
   } else {
@@ -260,8 +276,8 @@ int pcg_run(Ctx* c, int ik, int nb, const cplx<T>* rhs, cplx<T>* x, bool x0_zero
   return PARO_OK;
 }
 
-template int pcg_run<double>(Ctx*, int, int, const double2*, double2*, bool, double, int, int*);
-template int pcg_run<float>(Ctx*, int, int, const float2*, float2*, bool, double, int, int*);
+template int pcg_run<double>(Ctx*, int, int, const double2*, double2*, bool, double, int, int*, const double2*);
+template int pcg_run<float>(Ctx*, int, int, const float2*, float2*, bool, double, int, int*, const float2*);
 template int scale_rows<double>(Ctx*, int, int, const double2*, const double*, double2*);
 template int scale_rows<float>(Ctx*, int, int, const float2*, const double*, float2*);
 
