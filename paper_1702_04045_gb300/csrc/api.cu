@@ -196,8 +196,17 @@ static const char* wsn(bool f64, const char* a, const char* b) { return f64 ? a 
 // psi = first nb rows of C^T Y, H psi = C^T (H Y), residual norms. T = double: every step in FP64.
 // T = float (mixed): the Cholesky apply, H Y and the rotations in FP32; the Gram and H_sub products
 // accumulated in FP64 (upper halves, mirrored); Cholesky, eigensolver and residual norms in FP64.
+// HX (may be null): H X of the rows of X at the potential of the inner solves; dvplane (may be null): the
+// change of the local potential since then (V-plane layout). With HX, H Y = G H X (+ dV Y) replaces the
+// H application.
+template <typename T>
+static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal, cplx<T>* HX, const T* dvplane);
 template <typename T>
 static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal) {
+  return project<T>(c, ik, X, nx, orthonormal, nullptr, nullptr);
+}
+template <typename T>
+static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal, cplx<T>* HX, const T* dvplane) {
   Basis& b = c->bases[ik];
   const int npw = b.npw, nb = c->nb;
   const bool f64 = sizeof(T) == 8;
@@ -220,10 +229,19 @@ static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal) {
     }
     ProfTag t(c, "orth");
     if ((st = gemm_wx<T, T>(c, nx, npw, nx, G, nx, true, nullptr, X, npw, Y, npw, 0.0))) return st;
+    if (HX && (st = gemm_wx<T, T>(c, nx, npw, nx, G, nx, true, nullptr, HX, npw, HY, npw, 0.0))) return st;
   }
   {
     ProfTag t(c, "rr");
-    if ((st = apply_h<T>(c, ik, nx, Y, HY, 0.0, nullptr))) return st;
+    bool done = false;
+    if (HX) {
+      if (orthonormal)
+        PARO_CU(c, cudaMemcpyAsync(HY, HX, (size_t)nx * npw * sizeof(cplx<T>), cudaMemcpyDeviceToDevice,
+                                   c->stream));
+      done = true;
+      if (dvplane && (st = apply_dv<T>(c, ik, nx, Y, HY, dvplane, &done))) return st;
+    }
+    if (!done && (st = apply_h<T>(c, ik, nx, Y, HY, 0.0, nullptr))) return st;
   }
   {
     ProfTag t(c, "hsub");
@@ -288,7 +306,7 @@ static int source_rhs(Ctx* c, int ik, bool alg2, cplx<T>* rhs) {
 
 // Source problems of all bands of k-point ik; solutions in x (T), started at psi (Algorithm 1) or 0.
 template <typename T>
-static int solve_sources(Ctx* c, int ik, bool alg2, double rel_tol, int max_it, cplx<T>* x) {
+static int solve_sources(Ctx* c, int ik, bool alg2, double rel_tol, int max_it, cplx<T>* x, cplx<T>* hx = nullptr) {
   Basis& b = c->bases[ik];
   const int nb = c->nb, npw = b.npw;
   const bool f64 = sizeof(T) == 8;
@@ -300,7 +318,8 @@ static int solve_sources(Ctx* c, int ik, bool alg2, double rel_tol, int max_it, 
     PARO_CU(c, cudaMemcpyAsync(x, psi_of<T>(b), (size_t)nb * npw * sizeof(cplx<T>), cudaMemcpyDeviceToDevice,
                                c->stream));
   // Algorithm 1 starts from the orbitals, whose H psi the last Rayleigh-Ritz step left in hpsi
-  return pcg_run<T>(c, ik, nb, rhs, x, alg2, rel_tol, max_it, nullptr, alg2 ? nullptr : hpsi_of<T>(b));
+  return pcg_run<T>(c, ik, nb, rhs, x, alg2, rel_tol, max_it, nullptr, alg2 ? nullptr : hpsi_of<T>(b),
+                    alg2 ? nullptr : hx);
 }
 
 template <typename T>
@@ -376,8 +395,12 @@ static double max_occ_resid(const Ctx* c) {
 }
 
 // step 3 of Algorithm 1/2 for k-point ik: the new basis rows in X (T), count in nx
+// HX (may be null; Algorithm 1 only): receives H X of the sources, carried through the inner solves.
 template <typename T>
-static int source_step(Ctx* c, int ik, int alg, double rel_tol, int max_it, cplx<T>* X, int* nx) {
+static int source_step(Ctx* c, int ik, int alg, double rel_tol, int max_it, cplx<T>* X, int* nx,
+                       cplx<T>* HX = nullptr);
+template <typename T>
+static int source_step(Ctx* c, int ik, int alg, double rel_tol, int max_it, cplx<T>* X, int* nx, cplx<T>* HX) {
   const bool alg2 = alg == PARO_ALG2;
   const int npw = c->bases[ik].npw;
   cplx<T>* E = X;
@@ -385,7 +408,7 @@ static int source_step(Ctx* c, int ik, int alg, double rel_tol, int max_it, cplx
     E = static_cast<cplx<T>*>(ws_get(c, wsn(sizeof(T) == 8, "alg2_E64", "alg2_E32"), (size_t)c->nb * npw * sizeof(cplx<T>)));
     if (!E) return PARO_ERR_CUDA;
   }
-  int st = solve_sources<T>(c, ik, alg2, rel_tol, max_it, E);
+  int st = solve_sources<T>(c, ik, alg2, rel_tol, max_it, E, alg2 ? nullptr : HX);
   if (st) return st;
   if (!alg2) {
     *nx = c->nb;
@@ -396,7 +419,7 @@ static int source_step(Ctx* c, int ik, int alg, double rel_tol, int max_it, cplx
 
 // Cholesky-orthonormalise the first nx rows of X in place (Y = conj(L)^{-1} X); Gram in FP64.
 template <typename T>
-static int orthonormalize(Ctx* c, int ik, cplx<T>* X, int nx) {
+static int orthonormalize(Ctx* c, int ik, cplx<T>* X, int nx, cplx<T>* HX = nullptr) {
   const int npw = c->bases[ik].npw;
   const bool f64 = sizeof(T) == 8;
   double2* S = static_cast<double2*>(ws_get(c, "proj_S", (size_t)nx * nx * sizeof(double2)));
@@ -412,6 +435,10 @@ static int orthonormalize(Ctx* c, int ik, cplx<T>* X, int nx) {
   ProfTag t(c, "orth");
   if ((st = gemm_wx<T, T>(c, nx, npw, nx, G, nx, true, nullptr, X, npw, Y, npw, 0.0))) return st;
   PARO_CU(c, cudaMemcpyAsync(X, Y, (size_t)nx * npw * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, c->stream));
+  if (HX) {  // H Y = G (H X): the same combination of the known H X
+    if ((st = gemm_wx<T, T>(c, nx, npw, nx, G, nx, true, nullptr, HX, npw, Y, npw, 0.0))) return st;
+    PARO_CU(c, cudaMemcpyAsync(HX, Y, (size_t)nx * npw * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, c->stream));
+  }
   return PARO_OK;
 }
 
@@ -438,27 +465,61 @@ static int reproject(Ctx* c, int ik) {
   return project<double>(c, ik, X, c->nb, false);
 }
 
+// Algorithm 1 forms H of the Rayleigh-Ritz basis from the inner solves' own products (H X carried
+// through the iteration, G H X after orthonormalisation, plus dV Y when the potential moved). Every
+// kHxRefresh-th ParO iteration applies H directly instead, so the FP32 rounding of the carried H psi
+// cannot accumulate over many iterations.
+static const int kHxRefresh = 4;
+static bool carry_hx(Ctx* c, int alg) {
+  const bool carry = alg == PARO_ALG1 && c->hx_recur < kHxRefresh;
+  c->hx_recur = carry ? c->hx_recur + 1 : 0;
+  return carry;
+}
+
 // One ParO step (Algorithm 1 or 2) of k-point ik at the current potential.
 template <typename T>
 static int paro_step_k(Ctx* c, int ik, int alg, double rel_tol, int max_it) {
   cplx<T>* X = rows_ws<T>(c, "X", ik);
   if (!X) return PARO_ERR_CUDA;
+  cplx<T>* HX = carry_hx(c, alg) ? rows_ws<T>(c, "HX", ik) : nullptr;
   int nx = c->nb;
-  int st = source_step<T>(c, ik, alg, rel_tol, max_it, X, &nx);
-  return st ? st : project<T>(c, ik, X, nx, false);
+  int st = source_step<T>(c, ik, alg, rel_tol, max_it, X, &nx, HX);
+  return st ? st : project<T>(c, ik, X, nx, false, HX, nullptr);
+}
+
+template <typename T> static T* vplane_dev(Ctx* c);
+template <> double* vplane_dev<double>(Ctx* c) { return c->d_vplane; }
+template <> float* vplane_dev<float>(Ctx* c) { return c->d_vplane32; }
+
+// dv = v_new - dv (in place: dv holds the old planes on entry)
+template <typename T>
+__global__ void k_plane_delta(int n, const T* __restrict__ vnew, T* __restrict__ dv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dv[i] = vnew[i] - dv[i];
 }
 
 // The merged SCF iteration in precision T (see paro_scf_step).
 template <typename T>
 static int scf_iteration(Ctx* c, const paro_scf_opts* o) {
-  std::vector<cplx<T>*> xs(c->nk);
+  std::vector<cplx<T>*> xs(c->nk), hxs(c->nk, nullptr);
   std::vector<int> nxs(c->nk);
   int st;
+  const bool carry = carry_hx(c, o->alg);
   for (int ik = 0; ik < c->nk; ++ik) {
     xs[ik] = rows_ws<T>(c, "X", ik);
     if (!xs[ik]) return PARO_ERR_CUDA;
-    if ((st = source_step<T>(c, ik, o->alg, o->inner_rel_tol, o->inner_max_it, xs[ik], &nxs[ik]))) return st;
-    if ((st = orthonormalize<T>(c, ik, xs[ik], nxs[ik]))) return st;
+    if (carry && !(hxs[ik] = rows_ws<T>(c, "HX", ik))) return PARO_ERR_CUDA;
+    if ((st = source_step<T>(c, ik, o->alg, o->inner_rel_tol, o->inner_max_it, xs[ik], &nxs[ik], hxs[ik])))
+      return st;
+    if ((st = orthonormalize<T>(c, ik, xs[ik], nxs[ik], hxs[ik]))) return st;
+  }
+  // the potential planes of the inner solves, to form dV once the mixing has moved the potential
+  T* dv = nullptr;
+  if (carry) {
+    dv = static_cast<T*>(ws_get(c, sizeof(T) == 8 ? "dv_plane64" : "dv_plane32", (size_t)c->ngrid * sizeof(T)));
+    if (!dv) return PARO_ERR_CUDA;
+    PARO_CU(c, cudaMemcpyAsync(dv, vplane_dev<T>(c), (size_t)c->ngrid * sizeof(T), cudaMemcpyDeviceToDevice,
+                               c->stream));
   }
   // rho_in^{n+1/2} = Pulay(rho_in^n, rho[X]) (Algorithm 2: rho of the previous orbitals)
   double* rho_out = static_cast<double*>(ws_get(c, "scf_rho_out", (size_t)c->ngrid * sizeof(double)));
@@ -472,9 +533,13 @@ static int scf_iteration(Ctx* c, const paro_scf_opts* o) {
     if ((st = veff_from_density(c, c->d_rho_in, nullptr, nullptr))) return st;
   }
   update_sigma(c);
+  if (carry) {
+    k_plane_delta<T><<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, vplane_dev<T>(c), dv);
+    PARO_LAUNCH(c, "k_plane_delta");
+  }
   // step 4: Rayleigh-Ritz with V(rho_in^{n+1/2}) in the already orthonormal span
   for (int ik = 0; ik < c->nk; ++ik)
-    if ((st = project<T>(c, ik, xs[ik], nxs[ik], true))) return st;
+    if ((st = project<T>(c, ik, xs[ik], nxs[ik], true, hxs[ik], dv))) return st;
   return PARO_OK;
 }
 

@@ -136,7 +136,8 @@ __global__ void __launch_bounds__(256) k_plane_reg(cplx<T>* __restrict__ S, int 
   for (int c = threadIdx.x; c < ncol; c += blockDim.x) Sz[c] = Pl[col_x[c] * LS + col_y[c]];
 }
 
-template <typename T, int N3>
+// ACC: hpsi += the transformed potential term alone (no kinetic or shift term)
+template <typename T, int N3, bool ACC = false>
 __global__ void __launch_bounds__(256) k_zpass_fwd_reg(const cplx<T>* __restrict__ S, const cplx<T>* __restrict__ psi,
                                                        int ldpsi, cplx<T>* __restrict__ hpsi, int ldh,
                                                        const T* __restrict__ kin, T shift,
@@ -182,9 +183,13 @@ __global__ void __launch_bounds__(256) k_zpass_fwd_reg(const cplx<T>* __restrict
   cplx<T>* h = hpsi + (size_t)b * ldh;
   for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
     const cplx<T> v = line[(g_col[g] - c0) * LS + g_z[g]];
-    const cplx<T> cc = pp[g];
-    const T t = kin[g] - shift;
-    h[g] = mk<T>(v.x + t * cc.x, v.y + t * cc.y);
+    if (ACC) {
+      h[g] = cadd(h[g], v);
+    } else {
+      const cplx<T> cc = pp[g];
+      const T t = kin[g] - shift;
+      h[g] = mk<T>(v.x + t * cc.x, v.y + t * cc.y);
+    }
   }
 }
 
@@ -200,15 +205,16 @@ template <typename K> static int set_smem_once(Ctx* c, K kernel, int* done) {
 
 template <typename T, int N>
 static int passes_reg(Ctx* c, const Basis& B, int nb, const cplx<T>* psi, cplx<T>* S, cplx<T>* hpsi, double shift,
-                      const int* active) {
-  static int done[3][64];
+                      const int* active, const T* vplane = nullptr, bool acc = false) {
+  static int done[4][64];
   const int eb = (int)sizeof(cplx<T>);
   const bool f64 = sizeof(T) == 8;
   const size_t smz = (size_t)eb * (N + kStickBatch * (N + 1));
   const size_t smp = (size_t)eb * (2 * N + N * (N + 1));
   int st;
   if ((st = set_smem_once(c, k_zpass_inv_reg<T, N>, done[0])) || (st = set_smem_once(c, k_plane_reg<T, N, N>, done[1])) ||
-      (st = set_smem_once(c, k_zpass_fwd_reg<T, N>, done[2])))
+      (st = set_smem_once(c, k_zpass_fwd_reg<T, N>, done[2])) ||
+      (st = set_smem_once(c, k_zpass_fwd_reg<T, N, true>, done[3])))
     return st;
   const dim3 gz((B.ncol + kStickBatch - 1) / kStickBatch, nb);
   cudaEvent_t ev = prof_begin(c);
@@ -218,14 +224,19 @@ static int passes_reg(Ctx* c, const Basis& B, int nb, const cplx<T>* psi, cplx<T
   prof_end(c, f64 ? "k_zpass_inv<f64>" : "k_zpass_inv<f32>", ev);
   ev = prof_begin(c);
   k_plane_reg<T, N, N><<<dim3(c->N[2], nb), 256, smp, c->stream>>>(S, B.ncol, B.d_col_x, B.d_col_y, B.d_xrows, B.nxr,
-                                                                   tw_of<T>(c, 0), tw_of<T>(c, 1), vplane_of<T>(c),
-                                                                   active);
+                                                                   tw_of<T>(c, 0), tw_of<T>(c, 1),
+                                                                   vplane ? vplane : vplane_of<T>(c), active);
   PARO_LAUNCH(c, "k_plane_reg");
   prof_end(c, f64 ? "k_plane<f64>" : "k_plane<f32>", ev);
   ev = prof_begin(c);
-  k_zpass_fwd_reg<T, N><<<gz, 256, smz, c->stream>>>(S, psi, B.npw, hpsi, B.npw, kin_of<T>(B), (T)shift,
-                                                     B.d_col_off, B.d_g_col, B.d_g_z, B.ncol, tw_of<T>(c, 2), active,
-                                                     kStickBatch);
+  if (acc)
+    k_zpass_fwd_reg<T, N, true><<<gz, 256, smz, c->stream>>>(S, psi, B.npw, hpsi, B.npw, kin_of<T>(B), (T)shift,
+                                                             B.d_col_off, B.d_g_col, B.d_g_z, B.ncol, tw_of<T>(c, 2),
+                                                             active, kStickBatch);
+  else
+    k_zpass_fwd_reg<T, N><<<gz, 256, smz, c->stream>>>(S, psi, B.npw, hpsi, B.npw, kin_of<T>(B), (T)shift,
+                                                       B.d_col_off, B.d_g_col, B.d_g_z, B.ncol, tw_of<T>(c, 2), active,
+                                                       kStickBatch);
   PARO_LAUNCH(c, "k_zpass_fwd_reg");
   prof_end(c, f64 ? "k_zpass_fwd<f64>" : "k_zpass_fwd<f32>", ev);
   return PARO_OK;
@@ -234,18 +245,19 @@ static int passes_reg(Ctx* c, const Basis& B, int nb, const cplx<T>* psi, cplx<T
 // Register kernels when the grid is N^3 with a supported N and the plane fits in shared memory.
 template <typename T>
 static int passes_reg_dispatch(Ctx* c, const Basis& B, int nb, const cplx<T>* psi, cplx<T>* S, cplx<T>* hpsi,
-                               double shift, const int* active, bool* used) {
+                               double shift, const int* active, bool* used, const T* vplane = nullptr,
+                               bool acc = false) {
   *used = false;
   const int n = c->N[0];
   if (c->N[1] != n || c->N[2] != n) return PARO_OK;
   if ((size_t)sizeof(cplx<T>) * (2 * n + n * (n + 1)) > 227 * 1024) return PARO_OK;
   *used = true;
   switch (n) {
-    case 32: return passes_reg<T, 32>(c, B, nb, psi, S, hpsi, shift, active);
-    case 36: return passes_reg<T, 36>(c, B, nb, psi, S, hpsi, shift, active);
-    case 48: return passes_reg<T, 48>(c, B, nb, psi, S, hpsi, shift, active);
-    case 72: return passes_reg<T, 72>(c, B, nb, psi, S, hpsi, shift, active);
-    case 128: return passes_reg<T, 128>(c, B, nb, psi, S, hpsi, shift, active);
+    case 32: return passes_reg<T, 32>(c, B, nb, psi, S, hpsi, shift, active, vplane, acc);
+    case 36: return passes_reg<T, 36>(c, B, nb, psi, S, hpsi, shift, active, vplane, acc);
+    case 48: return passes_reg<T, 48>(c, B, nb, psi, S, hpsi, shift, active, vplane, acc);
+    case 72: return passes_reg<T, 72>(c, B, nb, psi, S, hpsi, shift, active, vplane, acc);
+    case 128: return passes_reg<T, 128>(c, B, nb, psi, S, hpsi, shift, active, vplane, acc);
     default: *used = false; return PARO_OK;
   }
 }

@@ -224,6 +224,23 @@ int apply_h(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* hpsi, double sh
   return PARO_OK;
 }
 
+// hpsi += dV psi for a change dV of the local potential (plane layout and scale of the context's V
+// planes: dV / N_grid, [z][x][y]): the three FFT passes with dV in place of V, no kinetic or projector
+// term. Register-FFT grids only; *used = false elsewhere (the caller applies H instead).
+template <typename T>
+int apply_dv(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* hpsi, const T* dvplane, bool* used) {
+  *used = false;
+  int st = configure<T>(c);
+  if (st) return st;
+  const Basis& B = c->bases[ik];
+  const size_t sbytes = (size_t)nb * c->N[2] * B.ncol * sizeof(cplx<T>);
+  cplx<T>* S = static_cast<cplx<T>*>(ws_get(c, sizeof(T) == 8 ? "sticks64" : "sticks32", sbytes));
+  if (!S) return PARO_ERR_CUDA;
+  return passes_reg_dispatch<T>(c, B, nb, psi, S, hpsi, 0.0, nullptr, used, dvplane, true);
+}
+template int apply_dv<double>(Ctx*, int, int, const double2*, double2*, const double*, bool*);
+template int apply_dv<float>(Ctx*, int, int, const float2*, float2*, const float*, bool*);
+
 template <typename T>
 int sticks_inverse(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* S) {
   int st = configure<T>(c);

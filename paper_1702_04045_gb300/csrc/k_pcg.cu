@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kVT) k_pcg_update(int npw, int nchunk, cplx<T>
                                                     const cplx<T>* __restrict__ ap, const T* __restrict__ kin,
                                                     T pshift, const double* __restrict__ alpha,
                                                     const int* __restrict__ active, double* __restrict__ prr,
-                                                    double* __restrict__ prz) {
+                                                    double* __restrict__ prz, cplx<T>* __restrict__ hx, T sigma) {
   __shared__ double red[32];
   const int b = blockIdx.y, ch = blockIdx.x;
   if (!active[b]) return;
@@ -113,6 +113,12 @@ __global__ void __launch_bounds__(kVT) k_pcg_update(int npw, int nchunk, cplx<T>
     rv.x -= a * av.x; rv.y -= a * av.y;
     x[o + g] = xv;
     r[o + g] = rv;
+    if (hx) {  // H x follows x: H p = ap + sigma p
+      cplx<T> hv = hx[o + g];
+      hv.x += a * (av.x + sigma * pv.x);
+      hv.y += a * (av.y + sigma * pv.y);
+      hx[o + g] = hv;
+    }
     const double q = (double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y;
     rr += q;
     rz += q * (double)((T)1 / (kin[g] + pshift));
@@ -201,10 +207,11 @@ __global__ void k_shift_known(int npw, const cplx<T>* __restrict__ hx, const cpl
 // x0_zero), on exit the approximate solutions. Every orbital stops once ||r_b|| <= rel_tol ||r_b^0||
 // or after max_it steps; iters (host, may be null) receives the steps taken. hx0 (may be null): H x
 // of the start vectors when the caller already has it (the orbitals' H psi from the last
-// Rayleigh-Ritz step), which saves the first H application.
+// Rayleigh-Ritz step), which saves the first H application. hx (may be null; needs hx0 or x0_zero):
+// receives H x of the solutions, carried along the iteration from the products the solver forms anyway.
 template <typename T>
 int pcg_run(Ctx* c, int ik, int nb, const cplx<T>* rhs, cplx<T>* x, bool x0_zero, double rel_tol, int max_it,
-            int* iters, const cplx<T>* hx0) {
+            int* iters, const cplx<T>* hx0, cplx<T>* hx) {
   ProfTag tag(c, "pcg");
   TcScope tcs(c);  // the inner solves tolerate the 3xTF32 products
   const Basis& B = c->bases[ik];
@@ -228,6 +235,11 @@ int pcg_run(Ctx* c, int ik, int nb, const cplx<T>* rhs, cplx<T>* x, bool x0_zero
   const int tb = (nb + 127) / 128;
   PARO_CU(c, cudaMemsetAsync(flags, 0, 2 * sizeof(int), c->stream));
   int st;
+  if (hx) {
+    if (x0_zero) PARO_CU(c, cudaMemsetAsync(hx, 0, vb, c->stream));
+    else if (hx0) PARO_CU(c, cudaMemcpyAsync(hx, hx0, vb, cudaMemcpyDeviceToDevice, c->stream));
+    else return fail(c, PARO_ERR_ARG, "pcg_run: H x of the solutions needs H x of the start vectors");
+  }
   if (!x0_zero && hx0) {
     k_shift_known<T><<<dim3((npw + 255) / 256, nb), 256, 0, c->stream>>>(npw, hx0, x, (T)sigma, ap);
     PARO_LAUNCH(c, "k_shift_known");
@@ -254,7 +266,7 @@ int pcg_run(Ctx* c, int ik, int nb, const cplx<T>* rhs, cplx<T>* x, bool x0_zero
     k_pcg_band_alpha<<<tb, 128, 0, c->stream>>>(nb, nchunk, prz, rz, active, alpha, flags + 1);
     PARO_LAUNCH(c, "k_pcg_band_alpha");
     k_pcg_update<T><<<gv, kVT, 0, c->stream>>>(npw, nchunk, x, r, p, ap, kin_ptr<T>(B), pshift, alpha, active, prr,
-                                               prz);
+                                               prz, hx, (T)sigma);
     PARO_LAUNCH(c, "k_pcg_update");
     PARO_CU(c, cudaMemsetAsync(flags, 0, sizeof(int), c->stream));
     k_pcg_band_beta<<<tb, 128, 0, c->stream>>>(nb, nchunk, prr, prz, r0n, rel_tol, rz, active, its, beta, still,
@@ -276,8 +288,9 @@ int pcg_run(Ctx* c, int ik, int nb, const cplx<T>* rhs, cplx<T>* x, bool x0_zero
   return PARO_OK;
 }
 
-template int pcg_run<double>(Ctx*, int, int, const double2*, double2*, bool, double, int, int*, const double2*);
-template int pcg_run<float>(Ctx*, int, int, const float2*, float2*, bool, double, int, int*, const float2*);
+template int pcg_run<double>(Ctx*, int, int, const double2*, double2*, bool, double, int, int*, const double2*,
+                             double2*);
+template int pcg_run<float>(Ctx*, int, int, const float2*, float2*, bool, double, int, int*, const float2*, float2*);
 template int scale_rows<double>(Ctx*, int, int, const double2*, const double*, double2*);
 template int scale_rows<float>(Ctx*, int, int, const float2*, const double*, float2*);
 

@@ -107,6 +107,7 @@ struct Ctx {
   // FP32 products may run on the tensor cores (3xTF32): inside the inexact inner solves and the adjoint,
   // not in the Rayleigh-Ritz step, the rotations or the energy, which fix the self-consistent result
   bool tc_scope = false;
+  int hx_recur = 0;  // ParO iterations since H of the Rayleigh-Ritz basis was last applied directly
 };
 
 // Status helpers (api.cu)
@@ -146,6 +147,10 @@ struct ProfTag {
 
 // ---- H psi (k_hpsi.cu) ----
 // hpsi = (H - shift) psi for nb bands, T = float or double; active: device int[nb] or nullptr.
+// hpsi += dV psi (dV: change of the local potential in the context's V-plane layout and scale); register
+// FFT grids only, *used = false otherwise (k_hpsi.cu)
+template <typename T>
+int apply_dv(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* hpsi, const T* dvplane, bool* used);
 template <typename T>
 int apply_h(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* hpsi, double shift, const int* active);
 // Checks that the FFT passes support this grid / precision (register and shared-memory budgets).
@@ -236,7 +241,7 @@ int vloc_position_grad(Ctx* c, const double* gv, double* gpos);
 // ---- batched PCG (k_pcg.cu) ----
 template <typename T>
 int pcg_run(Ctx* c, int ik, int nb, const cplx<T>* rhs, cplx<T>* x, bool x0_zero, double rel_tol, int max_it,
-            int* iters, const cplx<T>* hx0 = nullptr);
+            int* iters, const cplx<T>* hx0 = nullptr, cplx<T>* hx = nullptr);
 template <typename T>
 int scale_rows(Ctx* c, int nb, int npw, const cplx<T>* x, const double* f_dev, cplx<T>* y);
 
