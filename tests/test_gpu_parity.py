@@ -280,11 +280,13 @@ def test_scf_matches_oracle_fixed_point(alg, precision, n_iter, tol_e):
     assert np.abs(ctx.eigenvalues()[0][:8] - eps_ref[0][:8]).max() < 1e-6
 
 
-def test_scf_step_matches_oracle_step():
-    # One merged SCF/ParO iteration from the same start, fixed inner iteration counts.
+@pytest.mark.parametrize("ecut", [3.0, 10.0])
+def test_scf_step_matches_oracle_step(ecut):
+    # One merged SCF/ParO iteration from the same start, fixed inner iteration counts. At 10 Ha the grid
+    # is 32^3, where the Rayleigh-Ritz basis gets H from the inner solves' products plus dV Y.
     from paper_1702_04045_gb300 import paro
-    ctx, prob, (lat, pos, d) = _small(ecut=3.0, nb=12, nocc=8, seed=41)
-    sys_ = scf.ScfSystem(lat, pos, 3.0, 12, 8, inputs.LOCAL_PP, d, inputs.KB_RC)
+    ctx, prob, (lat, pos, d) = _small(ecut=ecut, nb=12, nocc=8, seed=41)
+    sys_ = scf.ScfSystem(lat, pos, ecut, 12, 8, inputs.LOCAL_PP, d, inputs.KB_RC)
     c0 = inputs.start_vectors(12, ctx.npw(), 3)
     ctx.set_orbitals(c0)
     log = []
