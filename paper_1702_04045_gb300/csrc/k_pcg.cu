@@ -10,6 +10,21 @@ namespace paro {
 static const int kChunk = 2048;  // plane waves per CTA in the vector kernels
 static const int kVT = 256;
 
+// Per-thread sum of the dot-product terms: FP64 for FP64 vectors; for FP32 vectors the FP32 terms are
+// added into an FP32 two-sum pair (no FP64 instructions per element, which GB300 issues at 1/64 rate,
+// and no accumulation error beyond the terms' own FP32 rounding).
+template <typename T> struct DotAcc;
+template <> struct DotAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct DotAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float v) { two_sum_acc(hi, lo, v); }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // r = b - Ax (or b when ax == nullptr), z = M r, p = z; partials of <r,z> and |r|^2
 template <typename T>
 __global__ void __launch_bounds__(kVT) k_pcg_init(int npw, int nchunk, const cplx<T>* __restrict__ bvec,
@@ -19,7 +34,7 @@ __global__ void __launch_bounds__(kVT) k_pcg_init(int npw, int nchunk, const cpl
   __shared__ double red[32];
   const int b = blockIdx.y, ch = blockIdx.x;
   const size_t o = (size_t)b * npw;
-  double rz = 0.0, rr = 0.0;
+  DotAcc<T> az, ar;
   const int g0 = ch * kChunk, g1 = min(npw, g0 + kChunk);
   for (int g = g0 + threadIdx.x; g < g1; g += kVT) {
     cplx<T> rv = bvec[o + g];
@@ -27,13 +42,13 @@ __global__ void __launch_bounds__(kVT) k_pcg_init(int npw, int nchunk, const cpl
     const T m = (T)1 / (kin[g] + pshift);
     r[o + g] = rv;
     p[o + g] = cscale(rv, m);
-    const double re = rv.x, im = rv.y;
-    rr += re * re + im * im;
-    rz += (re * re + im * im) * (double)m;
+    const T q = rv.x * rv.x + rv.y * rv.y;
+    ar.add(q);
+    az.add(q * m);
   }
-  rz = block_sum(rz, red);
+  double rz = block_sum(az.value(), red);
   if (threadIdx.x == 0) prz[(size_t)b * nchunk + ch] = rz;
-  rr = block_sum(rr, red);
+  double rr = block_sum(ar.value(), red);
   if (threadIdx.x == 0) prr[(size_t)b * nchunk + ch] = rr;
 }
 
@@ -63,13 +78,13 @@ __global__ void __launch_bounds__(kVT) k_pcg_dot(int npw, int nchunk, const cplx
   const int b = blockIdx.y, ch = blockIdx.x;
   if (!active[b]) return;
   const size_t o = (size_t)b * npw;
-  double s = 0.0;
+  DotAcc<T> acc;
   const int g0 = ch * kChunk, g1 = min(npw, g0 + kChunk);
   for (int g = g0 + threadIdx.x; g < g1; g += kVT) {
     const cplx<T> u = p[o + g], v = ap[o + g];
-    s += (double)u.x * (double)v.x + (double)u.y * (double)v.y;
+    acc.add(u.x * v.x + u.y * v.y);
   }
-  s = block_sum(s, red);
+  double s = block_sum(acc.value(), red);
   if (threadIdx.x == 0) part[(size_t)b * nchunk + ch] = s;
 }
 
@@ -104,7 +119,7 @@ __global__ void __launch_bounds__(kVT) k_pcg_update(int npw, int nchunk, cplx<T>
   if (!active[b]) return;
   const T a = (T)alpha[b];
   const size_t o = (size_t)b * npw;
-  double rr = 0.0, rz = 0.0;
+  DotAcc<T> ar, az;
   const int g0 = ch * kChunk, g1 = min(npw, g0 + kChunk);
   for (int g = g0 + threadIdx.x; g < g1; g += kVT) {
     const cplx<T> pv = p[o + g], av = ap[o + g];
@@ -119,13 +134,13 @@ __global__ void __launch_bounds__(kVT) k_pcg_update(int npw, int nchunk, cplx<T>
       hv.y += a * (av.y + sigma * pv.y);
       hx[o + g] = hv;
     }
-    const double q = (double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y;
-    rr += q;
-    rz += q * (double)((T)1 / (kin[g] + pshift));
+    const T q = rv.x * rv.x + rv.y * rv.y;
+    ar.add(q);
+    az.add(q * ((T)1 / (kin[g] + pshift)));
   }
-  rr = block_sum(rr, red);
+  double rr = block_sum(ar.value(), red);
   if (threadIdx.x == 0) prr[(size_t)b * nchunk + ch] = rr;
-  rz = block_sum(rz, red);
+  double rz = block_sum(az.value(), red);
   if (threadIdx.x == 0) prz[(size_t)b * nchunk + ch] = rz;
 }
 
