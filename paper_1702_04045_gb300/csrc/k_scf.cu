@@ -468,58 +468,69 @@ __global__ void k_to_complex(int n, const double* __restrict__ r, double2* __res
 
 // rho_g (unnormalised forward FFT of rho) -> V_H(G) = 4 pi rho(G)/G^2 with rho(G) = rho_g / N; partial
 // sums of |rho(G)|^2 / G^2 per block for E_H.
-__global__ void k_hartree_g(int N1, int N2, int N3, Mat3 B, double2* __restrict__ z, double* __restrict__ part) {
+// 1 / |G|^2 on the grid (0 at G = 0): the Coulomb factor of every Hartree solve, formed once per grid
+__global__ void k_inv_g2(int N1, int N2, int N3, Mat3 B, double* __restrict__ ig2) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N1 * N2 * N3) return;
+  const int j3 = idx % N3, j2 = (idx / N3) % N2, j1 = idx / (N2 * N3);
+  const int n1 = signed_index(j1, N1), n2 = signed_index(j2, N2), n3 = signed_index(j3, N3);
+  const double gx = n1 * B.m[0] + n2 * B.m[3] + n3 * B.m[6];
+  const double gy = n1 * B.m[1] + n2 * B.m[4] + n3 * B.m[7];
+  const double gz = n1 * B.m[2] + n2 * B.m[5] + n3 * B.m[8];
+  const double g2 = gx * gx + gy * gy + gz * gz;
+  ig2[idx] = g2 > 0.0 ? 1.0 / g2 : 0.0;
+}
+
+// V_H(G) = 4 pi rho(G) / |G|^2 in place (rho(G) = z / N_grid), and per block partials of |rho(G)|^2 / |G|^2
+__global__ void k_hartree_tab(int ng, const double* __restrict__ ig2, double2* __restrict__ z,
+                              double* __restrict__ part) {
   __shared__ double red[32];
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  const int ng = N1 * N2 * N3;
   double e = 0.0;
   if (idx < ng) {
-    const int j3 = idx % N3, j2 = (idx / N3) % N2, j1 = idx / (N2 * N3);
-    const int n1 = signed_index(j1, N1), n2 = signed_index(j2, N2), n3 = signed_index(j3, N3);
-    const double gx = n1 * B.m[0] + n2 * B.m[3] + n3 * B.m[6];
-    const double gy = n1 * B.m[1] + n2 * B.m[4] + n3 * B.m[7];
-    const double gz = n1 * B.m[2] + n2 * B.m[5] + n3 * B.m[8];
-    const double g2 = gx * gx + gy * gy + gz * gz;
-    double2 r = cscale(z[idx], 1.0 / ng);
-    if (g2 > 0.0) {
-      e = (r.x * r.x + r.y * r.y) / g2;
-      z[idx] = cscale(r, 4.0 * kPi / g2);
-    } else {
-      z[idx] = make_double2(0.0, 0.0);
-    }
+    const double f = ig2[idx];
+    const double2 r = cscale(z[idx], 1.0 / ng);
+    e = (r.x * r.x + r.y * r.y) * f;
+    z[idx] = cscale(r, 4.0 * kPi * f);
   }
   e = block_sum(e, red);
   if (threadIdx.x == 0) part[blockIdx.x] = e;
 }
 
-__device__ __forceinline__ void lda_pz(double rho, double* eps, double* v) {
-  if (!(rho >= 1e-30)) { *eps = 0.0; *v = 0.0; return; }
-  const double pi = kPi;
-  const double ex = -0.75 * cbrt(3.0 * rho / pi);
-  const double vx = 4.0 / 3.0 * ex;
-  const double rs = cbrt(3.0 / (4.0 * pi * rho));
-  double ec, vc;
-  if (rs >= 1.0) {
-    const double s = sqrt(rs);
-    const double den = 1.0 + 1.0529 * s + 0.3334 * rs;
-    ec = -0.1423 / den;
-    vc = ec * (1.0 + 7.0 / 6.0 * 1.0529 * s + 4.0 / 3.0 * 0.3334 * rs) / den;
+
+// Perdew-Zunger LDA exchange-correlation energy per electron and potential at density rho, in R
+// (double, or float where the potential only enters FP32 H psi and the energy sums stay FP64)
+template <typename R>
+__device__ __forceinline__ void lda_pz(R rho, R* eps, R* v) {
+  if (!(rho >= (R)1e-30)) { *eps = 0; *v = 0; return; }
+  const R pi = (R)kPi;
+  const R ex = (R)-0.75 * cbrt((R)3 * rho / pi);
+  const R vx = (R)4 / (R)3 * ex;
+  const R rs = cbrt((R)3 / ((R)4 * pi * rho));
+  R ec, vc;
+  if (rs >= (R)1) {
+    const R s = sqrt(rs);
+    const R den = (R)1 + (R)1.0529 * s + (R)0.3334 * rs;
+    ec = (R)-0.1423 / den;
+    vc = ec * ((R)1 + (R)7 / (R)6 * (R)1.0529 * s + (R)4 / (R)3 * (R)0.3334 * rs) / den;
   } else {
-    const double lr = log(rs);
-    ec = 0.0311 * lr - 0.048 + 0.0020 * rs * lr - 0.0116 * rs;
-    vc = 0.0311 * lr + (-0.048 - 0.0311 / 3.0) + 2.0 / 3.0 * 0.0020 * rs * lr + (2.0 * -0.0116 - 0.0020) / 3.0 * rs;
+    const R lr = log(rs);
+    ec = (R)0.0311 * lr - (R)0.048 + (R)0.0020 * rs * lr - (R)0.0116 * rs;
+    vc = (R)0.0311 * lr + ((R)-0.048 - (R)0.0311 / (R)3) + (R)2 / (R)3 * (R)0.0020 * rs * lr +
+         ((R)2 * (R)-0.0116 - (R)0.0020) / (R)3 * rs;
   }
   *eps = ex + ec;
   *v = vx + vc;
 }
 
+template <typename R>
 __global__ void k_veff_combine(int n, const double* __restrict__ vloc, const double2* __restrict__ vh,
                                const double* __restrict__ rho, double* __restrict__ veff) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double e, v;
-  lda_pz(rho[i], &e, &v);
-  veff[i] = vloc[i] + vh[i].x + v;
+  R e, v;
+  lda_pz<R>((R)rho[i], &e, &v);
+  veff[i] = vloc[i] + vh[i].x + (double)v;
 }
 
 static int sum_parts(Ctx* c, const double* part, int n, double* out) {
@@ -544,8 +555,15 @@ static int hartree_g(Ctx* c, const double* rho_dev, double2* z, double* part, bo
   PARO_LAUNCH(c, "k_to_complex");
   int st = fft3d(c, z, false);
   if (st) return st;
-  k_hartree_g<<<nblk, 256, 0, c->stream>>>(c->N[0], c->N[1], c->N[2], B, z, part);
-  PARO_LAUNCH(c, "k_hartree_g");
+  double* ig2 = static_cast<double*>(ws_get(c, "inv_g2", (size_t)c->ngrid * sizeof(double)));
+  if (!ig2) return PARO_ERR_CUDA;
+  if (!c->have_inv_g2) {  // the cell and grid are fixed for the context's life
+    k_inv_g2<<<nblk, 256, 0, c->stream>>>(c->N[0], c->N[1], c->N[2], B, ig2);
+    PARO_LAUNCH(c, "k_inv_g2");
+    c->have_inv_g2 = true;
+  }
+  k_hartree_tab<<<nblk, 256, 0, c->stream>>>(c->ngrid, ig2, z, part);
+  PARO_LAUNCH(c, "k_hartree_tab");
   if (potential && (st = fft3d(c, z, true))) return st;
   return PARO_OK;
 }
@@ -561,7 +579,10 @@ int veff_from_density(Ctx* c, const double* rho_dev, double* eh_out, double* exc
   if (!part) return PARO_ERR_CUDA;
   int st = hartree_g(c, rho_dev, z, part, true);
   if (st) return st;
-  k_veff_combine<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, c->d_vloc, z, rho_dev, v);
+  if (c->prec == PARO_MIXED)  // the potential reaches H psi as FP32 planes: V_xc in FP32 loses nothing
+    k_veff_combine<float><<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, c->d_vloc, z, rho_dev, v);
+  else
+    k_veff_combine<double><<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, c->d_vloc, z, rho_dev, v);
   PARO_LAUNCH(c, "k_veff_combine");
   if (eh_out) {
     double sp = 0;
@@ -613,10 +634,12 @@ __global__ void __launch_bounds__(512, 1) k_plane_density(const cplx<T>* __restr
 // rho[x][y][z] += sum_g part[g][z][x][y]
 __global__ void k_density_reduce(int N1, int N2, int N3, int ngrp, const double* __restrict__ part,
                                  double* __restrict__ rho, int accumulate) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // C order output
-  if (idx >= N1 * N2 * N3) return;
-  const int z = idx % N3, y = (idx / N3) % N2, x = idx / (N2 * N3);
-  const size_t pl = (size_t)z * N1 * N2 + (size_t)x * N2 + y;
+  // consecutive threads take consecutive plane-layout points: the ngrp partial planes are read coalesced
+  // (they are most of the traffic); the one C-order write per point is strided
+  const int pl = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pl >= N1 * N2 * N3) return;
+  const int y = pl % N2, x = (pl / N2) % N1, z = pl / (N1 * N2);
+  const size_t idx = ((size_t)x * N2 + y) * N3 + z;
   double s = 0.0;
   for (int g = 0; g < ngrp; ++g) s += part[(size_t)g * N1 * N2 * N3 + pl];
   rho[idx] = accumulate ? rho[idx] + s : s;
@@ -679,13 +702,24 @@ template int density<float>(Ctx*, const float2* const*, double*);
 // energy terms
 // ------------------------------------------------------------------------------------------------
 // per block partial sums of w_b * sum_g kin_g |c_bg|^2 over blocks (band, chunk)
-__global__ void k_kinetic(int npw, const double2* __restrict__ psi, const double* __restrict__ kin, double* part) {
+// FP32 orbitals (mixed precision): FP32 terms summed in an FP32 two-sum pair, no FP64 per coefficient
+template <typename T>
+__global__ void k_kinetic(int npw, const cplx<T>* __restrict__ psi, const T* __restrict__ kin, double* part) {
   __shared__ double red[32];
   const int b = blockIdx.x;
   double s = 0.0;
-  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
-    const double2 v = psi[(size_t)b * npw + g];
-    s += kin[g] * (v.x * v.x + v.y * v.y);
+  if (sizeof(T) == 4) {
+    float hi = 0.f, lo = 0.f;
+    for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+      const cplx<T> v = psi[(size_t)b * npw + g];
+      two_sum_acc(hi, lo, (float)(kin[g] * (v.x * v.x + v.y * v.y)));
+    }
+    s = (double)hi + (double)lo;
+  } else {
+    for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+      const cplx<T> v = psi[(size_t)b * npw + g];
+      s += (double)kin[g] * ((double)v.x * v.x + (double)v.y * v.y);
+    }
   }
   s = block_sum(s, red);
   if (threadIdx.x == 0) part[b] = s;
@@ -706,15 +740,16 @@ __global__ void k_nonlocal(int nproj, int nb, const double2* __restrict__ P, con
 }
 
 // per block partials of sum V_loc rho and sum rho eps_xc(rho)
+template <typename R>
 __global__ void k_grid_energies(int n, const double* __restrict__ vloc, const double* __restrict__ rho,
                                 double* __restrict__ part) {
   __shared__ double red[32];
   double sl = 0.0, sx = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double e, v;
-    lda_pz(rho[i], &e, &v);
+    R e, v;
+    lda_pz<R>((R)rho[i], &e, &v);
     sl += vloc[i] * rho[i];
-    sx += rho[i] * e;
+    sx += rho[i] * (double)e;
   }
   sl = block_sum(sl, red);
   if (threadIdx.x == 0) part[2 * blockIdx.x] = sl;
@@ -735,7 +770,10 @@ int energy_terms(Ctx* c, const double* rho_dev, double terms[7]) {
   int st;
   for (int ik = 0; ik < c->nk; ++ik) {
     const Basis& B = c->bases[ik];
-    k_kinetic<<<c->nocc, 256, 0, c->stream>>>(B.npw, B.d_psi, B.d_kin, pk + (size_t)ik * c->nocc);
+    if (c->prec == PARO_MIXED && B.d_psi32)
+      k_kinetic<float><<<c->nocc, 256, 0, c->stream>>>(B.npw, B.d_psi32, B.d_kin32, pk + (size_t)ik * c->nocc);
+    else
+      k_kinetic<double><<<c->nocc, 256, 0, c->stream>>>(B.npw, B.d_psi, B.d_kin, pk + (size_t)ik * c->nocc);
     PARO_LAUNCH(c, "k_kinetic");
     if (c->have_kb) {
       double2* P = static_cast<double2*>(ws_get(c, "kb_proj", (size_t)c->nproj * c->nb * sizeof(double2)));
@@ -752,7 +790,10 @@ int energy_terms(Ctx* c, const double* rho_dev, double terms[7]) {
       PARO_LAUNCH(c, "k_nonlocal");
     }
   }
-  k_grid_energies<<<nblk, 256, 0, c->stream>>>(c->ngrid, c->d_vloc, rho_dev, pg);
+  if (c->prec == PARO_MIXED)  // eps_xc per point in FP32, the sums in FP64
+    k_grid_energies<float><<<nblk, 256, 0, c->stream>>>(c->ngrid, c->d_vloc, rho_dev, pg);
+  else
+    k_grid_energies<double><<<nblk, 256, 0, c->stream>>>(c->ngrid, c->d_vloc, rho_dev, pg);
   PARO_LAUNCH(c, "k_grid_energies");
   if ((st = hartree_g(c, rho_dev, z, ph, false))) return st;
   std::vector<double> h(ntot);

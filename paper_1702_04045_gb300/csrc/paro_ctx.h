@@ -107,7 +107,8 @@ struct Ctx {
   // FP32 products may run on the tensor cores (3xTF32): inside the inexact inner solves and the adjoint,
   // not in the Rayleigh-Ritz step, the rotations or the energy, which fix the self-consistent result
   bool tc_scope = false;
-  int hx_recur = 0;  // ParO iterations since H of the Rayleigh-Ritz basis was last applied directly
+  int hx_recur = 0;
+  bool have_inv_g2 = false;  // the 1/|G|^2 table of the Hartree solve is in the "inv_g2" workspace  // ParO iterations since H of the Rayleigh-Ritz basis was last applied directly
 };
 
 // Status helpers (api.cu)
