@@ -466,10 +466,10 @@ static int reproject(Ctx* c, int ik) {
 }
 
 // Algorithm 1 forms H of the Rayleigh-Ritz basis from the inner solves' own products (H X carried
-// through the iteration, G H X after orthonormalisation, plus dV Y when the potential moved). Every
-// kHxRefresh-th ParO iteration applies H directly instead, so the FP32 rounding of the carried H psi
-// cannot accumulate over many iterations.
-static const int kHxRefresh = 4;
+// through the iteration, G H X after orthonormalisation, plus dV Y when the potential moved). After
+// kHxRefresh such iterations one applies H directly, so the FP32 rounding of the carried H psi cannot
+// accumulate over many iterations.
+static const int kHxRefresh = 8;
 static bool carry_hx(Ctx* c, int alg) {
   const bool carry = alg == PARO_ALG1 && c->hx_recur < kHxRefresh;
   c->hx_recur = carry ? c->hx_recur + 1 : 0;

@@ -284,6 +284,26 @@ __global__ void k_refine_e(int n, const double2* __restrict__ G, const double2* 
   }
 }
 
+// S_ij = x_i^H (A x_j) = sum_r conj(X[r][i]) T1[r][j] for the pairs (i, j) of one cluster only: the
+// Rayleigh-Ritz inside the clusters (and lambda of singletons) reads nothing else of S
+// one warp per pair (i, j), lanes over r
+__global__ void k_blockdiag_xhat(int n, const double2* __restrict__ X, const double2* __restrict__ T1,
+                                 const int* __restrict__ cl, double2* __restrict__ S) {
+  const int lane = threadIdx.x & 31;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (idx >= n * n) return;
+  const int i = idx / n, j = idx - i * n;
+  if (cl[i] != cl[j]) return;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int r = lane; r < n; r += 32) acc = cadd(acc, cmul(cconj(X[(size_t)r * n + i]), T1[(size_t)r * n + j]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  }
+  if (lane == 0) S[idx] = acc;
+}
+
 // Rayleigh-Ritz inside each cluster of two or more columns: S_c = (X^H A X)_cc (k x k, k <= 64)
 // diagonalised by Jacobi, X_c <- X_c Q, lam_c = its eigenvalues; one CTA per cluster. Singleton
 // clusters take lam_i = S_ii. info |= 4 for a cluster larger than 64, |= 8 if Jacobi did not converge.
@@ -434,7 +454,14 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
     if ((st = zgemm(c, n, X, false, T1, X, true, part))) return st;    // X += X E
   }
   if ((st = zgemm(c, n, Af, false, X, T1, false, part))) return st;    // T1 = A X
-  if ((st = zgemm(c, n, X, true, T1, S, false, part))) return st;      // S = X^H A X
+  if (refine_steps > 0) {  // the clusters exist: S = X^H A X inside them only
+    k_blockdiag_xhat<<<(int)((nn + 7) / 8), 256, 0, c->stream>>>(n, X, T1, cl, S);
+    PARO_LAUNCH(c, "k_blockdiag_xhat");
+  } else if ((st = zgemm(c, n, X, true, T1, S, false, part))) {
+    return st;
+  }
+  prof_end(c, "eigh_refine", ev);
+  ev = prof_begin(c);
   const size_t sm3 = (size_t)2 * 64 * 65 * sizeof(double2);
   PARO_CU(c, cudaFuncSetAttribute(k_cluster_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
   k_cluster_rr<<<n, 256, sm3, c->stream>>>(n, S, cst, ncl, X, lam, info);
@@ -443,7 +470,7 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
   PARO_LAUNCH(c, "k_eig_sort");
   k_eig_permute<<<(int)((nn + 255) / 256), 256, 0, c->stream>>>(n, lam, X, perm, w, v);
   PARO_LAUNCH(c, "k_eig_permute");
-  prof_end(c, "eigh_refine", ev);
+  prof_end(c, "eigh_cluster_rr", ev);
   int h = 0;
   PARO_CU(c, cudaMemcpyAsync(&h, info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   PARO_CU(c, cudaStreamSynchronize(c->stream));
