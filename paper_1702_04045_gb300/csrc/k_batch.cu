@@ -403,19 +403,23 @@ __global__ void __launch_bounds__(256) k_bpcg_pupdate(BandMap bm, cplx<T>* __res
 }
 
 // rhs = T((eps_b - sigma_p) psi64), x = psi_T (Algorithm 1 source problems, started at psi)
+// rhs = (eps - sigma) psi, x0 = psi, and (H - sigma) x0 = H psi - sigma psi from the H psi each context
+// keeps with its orbitals (the last Rayleigh-Ritz step's), so the solves need no first H application
 template <typename T>
-__global__ void k_brhs(BandMap bm, const double2* __restrict__ psi64, const double* __restrict__ eps,
-                       const double* __restrict__ sigma, cplx<T>* __restrict__ rhs, cplx<T>* __restrict__ x) {
+__global__ void k_brhs(BandMap bm, const double2* __restrict__ psi64, const double2* __restrict__ hpsi64,
+                       const double* __restrict__ eps, const double* __restrict__ sigma, cplx<T>* __restrict__ rhs,
+                       cplx<T>* __restrict__ x, cplx<T>* __restrict__ ax) {
   const int gb = blockIdx.y;
   const int pi = bm.prob[gb];
   const ProbDev& P = bm.probs[pi];
   const int npw = P.npw;
   const size_t o = P.off + (size_t)bm.row[gb] * npw;
-  const double f = eps[gb] - sigma[pi];
+  const double sg = sigma[pi], f = eps[gb] - sg;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < npw; g += gridDim.x * blockDim.x) {
-    const double2 v = psi64[o + g];
+    const double2 v = psi64[o + g], h = hpsi64[o + g];
     rhs[o + g] = mk<T>((T)(f * v.x), (T)(f * v.y));
     x[o + g] = mk<T>((T)v.x, (T)v.y);
+    ax[o + g] = mk<T>((T)(h.x - sg * v.x), (T)(h.y - sg * v.y));
   }
 }
 
@@ -804,12 +808,13 @@ int enqueue_step(paro_batch* b, double tol, int maxit) {
     const Basis& B = unwrap(b->ctxs[b->pk[i].first])->bases[b->pk[i].second];
     BCU(b, cudaMemcpyAsync(b->psi64 + P.off, B.d_psi, (size_t)P.nb * P.npw * sizeof(double2),
                            cudaMemcpyDeviceToDevice, s_));
+    BCU(b, cudaMemcpyAsync(b->hpsi64 + P.off, B.d_hpsi, (size_t)P.nb * P.npw * sizeof(double2),
+                           cudaMemcpyDeviceToDevice, s_));
   }
   BCU(b, cudaMemsetAsync(b->flags, 0, (size_t)(1 + b->nprob) * sizeof(int), s_));
   // step 3: (H - sigma) x = (eps - sigma) psi, x0 = psi
-  k_brhs<T><<<dim3(4, b->nbt), 256, 0, s_>>>(bm, b->psi64, b->eps, b->sigma, rhs, x);
+  k_brhs<T><<<dim3(4, b->nbt), 256, 0, s_>>>(bm, b->psi64, b->hpsi64, b->eps, b->sigma, rhs, x, ap);
   BLAUNCH(b, "k_brhs");
-  if ((st = launch_fused<T>(b, s_, x, ap, nullptr, 1, b->threads == 1 ? 0 : 1, b->grid))) return st;
   k_bpcg_init<T><<<gv, 256, 0, s_>>>(bm, b->nch, rhs, ap, r, p, b->pshift, b->prz, b->prr);
   BLAUNCH(b, "k_bpcg_init");
   k_bpcg_band_init<<<tb, 128, 0, s_>>>(b->nbt, b->nch, b->prz, b->prr, b->rz, b->r0n, b->active);
