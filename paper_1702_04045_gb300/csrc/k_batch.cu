@@ -328,7 +328,8 @@ __global__ void __launch_bounds__(256) k_bpcg_update(BandMap bm, int nch, cplx<T
                                                      cplx<T>* __restrict__ r, const cplx<T>* __restrict__ p,
                                                      const cplx<T>* __restrict__ ap, const double* __restrict__ pshift,
                                                      const double* __restrict__ alpha, const int* __restrict__ active,
-                                                     double* __restrict__ prr, double* __restrict__ prz) {
+                                                     double* __restrict__ prr, double* __restrict__ prz,
+                                                     cplx<T>* __restrict__ hx, const double* __restrict__ sigma) {
   __shared__ double red[32];
   const int gb = blockIdx.y, ch = blockIdx.x;
   if (!active[gb]) return;
@@ -339,6 +340,7 @@ __global__ void __launch_bounds__(256) k_bpcg_update(BandMap bm, int nch, cplx<T
   const T* kin = pd_kin<T>(P);
   const T ps = (T)pshift[pi];
   const T a = (T)alpha[gb];
+  const T sg = hx ? (T)sigma[pi] : (T)0;
   double rr = 0.0, rz = 0.0;
   const int g0 = ch * kBChunk, g1 = min(npw, g0 + kBChunk);
   for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
@@ -348,6 +350,12 @@ __global__ void __launch_bounds__(256) k_bpcg_update(BandMap bm, int nch, cplx<T
     rv.x -= a * av.x; rv.y -= a * av.y;
     x[o + g] = xv;
     r[o + g] = rv;
+    if (hx) {  // H x follows x: H p = ap + sigma p
+      cplx<T> hv = hx[o + g];
+      hv.x += a * (av.x + sg * pv.x);
+      hv.y += a * (av.y + sg * pv.y);
+      hx[o + g] = hv;
+    }
     const double q = (double)rv.x * rv.x + (double)rv.y * rv.y;
     rr += q;
     rz += q * (double)((T)1 / (kin[g] + ps));
@@ -408,7 +416,7 @@ __global__ void __launch_bounds__(256) k_bpcg_pupdate(BandMap bm, cplx<T>* __res
 template <typename T>
 __global__ void k_brhs(BandMap bm, const double2* __restrict__ psi64, const double2* __restrict__ hpsi64,
                        const double* __restrict__ eps, const double* __restrict__ sigma, cplx<T>* __restrict__ rhs,
-                       cplx<T>* __restrict__ x, cplx<T>* __restrict__ ax) {
+                       cplx<T>* __restrict__ x, cplx<T>* __restrict__ ax, cplx<T>* __restrict__ hx) {
   const int gb = blockIdx.y;
   const int pi = bm.prob[gb];
   const ProbDev& P = bm.probs[pi];
@@ -420,6 +428,7 @@ __global__ void k_brhs(BandMap bm, const double2* __restrict__ psi64, const doub
     rhs[o + g] = mk<T>((T)(f * v.x), (T)(f * v.y));
     x[o + g] = mk<T>((T)v.x, (T)v.y);
     ax[o + g] = mk<T>((T)(h.x - sg * v.x), (T)(h.y - sg * v.y));
+    if (hx) hx[o + g] = mk<T>((T)h.x, (T)h.y);
   }
 }
 
@@ -722,7 +731,11 @@ struct paro_batch {
   double *eps = nullptr, *res = nullptr, *sigma = nullptr, *pshift = nullptr;
   double* h_stage = nullptr;  // pinned: eps then res then sigma then pshift
   int* h_flags = nullptr;     // pinned
-  cudaGraphExec_t exec = nullptr;
+  cudaGraphExec_t exec = nullptr;   // the step that carries H x through the solves (H Y = G H X)
+  cudaGraphExec_t exec2 = nullptr;  // the step that applies H to the Rayleigh-Ritz basis directly
+  long long graph_kernels2 = 0;
+  int hx_recur = 0;                 // carried steps since the last direct one
+  void* hx = nullptr;
   double g_tol = -1.0;
   int g_maxit = -1;
   long long graph_kernels = 0;
@@ -789,7 +802,7 @@ int launch_fused(paro_batch* b, cudaStream_t s, const cplx<T>* X, cplx<T>* Y, co
 
 // the whole ParO step (Algorithm 1) for every problem, enqueued without any host wait
 template <typename T>
-int enqueue_step(paro_batch* b, double tol, int maxit) {
+int enqueue_step(paro_batch* b, double tol, int maxit, bool carry_hx) {
   cplx<T>* x = static_cast<cplx<T>*>(b->x);
   cplx<T>* r = static_cast<cplx<T>*>(b->r);
   cplx<T>* p = static_cast<cplx<T>*>(b->p);
@@ -813,7 +826,8 @@ int enqueue_step(paro_batch* b, double tol, int maxit) {
   }
   BCU(b, cudaMemsetAsync(b->flags, 0, (size_t)(1 + b->nprob) * sizeof(int), s_));
   // step 3: (H - sigma) x = (eps - sigma) psi, x0 = psi
-  k_brhs<T><<<dim3(4, b->nbt), 256, 0, s_>>>(bm, b->psi64, b->hpsi64, b->eps, b->sigma, rhs, x, ap);
+  cplx<T>* hx = carry_hx ? static_cast<cplx<T>*>(b->hx) : nullptr;
+  k_brhs<T><<<dim3(4, b->nbt), 256, 0, s_>>>(bm, b->psi64, b->hpsi64, b->eps, b->sigma, rhs, x, ap, hx);
   BLAUNCH(b, "k_brhs");
   k_bpcg_init<T><<<gv, 256, 0, s_>>>(bm, b->nch, rhs, ap, r, p, b->pshift, b->prz, b->prr);
   BLAUNCH(b, "k_bpcg_init");
@@ -826,7 +840,7 @@ int enqueue_step(paro_batch* b, double tol, int maxit) {
     k_bpcg_alpha<<<tb, 128, 0, s_>>>(b->nbt, b->nch, b->prz, b->rz, b->active, b->alpha, b->flags);
     BLAUNCH(b, "k_bpcg_alpha");
     k_bpcg_update<T><<<gv, 256, 0, s_>>>(bm, b->nch, x, r, p, ap, b->pshift, b->alpha, b->active, b->prr,
-                                             b->prz);
+                                             b->prz, hx, b->sigma);
     BLAUNCH(b, "k_bpcg_update");
     k_bpcg_beta<<<tb, 128, 0, s_>>>(b->nbt, b->nch, b->prr, b->prz, b->r0n, tol, b->rz, b->active, b->beta,
                                        b->still);
@@ -849,7 +863,12 @@ int enqueue_step(paro_batch* b, double tol, int maxit) {
   const dim3 gw((b->nch * kBChunk + 255) / 256, b->nprob);
   k_bwx<T><<<gw, 256, 0, s_>>>(b->d_prob, b->G, 1, x, y);
   BLAUNCH(b, "k_bwx");
-  if ((st = launch_fused<T>(b, s_, y, hy, nullptr, 0, b->threads == 1 ? 0 : 1, b->grid))) return st;
+  if (carry_hx) {  // H Y = G (H X): the potential is fixed within the step
+    k_bwx<T><<<gw, 256, 0, s_>>>(b->d_prob, b->G, 1, hx, hy);
+    BLAUNCH(b, "k_bwx");
+  } else if ((st = launch_fused<T>(b, s_, y, hy, nullptr, 0, b->threads == 1 ? 0 : 1, b->grid))) {
+    return st;
+  }
   if (carry)
     k_bgram<T, true><<<gg, 256, 0, s_>>>(b->d_prob, b->nslice, y, hy, b->part);
   else
@@ -950,9 +969,10 @@ int autotune(paro_batch* b) {
 
 void free_batch(paro_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->exec2) cudaGraphExecDestroy(b->exec2);
   if (b->ev) cudaEventDestroy(b->ev);
   if (b->gst) cudaStreamDestroy(b->gst);
-  void* bufs[] = {b->d_prob, b->d_items, b->d_bprob, b->d_brow, b->x, b->r, b->p, b->ap, b->rhs, b->y, b->hy,
+  void* bufs[] = {b->d_prob, b->d_items, b->d_bprob, b->d_brow, b->x, b->r, b->p, b->ap, b->rhs, b->y, b->hy, b->hx,
                   b->sbuf, b->dpbuf, b->d_u1, b->d_u2, b->d_u3, b->d_bar,
                   b->psi64, b->hpsi64, b->prz, b->prr, b->rz, b->r0n, b->alpha, b->beta, b->active, b->still,
                   b->flags, b->part, b->S, b->G, b->eps, b->res, b->sigma, b->pshift};
@@ -1110,7 +1130,7 @@ int paro_batch_create(paro_batch** out, paro_ctx* const* ctxs, int n_ctx) {
   al((void**)&b->d_items, items.size() * sizeof(int2));
   al((void**)&b->d_bprob, b->nbt * sizeof(int));
   al((void**)&b->d_brow, b->nbt * sizeof(int));
-  for (void** q : {&b->x, &b->r, &b->p, &b->ap, &b->rhs, &b->y, &b->hy}) al(q, vb);
+  for (void** q : {&b->x, &b->r, &b->p, &b->ap, &b->rhs, &b->y, &b->hy, &b->hx}) al(q, vb);
   al((void**)&b->psi64, b->nelem * sizeof(double2));
   al((void**)&b->hpsi64, b->nelem * sizeof(double2));
   al((void**)&b->prz, (size_t)b->nbt * b->nch * sizeof(double));
@@ -1185,17 +1205,34 @@ int paro_batch_step(paro_batch* b, double rel_tol, int max_it, double* max_resid
   BCU(b, cudaEventRecord(b->ev, b->st));  // work queued on the contexts' stream comes first
   BCU(b, cudaStreamWaitEvent(b->gst, b->ev, 0));
   if ((st = refresh_scalars(b))) return st;
-  if (!b->exec || rel_tol != b->g_tol || max_it != b->g_maxit) {
-    if (b->exec) {
-      cudaGraphExecDestroy(b->exec);
-      b->exec = nullptr;
-    }
+  if (rel_tol != b->g_tol || max_it != b->g_maxit) {  // new parameters: both graphs are stale
+    for (cudaGraphExec_t* e : {&b->exec, &b->exec2})
+      if (*e) {
+        cudaGraphExecDestroy(*e);
+        *e = nullptr;
+      }
+    b->g_tol = rel_tol;
+    b->g_maxit = max_it;
+  }
+  // eight steps carry H X through the solves, the ninth applies H to the Rayleigh-Ritz basis directly, so
+  // the FP32 rounding of the carried H psi cannot accumulate
+  const bool carry = b->hx_recur < 8;
+  b->hx_recur = carry ? b->hx_recur + 1 : 0;
+  for (int form = 0; form < 2; ++form) {  // both graphs at once, so no capture falls inside later steps
+  const bool fcarry = form == 0;
+  cudaGraphExec_t& exec = fcarry ? b->exec : b->exec2;
+  long long& nk = fcarry ? b->graph_kernels : b->graph_kernels2;
+  if (!exec) {
     cudaGraph_t g = nullptr;
     cudaError_t ec = cudaSuccess;
     for (int attempt = 0; attempt < 2; ++attempt) {
       BCU(b, cudaStreamBeginCapture(b->gst, cudaStreamCaptureModeThreadLocal));
+      const long long k0 = b->graph_kernels;
       b->graph_kernels = 0;
-      st = b->f64 ? enqueue_step<double>(b, rel_tol, max_it) : enqueue_step<float>(b, rel_tol, max_it);
+      st = b->f64 ? enqueue_step<double>(b, rel_tol, max_it, fcarry)
+                  : enqueue_step<float>(b, rel_tol, max_it, fcarry);
+      nk = b->graph_kernels;
+      if (!fcarry) b->graph_kernels = k0;
       ec = cudaStreamEndCapture(b->gst, &g);
       if (st == PARO_OK && ec == cudaSuccess) break;
       if (g) cudaGraphDestroy(g);
@@ -1206,15 +1243,14 @@ int paro_batch_step(paro_batch* b, double rel_tol, int max_it, double* max_resid
     }
     if (st) return st;
     if (ec != cudaSuccess) return berr(b, PARO_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
-    const cudaError_t ei = cudaGraphInstantiate(&b->exec, g, 0);
+    const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
     if (ei != cudaSuccess) return berr(b, PARO_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
-    b->g_tol = rel_tol;
-    b->g_maxit = max_it;
   }
-  BCU(b, cudaGraphLaunch(b->exec, b->gst));
+  }
+  BCU(b, cudaGraphLaunch(carry ? b->exec : b->exec2, b->gst));
   BCU(b, cudaStreamSynchronize(b->gst));
-  b->lead->launches += b->graph_kernels;
+  b->lead->launches += carry ? b->graph_kernels : b->graph_kernels2;
   unsigned hb[3] = {0, 0, 0};
   BCU(b, cudaMemcpy(hb, b->d_bar, sizeof(hb), cudaMemcpyDeviceToHost));
   if (hb[2]) return berr(b, PARO_ERR_TIMEOUT, "batch: grid barrier wait gave up");
