@@ -470,9 +470,9 @@ static int reproject(Ctx* c, int ik) {
 // kHxRefresh such iterations one applies H directly, so the FP32 rounding of the carried H psi cannot
 // accumulate over many iterations.
 static const int kHxRefresh = 8;
-static bool carry_hx(Ctx* c, int alg) {
-  const bool carry = alg == PARO_ALG1 && c->hx_recur < kHxRefresh;
-  c->hx_recur = carry ? c->hx_recur + 1 : 0;
+static bool carry_hx(Basis& b, int alg) {
+  const bool carry = alg == PARO_ALG1 && b.hx_recur < kHxRefresh;
+  b.hx_recur = carry ? b.hx_recur + 1 : 0;
   return carry;
 }
 
@@ -481,7 +481,7 @@ template <typename T>
 static int paro_step_k(Ctx* c, int ik, int alg, double rel_tol, int max_it) {
   cplx<T>* X = rows_ws<T>(c, "X", ik);
   if (!X) return PARO_ERR_CUDA;
-  cplx<T>* HX = carry_hx(c, alg) ? rows_ws<T>(c, "HX", ik) : nullptr;
+  cplx<T>* HX = carry_hx(c->bases[ik], alg) ? rows_ws<T>(c, "HX", ik) : nullptr;
   int nx = c->nb;
   int st = source_step<T>(c, ik, alg, rel_tol, max_it, X, &nx, HX);
   return st ? st : project<T>(c, ik, X, nx, false, HX, nullptr);
@@ -504,11 +504,14 @@ static int scf_iteration(Ctx* c, const paro_scf_opts* o) {
   std::vector<cplx<T>*> xs(c->nk), hxs(c->nk, nullptr);
   std::vector<int> nxs(c->nk);
   int st;
-  const bool carry = carry_hx(c, o->alg);
+  bool carry = false;  // some k-point carries H X this iteration (then dV is needed)
   for (int ik = 0; ik < c->nk; ++ik) {
     xs[ik] = rows_ws<T>(c, "X", ik);
     if (!xs[ik]) return PARO_ERR_CUDA;
-    if (carry && !(hxs[ik] = rows_ws<T>(c, "HX", ik))) return PARO_ERR_CUDA;
+    if (carry_hx(c->bases[ik], o->alg)) {
+      if (!(hxs[ik] = rows_ws<T>(c, "HX", ik))) return PARO_ERR_CUDA;
+      carry = true;
+    }
     if ((st = source_step<T>(c, ik, o->alg, o->inner_rel_tol, o->inner_max_it, xs[ik], &nxs[ik], hxs[ik])))
       return st;
     if ((st = orthonormalize<T>(c, ik, xs[ik], nxs[ik], hxs[ik]))) return st;

@@ -14,6 +14,7 @@ namespace paro {
 
 // Plane-wave basis of one k-point (Eq. e3) with the z-column ("stick") structure the FFT passes use.
 struct Basis {
+  int hx_recur = 0;  // ParO iterations of this k-point since H of its Rayleigh-Ritz basis was applied directly
   int npw = 0;
   double kfrac[3] = {0, 0, 0};
   double kcart[3] = {0, 0, 0};
@@ -107,8 +108,7 @@ struct Ctx {
   // FP32 products may run on the tensor cores (3xTF32): inside the inexact inner solves and the adjoint,
   // not in the Rayleigh-Ritz step, the rotations or the energy, which fix the self-consistent result
   bool tc_scope = false;
-  int hx_recur = 0;
-  bool have_inv_g2 = false;  // the 1/|G|^2 table of the Hartree solve is in the "inv_g2" workspace  // ParO iterations since H of the Rayleigh-Ritz basis was last applied directly
+  bool have_inv_g2 = false;  // the 1/|G|^2 table of the Hartree solve is in the "inv_g2" workspace
 };
 
 // Status helpers (api.cu)
