@@ -208,6 +208,19 @@ int paro_solve_source(paro_ctx* ctx, int ik, int nb, int dtype, const double* ep
                       double rel_tol, int max_it, int* iters_out);
 
 /*
+ * paro_orthonormalize -- the orthonormalisation of Algorithm 1 between the source solutions (step 3)
+ * and the Rayleigh-Ritz step (step 4): n rows x_i of k-point ik become orthonormal rows y_i with
+ * span{y_1..y_m} = span{x_1..x_m} for every m (Gram-Schmidt in row order, done by Cholesky):
+ *   S_ij = <x_i, x_j> = sum_G conj(x_iG) x_jG,  S = L L^H (L lower),  y = conj(L)^{-1} x.
+ *   dtype  PARO_C64 (S accumulated in FP64) or PARO_C32 (FP32 rows; S as FP32 sums of 16 products
+ *          added into an FP32 two-sum pair); the factorisation and L^{-1} are FP64 for both.
+ *   x, y   device n x npw complex of dtype (row = band); y may equal x (in place), else must not overlap.
+ * Errors: PARO_ERR_ARG for a bad argument or n > npw; PARO_ERR_BREAKDOWN when a pivot of the
+ * factorisation is not positive (rows linearly dependent to working precision).
+ */
+int paro_orthonormalize(paro_ctx* ctx, int ik, int n, int dtype, const void* x, void* y);
+
+/*
  * paro_set_orbitals -- start vectors of k-point ik (Algorithm 1, step 1): n_bands x npw complex double,
  * host or device. The library orthonormalises them (Cholesky of the Gram matrix, band order) and takes
  * the Ritz pairs of their span under the current potential.

@@ -228,8 +228,9 @@ static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal, cplx<T>
       if ((st = chol_inv(c, nx, S, G))) return st;
     }
     ProfTag t(c, "orth");
-    if ((st = gemm_wx<T, T>(c, nx, npw, nx, G, nx, true, nullptr, X, npw, Y, npw, 0.0))) return st;
-    if (HX && (st = gemm_wx<T, T>(c, nx, npw, nx, G, nx, true, nullptr, HX, npw, HY, npw, 0.0))) return st;
+    if ((st = gemm_wx<T, T>(c, nx, npw, nx, G, nx, true, nullptr, X, npw, Y, npw, 0.0, nullptr, true))) return st;
+    if (HX && (st = gemm_wx<T, T>(c, nx, npw, nx, G, nx, true, nullptr, HX, npw, HY, npw, 0.0, nullptr, true)))
+      return st;
   }
   {
     ProfTag t(c, "rr");
@@ -368,19 +369,28 @@ static int build_alg2_basis(Ctx* c, int ik, cplx<T>* E, cplx<T>* X, int* nx_out)
   return PARO_OK;
 }
 
+static cudaEvent_t prof_event(Ctx* c) {
+  if (!c->prof_pool.empty()) {
+    cudaEvent_t e = c->prof_pool.back();
+    c->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
+}
+
 cudaEvent_t prof_begin(Ctx* c) {
   if (!c->prof) return nullptr;
-  cudaEvent_t a = nullptr;
-  if (cudaEventCreate(&a) != cudaSuccess) return nullptr;
-  cudaEventRecord(a, c->stream);
+  cudaEvent_t a = prof_event(c);
+  if (a) cudaEventRecord(a, c->stream);
   return a;
 }
 
 void prof_end(Ctx* c, const char* name, cudaEvent_t a) {
   if (!c->prof || !a) return;
-  cudaEvent_t b = nullptr;
-  if (cudaEventCreate(&b) != cudaSuccess) {
-    cudaEventDestroy(a);
+  cudaEvent_t b = prof_event(c);
+  if (!b) {
+    c->prof_pool.push_back(a);
     return;
   }
   cudaEventRecord(b, c->stream);
@@ -433,10 +443,10 @@ static int orthonormalize(Ctx* c, int ik, cplx<T>* X, int nx, cplx<T>* HX = null
     if ((st = chol_inv(c, nx, S, G))) return st;
   }
   ProfTag t(c, "orth");
-  if ((st = gemm_wx<T, T>(c, nx, npw, nx, G, nx, true, nullptr, X, npw, Y, npw, 0.0))) return st;
+  if ((st = gemm_wx<T, T>(c, nx, npw, nx, G, nx, true, nullptr, X, npw, Y, npw, 0.0, nullptr, true))) return st;
   PARO_CU(c, cudaMemcpyAsync(X, Y, (size_t)nx * npw * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, c->stream));
   if (HX) {  // H Y = G (H X): the same combination of the known H X
-    if ((st = gemm_wx<T, T>(c, nx, npw, nx, G, nx, true, nullptr, HX, npw, Y, npw, 0.0))) return st;
+    if ((st = gemm_wx<T, T>(c, nx, npw, nx, G, nx, true, nullptr, HX, npw, Y, npw, 0.0, nullptr, true))) return st;
     PARO_CU(c, cudaMemcpyAsync(HX, Y, (size_t)nx * npw * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, c->stream));
   }
   return PARO_OK;
@@ -696,6 +706,7 @@ void paro_destroy(paro_ctx* ctx) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
   }
+  for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete ctx;
 }
@@ -858,6 +869,20 @@ int paro_apply_h_adjoint(paro_ctx* ctx, int ik, int nb, int dtype, const void* p
   if (!c->have_veff) return fail(c, PARO_ERR_STATE, "no effective potential set");
   if (dtype == PARO_C64 && check_fft_support(c, 16)) return PARO_ERR_ARG;
   return apply_h_adjoint(c, ik, nb, dtype, psi, w, g_psi, g_v, g_pos);
+}
+
+int paro_orthonormalize(paro_ctx* ctx, int ik, int n, int dtype, const void* x, void* y) {
+  CTX_CHECK(ctx);
+  if (ik < 0 || ik >= c->nk || n < 1 || !x || !y || (dtype != PARO_C64 && dtype != PARO_C32))
+    return fail(c, PARO_ERR_ARG, "paro_orthonormalize: bad argument");
+  const int npw = c->bases[ik].npw;
+  if (n > npw) return fail(c, PARO_ERR_ARG, "paro_orthonormalize: more rows than plane waves");
+  const size_t bytes = (size_t)n * npw * (dtype == PARO_C64 ? sizeof(double2) : sizeof(float2));
+  const char *xb = static_cast<const char*>(x), *yb = static_cast<const char*>(y);
+  if (x != y && xb < yb + bytes && yb < xb + bytes) return fail(c, PARO_ERR_ARG, "paro_orthonormalize: x and y overlap");
+  if (x != y) PARO_CU(c, cudaMemcpyAsync(y, x, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  return dtype == PARO_C64 ? orthonormalize<double>(c, ik, static_cast<double2*>(y), n)
+                           : orthonormalize<float>(c, ik, static_cast<float2*>(y), n);
 }
 
 int paro_solve_source(paro_ctx* ctx, int ik, int nb, int dtype, const double* eps, const void* psi, void* x,
@@ -1050,11 +1075,16 @@ int paro_profile(paro_ctx* ctx, int enable) {
   CTX_CHECK(ctx);
   cudaStreamSynchronize(c->stream);
   for (auto& e : c->prof_ev) {
-    cudaEventDestroy(e.a);
-    cudaEventDestroy(e.b);
+    c->prof_pool.push_back(e.a);
+    c->prof_pool.push_back(e.b);
   }
   c->prof_ev.clear();
   c->prof = enable != 0;
+  while (c->prof && c->prof_pool.size() < 512) {  // created here, not inside the recorded region
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) break;
+    c->prof_pool.push_back(e);
+  }
   return PARO_OK;
 }
 

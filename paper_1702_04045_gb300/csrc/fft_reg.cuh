@@ -137,6 +137,87 @@ __device__ __forceinline__ void line_fwd(cplx<T>* v, int p, const cplx<T>* tw) {
   RegDft<T, Q, false>::run(v, tw, P);
 }
 
+// ---- variants with the P-point DFTs of step C done inside the lanes (Q >= P) ----
+// Step C needs, for every k1, a P-point DFT over the P lanes of a line. For k1 < P the values go
+// through a P x (P + 1) tile in shared memory (row k1 = the P lanes' values of that k1), and lane p
+// transforms row k1 = p in registers; the Q - P remaining k1 keep the shuffle stages. One exchange
+// through shared memory replaces log2(P) rounds of shuffles for P of the Q values.
+// Layout D_T after the inverse: lane p holds v[k2] = X[p + Q k2] (k2 < P) and, for k1 = P + j,
+// v[P + j] = X[P + j + Q bitrev(p)]; line_fwd_t maps D_T back to D_in.
+// The tile is element e at scr[e * es]: a line's own storage in shared memory (Q P >= P (P + 1)
+// elements), free once the line is in registers, or separate memory. ok = false (a lane group without
+// a line) skips the tile's stores; its loads must still fall inside shared memory.
+template <int Q, int P> __device__ __forceinline__ int dt_index(int p, int pr, int k) {
+  return k < P ? p + Q * k : k + Q * pr;
+}
+
+template <typename T, int Q, int P>
+__device__ __forceinline__ void line_inv_t(cplx<T>* v, int p, const cplx<T>* tw, cplx<T>* scr, int es, bool ok) {
+  static_assert(Q >= P && Q * P >= P * (P + 1), "line_inv_t needs Q >= P");
+  constexpr int N = Q * P;
+  __syncwarp();  // every lane has loaded its values before the line's storage is reused
+  RegDft<T, Q, true>::run(v, tw, P);
+#pragma unroll
+  for (int k1 = 1; k1 < Q; ++k1)
+    if (p) v[k1] = cmul(v[k1], tw_get<T, true>(tw, p * k1));
+#pragma unroll
+  for (int h = P / 2; h >= 1; h >>= 1) {  // shuffle stages for k1 >= P only
+    const bool up = (p & h) != 0;
+    const cplx<T> w = tw_get<T, true>(tw, (p & (h - 1)) * (N / (2 * h)));
+#pragma unroll
+    for (int q = P; q < Q; ++q) {
+      const cplx<T> b = shfl_xor_c<T>(v[q], h);
+      v[q] = up ? cmul(csub(b, v[q]), w) : cadd(v[q], b);
+    }
+  }
+  if (ok)
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) scr[(k1 * (P + 1) + p) * es] = v[k1];
+  __syncwarp();
+  cplx<T> u[P];
+#pragma unroll
+  for (int j = 0; j < P; ++j) u[j] = scr[(p * (P + 1) + j) * es];
+  __syncwarp();
+  RegDft<T, P, true>::run(u, tw, Q);
+#pragma unroll
+  for (int k2 = 0; k2 < P; ++k2) v[k2] = u[k2];
+}
+
+template <typename T, int Q, int P>
+__device__ __forceinline__ void line_fwd_t(cplx<T>* v, int p, const cplx<T>* tw, cplx<T>* scr, int es, bool ok) {
+  static_assert(Q >= P && Q * P >= P * (P + 1), "line_fwd_t needs Q >= P");
+  constexpr int N = Q * P;
+  __syncwarp();  // every lane has loaded its values before the line's storage is reused
+  {
+    cplx<T> u[P];
+#pragma unroll
+    for (int k2 = 0; k2 < P; ++k2) u[k2] = v[k2];
+    RegDft<T, P, false>::run(u, tw, Q);
+    if (ok)
+#pragma unroll
+      for (int j = 0; j < P; ++j) scr[(p * (P + 1) + j) * es] = u[j];
+  }
+#pragma unroll
+  for (int h = 1; h < P; h <<= 1) {  // shuffle stages for k1 >= P only
+    const bool up = (p & h) != 0;
+    const cplx<T> wc = tw_get<T, false>(tw, (p & (h - 1)) * (N / (2 * h)));
+#pragma unroll
+    for (int q = P; q < Q; ++q) {
+      const cplx<T> t = up ? cmul(v[q], wc) : v[q];
+      const cplx<T> o = shfl_xor_c<T>(t, h);
+      v[q] = up ? csub(o, t) : cadd(t, o);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k1 = 0; k1 < P; ++k1) v[k1] = scr[(k1 * (P + 1) + p) * es];
+  __syncwarp();
+#pragma unroll
+  for (int k1 = 1; k1 < Q; ++k1)
+    if (p) v[k1] = cmul(v[k1], tw_get<T, false>(tw, p * k1));
+  RegDft<T, Q, false>::run(v, tw, P);
+}
+
 // Factorisations N = Q * P used by the register kernels (P lanes per line, Q values per lane).
 template <int N> struct LineShape;
 template <> struct LineShape<32> { static constexpr int Q = 4, P = 8; };

@@ -6,6 +6,16 @@
 // Register-FFT versions of the three passes for cubic grids N^3 with N in {32, 36, 48, 72, 128}
 // (line FFTs of fft_reg.cuh: one group of P lanes per line, Q values per lane).
 // ------------------------------------------------------------------------------------------------
+// FP32 lines with Q > P keep step C in the lanes (line_inv_t / line_fwd_t). The z-passes and the density
+// pass exchange through the line's own storage in shared memory; the plane pass, whose column tiles
+// would meet two-way bank conflicts in both directions, gives each lane group of a warp its own tile
+// (kWarpTile elements per warp).
+template <typename T, int N> struct PlaneLines {
+  static constexpr int Q = LineShape<N>::Q, P = LineShape<N>::P;
+  static constexpr bool kTile = sizeof(T) == 4 && Q > P;
+  static constexpr int kWarpTile = kTile ? (32 / P) * P * (P + 1) : 0;
+};
+
 template <typename T, int N3>
 __global__ void __launch_bounds__(256) k_zpass_inv_reg(const cplx<T>* __restrict__ psi, int ldpsi,
                                                        cplx<T>* __restrict__ S, const int* __restrict__ col_off,
@@ -37,11 +47,12 @@ __global__ void __launch_bounds__(256) k_zpass_inv_reg(const cplx<T>* __restrict
     cplx<T> v[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) v[q] = ok ? ln[P * q + p] : mk<T>(0, 0);
-    line_inv<T, Q, P>(v, p, tw);
+    if constexpr (PlaneLines<T, N3>::kTile) line_inv_t<T, Q, P>(v, p, tw, ln, 1, ok);
+    else line_inv<T, Q, P>(v, p, tw);
     __syncwarp();
     if (ok)
 #pragma unroll
-      for (int k = 0; k < Q; ++k) ln[k + Q * pr] = v[k];
+      for (int k = 0; k < Q; ++k) ln[PlaneLines<T, N3>::kTile ? dt_index<Q, P>(p, pr, k) : k + Q * pr] = v[k];
     __syncwarp();
   }
   __syncthreads();
@@ -60,11 +71,15 @@ __global__ void __launch_bounds__(256) k_plane_reg(cplx<T>* __restrict__ S, int 
                                                    const int* __restrict__ active) {
   using SX = LineShape<N1>;
   using SY = LineShape<N2>;
+  using LX = PlaneLines<T, N1>;
+  using LY = PlaneLines<T, N2>;
   constexpr int LS = N2 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* tx = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* ty = tx + N1;
   cplx<T>* Pl = ty + N2;
+  cplx<T>* tiles = Pl + N1 * LS;  // per warp: the larger of the two lines' kWarpTile
+  constexpr int kWT = LX::kWarpTile > LY::kWarpTile ? LX::kWarpTile : LY::kWarpTile;
   const int z = blockIdx.x, b = blockIdx.y, N3 = gridDim.x;
   if (active != nullptr && active[b] == 0) return;
   for (int i = threadIdx.x; i < N1; i += blockDim.x) tx[i] = twx[i];
@@ -85,11 +100,12 @@ __global__ void __launch_bounds__(256) k_plane_reg(cplx<T>* __restrict__ S, int 
       cplx<T> v[Q];
 #pragma unroll
       for (int q = 0; q < Q; ++q) v[q] = ok ? row[P * q + p] : mk<T>(0, 0);
-      line_inv<T, Q, P>(v, p, ty);
+      if constexpr (LY::kTile) line_inv_t<T, Q, P>(v, p, ty, tiles + warp * kWT + grp * P * (P + 1), 1, true);
+      else line_inv<T, Q, P>(v, p, ty);
       __syncwarp();
       if (ok)
 #pragma unroll
-        for (int k = 0; k < Q; ++k) row[k + Q * pr] = v[k];
+        for (int k = 0; k < Q; ++k) row[LY::kTile ? dt_index<Q, P>(p, pr, k) : k + Q * pr] = v[k];
       __syncwarp();
     }
   }
@@ -104,10 +120,18 @@ __global__ void __launch_bounds__(256) k_plane_reg(cplx<T>* __restrict__ S, int 
       cplx<T> v[Q];
 #pragma unroll
       for (int q = 0; q < Q; ++q) v[q] = ok ? Pl[(P * q + p) * LS + y] : mk<T>(0, 0);
-      line_inv<T, Q, P>(v, p, tx);
+      if constexpr (LX::kTile) {
+        cplx<T>* tile = tiles + warp * kWT + grp * P * (P + 1);
+        line_inv_t<T, Q, P>(v, p, tx, tile, 1, true);
 #pragma unroll
-      for (int k = 0; k < Q; ++k) v[k] = cscale(v[k], ok ? V[(k + Q * pr) * N2 + y] : (T)0);
-      line_fwd<T, Q, P>(v, p, tx);
+        for (int k = 0; k < Q; ++k) v[k] = cscale(v[k], ok ? V[dt_index<Q, P>(p, pr, k) * N2 + y] : (T)0);
+        line_fwd_t<T, Q, P>(v, p, tx, tile, 1, true);
+      } else {
+        line_inv<T, Q, P>(v, p, tx);
+#pragma unroll
+        for (int k = 0; k < Q; ++k) v[k] = cscale(v[k], ok ? V[(k + Q * pr) * N2 + y] : (T)0);
+        line_fwd<T, Q, P>(v, p, tx);
+      }
       if (ok)
 #pragma unroll
         for (int q = 0; q < Q; ++q) Pl[(P * q + p) * LS + y] = v[q];
@@ -123,8 +147,9 @@ __global__ void __launch_bounds__(256) k_plane_reg(cplx<T>* __restrict__ S, int 
       cplx<T>* row = Pl + (ok ? xrows[r] : 0) * LS;
       cplx<T> v[Q];
 #pragma unroll
-      for (int k = 0; k < Q; ++k) v[k] = ok ? row[k + Q * pr] : mk<T>(0, 0);
-      line_fwd<T, Q, P>(v, p, ty);
+      for (int k = 0; k < Q; ++k) v[k] = ok ? row[LY::kTile ? dt_index<Q, P>(p, pr, k) : k + Q * pr] : mk<T>(0, 0);
+      if constexpr (LY::kTile) line_fwd_t<T, Q, P>(v, p, ty, tiles + warp * kWT + grp * P * (P + 1), 1, true);
+      else line_fwd<T, Q, P>(v, p, ty);
       __syncwarp();
       if (ok)
 #pragma unroll
@@ -169,8 +194,9 @@ __global__ void __launch_bounds__(256) k_zpass_fwd_reg(const cplx<T>* __restrict
     cplx<T>* ln = line + (ok ? l : 0) * LS;
     cplx<T> v[Q];
 #pragma unroll
-    for (int k = 0; k < Q; ++k) v[k] = ok ? ln[k + Q * pr] : mk<T>(0, 0);
-    line_fwd<T, Q, P>(v, p, tw);
+    for (int k = 0; k < Q; ++k) v[k] = ok ? ln[PlaneLines<T, N3>::kTile ? dt_index<Q, P>(p, pr, k) : k + Q * pr] : mk<T>(0, 0);
+    if constexpr (PlaneLines<T, N3>::kTile) line_fwd_t<T, Q, P>(v, p, tw, ln, 1, ok);
+    else line_fwd<T, Q, P>(v, p, tw);
     __syncwarp();
     if (ok)
 #pragma unroll
@@ -210,7 +236,7 @@ static int passes_reg(Ctx* c, const Basis& B, int nb, const cplx<T>* psi, cplx<T
   const int eb = (int)sizeof(cplx<T>);
   const bool f64 = sizeof(T) == 8;
   const size_t smz = (size_t)eb * (N + kStickBatch * (N + 1));
-  const size_t smp = (size_t)eb * (2 * N + N * (N + 1));
+  const size_t smp = (size_t)eb * (2 * N + N * (N + 1) + 8 * PlaneLines<T, N>::kWarpTile);  // 8 warps
   int st;
   if ((st = set_smem_once(c, k_zpass_inv_reg<T, N>, done[0])) || (st = set_smem_once(c, k_plane_reg<T, N, N>, done[1])) ||
       (st = set_smem_once(c, k_zpass_fwd_reg<T, N>, done[2])) ||
@@ -304,11 +330,12 @@ __global__ void __launch_bounds__(256) k_plane_density_reg(const cplx<T>* __rest
         cplx<T> v[Q];
 #pragma unroll
         for (int q = 0; q < Q; ++q) v[q] = ok ? row[P * q + p] : mk<T>(0, 0);
-        line_inv<T, Q, P>(v, p, ty);
+        if constexpr (PlaneLines<T, N2>::kTile) line_inv_t<T, Q, P>(v, p, ty, row, 1, ok);
+        else line_inv<T, Q, P>(v, p, ty);
         __syncwarp();
         if (ok)
 #pragma unroll
-          for (int k = 0; k < Q; ++k) row[k + Q * pr] = v[k];
+          for (int k = 0; k < Q; ++k) row[PlaneLines<T, N2>::kTile ? dt_index<Q, P>(p, pr, k) : k + Q * pr] = v[k];
         __syncwarp();
       }
     }
@@ -322,12 +349,13 @@ __global__ void __launch_bounds__(256) k_plane_density_reg(const cplx<T>* __rest
         cplx<T> v[Q];
 #pragma unroll
         for (int q = 0; q < Q; ++q) v[q] = ok ? Pl[(P * q + p) * LS + y] : mk<T>(0, 0);
-        line_inv<T, Q, P>(v, p, tx);
+        if constexpr (PlaneLines<T, N1>::kTile) line_inv_t<T, Q, P>(v, p, tx, Pl + (ok ? y : 0), LS, ok);
+        else line_inv<T, Q, P>(v, p, tx);
         if (ok)
 #pragma unroll
           for (int k = 0; k < Q; ++k) {
             const TACC re = v[k].x, im = v[k].y;
-            acc[(k + Q * pr) * N2 + y] += re * re + im * im;
+            acc[(PlaneLines<T, N1>::kTile ? dt_index<Q, P>(p, pr, k) : k + Q * pr) * N2 + y] += re * re + im * im;
           }
       }
     }

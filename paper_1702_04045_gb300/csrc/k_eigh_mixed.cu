@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(256) k_zgemm16(int n, const double2* __restric
                                                  const double2* __restrict__ B, double2* __restrict__ part,
                                                  int kslice) {
   __shared__ double2 As[16][17], Bs[16][17];
+  if (ah > 1 && blockIdx.y < blockIdx.x) return;  // Hermitian result: tiles on and below the diagonal
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
   const int i0 = blockIdx.y * 16, j0 = blockIdx.x * 16;
   const int k0 = blockIdx.z * kslice, k1 = min(n, k0 + kslice);
@@ -202,12 +203,32 @@ __global__ void __launch_bounds__(256) k_zgemm16(int n, const double2* __restric
   if (i < n && jj < n) part[(size_t)blockIdx.z * n * n + (size_t)i * n + jj] = acc;
 }
 
-__global__ void k_zreduce(int n, int nz, const double2* __restrict__ part, double2* __restrict__ C, int add) {
+// nrm (optional, one float per CTA of 256 threads): the CTA's sum of |C_ij - d_ij|^2 over i != j plus, when
+// unit, |C_ii - 1|^2 on the diagonal (in FP32: it only sets the refinement's cluster threshold)
+__global__ void __launch_bounds__(256) k_zreduce(int n, int nz, const double2* __restrict__ part,
+                                                 double2* __restrict__ C, int add, int herm,
+                                                 float* __restrict__ nrm, int unit) {
+  __shared__ float red[32];
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n * n) return;
-  double2 s = add ? C[idx] : make_double2(0.0, 0.0);
-  for (int z = 0; z < nz; ++z) s = cadd(s, part[(size_t)z * n * n + idx]);
-  C[idx] = s;
+  float e = 0.f;
+  if (idx < n * n) {
+    const int i = idx / n, j = idx - i * n;
+    const bool mirror = herm && (i >> 4) < (j >> 4);  // tile above the diagonal: conj of the (j, i) sum
+    const size_t src = mirror ? (size_t)j * n + i : (size_t)idx;
+    double2 s = make_double2(0.0, 0.0);
+    for (int z = 0; z < nz; ++z) s = cadd(s, part[(size_t)z * n * n + src]);
+    if (mirror) s = cconj(s);
+    if (add) s = cadd(C[idx], s);
+    C[idx] = s;
+    if (nrm && (i != j || unit)) {
+      const float x = (float)(i == j ? s.x - 1.0 : s.x), y = (float)s.y;
+      e = x * x + y * y;
+    }
+  }
+  if (nrm) {
+    e = block_sumf(e, red);
+    if (threadIdx.x == 0) nrm[blockIdx.x] = e;
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -216,51 +237,59 @@ __global__ void k_zreduce(int n, int nz, const double2* __restrict__ part, doubl
 // cluster threshold, so its norms are summed in FP32 (no FP64 pipe on the n^2 sweep).
 // ------------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_refine_lam(int n, const double2* __restrict__ G,
-                                                     const double2* __restrict__ S, double* __restrict__ lam,
-                                                     int* __restrict__ cl, int* __restrict__ cst,
-                                                     int* __restrict__ ncl) {
+                                                     const double2* __restrict__ S, const float* __restrict__ nrm,
+                                                     int nnrm, double* __restrict__ lam, int* __restrict__ cl,
+                                                     int* __restrict__ cst, int* __restrict__ ncl) {
   __shared__ float red[32];
   __shared__ double s_lam[kMixMaxN];
-  const int tid = threadIdx.x;
+  __shared__ int s_wc[32];
+  __shared__ double s_delta;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < n; i += blockDim.x) {
     const double l = S[(size_t)i * n + i].x / G[(size_t)i * n + i].x;
     lam[i] = l;
     s_lam[i] = l;
   }
-  __syncthreads();
+  // ||S - diag||_F^2 (off-diagonal part) and ||I - G||_F^2 from the per-CTA sums of k_zreduce
   float ns = 0.f, nr = 0.f, na = 0.f;
-  for (int idx = tid; idx < n * n; idx += blockDim.x) {
-    const int i = idx / n, j = idx - i * n;
-    const double2 sv = S[idx], gv = G[idx];
-    const float sx = (float)(i == j ? sv.x - s_lam[i] : sv.x), sy = (float)sv.y;
-    const float rx = (float)(i == j ? 1.0 - gv.x : -gv.x), ry = (float)(-gv.y);
-    ns = fmaf(sx, sx, fmaf(sy, sy, ns));
-    nr = fmaf(rx, rx, fmaf(ry, ry, nr));
+  for (int b = tid; b < nnrm; b += blockDim.x) {
+    nr += nrm[b];
+    ns += nrm[nnrm + b];
   }
-  for (int i = tid; i < n; i += blockDim.x) na = fmaxf(na, (float)fabs(s_lam[i]));
+  __syncthreads();
+  for (int i = tid; i < n; i += blockDim.x) na = fmaxf(na, fabsf((float)s_lam[i]));
   ns = block_sumf(ns, red);
   __syncthreads();
   nr = block_sumf(nr, red);
   __syncthreads();
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) na = fmaxf(na, __shfl_xor_sync(0xffffffffu, na, o));
-  if ((tid & 31) == 0) red[tid >> 5] = na;
+  if (lane == 0) red[warp] = na;
   __syncthreads();
   if (tid == 0) {
     float mx = 0.f;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w]);
     // clusters: at least the FP32 solver's own (eigenvalues closer than 1e-3 ||A||, whose vectors inverse
     // iteration only orthogonalised), so that every pair corrected below is already accurate to first order
-    const double delta = fmax(2.0 * ((double)sqrtf(ns) + (double)mx * (double)sqrtf(nr)), 1e-3 * (double)mx);
-    int c = 0;
-    cst[0] = 0;
-    cl[0] = 0;
-    for (int i = 1; i < n; ++i) {
-      if (s_lam[i] - s_lam[i - 1] > delta) cst[++c] = i;
-      cl[i] = c;
+    s_delta = fmax(2.0 * ((double)sqrtf(ns) + (double)mx * (double)sqrtf(nr)), 1e-3 * (double)mx);
+  }
+  __syncthreads();
+  // a new cluster starts at i when lambda_i - lambda_{i-1} > delta: cluster index = inclusive count of
+  // starts up to i (ballot within a warp, then the warps' counts in order)
+  const int nw = (n + 31) / 32;
+  const bool start = tid < n && tid > 0 && s_lam[tid] - s_lam[tid - 1] > s_delta;
+  const unsigned bal = warp < nw ? __ballot_sync(0xffffffffu, start) : 0u;
+  if (warp < nw && lane == 0) s_wc[warp] = __popc(bal);
+  __syncthreads();
+  if (tid < n) {
+    int c = __popc(bal & (0xffffffffu >> (31 - lane)));
+    for (int w = 0; w < warp; ++w) c += s_wc[w];
+    cl[tid] = c;
+    if (tid == 0 || start) cst[c] = tid;
+    if (tid == n - 1) {
+      cst[c + 1] = n;
+      *ncl = c + 1;
     }
-    cst[c + 1] = n;
-    *ncl = c + 1;
   }
 }
 
@@ -390,15 +419,20 @@ __global__ void k_herm_full_mixed(int n, const double2* __restrict__ Ain, double
   A[idx] = (i >= j) ? Ain[idx] : cconj(Ain[(size_t)j * n + i]);
 }
 
-// C = op(A) B (+ C), n x n FP64
-static int zgemm(Ctx* c, int n, const double2* A, bool ah, const double2* B, double2* C, bool add, double2* part) {
+// C = op(A) B (+ C), n x n FP64. herm: the result is Hermitian (A^H A, or A^H M A with B = M A), so only
+// the tiles on and below the diagonal are computed and the rest mirrored.
+static int zgemm(Ctx* c, int n, const double2* A, bool ah, const double2* B, double2* C, bool add, double2* part,
+                 bool herm = false, float* nrm = nullptr, bool unit = false) {
   const int nz = std::max(1, std::min(8, (n + 47) / 48));
   const int kslice = ((n + nz - 1) / nz + 15) / 16 * 16;
   const int z = (n + kslice - 1) / kslice;
   const int t = (n + 15) / 16;
-  k_zgemm16<<<dim3(t, t, z), 256, 0, c->stream>>>(n, A, ah ? 1 : 0, B, part, kslice);
+  cudaEvent_t ev = prof_begin(c);
+  k_zgemm16<<<dim3(t, t, z), 256, 0, c->stream>>>(n, A, ah ? (herm ? 2 : 1) : 0, B, part, kslice);
   PARO_LAUNCH(c, "k_zgemm16");
-  k_zreduce<<<(n * n + 255) / 256, 256, 0, c->stream>>>(n, z, part, C, add ? 1 : 0);
+  k_zreduce<<<(n * n + 255) / 256, 256, 0, c->stream>>>(n, z, part, C, add ? 1 : 0, herm ? 1 : 0, nrm,
+                                                        unit ? 1 : 0);
+  prof_end(c, "zgemm", ev);
   PARO_LAUNCH(c, "k_zreduce");
   return PARO_OK;
 }
@@ -416,6 +450,9 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
   float2* V32 = static_cast<float2*>(ws_get(c, "em_V32", nn * sizeof(float2)));
   float* Z32 = static_cast<float*>(ws_get(c, "em_Z32", nn * sizeof(float)));
   float* r32 = static_cast<float*>(ws_get(c, "em_r32", (size_t)6 * n * sizeof(float)));
+  const int nnrm = (int)((nn + 255) / 256);  // per-CTA norm sums of G and of S, for the cluster threshold
+  float* nrm = static_cast<float*>(ws_get(c, "em_nrm", (size_t)2 * nnrm * sizeof(float)));
+  if (!nrm) return PARO_ERR_CUDA;
   double* lam = static_cast<double*>(ws_get(c, "em_lam", (size_t)n * sizeof(double)));
   int* ib = static_cast<int*>(ws_get(c, "em_int", (size_t)(3 * n + 8) * sizeof(int)));
   if (!Af || !X || !T1 || !G || !S || !part || !U32 || !V32 || !Z32 || !r32 || !lam || !ib) return PARO_ERR_CUDA;
@@ -444,19 +481,25 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
   k_f2d<<<(int)((nn + 255) / 256), 256, 0, c->stream>>>((int)nn, V32, X);
   PARO_LAUNCH(c, "k_f2d");
   for (int it = 0; it < refine_steps; ++it) {
-    if ((st = zgemm(c, n, X, true, X, G, false, part))) return st;    // G = X^H X
-    if ((st = zgemm(c, n, Af, false, X, T1, false, part))) return st;  // T1 = A X
-    if ((st = zgemm(c, n, X, true, T1, S, false, part))) return st;    // S = X^H A X
-    k_refine_lam<<<1, 1024, 0, c->stream>>>(n, G, S, lam, cl, cst, ncl);
+    if ((st = zgemm(c, n, X, true, X, G, false, part, true, nrm, true))) return st;          // G = X^H X
+    if ((st = zgemm(c, n, Af, false, X, T1, false, part))) return st;                         // T1 = A X
+    if ((st = zgemm(c, n, X, true, T1, S, false, part, true, nrm + nnrm, false))) return st;  // S = X^H A X
+    cudaEvent_t ev2 = prof_begin(c);
+    k_refine_lam<<<1, 1024, 0, c->stream>>>(n, G, S, nrm, nnrm, lam, cl, cst, ncl);
     PARO_LAUNCH(c, "k_refine_lam");
+    prof_end(c, "k_refine_lam", ev2);
+    ev2 = prof_begin(c);
     k_refine_e<<<(n * n + 255) / 256, 256, 0, c->stream>>>(n, G, S, lam, cl, T1);  // T1 = E
     PARO_LAUNCH(c, "k_refine_e");
+    prof_end(c, "k_refine_e", ev2);
     if ((st = zgemm(c, n, X, false, T1, X, true, part))) return st;    // X += X E
   }
   if ((st = zgemm(c, n, Af, false, X, T1, false, part))) return st;    // T1 = A X
   if (refine_steps > 0) {  // the clusters exist: S = X^H A X inside them only
+    cudaEvent_t ev2 = prof_begin(c);
     k_blockdiag_xhat<<<(int)((nn + 7) / 8), 256, 0, c->stream>>>(n, X, T1, cl, S);
     PARO_LAUNCH(c, "k_blockdiag_xhat");
+    prof_end(c, "k_blockdiag_xhat", ev2);
   } else if ((st = zgemm(c, n, X, true, T1, S, false, part))) {
     return st;
   }

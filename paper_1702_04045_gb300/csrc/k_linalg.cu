@@ -377,7 +377,10 @@ __global__ void k_w_to_f32(int M, int K, const double2* __restrict__ W, int ldw,
   }
 }
 
-template <int RM, int RN>
+// Thread (ty, tx) holds rows tm + RM ty + i (i < RM) and columns tn + tx + 16 j (j < RN), so a warp
+// (two ty) holds 2 RM consecutive rows. LW: W(k, m) = 0 for k > m; a warp skips the K steps that lie
+// beyond its last row, and the CTA those beyond its tile's last row.
+template <int RM, int RN, bool LW = false>
 __global__ void __launch_bounds__(256) k_gemm_wx32(int M, int N, int K, const float2* __restrict__ Wf,
                                                    const float2* __restrict__ X, int ldx, float2* __restrict__ Y,
                                                    int ldy, float beta) {
@@ -406,8 +409,9 @@ __global__ void __launch_bounds__(256) k_gemm_wx32(int M, int N, int K, const fl
   for (int i = 0; i < RM; ++i)
 #pragma unroll
     for (int j = 0; j < RN; ++j) acc[i][j] = make_float2(0.f, 0.f);
-  const int nk = (K + 15) / 16;
+  const int nk = LW ? min((K + 15) / 16, (tm + TM + 15) / 16) : (K + 15) / 16;
   if (nk > 0) stage(0, 0);
+  const int warp_last_row = tm + RM * (ty | 1) + RM - 1;
   for (int kt = 0; kt < nk; ++kt) {
     if (kt + 1 < nk) {
       stage(16 * (kt + 1), (kt + 1) & 1);  // the other buffer: its readers passed the barrier below
@@ -418,13 +422,14 @@ __global__ void __launch_bounds__(256) k_gemm_wx32(int M, int N, int K, const fl
     __syncthreads();
     const float2* Ws = wx_smem + (kt & 1) * STG;
     const float2* Xs = Ws + 16 * TM;
+    if (!LW || 16 * kt <= warp_last_row)
 #pragma unroll 4
     for (int kx = 0; kx < 16; ++kx) {
       float2 x[RN], w[RM];
 #pragma unroll
       for (int j = 0; j < RN; ++j) x[j] = Xs[kx * TN + tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < RM; ++i) w[i] = Ws[kx * TM + ty + 16 * i];
+      for (int i = 0; i < RM; ++i) w[i] = Ws[kx * TM + RM * ty + i];
 #pragma unroll
       for (int i = 0; i < RM; ++i)
 #pragma unroll
@@ -439,7 +444,7 @@ __global__ void __launch_bounds__(256) k_gemm_wx32(int M, int N, int K, const fl
   }
 #pragma unroll
   for (int i = 0; i < RM; ++i) {
-    const int m = tm + ty + 16 * i;
+    const int m = tm + RM * ty + i;
     if (m >= M) continue;
 #pragma unroll
     for (int j = 0; j < RN; ++j) {
@@ -458,7 +463,7 @@ __global__ void __launch_bounds__(256) k_gemm_wx32(int M, int N, int K, const fl
 // launch of k_gemm_wx32: RM = 9 (144-row blocks) unless M fits 64 rows; RN (32 or 64 columns) with the
 // smaller makespan in waves of 152 SMs x resident CTAs
 static int launch_wx32(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, const double* s,
-                       const float2* X, int ldx, float2* Y, int ldy, double beta, float2* Wf) {
+                       const float2* X, int ldx, float2* Y, int ldy, double beta, float2* Wf, bool lower) {
   const bool big = M > 64;
   const int tm = big ? 144 : 64;
   const int mt = (M + tm - 1) / tm;
@@ -481,9 +486,13 @@ static int launch_wx32(Ctx* c, int M, int N, int K, const double2* W, int ldw, b
   PARO_CU(c, cudaGetDevice(&dev));
   if (attr_dev != dev) {
     PARO_CU(c, cudaFuncSetAttribute(k_gemm_wx32<9, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+    PARO_CU(c, cudaFuncSetAttribute(k_gemm_wx32<9, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
     attr_dev = dev;
   }
-  if (big) {
+  if (big && lower) {
+    if (rn4) k_gemm_wx32<9, 4, true><<<grid, 256, sm, c->stream>>>(M, N, K, Wf, X, ldx, Y, ldy, fb);
+    else k_gemm_wx32<9, 2, true><<<grid, 256, sm, c->stream>>>(M, N, K, Wf, X, ldx, Y, ldy, fb);
+  } else if (big) {
     if (rn4) k_gemm_wx32<9, 4><<<grid, 256, sm, c->stream>>>(M, N, K, Wf, X, ldx, Y, ldy, fb);
     else k_gemm_wx32<9, 2><<<grid, 256, sm, c->stream>>>(M, N, K, Wf, X, ldx, Y, ldy, fb);
   } else {
@@ -496,7 +505,7 @@ static int launch_wx32(Ctx* c, int M, int N, int K, const double2* W, int ldw, b
 
 template <typename TX, typename TY>
 int gemm_wx(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, const double* s, const cplx<TX>* X,
-            int ldx, cplx<TY>* Y, int ldy, double beta, float2* wf) {
+            int ldx, cplx<TY>* Y, int ldy, double beta, float2* wf, bool lower) {
   if (M <= 0 || N <= 0) return PARO_OK;
   if constexpr (sizeof(TX) == 4 && sizeof(TY) == 4) {
     if (c->tc_scope && tc_enabled()) {
@@ -509,7 +518,7 @@ int gemm_wx(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, con
       return PARO_OK;
     }
     cudaEvent_t ev = prof_begin(c);
-    int st = launch_wx32(c, M, N, K, W, ldw, wt, s, X, ldx, Y, ldy, beta, wf);
+    int st = launch_wx32(c, M, N, K, W, ldw, wt, s, X, ldx, Y, ldy, beta, wf, lower);
     if (st) return st;
     prof_end(c, "k_gemm_wx<f32>", ev);
     return PARO_OK;
@@ -676,64 +685,296 @@ __global__ void __launch_bounds__(1024) k_chol_cluster(int n, const double2* __r
   cl.sync();  // no CTA leaves while another may still write into its shared memory
 }
 
-// cluster size (16, else 8; 0 = neither fits) and threads for k_chol_cluster
-static int chol_cluster_shape(Ctx* c, int n, int* cls, int* thr, size_t* smem) {
-  *cls = 0;
-  PARO_CU(c, cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-  PARO_CU(c, cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  for (int C : {16, 8}) {
-    const int R = (n + C - 1) / C;
-    const size_t sm = ((size_t)R * 2 * n + 4 * (size_t)n) * sizeof(double2);  // rows, two pivot buffers
-    if (sm > 200 * 1024) continue;
-    const int warps = R < 4 ? 4 : (R > 32 ? 32 : R);
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = C;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(C);
-    cfg.blockDim = dim3(32 * warps);
-    cfg.dynamicSmemBytes = sm;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, k_chol_cluster, &cfg) != cudaSuccess) {
-      cudaGetLastError();
-      continue;
-    }
-    if (nclusters >= 1) {
-      *cls = C;
-      *thr = 32 * warps;
-      *smem = sm;
-      return PARO_OK;
+// Blocked form of the same factorisation (right-looking block Cholesky, blocks of C columns, row g in
+// CTA g mod C, so each CTA owns exactly one row of every block). Block J (columns c0 .. c1 - 1) takes
+// two cluster barriers instead of one per column:
+//   every CTA factors the pushed diagonal block D = A_JJ itself by elimination of [D | I] (giving
+//   D = L_u diag(d) L_u^H and L_u^{-1}, so L_JJ^{-1} = diag(d)^{-1/2} L_u^{-1});
+//   each CTA forms the panel rows L_iJ = A_iJ L_JJ^{-H} of its rows below the block, and the owner
+//   of diagonal row t the finished row t of L^{-1}, (L_JJ^{-1} B_J)_t, where B_J holds the rows of
+//   the block after the earlier block updates of the right half; both go to every CTA; barrier;
+//   each CTA updates its rows below: a_ik -= L_iJ conj(L_kJ) (lower triangle), b_ik -= L_iJ (L^{-1})_Jk;
+//   the owners of the next block push its diagonal rows; barrier.
+// Shared memory (double2): rows R x 2n ([a_i | b_i]), panel C x n (pan[s][k] = L_k,c0+s), linv C x n
+// (rows of L^{-1} of the block), brow C x n (pushed B_J), dblk, dinv C x C. info as k_chol_cluster.
+// acc + a b and acc + a conj(b) as four FMAs
+__device__ __forceinline__ double2 zfma(double2 acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+  return acc;
+}
+__device__ __forceinline__ double2 zfma_conj(double2 acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.y, b.x, acc.y);
+  acc.y = fma(-a.x, b.y, acc.y);
+  return acc;
+}
+
+__global__ void __launch_bounds__(512) k_chol_blocked(int n, const double2* __restrict__ s, double2* __restrict__ g,
+                                                      int* __restrict__ info) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), q = (int)cl.block_rank();
+  const int R = (n + C - 1) / C, W2 = 2 * n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* rows = reinterpret_cast<double2*>(smem_raw);  // R x 2n
+  double2* pan = rows + (size_t)R * W2;                  // C x n
+  double2* linv = pan + (size_t)C * n;                   // C x n
+  double2* brow = linv + (size_t)C * n;                  // C x n
+  double2* dblk = brow + (size_t)C * n;                  // C x C (lower)
+  double2* dinv = dblk + C * C;                          // C x C (lower)
+  __shared__ double s_rcp[32], s_isq[32];
+  __shared__ int s_bad, s_off[64];
+  __shared__ unsigned char s_trow[16 * 17 / 2], s_tcol[16 * 17 / 2];  // lower triangle of order <= 16
+  const int tid = threadIdx.x, nth = blockDim.x;
+  if (tid == 0) s_bad = 0;
+  if (tid < 16) {
+    const int t = tid;
+    for (int l = 0; l <= t; ++l) {
+      s_trow[t * (t + 1) / 2 + l] = (unsigned char)t;
+      s_tcol[t * (t + 1) / 2 + l] = (unsigned char)l;
     }
   }
+  for (size_t idx = tid; idx < (size_t)R * W2; idx += nth) {
+    const int r = (int)(idx / W2), k = (int)(idx - (size_t)r * W2), gi = q + C * r;
+    double2 v = make_double2(0.0, 0.0);
+    if (gi < n) v = k < n ? s[(size_t)gi * n + k] : make_double2(k - n == gi ? 1.0 : 0.0, 0.0);
+    rows[idx] = v;
+  }
+  // this CTA's row of the block starting at c: diagonal-block part and B part into every CTA
+  auto push_diag = [&](int c) {
+    const int gi = c + q;
+    if (gi >= n) return;
+    const int t = q, c1 = min(c + C, n);
+    const double2* row = rows + (size_t)(gi / C) * W2;
+    for (int u = tid; u < (t + 1 + c1) * C; u += nth) {
+      const int e = u / C, tgt = u - e * C;
+      if (e <= t) cl.map_shared_rank(dblk, tgt)[t * C + e] = row[c + e];
+      else cl.map_shared_rank(brow, tgt)[(size_t)t * n + (e - t - 1)] = row[n + e - t - 1];
+    }
+  };
+  cl.sync();  // every CTA of the cluster is running before shared memory is written remotely
+  __syncthreads();
+  push_diag(0);
+  cl.sync();
+  for (int c0 = 0; c0 < n; c0 += C) {
+    const int c1 = min(c0 + C, n), w = c1 - c0;
+    // ---- diagonal block: elimination of [D | I], redundantly in every CTA ----
+    for (int u = tid; u < w * w; u += nth) {
+      const int t = u / w, e = u - t * w;
+      dinv[t * C + e] = make_double2(t == e ? 1.0 : 0.0, 0.0);
+    }
+    if (tid == 0) {
+      double d = dblk[0].x;
+      if (!(d > 0.0) || !isfinite(d)) {
+        if (s_bad == 0) s_bad = c0 + 1;
+        d = 1.0;
+        dblk[0] = make_double2(1.0, 0.0);
+      }
+      s_rcp[0] = 1.0 / d;
+    }
+    __syncthreads();
+    // Step j updates rows t > j: t - j entries of the left block (columns j + 1 .. t) and j + 1 of the
+    // right (columns 0 .. j), t + 1 in all. The entries of all rows are packed densely onto consecutive
+    // threads (a warp's FP64 instruction costs the same with idle lanes): entry u of step j is entry
+    // v = u + (j + 1)(j + 2) / 2 of the row-major lower triangle, row s_trow[v], position s_tcol[v].
+    for (int j = 0; j + 1 < w; ++j) {
+      const int v0 = (j + 1) * (j + 2) / 2, nitem = w * (w + 1) / 2 - v0;
+      if (tid < nitem) {
+        const int v = tid + v0, t = s_trow[v], l = s_tcol[v];
+        const double2 a = dblk[t * C + j];
+        const double r = s_rcp[j];
+        const double2 m = make_double2(a.x * r, a.y * r);
+        if (l < t - j) {  // x -= m conj(y)
+          const int e = j + 1 + l;
+          const double2 y = dblk[e * C + j];
+          double2 x = dblk[t * C + e];
+          x.x = fma(-m.x, y.x, x.x);
+          x.x = fma(-m.y, y.y, x.x);
+          x.y = fma(-m.y, y.x, x.y);
+          x.y = fma(m.x, y.y, x.y);
+          dblk[t * C + e] = x;
+          if (e == t && t == j + 1) {  // the next pivot is final
+            double d = x.x;
+            if (!(d > 0.0) || !isfinite(d)) {
+              if (s_bad == 0) s_bad = c0 + t + 1;
+              d = 1.0;
+              dblk[t * C + t] = make_double2(1.0, 0.0);
+            }
+            s_rcp[t] = 1.0 / d;
+          }
+        } else {  // x -= m y
+          const int e = l - (t - j);
+          const double2 y = dinv[j * C + e];
+          double2 x = dinv[t * C + e];
+          x.x = fma(-m.x, y.x, x.x);
+          x.x = fma(m.y, y.y, x.x);
+          x.y = fma(-m.x, y.y, x.y);
+          x.y = fma(-m.y, y.x, x.y);
+          dinv[t * C + e] = x;
+        }
+      }
+      __syncthreads();
+    }
+    if (tid < w) s_isq[tid] = 1.0 / sqrt(dblk[tid * C + tid].x);
+    __syncthreads();
+    // ---- panel rows of this CTA below the block, and the finished row t = q of L^{-1} ----
+    const int rb = (c1 > q) ? (c1 - q + C - 1) / C : 0;  // first local row with g >= c1
+    const int nbelow = max(0, min(R, (n - q + C - 1) / C) - rb);
+    const int n3a = nbelow * w;
+    const int n3b = (q < w) ? c1 : 0;
+    for (int u = tid; u < n3a + n3b; u += nth) {
+      if (u < n3a) {  // s-major: the entries of a warp have inner sums of similar length
+        const int sidx = u / nbelow, r = rb + (u - sidx * nbelow), gi = q + C * r;
+        const double2* a = rows + (size_t)r * W2 + c0;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int t = 0; t <= sidx; ++t) acc = zfma_conj(acc, a[t], dinv[sidx * C + t]);
+        acc = cscale(acc, s_isq[sidx]);
+        for (int tgt = 0; tgt < C; ++tgt) cl.map_shared_rank(pan, tgt)[(size_t)sidx * n + gi] = acc;
+      } else {
+        const int k = u - n3a, t = q;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int e = 0; e <= t; ++e) acc = zfma(acc, dinv[t * C + e], brow[(size_t)e * n + k]);
+        acc = cscale(acc, s_isq[t]);
+        rows[(size_t)((c0 + t) / C) * W2 + n + k] = acc;  // final row c0 + t of L^{-1}
+        for (int tgt = 0; tgt < C; ++tgt) cl.map_shared_rank(linv, tgt)[(size_t)t * n + k] = acc;
+      }
+    }
+    cl.sync();
+    if (c1 >= n) break;
+    // ---- update of this CTA's rows below the block: k < c1 in the right half, c1 <= k <= g on the left ----
+    if (tid == 0) {
+      int o = 0;
+      for (int r = 0; r < nbelow; ++r) {
+        s_off[r] = o;
+        o += q + C * (rb + r) + 1;
+      }
+      s_off[nbelow] = o;
+    }
+    __syncthreads();
+    const int nitem = s_off[nbelow];
+    for (int u = tid; u < nitem; u += nth) {
+      int r = 0;
+      while (s_off[r + 1] <= u) ++r;
+      const int k = u - s_off[r], lr = rb + r, gi = q + C * lr;
+      double2* row = rows + (size_t)lr * W2;
+      double2 acc = make_double2(0.0, 0.0);
+      if (k < c1) {
+        for (int e = 0; e < w; ++e) acc = zfma(acc, pan[(size_t)e * n + gi], linv[(size_t)e * n + k]);
+        row[n + k] = csub(row[n + k], acc);
+      } else {
+        for (int e = 0; e < w; ++e) acc = zfma_conj(acc, pan[(size_t)e * n + gi], pan[(size_t)e * n + k]);
+        row[k] = csub(row[k], acc);
+      }
+    }
+    __syncthreads();
+    push_diag(c1);
+    cl.sync();
+  }
+  for (size_t idx = tid; idx < (size_t)R * n; idx += nth) {
+    const int r = (int)(idx / n), k = (int)(idx - (size_t)r * n), gi = q + C * r;
+    if (gi >= n) continue;
+    g[(size_t)gi * n + k] = k <= gi ? cconj(rows[(size_t)r * W2 + n + k]) : make_double2(0.0, 0.0);
+  }
+  if (q == 0 && tid == 0) *info = s_bad;
+  cl.sync();  // no CTA leaves while another may still write into its shared memory
+}
+
+static size_t chol_blocked_smem(int n, int C) {
+  const int R = (n + C - 1) / C;
+  return ((size_t)R * 2 * n + 3 * (size_t)C * n + 2 * (size_t)C * C) * sizeof(double2);
+}
+
+// Launch shape of the cluster Cholesky for order n: the blocked kernel where its shared memory fits,
+// else the column-by-column one; cluster size 16, else 8. kind 0: neither fits (cooperative fallback).
+static int chol_cluster_shape(Ctx* c, int n, Ctx::CholShape* out) {
+  int dev = 0;
+  PARO_CU(c, cudaGetDevice(&dev));
+  if (c->chol_shape.n == n && c->chol_shape.dev == dev) {
+    *out = c->chol_shape;
+    return PARO_OK;
+  }
+  const size_t cap = 220 * 1024;
+  PARO_CU(c, cudaFuncSetAttribute(k_chol_blocked, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  PARO_CU(c, cudaFuncSetAttribute(k_chol_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+  PARO_CU(c, cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  PARO_CU(c, cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  Ctx::CholShape sh;
+  sh.n = n;
+  sh.dev = dev;
+  for (int kind : {1, 2}) {
+    for (int C : {16, 8}) {
+      const int R = (n + C - 1) / C;
+      size_t sm;
+      int thr;
+      const void* kern;
+      if (kind == 1) {  // blocked: s_off holds R + 1 row offsets
+        sm = chol_blocked_smem(n, C);
+        thr = 512;
+        kern = (const void*)k_chol_blocked;
+        if (sm > cap || R > 62) continue;
+      } else {
+        sm = ((size_t)R * 2 * n + 4 * (size_t)n) * sizeof(double2);  // rows, two pivot buffers
+        thr = 32 * (R < 4 ? 4 : (R > 32 ? 32 : R));
+        kern = (const void*)k_chol_cluster;
+        if (sm > 200 * 1024) continue;
+      }
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = C;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(C);
+      cfg.blockDim = dim3(thr);
+      cfg.dynamicSmemBytes = sm;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      if (nclusters >= 1) {
+        sh.kind = kind;
+        sh.cls = C;
+        sh.thr = thr;
+        sh.smem = sm;
+        c->chol_shape = *out = sh;
+        return PARO_OK;
+      }
+    }
+  }
+  c->chol_shape = *out = sh;
   return PARO_OK;
 }
 
 int chol_inv(Ctx* c, int n, const double2* s, double2* g) {
   {
-    int cls = 0, thr = 0, st;
-    size_t sm = 0;
-    if ((st = chol_cluster_shape(c, n, &cls, &thr, &sm))) return st;
-    if (cls > 0) {
+    Ctx::CholShape sh;
+    int st;
+    if ((st = chol_cluster_shape(c, n, &sh))) return st;
+    if (sh.kind > 0) {
       int* flags = static_cast<int*>(ws_get(c, "chol_flags", 8 * sizeof(int)));
       if (!flags) return PARO_ERR_CUDA;
       cudaLaunchConfig_t cfg = {};
       cudaLaunchAttribute at[1];
       at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = cls;
+      at[0].val.clusterDim.x = sh.cls;
       at[0].val.clusterDim.y = 1;
       at[0].val.clusterDim.z = 1;
-      cfg.gridDim = dim3(cls);
-      cfg.blockDim = dim3(thr);
-      cfg.dynamicSmemBytes = sm;
+      cfg.gridDim = dim3(sh.cls);
+      cfg.blockDim = dim3(sh.thr);
+      cfg.dynamicSmemBytes = sh.smem;
       cfg.stream = c->stream;
       cfg.attrs = at;
       cfg.numAttrs = 1;
       cudaEvent_t ev = prof_begin(c);
-      PARO_CU(c, cudaLaunchKernelEx(&cfg, k_chol_cluster, n, s, g, flags));
+      if (sh.kind == 1) PARO_CU(c, cudaLaunchKernelEx(&cfg, k_chol_blocked, n, s, g, flags));
+      else PARO_CU(c, cudaLaunchKernelEx(&cfg, k_chol_cluster, n, s, g, flags));
       ++c->launches;
       prof_end(c, "k_chol_cluster", ev);
       int h = 0;
@@ -849,11 +1090,11 @@ template int gemm_cn<double, double, double>(Ctx*, int, int, int, const double2*
 template int gemm_cn<float, float, float>(Ctx*, int, int, int, const float2*, int, const float2*, int, double2*, int,
                                           bool, bool);
 template int gemm_wx<double, double>(Ctx*, int, int, int, const double2*, int, bool, const double*, const double2*,
-                                     int, double2*, int, double, float2*);
+                                     int, double2*, int, double, float2*, bool);
 template int gemm_wx<float, float>(Ctx*, int, int, int, const double2*, int, bool, const double*, const float2*, int,
-                                   float2*, int, double, float2*);
+                                   float2*, int, double, float2*, bool);
 template int gemm_wx<float, double>(Ctx*, int, int, int, const double2*, int, bool, const double*, const float2*,
-                                    int, double2*, int, double, float2*);
+                                    int, double2*, int, double, float2*, bool);
 template int band_norms<double>(Ctx*, int, int, const double2*, int, double*);
 template int band_norms<float>(Ctx*, int, int, const float2*, int, double*);
 template int convert<double, float>(Ctx*, size_t, const double2*, float2*);

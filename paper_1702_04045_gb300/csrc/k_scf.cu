@@ -40,13 +40,13 @@ int build_twiddles(Ctx* c) {
 // ------------------------------------------------------------------------------------------------
 static const int kLB = 16;  // lines per CTA
 
-template <bool INV>
-__global__ void __launch_bounds__(256) k_fft_z(double2* __restrict__ data, int nlines, FftPlan p,
-                                               const double2* __restrict__ twg) {
+template <typename T, bool INV>
+__global__ void __launch_bounds__(256) k_fft_z(cplx<T>* __restrict__ data, int nlines, FftPlan p,
+                                               const cplx<T>* __restrict__ twg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = p.n, ls = n + 1;
-  double2* tw = reinterpret_cast<double2*>(smem_raw);
-  double2* lines = tw + n;
+  cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* lines = tw + n;
   const int l0 = blockIdx.x * kLB, nl = min(kLB, nlines - l0);
   for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
   for (int i = threadIdx.x; i < nl * n; i += blockDim.x) {
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(256) k_fft_z(double2* __restrict__ data, int n
     lines[l * ls + j] = data[(size_t)(l0 + l) * n + j];
   }
   __syncthreads();
-  fft_lines<double, INV, false>(lines, p, nl, 1, LinesDirect{ls}, tw);
+  fft_lines<T, INV, false>(lines, p, nl, 1, LinesDirect{ls}, tw);
   for (int i = threadIdx.x; i < nl * n; i += blockDim.x) {
     const int l = i / n, j = i - l * n;
     data[(size_t)(l0 + l) * n + j] = lines[l * ls + j];
@@ -62,13 +62,13 @@ __global__ void __launch_bounds__(256) k_fft_z(double2* __restrict__ data, int n
 }
 
 // lines along an axis of element stride es; a CTA takes 16 consecutive z positions of one outer index
-template <bool INV>
-__global__ void __launch_bounds__(256) k_fft_strided(double2* __restrict__ data, FftPlan p, int es, int os,
-                                                     int ninner, const double2* __restrict__ twg) {
+template <typename T, bool INV>
+__global__ void __launch_bounds__(256) k_fft_strided(cplx<T>* __restrict__ data, FftPlan p, int es, int os,
+                                                     int ninner, const cplx<T>* __restrict__ twg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = p.n, ls = n + 1;
-  double2* tw = reinterpret_cast<double2*>(smem_raw);
-  double2* lines = tw + n;
+  cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* lines = tw + n;
   const int z0 = blockIdx.x * kLB, nz = min(kLB, ninner - z0);
   const size_t base = (size_t)blockIdx.y * os + z0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
@@ -77,38 +77,42 @@ __global__ void __launch_bounds__(256) k_fft_strided(double2* __restrict__ data,
     lines[l * ls + j] = data[base + (size_t)j * es + l];
   }
   __syncthreads();
-  fft_lines<double, INV, false>(lines, p, nz, 1, LinesDirect{ls}, tw);
+  fft_lines<T, INV, false>(lines, p, nz, 1, LinesDirect{ls}, tw);
   for (int i = threadIdx.x; i < nz * n; i += blockDim.x) {
     const int l = i % nz, j = i / nz;
     data[base + (size_t)j * es + l] = lines[l * ls + j];
   }
 }
 
-int fft3d(Ctx* c, double2* data, bool inverse) {
+template <typename T, bool INV>
+static int fft3d_dir(Ctx* c, cplx<T>* data) {
   const int N1 = c->N[0], N2 = c->N[1], N3 = c->N[2];
-  const size_t smz = (size_t)(N3 + kLB * (N3 + 1)) * sizeof(double2);
-  const size_t smy = (size_t)(N2 + kLB * (N2 + 1)) * sizeof(double2);
-  const size_t smx = (size_t)(N1 + kLB * (N1 + 1)) * sizeof(double2);
-  if (inverse) {
-    PARO_CU(c, cudaFuncSetAttribute(k_fft_z<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-    PARO_CU(c, cudaFuncSetAttribute(k_fft_strided<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-    k_fft_z<true><<<(N1 * N2 + kLB - 1) / kLB, 256, smz, c->stream>>>(data, N1 * N2, c->plan[2], c->d_tw64[2]);
-    k_fft_strided<true><<<dim3((N3 + kLB - 1) / kLB, N1), 256, smy, c->stream>>>(data, c->plan[1], N3, N2 * N3, N3,
-                                                                               c->d_tw64[1]);
-    k_fft_strided<true><<<dim3((N3 + kLB - 1) / kLB, N2), 256, smx, c->stream>>>(data, c->plan[0], N2 * N3, N3, N3,
-                                                                               c->d_tw64[0]);
-  } else {
-    PARO_CU(c, cudaFuncSetAttribute(k_fft_z<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-    PARO_CU(c, cudaFuncSetAttribute(k_fft_strided<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-    k_fft_z<false><<<(N1 * N2 + kLB - 1) / kLB, 256, smz, c->stream>>>(data, N1 * N2, c->plan[2], c->d_tw64[2]);
-    k_fft_strided<false><<<dim3((N3 + kLB - 1) / kLB, N1), 256, smy, c->stream>>>(data, c->plan[1], N3, N2 * N3, N3,
-                                                                                c->d_tw64[1]);
-    k_fft_strided<false><<<dim3((N3 + kLB - 1) / kLB, N2), 256, smx, c->stream>>>(data, c->plan[0], N2 * N3, N3, N3,
-                                                                                c->d_tw64[0]);
-  }
+  const size_t eb = sizeof(cplx<T>);
+  const size_t smz = (size_t)(N3 + kLB * (N3 + 1)) * eb;
+  const size_t smy = (size_t)(N2 + kLB * (N2 + 1)) * eb;
+  const size_t smx = (size_t)(N1 + kLB * (N1 + 1)) * eb;
+  const cplx<T>* const* tw;
+  if constexpr (sizeof(T) == 8) tw = c->d_tw64;
+  else tw = c->d_tw32;
+  PARO_CU(c, cudaFuncSetAttribute(k_fft_z<T, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+  PARO_CU(c, cudaFuncSetAttribute(k_fft_strided<T, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+  cudaEvent_t ev = prof_begin(c);
+  k_fft_z<T, INV><<<(N1 * N2 + kLB - 1) / kLB, 256, smz, c->stream>>>(data, N1 * N2, c->plan[2], tw[2]);
+  k_fft_strided<T, INV><<<dim3((N3 + kLB - 1) / kLB, N1), 256, smy, c->stream>>>(data, c->plan[1], N3, N2 * N3, N3,
+                                                                               tw[1]);
+  k_fft_strided<T, INV><<<dim3((N3 + kLB - 1) / kLB, N2), 256, smx, c->stream>>>(data, c->plan[0], N2 * N3, N3, N3,
+                                                                               tw[0]);
   PARO_LAUNCH(c, "fft3d");
+  prof_end(c, sizeof(T) == 8 ? "fft3d<f64>" : "fft3d<f32>", ev);
   return PARO_OK;
 }
+
+template <typename T>
+int fft3d(Ctx* c, cplx<T>* data, bool inverse) {
+  return inverse ? fft3d_dir<T, true>(c, data) : fft3d_dir<T, false>(c, data);
+}
+template int fft3d<double>(Ctx*, double2*, bool);
+template int fft3d<float>(Ctx*, float2*, bool);
 
 // ------------------------------------------------------------------------------------------------
 // structure-factor phase tables: ph[a][I][j] = exp(-i 2 pi n f_{I,a}), n = signed grid index j
@@ -201,7 +205,7 @@ int build_vloc(Ctx* c) {
   k_vloc_g<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->N[0], c->N[1], c->N[2], B, 4.0 * c->ecut, c->Z, c->rc,
                                                           c->A, c->a, c->omega, c->nat, ph, vg);
   PARO_LAUNCH(c, "k_vloc_g");
-  int st = fft3d(c, vg, true);
+  int st = fft3d<double>(c, vg, true);
   if (st) return st;
   if (!c->d_vloc) PARO_CU(c, cudaMalloc(&c->d_vloc, (size_t)c->ngrid * sizeof(double)));
   k_real_part<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, vg, c->d_vloc);
@@ -279,7 +283,7 @@ int vloc_position_grad(Ctx* c, const double* gv, double* gpos) {
   if (!ph || !g || !part) return PARO_ERR_CUDA;
   k_to_complex<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, gv, g);
   PARO_LAUNCH(c, "k_to_complex");
-  int st = fft3d(c, g, false);
+  int st = fft3d<double>(c, g, false);
   if (st) return st;
   Mat3 B;
   for (int i = 0; i < 9; ++i) B.m[i] = c->bmat[i];
@@ -543,35 +547,79 @@ static int sum_parts(Ctx* c, const double* part, int n, double* out) {
   return PARO_OK;
 }
 
+static const double* inv_g2_table(Ctx* c);
+
 // Partial sums of E_H of rho (hartree_blocks(c) doubles in part; E_H = 2 pi Omega times their sum) and,
 // when potential, V_H(r) in z (real parts). Launches only: the energy alone needs only the forward FFT
 // and no host synchronisation until the caller reads the partials.
 static int hartree_blocks(const Ctx* c) { return (c->ngrid + 255) / 256; }
 static int hartree_g(Ctx* c, const double* rho_dev, double2* z, double* part, bool potential) {
-  Mat3 B;
-  for (int i = 0; i < 9; ++i) B.m[i] = c->bmat[i];
   const int nblk = hartree_blocks(c);
   k_to_complex<<<nblk, 256, 0, c->stream>>>(c->ngrid, rho_dev, z);
   PARO_LAUNCH(c, "k_to_complex");
-  int st = fft3d(c, z, false);
+  int st = fft3d<double>(c, z, false);
   if (st) return st;
-  double* ig2 = static_cast<double*>(ws_get(c, "inv_g2", (size_t)c->ngrid * sizeof(double)));
-  if (!ig2) return PARO_ERR_CUDA;
-  if (!c->have_inv_g2) {  // the cell and grid are fixed for the context's life
-    k_inv_g2<<<nblk, 256, 0, c->stream>>>(c->N[0], c->N[1], c->N[2], B, ig2);
-    PARO_LAUNCH(c, "k_inv_g2");
-    c->have_inv_g2 = true;
-  }
+  const double* ig2 = inv_g2_table(c);
+  if (!ig2) return fail(c, PARO_ERR_CUDA, "hartree: 1/|G|^2 table");
   k_hartree_tab<<<nblk, 256, 0, c->stream>>>(c->ngrid, ig2, z, part);
   PARO_LAUNCH(c, "k_hartree_tab");
-  if (potential && (st = fft3d(c, z, true))) return st;
+  if (potential && (st = fft3d<double>(c, z, true))) return st;
   return PARO_OK;
 }
 static double hartree_energy(const Ctx* c, double part_sum) { return 0.5 * c->omega * 4.0 * kPi * part_sum; }
 
+// V_H(r) for the mixed path: the density's FFT, 4 pi / |G|^2 and the inverse FFT in FP32 (the potential
+// enters H psi as FP32 planes); no energy.
+__global__ void k_to_complex32(int n, const double* __restrict__ r, float2* __restrict__ z) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[i] = make_float2((float)r[i], 0.f);
+}
+__global__ void k_hartree_pot32(int ng, const double* __restrict__ ig2, float2* __restrict__ z) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ng) z[i] = cscale(z[i], (float)(4.0 * kPi * ig2[i] / ng));
+}
+__global__ void k_veff_combine32(int n, const double* __restrict__ vloc, const float2* __restrict__ vh,
+                                 const double* __restrict__ rho, double* __restrict__ veff) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float e, v;
+  lda_pz<float>((float)rho[i], &e, &v);
+  veff[i] = vloc[i] + (double)(vh[i].x + v);
+}
+
+static const double* inv_g2_table(Ctx* c) {
+  double* ig2 = static_cast<double*>(ws_get(c, "inv_g2", (size_t)c->ngrid * sizeof(double)));
+  if (!ig2) return nullptr;
+  if (!c->have_inv_g2) {  // the cell and grid are fixed for the context's life
+    Mat3 B;
+    for (int i = 0; i < 9; ++i) B.m[i] = c->bmat[i];
+    k_inv_g2<<<hartree_blocks(c), 256, 0, c->stream>>>(c->N[0], c->N[1], c->N[2], B, ig2);
+    if (cudaGetLastError() != cudaSuccess) return nullptr;
+    c->have_inv_g2 = true;
+  }
+  return ig2;
+}
+
 int veff_from_density(Ctx* c, const double* rho_dev, double* eh_out, double* exc_out) {
   (void)exc_out;
   if (!c->have_pp) return fail(c, PARO_ERR_STATE, "no local pseudopotential set");
+  if (c->prec == PARO_MIXED && !eh_out) {
+    float2* z = static_cast<float2*>(ws_get(c, "grid_c0_32", (size_t)c->ngrid * sizeof(float2)));
+    double* v = static_cast<double*>(ws_get(c, "grid_r0", (size_t)c->ngrid * sizeof(double)));
+    const double* ig2 = inv_g2_table(c);
+    if (!z || !v || !ig2) return fail(c, PARO_ERR_CUDA, "veff_from_density: workspace");
+    const int nblk = hartree_blocks(c);
+    k_to_complex32<<<nblk, 256, 0, c->stream>>>(c->ngrid, rho_dev, z);
+    PARO_LAUNCH(c, "k_to_complex32");
+    int st = fft3d<float>(c, z, false);
+    if (st) return st;
+    k_hartree_pot32<<<nblk, 256, 0, c->stream>>>(c->ngrid, ig2, z);
+    PARO_LAUNCH(c, "k_hartree_pot32");
+    if ((st = fft3d<float>(c, z, true))) return st;
+    k_veff_combine32<<<nblk, 256, 0, c->stream>>>(c->ngrid, c->d_vloc, z, rho_dev, v);
+    PARO_LAUNCH(c, "k_veff_combine32");
+    return set_veff_device(c, v);
+  }
   double2* z = static_cast<double2*>(ws_get(c, "grid_c0", (size_t)c->ngrid * sizeof(double2)));
   double* v = static_cast<double*>(ws_get(c, "grid_r0", (size_t)c->ngrid * sizeof(double)));
   if (!z || !v) return PARO_ERR_CUDA;

@@ -101,6 +101,7 @@ struct Ctx {
     cudaEvent_t a, b;
   };
   std::vector<ProfEv> prof_ev;
+  std::vector<cudaEvent_t> prof_pool;  // timing events kept for reuse between recorded ranges
   const char* prof_tag = nullptr;  // phase prefix of recorded names ("pcg", "rr", ...)
   // workspaces by name
   std::map<std::string, std::pair<void*, size_t>> ws;
@@ -108,6 +109,10 @@ struct Ctx {
   // FP32 products may run on the tensor cores (3xTF32): inside the inexact inner solves and the adjoint,
   // not in the Rayleigh-Ritz step, the rotations or the energy, which fix the self-consistent result
   bool tc_scope = false;
+  struct CholShape {  // launch shape of the cluster Cholesky for order n on device dev
+    int n = -1, dev = -1, kind = 0, cls = 0, thr = 0;
+    size_t smem = 0;
+  } chol_shape;
   bool have_inv_g2 = false;  // the 1/|G|^2 table of the Hartree solve is in the "inv_g2" workspace
 };
 
@@ -168,10 +173,11 @@ int gemm_cn(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, const cplx<
 // Y[m][n] = beta Y[m][n] + sum_k s_k W(k, m) X[k][n]; W: complex double, element (k, m) at W[k*ldw + m]
 // (or at W[m*ldw + k] when wt); s: device double[K] or nullptr (1); X: K x N (ldx) of TX;
 // Y: M x N (ldy) of TY; accumulation in TY. wf: device scratch of M K float2 for the FP32 form's converted
-// W (nullptr: a workspace of the context, allocated on first use).
+// W (nullptr: a workspace of the context, allocated on first use). lower: W(k, m) = 0 for k > m (a
+// triangular factor), which lets the FP32 form skip the zero products.
 template <typename TX, typename TY>
 int gemm_wx(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, const double* s, const cplx<TX>* X,
-            int ldx, cplx<TY>* Y, int ldy, double beta, float2* wf = nullptr);
+            int ldx, cplx<TY>* Y, int ldy, double beta, float2* wf = nullptr, bool lower = false);
 // gemm_cn with the K-slice partials in caller memory (part_elems complex doubles); allocates nothing.
 template <typename TA, typename TB, typename ACC>
 int gemm_cn_scratch(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb,
@@ -218,7 +224,8 @@ template <typename T>
 int density(Ctx* c, const cplx<T>* const* psis, double* rho_dev);  // from given orbitals (occupied)
 int energy_terms(Ctx* c, const double* rho_dev, double terms[7]);
 int pulay_mix(Ctx* c, const double* rho_out, int depth, double beta);
-int fft3d(Ctx* c, double2* data, bool inverse);  // in place, unnormalised, C order grid
+template <typename T>
+int fft3d(Ctx* c, cplx<T>* data, bool inverse);  // in place, unnormalised, C order grid
 double ewald(const Ctx* c);
 
 int build_twiddles(Ctx* c);

@@ -26,7 +26,7 @@ ENERGY_TERMS = ("kinetic", "nonlocal", "local", "hartree", "xc", "ewald", "total
 EXPORTS = (
     "paro_create", "paro_set_local_pp", "paro_set_kb", "paro_set_positions", "paro_set_veff", "paro_get_veff",
     "paro_get_vloc", "paro_set_density", "paro_grid", "paro_npw", "paro_miller", "paro_sigma", "paro_apply_h",
-    "paro_apply_h_noalloc", "paro_apply_h_adjoint", "paro_solve_source", "paro_batch_create", "paro_batch_apply_h",
+    "paro_apply_h_noalloc", "paro_apply_h_adjoint", "paro_orthonormalize", "paro_solve_source", "paro_batch_create", "paro_batch_apply_h",
     "paro_batch_step", "paro_batch_info", "paro_batch_destroy",
     "paro_set_orbitals", "paro_get_orbitals", "paro_get_eigenvalues", "paro_get_residuals", "paro_step",
     "paro_eigh", "paro_density", "paro_energy", "paro_scf_step", "paro_scf", "paro_set_state", "paro_profile",
@@ -67,6 +67,7 @@ _SIGS = {
     "paro_apply_h_adjoint": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp,
                                             _vp]),
     "paro_set_positions": (ctypes.c_int, [_vp, _c_dbl_p]),
+    "paro_orthonormalize": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "paro_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int]),
     "paro_batch_apply_h": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "paro_batch_step": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, _c_dbl_p]),
@@ -274,6 +275,18 @@ class Context:
         v = np.empty(self.grid, dtype=np.float64)
         self._check(self.lib.paro_get_vloc(self.h, _dptr(v)))
         return v
+
+    def orthonormalize(self, x, ik=0, out=None):
+        """Rows x -> orthonormal rows spanning the same nested subspaces (Cholesky of the Gram matrix);
+        out may be x itself (in place)."""
+        torch = self.torch
+        dt = PARO_C64 if x.dtype == torch.complex128 else PARO_C32
+        x = x.contiguous()
+        if out is None:
+            out = torch.empty_like(x)
+        self._check(self.lib.paro_orthonormalize(self.h, ik, x.shape[0], dt, _vp(x.data_ptr()),
+                                                 _vp(out.data_ptr())))
+        return out
 
     def solve_source(self, eps, psi, rel_tol, max_it, ik=0):
         torch = self.torch

@@ -182,6 +182,32 @@ def test_eigh_matches_lapack(n, precision):
     assert np.abs(a @ v - v * w).max() < 1e-11 * scale * max(1, n / 20)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("n", [1, 5, 12, 16, 17, 33, 144, 150, 176, 200, 288])
+def test_orthonormalize_matches_oracle(n, precision):
+    # n <= 176: blocked Cholesky on one 16-CTA cluster (ragged last block unless n % 16 == 0);
+    # 200 and 288: the column-by-column cluster kernel
+    ctx, _, _ = _small(precision=precision)
+    npw = ctx.npw()
+    assert npw > 288
+    rng = np.random.default_rng(1000 + n)
+    x = rng.standard_normal((n, npw)) + 1j * rng.standard_normal((n, npw))
+    x[1::3] += 0.5 * x[0::3][: x[1::3].shape[0]]  # correlated rows: a Gram matrix far from diagonal
+    if precision == "fp64":
+        xt = torch.from_numpy(x).cuda()
+        tol, tol_o = 1e-11, 1e-12
+    else:
+        xt = torch.from_numpy(x.astype(np.complex64)).cuda()
+        x = xt.cpu().numpy().astype(np.complex128)
+        tol, tol_o = 2e-5, 2e-5
+    y = ctx.orthonormalize(xt).cpu().numpy().astype(np.complex128)
+    ref = opar.cholesky_orthonormalize(x)
+    assert _rel(y, ref) < tol * max(1, n / 20)
+    assert np.abs(np.conj(y) @ y.T - np.eye(n)).max() < tol_o * max(1, n / 20)
+    ctx.orthonormalize(xt, out=xt)  # in place
+    assert _rel(xt.cpu().numpy().astype(np.complex128), ref) < tol * max(1, n / 20)
+
+
 def test_initial_ritz_pairs_match_oracle():
     ctx, prob, _ = _small()
     c0 = inputs.start_vectors(12, prob.basis.npw, 8)
