@@ -260,8 +260,10 @@ static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal, cplx<T>
   if (!f64) {
     if ((st = convert<float, double>(c, (size_t)nb * npw, b.d_psi32, b.d_psi))) return st;
     if ((st = convert<float, double>(c, (size_t)nb * npw, b.d_hpsi32, b.d_hpsi))) return st;
+    if ((st = residual_norms32(c, nb, npw, b.d_psi32, b.d_hpsi32, w, res))) return st;
+  } else if ((st = residual_norms(c, nb, npw, b.d_psi, b.d_hpsi, w, res))) {
+    return st;
   }
-  if ((st = residual_norms(c, nb, npw, b.d_psi, b.d_hpsi, w, res))) return st;
   b.eps.resize(nb);
   b.res.resize(nb);
   PARO_CU(c, cudaMemcpyAsync(b.eps.data(), w, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -292,6 +294,8 @@ static int source_rhs(Ctx* c, int ik, bool alg2, cplx<T>* rhs) {
   std::vector<double> hf(nb);
   for (int i = 0; i < nb; ++i) hf[i] = alg2 ? b.eps[i] : b.eps[i] - c->sigma_k[ik];
   PARO_CU(c, cudaMemcpyAsync(f, hf.data(), nb * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (sizeof(T) == 4 && !alg2 && b.d_psi32)  // (eps - sigma) psi straight from the FP32 orbitals
+    return scale_rows<float>(c, nb, npw, b.d_psi32, f, reinterpret_cast<float2*>(rhs));
   int st = scale_rows<double>(c, nb, npw, b.d_psi, f, tmp);
   if (st) return st;
   if (alg2) {
@@ -698,7 +702,7 @@ void paro_destroy(paro_ctx* ctx) {
   }
   void* ps[] = {c->d_tw64[0], c->d_tw64[1], c->d_tw64[2], c->d_tw32[0], c->d_tw32[1], c->d_tw32[2],
                 c->d_vloc, c->d_dvec, c->d_dvec32, c->d_veff, c->d_vplane, c->d_vplane32,
-                c->d_rho_in, c->d_pulay_rho, c->d_pulay_res, c->d_tc_err};
+                c->d_rho_in, c->d_pulay_rho, c->d_pulay_res, c->d_pulay_gram, c->d_tc_err};
   for (void* p : ps)
     if (p) cudaFree(p);
   for (auto& kv : c->ws) cudaFree(kv.second.first);

@@ -361,8 +361,13 @@ __global__ void __launch_bounds__(256) k_plane_density_reg(const cplx<T>* __rest
     }
     __syncthreads();
   }
-  double* out = part + ((size_t)grp_b * N3 + z) * N1 * N2;
-  for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) out[i] = (double)acc[i] * wfac;
+  if constexpr (sizeof(TACC) == 4) {  // FP32 sums stored as they are (half the traffic); the caller scales
+    float* out = reinterpret_cast<float*>(part) + ((size_t)grp_b * N3 + z) * N1 * N2;
+    for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) out[i] = acc[i];
+  } else {
+    double* out = part + ((size_t)grp_b * N3 + z) * N1 * N2;
+    for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) out[i] = (double)acc[i] * wfac;
+  }
 }
 
 template <typename T, int N, typename TACC>
@@ -396,8 +401,9 @@ static int density_planes_reg_n(Ctx* c, const Basis& B, const cplx<T>* S, int nb
 
 template <typename T>
 int density_planes_reg(Ctx* c, int ik, const cplx<T>* S, int nbands, int ngrp, int gsize, double wfac, double* part,
-                       bool* used) {
+                       bool* used, bool* f32part) {
   *used = false;
+  *f32part = sizeof(T) == 4;  // FP32 orbitals: unscaled FP32 partial planes (density_planes_reg_n)
   const int n = c->N[0];
   if (c->N[1] != n || c->N[2] != n) return PARO_OK;
   const size_t acc_bytes = (sizeof(T) == 4 && gsize <= 8) ? sizeof(float) : sizeof(double);

@@ -1061,6 +1061,45 @@ __global__ void k_resid(int npw, const double2* __restrict__ psi, const double2*
   if (threadIdx.x == 0) out[b] = sqrt(acc);
 }
 
+// FP32 rows (mixed path): the row's chunk blockIdx.y of || h - eps p ||^2 with FP32 terms in an FP32
+// two-sum pair; part[b * gridDim.y + chunk]. k_resid_final sums a band's chunks in order.
+__global__ void __launch_bounds__(256) k_resid32(int npw, const float2* __restrict__ psi,
+                                                 const float2* __restrict__ hpsi, const double* __restrict__ eps,
+                                                 double* __restrict__ part) {
+  __shared__ double red[32];
+  const int b = blockIdx.x, len = (npw + gridDim.y - 1) / gridDim.y;
+  const int g0 = blockIdx.y * len, g1 = min(npw, g0 + len);
+  const float e = (float)eps[b];
+  float hi = 0.f, lo = 0.f;
+  for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+    const float2 p = psi[(size_t)b * npw + g], h = hpsi[(size_t)b * npw + g];
+    const float re = fmaf(-e, p.x, h.x), im = fmaf(-e, p.y, h.y);
+    two_sum_acc(hi, lo, fmaf(re, re, im * im));
+  }
+  const double acc = block_sum((double)hi + (double)lo, red);
+  if (threadIdx.x == 0) part[(size_t)b * gridDim.y + blockIdx.y] = acc;
+}
+
+__global__ void k_resid_final(int nb, int nch, const double* __restrict__ part, double* __restrict__ out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  double s = 0.0;
+  for (int ch = 0; ch < nch; ++ch) s += part[(size_t)b * nch + ch];
+  out[b] = sqrt(s);
+}
+
+int residual_norms32(Ctx* c, int nb, int npw, const float2* psi, const float2* hpsi, const double* eps_dev,
+                     double* out_dev) {
+  constexpr int kCh = 4;
+  double* part = static_cast<double*>(ws_get(c, "resid_part", (size_t)nb * kCh * sizeof(double)));
+  if (!part) return PARO_ERR_CUDA;
+  k_resid32<<<dim3(nb, kCh), 256, 0, c->stream>>>(npw, psi, hpsi, eps_dev, part);
+  PARO_LAUNCH(c, "k_resid32");
+  k_resid_final<<<(nb + 127) / 128, 128, 0, c->stream>>>(nb, kCh, part, out_dev);
+  PARO_LAUNCH(c, "k_resid_final");
+  return PARO_OK;
+}
+
 int residual_norms(Ctx* c, int nb, int npw, const double2* psi, const double2* hpsi, const double* eps_dev,
                    double* out_dev) {
   k_resid<<<nb, 256, 0, c->stream>>>(npw, psi, hpsi, eps_dev, out_dev, c->prec == PARO_MIXED ? 1 : 0);

@@ -693,6 +693,19 @@ __global__ void k_density_reduce(int N1, int N2, int N3, int ngrp, const double*
   rho[idx] = accumulate ? rho[idx] + s : s;
 }
 
+// the same for unscaled FP32 partial planes: rho (+)= wfac sum_g part_g, summed in FP64
+__global__ void k_density_reduce32(int N1, int N2, int N3, int ngrp, const float* __restrict__ part, double wfac,
+                                   double* __restrict__ rho, int accumulate) {
+  const int pl = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pl >= N1 * N2 * N3) return;
+  const int y = pl % N2, x = (pl / N2) % N1, z = pl / (N1 * N2);
+  const size_t idx = ((size_t)x * N2 + y) * N3 + z;
+  double s = 0.0;
+  for (int g = 0; g < ngrp; ++g) s += (double)part[(size_t)g * N1 * N2 * N3 + pl];
+  s *= wfac;
+  rho[idx] = accumulate ? rho[idx] + s : s;
+}
+
 template <typename T> static const cplx<T>* twid(const Ctx* c, int ax);
 template <> const double2* twid<double>(const Ctx* c, int ax) { return c->d_tw64[ax]; }
 template <> const float2* twid<float>(const Ctx* c, int ax) { return c->d_tw32[ax]; }
@@ -715,8 +728,8 @@ int density_bands(Ctx* c, int ik, int nbands, const cplx<T>* psi, double wfac, d
   int st = sticks_inverse<T>(c, ik, nbands, psi, S);
   if (st) return st;
   cudaEvent_t ev = prof_begin(c);
-  bool used = false;
-  if ((st = density_planes_reg<T>(c, ik, S, nbands, ngrp, gsize, wfac, part, &used))) return st;
+  bool used = false, f32part = false;
+  if ((st = density_planes_reg<T>(c, ik, S, nbands, ngrp, gsize, wfac, part, &used, &f32part))) return st;
   if (!used) {
     if (smem > 227 * 1024) return fail(c, PARO_ERR_ARG, "density: plane too large for shared memory");
     PARO_CU(c, cudaFuncSetAttribute(k_plane_density<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
@@ -726,7 +739,12 @@ int density_bands(Ctx* c, int ik, int nbands, const cplx<T>* psi, double wfac, d
     PARO_LAUNCH(c, "k_plane_density");
   }
   prof_end(c, sizeof(T) == 8 ? "k_plane_density<f64>" : "k_plane_density<f32>", ev);
-  k_density_reduce<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(N1, N2, N3, ngrp, part, rho_dev, accumulate);
+  if (used && f32part)
+    k_density_reduce32<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(N1, N2, N3, ngrp,
+                                                                      reinterpret_cast<const float*>(part), wfac,
+                                                                      rho_dev, accumulate);
+  else
+    k_density_reduce<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(N1, N2, N3, ngrp, part, rho_dev, accumulate);
   PARO_LAUNCH(c, "k_density_reduce");
   return PARO_OK;
 }
@@ -751,26 +769,28 @@ template int density<float>(Ctx*, const float2* const*, double*);
 // ------------------------------------------------------------------------------------------------
 // per block partial sums of w_b * sum_g kin_g |c_bg|^2 over blocks (band, chunk)
 // FP32 orbitals (mixed precision): FP32 terms summed in an FP32 two-sum pair, no FP64 per coefficient
+// (grid: band x chunk of the row; part[b * gridDim.y + chunk])
 template <typename T>
 __global__ void k_kinetic(int npw, const cplx<T>* __restrict__ psi, const T* __restrict__ kin, double* part) {
   __shared__ double red[32];
-  const int b = blockIdx.x;
+  const int b = blockIdx.x, len = (npw + gridDim.y - 1) / gridDim.y;
+  const int g0 = blockIdx.y * len, g1 = min(npw, g0 + len);
   double s = 0.0;
   if (sizeof(T) == 4) {
     float hi = 0.f, lo = 0.f;
-    for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+    for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
       const cplx<T> v = psi[(size_t)b * npw + g];
       two_sum_acc(hi, lo, (float)(kin[g] * (v.x * v.x + v.y * v.y)));
     }
     s = (double)hi + (double)lo;
   } else {
-    for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+    for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
       const cplx<T> v = psi[(size_t)b * npw + g];
       s += (double)kin[g] * ((double)v.x * v.x + (double)v.y * v.y);
     }
   }
   s = block_sum(s, red);
-  if (threadIdx.x == 0) part[b] = s;
+  if (threadIdx.x == 0) part[(size_t)b * gridDim.y + blockIdx.y] = s;
 }
 
 // sum_p D_p |P[p][b]|^2 per band b
@@ -808,20 +828,22 @@ __global__ void k_grid_energies(int n, const double* __restrict__ vloc, const do
 int energy_terms(Ctx* c, const double* rho_dev, double terms[7]) {
   for (int i = 0; i < 7; ++i) terms[i] = 0.0;
   // every partial sum lands in one buffer, read back with a single synchronisation:
-  // [kinetic: nk x nocc][nonlocal: nk x nocc][V_loc rho, rho eps_xc: 2 x 304][Hartree blocks]
-  const int nblk = 304, nh = hartree_blocks(c), nkb = c->nk * c->nocc;
-  const size_t ntot = (size_t)2 * nkb + 2 * nblk + nh;
+  // [kinetic: nk x nocc x kKch][nonlocal: nk x nocc][V_loc rho, rho eps_xc: 2 x 304][Hartree blocks]
+  constexpr int kKch = 4;  // chunks of each row for the kinetic sums (enough CTAs to fill the GPU)
+  const int nblk = 304, nh = hartree_blocks(c), nkb = c->nk * c->nocc, nkk = nkb * kKch;
+  const size_t ntot = (size_t)nkk + nkb + 2 * nblk + nh;
   double* part = static_cast<double*>(ws_get(c, "energy_part", ntot * sizeof(double)));
   double2* z = static_cast<double2*>(ws_get(c, "grid_c0", (size_t)c->ngrid * sizeof(double2)));
   if (!part || !z) return PARO_ERR_CUDA;
-  double *pk = part, *pn = part + nkb, *pg = part + 2 * nkb, *ph = pg + 2 * nblk;
+  double *pk = part, *pn = part + nkk, *pg = pn + nkb, *ph = pg + 2 * nblk;
   int st;
   for (int ik = 0; ik < c->nk; ++ik) {
     const Basis& B = c->bases[ik];
+    const dim3 gk(c->nocc, kKch);
     if (c->prec == PARO_MIXED && B.d_psi32)
-      k_kinetic<float><<<c->nocc, 256, 0, c->stream>>>(B.npw, B.d_psi32, B.d_kin32, pk + (size_t)ik * c->nocc);
+      k_kinetic<float><<<gk, 256, 0, c->stream>>>(B.npw, B.d_psi32, B.d_kin32, pk + (size_t)ik * c->nocc * kKch);
     else
-      k_kinetic<double><<<c->nocc, 256, 0, c->stream>>>(B.npw, B.d_psi, B.d_kin, pk + (size_t)ik * c->nocc);
+      k_kinetic<double><<<gk, 256, 0, c->stream>>>(B.npw, B.d_psi, B.d_kin, pk + (size_t)ik * c->nocc * kKch);
     PARO_LAUNCH(c, "k_kinetic");
     if (c->have_kb) {
       double2* P = static_cast<double2*>(ws_get(c, "kb_proj", (size_t)c->nproj * c->nb * sizeof(double2)));
@@ -850,18 +872,18 @@ int energy_terms(Ctx* c, const double* rho_dev, double terms[7]) {
   for (int ik = 0; ik < c->nk; ++ik) {
     double sk = 0, sn = 0;
     for (int b = 0; b < c->nocc; ++b) {
-      sk += h[(size_t)ik * c->nocc + b];
-      sn += h[nkb + (size_t)ik * c->nocc + b];
+      for (int ch = 0; ch < kKch; ++ch) sk += h[((size_t)ik * c->nocc + b) * kKch + ch];
+      sn += h[nkk + (size_t)ik * c->nocc + b];
     }
     terms[PARO_E_KINETIC] += 2.0 * c->kw[ik] * sk;
     if (c->have_kb) terms[PARO_E_NONLOCAL] += 2.0 * c->kw[ik] * sn;
   }
   double sl = 0, sx = 0, sh = 0;
   for (int i = 0; i < nblk; ++i) {
-    sl += h[2 * nkb + 2 * i];
-    sx += h[2 * nkb + 2 * i + 1];
+    sl += h[nkk + nkb + 2 * i];
+    sx += h[nkk + nkb + 2 * i + 1];
   }
-  for (int i = 0; i < nh; ++i) sh += h[2 * nkb + 2 * nblk + i];
+  for (int i = 0; i < nh; ++i) sh += h[nkk + nkb + 2 * nblk + i];
   const double dv = c->omega / c->ngrid;
   terms[PARO_E_LOCAL] = dv * sl;
   terms[PARO_E_XC] = dv * sx;
@@ -884,36 +906,55 @@ __global__ void k_pulay_push(int n, const double* __restrict__ rin, const double
 }
 
 // part[blk][i*m + j] = block partial of <R_i, R_j> (i <= j)
-__global__ void k_pulay_dots(int n, int m, const double* __restrict__ hres, const int* __restrict__ slot,
-                             double* __restrict__ part) {
+// <res_new, res_slot[i]> for the m slots of the history (the new residual is one of them): one pass over
+// the vectors, per-CTA partials part[block * 16 + i]. The other pairs were formed when the later of the
+// two arrived and are kept in the Gram cache.
+__global__ void __launch_bounds__(256) k_pulay_dots(int n, int m, const double* __restrict__ hres,
+                                                    const int* __restrict__ slot, int snew,
+                                                    double* __restrict__ part) {
   __shared__ double red[32];
-  for (int i = 0; i < m; ++i)
-    for (int j = i; j < m; ++j) {
-      const double* ri = hres + (size_t)slot[i] * n;
-      const double* rj = hres + (size_t)slot[j] * n;
-      double s = 0.0;
-      for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) s += ri[t] * rj[t];
-      s = block_sum(s, red);
-      if (threadIdx.x == 0) part[(size_t)blockIdx.x * m * m + i * m + j] = s;
-      __syncthreads();
-    }
+  double acc[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) acc[i] = 0.0;
+  const double* rn = hres + (size_t)snew * n;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const double x = rn[t];
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (i < m) acc[i] = fma(x, hres[(size_t)slot[i] * n + t], acc[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    if (i >= m) break;
+    const double v = block_sum(acc[i], red);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * 16 + i] = v;
+    __syncthreads();
+  }
 }
 
-// one thread: sum partials, build the bordered system, Gaussian elimination with partial pivoting
+// one CTA: the new row of the Gram cache from the partials, then the bordered system by one thread,
+// Gaussian elimination with partial pivoting
 __global__ void __launch_bounds__(256) k_pulay_solve(int m, int nblk, const double* __restrict__ part,
-                                                     double* __restrict__ coef) {
+                                                     const int* __restrict__ slot, int snew,
+                                                     double* __restrict__ gram, double* __restrict__ coef) {
   __shared__ double sa[16 * 16];
-  {  // the block partials of each (i, j) summed by one warp (lane-strided, then a shuffle tree)
+  {  // the block partials of each new dot summed by one warp (lane-strided, then a shuffle tree)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int ij = warp; ij < m * m; ij += nw) {
-      const int i = ij / m, j = ij - i * m;
+    for (int i = warp; i < m; i += nw) {
       double s = 0.0;
-      if (j >= i)
-        for (int b = lane; b < nblk; b += 32) s += part[(size_t)b * m * m + ij];
+      for (int b = lane; b < nblk; b += 32) s += part[(size_t)b * 16 + i];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) sa[ij] = s;
+      if (lane == 0) {
+        gram[snew * 16 + slot[i]] = s;
+        gram[slot[i] * 16 + snew] = s;
+      }
     }
+  }
+  __syncthreads();
+  for (int ij = threadIdx.x; ij < m * m; ij += blockDim.x) {
+    const int i = ij / m, j = ij - i * m;
+    sa[ij] = gram[slot[i] * 16 + slot[j]];
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
@@ -965,6 +1006,7 @@ int pulay_mix(Ctx* c, const double* rho_out, int depth, double beta) {
     if (c->d_pulay_rho) { cudaFree(c->d_pulay_rho); cudaFree(c->d_pulay_res); }
     PARO_CU(c, cudaMalloc(&c->d_pulay_rho, (size_t)depth * n * sizeof(double)));
     PARO_CU(c, cudaMalloc(&c->d_pulay_res, (size_t)depth * n * sizeof(double)));
+    if (!c->d_pulay_gram) PARO_CU(c, cudaMalloc(&c->d_pulay_gram, 16 * 16 * sizeof(double)));
     c->pulay_cap = depth;
     c->pulay_n = 0;
     c->pulay_head = 0;
@@ -976,23 +1018,22 @@ int pulay_mix(Ctx* c, const double* rho_out, int depth, double beta) {
   c->pulay_head = (c->pulay_head + 1) % depth;
   if (c->pulay_n < depth) ++c->pulay_n;
   const int m = c->pulay_n;
-  std::vector<int> slots(m);
-  for (int i = 0; i < m; ++i) slots[i] = ((c->pulay_head - m + i) % depth + depth) % depth;  // oldest first
+  // oldest first; kept in the context, so the asynchronous copy below may read it after this returns
+  c->pulay_slots.resize(m);
+  for (int i = 0; i < m; ++i) c->pulay_slots[i] = ((c->pulay_head - m + i) % depth + depth) % depth;
   int* dslot = static_cast<int*>(ws_get(c, "pulay_slot", 16 * sizeof(int)));
   const int nblk = 152;
-  double* part = static_cast<double*>(ws_get(c, "pulay_part", (size_t)nblk * 16 * 16 * sizeof(double)));
+  double* part = static_cast<double*>(ws_get(c, "pulay_part", (size_t)nblk * 16 * sizeof(double)));
   double* coef = static_cast<double*>(ws_get(c, "pulay_coef", 16 * sizeof(double)));
   if (!dslot || !part || !coef) return PARO_ERR_CUDA;
-  PARO_CU(c, cudaMemcpyAsync(dslot, slots.data(), m * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-  k_pulay_dots<<<nblk, 256, 0, c->stream>>>(n, m, c->d_pulay_res, dslot, part);
+  PARO_CU(c, cudaMemcpyAsync(dslot, c->pulay_slots.data(), m * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  k_pulay_dots<<<nblk, 256, 0, c->stream>>>(n, m, c->d_pulay_res, dslot, slot_new, part);
   PARO_LAUNCH(c, "k_pulay_dots");
-  k_pulay_solve<<<1, 256, 0, c->stream>>>(m, nblk, part, coef);
+  k_pulay_solve<<<1, 256, 0, c->stream>>>(m, nblk, part, dslot, slot_new, c->d_pulay_gram, coef);
   PARO_LAUNCH(c, "k_pulay_solve");
   k_pulay_mix<<<(n + 255) / 256, 256, 0, c->stream>>>(n, m, c->d_pulay_rho, c->d_pulay_res, dslot, coef, beta,
                                                       c->d_rho_in);
   PARO_LAUNCH(c, "k_pulay_mix");
-  // keep the host copy of slots alive until the copy above has been consumed
-  PARO_CU(c, cudaStreamSynchronize(c->stream));
   return PARO_OK;
 }
 

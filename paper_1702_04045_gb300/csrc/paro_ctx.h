@@ -90,6 +90,8 @@ struct Ctx {
   int pulay_n = 0, pulay_head = 0, pulay_cap = 0;
   double* d_pulay_rho = nullptr;  // pulay_cap x ngrid
   double* d_pulay_res = nullptr;
+  double* d_pulay_gram = nullptr;  // 16 x 16: <res_s, res_t> by ring slot, filled as residuals arrive
+  std::vector<int> pulay_slots;    // host source of the slot list copied each mixing step
   double e_prev = 0;
   int scf_iter = 0, scf_small = 0;
   bool fft_configured[2] = {false, false};
@@ -208,6 +210,9 @@ int band_norms(Ctx* c, int nb, int npw, const cplx<T>* x, int ldx, double* out_d
 // residual norms ||hpsi_b - eps_b psi_b||, eps device
 int residual_norms(Ctx* c, int nb, int npw, const double2* psi, const double2* hpsi, const double* eps_dev,
                    double* out_dev);
+// the same from FP32 rows in FP32 arithmetic (mixed path)
+int residual_norms32(Ctx* c, int nb, int npw, const float2* psi, const float2* hpsi, const double* eps_dev,
+                     double* out_dev);
 template <typename TS, typename TD>
 int convert(Ctx* c, size_t n, const cplx<TS>* src, cplx<TD>* dst);
 
@@ -235,7 +240,7 @@ int sticks_inverse(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* S);
 // density planes with the register FFT (cubic grids it supports); *used = false otherwise
 template <typename T>
 int density_planes_reg(Ctx* c, int ik, const cplx<T>* S, int nbands, int ngrp, int gsize, double wfac, double* part,
-                       bool* used);
+                       bool* used, bool* f32part);
 // rho(r) (+)= wfac sum_b |psi~_b(r)|^2 over nbands rows of psi at k-point ik (psi~: unnormalised inverse DFT)
 template <typename T>
 int density_bands(Ctx* c, int ik, int nbands, const cplx<T>* psi, double wfac, double* rho_dev, bool accumulate);
