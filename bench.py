@@ -169,9 +169,10 @@ def launch_work(name: str, s):
     if kern == "eigh_refine":  # two refinement steps + the cluster Rayleigh-Ritz: 10 FP64 n x n complex GEMMs
         return "alu64", 10 * 8.0 * nb ** 3
     if kern.startswith("k_plane_density") and tag in ("energy", "mix"):
-        # inverse plane FFTs of the occupied orbitals: stick buffer read once, FP64 partial planes written
+        # inverse plane FFTs of the occupied orbitals: stick buffer read once, one partial plane per group
+        # of 8 bands written (FP32 sums for FP32 orbitals, FP64 otherwise)
         nocc = s["nocc"]
-        return "hbm", nocc * n3 * ncol * b + (nocc + 7) // 8 * ng * 8
+        return "hbm", nocc * n3 * ncol * b + (nocc + 7) // 8 * ng * (4 if b == 8 else 8)
     if kern.startswith("k_chol"):
         return "alu64", 4.0 / 3.0 * nb ** 3 * 2
     return None, None

@@ -387,7 +387,7 @@ __global__ void k_invit_prep(int n, const R* __restrict__ d, const R* __restrict
 template <typename R>
 __global__ void k_invit_solve(int n, const R* __restrict__ d, const R* __restrict__ e, const R* __restrict__ lam,
                               const R* __restrict__ tinyp, R* __restrict__ Z, int first, R* __restrict__ fac,
-                              unsigned char* __restrict__ swg) {
+                              unsigned char* __restrict__ swg, int* __restrict__ info) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int E = blockDim.x, t = threadIdx.x, j = blockIdx.x * E + t;
   R* R0 = reinterpret_cast<R*>(smem_raw);  // 1 / (guarded pivot)
@@ -399,7 +399,8 @@ __global__ void k_invit_solve(int n, const R* __restrict__ d, const R* __restric
   if (j >= n) return;  // no barriers below
   const size_t nn = (size_t)n * n;
   if (!first) {
-    for (int i = 0; i < n; ++i) {
+#pragma unroll 8
+    for (int i = 0; i < n; ++i) {  // independent loads: unrolled so that many are in flight
       const size_t o = (size_t)i * E + t, g = (size_t)i * n + j;
       R0[o] = fac[g]; U1[o] = fac[nn + g]; U2[o] = fac[2 * nn + g]; Lm[o] = fac[3 * nn + g]; SW[o] = swg[g];
     }
@@ -437,6 +438,7 @@ __global__ void k_invit_solve(int n, const R* __restrict__ d, const R* __restric
     fac[g] = R0[o]; fac[nn + g] = U1[o]; fac[2 * nn + g] = U2[o]; fac[3 * nn + g] = Lm[o]; swg[g] = SW[o];
   }
   }
+#pragma unroll 8
   for (int i = 0; i < n; ++i)
     z[(size_t)i * E + t] = first ? (R)(((i * 7919 + j * 104729) % 1999) + 1) / (R)1999 - (R)0.5 : Z[(size_t)i * n + j];
   for (int i = 0; i + 1 < n; ++i) {  // forward: row interchanges and multipliers
@@ -446,14 +448,23 @@ __global__ void k_invit_solve(int n, const R* __restrict__ d, const R* __restric
     z[o] = zi;
     z[o + E] = zi1 - Lm[o] * zi;
   }
+  R nrm = 0;
   for (int i = n - 1; i >= 0; --i) {  // back substitution with U (bandwidth 3)
     const size_t o = (size_t)i * E + t;
     R sv = z[o];
     if (i + 1 < n) sv -= U1[o] * z[o + E];
     if (i + 2 < n) sv -= U2[o] * z[o + 2 * E];
-    z[o] = sv * R0[o];
+    sv *= R0[o];
+    z[o] = sv;
+    nrm += sv * sv;
   }
-  for (int i = 0; i < n; ++i) Z[(size_t)i * n + j] = z[(size_t)i * E + t];
+  // normalised here (k_invit_mgs orthogonalises and normalises again inside clusters of two or more)
+  if (!(nrm > (R)0) || !isfinite(nrm)) {
+    atomicExch(info, 1);
+    nrm = 1;
+  }
+  const R inv = (R)1 / sqrt(nrm);
+  for (int i = 0; i < n; ++i) Z[(size_t)i * n + j] = z[(size_t)i * E + t] * inv;
 }
 
 template <typename R>
@@ -463,6 +474,7 @@ __global__ void k_invit_mgs(int n, R* __restrict__ Z, const int* __restrict__ cs
   const int cl = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (cl >= *nclu) return;
   const int c0 = cstart[cl], c1 = cstart[cl + 1];
+  if (c1 - c0 < 2) return;  // a single vector: k_invit_solve has normalised it
   for (int j = c0; j < c1; ++j) {
     for (int q = c0; q < j; ++q) {
       R s = 0;
@@ -742,7 +754,8 @@ int invit(Ctx* c, int n, const R* d, const R* e, const R* w, R* Z, int* info) {
   unsigned char* swg = static_cast<unsigned char*>(ws_get(c, "invit_sw", (size_t)n * n));
   if (!fac || !swg) return PARO_ERR_CUDA;
   for (int it = 0; it < 3; ++it) {
-    k_invit_solve<R><<<(n + E - 1) / E, E, sm, c->stream>>>(n, d, e, lam, tiny, Z, it == 0 ? 1 : 0, fac, swg);
+    k_invit_solve<R><<<(n + E - 1) / E, E, sm, c->stream>>>(n, d, e, lam, tiny, Z, it == 0 ? 1 : 0, fac, swg,
+                                                            info);
     PARO_LAUNCH(c, "k_invit_solve");
     k_invit_mgs<R><<<(n + 3) / 4, 128, 0, c->stream>>>(n, Z, cst, nclu, info);
     PARO_LAUNCH(c, "k_invit_mgs");

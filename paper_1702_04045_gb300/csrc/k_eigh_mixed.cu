@@ -48,7 +48,6 @@ __global__ void __launch_bounds__(1024) k_tridiag_cta(int n, const double2* __re
   float2* A = reinterpret_cast<float2*>(smem_raw);  // n x ld
   float2* u = A + (size_t)n * ld;
   float2* w = u + n;
-  __shared__ float s_t[2];  // by parity of j: a CTA that skips column j (t = 0) still reads it safely
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   for (int idx = tid; idx < n * n; idx += blockDim.x) {
     const int i = idx / n, k = idx - i * n;
@@ -58,47 +57,47 @@ __global__ void __launch_bounds__(1024) k_tridiag_cta(int n, const double2* __re
   __syncthreads();
   for (int j = 0; j + 1 < n; ++j) {
     const int m = n - j - 1;
-    if (warp == 0) {  // the reflector of column j, by one warp (FP32: the FP64 refinement follows)
-      float nrm2 = 0.f;
-      for (int i = lane; i < m; i += 32) {
-        const float2 x = A[(j + 1 + i) * ld + j];
-        u[i] = x;
-        nrm2 += x.x * x.x + x.y * x.y;
-      }
+    // The reflector of column j, by every warp from the column in registers (FP32: the FP64 refinement
+    // follows), so no barrier separates it from the matrix-vector product; lane holds u_k for
+    // k = lane + 32 c (c < KC). Warp 0 also writes it to shared memory (read by the update) and out.
+    constexpr int KC = (kMixMaxN + 31) / 32;
+    float2 ur[KC];
+    float nrm2 = 0.f;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) nrm2 += __shfl_xor_sync(0xffffffffu, nrm2, o);
-      __syncwarp();
-      if (lane == 0) {
-        const float2 x0 = u[0];
-        const float ax0 = hypotf(x0.x, x0.y);
-        const float nx = sqrtf(nrm2);
-        float2 alpha = x0;
-        float t = 0.f;
-        if (m > 1 && nx > 0.f && nrm2 - ax0 * ax0 > 0.f) {
-          const float2 phs = ax0 > 0.f ? make_float2(x0.x / ax0, x0.y / ax0) : make_float2(1.f, 0.f);
-          alpha = make_float2(-phs.x * nx, -phs.y * nx);
-          u[0] = csub(x0, alpha);
-          t = 1.f / (nrm2 + nx * ax0);
+    for (int c = 0; c < KC; ++c) {
+      const int k = lane + 32 * c;
+      ur[c] = k < m ? A[(j + 1 + k) * ld + j] : make_float2(0.f, 0.f);
+      nrm2 += ur[c].x * ur[c].x + ur[c].y * ur[c].y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nrm2 += __shfl_xor_sync(0xffffffffu, nrm2, o);
+    const float2 x0 = make_float2(__shfl_sync(0xffffffffu, ur[0].x, 0), __shfl_sync(0xffffffffu, ur[0].y, 0));
+    const float ax0 = hypotf(x0.x, x0.y);
+    const float nx = sqrtf(nrm2);
+    float2 alpha = x0;
+    float t = 0.f;
+    if (m > 1 && nx > 0.f && nrm2 - ax0 * ax0 > 0.f) {
+      const float2 phs = ax0 > 0.f ? make_float2(x0.x / ax0, x0.y / ax0) : make_float2(1.f, 0.f);
+      alpha = make_float2(-phs.x * nx, -phs.y * nx);
+      if (lane == 0) ur[0] = csub(x0, alpha);
+      t = 1.f / (nrm2 + nx * ax0);
+    }
+    if (warp == 0) {
+#pragma unroll
+      for (int c = 0; c < KC; ++c) {
+        const int k = lane + 32 * c;
+        if (k < m) {
+          u[k] = ur[c];
+          U[(size_t)j * n + k] = ur[c];
         }
-        s_t[j & 1] = t;
+      }
+      if (lane == 0) {
         tau[j] = t;
         ecx[j] = alpha;
         d[j] = A[j * ld + j].x;
       }
-      __syncwarp();
-      for (int i = lane; i < m; i += 32) U[(size_t)j * n + i] = u[i];
     }
-    __syncthreads();
-    const float t = s_t[j & 1];
-    if (t == 0.f) continue;
-    // u cached in registers: lane holds u_k for k = lane + 32 c (c < KC)
-    constexpr int KC = (kMixMaxN + 31) / 32;
-    float2 ur[KC];
-#pragma unroll
-    for (int c = 0; c < KC; ++c) {
-      const int k = lane + 32 * c;
-      ur[c] = k < m ? u[k] : make_float2(0.f, 0.f);
-    }
+    if (t == 0.f) continue;  // the same in every warp: no barrier is skipped by some warps only
     for (int i = warp; i < m; i += nwarp) {  // p_i = t sum_k B_ik u_k, B_ik = conj(B_ki) above the diagonal
       const float2* row = A + (j + 1 + i) * ld + (j + 1);
       const float2* col = A + (j + 1) * ld + (j + 1 + i);
