@@ -86,8 +86,30 @@ __device__ __forceinline__ void reg_dft_2f(cplx<T>* v, const cplx<T>* tw, int st
 template <typename T, bool INV> struct RegDft<T, 6, INV> {
   static __device__ __forceinline__ void run(cplx<T>* v, const cplx<T>* tw, int s) { reg_dft_2f<T, 2, 3, INV>(v, tw, s); }
 };
+// 9 = 3 x 3 as reg_dft_2f<3, 3>, with the twiddles W_9^{q2 k1} (q2 k1 in {1, 2, 4}) as constants
 template <typename T, bool INV> struct RegDft<T, 9, INV> {
-  static __device__ __forceinline__ void run(cplx<T>* v, const cplx<T>* tw, int s) { reg_dft_2f<T, 3, 3, INV>(v, tw, s); }
+  static __device__ __forceinline__ void run(cplx<T>* v, const cplx<T>*, int) {
+    const T cs[5] = {(T)1, (T)0.766044443118978, (T)0.17364817766693041, (T)0, (T)-0.9396926207859083};
+    const T sn[5] = {(T)0, (T)0.6427876096865393, (T)0.984807753012208, (T)0, (T)0.3420201433256689};
+    cplx<T> a[9];
+#pragma unroll
+    for (int q2 = 0; q2 < 3; ++q2) {
+      cplx<T> t[3] = {v[q2], v[3 + q2], v[6 + q2]};
+      dft3<T, INV>(t);
+#pragma unroll
+      for (int k1 = 0; k1 < 3; ++k1) {
+        const int m = q2 * k1;  // exp(-+ 2 pi i m / 9)
+        a[k1 * 3 + q2] = m == 0 ? t[k1] : cmul(t[k1], mk<T>(cs[m], INV ? sn[m] : -sn[m]));
+      }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) {
+      cplx<T> u[3] = {a[k1 * 3], a[k1 * 3 + 1], a[k1 * 3 + 2]};
+      dft3<T, INV>(u);
+#pragma unroll
+      for (int k2 = 0; k2 < 3; ++k2) v[k1 + 3 * k2] = u[k2];
+    }
+  }
 };
 template <typename T, bool INV> struct RegDft<T, 12, INV> {
   static __device__ __forceinline__ void run(cplx<T>* v, const cplx<T>* tw, int s) { reg_dft_2f<T, 4, 3, INV>(v, tw, s); }
@@ -150,6 +172,26 @@ __device__ __forceinline__ void line_fwd(cplx<T>* v, int p, const cplx<T>* tw) {
 template <int Q, int P> __device__ __forceinline__ int dt_index(int p, int pr, int k) {
   return k < P ? p + Q * k : k + Q * pr;
 }
+
+// A lane's twiddles of steps B and C for lines of N = Q P, loaded once and kept in registers across the
+// lines a warp transforms: b[k1] = W_N^{p k1} (k1 >= 1), c[s] = the shuffle stage h = P / 2^(s+1)'s
+// W_N^{(p mod h) N / (2h)} (forward sign; the inverse uses the conjugates).
+template <typename T, int Q, int P> struct LaneTw {
+  static constexpr int kS = P == 1 ? 1 : (P == 2 ? 1 : P == 4 ? 2 : P == 8 ? 3 : P == 16 ? 4 : 5);
+  cplx<T> b[Q];
+  cplx<T> c[kS];
+  __device__ __forceinline__ LaneTw(const cplx<T>* tw, int p) {
+    constexpr int N = Q * P;
+#pragma unroll
+    for (int k1 = 1; k1 < Q; ++k1) b[k1] = tw[p * k1];
+    b[0] = mk<T>(1, 0);
+#pragma unroll
+    for (int s = 0; s < kS; ++s) {
+      const int h = P >> (s + 1);
+      c[s] = h >= 1 ? tw[(p & (h - 1)) * (N / (2 * h))] : mk<T>(1, 0);
+    }
+  }
+};
 
 template <typename T, int Q, int P>
 __device__ __forceinline__ void line_inv_t(cplx<T>* v, int p, const cplx<T>* tw, cplx<T>* scr, int es, bool ok) {
@@ -216,6 +258,77 @@ __device__ __forceinline__ void line_fwd_t(cplx<T>* v, int p, const cplx<T>* tw,
   for (int k1 = 1; k1 < Q; ++k1)
     if (p) v[k1] = cmul(v[k1], tw_get<T, false>(tw, p * k1));
   RegDft<T, Q, false>::run(v, tw, P);
+}
+
+// line_inv_t / line_fwd_t with the lane's twiddles from registers (lt) instead of the table
+template <typename T, int Q, int P>
+__device__ __forceinline__ void line_inv_tr(cplx<T>* v, int p, const LaneTw<T, Q, P>& lt, cplx<T>* scr, int es,
+                                            bool ok) {
+  static_assert(Q == 9 && P <= 8, "line_inv_tr: constant-twiddle Q-point DFT (Q = 9) only");
+  __syncwarp();  // every lane has loaded its values before the line's storage is reused
+  RegDft<T, Q, true>::run(v, nullptr, P);
+#pragma unroll
+  for (int k1 = 1; k1 < Q; ++k1)
+    if (p) v[k1] = cmul(v[k1], cconj(lt.b[k1]));
+#pragma unroll
+  for (int s = 0; (P >> (s + 1)) >= 1; ++s) {  // shuffle stages h = P/2 .. 1 for k1 >= P only
+    const int h = P >> (s + 1);
+    const bool up = (p & h) != 0;
+    const cplx<T> w = cconj(lt.c[s]);
+#pragma unroll
+    for (int q = P; q < Q; ++q) {
+      const cplx<T> b = shfl_xor_c<T>(v[q], h);
+      v[q] = up ? (h > 1 ? cmul(csub(b, v[q]), w) : csub(b, v[q])) : cadd(v[q], b);
+    }
+  }
+  if (ok)
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) scr[(k1 * (P + 1) + p) * es] = v[k1];
+  __syncwarp();
+  cplx<T> u[P];
+#pragma unroll
+  for (int j = 0; j < P; ++j) u[j] = scr[(p * (P + 1) + j) * es];
+  __syncwarp();
+  RegDft<T, P, true>::run(u, nullptr, Q);
+#pragma unroll
+  for (int k2 = 0; k2 < P; ++k2) v[k2] = u[k2];
+}
+
+template <typename T, int Q, int P>
+__device__ __forceinline__ void line_fwd_tr(cplx<T>* v, int p, const LaneTw<T, Q, P>& lt, cplx<T>* scr, int es,
+                                            bool ok) {
+  static_assert(Q == 9 && P <= 8, "line_fwd_tr: constant-twiddle Q-point DFT (Q = 9) only");
+  __syncwarp();  // every lane has loaded its values before the line's storage is reused
+  {
+    cplx<T> u[P];
+#pragma unroll
+    for (int k2 = 0; k2 < P; ++k2) u[k2] = v[k2];
+    RegDft<T, P, false>::run(u, nullptr, Q);
+    if (ok)
+#pragma unroll
+      for (int j = 0; j < P; ++j) scr[(p * (P + 1) + j) * es] = u[j];
+  }
+#pragma unroll
+  for (int s = LaneTw<T, Q, P>::kS - 1; s >= 0; --s) {  // shuffle stages h = 1 .. P/2 for k1 >= P only
+    const int h = P >> (s + 1);
+    if (h < 1) continue;
+    const bool up = (p & h) != 0;
+    const cplx<T> wc = lt.c[s];
+#pragma unroll
+    for (int q = P; q < Q; ++q) {
+      const cplx<T> t = up && h > 1 ? cmul(v[q], wc) : v[q];
+      const cplx<T> o = shfl_xor_c<T>(t, h);
+      v[q] = up ? csub(o, t) : cadd(t, o);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k1 = 0; k1 < P; ++k1) v[k1] = scr[(k1 * (P + 1) + p) * es];
+  __syncwarp();
+#pragma unroll
+  for (int k1 = 1; k1 < Q; ++k1)
+    if (p) v[k1] = cmul(v[k1], lt.b[k1]);
+  RegDft<T, Q, false>::run(v, nullptr, P);
 }
 
 // Factorisations N = Q * P used by the register kernels (P lanes per line, Q values per lane).

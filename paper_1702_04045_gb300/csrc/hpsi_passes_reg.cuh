@@ -323,6 +323,7 @@ __global__ void __launch_bounds__(256) k_plane_density_reg(const cplx<T>* __rest
     {
       constexpr int Q = SY::Q, P = SY::P, G = 32 / P;
       const int grp = lane / P, p = lane % P, pr = bitrev_lane<P>(p);
+      const LaneTw<T, Q, P> lty(ty, p);
       for (int r0 = warp * G; r0 < nxr; r0 += nw * G) {
         const int r = r0 + grp;
         const bool ok = r < nxr;
@@ -330,7 +331,7 @@ __global__ void __launch_bounds__(256) k_plane_density_reg(const cplx<T>* __rest
         cplx<T> v[Q];
 #pragma unroll
         for (int q = 0; q < Q; ++q) v[q] = ok ? row[P * q + p] : mk<T>(0, 0);
-        if constexpr (PlaneLines<T, N2>::kTile) line_inv_t<T, Q, P>(v, p, ty, row, 1, ok);
+        if constexpr (PlaneLines<T, N2>::kTile) line_inv_tr<T, Q, P>(v, p, lty, row, 1, ok);
         else line_inv<T, Q, P>(v, p, ty);
         __syncwarp();
         if (ok)
@@ -343,13 +344,14 @@ __global__ void __launch_bounds__(256) k_plane_density_reg(const cplx<T>* __rest
     {
       constexpr int Q = SX::Q, P = SX::P, G = 32 / P;
       const int grp = lane / P, p = lane % P, pr = bitrev_lane<P>(p);
+      const LaneTw<T, Q, P> ltx(tx, p);
       for (int c0 = warp * G; c0 < N2; c0 += nw * G) {
         const int y = c0 + grp;
         const bool ok = y < N2;
         cplx<T> v[Q];
 #pragma unroll
         for (int q = 0; q < Q; ++q) v[q] = ok ? Pl[(P * q + p) * LS + y] : mk<T>(0, 0);
-        if constexpr (PlaneLines<T, N1>::kTile) line_inv_t<T, Q, P>(v, p, tx, Pl + (ok ? y : 0), LS, ok);
+        if constexpr (PlaneLines<T, N1>::kTile) line_inv_tr<T, Q, P>(v, p, ltx, Pl + (ok ? y : 0), LS, ok);
         else line_inv<T, Q, P>(v, p, tx);
         if (ok)
 #pragma unroll
