@@ -181,8 +181,8 @@ def launch_work(name: str, s):
 # DRAM bytes per launch from one ncu capture, valid only for the kernel source it was taken on
 # (sha256 prefix of the file defining the kernel); otherwise the roofline's traffic is null.
 TRAFFIC = {
-    # k_plane_reg<float, 72, 72>, one Rayleigh-Ritz launch (144 bands): 84.27 MB read + 24.09 MB written
-    "k_plane<f32>": (108361728, "paper_1702_04045_gb300/csrc/hpsi_passes_reg.cuh", "6d6876b399cda0f7"),
+    # k_plane_reg<float, 72, 72>, one full 144-band launch: 84.24 MB read + 24.07 MB written
+    "k_plane<f32>": (108304640, "paper_1702_04045_gb300/csrc/hpsi_passes_reg.cuh", "712e0592f863882b"),
 }
 
 
