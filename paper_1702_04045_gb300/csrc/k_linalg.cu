@@ -1107,10 +1107,26 @@ int residual_norms(Ctx* c, int nb, int npw, const double2* psi, const double2* h
   return PARO_OK;
 }
 
+// FP32 -> FP64 by the IEEE 754 bit layouts (sign, exponent rebiased by 1023 - 127, mantissa shifted by
+// 29): exact, and on the integer pipe instead of GB300's narrow FP64 pipe; zeros, subnormals, infinities
+// and NaNs take the ordinary conversion
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)b);
+}
+
 template <typename TS, typename TD>
 __global__ void k_convert(size_t n, const cplx<TS>* __restrict__ s, cplx<TD>* __restrict__ d) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    d[i] = mk<TD>((TD)s[i].x, (TD)s[i].y);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    if constexpr (sizeof(TS) == 4 && sizeof(TD) == 8)
+      d[i] = mk<TD>(f32_to_f64_bits(s[i].x), f32_to_f64_bits(s[i].y));
+    else
+      d[i] = mk<TD>((TD)s[i].x, (TD)s[i].y);
+  }
 }
 
 template <typename TS, typename TD>

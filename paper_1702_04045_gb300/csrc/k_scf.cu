@@ -700,9 +700,10 @@ __global__ void k_density_reduce32(int N1, int N2, int N3, int ngrp, const float
   if (pl >= N1 * N2 * N3) return;
   const int y = pl % N2, x = (pl / N2) % N1, z = pl / (N1 * N2);
   const size_t idx = ((size_t)x * N2 + y) * N3 + z;
-  double s = 0.0;
-  for (int g = 0; g < ngrp; ++g) s += (double)part[(size_t)g * N1 * N2 * N3 + pl];
-  s *= wfac;
+  // the groups summed in a compensated FP32 pair (two-sum; within ~2^-46 of the FP64 sum), converted once
+  float hi = 0.f, lo = 0.f;
+  for (int g = 0; g < ngrp; ++g) two_sum_acc(hi, lo, part[(size_t)g * N1 * N2 * N3 + pl]);
+  const double s = ((double)hi + (double)lo) * wfac;
   rho[idx] = accumulate ? rho[idx] + s : s;
 }
 
