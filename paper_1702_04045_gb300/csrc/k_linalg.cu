@@ -160,17 +160,18 @@ static int pick_r(int M, int N, bool herm) {
 // K slices: the count nz (at most one per 256 of K, at most max_slices) that minimises the modelled
 // makespan, ceil(tiles nz / 152) waves of CTAs sharing an SM times the 16-wide steps of one slice;
 // ties go to fewer slices (less partial-sum traffic).
-static void split_k(int tiles, int K, size_t max_slices, int* nz_out, int* kslice_out) {
+static void split_k(int tiles, int K, size_t max_slices, int* nz_out, int* kslice_out, int resident = 1) {
   const int steps = (K + 15) / 16;
   int maxz = (K + 255) / 256;
   if ((size_t)maxz > max_slices) maxz = (int)max_slices;
   if (maxz < 1) maxz = 1;
+  const long long slots = 152LL * (resident < 1 ? 1 : resident);  // CTAs resident at once
   long long best = -1;
   int best_nz = 1, best_steps = steps;
   for (int nz = 1; nz <= maxz; ++nz) {
     const int s = (steps + nz - 1) / nz;
     const int z = (steps + s - 1) / s;
-    const long long waves = ((long long)tiles * z + 151) / 152;
+    const long long waves = ((long long)tiles * z + slots - 1) / slots;
     const long long cost = waves * s;
     if (best < 0 || cost < best) {
       best = cost;
@@ -207,6 +208,38 @@ static void launch_cn_r(int r, dim3 grid, cudaStream_t st, int M, int N, int K, 
     cn_smem_attr<TA, TB, ACC, 4, CARRY>(sm);
     k_gemm_cn<TA, TB, ACC, 4, CARRY><<<grid, 256, sm, st>>>(M, N, K, kslice, A, lda, B, ldb, part, herm);
   }
+}
+
+// resident CTAs per SM of the k_gemm_cn form (r, carry), from the occupancy calculator, cached per form
+template <typename TA, typename TB, typename ACC, bool CARRY>
+static int cn_resident_r(int r) {
+  static int cached[5] = {0, 0, 0, 0, 0};
+  if (r < 2 || r > 4) return 1;
+  if (cached[r]) return cached[r];
+  const size_t sm = (size_t)2 * 2 * 16 * (16 * r + 1) * sizeof(cplx<ACC>);
+  int nb = 1;
+  cudaError_t e;
+  if (r == 2) {
+    cn_smem_attr<TA, TB, ACC, 2, CARRY>(sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gemm_cn<TA, TB, ACC, 2, CARRY>, 256, sm);
+  } else if (r == 3) {
+    cn_smem_attr<TA, TB, ACC, 3, CARRY>(sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gemm_cn<TA, TB, ACC, 3, CARRY>, 256, sm);
+  } else {
+    cn_smem_attr<TA, TB, ACC, 4, CARRY>(sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gemm_cn<TA, TB, ACC, 4, CARRY>, 256, sm);
+  }
+  if (e != cudaSuccess || nb < 1) {
+    cudaGetLastError();
+    nb = 1;
+  }
+  cached[r] = nb;
+  return nb;
+}
+
+template <typename TA, typename TB, typename ACC>
+static int cn_resident(int r, bool carry) {
+  return carry && sizeof(ACC) == 4 ? cn_resident_r<TA, TB, ACC, true>(r) : cn_resident_r<TA, TB, ACC, false>(r);
 }
 
 template <typename TA, typename TB, typename ACC>
@@ -262,7 +295,7 @@ int gemm_cn(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, const cplx<
   const int tiles_m = (M + tile - 1) / tile, tiles_n = (N + tile - 1) / tile;
   const int tiles = herm ? tiles_m * (tiles_m + 1) / 2 : tiles_m * tiles_n;
   int nz = 1, kslice = 16;
-  split_k(tiles, K, (size_t)1 << 20, &nz, &kslice);
+  split_k(tiles, K, (size_t)1 << 20, &nz, &kslice, cn_resident<TA, TB, ACC>(r, carry));
   double2* part = static_cast<double2*>(ws_get(c, "gemm_parts", (size_t)nz * M * N * sizeof(double2)));
   if (!part) return PARO_ERR_CUDA;
   if (K == 0) {
