@@ -98,31 +98,50 @@ __global__ void __launch_bounds__(1024) k_tridiag_cta(int n, const double2* __re
       }
     }
     if (t == 0.f) continue;  // the same in every warp: no barrier is skipped by some warps only
-    for (int i = warp; i < m; i += nwarp) {  // p_i = t sum_k B_ik u_k, B_ik = conj(B_ki) above the diagonal
-      const float2* row = A + (j + 1 + i) * ld + (j + 1);
-      const float2* col = A + (j + 1) * ld + (j + 1 + i);
-      float2 acc = make_float2(0.f, 0.f);
+    // p_i = t sum_k B_ik u_k (B_ik = conj(B_ki) above the diagonal): rows i and i + nwarp together, so that
+    // the two 32-lane reductions overlap
+    for (int i0 = warp; i0 < m; i0 += 2 * nwarp) {
+      const int i1 = i0 + nwarp;
+      const bool has1 = i1 < m;
+      const float2* row0 = A + (j + 1 + i0) * ld + (j + 1);
+      const float2* col0 = A + (j + 1) * ld + (j + 1 + i0);
+      const float2* row1 = A + (j + 1 + (has1 ? i1 : i0)) * ld + (j + 1);
+      const float2* col1 = A + (j + 1) * ld + (j + 1 + (has1 ? i1 : i0));
+      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
 #pragma unroll
       for (int c = 0; c < KC; ++c) {
         const int k = lane + 32 * c;
         if (k < m) {
-          float2 bv;
-          if (k <= i) {
-            bv = row[k];
+          float2 b0, b1;
+          if (k <= i0) {
+            b0 = row0[k];
           } else {
-            bv = col[k * ld];
-            bv.y = -bv.y;
+            b0 = col0[k * ld];
+            b0.y = -b0.y;
           }
-          acc.x = fmaf(bv.x, ur[c].x, fmaf(-bv.y, ur[c].y, acc.x));
-          acc.y = fmaf(bv.x, ur[c].y, fmaf(bv.y, ur[c].x, acc.y));
+          if (k <= i1) {
+            b1 = row1[k];
+          } else {
+            b1 = col1[k * ld];
+            b1.y = -b1.y;
+          }
+          a0.x = fmaf(b0.x, ur[c].x, fmaf(-b0.y, ur[c].y, a0.x));
+          a0.y = fmaf(b0.x, ur[c].y, fmaf(b0.y, ur[c].x, a0.y));
+          a1.x = fmaf(b1.x, ur[c].x, fmaf(-b1.y, ur[c].y, a1.x));
+          a1.y = fmaf(b1.x, ur[c].y, fmaf(b1.y, ur[c].x, a1.y));
         }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        a0.x += __shfl_xor_sync(0xffffffffu, a0.x, o);
+        a0.y += __shfl_xor_sync(0xffffffffu, a0.y, o);
+        a1.x += __shfl_xor_sync(0xffffffffu, a1.x, o);
+        a1.y += __shfl_xor_sync(0xffffffffu, a1.y, o);
       }
-      if (lane == 0) w[i] = make_float2(t * acc.x, t * acc.y);
+      if (lane == 0) {
+        w[i0] = make_float2(t * a0.x, t * a0.y);
+        if (has1) w[i1] = make_float2(t * a1.x, t * a1.y);
+      }
     }
     __syncthreads();
     // every warp: K = (t/2) u^H p (real), w = p - K u in registers (no second barrier for w)
