@@ -7,6 +7,7 @@ which it shares no code. Modules:
   paro   PCG source problems and the ParO projection step (Algorithms 1 and 2)
   scf    density, Hartree, LDA-PZ, Pulay, Ewald, energies and the ParO-merged SCF (Section 2.3)
 
-Parity unpinned (no independent check exists): the ParO iteration counts; the PZ-LDA constants
-beyond their finite-difference and continuity checks.
+Parity unpinned (no independent check exists): the ParO iteration counts. The PZ-LDA constants are
+pinned by the exact high-density coefficient and by an independent fit of the same Monte Carlo data;
+the energy assembly by its variational derivative and the double-counting identity.
 """
