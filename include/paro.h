@@ -53,9 +53,12 @@ enum {
  *   k_frac    host double[n_k*3], k in reduced coordinates of the reciprocal lattice (NULL: Gamma only,
  *             n_k must be 1); k_w host double[n_k], weights summing to 1 (NULL: 1/n_k each).
  *   n_bands   orbitals per k (occupied + extra); n_occ the occupied ones (occupation 2 each).
- *   precision PARO_FP64: every step in FP64. PARO_MIXED: FFTs, V.psi, the KB projector GEMMs and
- *             the inner PCG in FP32 (dot products accumulated in FP64); Gram, Cholesky, Rayleigh-Ritz,
- *             residual norms and energies in FP64.
+ *   precision PARO_FP64: every step in FP64. PARO_MIXED: orbitals stored in FP32; FFTs, V.psi, the KB
+ *             projector products (3xTF32 tensor cores inside the source solves), the inner PCG, the
+ *             Cholesky apply and the subspace rotations in FP32; the PCG dot products, the residual
+ *             norms and the Gram and H_sub matrices as FP32 partial sums added into an error-free FP32
+ *             two-sum pair and returned in FP64; Cholesky factor, Rayleigh-Ritz eigensolve (FP32 solve
+ *             refined to FP64 accuracy), density accumulation and energy sums in FP64.
  *   stream    cudaStream_t to enqueue all work on; NULL means the default stream.
  * The FFT grid is the smallest 2^a 3^b per axis with N_i > m_V,i + s_psi,i (m_V: largest |n_i| of the
  * density sphere |G|^2/2 <= 4 ecut; s_psi: span of n_i over every k's basis), so that V.psi is alias
@@ -94,6 +97,12 @@ int paro_set_positions(paro_ctx* ctx, const double* pos);
 /* paro_set_veff -- fixed effective potential V_eff(r) (Ha) on the grid, C order (N1, N2, N3);
  * host (on_device = 0) or device (on_device = 1) double[N1*N2*N3]. */
 int paro_set_veff(paro_ctx* ctx, const double* v_r, int on_device);
+/* paro_set_veff_rest -- V_eff = V_loc(R) + v_rest: the local pseudopotential of the current positions
+ * (Section 2.2, V_loc) plus the rest of the effective potential (Hartree, exchange-correlation or any
+ * external part; Section 2.1), v_rest host (on_device = 0) or device (on_device = 1) double[N1*N2*N3],
+ * C order, Ha. After paro_set_positions this keeps the rest and follows the atoms. PARO_ERR_STATE
+ * before paro_set_local_pp. */
+int paro_set_veff_rest(paro_ctx* ctx, const double* v_rest, int on_device);
 /* paro_get_veff -- copy the current V_eff(r) to a host double[N1*N2*N3]. */
 int paro_get_veff(paro_ctx* ctx, double* v_r);
 /* paro_get_vloc -- copy the local pseudopotential V_loc(r) of the current positions (Section 2.2,
@@ -130,9 +139,13 @@ int paro_apply_h(paro_ctx* ctx, int ik, int nb, int dtype, const void* psi, void
  *   Arguments, layout and ownership as paro_apply_h. The call allocates nothing: its scratch (stick
  *   buffer, KB projections, split-K partial sums) is one fixed 32 MiB device array inside the library,
  *   which every GPU that loads the library holds until the process exits.
- *   Size limit: nb * N3 * (stick columns) * element size, plus 2 * n_proj * nb * 16 bytes with KB
- *   projectors, must fit in 32 MiB; larger requests fail with PARO_ERR_ARG and a message giving the
- *   bytes needed (split the bands over several calls).
+ *   Size limit: with r(x) = x rounded up to a multiple of 256 bytes, e the bytes of one complex element
+ *   of dtype (16 or 8) and P = n_proj * nb, the scratch needed is
+ *     r(nb * N3 * (stick columns) * e)                                  (stick buffer)
+ *     + [KB projectors only] r(P * 16) + P * 16                          (projections, one K slice)
+ *     + [KB projectors and PARO_C32 only] r(P * 8)                       (FP32 copy of D o P)
+ *   and must not exceed 32 MiB (33554432 bytes); larger requests fail with PARO_ERR_ARG and a message
+ *   giving the bytes needed (split the bands over several calls).
  *   The first call on a device looks up the array's device address (with that device current) and
  *   caches it; make that first call before any stream capture.
  *   Every call shares the one array, and each call overwrites the scratch it reads: calls that

@@ -822,6 +822,22 @@ int paro_set_veff(paro_ctx* ctx, const double* v_r, int on_device) {
   return PARO_OK;
 }
 
+int paro_set_veff_rest(paro_ctx* ctx, const double* v_rest, int on_device) {
+  CTX_CHECK(ctx);
+  if (!v_rest) return fail(c, PARO_ERR_ARG, "null potential");
+  if (!c->have_pp) return fail(c, PARO_ERR_STATE, "paro_set_veff_rest: no local pseudopotential");
+  double* tmp = static_cast<double*>(ws_get(c, "grid_r1", (size_t)c->ngrid * sizeof(double)));
+  if (!tmp) return PARO_ERR_CUDA;
+  PARO_CU(c, cudaMemcpyAsync(tmp, v_rest, (size_t)c->ngrid * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  k_axpy_grid<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, 1.0, c->d_vloc, tmp);
+  PARO_LAUNCH(c, "k_axpy_grid");
+  int st = set_veff_device(c, tmp);
+  if (st) return st;
+  update_sigma(c);
+  return PARO_OK;
+}
+
 int paro_get_veff(paro_ctx* ctx, double* v_r) {
   CTX_CHECK(ctx);
   if (!v_r) return PARO_ERR_ARG;

@@ -325,7 +325,8 @@ static int apply_h_noalloc(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* 
   const size_t sticks = round256((size_t)nb * c->N[2] * B.ncol * eb);
   const size_t proj = c->have_kb ? round256((size_t)c->nproj * nb * sizeof(double2)) : 0;
   const size_t slice = c->have_kb ? (size_t)c->nproj * nb * sizeof(double2) : 0;  // one split-K slice
-  const size_t wconv = c->have_kb ? round256((size_t)c->nproj * nb * sizeof(float2)) : 0;  // FP32 D P
+  // the FP32 copy of D o P that the FP32 update product reads (the FP64 product reads D o P directly)
+  const size_t wconv = c->have_kb && sizeof(T) == 4 ? round256((size_t)c->nproj * nb * sizeof(float2)) : 0;
   const size_t need = sticks + proj + wconv + slice;
   if (need > kNoAllocScratchBytes)
     return fail(c, PARO_ERR_ARG, "paro_apply_h_noalloc: this H psi needs " + std::to_string(need) +
@@ -349,7 +350,7 @@ static int apply_h_noalloc(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* 
   PARO_LAUNCH(c, "k_zpass_fwd");
   if (!c->have_kb) return PARO_OK;
   double2* P = reinterpret_cast<double2*>(base + sticks);
-  float2* wf = reinterpret_cast<float2*>(base + sticks + proj);
+  float2* wf = wconv ? reinterpret_cast<float2*>(base + sticks + proj) : nullptr;
   double2* part = reinterpret_cast<double2*>(base + sticks + proj + wconv);
   const size_t part_elems = (kNoAllocScratchBytes - sticks - proj - wconv) / sizeof(double2);
   if ((st = gemm_cn_scratch<T, T, T>(c, c->nproj, nb, B.npw, beta_of<T>(B), B.npw, psi, B.npw, P, nb, part,

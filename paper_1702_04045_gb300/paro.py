@@ -24,7 +24,8 @@ ENERGY_TERMS = ("kinetic", "nonlocal", "local", "hartree", "xc", "ewald", "total
 
 # Every symbol include/paro.h declares.
 EXPORTS = (
-    "paro_create", "paro_set_local_pp", "paro_set_kb", "paro_set_positions", "paro_set_veff", "paro_get_veff",
+    "paro_create", "paro_set_local_pp", "paro_set_kb", "paro_set_positions", "paro_set_veff", "paro_set_veff_rest",
+    "paro_get_veff",
     "paro_get_vloc", "paro_set_density", "paro_grid", "paro_npw", "paro_miller", "paro_sigma", "paro_apply_h",
     "paro_apply_h_noalloc", "paro_apply_h_adjoint", "paro_orthonormalize", "paro_solve_source", "paro_batch_create", "paro_batch_apply_h",
     "paro_batch_step", "paro_batch_info", "paro_batch_destroy",
@@ -56,6 +57,7 @@ _SIGS = {
     "paro_set_local_pp": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "paro_set_kb": (ctypes.c_int, [_vp, ctypes.c_double, _c_dbl_p]),
     "paro_set_veff": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "paro_set_veff_rest": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "paro_get_veff": (ctypes.c_int, [_vp, _c_dbl_p]),
     "paro_set_density": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "paro_grid": (ctypes.c_int, [_vp, _c_int_p]),
@@ -196,6 +198,15 @@ class Context:
             a = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(-1))
             self._check(self.lib.paro_set_veff(self.h, _vp(a.ctypes.data), 0))
 
+    def set_veff_rest(self, v_rest):
+        """V_eff = V_loc(current positions) + v_rest, formed by the library (host array or CUDA tensor)."""
+        if hasattr(v_rest, "is_cuda") and v_rest.is_cuda:
+            t = v_rest.detach().contiguous().to(self.torch.float64)
+            self._check(self.lib.paro_set_veff_rest(self.h, _vp(t.data_ptr()), 1))
+        else:
+            a = np.ascontiguousarray(np.asarray(v_rest, dtype=np.float64).reshape(-1))
+            self._check(self.lib.paro_set_veff_rest(self.h, _vp(a.ctypes.data), 0))
+
     def get_veff(self):
         out = np.empty(self.grid, dtype=np.float64)
         self._check(self.lib.paro_get_veff(self.h, _dptr(out)))
@@ -238,8 +249,18 @@ class Context:
         return out
 
     def apply_h_noalloc(self, psi, out, ik=0):
-        """H psi into a caller-provided output through the library's allocation-free entry point."""
+        """H psi into a caller-provided output through the library's allocation-free entry point.
+        psi and out: CUDA tensors of the same shape (nb, npw(ik)) and dtype (complex128 or complex64);
+        out must be contiguous (it is written in place)."""
         torch = self.torch
+        if psi.dtype not in (torch.complex128, torch.complex64):
+            raise ParoError(PARO_ERR_ARG, "apply_h_noalloc: psi must be complex128 or complex64")
+        if psi.dim() != 2 or psi.shape[1] != self.npw(ik):
+            raise ParoError(PARO_ERR_ARG, f"apply_h_noalloc: psi must have shape (nb, {self.npw(ik)})")
+        if (not (psi.is_cuda and out.is_cuda) or out.dtype != psi.dtype or tuple(out.shape) != tuple(psi.shape)
+                or not out.is_contiguous() or out.device != psi.device):
+            raise ParoError(PARO_ERR_ARG, "apply_h_noalloc: out must be a contiguous CUDA tensor of psi's shape, "
+                                          "dtype and device")
         dt = PARO_C64 if psi.dtype == torch.complex128 else PARO_C32
         psi = psi.contiguous()
         self._check(self.lib.paro_apply_h_noalloc(self.h, ik, psi.shape[0], dt, _vp(psi.data_ptr()),
@@ -468,8 +489,7 @@ def hpsi(ctx: Context, psi, v_rest, pos, ik=0):
             @staticmethod
             def forward(fctx, psi_, v_rest_, pos_, c, k):
                 c.set_positions(pos_.detach().cpu().numpy())
-                v = torch.from_numpy(c.get_vloc()).to(v_rest_.device) + v_rest_.detach().to(torch.float64)
-                c.set_veff(v.contiguous())
+                c.set_veff_rest(v_rest_)
                 y = c.apply_h(psi_.detach(), ik=k)
                 fctx.save_for_backward(psi_.detach())
                 fctx.c, fctx.k = c, k
