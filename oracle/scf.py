@@ -18,7 +18,13 @@ Readings of points the paper leaves open:
     density of the Cholesky-orthonormalised solutions is mixed into rho_in^{n+1/2}, whose potential
     drives the Rayleigh-Ritz step (Algorithm 1, step 4); rho_in^{n+1} := rho_in^{n+1/2};
   * convergence: |E^{n+1} - E^n| / N_atom below tol on two consecutive iterations;
-  * initial density: uniform N_e / Omega.
+  * initial density: uniform N_e / Omega;
+  * occupations with smearing (kT > 0; the paper is silent, and a cell whose highest occupied and
+    lowest empty levels cross has no fixed point at integer occupations): Fermi-Dirac
+    f_ik = 2 / (1 + exp((eps_ik - mu)/kT)) over all n_bands, mu fixed by sum_k w_k sum_i f_ik = 2 n_occ,
+    and the energy is the Mermin free energy E - T S, S = -sum_k w_k sum_i 2 [g ln g + (1-g) ln(1-g)],
+    g = f/2. Within an iteration the source solutions x_i carry the occupations of the eps_i^n they
+    were solved with; the Rayleigh-Ritz result carries those of its own Ritz values.
 """
 from __future__ import annotations
 
@@ -182,13 +188,43 @@ class Pulay:
 
 
 # ----------------------------------------------------------------------------------------------
+# Fermi-Dirac occupations (fractional occupations for cells without a gap at the Fermi level)
+# ----------------------------------------------------------------------------------------------
+
+def fermi_occupations(eps_list, kw, n_el: float, kT: float):
+    """f_ik = 2 g((eps_ik - mu)/kT), g(x) = 1/(1 + e^x), with mu found by bisection so that
+    sum_k w_k sum_i f_ik = n_el. Returns (list of f arrays, mu, -T S) with the spin-summed entropy
+    S = -sum_k w_k sum_i 2 [g ln g + (1 - g) ln(1 - g)]."""
+    e_all = np.concatenate([np.asarray(e, dtype=np.float64) for e in eps_list])
+    lo, hi = float(e_all.min()) - 40.0 * kT - 1.0, float(e_all.max()) + 40.0 * kT + 1.0
+
+    def count(mu):
+        return sum(w * float(np.sum(2.0 * sps.expit(-(np.asarray(e) - mu) / kT))) for e, w in zip(eps_list, kw))
+
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if count(mid) < n_el:
+            lo = mid
+        else:
+            hi = mid
+    mu = 0.5 * (lo + hi)
+    occ, ts = [], 0.0
+    for e, w in zip(eps_list, kw):
+        g = sps.expit(-(np.asarray(e, dtype=np.float64) - mu) / kT)
+        occ.append(2.0 * g)
+        ent = -(sps.xlogy(g, g) + sps.xlogy(1.0 - g, 1.0 - g))
+        ts += w * 2.0 * kT * float(np.sum(ent))
+    return occ, mu, -ts
+
+
+# ----------------------------------------------------------------------------------------------
 # The SCF system
 # ----------------------------------------------------------------------------------------------
 
 class ScfSystem:
     """Cell, pseudopotentials and bases of one SCF problem (one or more k-points)."""
 
-    def __init__(self, lat, pos, ecut, n_bands, n_occ, pp, dstr=None, kb_rc=1.2, kpts=None, kw=None):
+    def __init__(self, lat, pos, ecut, n_bands, n_occ, pp, dstr=None, kb_rc=1.2, kpts=None, kw=None, kT=0.0):
         self.lat = np.asarray(lat, dtype=np.float64)
         self.pos = np.asarray(pos, dtype=np.float64)
         self.ecut, self.n_bands, self.n_occ = float(ecut), int(n_bands), int(n_occ)
@@ -206,25 +242,43 @@ class ScfSystem:
         self.betas = [pw.kb_beta(self.lat, self.pos, b.q, kb_rc) if dstr is not None else None
                       for b in self.bases]
         self.e_ewald = ewald(self.lat, self.pos, self.pp["Z"])
+        self.kT = float(kT)
+
+    def occupations(self, eps_list):
+        """(occupation array per k, -T S): the lowest n_occ bands doubly occupied when kT = 0, else
+        Fermi-Dirac occupations of the eigenvalues eps_list (one array per k)."""
+        if self.kT <= 0.0:
+            return [self.occ.copy() for _ in self.kpts], 0.0
+        occ, _, mts = fermi_occupations(eps_list, self.kw, self.n_el, self.kT)
+        return occ, mts
 
     def veff(self, rho):
         vh, eh = hartree(self.lat, self.grid, rho)
         exc_d, vxc = lda_pz(rho)
         return self.v_loc + vh + vxc, eh, exc_d
 
-    def density(self, psis):
+    def density(self, psis, occs=None):
+        """rho of the orbitals psis with occupations occs (one array per k; None: fixed occupations)."""
         rho = np.zeros(self.grid)
-        for b, w, psi in zip(self.bases, self.kw, psis):
-            rho += density(b, psi[: self.n_occ], self.occ[: self.n_occ], w)
+        if occs is None:
+            occs = [self.occ] * len(psis)
+        for b, w, psi, f in zip(self.bases, self.kw, psis, occs):
+            n = int(np.count_nonzero(f))
+            if n:
+                rho += density(b, psi[:n], np.asarray(f)[:n], w)
         return rho
 
-    def energy(self, psis):
-        """Total energy of the orbitals psis (one (n_bands, npw) array per k) and their density."""
-        rho = self.density(psis)
+    def energy(self, psis, occs=None, minus_ts=0.0):
+        """Total energy of the orbitals psis (one (n_bands, npw) array per k) with occupations occs
+        (None: fixed) and their density; with smearing the Mermin free energy, its -T S term given."""
+        if occs is None:
+            occs = [self.occ] * len(psis)
+        rho = self.density(psis, occs)
         e_kin = e_nl = 0.0
-        for b, w, psi, beta in zip(self.bases, self.kw, psis, self.betas):
-            po = psi[: self.n_occ]
-            f = self.occ[: self.n_occ]
+        for b, w, psi, beta, fo in zip(self.bases, self.kw, psis, self.betas, occs):
+            n = int(np.count_nonzero(fo))
+            po = psi[:n]
+            f = np.asarray(fo)[:n]
             e_kin += w * float(np.sum(f[:, None] * b.kin[None, :] * np.abs(po) ** 2))
             if beta is not None:
                 proj = np.conj(beta) @ po.T
@@ -235,6 +289,8 @@ class ScfSystem:
         exc_d, _ = lda_pz(rho)
         e_xc = dv * float(np.sum(rho * exc_d))
         terms = {"kinetic": e_kin, "nonlocal": e_nl, "local": e_loc, "hartree": e_h, "xc": e_xc, "ewald": self.e_ewald}
+        if self.kT > 0.0:
+            terms["smearing"] = minus_ts
         terms["total"] = sum(terms.values())
         return terms, rho
 
@@ -248,6 +304,7 @@ def paro_scf(sys: ScfSystem, c0s, tol=1e-8, max_iter=500, eta=paro.INNER_RTOL,
     v, _, _ = sys.veff(rho_in)
     probs = [paro.ParoProblem(b, v, beta, sys.dstr, delta) for b, beta in zip(sys.bases, sys.betas)]
     state = [paro.initial_state(p, c0) for p, c0 in zip(probs, c0s)]
+    occs, _ = sys.occupations([s[0][: sys.n_bands] for s in state])
     e_old = None
     small = 0
     for it in range(1, max_iter + 1):
@@ -264,7 +321,7 @@ def paro_scf(sys: ScfSystem, c0s, tol=1e-8, max_iter=500, eta=paro.INNER_RTOL,
                 keep = np.linalg.norm(e, axis=1) > 1e-10
                 xs.append(paro.cholesky_orthonormalize(np.concatenate([psi, e[keep]], axis=0)))
         # rho_in^{n+1/2} from the new orbitals and the history
-        rho_out = sys.density(xs) if alg == 1 else sys.density([s[1] for s in state])
+        rho_out = sys.density(xs, occs) if alg == 1 else sys.density([s[1] for s in state], occs)
         rho_in = mixer.mix(rho_in, rho_out)
         v, _, _ = sys.veff(rho_in)
         probs = [paro.ParoProblem(b, v, beta, sys.dstr, delta) for b, beta in zip(sys.bases, sys.betas)]
@@ -273,7 +330,8 @@ def paro_scf(sys: ScfSystem, c0s, tol=1e-8, max_iter=500, eta=paro.INNER_RTOL,
         for p, y in zip(probs, xs):
             eps, psi, hpsi = paro.rayleigh_ritz(y, p.h(y))
             state.append((eps[: sys.n_bands], psi[: sys.n_bands], hpsi[: sys.n_bands]))
-        terms, _ = sys.energy([s[1] for s in state])
+        occs, mts = sys.occupations([s[0] for s in state])
+        terms, _ = sys.energy([s[1] for s in state], occs, mts)
         e = terms["total"]
         if log is not None:
             log.append(dict(it=it, energy=e, eta=eta))
@@ -301,7 +359,8 @@ def dense_scf(sys: ScfSystem, tol=1e-8, max_iter=200, pulay_depth=8, pulay_beta=
             eps, vec = np.linalg.eigh(h)
             psis.append(vec[:, : sys.n_bands].T.copy())
             epss.append(eps[: sys.n_bands])
-        terms, rho_out = sys.energy(psis)
+        occs, mts = sys.occupations(epss)
+        terms, rho_out = sys.energy(psis, occs, mts)
         e = terms["total"]
         if e_old is not None and abs(e - e_old) / len(sys.pos) < tol:
             small += 1
