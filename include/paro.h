@@ -52,7 +52,8 @@ enum {
  *             lexicographic Miller order (n1, n2, n3).
  *   k_frac    host double[n_k*3], k in reduced coordinates of the reciprocal lattice (NULL: Gamma only,
  *             n_k must be 1); k_w host double[n_k], weights summing to 1 (NULL: 1/n_k each).
- *   n_bands   orbitals per k (occupied + extra); n_occ the occupied ones (occupation 2 each).
+ *   n_bands   orbitals per k (occupied + extra); n_occ the occupied ones: 2 n_occ electrons, occupation
+ *             2 for each of the lowest n_occ bands, or Fermi-Dirac occupations after paro_set_smearing.
  *   precision PARO_FP64: every step in FP64. PARO_MIXED: orbitals stored in FP32; FFTs, V.psi, the KB
  *             projector products (3xTF32 tensor cores inside the source solves), the inner PCG, the
  *             Cholesky apply and the subspace rotations in FP32; the PCG dot products, the residual
@@ -113,6 +114,21 @@ int paro_get_vloc(paro_ctx* ctx, double* v_r);
  * C order, host or device double[N1*N2*N3]): Hartree V_H(G) = 4 pi rho(G)/G^2 (G != 0), LDA
  * Perdew-Zunger exchange-correlation (Section 2.1, V_H and V_xc). Also becomes the SCF input density. */
 int paro_set_density(paro_ctx* ctx, const double* rho, int on_device);
+
+/*
+ * paro_set_smearing -- occupations of the density and energy (the paper is silent on them; a cell whose
+ * highest occupied and lowest empty levels cross has no SCF fixed point at integer occupations).
+ * kT = 0 (the default): occupation 2 for the lowest n_occ bands of every k-point. kT > 0 (Ha):
+ * Fermi-Dirac occupations of the current Ritz values, f_ik = 2 / (1 + exp((eps_ik - mu)/kT)) over all
+ * n_bands, mu fixed by sum_k w_k sum_i f_ik = 2 n_occ, and PARO_E_TOTAL becomes the Mermin free
+ * energy E - T S with S = -sum_k w_k sum_i 2 [g ln g + (1 - g) ln(1 - g)], g = f/2. In a ParO-SCF
+ * iteration the source solutions carry the occupations of the eigenvalues they were solved with.
+ * Errors: PARO_ERR_ARG for a negative or non-finite kT.
+ * paro_get_occupations -- the occupations of the current orbitals: f host double[n_k * n_bands] (or
+ * NULL), the Fermi level mu (0 without smearing) and the free-energy term -T S (0 without smearing).
+ */
+int paro_set_smearing(paro_ctx* ctx, double kT);
+int paro_get_occupations(paro_ctx* ctx, double* f, double* mu, double* minus_ts);
 
 /* Queries: FFT grid, plane-wave count of k-point ik, Miller indices (host int[npw*3]) of its basis,
  * the PCG shift sigma of the current potential (see paro_solve_source). */
@@ -268,12 +284,14 @@ int paro_step(paro_ctx* ctx, int alg, double rel_tol, int max_it, double* max_re
  */
 int paro_eigh(paro_ctx* ctx, int n, const void* a, double* w, void* v);
 
-/* paro_density -- rho(r) = sum_k w_k sum_{i<n_occ} 2 |psi_ik(r)|^2 of the current orbitals
- * (Section 2.1 and Section 2.2, k-point sum), device double[N1*N2*N3], C order. */
+/* paro_density -- rho(r) = sum_k w_k sum_i f_ik |psi_ik(r)|^2 of the current orbitals (Section 2.1 and
+ * Section 2.2, k-point sum; f_ik = 2 for i < n_occ, or the Fermi-Dirac occupations with smearing),
+ * device double[N1*N2*N3], C order. */
 int paro_density(paro_ctx* ctx, double* rho_dev);
 
 /* paro_energy -- total energy of the current orbitals and their density (terms as PARO_E_*):
- * sum f <psi|T + V_nl|psi> + int V_loc rho + E_H + E_xc + E_Ewald (point ions, neutralising background). */
+ * sum f <psi|T + V_nl|psi> + int V_loc rho + E_H + E_xc + E_Ewald (point ions, neutralising background);
+ * with smearing PARO_E_TOTAL also holds -T S (the Mermin free energy; see paro_get_occupations). */
 int paro_energy(paro_ctx* ctx, double terms[7]);
 
 typedef struct {

@@ -401,6 +401,70 @@ void prof_end(Ctx* c, const char* name, cudaEvent_t a) {
   c->prof_ev.push_back({c->prof_tag ? std::string(c->prof_tag) + ":" + name : std::string(name), a, b});
 }
 
+// Occupations of the current Ritz values. kT = 0: f = 2 for the lowest nocc bands of every k-point.
+// kT > 0 (Fermi-Dirac): mu by bisection on the electron count sum_k w_k sum_i f_ik = 2 nocc, and
+// -T S = -kT sum_k w_k sum_i 2 s(g), s(g) = -(g ln g + (1 - g) ln(1 - g)), g = f/2.
+static double fermi_g(double x) {  // 1 / (1 + e^x) without overflow
+  return x > 0 ? std::exp(-x) / (1.0 + std::exp(-x)) : 1.0 / (1.0 + std::exp(x));
+}
+
+int update_occupations(Ctx* c) {
+  const int nk = c->nk, nb = c->nb;
+  c->occ.assign((size_t)nk * nb, 0.0);
+  if (c->kT <= 0) {
+    for (int ik = 0; ik < nk; ++ik)
+      for (int i = 0; i < c->nocc; ++i) c->occ[(size_t)ik * nb + i] = 2.0;
+    c->nocc_eff = c->nocc;
+    c->mu = 0;
+    c->mts = 0;
+    return PARO_OK;
+  }
+  double lo = 1e300, hi = -1e300;
+  for (int ik = 0; ik < nk; ++ik) {
+    if ((int)c->bases[ik].eps.size() < nb) return fail(c, PARO_ERR_STATE, "occupations: no Ritz values");
+    for (int i = 0; i < nb; ++i) {
+      lo = std::min(lo, c->bases[ik].eps[i]);
+      hi = std::max(hi, c->bases[ik].eps[i]);
+    }
+  }
+  const double kT = c->kT, nel = 2.0 * c->nocc;
+  lo -= 40 * kT + 1;
+  hi += 40 * kT + 1;
+  auto count = [&](double mu) {
+    double n = 0;
+    for (int ik = 0; ik < nk; ++ik)
+      for (int i = 0; i < nb; ++i) n += c->kw[ik] * 2.0 * fermi_g((c->bases[ik].eps[i] - mu) / kT);
+    return n;
+  };
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (count(mid) < nel) lo = mid;
+    else hi = mid;
+  }
+  c->mu = 0.5 * (lo + hi);
+  double ts = 0;
+  int neff = 0;
+  std::vector<double> sq((size_t)nk * nb);
+  for (int ik = 0; ik < nk; ++ik)
+    for (int i = 0; i < nb; ++i) {
+      const double g = fermi_g((c->bases[ik].eps[i] - c->mu) / kT);
+      const size_t o = (size_t)ik * nb + i;
+      c->occ[o] = 2.0 * g;
+      sq[o] = std::sqrt(2.0 * g);
+      if (g > 0) ts -= c->kw[ik] * 2.0 * kT * g * std::log(g);
+      if (g < 1) ts -= c->kw[ik] * 2.0 * kT * (1.0 - g) * std::log1p(-g);
+      if (2.0 * g > 1e-15) neff = std::max(neff, i + 1);
+    }
+  c->mts = -ts;
+  c->nocc_eff = std::max(neff, 1);
+  if (!c->d_occ_sqrt) PARO_CU(c, cudaMalloc(&c->d_occ_sqrt, (size_t)nk * nb * sizeof(double)));
+  PARO_CU(c, cudaMemcpyAsync(c->d_occ_sqrt, sq.data(), sq.size() * sizeof(double), cudaMemcpyHostToDevice,
+                             c->stream));
+  // the host vector is read by the copy engine until the stream reaches it
+  PARO_CU(c, cudaStreamSynchronize(c->stream));
+  return PARO_OK;
+}
+
 static double max_occ_resid(const Ctx* c) {
   double m = 0;
   for (const Basis& b : c->bases)
@@ -518,6 +582,8 @@ static int scf_iteration(Ctx* c, const paro_scf_opts* o) {
   std::vector<cplx<T>*> xs(c->nk), hxs(c->nk, nullptr);
   std::vector<int> nxs(c->nk);
   int st;
+  // the source solutions x_i carry the occupations of the eps_i^n they are solved with
+  if ((st = update_occupations(c))) return st;
   bool carry = false;  // some k-point carries H X this iteration (then dV is needed)
   for (int ik = 0; ik < c->nk; ++ik) {
     xs[ik] = rows_ws<T>(c, "X", ik);
@@ -562,6 +628,8 @@ static int scf_iteration(Ctx* c, const paro_scf_opts* o) {
 
 // density of the current orbitals, in the working precision
 static int current_density(Ctx* c, double* rho) {
+  int st = update_occupations(c);
+  if (st) return st;
   if (c->prec == PARO_MIXED) {
     std::vector<const float2*> ps(c->nk);
     for (int ik = 0; ik < c->nk; ++ik) ps[ik] = c->bases[ik].d_psi32;
@@ -702,7 +770,7 @@ void paro_destroy(paro_ctx* ctx) {
   }
   void* ps[] = {c->d_tw64[0], c->d_tw64[1], c->d_tw64[2], c->d_tw32[0], c->d_tw32[1], c->d_tw32[2],
                 c->d_vloc, c->d_dvec, c->d_dvec32, c->d_veff, c->d_vplane, c->d_vplane32,
-                c->d_rho_in, c->d_pulay_rho, c->d_pulay_res, c->d_pulay_gram, c->d_tc_err};
+                c->d_rho_in, c->d_pulay_rho, c->d_pulay_res, c->d_pulay_gram, c->d_tc_err, c->d_occ_sqrt};
   for (void* p : ps)
     if (p) cudaFree(p);
   for (auto& kv : c->ws) cudaFree(kv.second.first);
@@ -866,6 +934,25 @@ int paro_set_density(paro_ctx* ctx, const double* rho, int on_device) {
   if (st) return st;
   c->have_rho = true;
   update_sigma(c);
+  return PARO_OK;
+}
+
+int paro_set_smearing(paro_ctx* ctx, double kT) {
+  CTX_CHECK(ctx);
+  if (!(kT >= 0) || !std::isfinite(kT)) return fail(c, PARO_ERR_ARG, "paro_set_smearing: kT must be >= 0");
+  c->kT = kT;
+  return PARO_OK;
+}
+
+int paro_get_occupations(paro_ctx* ctx, double* f, double* mu, double* minus_ts) {
+  CTX_CHECK(ctx);
+  for (int ik = 0; ik < c->nk; ++ik)
+    if (!c->bases[ik].have_psi) return fail(c, PARO_ERR_STATE, "no orbitals");
+  int st = update_occupations(c);
+  if (st) return st;
+  if (f) std::copy(c->occ.begin(), c->occ.end(), f);
+  if (mu) *mu = c->mu;
+  if (minus_ts) *minus_ts = c->mts;
   return PARO_OK;
 }
 

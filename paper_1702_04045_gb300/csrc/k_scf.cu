@@ -750,11 +750,26 @@ int density_bands(Ctx* c, int ik, int nbands, const cplx<T>* psi, double wfac, d
   return PARO_OK;
 }
 
-// rho(r) = sum_k w_k 2 sum_{occupied b} |psi_kb(r)|^2 / Omega from orbitals in precision T
+// rho(r) = sum_k w_k sum_b f_kb |psi_kb(r)|^2 / Omega from orbitals in precision T (occupations of the
+// context: f = 2 for the lowest nocc bands, or, with smearing, the rows scaled by sqrt(f_kb) first)
 template <typename T>
 int density(Ctx* c, const cplx<T>* const* psis, double* rho_dev) {
+  if (c->occ.size() != (size_t)c->nk * c->nb) {
+    const int st = update_occupations(c);
+    if (st) return st;
+  }
   for (int ik = 0; ik < c->nk; ++ik) {
-    const int st = density_bands<T>(c, ik, c->nocc, psis[ik], 2.0 * c->kw[ik] / c->omega, rho_dev, ik > 0);
+    int st;
+    if (c->kT > 0) {
+      const int n = c->nocc_eff, npw = c->bases[ik].npw;
+      cplx<T>* y = static_cast<cplx<T>*>(
+          ws_get(c, sizeof(T) == 8 ? "dens_scaled64" : "dens_scaled32", (size_t)n * npw * sizeof(cplx<T>)));
+      if (!y) return PARO_ERR_CUDA;
+      if ((st = scale_rows<T>(c, n, npw, psis[ik], c->d_occ_sqrt + (size_t)ik * c->nb, y))) return st;
+      st = density_bands<T>(c, ik, n, y, c->kw[ik] / c->omega, rho_dev, ik > 0);
+    } else {
+      st = density_bands<T>(c, ik, c->nocc, psis[ik], 2.0 * c->kw[ik] / c->omega, rho_dev, ik > 0);
+    }
     if (st) return st;
   }
   return PARO_OK;
@@ -831,7 +846,12 @@ int energy_terms(Ctx* c, const double* rho_dev, double terms[7]) {
   // every partial sum lands in one buffer, read back with a single synchronisation:
   // [kinetic: nk x nocc x kKch][nonlocal: nk x nocc][V_loc rho, rho eps_xc: 2 x 304][Hartree blocks]
   constexpr int kKch = 4;  // chunks of each row for the kinetic sums (enough CTAs to fill the GPU)
-  const int nblk = 304, nh = hartree_blocks(c), nkb = c->nk * c->nocc, nkk = nkb * kKch;
+  if (c->occ.size() != (size_t)c->nk * c->nb) {
+    const int st = update_occupations(c);
+    if (st) return st;
+  }
+  const int nocc = c->kT > 0 ? c->nocc_eff : c->nocc;  // bands with an occupation
+  const int nblk = 304, nh = hartree_blocks(c), nkb = c->nk * nocc, nkk = nkb * kKch;
   const size_t ntot = (size_t)nkk + nkb + 2 * nblk + nh;
   double* part = static_cast<double*>(ws_get(c, "energy_part", ntot * sizeof(double)));
   double2* z = static_cast<double2*>(ws_get(c, "grid_c0", (size_t)c->ngrid * sizeof(double2)));
@@ -840,11 +860,11 @@ int energy_terms(Ctx* c, const double* rho_dev, double terms[7]) {
   int st;
   for (int ik = 0; ik < c->nk; ++ik) {
     const Basis& B = c->bases[ik];
-    const dim3 gk(c->nocc, kKch);
+    const dim3 gk(nocc, kKch);
     if (c->prec == PARO_MIXED && B.d_psi32)
-      k_kinetic<float><<<gk, 256, 0, c->stream>>>(B.npw, B.d_psi32, B.d_kin32, pk + (size_t)ik * c->nocc * kKch);
+      k_kinetic<float><<<gk, 256, 0, c->stream>>>(B.npw, B.d_psi32, B.d_kin32, pk + (size_t)ik * nocc * kKch);
     else
-      k_kinetic<double><<<gk, 256, 0, c->stream>>>(B.npw, B.d_psi, B.d_kin, pk + (size_t)ik * c->nocc * kKch);
+      k_kinetic<double><<<gk, 256, 0, c->stream>>>(B.npw, B.d_psi, B.d_kin, pk + (size_t)ik * nocc * kKch);
     PARO_LAUNCH(c, "k_kinetic");
     if (c->have_kb) {
       double2* P = static_cast<double2*>(ws_get(c, "kb_proj", (size_t)c->nproj * c->nb * sizeof(double2)));
@@ -852,12 +872,12 @@ int energy_terms(Ctx* c, const double* rho_dev, double terms[7]) {
       // <beta|psi>: FP64 on the FP64 path; the mixed path projects its FP32 orbitals in FP32 (the
       // energy sum itself stays FP64)
       st = c->prec == PARO_MIXED && B.d_psi32
-               ? gemm_cn<float, float, float>(c, c->nproj, c->nocc, B.npw, B.d_beta32, B.npw, B.d_psi32, B.npw, P,
-                                              c->nocc, false)
-               : gemm_cn<double, double, double>(c, c->nproj, c->nocc, B.npw, B.d_beta, B.npw, B.d_psi, B.npw, P,
-                                                 c->nocc, false);
+               ? gemm_cn<float, float, float>(c, c->nproj, nocc, B.npw, B.d_beta32, B.npw, B.d_psi32, B.npw, P,
+                                              nocc, false)
+               : gemm_cn<double, double, double>(c, c->nproj, nocc, B.npw, B.d_beta, B.npw, B.d_psi, B.npw, P,
+                                                 nocc, false);
       if (st) return st;
-      k_nonlocal<<<c->nocc, 256, 0, c->stream>>>(c->nproj, c->nocc, P, c->d_dvec, pn + (size_t)ik * c->nocc);
+      k_nonlocal<<<nocc, 256, 0, c->stream>>>(c->nproj, nocc, P, c->d_dvec, pn + (size_t)ik * nocc);
       PARO_LAUNCH(c, "k_nonlocal");
     }
   }
@@ -872,12 +892,15 @@ int energy_terms(Ctx* c, const double* rho_dev, double terms[7]) {
   PARO_CU(c, cudaStreamSynchronize(c->stream));
   for (int ik = 0; ik < c->nk; ++ik) {
     double sk = 0, sn = 0;
-    for (int b = 0; b < c->nocc; ++b) {
-      for (int ch = 0; ch < kKch; ++ch) sk += h[((size_t)ik * c->nocc + b) * kKch + ch];
-      sn += h[nkk + (size_t)ik * c->nocc + b];
+    for (int b = 0; b < nocc; ++b) {
+      const double f = c->occ[(size_t)ik * c->nb + b];
+      double kb = 0;
+      for (int ch = 0; ch < kKch; ++ch) kb += h[((size_t)ik * nocc + b) * kKch + ch];
+      sk += f * kb;
+      sn += f * h[nkk + (size_t)ik * nocc + b];
     }
-    terms[PARO_E_KINETIC] += 2.0 * c->kw[ik] * sk;
-    if (c->have_kb) terms[PARO_E_NONLOCAL] += 2.0 * c->kw[ik] * sn;
+    terms[PARO_E_KINETIC] += c->kw[ik] * sk;
+    if (c->have_kb) terms[PARO_E_NONLOCAL] += c->kw[ik] * sn;
   }
   double sl = 0, sx = 0, sh = 0;
   for (int i = 0; i < nblk; ++i) {
@@ -890,7 +913,8 @@ int energy_terms(Ctx* c, const double* rho_dev, double terms[7]) {
   terms[PARO_E_XC] = dv * sx;
   terms[PARO_E_HARTREE] = hartree_energy(c, sh);
   terms[PARO_E_EWALD] = c->e_ewald;
-  terms[PARO_E_TOTAL] = terms[0] + terms[1] + terms[2] + terms[3] + terms[4] + terms[5];
+  // with smearing the total is the Mermin free energy E - T S
+  terms[PARO_E_TOTAL] = terms[0] + terms[1] + terms[2] + terms[3] + terms[4] + terms[5] + (c->kT > 0 ? c->mts : 0.0);
   return PARO_OK;
 }
 

@@ -94,6 +94,13 @@ struct Ctx {
   std::vector<int> pulay_slots;    // host source of the slot list copied each mixing step
   double e_prev = 0;
   int scf_iter = 0, scf_small = 0;
+  // occupations: kT = 0, the lowest nocc bands doubly occupied; kT > 0, Fermi-Dirac occupations of the
+  // current Ritz values, 2 / (1 + exp((eps - mu)/kT)) with sum_k w_k sum_i f_ik = 2 nocc, and the Mermin
+  // free energy E - T S (mts = -T S)
+  double kT = 0, mu = 0, mts = 0;
+  std::vector<double> occ;  // nk x nb, f_ik
+  int nocc_eff = 0;         // bands per k from the first up to the last with an occupation above 1e-15
+  double* d_occ_sqrt = nullptr;  // nk x nb, sqrt(f_ik), for the density of smeared orbitals
   bool fft_configured[2] = {false, false};
   // instrumentation: kernels launched, and CUDA-event pairs around named kernels while profiling
   long long launches = 0;
@@ -219,6 +226,10 @@ int convert(Ctx* c, size_t n, const cplx<TS>* src, cplx<TD>* dst);
 // ---- KB projectors (k_hpsi.cu) ----
 template <typename T>
 int kb_apply(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* hpsi);
+
+// ---- occupations (api.cu) ----
+// c->occ, c->nocc_eff, c->mu, c->mts (and d_occ_sqrt with smearing) from the current Ritz values
+int update_occupations(Ctx* c);
 
 // ---- setup / SCF (k_scf.cu) ----
 int build_vloc(Ctx* c);                   // d_vloc from (Z, rc, A, a)

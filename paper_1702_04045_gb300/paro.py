@@ -26,7 +26,7 @@ ENERGY_TERMS = ("kinetic", "nonlocal", "local", "hartree", "xc", "ewald", "total
 EXPORTS = (
     "paro_create", "paro_set_local_pp", "paro_set_kb", "paro_set_positions", "paro_set_veff", "paro_set_veff_rest",
     "paro_get_veff",
-    "paro_get_vloc", "paro_set_density", "paro_grid", "paro_npw", "paro_miller", "paro_sigma", "paro_apply_h",
+    "paro_get_vloc", "paro_set_density", "paro_set_smearing", "paro_get_occupations", "paro_grid", "paro_npw", "paro_miller", "paro_sigma", "paro_apply_h",
     "paro_apply_h_noalloc", "paro_apply_h_adjoint", "paro_orthonormalize", "paro_solve_source", "paro_batch_create", "paro_batch_apply_h",
     "paro_batch_step", "paro_batch_info", "paro_batch_destroy",
     "paro_set_orbitals", "paro_get_orbitals", "paro_get_eigenvalues", "paro_get_residuals", "paro_step",
@@ -60,6 +60,8 @@ _SIGS = {
     "paro_set_veff_rest": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "paro_get_veff": (ctypes.c_int, [_vp, _c_dbl_p]),
     "paro_set_density": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "paro_set_smearing": (ctypes.c_int, [_vp, ctypes.c_double]),
+    "paro_get_occupations": (ctypes.c_int, [_vp, _c_dbl_p, _c_dbl_p, _c_dbl_p]),
     "paro_grid": (ctypes.c_int, [_vp, _c_int_p]),
     "paro_npw": (ctypes.c_int, [_vp, ctypes.c_int, _c_int_p]),
     "paro_miller": (ctypes.c_int, [_vp, ctypes.c_int, _c_int_p]),
@@ -215,6 +217,17 @@ class Context:
     def set_density(self, rho):
         a = np.ascontiguousarray(np.asarray(rho, dtype=np.float64).reshape(-1))
         self._check(self.lib.paro_set_density(self.h, _vp(a.ctypes.data), 0))
+
+    def set_smearing(self, kT):
+        """Fermi-Dirac occupations of width kT (Ha); 0 restores integer occupations of the n_occ lowest bands."""
+        self._check(self.lib.paro_set_smearing(self.h, float(kT)))
+
+    def occupations(self):
+        """(f of shape (n_k, n_bands), mu, -T S) of the current orbitals."""
+        f = np.empty((self.nk, self.n_bands), dtype=np.float64)
+        mu, mts = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.paro_get_occupations(self.h, _dptr(f), ctypes.byref(mu), ctypes.byref(mts)))
+        return f, mu.value, mts.value
 
     @property
     def grid(self):
