@@ -6,8 +6,12 @@ Pulay depth 8), in mixed precision (FP32 FFT / V.psi / PCG / KB projectors, FP64
 Rayleigh-Ritz, residuals and energies), with the plain-FP64 GPU iteration timed beside it.
 
 One step = one ParO-SCF iteration: source problems by batched PCG, Cholesky orthonormalisation,
-density and Pulay mixing, new potential, Rayleigh-Ritz, energy. Every step's working set (orbitals,
-stick buffers, PCG vectors: several hundred MB) exceeds the 129 MB L2, so no flush is needed.
+density and Pulay mixing, new potential, Rayleigh-Ritz, energy. The cell's bands 128 and 129 cross, so
+the SCF uses Fermi-Dirac occupations (kT = 0.002 Ha). The timed iterations are those of the converged
+run: the SCF first iterates from the seeded start vectors until the free energy changes by less than
+1e-6 Ha/atom on two consecutive iterations. The mixed result is then compared with an FP64 run at
+the fixed point, whose converged iteration is timed too. Every step's working set (orbitals, stick
+buffers, PCG vectors: several hundred MB) exceeds the 129 MB L2, so no flush is needed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -52,6 +56,10 @@ def peaks():
 
 # FP64 FMA rate of GB300 (plain ALU; the recipe's 1.25 TFLOP/s, which a probe reproduced).
 FP64_TFLOPS = 1.25
+FP64_SOURCE = "FP64 1.25 TFLOP/s (nominal, the profiling recipe's table)"
+# FP32 FMA rate: nominal 152 SMs x 128 lanes x 2 flops x 2.07 GHz (maximum SM clock) = 80.5 TFLOP/s.
+FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP32_SOURCE = "FP32 nominal: 152 SMs x 128 FMA lanes x 2 x 2070 MHz"
 
 
 class Clocks:
@@ -214,16 +222,53 @@ def hpsi_bytes(s, b):
     return s["nb"] * (3 * s["npw"] * b + 4 * s["ncol"] * s["n3"] * b) + s["ngrid"] * b // 2
 
 
+def _scf_until(ctx, opts, nat, tol, max_it, min_it=2):
+    """SCF steps until |F^{n+1} - F^n| / atom < tol on two consecutive iterations (or max_it); returns
+    (iterations, seconds on the device, last energy terms)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    prev, small, terms = None, 0, None
+    for it in range(1, max_it + 1):
+        terms, _ = ctx.scf_step(opts)
+        e = terms["total"]
+        small = small + 1 if prev is not None and abs(e - prev) / nat < tol else 0
+        prev = e
+        if small >= 2 and it >= min_it:
+            break
+    e1.record()
+    torch.cuda.synchronize()
+    return it, e0.elapsed_time(e1) / 1e3, terms
+
+
+def _timed_steps(ctx, opts, k):
+    """k SCF steps bracketed by CUDA events on torch's current stream (the library's stream): ms, energy."""
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    terms = None
+    for _ in range(k):
+        terms, _ = ctx.scf_step(opts)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), terms
+
+
 def run_ours(args, rank, world, local, pg):
     import torch
     from paper_1702_04045_gb300 import inputs, paro
     torch.cuda.set_device(local)
     lat, pos, d, c = inputs.config_inputs(args.workload)
+    nat = len(pos)
     ctx = paro.context_from_config(args.workload, args.precision)
     nb, npw = c["n_bands"], ctx.npw()
     c0 = inputs.start_vectors(nb, npw, c["seed_psi"] + 7919 * rank)
     ctx.set_orbitals(c0)
     opts = paro.ScfOptions(alg=args.alg, tol_per_atom=0.0, inner_rel_tol=0.25, inner_max_it=8)
+    # 1. converge from the seeded start vectors (|dF|/atom < conv_tol twice); not timed as the metric
+    n_conv, s_conv, _ = _scf_until(ctx, opts, nat, args.conv_tol, args.max_conv_iter)
+    # 2. the metric: K converged iterations after W warm-up iterations, CUDA events, no instrumentation
     for _ in range(args.warmup):
         ctx.scf_step(opts)
     torch.cuda.synchronize()
@@ -231,24 +276,19 @@ def run_ours(args, rank, world, local, pg):
     torch.cuda.synchronize()
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
-    ctx.profile(True)
     l0 = ctx.launch_count()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    energy = None
-    for _ in range(args.steps):
-        energy, resid = ctx.scf_step(opts)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms, terms = _timed_steps(ctx, opts, args.steps)
     launches = ctx.launch_count() - l0
-    prof = {n: ctx.profile_read(n) for n in ctx.profile_names()}
-    ctx.profile(False)
     clk = clocks.stop()
     barrier(pg)
     ms_max = max_over_ranks(pg, ms)
+    # 3. the same iterations once more with the library's per-kernel CUDA events (roofline of each kernel)
+    ctx.profile(True)
+    ms_prof, _ = _timed_steps(ctx, opts, args.steps)
+    prof = {n: ctx.profile_read(n) for n in ctx.profile_names()}
+    ctx.profile(False)
 
-    # end to end through the C ABI with host buffers: restore the state from pinned host memory,
+    # 4. end to end through the C ABI with host buffers: restore the state from pinned host memory,
     # run the iteration, read the energy back
     psi_h = torch.from_numpy(ctx.get_orbitals()).pin_memory()
     eps_h = ctx.eigenvalues()[0].copy()
@@ -261,33 +301,27 @@ def run_ours(args, rank, world, local, pg):
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
 
-    # plain FP64 GPU iteration on the same cell, for the mixed-vs-FP64 speedup
-    fp64 = None
-    if not args.no_fp64 and args.precision != "fp64":
-        ctx64 = paro.context_from_config(args.workload, "fp64")
-        ctx64.set_orbitals(c0)
-        ctx64.scf_step(opts)
-        torch.cuda.synchronize()
-        f0 = time.perf_counter()
-        k64 = max(1, min(2, args.steps))
-        for _ in range(k64):
-            ctx64.scf_step(opts)
-        torch.cuda.synchronize()
-        fp64 = (time.perf_counter() - f0) / k64 * 1e3
-        ctx64.close()
+    # 5. mixed against FP64 at the converged state (rank 0, N = 1): the mixed run goes on to its fixed
+    # point with Algorithm 2 (MParO I, the same fixed point, fewer iterations), an FP64 context starts
+    # from that state and iterates to its own fixed point; per-eigenvalue and per-atom errors of the
+    # mixed result, and the FP64 iteration time at the converged state (CUDA events, nine iterations:
+    # one whole cycle of eight carried and one direct H application)
+    cmp = None
+    if not args.no_fp64 and args.precision != "fp64" and world == 1:
+        cmp = compare_fp64(ctx, args, nat, opts)
 
     s = shapes(ctx)
-    # dominant kernel and its roofline (per launch, CUDA events recorded inside the timed region)
     totals = {n: t for n, (k, t) in prof.items()}
     dom = max(totals, key=totals.get) if totals else None
     hbm, hbm_src = peaks()
+
     def roof_of(cand):
         kind, work = launch_work(cand, s)
         if kind is None:
             return None
         cnt, tot = prof[cand]
         avg_s = tot / cnt / 1e3
-        common = {"kernel": cand, "avg_launch_ms": avg_s * 1e3, "share_of_step": tot / ms,
+        common = {"kernel": cand, "avg_launch_ms": avg_s * 1e3, "share_of_step": tot / ms_prof,
                   "traffic": traffic_of(cand)}
         if kind == "hbm":
             ach = work / avg_s / 1e9
@@ -299,11 +333,10 @@ def run_ours(args, rank, world, local, pg):
             return dict(common, bound="tensor", achieved=ach, peak=tp, unit="TFLOP/s", frac=ach / tp,
                         peak_source=tsrc, flops_per_launch=work,
                         note="3xTF32: three TF32 MMAs per real product; achieved counts all three")
-        peak = FP64_TFLOPS if kind == "alu64" else 67.0  # alu32: FP32 FMA rate of the probe
+        peak = FP64_TFLOPS if kind == "alu64" else FP32_TFLOPS
         ach = work / avg_s / 1e12
         return dict(common, bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
-                    peak_source="FP64 1.25 TFLOP/s (recipe table, reproduced by a probe)" if kind == "alu64"
-                    else "FP32 FMA 67 TFLOP/s (probe)", flops_per_launch=work)
+                    peak_source=FP64_SOURCE if kind == "alu64" else FP32_SOURCE, flops_per_launch=work)
 
     # the dominant kernel: the largest total over all its call sites; its roofline from the call site with
     # a fixed per-launch shape (e.g. the H psi plane pass runs masked to the active orbitals inside the
@@ -316,21 +349,21 @@ def run_ours(args, rank, world, local, pg):
         for _, cand in sorted(by_kernel[kern], reverse=True):
             roof = roof_of(cand)
             if roof:
-                roof["kernel_share_all_sites"] = sum(t for t, _ in by_kernel[kern]) / ms
+                roof["kernel_share_all_sites"] = sum(t for t, _ in by_kernel[kern]) / ms_prof
                 break
         if roof:
             break
-    # the tensor-core projector products of the inner solves (every source column, fixed shape)
     roof_tensor = {k: roof_of(k) for k in ("pcg:k_gemm_cn_tc", "pcg:k_gemm_wx_tc") if k in prof} or None
-    # H psi GB/s over the three full-batch passes of the Rayleigh-Ritz apply
     bsz = 16 if args.precision == "fp64" else 8
-    pas = [f"rr:k_zpass_inv<{'f64' if bsz == 16 else 'f32'}>", f"rr:k_plane<{'f64' if bsz == 16 else 'f32'}>",
-           f"rr:k_zpass_fwd<{'f64' if bsz == 16 else 'f32'}>"]
+    tag = "f64" if bsz == 16 else "f32"
     hpsi = None
-    if all(p in prof for p in pas):
-        t_h = sum(prof[p][1] / prof[p][0] for p in pas) / 1e3
-        hpsi = {"gbs": hpsi_bytes(s, bsz) / t_h / 1e9, "ms_per_batch": t_h * 1e3, "bands": s["nb"],
-                "frac_of_hbm": hpsi_bytes(s, bsz) / t_h / 1e9 / hbm, "bytes_per_batch": hpsi_bytes(s, bsz)}
+    for site in ("rr", "pcg"):
+        pas = [f"{site}:k_zpass_inv<{tag}>", f"{site}:k_plane<{tag}>", f"{site}:k_zpass_fwd<{tag}>"]
+        if site == "rr" and all(p in prof for p in pas):
+            t_h = sum(prof[p][1] / prof[p][0] for p in pas) / 1e3
+            hpsi = {"gbs": hpsi_bytes(s, bsz) / t_h / 1e9, "ms_per_batch": t_h * 1e3, "bands": s["nb"],
+                    "frac_of_hbm": hpsi_bytes(s, bsz) / t_h / 1e9 / hbm, "bytes_per_batch": hpsi_bytes(s, bsz),
+                    "site": "Rayleigh-Ritz apply (all bands)"}
     out = {
         "metric": METRIC, "value": world * args.steps / (ms_max / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -338,23 +371,64 @@ def run_ours(args, rank, world, local, pg):
         "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "precision": args.precision, "algorithm": args.alg,
                    "inner_pcg": "rel_tol 0.25, max 8 steps", "parallelism": f"replicas x{world}",
+                   "state": f"converged: timed after |dF|/atom < {args.conv_tol:g} twice (+{args.warmup} warm-up)",
+                   "smearing_kT_ha": c.get("kT", 0.0),
                    "l2": "working set per iteration > L2 (no flush)"},
         "e2e": {"value": world * args.steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": nb * npw * 16 + nb * 8, "d2h_bytes_per_step": 8 * 8},
         "gpu_launches": launches,
+        "convergence": {"precision": args.precision, "algorithm": args.alg, "tol_per_atom": args.conv_tol,
+                        "iterations": n_conv, "seconds": s_conv, "ms_per_iteration": s_conv / n_conv * 1e3},
         "roofline": roof,
         "roofline_tensor_projector": roof_tensor,
         "hpsi": hpsi,
-        "fp64_ms_per_step": fp64,
-        "speedup_vs_fp64": (fp64 / (ms_max / args.steps)) if fp64 else None,
+        "mixed_vs_fp64": cmp,
+        "fp64_ms_per_step": cmp["fp64_ms_per_step"] if cmp else None,
+        "speedup_vs_fp64": (cmp["fp64_ms_per_step"] / (ms_max / args.steps)) if cmp else None,
         "dominant_kernel": dom,
+        "profiled_ms_per_step": ms_prof / args.steps,
         "kernel_ms": {k: round(v[1], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
         "kernel_calls": {k: v[0] for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
         "clocks": clk,
-        "energy_last_step": energy["total"] if energy else None,
+        "energy_last_step": terms["total"] if terms else None,
     }
     ctx.close()
     return out
+
+
+def compare_fp64(ctx, args, nat, opts):
+    """Mixed vs FP64 at the SCF fixed point of the same cell (see run_ours, step 5)."""
+    import torch
+    from paper_1702_04045_gb300 import paro
+    o2 = paro.ScfOptions(alg=2, tol_per_atom=0.0, inner_rel_tol=0.25, inner_max_it=8)
+    n_mix, s_mix, t_mix = _scf_until(ctx, o2, nat, args.fix_tol, args.max_fix_iter, min_it=5)
+    eps_mix = ctx.eigenvalues()[0]
+    f_mix, mu_mix, _ = ctx.occupations()
+    psi = ctx.get_orbitals(device=True)
+    rho = ctx.density()
+    ctx64 = paro.context_from_config(args.workload, "fp64")
+    ctx64.set_density(rho)
+    ctx64.set_orbitals(psi)
+    n64, s64, t64 = _scf_until(ctx64, o2, nat, args.fix_tol, args.max_fix_iter, min_it=5)
+    eps64 = ctx64.eigenvalues()[0]
+    f64, mu64, _ = ctx64.occupations()
+    occ = f64[0] > 1e-3  # bands that carry charge
+    # orthonormality of the mixed orbitals as stored (FP32 rows widened to FP64)
+    g = psi.conj() @ psi.T
+    orth = float((g - torch.eye(g.shape[0], dtype=g.dtype, device=g.device)).abs().max())
+    # FP64 iteration time at its converged state: one whole 9-iteration cycle of carried / direct H
+    ms64, _ = _timed_steps(ctx64, opts, 9)
+    ctx64.close()
+    return {"reference": "FP64 GPU run from the mixed fixed point to its own (Algorithm 2)",
+            "tol_per_atom": args.fix_tol,
+            "mixed_iterations_alg2": n_mix, "fp64_iterations_alg2": n64,
+            "max_eig_err_occupied_ha": float(np.abs(eps_mix[occ] - eps64[occ]).max()),
+            "e_per_atom_err_ha": abs(t_mix["total"] - t64["total"]) / nat,
+            "fermi_level_err_ha": abs(mu_mix - mu64),
+            "mixed_orthonormality_err": orth,
+            "within_1e-6_ha": bool(np.abs(eps_mix[occ] - eps64[occ]).max() < 1e-6
+                                   and abs(t_mix["total"] - t64["total"]) / nat < 1e-6),
+            "fp64_ms_per_step": ms64 / 9, "fp64_alg": args.alg}
 
 
 def run_adjoint(nb=1088, calls=2):
@@ -386,6 +460,46 @@ def run_adjoint(nb=1088, calls=2):
            "kernel_ms_per_call": {k: round(v[1] / calls, 3) for k, v in top}}
     ctx.close()
     return out
+
+
+def run_hpsi512(nb=1088, calls=3):
+    """Forward H psi batch of the 512-atom cell (137059 plane waves, 128^3 grid, 2048 KB projectors), all
+    1088 bands in FP32 through paro_apply_h: ms per batch with CUDA events, the three FFT passes' share
+    (the library's per-kernel events) and their algorithmic GB/s (3 N_pw b + 4 N_col N_3 b per band, plus V)."""
+    import torch
+    from paper_1702_04045_gb300 import paro
+    ctx = paro.context_from_config("si512", "mixed")
+    npw = ctx.npw()
+    g = torch.Generator(device="cuda").manual_seed(5125)
+    psi = torch.randn((nb, npw), dtype=torch.complex64, device="cuda", generator=g)
+    out = torch.empty_like(psi)
+    ctx.apply_h(psi, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(calls):
+        ctx.apply_h(psi, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / calls
+    ctx.profile(True)
+    for _ in range(calls):
+        ctx.apply_h(psi, out=out)
+    prof = {n: ctx.profile_read(n) for n in ctx.profile_names()}
+    ctx.profile(False)
+    s = shapes(ctx)
+    s["nb"] = nb
+    fft = [k for k in prof if k.startswith(("k_zpass_inv", "k_plane", "k_zpass_fwd"))]
+    t_fft = sum(prof[k][1] for k in fft) / calls / 1e3
+    byt = hpsi_bytes(s, 8)
+    hbm, src = peaks()
+    res = {"workload": "512-atom diamond cell a=41.04 Bohr, Ecut 12 Ha (137059 PW, 128^3 grid), 1088 bands, "
+                       "2048 KB projectors, FP32", "ms_per_batch": ms,
+           "fft_passes_ms": t_fft * 1e3, "fft_passes_gbs": byt / t_fft / 1e9, "fft_passes_frac_of_hbm": byt / t_fft / 1e9 / hbm,
+           "bytes_per_batch": byt, "peak_source": src,
+           "kernel_ms_per_batch": {k: round(v[1] / calls, 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
+    ctx.close()
+    return res
 
 
 def run_batched(name, steps=10, warmup=3, ref_steps=3):
@@ -449,7 +563,8 @@ def cpu_sample(args, steps=1, warmup=0):
     from oracle import scf
     from paper_1702_04045_gb300 import inputs
     lat, pos, d, c = inputs.config_inputs(args.workload)
-    sys_ = scf.ScfSystem(lat, pos, c["ecut"], c["n_bands"], c["n_occ"], inputs.LOCAL_PP, d, inputs.KB_RC)
+    sys_ = scf.ScfSystem(lat, pos, c["ecut"], c["n_bands"], c["n_occ"], inputs.LOCAL_PP, d, inputs.KB_RC,
+                         kT=c.get("kT", 0.0))
     c0 = inputs.start_vectors(c["n_bands"], sys_.bases[0].npw, c["seed_psi"])
     times = []
     for i in range(warmup + steps):
@@ -492,6 +607,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-hpsi512", action="store_true")
+    ap.add_argument("--conv-tol", type=float, default=1e-6, help="|dF|/atom before the timed region")
+    ap.add_argument("--max-conv-iter", type=int, default=4000)
+    ap.add_argument("--fix-tol", type=float, default=1e-9, help="|dF|/atom of the mixed-vs-FP64 fixed points")
+    ap.add_argument("--max-fix-iter", type=int, default=300)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -502,6 +622,8 @@ def main():
             print(json.dumps(out))
         return
     out = run_ours(args, rank, world, local, pg)
+    if rank == 0 and world == 1 and not args.no_hpsi512:
+        out["hpsi_512"] = run_hpsi512()
     if rank == 0 and world == 1 and not args.no_adjoint:
         out["adjoint_512"] = run_adjoint()
     if rank == 0 and world == 1 and not args.no_batched:

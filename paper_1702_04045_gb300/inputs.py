@@ -76,9 +76,10 @@ CONFIGS = {
     # 8-atom cell, local pseudopotential only, fixed potential, FP64.
     "si8_local": dict(n_rep=1, a=10.26, ecut=10.0, n_bands=20, n_occ=16, kb=False,
                       seed_pos=1001, seed_psi=1002, seed_kb=None),
-    # 64-atom cell, local + KB, SCF (LDA, Pulay 8).
+    # 64-atom cell, local + KB, SCF (LDA, Pulay 8). Its bands 128 and 129 are degenerate to ~1e-5 Ha, so
+    # the SCF uses Fermi-Dirac occupations of width kT (Ha) over the 144 bands (256 electrons).
     "si64_scf": dict(n_rep=2, a=10.26, ecut=15.0, n_bands=144, n_occ=128, kb=True,
-                     seed_pos=2001, seed_psi=2002, seed_kb=2003),
+                     seed_pos=2001, seed_psi=2002, seed_kb=2003, kT=0.002),
     # 512-atom cell, local + KB, 1088 orbitals.
     "si512": dict(n_rep=4, a=10.26, ecut=12.0, n_bands=1088, n_occ=1024, kb=True,
                   seed_pos=5001, seed_psi=5002, seed_kb=5003),

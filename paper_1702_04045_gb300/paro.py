@@ -215,8 +215,13 @@ class Context:
         return out
 
     def set_density(self, rho):
-        a = np.ascontiguousarray(np.asarray(rho, dtype=np.float64).reshape(-1))
-        self._check(self.lib.paro_set_density(self.h, _vp(a.ctypes.data), 0))
+        """Input density of the SCF (host array or CUDA tensor, the grid's shape, electrons / Bohr^3)."""
+        if hasattr(rho, "is_cuda") and rho.is_cuda:
+            t = rho.detach().contiguous().to(self.torch.float64)
+            self._check(self.lib.paro_set_density(self.h, _vp(t.data_ptr()), 1))
+        else:
+            a = np.ascontiguousarray(np.asarray(rho, dtype=np.float64).reshape(-1))
+            self._check(self.lib.paro_set_density(self.h, _vp(a.ctypes.data), 0))
 
     def set_smearing(self, kT):
         """Fermi-Dirac occupations of width kT (Ha); 0 restores integer occupations of the n_occ lowest bands."""
@@ -526,4 +531,6 @@ def context_from_config(name: str, precision: str = "fp64", **kw) -> Context:
     ctx.set_local_pp(**inputs.LOCAL_PP)
     if d is not None:
         ctx.set_kb(inputs.KB_RC, d)
+    if c.get("kT"):
+        ctx.set_smearing(c["kT"])
     return ctx

@@ -93,20 +93,20 @@ def test_fp64_scf_fixed_point_matches_dense_oracle_register_grid():
     ctx = _ctx("fp64")
     ctx.set_orbitals(inputs.start_vectors(12, ctx.npw(), 2))
     # eigenvalues follow the density error at first order, the energy at second: iterate until the
-    # energy has stood still to 1e-12 Ha for 20 iterations, not only until the energy criterion first holds
+    # eigenvalues themselves have stood still to 1e-12 Ha for 10 iterations
     opts = paro.ScfOptions(alg=2, tol_per_atom=0.0)
-    e_prev, small = None, 0
-    for it in range(800):
+    eps_prev, small = None, 0
+    for it in range(1500):
         terms, _ = ctx.scf_step(opts)
         e = terms["total"]
-        small = small + 1 if e_prev is not None and abs(e - e_prev) < 1e-12 else 0
-        e_prev = e
-        if small >= 20:
+        eps = ctx.eigenvalues()[0][:8]
+        small = small + 1 if eps_prev is not None and np.abs(eps - eps_prev).max() < 1e-12 else 0
+        eps_prev = eps
+        if small >= 10:
             break
-    eps = ctx.eigenvalues()[0][:8]
     e_err = abs(e - ref["energy"]["total"]) / 8
     eig_err = float(np.abs(eps - np.array(ref["eigenvalues"][:8])).max())
     print(f"FP64 Algorithm 2 SCF, {it + 1} iterations: energy error {e_err:.2e} Ha/atom, "
           f"eigenvalue error {eig_err:.2e} Ha")
-    assert e_err < 1e-9
-    assert eig_err < 1e-7
+    assert e_err < 1e-10
+    assert eig_err < 1e-9
