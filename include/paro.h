@@ -116,6 +116,20 @@ int paro_get_vloc(paro_ctx* ctx, double* v_r);
 int paro_set_density(paro_ctx* ctx, const double* rho, int on_device);
 
 /*
+ * paro_set_ecut -- one step of the cutoff ladder of Algorithm 1 (step 2: raise E_cut^(n) to E_cut^(n+1)
+ * and go on in the larger plane-wave space V_{N_G^{n+1}}, which contains the old one). The basis of every
+ * k-point and the FFT grid are rebuilt for ecut_ha (the rules of paro_create), and with them V_loc and
+ * the KB projectors. The orbitals of the old level are embedded in the new basis (new coefficients zero,
+ * so they stay orthonormal) and keep their eigenvalue estimates; H psi and the residuals are recomputed.
+ * Grid functions are carried to the new grid by Fourier interpolation (their coefficients with
+ * |n_i| < N_i/2 on the old grid are kept, exact for band-limited functions): the SCF input density when
+ * one is set (V_eff is then rebuilt from it and the Pulay history restarts), else the rest V_eff - V_loc
+ * of the set potential. The SCF energy criterion restarts too. ecut_ha below the current cutoff is
+ * PARO_ERR_ARG (the same cutoff is a no-op). A batch that holds the context must be destroyed first.
+ */
+int paro_set_ecut(paro_ctx* ctx, double ecut_ha);
+
+/*
  * paro_set_smearing -- occupations of the density and energy (the paper is silent on them; a cell whose
  * highest occupied and lowest empty levels cross has no SCF fixed point at integer occupations).
  * kT = 0 (the default): occupation 2 for the lowest n_occ bands of every k-point. kT > 0 (Ha):

@@ -295,6 +295,40 @@ class ScfSystem:
         return terms, rho
 
 
+def scf_step(sys: ScfSystem, state, occs, rho_in, mixer, alg=1, eta=paro.INNER_RTOL, max_inner=paro.INNER_MAX_IT,
+             delta=0.5):
+    """One ParO iteration merged with one SCF iteration (Algorithm 1 or 2, Section 2.3) from the state
+    (per k: eps, psi, H psi), its occupations and the input density rho_in. Returns the new state, its
+    occupations, rho_in^{n+1} (= rho_in^{n+1/2}) and the energy terms of the new orbitals."""
+    v, _, _ = sys.veff(rho_in)
+    probs = [paro.ParoProblem(b, v, beta, sys.dstr, delta) for b, beta in zip(sys.bases, sys.betas)]
+    # step 3: source problems with V(rho_in^n)
+    xs = []
+    for p, (eps, psi, hpsi) in zip(probs, state):
+        if alg == 1:
+            x, _ = paro.source_solve(p, psi, eps, eta, max_inner)
+            xs.append(paro.cholesky_orthonormalize(x))
+        else:
+            b = -(hpsi - eps[:, None] * psi)
+            e, _ = paro.pcg(p.a, b, np.zeros_like(psi), p.precond, eta, max_inner)
+            e = e - (e @ np.conj(psi).T) @ psi
+            keep = np.linalg.norm(e, axis=1) > 1e-10
+            xs.append(paro.cholesky_orthonormalize(np.concatenate([psi, e[keep]], axis=0)))
+    # rho_in^{n+1/2} from the new orbitals and the history
+    rho_out = sys.density(xs, occs) if alg == 1 else sys.density([s[1] for s in state], occs)
+    rho_in = mixer.mix(rho_in, rho_out)
+    v, _, _ = sys.veff(rho_in)
+    probs = [paro.ParoProblem(b, v, beta, sys.dstr, delta) for b, beta in zip(sys.bases, sys.betas)]
+    # step 4: Rayleigh-Ritz with V(rho_in^{n+1/2})
+    state = []
+    for p, y in zip(probs, xs):
+        eps, psi, hpsi = paro.rayleigh_ritz(y, p.h(y))
+        state.append((eps[: sys.n_bands], psi[: sys.n_bands], hpsi[: sys.n_bands]))
+    occs, mts = sys.occupations([s[0] for s in state])
+    terms, _ = sys.energy([s[1] for s in state], occs, mts)
+    return state, occs, rho_in, terms
+
+
 def paro_scf(sys: ScfSystem, c0s, tol=1e-8, max_iter=500, eta=paro.INNER_RTOL,
              max_inner=paro.INNER_MAX_IT, delta=0.5,
              pulay_depth=8, pulay_beta=0.7, alg=1, log=None):
@@ -308,33 +342,10 @@ def paro_scf(sys: ScfSystem, c0s, tol=1e-8, max_iter=500, eta=paro.INNER_RTOL,
     e_old = None
     small = 0
     for it in range(1, max_iter + 1):
-        # step 3: source problems with V(rho_in^n)
-        xs = []
-        for p, (eps, psi, hpsi) in zip(probs, state):
-            if alg == 1:
-                x, _ = paro.source_solve(p, psi, eps, eta, max_inner)
-                xs.append(paro.cholesky_orthonormalize(x))
-            else:
-                b = -(hpsi - eps[:, None] * psi)
-                e, _ = paro.pcg(p.a, b, np.zeros_like(psi), p.precond, eta, max_inner)
-                e = e - (e @ np.conj(psi).T) @ psi
-                keep = np.linalg.norm(e, axis=1) > 1e-10
-                xs.append(paro.cholesky_orthonormalize(np.concatenate([psi, e[keep]], axis=0)))
-        # rho_in^{n+1/2} from the new orbitals and the history
-        rho_out = sys.density(xs, occs) if alg == 1 else sys.density([s[1] for s in state], occs)
-        rho_in = mixer.mix(rho_in, rho_out)
-        v, _, _ = sys.veff(rho_in)
-        probs = [paro.ParoProblem(b, v, beta, sys.dstr, delta) for b, beta in zip(sys.bases, sys.betas)]
-        # step 4: Rayleigh-Ritz with V(rho_in^{n+1/2})
-        state = []
-        for p, y in zip(probs, xs):
-            eps, psi, hpsi = paro.rayleigh_ritz(y, p.h(y))
-            state.append((eps[: sys.n_bands], psi[: sys.n_bands], hpsi[: sys.n_bands]))
-        occs, mts = sys.occupations([s[0] for s in state])
-        terms, _ = sys.energy([s[1] for s in state], occs, mts)
+        state, occs, rho_in, terms = scf_step(sys, state, occs, rho_in, mixer, alg, eta, max_inner, delta)
         e = terms["total"]
         if log is not None:
-            log.append(dict(it=it, energy=e, eta=eta))
+            log.append(dict(it=it, energy=e, eta=eta, state=state, rho_in=rho_in))
         if e_old is not None and abs(e - e_old) / len(sys.pos) < tol:
             small += 1
             if small >= 2:

@@ -144,6 +144,75 @@ static int build_basis(Ctx* c, Basis& b) {
   return PARO_OK;
 }
 
+// Every device array of a basis (plane-wave tables, KB projectors, orbitals); the host tables are kept.
+static void free_basis(Basis& b) {
+  void** ps[] = {(void**)&b.d_miller, (void**)&b.d_kin,    (void**)&b.d_kin32,  (void**)&b.d_col_x,
+                 (void**)&b.d_col_y,  (void**)&b.d_col_off, (void**)&b.d_g_col,  (void**)&b.d_g_z,
+                 (void**)&b.d_xrows,  (void**)&b.d_beta,   (void**)&b.d_beta32, (void**)&b.d_prec_base,
+                 (void**)&b.d_psi,    (void**)&b.d_hpsi,   (void**)&b.d_psi32,  (void**)&b.d_hpsi32};
+  for (void** p : ps) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+}
+
+// The plane-wave basis of every k-point for the cutoff c->ecut (Eq. e3) and the FFT grid of the alias-free
+// rule, N_i = smallest 2^a 3^b above m_V,i + s_psi,i (m_V: largest |n_i| of the density sphere
+// |G|^2/2 <= 4 E_cut; s_psi: span of n_i over every k's basis), with the grid's twiddle tables. Earlier
+// bases (their orbitals included) and twiddles are freed; k-points (kfrac, kcart) are kept.
+static int setup_bases(Ctx* c) {
+  const double ecut = c->ecut;
+  int span[3] = {0, 0, 0}, mv[3] = {0, 0, 0};
+  {
+    std::vector<int> mil;
+    std::vector<double> kin;
+    const double zero[3] = {0, 0, 0};
+    sphere(c, zero, 4.0 * ecut, mil, kin);
+    for (size_t g = 0; g < kin.size(); ++g)
+      for (int i = 0; i < 3; ++i) mv[i] = std::max(mv[i], std::abs(mil[3 * g + i]));
+  }
+  for (int ik = 0; ik < c->nk; ++ik) {
+    std::vector<int> mil;
+    std::vector<double> kin;
+    sphere(c, c->bases[ik].kfrac, ecut, mil, kin);
+    if ((int)kin.size() < c->nb) return fail(c, PARO_ERR_ARG, "fewer plane waves than bands");
+    for (int i = 0; i < 3; ++i) {
+      int lo = 1 << 30, hi = -(1 << 30);
+      for (size_t g = 0; g < kin.size(); ++g) {
+        lo = std::min(lo, mil[3 * g + i]);
+        hi = std::max(hi, mil[3 * g + i]);
+      }
+      span[i] = std::max(span[i], hi - lo);
+    }
+  }
+  for (int i = 0; i < 3; ++i) {
+    c->N[i] = smooth23_above(mv[i] + span[i]);
+    c->plan[i] = make_plan(c->N[i]);
+  }
+  c->ngrid = c->N[0] * c->N[1] * c->N[2];
+  c->max_npw = 0;
+  for (int ik = 0; ik < c->nk; ++ik) {
+    Basis& b = c->bases[ik];
+    free_basis(b);
+    b.have_psi = false;
+    b.hx_recur = 0;
+    b.eps.clear();
+    b.res.clear();
+    int st = build_basis(c, b);
+    if (st) return st;
+    c->max_npw = std::max(c->max_npw, b.npw);
+  }
+  for (int ax = 0; ax < 3; ++ax) {
+    if (c->d_tw64[ax]) cudaFree(c->d_tw64[ax]);
+    if (c->d_tw32[ax]) cudaFree(c->d_tw32[ax]);
+    c->d_tw64[ax] = nullptr;
+    c->d_tw32[ax] = nullptr;
+  }
+  int st = build_twiddles(c);
+  if (st) return st;
+  return check_fft_support(c, c->prec == PARO_MIXED ? 8 : 16);
+}
+
 static void update_sigma(Ctx* c) {
   c->sigma_k.assign(c->nk, 0.0);
   for (int ik = 0; ik < c->nk; ++ik) {
@@ -527,6 +596,32 @@ static cplx<T>* rows_ws(Ctx* c, const char* base, int ik) {
   return static_cast<cplx<T>*>(ws_get(c, name.c_str(), (size_t)2 * c->nb * c->bases[ik].npw * sizeof(cplx<T>)));
 }
 
+// Takes the FP64 orbitals in d_psi with the eigenvalue estimates in b.eps as the current state (no
+// orthonormalisation, no Rayleigh-Ritz): the working-precision copy, H psi under the current potential
+// and the residual norms.
+static int adopt_orbitals(Ctx* c, int ik) {
+  Basis& b = c->bases[ik];
+  int st;
+  double* w = static_cast<double*>(ws_get(c, "state_eps", (size_t)c->nb * sizeof(double)));
+  double* res = static_cast<double*>(ws_get(c, "state_res", (size_t)c->nb * sizeof(double)));
+  if (!w || !res) return PARO_ERR_CUDA;
+  PARO_CU(c, cudaMemcpyAsync(w, b.eps.data(), c->nb * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (c->prec == PARO_MIXED) {
+    if ((st = convert<double, float>(c, (size_t)c->nb * b.npw, b.d_psi, b.d_psi32))) return st;
+    if ((st = apply_h<float>(c, ik, c->nb, b.d_psi32, b.d_hpsi32, 0.0, nullptr))) return st;
+    if ((st = convert<float, double>(c, (size_t)c->nb * b.npw, b.d_hpsi32, b.d_hpsi))) return st;
+  } else if ((st = apply_h<double>(c, ik, c->nb, b.d_psi, b.d_hpsi, 0.0, nullptr))) {
+    return st;
+  }
+  if ((st = residual_norms(c, c->nb, b.npw, b.d_psi, b.d_hpsi, w, res))) return st;
+  b.res.resize(c->nb);
+  PARO_CU(c, cudaMemcpyAsync(b.res.data(), res, c->nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PARO_CU(c, cudaStreamSynchronize(c->stream));
+  b.hx_recur = 0;
+  b.have_psi = true;
+  return PARO_OK;
+}
+
 // Rayleigh-Ritz of the span of the current orbitals (after a change of potential or a restart)
 static int reproject(Ctx* c, int ik) {
   Basis& b = c->bases[ik];
@@ -650,6 +745,151 @@ __global__ void k_axpy_grid(int n, double a, const double* __restrict__ x, doubl
   if (i < n) y[i] += a * x[i];
 }
 
+__global__ void k_real_part_api(int n, const double2* __restrict__ z, double* __restrict__ r) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) r[i] = z[i].x;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Cutoff ladder (Algorithm 1 step 2): orbitals embedded in the larger basis, grid functions carried to
+// the new grid by Fourier interpolation
+// ------------------------------------------------------------------------------------------------
+// z = v - vl (vl may be null)
+__global__ void k_rest_complex(int n, const double* __restrict__ v, const double* __restrict__ vl,
+                               double2* __restrict__ z) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[i] = make_double2(v[i] - (vl ? vl[i] : 0.0), 0.0);
+}
+
+// fnew[n mod Nnew] = scale * fold[n mod Nold] for every signed index n with 2 |n_i| < Nold_i (the old
+// grid's Nyquist planes are dropped); fnew is zero elsewhere (cleared by the caller)
+__global__ void k_fourier_carry(int o1, int o2, int o3, int m1, int m2, int m3, const double2* __restrict__ fold,
+                                double2* __restrict__ fnew, double scale) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= o1 * o2 * o3) return;
+  const int j3 = idx % o3, j2 = (idx / o3) % o2, j1 = idx / (o2 * o3);
+  const int n1 = j1 * 2 < o1 ? j1 : j1 - o1, n2 = j2 * 2 < o2 ? j2 : j2 - o2, n3 = j3 * 2 < o3 ? j3 : j3 - o3;
+  if (2 * abs(n1) >= o1 || 2 * abs(n2) >= o2 || 2 * abs(n3) >= o3) return;
+  const int k1 = (n1 + m1) % m1, k2 = (n2 + m2) % m2, k3 = (n3 + m3) % m3;
+  const double2 v = fold[idx];
+  fnew[((size_t)k1 * m2 + k2) * m3 + k3] = make_double2(v.x * scale, v.y * scale);
+}
+
+// row b of the larger basis: dst[b][map[g]] = src[b][g] (the other coefficients were cleared)
+__global__ void k_prolong(int npw_old, int npw_new, const int* __restrict__ map, const double2* __restrict__ src,
+                          double2* __restrict__ dst) {
+  const int b = blockIdx.y;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < npw_old; g += gridDim.x * blockDim.x)
+    dst[(size_t)b * npw_new + map[g]] = src[(size_t)b * npw_old + g];
+}
+
+static int set_ecut(Ctx* c, double ecut_new) {
+  int st;
+  const int o[3] = {c->N[0], c->N[1], c->N[2]};
+  const int ngold = c->ngrid;
+  // 1. the carried grid function's Fourier coefficients on the old grid: the SCF input density, or the
+  //    rest V_eff - V_loc of a set potential
+  const bool carry_rho = c->have_rho && c->d_rho_in;
+  const bool carry_rest = !carry_rho && c->have_veff;
+  double2* fold = nullptr;
+  if (carry_rho || carry_rest) {
+    PARO_CU(c, cudaMalloc(&fold, (size_t)ngold * sizeof(double2)));
+    k_rest_complex<<<(ngold + 255) / 256, 256, 0, c->stream>>>(ngold, carry_rho ? c->d_rho_in : c->d_veff,
+                                                              carry_rest && c->have_pp ? c->d_vloc : nullptr, fold);
+    PARO_LAUNCH(c, "k_rest_complex");
+    if ((st = fft3d<double>(c, fold, false))) return st;
+  }
+  // 2. the old level's orbitals (FP64), Miller lists and eigenvalue estimates
+  std::vector<double2*> old_psi(c->nk, nullptr);
+  std::vector<std::vector<int>> old_mil(c->nk);
+  std::vector<std::vector<double>> old_eps(c->nk);
+  std::vector<int> old_npw(c->nk);
+  for (int ik = 0; ik < c->nk; ++ik) {
+    Basis& b = c->bases[ik];
+    if (!b.have_psi) continue;
+    old_psi[ik] = b.d_psi;
+    b.d_psi = nullptr;
+    old_mil[ik] = b.miller;
+    old_eps[ik] = b.eps;
+    old_npw[ik] = b.npw;
+  }
+  // 3. everything sized by the grid or the basis is rebuilt
+  PARO_CU(c, cudaStreamSynchronize(c->stream));
+  for (auto& kv : c->ws) cudaFree(kv.second.first);
+  c->ws.clear();
+  double** grid_bufs[] = {&c->d_vloc, &c->d_veff, &c->d_vplane, &c->d_rho_in, &c->d_pulay_rho, &c->d_pulay_res};
+  for (double** p : grid_bufs) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  if (c->d_vplane32) cudaFree(c->d_vplane32);
+  c->d_vplane32 = nullptr;
+  c->pulay_n = c->pulay_head = 0;
+  c->have_inv_g2 = false;
+  c->have_veff = false;
+  c->ecut = ecut_new;
+  c->scf_iter = c->scf_small = 0;
+  if ((st = setup_bases(c))) return st;
+  if (c->have_pp && (st = build_vloc(c))) return st;
+  if (c->have_kb && (st = build_beta(c))) return st;
+  // 4. the carried function on the new grid: f(j') = sum_n F(n) exp(2 pi i n.j'/N'), F = fold / N_old
+  if (fold) {
+    double2* fnew = static_cast<double2*>(ws_get(c, "grid_c0", (size_t)c->ngrid * sizeof(double2)));
+    double* fr = static_cast<double*>(ws_get(c, "grid_r1", (size_t)c->ngrid * sizeof(double)));
+    if (!fnew || !fr) return PARO_ERR_CUDA;
+    PARO_CU(c, cudaMemsetAsync(fnew, 0, (size_t)c->ngrid * sizeof(double2), c->stream));
+    k_fourier_carry<<<(ngold + 255) / 256, 256, 0, c->stream>>>(o[0], o[1], o[2], c->N[0], c->N[1], c->N[2], fold,
+                                                               fnew, 1.0 / ngold);
+    PARO_LAUNCH(c, "k_fourier_carry");
+    if ((st = fft3d<double>(c, fnew, true))) return st;
+    k_real_part_api<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, fnew, fr);
+    PARO_LAUNCH(c, "k_real_part");
+    PARO_CU(c, cudaStreamSynchronize(c->stream));
+    cudaFree(fold);
+    if (carry_rho) {
+      PARO_CU(c, cudaMalloc(&c->d_rho_in, (size_t)c->ngrid * sizeof(double)));
+      PARO_CU(c, cudaMemcpyAsync(c->d_rho_in, fr, (size_t)c->ngrid * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 c->stream));
+      if ((st = veff_from_density(c, c->d_rho_in, nullptr, nullptr))) return st;
+    } else {
+      if (c->have_pp) {
+        k_axpy_grid<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, 1.0, c->d_vloc, fr);
+        PARO_LAUNCH(c, "k_axpy_grid");
+      }
+      if ((st = set_veff_device(c, fr))) return st;
+    }
+    update_sigma(c);
+  }
+  // 5. the orbitals embedded in the new bases, eigenvalue estimates kept
+  for (int ik = 0; ik < c->nk; ++ik) {
+    if (!old_psi[ik]) continue;
+    Basis& b = c->bases[ik];
+    std::map<long long, int> where;
+    auto key = [](int a, int bb, int cc) { return ((long long)(a + 4096) * 8192 + (bb + 4096)) * 8192 + (cc + 4096); };
+    for (int g = 0; g < b.npw; ++g) where[key(b.miller[3 * g], b.miller[3 * g + 1], b.miller[3 * g + 2])] = g;
+    std::vector<int> map(old_npw[ik]);
+    for (int g = 0; g < old_npw[ik]; ++g) {
+      auto it = where.find(key(old_mil[ik][3 * g], old_mil[ik][3 * g + 1], old_mil[ik][3 * g + 2]));
+      if (it == where.end()) return fail(c, PARO_ERR_STATE, "paro_set_ecut: old basis not inside the new one");
+      map[g] = it->second;
+    }
+    int* dmap = static_cast<int*>(ws_get(c, "prolong_map", (size_t)old_npw[ik] * sizeof(int)));
+    if (!dmap) return PARO_ERR_CUDA;
+    if ((st = alloc_orbitals(c, b))) return st;
+    PARO_CU(c, cudaMemcpyAsync(dmap, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    PARO_CU(c, cudaMemsetAsync(b.d_psi, 0, (size_t)c->nb * b.npw * sizeof(double2), c->stream));
+    k_prolong<<<dim3((old_npw[ik] + 255) / 256, c->nb), 256, 0, c->stream>>>(old_npw[ik], b.npw, dmap, old_psi[ik],
+                                                                           b.d_psi);
+    PARO_LAUNCH(c, "k_prolong");
+    PARO_CU(c, cudaStreamSynchronize(c->stream));
+    cudaFree(old_psi[ik]);
+    old_psi[ik] = nullptr;
+    b.eps = old_eps[ik];
+    if (c->have_veff && (st = adopt_orbitals(c, ik))) return st;
+  }
+  return PARO_OK;
+}
+
 // ================================================================================================
 // C ABI
 // ================================================================================================
@@ -710,49 +950,18 @@ int paro_create(paro_ctx** out, const double lattice[9], int n_atoms, const doub
   }
   c->stream = static_cast<cudaStream_t>(stream);  // NULL: the default stream
   c->own_stream = false;
-  // bases and the FFT grid: N_i = smallest 2^a 3^b above m_V,i + s_psi,i
+  // bases and the FFT grid of the cutoff
   c->bases.resize(n_k);
-  int span[3] = {0, 0, 0}, mv[3] = {0, 0, 0};
-  {
-    std::vector<int> mil;
-    std::vector<double> kin;
-    const double zero[3] = {0, 0, 0};
-    sphere(c, zero, 4.0 * ecut_ha, mil, kin);
-    for (size_t g = 0; g < kin.size(); ++g)
-      for (int i = 0; i < 3; ++i) mv[i] = std::max(mv[i], std::abs(mil[3 * g + i]));
-  }
   for (int ik = 0; ik < n_k; ++ik) {
     Basis& b = c->bases[ik];
     for (int i = 0; i < 3; ++i) b.kfrac[i] = k_frac ? k_frac[3 * ik + i] : 0.0;
     for (int x = 0; x < 3; ++x)
       b.kcart[x] = b.kfrac[0] * c->bmat[x] + b.kfrac[1] * c->bmat[3 + x] + b.kfrac[2] * c->bmat[6 + x];
-    std::vector<int> mil;
-    std::vector<double> kin;
-    sphere(c, b.kfrac, ecut_ha, mil, kin);
-    if ((int)kin.size() < n_bands) {
-      c->err = "paro_create: fewer plane waves than bands";
-      return bail(PARO_ERR_ARG);
-    }
-    for (int i = 0; i < 3; ++i) {
-      int lo = 1 << 30, hi = -(1 << 30);
-      for (size_t g = 0; g < kin.size(); ++g) {
-        lo = std::min(lo, mil[3 * g + i]);
-        hi = std::max(hi, mil[3 * g + i]);
-      }
-      span[i] = std::max(span[i], hi - lo);
-    }
   }
-  for (int i = 0; i < 3; ++i) {
-    c->N[i] = smooth23_above(mv[i] + span[i]);
-    c->plan[i] = make_plan(c->N[i]);
+  if (int st = setup_bases(c)) {
+    c->err = "paro_create: " + (c->err.empty() ? std::string("basis setup failed") : c->err);
+    return bail(st);
   }
-  c->ngrid = c->N[0] * c->N[1] * c->N[2];
-  for (int ik = 0; ik < n_k; ++ik) {
-    if (build_basis(c, c->bases[ik])) return bail(PARO_ERR_CUDA);
-    c->max_npw = std::max(c->max_npw, c->bases[ik].npw);
-  }
-  if (build_twiddles(c)) return bail(PARO_ERR_CUDA);
-  if (check_fft_support(c, precision == PARO_MIXED ? 8 : 16)) return bail(PARO_ERR_ARG);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(PARO_ERR_CUDA);
   *out = ctx;
   return PARO_OK;
@@ -762,12 +971,7 @@ void paro_destroy(paro_ctx* ctx) {
   if (!ctx) return;
   Ctx* c = &ctx->c;
   if (c->stream) cudaStreamSynchronize(c->stream);
-  for (Basis& b : c->bases) {
-    void* ps[] = {b.d_miller, b.d_kin, b.d_kin32, b.d_col_x, b.d_col_y, b.d_col_off, b.d_g_col, b.d_g_z,
-                  b.d_xrows, b.d_beta, b.d_beta32, b.d_prec_base, b.d_psi, b.d_hpsi, b.d_psi32, b.d_hpsi32};
-    for (void* p : ps)
-      if (p) cudaFree(p);
-  }
+  for (Basis& b : c->bases) free_basis(b);
   void* ps[] = {c->d_tw64[0], c->d_tw64[1], c->d_tw64[2], c->d_tw32[0], c->d_tw32[1], c->d_tw32[2],
                 c->d_vloc, c->d_dvec, c->d_dvec32, c->d_veff, c->d_vplane, c->d_vplane32,
                 c->d_rho_in, c->d_pulay_rho, c->d_pulay_res, c->d_pulay_gram, c->d_tc_err, c->d_occ_sqrt};
@@ -935,6 +1139,17 @@ int paro_set_density(paro_ctx* ctx, const double* rho, int on_device) {
   c->have_rho = true;
   update_sigma(c);
   return PARO_OK;
+}
+
+int paro_set_ecut(paro_ctx* ctx, double ecut_ha) {
+  CTX_CHECK(ctx);
+  if (!std::isfinite(ecut_ha) || ecut_ha < c->ecut)
+    return fail(c, PARO_ERR_ARG, "paro_set_ecut: the cutoff ladder only raises E_cut");
+  if (ecut_ha == c->ecut) return PARO_OK;
+  const double old = c->ecut;
+  int st = set_ecut(c, ecut_ha);
+  if (st && c->ecut != old && c->err.empty()) c->err = "paro_set_ecut failed";
+  return st;
 }
 
 int paro_set_smearing(paro_ctx* ctx, double kT) {
@@ -1159,23 +1374,7 @@ int paro_set_state(paro_ctx* ctx, int ik, const void* psi, const double* eps, in
   PARO_CU(c, cudaMemcpyAsync(b.d_psi, psi, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                              c->stream));
   b.eps.assign(eps, eps + c->nb);
-  double* w = static_cast<double*>(ws_get(c, "state_eps", (size_t)c->nb * sizeof(double)));
-  double* res = static_cast<double*>(ws_get(c, "state_res", (size_t)c->nb * sizeof(double)));
-  if (!w || !res) return PARO_ERR_CUDA;
-  PARO_CU(c, cudaMemcpyAsync(w, b.eps.data(), c->nb * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  if (c->prec == PARO_MIXED) {
-    if ((st = convert<double, float>(c, (size_t)c->nb * b.npw, b.d_psi, b.d_psi32))) return st;
-    if ((st = apply_h<float>(c, ik, c->nb, b.d_psi32, b.d_hpsi32, 0.0, nullptr))) return st;
-    if ((st = convert<float, double>(c, (size_t)c->nb * b.npw, b.d_hpsi32, b.d_hpsi))) return st;
-  } else if ((st = apply_h<double>(c, ik, c->nb, b.d_psi, b.d_hpsi, 0.0, nullptr))) {
-    return st;
-  }
-  if ((st = residual_norms(c, c->nb, b.npw, b.d_psi, b.d_hpsi, w, res))) return st;
-  b.res.resize(c->nb);
-  PARO_CU(c, cudaMemcpyAsync(b.res.data(), res, c->nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  PARO_CU(c, cudaStreamSynchronize(c->stream));
-  b.have_psi = true;
-  return PARO_OK;
+  return adopt_orbitals(c, ik);
 }
 
 int paro_profile(paro_ctx* ctx, int enable) {
