@@ -13,6 +13,13 @@ Readings of points the paper leaves open:
     x = psi_i (Algorithm 1) or e = 0 (Algorithm 2), stopped once its residual has dropped by a
     factor tol or after max_it steps (the paper only asks for the source problems to be solved).
   * Orthonormality (Algorithm 1 step 4) is imposed by Cholesky of the Gram matrix in band order.
+  * Algorithm 3 (MParO II), step 3: the projected correction equation
+    (I - P_i)(H - lambda_i)(I - P_i) e_i = (eps_i - H) psi_i, P_i = |psi_i><psi_i|, with lambda_i^n,
+    which the paper never defines, read as eps_i^n. The operator is Hermitian and indefinite on the
+    complement of psi_i, so it is solved there by preconditioned MINRES (Paige and Saunders), with
+    the projected preconditioner (I - P_i) D (I - P_i), D the PCG preconditioner (positive definite on
+    that complement), started at e = 0 and stopped like the PCG (residual estimate reduced by tol, or
+    max_it steps). The Rayleigh-Ritz step then works as in Algorithm 2.
 """
 from __future__ import annotations
 
@@ -154,6 +161,88 @@ def paro_step_alg2(prob: ParoProblem, psi, hpsi, eps, tol, max_it, drop=1e-10):
     return eps2[:nb], psi2[:nb], hpsi2[:nb], its
 
 
+def minres(apply_a, b, apply_minv, tol, max_it):
+    """Preconditioned MINRES, one independent Hermitian system A_i e_i = b_i per row of b, started at 0,
+    with a Hermitian positive definite preconditioner M^{-1} (apply_minv). Lanczos in the M^{-1} inner
+    product, the tridiagonal reduced by Givens rotations; eta_i estimates ||b_i - A_i e_i||_{M^{-1}}.
+    Row i stops once |eta_i| <= tol |eta_i^0| or after max_it steps. Returns (e, steps per row)."""
+    b = b.astype(np.complex128)
+    n = b.shape[0]
+    x = np.zeros_like(b)
+    v_old = np.zeros_like(b)
+    v = b.copy()
+    z = apply_minv(v)
+    gamma = np.sqrt(np.maximum(np.real(np.sum(np.conj(z) * v, axis=1)), 0.0))
+    gamma_old = np.ones(n)
+    eta = gamma.copy()
+    eta0 = gamma.copy()
+    c_old, c = np.ones(n), np.ones(n)
+    s_old, s = np.zeros(n), np.zeros(n)
+    w_old = np.zeros_like(b)
+    w = np.zeros_like(b)
+    active = gamma > 0.0
+    its = np.zeros(n, dtype=np.int64)
+    for _ in range(max_it):
+        if not np.any(active):
+            break
+        g = np.where(active, gamma, 1.0)
+        zn = z / g[:, None]
+        az = apply_a(zn)
+        delta = np.real(np.sum(np.conj(az) * zn, axis=1))
+        v_new = az - (delta / g)[:, None] * v - (g / gamma_old)[:, None] * v_old
+        z_new = apply_minv(v_new)
+        gamma_new = np.sqrt(np.maximum(np.real(np.sum(np.conj(z_new) * v_new, axis=1)), 0.0))
+        a0 = c * delta - c_old * s * g
+        a1 = np.sqrt(a0 * a0 + gamma_new * gamma_new)
+        a2 = s * delta + c_old * c * g
+        a3 = s_old * g
+        a1s = np.where(a1 > 0.0, a1, 1.0)
+        c_new, s_new = a0 / a1s, gamma_new / a1s
+        w_new = (zn - a3[:, None] * w_old - a2[:, None] * w) / a1s[:, None]
+        upd = active[:, None]
+        x = np.where(upd, x + (c_new * eta)[:, None] * w_new, x)
+        eta_new = -s_new * eta
+        # advance the recurrences of the active rows
+        v_old, v = np.where(upd, v, v_old), np.where(upd, v_new, v)
+        z = np.where(upd, z_new, z)
+        w_old, w = np.where(upd, w, w_old), np.where(upd, w_new, w)
+        gamma_old, gamma = np.where(active, g, gamma_old), np.where(active, gamma_new, gamma)
+        c_old, c = np.where(active, c, c_old), np.where(active, c_new, c)
+        s_old, s = np.where(active, s, s_old), np.where(active, s_new, s)
+        eta = np.where(active, eta_new, eta)
+        its += active
+        active = active & (np.abs(eta) > tol * eta0) & (gamma > 0.0)
+    return x, its
+
+
+def correction_alg3(prob: "ParoProblem", psi, hpsi, eps, tol, max_it):
+    """Algorithm 3 step 3 for every orbital: (I - P_i)(H - eps_i)(I - P_i) e_i = -(H psi_i - eps_i psi_i)
+    on the complement of psi_i, by preconditioned MINRES with M^{-1} = (I - P_i) D (I - P_i)."""
+    def proj(v):
+        return v - np.sum(np.conj(psi) * v, axis=1)[:, None] * psi
+
+    def apply_a(v):
+        pv = proj(v)
+        return proj(prob.h(pv) - eps[:, None] * pv)
+
+    def apply_minv(v):
+        return proj(prob.precond[None, :] * proj(v))
+
+    return minres(apply_a, proj(-(hpsi - eps[:, None] * psi)), apply_minv, tol, max_it)
+
+
+def paro_step_alg3(prob: "ParoProblem", psi, hpsi, eps, tol, max_it, drop=1e-10):
+    """One iteration of Algorithm 3 (MParO II): the projected corrections e_i (correction_alg3), then
+    Rayleigh-Ritz in span{psi, e} exactly as in Algorithm 2. Returns the lowest N Ritz pairs."""
+    nb = psi.shape[0]
+    e, its = correction_alg3(prob, psi, hpsi, eps, tol, max_it)
+    e = e - (e @ np.conj(psi).T) @ psi               # out of span{psi} (each e_i is already out of psi_i)
+    keep = np.linalg.norm(e, axis=1) > drop
+    y = cholesky_orthonormalize(np.concatenate([psi, e[keep]], axis=0))
+    eps3, psi3, hpsi3 = rayleigh_ritz(y, prob.h(y))
+    return eps3[:nb], psi3[:nb], hpsi3[:nb], its
+
+
 # Inexact inner solves: each PCG reduces its own residual by INNER_RTOL, in at most INNER_MAX_IT
 # steps. More inner work barely changes the outer rate, which is that of subspace inverse iteration.
 INNER_RTOL = 0.25
@@ -162,7 +251,7 @@ INNER_MAX_IT = 8
 
 def paro_fixed_potential(prob: ParoProblem, c0, n_occ, tol=1e-8, max_iter=2000,
                          eta=INNER_RTOL, max_inner=INNER_MAX_IT, alg=1):
-    """Iterate Algorithm 1 (or 2) at a fixed potential until max_{i<n_occ} ||H psi_i - eps_i psi_i|| < tol."""
+    """Iterate Algorithm 1 (2, 3) at a fixed potential until max_{i<n_occ} ||H psi_i - eps_i psi_i|| < tol."""
     eps, psi, hpsi = initial_state(prob, c0)
     res = residuals(psi, hpsi, eps)
     hist = []
@@ -171,8 +260,10 @@ def paro_fixed_potential(prob: ParoProblem, c0, n_occ, tol=1e-8, max_iter=2000,
             return eps, psi, res, it, hist
         if alg == 1:
             eps, psi, hpsi, _ = paro_step_alg1(prob, psi, eps, eta, max_inner)
-        else:
+        elif alg == 2:
             eps, psi, hpsi, _ = paro_step_alg2(prob, psi, hpsi, eps, eta, max_inner)
+        else:
+            eps, psi, hpsi, _ = paro_step_alg3(prob, psi, hpsi, eps, eta, max_inner)
         res = residuals(psi, hpsi, eps)
         hist.append(float(np.max(res[:n_occ])))
     raise RuntimeError("ParO did not converge")

@@ -297,7 +297,7 @@ class ScfSystem:
 
 def scf_step(sys: ScfSystem, state, occs, rho_in, mixer, alg=1, eta=paro.INNER_RTOL, max_inner=paro.INNER_MAX_IT,
              delta=0.5):
-    """One ParO iteration merged with one SCF iteration (Algorithm 1 or 2, Section 2.3) from the state
+    """One ParO iteration merged with one SCF iteration (Algorithm 1, 2 or 3, Section 2.3) from the state
     (per k: eps, psi, H psi), its occupations and the input density rho_in. Returns the new state, its
     occupations, rho_in^{n+1} (= rho_in^{n+1/2}) and the energy terms of the new orbitals."""
     v, _, _ = sys.veff(rho_in)
@@ -309,8 +309,11 @@ def scf_step(sys: ScfSystem, state, occs, rho_in, mixer, alg=1, eta=paro.INNER_R
             x, _ = paro.source_solve(p, psi, eps, eta, max_inner)
             xs.append(paro.cholesky_orthonormalize(x))
         else:
-            b = -(hpsi - eps[:, None] * psi)
-            e, _ = paro.pcg(p.a, b, np.zeros_like(psi), p.precond, eta, max_inner)
+            if alg == 2:
+                b = -(hpsi - eps[:, None] * psi)
+                e, _ = paro.pcg(p.a, b, np.zeros_like(psi), p.precond, eta, max_inner)
+            else:
+                e, _ = paro.correction_alg3(p, psi, hpsi, eps, eta, max_inner)
             e = e - (e @ np.conj(psi).T) @ psi
             keep = np.linalg.norm(e, axis=1) > 1e-10
             xs.append(paro.cholesky_orthonormalize(np.concatenate([psi, e[keep]], axis=0)))
@@ -332,7 +335,8 @@ def scf_step(sys: ScfSystem, state, occs, rho_in, mixer, alg=1, eta=paro.INNER_R
 def paro_scf(sys: ScfSystem, c0s, tol=1e-8, max_iter=500, eta=paro.INNER_RTOL,
              max_inner=paro.INNER_MAX_IT, delta=0.5,
              pulay_depth=8, pulay_beta=0.7, alg=1, log=None):
-    """ParO merged with SCF (Algorithm 1; Algorithm 2 with alg=2). Returns (energy terms, eps, psis, n_iter)."""
+    """ParO merged with SCF (Algorithm 1; Algorithms 2 and 3 with alg=2, 3). Returns (energy terms, eps, psis,
+    n_iter)."""
     rho_in = np.full(sys.grid, sys.n_el / sys.omega)
     mixer = Pulay(pulay_depth, pulay_beta)
     v, _, _ = sys.veff(rho_in)
