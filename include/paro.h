@@ -35,7 +35,7 @@ typedef enum {
 } paro_status;
 
 typedef enum { PARO_FP64 = 0, PARO_MIXED = 1 } paro_precision;
-typedef enum { PARO_ALG1 = 1, PARO_ALG2 = 2 } paro_algorithm;
+typedef enum { PARO_ALG1 = 1, PARO_ALG2 = 2, PARO_ALG3 = 3 } paro_algorithm;
 typedef enum { PARO_C64 = 0, PARO_C32 = 1 } paro_dtype; /* complex double / complex float */
 
 /* Energy terms reported by paro_energy / paro_scf (Ha): indices into a double[7]. */
@@ -282,6 +282,11 @@ int paro_get_residuals(paro_ctx* ctx, double* res);
  *     orthonormalisation of X, Rayleigh-Ritz in span{x_i}: H_sub = X^H H X, H_sub C = C diag(eps).
  *   PARO_ALG2 (Algorithm 2): corrections (H - sigma) e_i = -(H psi_i - eps_i psi_i) started at e = 0,
  *     projected out of span{psi}; Rayleigh-Ritz in span{psi, e} (dimension up to 2 n_bands).
+ *   PARO_ALG3 (Algorithm 3): projected corrections (I - P_i)(H - lambda_i)(I - P_i) e_i = (eps_i - H) psi_i,
+ *     P_i = |psi_i><psi_i|, lambda_i (undefined in the paper) read as eps_i; the operator is Hermitian
+ *     and indefinite on the complement of psi_i, so each is solved there by preconditioned MINRES from
+ *     e = 0 with the projected preconditioner (I - P_i) D (I - P_i), D the PCG preconditioner; then the
+ *     Rayleigh-Ritz step of Algorithm 2. rel_tol bounds the MINRES residual estimate's reduction.
  *   rel_tol, max_it: inner PCG stopping rule (see paro_solve_source).
  *   max_resid_out: host, max over k and occupied bands of ||H psi_i - eps_i psi_i|| after the step.
  */
@@ -309,7 +314,7 @@ int paro_density(paro_ctx* ctx, double* rho_dev);
 int paro_energy(paro_ctx* ctx, double terms[7]);
 
 typedef struct {
-  int alg;                 /* PARO_ALG1 or PARO_ALG2 */
+  int alg;                 /* PARO_ALG1, PARO_ALG2 or PARO_ALG3 */
   double tol_per_atom;     /* stop when |E^{n+1} - E^n| / n_atoms < tol on two consecutive iterations */
   int max_iter;            /* ParO/SCF iterations */
   double inner_rel_tol;    /* PCG residual reduction per source problem */

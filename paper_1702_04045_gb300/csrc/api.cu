@@ -548,14 +548,18 @@ static int source_step(Ctx* c, int ik, int alg, double rel_tol, int max_it, cplx
                        cplx<T>* HX = nullptr);
 template <typename T>
 static int source_step(Ctx* c, int ik, int alg, double rel_tol, int max_it, cplx<T>* X, int* nx, cplx<T>* HX) {
-  const bool alg2 = alg == PARO_ALG2;
+  const bool alg2 = alg == PARO_ALG2 || alg == PARO_ALG3;
   const int npw = c->bases[ik].npw;
   cplx<T>* E = X;
   if (alg2) {
     E = static_cast<cplx<T>*>(ws_get(c, wsn(sizeof(T) == 8, "alg2_E64", "alg2_E32"), (size_t)c->nb * npw * sizeof(cplx<T>)));
     if (!E) return PARO_ERR_CUDA;
   }
-  int st = solve_sources<T>(c, ik, alg2, rel_tol, max_it, E, alg2 ? nullptr : HX);
+  // Algorithm 3: the projected correction equations with lambda_i = eps_i, by batched MINRES
+  Basis& b = c->bases[ik];
+  int st = alg == PARO_ALG3
+               ? minres_run<T>(c, ik, c->nb, psi_of<T>(b), hpsi_of<T>(b), b.eps.data(), E, rel_tol, max_it, nullptr)
+               : solve_sources<T>(c, ik, alg2, rel_tol, max_it, E, alg2 ? nullptr : HX);
   if (st) return st;
   if (!alg2) {
     *nx = c->nb;
@@ -703,7 +707,7 @@ static int scf_iteration(Ctx* c, const paro_scf_opts* o) {
   double* rho_out = static_cast<double*>(ws_get(c, "scf_rho_out", (size_t)c->ngrid * sizeof(double)));
   if (!rho_out) return PARO_ERR_CUDA;
   std::vector<const cplx<T>*> dens_src(c->nk);
-  for (int ik = 0; ik < c->nk; ++ik) dens_src[ik] = o->alg == PARO_ALG1 ? xs[ik] : psi_of<T>(c->bases[ik]);
+  for (int ik = 0; ik < c->nk; ++ik) dens_src[ik] = o->alg == PARO_ALG1 ? xs[ik] : psi_of<T>(c->bases[ik]);  // 2, 3
   {
     ProfTag t(c, "mix");
     if ((st = density<T>(c, dens_src.data(), rho_out))) return st;
@@ -1281,7 +1285,8 @@ int paro_get_residuals(paro_ctx* ctx, double* res) {
 
 int paro_step(paro_ctx* ctx, int alg, double rel_tol, int max_it, double* max_resid_out) {
   CTX_CHECK(ctx);
-  if ((alg != PARO_ALG1 && alg != PARO_ALG2) || max_it < 0) return fail(c, PARO_ERR_ARG, "paro_step: bad argument");
+  if ((alg != PARO_ALG1 && alg != PARO_ALG2 && alg != PARO_ALG3) || max_it < 0)
+    return fail(c, PARO_ERR_ARG, "paro_step: bad argument");
   for (int ik = 0; ik < c->nk; ++ik) {
     if (!c->bases[ik].have_psi) return fail(c, PARO_ERR_STATE, "paro_step: orbitals not set");
     int st = c->prec == PARO_MIXED ? paro_step_k<float>(c, ik, alg, rel_tol, max_it)
@@ -1325,7 +1330,8 @@ __global__ void k_fill(int n, double v, double* __restrict__ x) {
 
 int paro_scf_step(paro_ctx* ctx, const paro_scf_opts* o, double energy[7], double* max_resid_out) {
   CTX_CHECK(ctx);
-  if (!o || (o->alg != PARO_ALG1 && o->alg != PARO_ALG2)) return fail(c, PARO_ERR_ARG, "paro_scf_step: bad options");
+  if (!o || (o->alg != PARO_ALG1 && o->alg != PARO_ALG2 && o->alg != PARO_ALG3))
+    return fail(c, PARO_ERR_ARG, "paro_scf_step: bad options");
   if (!c->have_pp) return fail(c, PARO_ERR_STATE, "no local pseudopotential");
   for (int ik = 0; ik < c->nk; ++ik)
     if (!c->bases[ik].have_psi) return fail(c, PARO_ERR_STATE, "orbitals not set");

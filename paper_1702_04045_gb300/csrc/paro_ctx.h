@@ -269,4 +269,11 @@ int pcg_run(Ctx* c, int ik, int nb, const cplx<T>* rhs, cplx<T>* x, bool x0_zero
 template <typename T>
 int scale_rows(Ctx* c, int nb, int npw, const cplx<T>* x, const double* f_dev, cplx<T>* y);
 
+// ---- batched preconditioned MINRES for the projected correction equations of Algorithm 3 (k_minres.cu) ----
+// e_b ~ solution of (I - P_b)(H - eps_b)(I - P_b) e_b = -(H psi_b - eps_b psi_b) on the complement of psi_b;
+// eps host double[nb]; iters (host, may be null) receives the steps per orbital.
+template <typename T>
+int minres_run(Ctx* c, int ik, int nb, const cplx<T>* psi, const cplx<T>* hpsi, const double* eps, cplx<T>* e,
+               double rel_tol, int max_it, int* iters);
+
 }  // namespace paro

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libparo.so")
 PARO_OK, PARO_ERR_ARG, PARO_ERR_CUDA, PARO_ERR_BREAKDOWN, PARO_ERR_NOT_CONVERGED, PARO_ERR_STATE = 0, -1, -2, -3, -4, -6
 PARO_FP64, PARO_MIXED = 0, 1
 PARO_C64, PARO_C32 = 0, 1
-PARO_ALG1, PARO_ALG2 = 1, 2
+PARO_ALG1, PARO_ALG2, PARO_ALG3 = 1, 2, 3
 ENERGY_TERMS = ("kinetic", "nonlocal", "local", "hartree", "xc", "ewald", "total")
 
 # Every symbol include/paro.h declares.
