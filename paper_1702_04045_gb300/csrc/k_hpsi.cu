@@ -270,7 +270,10 @@ int kb_apply(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* hpsi) {
   const Basis& B = c->bases[ik];
   double2* P = static_cast<double2*>(ws_get(c, "kb_proj", (size_t)c->nproj * nb * sizeof(double2)));
   if (!P) return PARO_ERR_CUDA;
-  int st = gemm_cn<T, T, T>(c, c->nproj, nb, B.npw, beta_of<T>(B), B.npw, psi, B.npw, P, nb, false);
+  // FP32 projections outside the inexact inner solves carry their sums in a two-sum pair: a long FP32
+  // accumulation biases |<beta|psi>|^2 (and with it the Rayleigh-Ritz H and the energy) at the 1e-6 level
+  const bool carry = sizeof(T) == 4 && !c->tc_scope;
+  int st = gemm_cn<T, T, T>(c, c->nproj, nb, B.npw, beta_of<T>(B), B.npw, psi, B.npw, P, nb, false, carry);
   if (st) return st;
   // W(k = p, m = b) = D_p P[p][b]
   return gemm_wx<T, T>(c, nb, B.npw, c->nproj, P, nb, false, c->d_dvec, beta_of<T>(B), B.npw, hpsi, B.npw, 1.0);

@@ -869,11 +869,11 @@ int energy_terms(Ctx* c, const double* rho_dev, double terms[7]) {
     if (c->have_kb) {
       double2* P = static_cast<double2*>(ws_get(c, "kb_proj", (size_t)c->nproj * c->nb * sizeof(double2)));
       if (!P) return PARO_ERR_CUDA;
-      // <beta|psi>: FP64 on the FP64 path; the mixed path projects its FP32 orbitals in FP32 (the
-      // energy sum itself stays FP64)
+      // <beta|psi>: FP64 on the FP64 path; the mixed path projects its FP32 orbitals in FP32 with the
+      // sums carried in a two-sum pair (the energy sum itself stays FP64)
       st = c->prec == PARO_MIXED && B.d_psi32
                ? gemm_cn<float, float, float>(c, c->nproj, nocc, B.npw, B.d_beta32, B.npw, B.d_psi32, B.npw, P,
-                                              nocc, false)
+                                              nocc, false, true)
                : gemm_cn<double, double, double>(c, c->nproj, nocc, B.npw, B.d_beta, B.npw, B.d_psi, B.npw, P,
                                                  nocc, false);
       if (st) return st;
@@ -881,10 +881,9 @@ int energy_terms(Ctx* c, const double* rho_dev, double terms[7]) {
       PARO_LAUNCH(c, "k_nonlocal");
     }
   }
-  if (c->prec == PARO_MIXED)  // eps_xc per point in FP32, the sums in FP64
-    k_grid_energies<float><<<nblk, 256, 0, c->stream>>>(c->ngrid, c->d_vloc, rho_dev, pg);
-  else
-    k_grid_energies<double><<<nblk, 256, 0, c->stream>>>(c->ngrid, c->d_vloc, rho_dev, pg);
+  // eps_xc per point in FP64 on both paths (an FP32 evaluation shifts E_xc of the 64-atom cell by ~1e-5 Ha;
+  // one pass over the grid, a few tens of microseconds in FP64)
+  k_grid_energies<double><<<nblk, 256, 0, c->stream>>>(c->ngrid, c->d_vloc, rho_dev, pg);
   PARO_LAUNCH(c, "k_grid_energies");
   if ((st = hartree_g(c, rho_dev, z, ph, false))) return st;
   std::vector<double> h(ntot);
