@@ -750,27 +750,73 @@ int density_bands(Ctx* c, int ik, int nbands, const cplx<T>* psi, double wfac, d
   return PARO_OK;
 }
 
+// per-block partial sums of a grid function (fixed chunks, summed on the host in order)
+__global__ void k_grid_sum(int n, const double* __restrict__ x, double* __restrict__ part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += x[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_grid_scale(int n, double a, double* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] *= a;
+}
+
 // rho(r) = sum_k w_k sum_b f_kb |psi_kb(r)|^2 / Omega from orbitals in precision T (occupations of the
-// context: f = 2 for the lowest nocc bands, or, with smearing, the rows scaled by sqrt(f_kb) first)
+// context: f = 2 for the lowest nocc bands, or, with smearing, the rows scaled by sqrt(f_kb) first).
+// FP32 orbitals: the FP32 transforms' gain (rounded twiddles, FP32 butterflies) biases the density's scale
+// by ~1e-7, which the SCF fixed point amplifies; the exact discrete Parseval identity
+// (Omega/N) sum_r rho(r) = sum_k w_k sum_b f_kb ||c_kb||^2 restores its normalisation (the norms summed in
+// FP64 from the same FP32 rows).
 template <typename T>
 int density(Ctx* c, const cplx<T>* const* psis, double* rho_dev) {
   if (c->occ.size() != (size_t)c->nk * c->nb) {
     const int st = update_occupations(c);
     if (st) return st;
   }
+  const bool renorm = sizeof(T) == 4;
+  const int nrow = c->kT > 0 ? c->nocc_eff : c->nocc;
+  double* norms = renorm ? static_cast<double*>(ws_get(c, "dens_norms", (size_t)c->nk * c->nb * sizeof(double)))
+                         : nullptr;
+  if (renorm && !norms) return PARO_ERR_CUDA;
   for (int ik = 0; ik < c->nk; ++ik) {
     int st;
+    const int npw = c->bases[ik].npw;
+    const cplx<T>* rows = psis[ik];
     if (c->kT > 0) {
-      const int n = c->nocc_eff, npw = c->bases[ik].npw;
       cplx<T>* y = static_cast<cplx<T>*>(
-          ws_get(c, sizeof(T) == 8 ? "dens_scaled64" : "dens_scaled32", (size_t)n * npw * sizeof(cplx<T>)));
+          ws_get(c, sizeof(T) == 8 ? "dens_scaled64" : "dens_scaled32", (size_t)nrow * npw * sizeof(cplx<T>)));
       if (!y) return PARO_ERR_CUDA;
-      if ((st = scale_rows<T>(c, n, npw, psis[ik], c->d_occ_sqrt + (size_t)ik * c->nb, y))) return st;
-      st = density_bands<T>(c, ik, n, y, c->kw[ik] / c->omega, rho_dev, ik > 0);
+      if ((st = scale_rows<T>(c, nrow, npw, psis[ik], c->d_occ_sqrt + (size_t)ik * c->nb, y))) return st;
+      rows = y;
+      st = density_bands<T>(c, ik, nrow, y, c->kw[ik] / c->omega, rho_dev, ik > 0);
     } else {
-      st = density_bands<T>(c, ik, c->nocc, psis[ik], 2.0 * c->kw[ik] / c->omega, rho_dev, ik > 0);
+      st = density_bands<T>(c, ik, nrow, psis[ik], 2.0 * c->kw[ik] / c->omega, rho_dev, ik > 0);
     }
     if (st) return st;
+    if (renorm && (st = band_norms<T>(c, nrow, npw, rows, npw, norms + (size_t)ik * c->nb))) return st;
+  }
+  if (!renorm) return PARO_OK;
+  const int nblk = 304;
+  double* part = static_cast<double*>(ws_get(c, "dens_sum_part", nblk * sizeof(double)));
+  if (!part) return PARO_ERR_CUDA;
+  k_grid_sum<<<nblk, 256, 0, c->stream>>>(c->ngrid, rho_dev, part);
+  PARO_LAUNCH(c, "k_grid_sum");
+  std::vector<double> hp(nblk), hn((size_t)c->nk * c->nb);
+  PARO_CU(c, cudaMemcpyAsync(hp.data(), part, nblk * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PARO_CU(c, cudaMemcpyAsync(hn.data(), norms, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PARO_CU(c, cudaStreamSynchronize(c->stream));
+  double total = 0.0, target = 0.0;
+  for (int i = 0; i < nblk; ++i) total += hp[i];
+  total *= c->omega / c->ngrid;
+  for (int ik = 0; ik < c->nk; ++ik)
+    for (int b = 0; b < nrow; ++b)  // smeared rows already carry sqrt(f) in their norms
+      target += c->kw[ik] * (c->kT > 0 ? 1.0 : 2.0) * hn[(size_t)ik * c->nb + b];
+  if (total > 0.0 && target > 0.0) {
+    k_grid_scale<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, target / total, rho_dev);
+    PARO_LAUNCH(c, "k_grid_scale");
   }
   return PARO_OK;
 }
