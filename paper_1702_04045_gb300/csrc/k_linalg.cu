@@ -1051,9 +1051,15 @@ __global__ void k_band_norm2(int npw, const cplx<T>* __restrict__ x, int ldx, do
   const int b = blockIdx.x;
   const cplx<T>* xb = x + (size_t)b * ldx;
   double acc = 0.0;
-  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
-    const double re = xb[g].x, im = xb[g].y;
-    acc += re * re + im * im;
+  if constexpr (sizeof(T) == 4) {  // FP32 rows: FP32 squares (exact enough) in an FP32 two-sum pair
+    float hi = 0.f, lo = 0.f;
+    for (int g = threadIdx.x; g < npw; g += blockDim.x) two_sum_acc(hi, lo, fmaf(xb[g].x, xb[g].x, xb[g].y * xb[g].y));
+    acc = (double)hi + (double)lo;
+  } else {
+    for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+      const double re = xb[g].x, im = xb[g].y;
+      acc += re * re + im * im;
+    }
   }
   acc = block_sum(acc, red);
   if (threadIdx.x == 0) out[b] = acc;

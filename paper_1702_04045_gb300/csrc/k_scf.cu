@@ -759,9 +759,27 @@ __global__ void k_grid_sum(int n, const double* __restrict__ x, double* __restri
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-__global__ void k_grid_scale(int n, double a, double* __restrict__ x) {
+// a = target / total with total = (Omega/N) sum of the grid partials and target = sum_k w_k fac sum_b
+// norms[k][b] (one warp, fixed order); the scale stays on the device
+__global__ void k_renorm_scalar(int nblk, const double* __restrict__ part, int nk, int nb, int nrow,
+                                const double* __restrict__ wk, double fac, const double* __restrict__ norms,
+                                double dv, double* __restrict__ a) {
+  const int lane = threadIdx.x;
+  double t = 0.0, g = 0.0;
+  for (int i = lane; i < nblk; i += 32) t += part[i];
+  for (int k = 0; k < nk; ++k)
+    for (int b = lane; b < nrow; b += 32) g += wk[k] * fac * norms[(size_t)k * nb + b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    t += __shfl_xor_sync(0xffffffffu, t, o);
+    g += __shfl_xor_sync(0xffffffffu, g, o);
+  }
+  if (lane == 0) *a = (t > 0.0 && g > 0.0) ? g / (t * dv) : 1.0;
+}
+
+__global__ void k_grid_scale(int n, const double* __restrict__ a, double* __restrict__ x) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) x[i] *= a;
+  if (i < n) x[i] *= *a;
 }
 
 // rho(r) = sum_k w_k sum_b f_kb |psi_kb(r)|^2 / Omega from orbitals in precision T (occupations of the
@@ -800,24 +818,18 @@ int density(Ctx* c, const cplx<T>* const* psis, double* rho_dev) {
   }
   if (!renorm) return PARO_OK;
   const int nblk = 304;
-  double* part = static_cast<double*>(ws_get(c, "dens_sum_part", nblk * sizeof(double)));
-  if (!part) return PARO_ERR_CUDA;
+  double* part = static_cast<double*>(ws_get(c, "dens_sum_part", (nblk + 1) * sizeof(double)));
+  double* wk = static_cast<double*>(ws_get(c, "dens_kw", (size_t)c->nk * sizeof(double)));
+  if (!part || !wk) return PARO_ERR_CUDA;
+  PARO_CU(c, cudaMemcpyAsync(wk, c->kw.data(), c->nk * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   k_grid_sum<<<nblk, 256, 0, c->stream>>>(c->ngrid, rho_dev, part);
   PARO_LAUNCH(c, "k_grid_sum");
-  std::vector<double> hp(nblk), hn((size_t)c->nk * c->nb);
-  PARO_CU(c, cudaMemcpyAsync(hp.data(), part, nblk * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  PARO_CU(c, cudaMemcpyAsync(hn.data(), norms, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  PARO_CU(c, cudaStreamSynchronize(c->stream));
-  double total = 0.0, target = 0.0;
-  for (int i = 0; i < nblk; ++i) total += hp[i];
-  total *= c->omega / c->ngrid;
-  for (int ik = 0; ik < c->nk; ++ik)
-    for (int b = 0; b < nrow; ++b)  // smeared rows already carry sqrt(f) in their norms
-      target += c->kw[ik] * (c->kT > 0 ? 1.0 : 2.0) * hn[(size_t)ik * c->nb + b];
-  if (total > 0.0 && target > 0.0) {
-    k_grid_scale<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, target / total, rho_dev);
-    PARO_LAUNCH(c, "k_grid_scale");
-  }
+  // smeared rows already carry sqrt(f) in their norms; otherwise f = 2
+  k_renorm_scalar<<<1, 32, 0, c->stream>>>(nblk, part, c->nk, c->nb, nrow, wk, c->kT > 0 ? 1.0 : 2.0, norms,
+                                           c->omega / c->ngrid, part + nblk);
+  PARO_LAUNCH(c, "k_renorm_scalar");
+  k_grid_scale<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, part + nblk, rho_dev);
+  PARO_LAUNCH(c, "k_grid_scale");
   return PARO_OK;
 }
 
