@@ -130,6 +130,23 @@ int paro_set_density(paro_ctx* ctx, const double* rho, int on_device);
 int paro_set_ecut(paro_ctx* ctx, double ecut_ha);
 
 /*
+ * paro_set_gamma_real -- the Gamma-point real-wavefunction mode (not in the paper; the standard companion of
+ * a plane-wave method at k = 0), for contexts whose only k-point is Gamma. V_eff(r) and the KB projectors
+ * are real there, so H maps real orbitals (coefficients with c(-G) = conj(c(G))) to real ones, and the
+ * ParO iteration of the context (paro_step, paro_scf_step, paro_scf) then carries two real orbitals in one
+ * complex row phi = a + i b: H phi = H a + i H b is split as (H a)(G) = [y(G) + conj(y(-G))]/2,
+ * (H b)(G) = [y(G) - conj(y(-G))]/(2i), and |phi(r)|^2 = a(r)^2 + b(r)^2 gives two orbitals' density per
+ * transform, which halves the FFT and projector work of H psi and of the density. The Gram and
+ * Rayleigh-Ritz matrices are real symmetric (imaginary parts dropped) and orbitals are kept real: orbitals
+ * given to paro_set_orbitals / paro_set_state are replaced by their real part (coefficients
+ * [c(G) + conj(c(-G))]/2), and enabling the mode does the same to the current orbitals and re-takes their
+ * Ritz pairs. Calls on general complex vectors (paro_apply_h, paro_apply_h_adjoint, paro_solve_source,
+ * paro_orthonormalize) keep the complex path. enable = 0 leaves the mode. PARO_ERR_ARG for a k-point other
+ * than Gamma; batches do not take contexts in this mode.
+ */
+int paro_set_gamma_real(paro_ctx* ctx, int enable);
+
+/*
  * paro_set_smearing -- occupations of the density and energy (the paper is silent on them; a cell whose
  * highest occupied and lowest empty levels cross has no SCF fixed point at integer occupations).
  * kT = 0 (the default): occupation 2 for the lowest n_occ bands of every k-point. kT > 0 (Ha):

@@ -149,6 +149,7 @@ static void free_basis(Basis& b) {
   void** ps[] = {(void**)&b.d_miller, (void**)&b.d_kin,    (void**)&b.d_kin32,  (void**)&b.d_col_x,
                  (void**)&b.d_col_y,  (void**)&b.d_col_off, (void**)&b.d_g_col,  (void**)&b.d_g_z,
                  (void**)&b.d_xrows,  (void**)&b.d_beta,   (void**)&b.d_beta32, (void**)&b.d_prec_base,
+                 (void**)&b.d_mg,
                  (void**)&b.d_psi,    (void**)&b.d_hpsi,   (void**)&b.d_psi32,  (void**)&b.d_hpsi32};
   for (void** p : ps) {
     if (*p) cudaFree(*p);
@@ -294,6 +295,7 @@ static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal, cplx<T>
     {
       ProfTag t(c, "gram");
       if ((st = gemm_cn<T, T, T>(c, nx, nx, npw, X, npw, X, npw, S, nx, true, true))) return st;
+      if (gamma_on(c) && (st = gamma_real_matrix(c, nx, S))) return st;  // real orbitals: real Gram
       if ((st = chol_inv(c, nx, S, G))) return st;
     }
     ProfTag t(c, "orth");
@@ -316,6 +318,7 @@ static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal, cplx<T>
   {
     ProfTag t(c, "hsub");
     if ((st = gemm_cn<T, T, T>(c, nx, nx, npw, Y, npw, HY, npw, S, nx, true, true))) return st;
+    if (gamma_on(c) && (st = gamma_real_matrix(c, nx, S))) return st;  // real orbitals: real symmetric H_sub
     k_hermitize<<<(nx * nx + 255) / 256, 256, 0, c->stream>>>(nx, S);
     PARO_LAUNCH(c, "k_hermitize");
     // mixed: one refinement step (FP64 Ritz values, vectors well below the FP32 level of the orbitals)
@@ -325,6 +328,10 @@ static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal, cplx<T>
     ProfTag t(c, "rot");
     if ((st = gemm_wx<T, T>(c, nb, npw, nx, G, nx, false, nullptr, Y, npw, psi_of<T>(b), npw, 0.0))) return st;
     if ((st = gemm_wx<T, T>(c, nb, npw, nx, G, nx, false, nullptr, HY, npw, hpsi_of<T>(b), npw, 0.0))) return st;
+    if (gamma_on(c)) {  // real orbitals stay real (the rotation's rounding may not keep c(-G) = conj c(G))
+      if ((st = gamma_real_rows<T>(c, ik, nb, psi_of<T>(b))) || (st = gamma_real_rows<T>(c, ik, nb, hpsi_of<T>(b))))
+        return st;
+    }
   }
   if (!f64) {
     if ((st = convert<float, double>(c, (size_t)nb * npw, b.d_psi32, b.d_psi))) return st;
@@ -421,6 +428,7 @@ static int build_alg2_basis(Ctx* c, int ik, cplx<T>* E, cplx<T>* X, int* nx_out)
   int st;
   // P[i][j] = <psi_i, e_j>;  e_j -= sum_i psi_i P[i][j]
   if ((st = gemm_cn<T, T, T>(c, nb, nb, npw, psi, npw, E, npw, P, nb, false, true))) return st;
+  if (gamma_on(c) && (st = gamma_real_matrix(c, nb, P))) return st;
   if ((st = gemm_wx<T, T>(c, nb, npw, nb, P, nb, false, nullptr, psi, npw, tmp, npw, 0.0))) return st;
   k_axpy_rows<T><<<dim3((npw + 255) / 256, nb), 256, 0, c->stream>>>(npw, E, tmp, (T)-1);
   PARO_LAUNCH(c, "k_axpy_rows");
@@ -581,6 +589,7 @@ static int orthonormalize(Ctx* c, int ik, cplx<T>* X, int nx, cplx<T>* HX = null
   {
     ProfTag t(c, "gram");
     if ((st = gemm_cn<T, T, T>(c, nx, nx, npw, X, npw, X, npw, S, nx, true, true))) return st;
+    if (gamma_on(c) && (st = gamma_real_matrix(c, nx, S))) return st;
     if ((st = chol_inv(c, nx, S, G))) return st;
   }
   ProfTag t(c, "orth");
@@ -834,6 +843,7 @@ static int set_ecut(Ctx* c, double ecut_new) {
   c->ecut = ecut_new;
   c->scf_iter = c->scf_small = 0;
   if ((st = setup_bases(c))) return st;
+  if (c->gamma_real && (st = gamma_build_table(c, 0))) return st;
   if (c->have_pp && (st = build_vloc(c))) return st;
   if (c->have_kb && (st = build_beta(c))) return st;
   // 4. the carried function on the new grid: f(j') = sum_n F(n) exp(2 pi i n.j'/N'), F = fold / N_old
@@ -1156,6 +1166,25 @@ int paro_set_ecut(paro_ctx* ctx, double ecut_ha) {
   return st;
 }
 
+int paro_set_gamma_real(paro_ctx* ctx, int enable) {
+  CTX_CHECK(ctx);
+  if (!enable) {
+    c->gamma_real = false;
+    return PARO_OK;
+  }
+  const Basis& b0 = c->bases[0];
+  if (c->nk != 1 || b0.kfrac[0] != 0 || b0.kfrac[1] != 0 || b0.kfrac[2] != 0)
+    return fail(c, PARO_ERR_ARG, "paro_set_gamma_real: the real-wavefunction mode needs the Gamma point only");
+  int st = gamma_build_table(c, 0);
+  if (st) return st;
+  c->gamma_real = true;
+  if (c->bases[0].have_psi) {  // the current orbitals become real and take their Ritz pairs again
+    if ((st = gamma_real_rows<double>(c, 0, c->nb, c->bases[0].d_psi))) return st;
+    if ((st = reproject(c, 0))) return st;
+  }
+  return PARO_OK;
+}
+
 int paro_set_smearing(paro_ctx* ctx, double kT) {
   CTX_CHECK(ctx);
   if (!(kT >= 0) || !std::isfinite(kT)) return fail(c, PARO_ERR_ARG, "paro_set_smearing: kT must be >= 0");
@@ -1181,6 +1210,7 @@ int paro_apply_h(paro_ctx* ctx, int ik, int nb, int dtype, const void* psi, void
       (dtype != PARO_C64 && dtype != PARO_C32))
     return fail(c, PARO_ERR_ARG, "paro_apply_h: bad argument");
   if (dtype == PARO_C64 && check_fft_support(c, 16)) return PARO_ERR_ARG;
+  GammaPackOff general(c);  // the caller's vectors are general complex rows
   return dtype == PARO_C64
              ? apply_h<double>(c, ik, nb, static_cast<const double2*>(psi), static_cast<double2*>(hpsi), 0.0, nullptr)
              : apply_h<float>(c, ik, nb, static_cast<const float2*>(psi), static_cast<float2*>(hpsi), 0.0, nullptr);
@@ -1194,6 +1224,7 @@ int paro_apply_h_adjoint(paro_ctx* ctx, int ik, int nb, int dtype, const void* p
     return fail(c, PARO_ERR_ARG, "paro_apply_h_adjoint: bad argument");
   if (!c->have_veff) return fail(c, PARO_ERR_STATE, "no effective potential set");
   if (dtype == PARO_C64 && check_fft_support(c, 16)) return PARO_ERR_ARG;
+  GammaPackOff general(c);
   return apply_h_adjoint(c, ik, nb, dtype, psi, w, g_psi, g_v, g_pos);
 }
 
@@ -1207,6 +1238,7 @@ int paro_orthonormalize(paro_ctx* ctx, int ik, int n, int dtype, const void* x, 
   const char *xb = static_cast<const char*>(x), *yb = static_cast<const char*>(y);
   if (x != y && xb < yb + bytes && yb < xb + bytes) return fail(c, PARO_ERR_ARG, "paro_orthonormalize: x and y overlap");
   if (x != y) PARO_CU(c, cudaMemcpyAsync(y, x, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  GammaPackOff general(c);
   return dtype == PARO_C64 ? orthonormalize<double>(c, ik, static_cast<double2*>(y), n)
                            : orthonormalize<float>(c, ik, static_cast<float2*>(y), n);
 }
@@ -1218,6 +1250,7 @@ int paro_solve_source(paro_ctx* ctx, int ik, int nb, int dtype, const double* ep
       (dtype != PARO_C64 && dtype != PARO_C32))
     return fail(c, PARO_ERR_ARG, "paro_solve_source: bad argument");
   if (!c->have_veff) return fail(c, PARO_ERR_STATE, "no effective potential set");
+  GammaPackOff general(c);
   const int npw = c->bases[ik].npw;
   double* f = static_cast<double*>(ws_get(c, "ss_f", (size_t)nb * sizeof(double)));
   if (!f) return PARO_ERR_CUDA;
@@ -1249,6 +1282,7 @@ int paro_set_orbitals(paro_ctx* ctx, int ik, const void* psi, int on_device) {
   if (st) return st;
   PARO_CU(c, cudaMemcpyAsync(b.d_psi, psi, (size_t)c->nb * b.npw * sizeof(double2),
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  if (c->gamma_real && (st = gamma_real_rows<double>(c, ik, c->nb, b.d_psi))) return st;
   return reproject(c, ik);
 }
 
@@ -1379,6 +1413,7 @@ int paro_set_state(paro_ctx* ctx, int ik, const void* psi, const double* eps, in
   const size_t bytes = (size_t)c->nb * b.npw * sizeof(double2);
   PARO_CU(c, cudaMemcpyAsync(b.d_psi, psi, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                              c->stream));
+  if (c->gamma_real && (st = gamma_real_rows<double>(c, ik, c->nb, b.d_psi))) return st;
   b.eps.assign(eps, eps + c->nb);
   return adopt_orbitals(c, ik);
 }

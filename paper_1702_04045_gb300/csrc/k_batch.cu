@@ -1032,6 +1032,7 @@ int paro_batch_create(paro_batch** out, paro_ctx* const* ctxs, int n_ctx) {
     if ((c.prec == PARO_FP64) != b->f64) return bail(PARO_ERR_ARG, "batch: contexts differ in precision");
     if (!c.have_veff) return bail(PARO_ERR_STATE, "batch: every context needs a potential");
     if (c.nb > kBMaxBands) return bail(PARO_ERR_ARG, "batch: at most 64 bands per context");
+    if (c.gamma_real) return bail(PARO_ERR_ARG, "batch: contexts in the real-wavefunction mode are not batched");
     if (c.stream != b->st) return bail(PARO_ERR_ARG, "batch: contexts must share one stream");
     for (int ik = 0; ik < c.nk; ++ik) {
       const Basis& B = c.bases[ik];

@@ -177,6 +177,7 @@ template <> const float* kin_of<float>(const Basis& b) { return b.d_kin32; }
 template <typename T>
 int apply_h(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* hpsi, double shift, const int* active) {
   if (!c->have_veff) return fail(c, PARO_ERR_STATE, "no effective potential set");
+  if (gamma_on(c)) return gamma_apply<T>(c, ik, nb, psi, hpsi, shift, active, nullptr, nullptr);
   int st = configure<T>(c);
   if (st) return st;
   const Basis& B = c->bases[ik];
@@ -230,6 +231,7 @@ int apply_h(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* hpsi, double sh
 template <typename T>
 int apply_dv(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* hpsi, const T* dvplane, bool* used) {
   *used = false;
+  if (gamma_on(c)) return gamma_apply<T>(c, ik, nb, psi, hpsi, 0.0, nullptr, dvplane, used);
   int st = configure<T>(c);
   if (st) return st;
   const Basis& B = c->bases[ik];

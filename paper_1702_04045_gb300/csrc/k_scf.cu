@@ -809,12 +809,21 @@ int density(Ctx* c, const cplx<T>* const* psis, double* rho_dev) {
       if (!y) return PARO_ERR_CUDA;
       if ((st = scale_rows<T>(c, nrow, npw, psis[ik], c->d_occ_sqrt + (size_t)ik * c->nb, y))) return st;
       rows = y;
-      st = density_bands<T>(c, ik, nrow, y, c->kw[ik] / c->omega, rho_dev, ik > 0);
+    }
+    const double wfac = (c->kT > 0 ? 1.0 : 2.0) * c->kw[ik] / c->omega;
+    int nnorm = nrow;
+    if (gamma_on(c)) {  // real orbitals: two per transform, |a + i b|^2 = a^2 + b^2
+      st = gamma_density_rows<T>(c, ik, nrow, rows, wfac, rho_dev, ik > 0, &nnorm, &rows);
     } else {
-      st = density_bands<T>(c, ik, nrow, psis[ik], 2.0 * c->kw[ik] / c->omega, rho_dev, ik > 0);
+      st = density_bands<T>(c, ik, nrow, rows, wfac, rho_dev, ik > 0);
     }
     if (st) return st;
-    if (renorm && (st = band_norms<T>(c, nrow, npw, rows, npw, norms + (size_t)ik * c->nb))) return st;
+    if (renorm) {
+      if ((st = band_norms<T>(c, nnorm, npw, rows, npw, norms + (size_t)ik * c->nb))) return st;
+      if (nnorm < nrow)  // packed rows: ||a + i b||^2 = ||a||^2 + ||b||^2; the slots behind them count zero
+        PARO_CU(c, cudaMemsetAsync(norms + (size_t)ik * c->nb + nnorm, 0, (size_t)(nrow - nnorm) * sizeof(double),
+                                   c->stream));
+    }
   }
   if (!renorm) return PARO_OK;
   const int nblk = 304;

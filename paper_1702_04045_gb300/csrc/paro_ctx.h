@@ -33,6 +33,7 @@ struct Basis {
   int* d_g_col = nullptr;         // stick of coefficient g
   int* d_g_z = nullptr;           // grid index j3 of coefficient g
   int* d_xrows = nullptr;         // the nxr rows j1 with sticks
+  int* d_mg = nullptr;            // real-wavefunction mode (k = 0): index of -G for every G
   double2* d_beta = nullptr;      // KB projectors, nproj x npw
   float2* d_beta32 = nullptr;
   double* d_prec_base = nullptr;  // |k+G|^2/2 (copy used by the preconditioner)
@@ -101,6 +102,11 @@ struct Ctx {
   std::vector<double> occ;  // nk x nb, f_ik
   int nocc_eff = 0;         // bands per k from the first up to the last with an occupation above 1e-15
   double* d_occ_sqrt = nullptr;  // nk x nb, sqrt(f_ik), for the density of smeared orbitals
+  // Gamma-point real-wavefunction mode: the ParO iteration treats its orbitals as real functions (two per
+  // packed complex H application and density transform, real Gram and Rayleigh-Ritz matrices);
+  // gamma_pack_off suspends it for calls on general complex vectors
+  bool gamma_real = false;
+  bool gamma_pack_off = false;
   bool fft_configured[2] = {false, false};
   // instrumentation: kernels launched, and CUDA-event pairs around named kernels while profiling
   long long launches = 0;
@@ -226,6 +232,27 @@ int convert(Ctx* c, size_t n, const cplx<TS>* src, cplx<TD>* dst);
 // ---- KB projectors (k_hpsi.cu) ----
 template <typename T>
 int kb_apply(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* hpsi);
+
+// Suspends the real-wavefunction mode for the scope (calls on general complex vectors, packed rows).
+struct GammaPackOff {
+  Ctx* c;
+  bool old;
+  explicit GammaPackOff(Ctx* ctx) : c(ctx), old(ctx->gamma_pack_off) { ctx->gamma_pack_off = true; }
+  ~GammaPackOff() { c->gamma_pack_off = old; }
+};
+inline bool gamma_on(const Ctx* c) { return c->gamma_real && !c->gamma_pack_off; }
+
+// ---- Gamma-point real-wavefunction mode (k_gamma.cu) ----
+template <typename T>
+int gamma_apply(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* hpsi, double shift, const int* active,
+                const T* dvplane, bool* used);
+template <typename T>
+int gamma_real_rows(Ctx* c, int ik, int nb, cplx<T>* x);   // rows <- their real part, in place
+int gamma_real_matrix(Ctx* c, int n, double2* a);          // imaginary parts of an n x n matrix dropped
+template <typename T>
+int gamma_density_rows(Ctx* c, int ik, int nrow, const cplx<T>* rows, double wfac, double* rho, bool accumulate,
+                       int* npacked, const cplx<T>** packed);
+int gamma_build_table(Ctx* c, int ik);
 
 // ---- occupations (api.cu) ----
 // c->occ, c->nocc_eff, c->mu, c->mts (and d_occ_sqrt with smearing) from the current Ritz values

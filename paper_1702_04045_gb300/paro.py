@@ -26,7 +26,7 @@ ENERGY_TERMS = ("kinetic", "nonlocal", "local", "hartree", "xc", "ewald", "total
 EXPORTS = (
     "paro_create", "paro_set_local_pp", "paro_set_kb", "paro_set_positions", "paro_set_veff", "paro_set_veff_rest",
     "paro_get_veff",
-    "paro_get_vloc", "paro_set_density", "paro_set_ecut", "paro_set_smearing", "paro_get_occupations", "paro_grid", "paro_npw", "paro_miller", "paro_sigma", "paro_apply_h",
+    "paro_get_vloc", "paro_set_density", "paro_set_ecut", "paro_set_gamma_real", "paro_set_smearing", "paro_get_occupations", "paro_grid", "paro_npw", "paro_miller", "paro_sigma", "paro_apply_h",
     "paro_apply_h_noalloc", "paro_apply_h_adjoint", "paro_orthonormalize", "paro_solve_source", "paro_batch_create", "paro_batch_apply_h",
     "paro_batch_step", "paro_batch_info", "paro_batch_destroy",
     "paro_set_orbitals", "paro_get_orbitals", "paro_get_eigenvalues", "paro_get_residuals", "paro_step",
@@ -62,6 +62,7 @@ _SIGS = {
     "paro_set_density": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "paro_set_smearing": (ctypes.c_int, [_vp, ctypes.c_double]),
     "paro_set_ecut": (ctypes.c_int, [_vp, ctypes.c_double]),
+    "paro_set_gamma_real": (ctypes.c_int, [_vp, ctypes.c_int]),
     "paro_get_occupations": (ctypes.c_int, [_vp, _c_dbl_p, _c_dbl_p, _c_dbl_p]),
     "paro_grid": (ctypes.c_int, [_vp, _c_int_p]),
     "paro_npw": (ctypes.c_int, [_vp, ctypes.c_int, _c_int_p]),
@@ -228,6 +229,11 @@ class Context:
         """One step of the cutoff ladder (Algorithm 1 step 2): the basis and grid of the larger cutoff, the
         orbitals embedded in it."""
         self._check(self.lib.paro_set_ecut(self.h, float(ecut)))
+
+    def set_gamma_real(self, enable=True):
+        """Gamma-point real-wavefunction mode: two real orbitals per complex H application and density
+        transform in the ParO iteration (k = 0 contexts only)."""
+        self._check(self.lib.paro_set_gamma_real(self.h, 1 if enable else 0))
 
     def set_smearing(self, kT):
         """Fermi-Dirac occupations of width kT (Ha); 0 restores integer occupations of the n_occ lowest bands."""
