@@ -476,6 +476,27 @@ def run_adjoint(nb=1088, calls=2):
     return out
 
 
+def run_gamma(args):
+    """The same cell and converged-iteration timing with the Gamma-point real-wavefunction mode (two real
+    orbitals per packed complex H application and density transform): its own convergence from the seeded
+    start vectors, then K timed iterations (CUDA events)."""
+    import torch
+    from paper_1702_04045_gb300 import inputs, paro
+    lat, pos, d, c = inputs.config_inputs(args.workload)
+    ctx = paro.context_from_config(args.workload, args.precision)
+    ctx.set_gamma_real(True)
+    ctx.set_orbitals(inputs.start_vectors(c["n_bands"], ctx.npw(), c["seed_psi"]))
+    opts = paro.ScfOptions(alg=args.alg, tol_per_atom=0.0, inner_rel_tol=0.25, inner_max_it=8)
+    n_conv, s_conv, _ = _scf_until(ctx, opts, len(pos), args.conv_tol, args.max_conv_iter)
+    for _ in range(args.warmup):
+        ctx.scf_step(opts)
+    ms, terms = _timed_steps(ctx, opts, args.steps)
+    out = {"mode": "Gamma-point real wavefunctions (paro_set_gamma_real)", "ms_per_step": ms / args.steps,
+           "iterations_to_converge": n_conv, "seconds_to_converge": s_conv, "energy_last_step": terms["total"]}
+    ctx.close()
+    return out
+
+
 def run_hpsi512(nb=1088, calls=3):
     """Forward H psi batch of the 512-atom cell (137059 plane waves, 128^3 grid, 2048 KB projectors), all
     1088 bands in FP32 through paro_apply_h: ms per batch with CUDA events, the three FFT passes' share
@@ -622,6 +643,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-hpsi512", action="store_true")
+    ap.add_argument("--no-gamma", action="store_true")
     ap.add_argument("--conv-tol", type=float, default=1e-6, help="|dF|/atom before the timed region")
     ap.add_argument("--max-conv-iter", type=int, default=4000)
     ap.add_argument("--fix-tol", type=float, default=1e-9, help="|dF|/atom of the mixed-vs-FP64 fixed points")
@@ -636,6 +658,9 @@ def main():
             print(json.dumps(out))
         return
     out = run_ours(args, rank, world, local, pg)
+    if rank == 0 and world == 1 and not args.no_gamma:
+        out["gamma_real"] = run_gamma(args)
+        out["gamma_real"]["speedup_vs_complex"] = out["ms_per_step"] / out["gamma_real"]["ms_per_step"]
     if rank == 0 and world == 1 and not args.no_hpsi512:
         out["hpsi_512"] = run_hpsi512()
     if rank == 0 and world == 1 and not args.no_adjoint:
