@@ -63,8 +63,13 @@ __global__ void __launch_bounds__(256) k_zpass_inv_reg(const cplx<T>* __restrict
   }
 }
 
-template <typename T, int N1, int N2>
-__global__ void __launch_bounds__(256) k_plane_reg(cplx<T>* __restrict__ S, int ncol, const int* __restrict__ col_x,
+// Warps per plane-pass CTA: 9 for N = 72 (a warp holds 4 lines of 8 lanes, so the ~35 stick rows of the
+// y-pass take one round of 36 lines and the 72 columns of the x-pass two), 8 otherwise.
+template <int N> struct PlaneWarps { static constexpr int value = 8; };
+template <> struct PlaneWarps<72> { static constexpr int value = 9; };
+
+template <typename T, int N1, int N2, int NW = PlaneWarps<N1>::value>
+__global__ void __launch_bounds__(32 * NW) k_plane_reg(cplx<T>* __restrict__ S, int ncol, const int* __restrict__ col_x,
                                                    const int* __restrict__ col_y, const int* __restrict__ xrows,
                                                    int nxr, const cplx<T>* __restrict__ twx,
                                                    const cplx<T>* __restrict__ twy, const T* __restrict__ vplane,
@@ -236,7 +241,8 @@ static int passes_reg(Ctx* c, const Basis& B, int nb, const cplx<T>* psi, cplx<T
   const int eb = (int)sizeof(cplx<T>);
   const bool f64 = sizeof(T) == 8;
   const size_t smz = (size_t)eb * (N + kStickBatch * (N + 1));
-  const size_t smp = (size_t)eb * (2 * N + N * (N + 1) + 8 * PlaneLines<T, N>::kWarpTile);  // 8 warps
+  constexpr int kPW = PlaneWarps<N>::value;
+  const size_t smp = (size_t)eb * (2 * N + N * (N + 1) + kPW * PlaneLines<T, N>::kWarpTile);
   int st;
   if ((st = set_smem_once(c, k_zpass_inv_reg<T, N>, done[0])) || (st = set_smem_once(c, k_plane_reg<T, N, N>, done[1])) ||
       (st = set_smem_once(c, k_zpass_fwd_reg<T, N>, done[2])) ||
@@ -249,7 +255,7 @@ static int passes_reg(Ctx* c, const Basis& B, int nb, const cplx<T>* psi, cplx<T
   PARO_LAUNCH(c, "k_zpass_inv_reg");
   prof_end(c, f64 ? "k_zpass_inv<f64>" : "k_zpass_inv<f32>", ev);
   ev = prof_begin(c);
-  k_plane_reg<T, N, N><<<dim3(c->N[2], nb), 256, smp, c->stream>>>(S, B.ncol, B.d_col_x, B.d_col_y, B.d_xrows, B.nxr,
+  k_plane_reg<T, N, N><<<dim3(c->N[2], nb), 32 * kPW, smp, c->stream>>>(S, B.ncol, B.d_col_x, B.d_col_y, B.d_xrows, B.nxr,
                                                                    tw_of<T>(c, 0), tw_of<T>(c, 1),
                                                                    vplane ? vplane : vplane_of<T>(c), active);
   PARO_LAUNCH(c, "k_plane_reg");
