@@ -322,7 +322,7 @@ static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal, cplx<T>
     k_hermitize<<<(nx * nx + 255) / 256, 256, 0, c->stream>>>(nx, S);
     PARO_LAUNCH(c, "k_hermitize");
     // mixed: one refinement step (FP64 Ritz values, vectors well below the FP32 level of the orbitals)
-    if ((st = f64 ? eigh(c, nx, S, w, G) : eigh_mixed(c, nx, S, w, G, 1))) return st;  // G <- eigenvectors C
+    if ((st = f64 ? eigh(c, nx, S, w, G) : eigh_mixed(c, nx, S, w, G, 1, true))) return st;  // G <- eigenvectors C
   }
   {
     ProfTag t(c, "rot");

@@ -67,6 +67,11 @@ __global__ void __launch_bounds__(256) k_zpass_inv_reg(const cplx<T>* __restrict
 // y-pass take one round of 36 lines and the 72 columns of the x-pass two), 8 otherwise.
 template <int N> struct PlaneWarps { static constexpr int value = 8; };
 template <> struct PlaneWarps<72> { static constexpr int value = 9; };
+// Row stride of the plane in shared memory (complex elements). The x-pass reads a column with 8 lanes
+// per line and 4 lines per warp: with a stride of 74 (10 mod 16) the 16 8-byte elements of a half-warp fall
+// in distinct bank pairs, where 73 gave two-way conflicts.
+template <int N> struct PlaneStride { static constexpr int value = N + 1; };
+template <> struct PlaneStride<72> { static constexpr int value = 74; };
 
 template <typename T, int N1, int N2, int NW = PlaneWarps<N1>::value>
 __global__ void __launch_bounds__(32 * NW) k_plane_reg(cplx<T>* __restrict__ S, int ncol, const int* __restrict__ col_x,
@@ -78,7 +83,7 @@ __global__ void __launch_bounds__(32 * NW) k_plane_reg(cplx<T>* __restrict__ S, 
   using SY = LineShape<N2>;
   using LX = PlaneLines<T, N1>;
   using LY = PlaneLines<T, N2>;
-  constexpr int LS = N2 + 1;
+  constexpr int LS = PlaneStride<N2>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* tx = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* ty = tx + N1;
@@ -242,7 +247,7 @@ static int passes_reg(Ctx* c, const Basis& B, int nb, const cplx<T>* psi, cplx<T
   const bool f64 = sizeof(T) == 8;
   const size_t smz = (size_t)eb * (N + kStickBatch * (N + 1));
   constexpr int kPW = PlaneWarps<N>::value;
-  const size_t smp = (size_t)eb * (2 * N + N * (N + 1) + kPW * PlaneLines<T, N>::kWarpTile);
+  const size_t smp = (size_t)eb * (2 * N + N * PlaneStride<N>::value + kPW * PlaneLines<T, N>::kWarpTile);
   int st;
   if ((st = set_smem_once(c, k_zpass_inv_reg<T, N>, done[0])) || (st = set_smem_once(c, k_plane_reg<T, N, N>, done[1])) ||
       (st = set_smem_once(c, k_zpass_fwd_reg<T, N>, done[2])) ||

@@ -455,7 +455,41 @@ static int zgemm(Ctx* c, int n, const double2* A, bool ah, const double2* B, dou
   return PARO_OK;
 }
 
-int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refine_steps) {
+// Warm start of the refinement: X = the permutation that sorts the diagonal of A (one CTA, n <= 1024):
+// column rank(i) is e_i, rank(i) = #{j : a_jj < a_ii, or a_jj = a_ii and j < i}
+__global__ void k_warm_perm(int n, const double2* __restrict__ A, double2* __restrict__ X) {
+  const int i = threadIdx.x;
+  if (i >= n) return;
+  const double d = A[(size_t)i * n + i].x;
+  int r = 0;
+  for (int j = 0; j < n; ++j) {
+    const double e = A[(size_t)j * n + j].x;
+    r += (e < d || (e == d && j < i)) ? 1 : 0;
+  }
+  X[(size_t)i * n + r] = make_double2(1.0, 0.0);
+}
+
+// max |E_ij| over the matrix into *out (one CTA; the warm start's convergence test)
+__global__ void k_absmax(int nn, const double2* __restrict__ E, float* __restrict__ out) {
+  __shared__ float red[32];
+  float m = 0.f;
+  for (int i = threadIdx.x; i < nn; i += blockDim.x) m = fmaxf(m, (float)fmax(fabs(E[i].x), fabs(E[i].y)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float r = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, red[w]);
+    *out = r;
+  }
+}
+
+static int eigh_finish(Ctx* c, int n, const double2* a, const double2* Af, double2* X, double2* T1, double2* S,
+                       double2* part, const int* cl, const int* cst, const int* ncl, double* lam, double* w,
+                       double2* v, int* perm, int* info, bool clusters);
+
+int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refine_steps, bool warm) {
   if (n < 2 || n > kMixMaxN) return eigh(c, n, a, w, v);
   const size_t nn = (size_t)n * n;
   double2* Af = static_cast<double2*>(ws_get(c, "em_A", nn * sizeof(double2)));
@@ -485,6 +519,39 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
   PARO_CU(c, cudaMemsetAsync(flags, 0, 6 * sizeof(int), c->stream));
   k_herm_full_mixed<<<(int)((nn + 255) / 256), 256, 0, c->stream>>>(n, a, Af);
   PARO_LAUNCH(c, "k_herm_full");
+  int st;
+  // Rayleigh-Ritz near convergence: the matrix of a basis that already is close to the eigenvectors is
+  // nearly diagonal, and two refinement steps from the permutation that sorts its diagonal reach the
+  // accuracy one step gives from the FP32 eigenvectors; accepted when the last correction is below
+  // 1e-4 (the remaining error is of its square), else the FP32 solve below runs
+  if (warm && c->eig_warm_skip > 0) {
+    --c->eig_warm_skip;
+  } else if (warm) {
+    cudaEvent_t evw = prof_begin(c);
+    PARO_CU(c, cudaMemsetAsync(X, 0, nn * sizeof(double2), c->stream));
+    k_warm_perm<<<1, 1024, 0, c->stream>>>(n, Af, X);
+    PARO_LAUNCH(c, "k_warm_perm");
+    for (int it = 0; it < 2; ++it) {
+      if ((st = zgemm(c, n, X, true, X, G, false, part, true, nrm, true))) return st;
+      if ((st = zgemm(c, n, Af, false, X, T1, false, part))) return st;
+      if ((st = zgemm(c, n, X, true, T1, S, false, part, true, nrm + nnrm, false))) return st;
+      k_refine_lam<<<1, 1024, 0, c->stream>>>(n, G, S, nrm, nnrm, lam, cl, cst, ncl);
+      PARO_LAUNCH(c, "k_refine_lam");
+      k_refine_e<<<(n * n + 255) / 256, 256, 0, c->stream>>>(n, G, S, lam, cl, T1);
+      PARO_LAUNCH(c, "k_refine_e");
+      if (it == 1) {
+        k_absmax<<<1, 1024, 0, c->stream>>>((int)nn, T1, r32);
+        PARO_LAUNCH(c, "k_absmax");
+      }
+      if ((st = zgemm(c, n, X, false, T1, X, true, part))) return st;
+    }
+    float emax = 1.f;
+    PARO_CU(c, cudaMemcpyAsync(&emax, r32, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    PARO_CU(c, cudaStreamSynchronize(c->stream));
+    prof_end(c, "eigh_warm", evw);
+    if (emax < 1e-4f) return eigh_finish(c, n, a, Af, X, T1, S, part, cl, cst, ncl, lam, w, v, perm, info, true);
+    c->eig_warm_skip = 8;  // not close enough yet: the FP32 solve for the next calls
+  }
   // 1. FP32 solve
   cudaEvent_t ev = prof_begin(c);
   const size_t sm1 = ((size_t)n * (n + 1) + 2 * (size_t)n) * sizeof(float2);
@@ -492,7 +559,7 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
   k_tridiag_cta<<<1, 1024, sm1, c->stream>>>(n, Af, U32, d32, e32, ph32, tau32, ecx32);
   PARO_LAUNCH(c, "k_tridiag_cta");
   prof_end(c, "k_tridiag_cta", ev);
-  int st = eigh_fp32_pieces(c, n, d32, e32, w32, U32, tau32, ph32, Z32, V32, info);
+  st = eigh_fp32_pieces(c, n, d32, e32, w32, U32, tau32, ph32, Z32, V32, info);
   if (st) return st;
   // 2. FP64 refinement (refine_steps steps), 3. Rayleigh-Ritz in the clusters
   ev = prof_begin(c);
@@ -512,16 +579,26 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
     prof_end(c, "k_refine_e", ev2);
     if ((st = zgemm(c, n, X, false, T1, X, true, part))) return st;    // X += X E
   }
+  prof_end(c, "eigh_refine", ev);
+  return eigh_finish(c, n, a, Af, X, T1, S, part, cl, cst, ncl, lam, w, v, perm, info, refine_steps > 0);
+}
+
+// The end of the mixed solve from refined vectors X: T1 = A X, S = X^H A X (inside the clusters when they
+// exist), Rayleigh-Ritz inside each cluster, eigenvalues sorted.
+static int eigh_finish(Ctx* c, int n, const double2* a, const double2* Af, double2* X, double2* T1, double2* S,
+                       double2* part, const int* cl, const int* cst, const int* ncl, double* lam, double* w,
+                       double2* v, int* perm, int* info, bool clusters) {
+  const size_t nn = (size_t)n * n;
+  int st;
+  cudaEvent_t ev = prof_begin(c);
   if ((st = zgemm(c, n, Af, false, X, T1, false, part))) return st;    // T1 = A X
-  if (refine_steps > 0) {  // the clusters exist: S = X^H A X inside them only
-    cudaEvent_t ev2 = prof_begin(c);
+  if (clusters) {  // the clusters exist: S = X^H A X inside them only
     k_blockdiag_xhat<<<(int)((nn + 7) / 8), 256, 0, c->stream>>>(n, X, T1, cl, S);
     PARO_LAUNCH(c, "k_blockdiag_xhat");
-    prof_end(c, "k_blockdiag_xhat", ev2);
   } else if ((st = zgemm(c, n, X, true, T1, S, false, part))) {
     return st;
   }
-  prof_end(c, "eigh_refine", ev);
+  prof_end(c, "eigh_finish", ev);
   ev = prof_begin(c);
   const size_t sm3 = (size_t)2 * 64 * 65 * sizeof(double2);
   PARO_CU(c, cudaFuncSetAttribute(k_cluster_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));

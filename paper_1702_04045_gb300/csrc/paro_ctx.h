@@ -107,6 +107,7 @@ struct Ctx {
   // gamma_pack_off suspends it for calls on general complex vectors
   bool gamma_real = false;
   bool gamma_pack_off = false;
+  int eig_warm_skip = 0;  // Rayleigh-Ritz eigensolves left before the warm start is tried again
   bool fft_configured[2] = {false, false};
   // instrumentation: kernels launched, and CUDA-event pairs around named kernels while profiling
   long long launches = 0;
@@ -216,7 +217,10 @@ int eigh(Ctx* c, int n, const double2* a, double* w, double2* v);
 // The same result from an FP32 solve refined in FP64 (k_eigh_mixed.cu); FP64 solver for n > 160. Each
 // refinement step squares the eigenvector error across clusters: one step takes the FP32 vectors (~1e-4)
 // to ~1e-8 with Rayleigh quotients at FP64 accuracy, two to FP64 vectors.
-int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refine_steps);
+// warm: the matrix may already be nearly diagonal (a Rayleigh-Ritz basis close to the eigenvectors); then
+// two refinement steps from the permutation that sorts its diagonal replace the FP32 solve when their last
+// correction is small, with the FP32 solve as the fallback.
+int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refine_steps, bool warm = false);
 // Per-band partial sums: out[b] = sum_g Re conj(x[b][g]) y[b][g] (weights optional) — helpers.
 template <typename T>
 int band_norms(Ctx* c, int nb, int npw, const cplx<T>* x, int ldx, double* out_dev);
