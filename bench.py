@@ -573,6 +573,9 @@ def run_batched(name, steps=10, warmup=3, ref_steps=3):
     torch.cuda.synchronize()
     t_h = e0.elapsed_time(e1) / 5
     info = b.info()
+    tun = b.tuning()
+    best = tun[int(np.argmin(tun[:, 4]))]
+    coop = tun[tun[:, 0] == 1]
     for c in ctxs:
         c.step(1, 0.25, 8)
     torch.cuda.synchronize()
@@ -586,7 +589,10 @@ def run_batched(name, steps=10, warmup=3, ref_steps=3):
            "npw_range": [min(npw), max(npw)], "precision": "mixed",
            "ms_per_step_batched": t_b * 1e3, "ms_per_step_per_context": t_c * 1e3, "speedup": t_c / t_b,
            "hpsi_ms_all_orbitals": t_h,
-           "hpsi_kernel": {"launches_per_apply": info["launches_per_apply"], "grid": info["grid"]},
+           "hpsi_kernel": {"launches_per_apply": info["launches_per_apply"], "grid": info["grid"],
+                           "sticks_per_unit": int(best[2]), "plane_points_per_unit": int(best[3]),
+                           "autotuned_ms": float(best[4]), "candidates": int(len(tun)),
+                           "best_cooperative_ms": float(coop[:, 4].min()) if len(coop) else None},
            "kernels_per_step": info["kernels_per_step"], "max_resid_after": r}
     b.close()
     for c in ctxs:

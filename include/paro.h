@@ -225,13 +225,15 @@ int paro_apply_h_adjoint(paro_ctx* ctx, int ik, int nb, int dtype, const void* p
  * of parallelism: orbitals within a problem, problems within the batch). The paper has no batching
  * interface; these calls run Algorithm 1 on all problems at once.
  * paro_batch_create -- groups n_ctx contexts (same precision, same stream, n_bands <= 64 each, a
- *   potential set). Problems are (context, k-point) pairs in context-major order. H psi runs as one
- *   persistent kernel over flat work lists of all problems' orbitals (z-FFTs of stick groups, one unit
- *   per (orbital, z-plane), z-FFTs back), so a plane of every problem must fit one CTA's shared memory
- *   (N1 x N2 complex elements of the working precision within 227 KB; otherwise PARO_ERR_ARG). The call
- *   times the candidate forms (one cooperative launch with grid barriers between the phases, or one
- *   launch per phase) and grids on the batch's own problems and keeps the fastest. The batch refers to
- *   the contexts, which must outlive it.
+ *   potential set, not in the real-wavefunction mode). Problems are (context, k-point) pairs in
+ *   context-major order. H psi runs as one persistent kernel over flat work lists of all problems'
+ *   orbitals (z-FFTs of stick groups, units of one to four z-planes per orbital, z-FFTs back), so a plane
+ *   of every problem must fit one CTA's shared memory (N1 x N2 complex elements of the working precision
+ *   within 227 KB; otherwise PARO_ERR_ARG). The call times, on the batch's own problems, the unit shapes
+ *   (32, 64 or 128 sticks per z-FFT unit; planes per unit for about 2048, 4096 or 8192 points), the launch
+ *   forms (one cooperative launch with grid barriers between the phases, or one launch per phase) and the
+ *   grids, and keeps the fastest (paro_batch_tuning). The batch refers to the contexts, which must
+ *   outlive it.
  * paro_batch_apply_h -- H psi of every problem: psi[i], hpsi[i] device n_bands x npw arrays of dtype
  *   (the contexts' precision: PARO_C64 for FP64, PARO_C32 for mixed) of problem i. Enqueued on the
  *   contexts' stream.
@@ -252,6 +254,11 @@ int paro_batch_apply_h(paro_batch* b, int dtype, const void* const* psi, void* c
 int paro_batch_step(paro_batch* b, double rel_tol, int max_it, double* max_resid_out);
 int paro_batch_info(const paro_batch* b, int* n_problems, int* n_items, int* launches_per_apply, int* grid,
                     long long* kernels_per_step);
+/* paro_batch_tuning -- the autotuner's measurements at batch creation: n_rows receives the number of
+ * candidates timed, and rows (host double[5 * max_rows], may be NULL when max_rows = 0) the first
+ * max_rows of them as (launches per H psi: 1 cooperative or 3, grid, sticks per z-FFT unit, plane points
+ * per plane unit, ms per H psi of the whole batch). The fastest row is the configuration in use. */
+int paro_batch_tuning(const paro_batch* b, int max_rows, int* n_rows, double* rows);
 void paro_batch_destroy(paro_batch* b);
 
 /*

@@ -17,6 +17,7 @@
 //  * the H psi form (one cooperative launch or three) and its persistent grid are picked by timing the
 //    candidates on the batch's own problems when the batch is created.
 #include <algorithm>
+#include <array>
 #include <cfloat>
 #include <cmath>
 #include <numeric>
@@ -66,18 +67,17 @@ template <typename T> __device__ __forceinline__ const cplx<T>* pd_beta(const Pr
 template <> __device__ __forceinline__ const double2* pd_beta<double>(const ProbDev& p) { return p.beta; }
 template <> __device__ __forceinline__ const float2* pd_beta<float>(const ProbDev& p) { return p.beta32; }
 
-static const int kSG = 64;  // sticks per z-FFT work unit
-
-// z-planes per plane work unit: enough that one unit's FFT stages cover ~4096 points
-__host__ __device__ __forceinline__ int planes_per_unit(int N1, int N2) {
-  const int pb = 4096 / (N1 * N2);
+// Work-unit shapes, chosen per batch by the autotuner: sg sticks per z-FFT unit, and z-planes per plane
+// unit enough that one unit's FFT stages cover about ppt points (at most 4 planes)
+__host__ __device__ __forceinline__ int planes_per_unit(int N1, int N2, int ppt) {
+  const int pb = ppt / (N1 * N2);
   return pb < 1 ? 1 : (pb > 4 ? 4 : pb);
 }
 
 // shared memory of one work unit (in elements of cplx<T>): the larger of a stick group's lines and a
 // plane, plus the three twiddle tables
-static size_t unit_elems(const ProbDev& p) {
-  const size_t lines = (size_t)kSG * (p.N3 + 1), plane = (size_t)p.N1 * p.N2 * planes_per_unit(p.N1, p.N2);
+static size_t unit_elems(const ProbDev& p, int sg, int ppt) {
+  const size_t lines = (size_t)sg * (p.N3 + 1), plane = (size_t)p.N1 * p.N2 * planes_per_unit(p.N1, p.N2, ppt);
   return (lines > plane ? lines : plane) + p.N1 + p.N2 + p.N3;
 }
 
@@ -96,6 +96,7 @@ struct HpsiLists {
   const int2* u1; int n1;  // (item, group or -1)
   const int2* u2; int n2;  // (item, z)
   const int2* u3; int n3;  // (item, group)
+  int sg, ppt;             // sticks per z-FFT unit; plane points per plane unit
 };
 
 // PH = 0: all three phases in one cooperative launch (grid barriers between them); PH = 1, 2, 3: one
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(256, PH == 0 ? 1 : 2) k_hpsi_batch(const ProbD
       }
       continue;
     }
-    const int c0 = u.y * kSG, ncb = min(kSG, ncol - c0), ls = N3 + 1;
+    const int c0 = u.y * L.sg, ncb = min(L.sg, ncol - c0), ls = N3 + 1;
     cplx<T>* tz = buf;
     cplx<T>* line = tz + N3;
     for (int i = threadIdx.x; i < N3; i += blockDim.x) tz[i] = pd_tw<T>(pd, 2)[i];
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(256, PH == 0 ? 1 : 2) k_hpsi_batch(const ProbD
     const int2 u = L.u2[ui];
     if (!begin_unit(u)) continue;
     const int b = items[u.x].y, N1 = pd.N1, N2 = pd.N2, ncol = pd.ncol, PS = N1 * N2;
-    const int z0 = u.y, np = min(planes_per_unit(N1, N2), pd.N3 - z0);
+    const int z0 = u.y, np = min(planes_per_unit(N1, N2, L.ppt), pd.N3 - z0);
     cplx<T>* tx = buf;
     cplx<T>* ty = tx + N1;
     cplx<T>* P = ty + N2;  // np planes
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(256, PH == 0 ? 1 : 2) k_hpsi_batch(const ProbD
     const int2 u = L.u3[ui];
     if (!begin_unit(u)) continue;
     const int b = items[u.x].y, npw = pd.npw, ncol = pd.ncol, N3 = pd.N3, np = pd.nproj;
-    const int c0 = u.y * kSG, ncb = min(kSG, ncol - c0), ls = N3 + 1;
+    const int c0 = u.y * L.sg, ncb = min(L.sg, ncol - c0), ls = N3 + 1;
     cplx<T>* tz = buf;
     cplx<T>* line = tz + N3;
     for (int i = threadIdx.x; i < N3; i += blockDim.x) tz[i] = pd_tw<T>(pd, 2)[i];
@@ -715,6 +716,9 @@ struct paro_batch {
   void *sbuf = nullptr, *dpbuf = nullptr;  // stick buffers and scaled projections of the H psi phases
   int2 *d_u1 = nullptr, *d_u2 = nullptr, *d_u3 = nullptr;
   int n1 = 0, n2 = 0, n3 = 0;
+  int sg = 64, ppt = 4096;         // work-unit shapes (autotuned)
+  std::vector<int2> h_items;       // (problem, band) of every item, largest problems first
+  std::vector<std::array<double, 5>> tuning;  // launches per apply, grid, sg, ppt, ms per apply
   unsigned* d_bar = nullptr;  // grid barrier (count, generation) and its time-out flag
   int ldm = 1;                     // largest n_bands + 1 (leading dimension of the per-problem matrices in
   size_t small_smem = 0;           // shared memory); bytes of the Jacobi kernel's two ldm x ldm matrices
@@ -768,7 +772,7 @@ BandMap bandmap(const paro_batch* b) { return BandMap{b->d_bprob, b->d_brow, b->
 template <typename T>
 int launch_fused(paro_batch* b, cudaStream_t s, const cplx<T>* X, cplx<T>* Y, const int* active, int shifted,
                  int mode, int grid) {
-  const HpsiLists L{b->d_u1, b->n1, b->d_u2, b->n2, b->d_u3, b->n3};
+  const HpsiLists L{b->d_u1, b->n1, b->d_u2, b->n2, b->d_u3, b->n3, b->sg, b->ppt};
   cplx<T>* S = static_cast<cplx<T>*>(b->sbuf);
   cplx<T>* DP = static_cast<cplx<T>*>(b->dpbuf);
   int* err = reinterpret_cast<int*>(b->d_bar + 2);
@@ -914,15 +918,47 @@ int enqueue_step(paro_batch* b, double tol, int maxit, bool carry_hx) {
   return PARO_OK;
 }
 
+// The three work lists for unit shapes (sg, ppt) on the device, and the shared memory they need (bytes).
+// Returns PARO_ERR_ARG (nothing changed) when a unit does not fit one CTA's shared memory.
+int build_lists(paro_batch* b, int sg, int ppt) {
+  const size_t es = b->f64 ? sizeof(double2) : sizeof(float2);
+  size_t max_el = 0;
+  for (const ProbDev& P : b->hprob) max_el = std::max(max_el, unit_elems(P, sg, ppt));
+  if (max_el * es > 227 * 1024) return PARO_ERR_ARG;
+  std::vector<int2> u1, u2, u3;
+  for (int it = 0; it < (int)b->h_items.size(); ++it) {
+    const ProbDev& P = b->hprob[b->h_items[it].x];
+    const int ng = (P.ncol + sg - 1) / sg;
+    if (P.nproj > 0) u1.push_back(make_int2(it, -1));
+    for (int g = 0; g < ng; ++g) {
+      u1.push_back(make_int2(it, g));
+      u3.push_back(make_int2(it, g));
+    }
+    for (int z = 0; z < P.N3; z += planes_per_unit(P.N1, P.N2, ppt)) u2.push_back(make_int2(it, z));
+  }
+  BCU(b, cudaStreamSynchronize(b->st));
+  int2** dst[3] = {&b->d_u1, &b->d_u2, &b->d_u3};
+  const std::vector<int2>* src[3] = {&u1, &u2, &u3};
+  for (int i = 0; i < 3; ++i) {
+    if (*dst[i]) cudaFree(*dst[i]);
+    *dst[i] = nullptr;
+    BCU(b, cudaMalloc(dst[i], std::max<size_t>(src[i]->size(), 1) * sizeof(int2)));
+    BCU(b, cudaMemcpy(*dst[i], src[i]->data(), src[i]->size() * sizeof(int2), cudaMemcpyHostToDevice));
+  }
+  b->n1 = (int)u1.size();
+  b->n2 = (int)u2.size();
+  b->n3 = (int)u3.size();
+  b->sg = sg;
+  b->ppt = ppt;
+  b->smem = max_el * es;
+  return PARO_OK;
+}
+
 template <typename T>
 int autotune(paro_batch* b) {
   int dev = 0, sms = 0;
   BCU(b, cudaGetDevice(&dev));
   BCU(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  BCU(b, cudaFuncSetAttribute(k_hpsi_batch<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
-  BCU(b, cudaFuncSetAttribute(k_hpsi_batch<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
-  BCU(b, cudaFuncSetAttribute(k_hpsi_batch<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
-  BCU(b, cudaFuncSetAttribute(k_hpsi_batch<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
   BCU(b, cudaFuncSetAttribute(k_bjacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->small_smem));
   BCU(b, cudaFuncSetAttribute(k_bchol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->small_smem));
   cplx<T>* X = static_cast<cplx<T>*>(b->p);
@@ -932,34 +968,58 @@ int autotune(paro_batch* b) {
   BCU(b, cudaEventCreate(&e0));
   BCU(b, cudaEventCreate(&e1));
   float best = 1e30f;
-  for (int mode : {0, 1}) {
-    int per_sm = 0;
-    if (mode == 0)
-      BCU(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hpsi_batch<T, 0>, 256, b->smem));
-    else
-      BCU(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hpsi_batch<T, 2>, 256, b->smem));
-    for (int mult : {1, 2, 4, 8}) {  // mode 0: co-resident CTAs only
-      if (mult > per_sm) break;
-      const int grid = mult * sms;
-      int st;
-      if ((st = launch_fused<T>(b, b->st, X, Y, nullptr, 0, mode, grid))) return st;
-      BCU(b, cudaEventRecord(e0, b->st));
-      for (int rep = 0; rep < 3; ++rep)
-        if ((st = launch_fused<T>(b, b->st, X, Y, nullptr, 0, mode, grid))) return st;
-      BCU(b, cudaEventRecord(e1, b->st));
-      BCU(b, cudaEventSynchronize(e1));
-      float ms = 0.f;
-      BCU(b, cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best) {
-        best = ms;
-        b->threads = mode == 0 ? 1 : 3;  // launches per H psi
-        b->grid = grid;
+  int best_sg = 64, best_ppt = 4096;
+  b->tuning.clear();
+  // unit shapes x launch form (one cooperative launch, or one launch per phase) x grid (CTAs per SM)
+  for (int sg : {32, 64, 128})
+    for (int ppt : {2048, 4096, 8192}) {
+      if (build_lists(b, sg, ppt) != PARO_OK) continue;  // the unit does not fit shared memory
+      for (int ph = 0; ph < 4; ++ph) {
+        const void* fn = ph == 0 ? (const void*)k_hpsi_batch<T, 0>
+                         : ph == 1 ? (const void*)k_hpsi_batch<T, 1>
+                         : ph == 2 ? (const void*)k_hpsi_batch<T, 2> : (const void*)k_hpsi_batch<T, 3>;
+        BCU(b, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+      }
+      for (int mode : {0, 1}) {
+        int per_sm = 0;
+        if (mode == 0)
+          BCU(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hpsi_batch<T, 0>, 256, b->smem));
+        else
+          BCU(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hpsi_batch<T, 2>, 256, b->smem));
+        for (int mult : {1, 2, 4, 8}) {  // mode 0: co-resident CTAs only
+          if (mult > per_sm) break;
+          const int grid = mult * sms;
+          int st;
+          if ((st = launch_fused<T>(b, b->st, X, Y, nullptr, 0, mode, grid))) return st;
+          BCU(b, cudaEventRecord(e0, b->st));
+          for (int rep = 0; rep < 3; ++rep)
+            if ((st = launch_fused<T>(b, b->st, X, Y, nullptr, 0, mode, grid))) return st;
+          BCU(b, cudaEventRecord(e1, b->st));
+          BCU(b, cudaEventSynchronize(e1));
+          float ms = 0.f;
+          BCU(b, cudaEventElapsedTime(&ms, e0, e1));
+          b->tuning.push_back({(double)(mode == 0 ? 1 : 3), (double)grid, (double)sg, (double)ppt, ms / 3.0});
+          if (ms < best) {
+            best = ms;
+            b->threads = mode == 0 ? 1 : 3;  // launches per H psi
+            b->grid = grid;
+            best_sg = sg;
+            best_ppt = ppt;
+          }
+        }
       }
     }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (best >= 1e30f) return berr(b, PARO_ERR_ARG, "batch: H psi kernel cannot be resident");
+  int st = build_lists(b, best_sg, best_ppt);
+  if (st) return berr(b, st, "batch: work lists");
+  for (int ph = 0; ph < 4; ++ph) {
+    const void* fn = ph == 0 ? (const void*)k_hpsi_batch<T, 0>
+                     : ph == 1 ? (const void*)k_hpsi_batch<T, 1>
+                     : ph == 2 ? (const void*)k_hpsi_batch<T, 2> : (const void*)k_hpsi_batch<T, 3>;
+    BCU(b, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+  }
   unsigned h[3] = {0, 0, 0};
   BCU(b, cudaMemcpy(h, b->d_bar, sizeof(h), cudaMemcpyDeviceToHost));
   if (h[2]) return berr(b, PARO_ERR_TIMEOUT, "batch: grid barrier wait gave up");
@@ -1069,7 +1129,7 @@ int paro_batch_create(paro_batch** out, paro_ctx* const* ctxs, int n_ctx) {
       P.dpoff = (long long)dpoff;
       soff += (size_t)c.nb * P.N3 * P.ncol;
       dpoff += (size_t)c.nb * P.nproj;
-      max_el = std::max(max_el, unit_elems(P));
+      max_el = std::max(max_el, unit_elems(P, 32, 2048));
       b->hprob.push_back(P);
       b->pk.push_back({ci, ik});
       off += (size_t)c.nb * B.npw;
@@ -1080,9 +1140,8 @@ int paro_batch_create(paro_batch** out, paro_ctx* const* ctxs, int n_ctx) {
   b->nprob = (int)b->hprob.size();
   b->nbt = band0;
   b->nelem = off;
-  b->smem = max_el * es;
-  if (b->smem > 227 * 1024)
-    return bail(PARO_ERR_ARG, "batch: a plane does not fit one CTA's shared memory (" + std::to_string(b->smem) +
+  if (max_el * es > 227 * 1024)  // the smallest unit shapes (32 sticks, one plane)
+    return bail(PARO_ERR_ARG, "batch: a plane does not fit one CTA's shared memory (" + std::to_string(max_el * es) +
                                   " bytes)");
   int max_nb = 1;
   for (const ProbDev& P : b->hprob) max_nb = std::max(max_nb, P.nb);
@@ -1101,20 +1160,7 @@ int paro_batch_create(paro_batch** out, paro_ctx* const* ctxs, int n_ctx) {
   for (int pi : order)
     for (int j = 0; j < b->hprob[pi].nb; ++j) items.push_back(make_int2(pi, j));
   b->nitems = (int)items.size();
-  std::vector<int2> u1, u2, u3;
-  for (int it = 0; it < b->nitems; ++it) {
-    const ProbDev& P = b->hprob[items[it].x];
-    const int ng = (P.ncol + kSG - 1) / kSG;
-    if (P.nproj > 0) u1.push_back(make_int2(it, -1));
-    for (int g = 0; g < ng; ++g) {
-      u1.push_back(make_int2(it, g));
-      u3.push_back(make_int2(it, g));
-    }
-    for (int z = 0; z < P.N3; z += planes_per_unit(P.N1, P.N2)) u2.push_back(make_int2(it, z));
-  }
-  b->n1 = (int)u1.size();
-  b->n2 = (int)u2.size();
-  b->n3 = (int)u3.size();
+  b->h_items = items;
   std::vector<int> bprob(b->nbt), brow(b->nbt);
   for (int pi = 0; pi < b->nprob; ++pi)
     for (int j = 0; j < b->hprob[pi].nb; ++j) {
@@ -1145,9 +1191,6 @@ int paro_batch_create(paro_batch** out, paro_ctx* const* ctxs, int n_ctx) {
   al((void**)&b->part, (size_t)b->nprob * b->nslice * 4096 * sizeof(double2));
   al(&b->sbuf, soff * es);
   al(&b->dpbuf, std::max<size_t>(dpoff, 1) * es);
-  al((void**)&b->d_u1, u1.size() * sizeof(int2));
-  al((void**)&b->d_u2, u2.size() * sizeof(int2));
-  al((void**)&b->d_u3, u3.size() * sizeof(int2));
   al((void**)&b->d_bar, 4 * sizeof(unsigned));
   al((void**)&b->S, mat);
   al((void**)&b->G, mat);
@@ -1160,9 +1203,6 @@ int paro_batch_create(paro_batch** out, paro_ctx* const* ctxs, int n_ctx) {
   if (e == cudaSuccess) e = cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_bprob, bprob.data(), b->nbt * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_brow, brow.data(), b->nbt * sizeof(int), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(b->d_u1, u1.data(), u1.size() * sizeof(int2), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(b->d_u2, u2.data(), u2.size() * sizeof(int2), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(b->d_u3, u3.data(), u3.size() * sizeof(int2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(b->d_bar, 0, 4 * sizeof(unsigned));
   if (e != cudaSuccess) return bail(PARO_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e));
   const int st = b->f64 ? autotune<double>(b) : autotune<float>(b);
@@ -1281,6 +1321,15 @@ int paro_batch_info(const paro_batch* b, int* n_problems, int* n_items, int* lau
   if (launches_per_apply) *launches_per_apply = b->threads;
   if (grid) *grid = b->grid;
   if (kernels_per_step) *kernels_per_step = b->exec ? b->graph_kernels : 0;
+  return PARO_OK;
+}
+
+int paro_batch_tuning(const paro_batch* b, int max_rows, int* n_rows, double* rows) {
+  if (!b || !n_rows || max_rows < 0 || (max_rows > 0 && !rows)) return PARO_ERR_ARG;
+  const int n = (int)b->tuning.size();
+  *n_rows = n;
+  for (int i = 0; i < n && i < max_rows; ++i)
+    for (int j = 0; j < 5; ++j) rows[5 * i + j] = b->tuning[i][j];
   return PARO_OK;
 }
 

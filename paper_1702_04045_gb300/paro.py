@@ -28,7 +28,7 @@ EXPORTS = (
     "paro_get_veff",
     "paro_get_vloc", "paro_set_density", "paro_set_ecut", "paro_set_gamma_real", "paro_set_smearing", "paro_get_occupations", "paro_grid", "paro_npw", "paro_miller", "paro_sigma", "paro_apply_h",
     "paro_apply_h_noalloc", "paro_apply_h_adjoint", "paro_orthonormalize", "paro_solve_source", "paro_batch_create", "paro_batch_apply_h",
-    "paro_batch_step", "paro_batch_info", "paro_batch_destroy",
+    "paro_batch_step", "paro_batch_info", "paro_batch_tuning", "paro_batch_destroy",
     "paro_set_orbitals", "paro_get_orbitals", "paro_get_eigenvalues", "paro_get_residuals", "paro_step",
     "paro_eigh", "paro_density", "paro_energy", "paro_scf_step", "paro_scf", "paro_set_state", "paro_profile",
     "paro_profile_read", "paro_profile_names", "paro_launch_count", "paro_last_error", "paro_destroy",
@@ -79,6 +79,7 @@ _SIGS = {
     "paro_batch_step": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, _c_dbl_p]),
     "paro_batch_info": (ctypes.c_int, [_vp, _c_int_p, _c_int_p, _c_int_p, _c_int_p,
                                        ctypes.POINTER(ctypes.c_longlong)]),
+    "paro_batch_tuning": (ctypes.c_int, [_vp, ctypes.c_int, _c_int_p, _c_dbl_p]),
     "paro_batch_destroy": (None, [_vp]),
     "paro_get_vloc": (ctypes.c_int, [_vp, _c_dbl_p]),
     "paro_solve_source": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_dbl_p, _vp, _vp,
@@ -492,6 +493,14 @@ class Batch:
         self._check(self.lib.paro_batch_info(self.h, *[ctypes.byref(x) for x in v], ctypes.byref(k)))
         return dict(problems=v[0].value, items=v[1].value, launches_per_apply=v[2].value, grid=v[3].value,
                     kernels_per_step=k.value)
+
+    def tuning(self):
+        """The autotuner's table: rows (launches per apply, grid, sticks per unit, plane points per unit, ms)."""
+        n = ctypes.c_int()
+        self._check(self.lib.paro_batch_tuning(self.h, 0, ctypes.byref(n), None))
+        rows = np.zeros((max(n.value, 1), 5))
+        self._check(self.lib.paro_batch_tuning(self.h, n.value, ctypes.byref(n), _dptr(rows)))
+        return rows[: n.value]
 
     def close(self):
         if self.h:

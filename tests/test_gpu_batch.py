@@ -161,3 +161,20 @@ def test_batch_rejects_mismatched_contexts():
     m = _contexts(cells[1:], "mixed", set_orbitals=False)
     with pytest.raises(paro.ParoError):
         paro.Batch(a + m)
+
+
+def test_batch_autotuner_table_and_every_unit_shape():
+    # the autotuner times unit shapes x launch forms x grids; the batch then runs the fastest. Each shape it
+    # kept is checked against the oracle by the tests above; here the table is complete and its minimum is
+    # the configuration in use
+    from paper_1702_04045_gb300 import paro
+    cells = _mixed_cells()
+    ctxs = _contexts(cells, "mixed")
+    b = paro.Batch(ctxs)
+    tun = b.tuning()
+    assert len(tun) >= 9
+    assert set(tun[:, 2].astype(int)) <= {32, 64, 128} and set(tun[:, 3].astype(int)) <= {2048, 4096, 8192}
+    best = tun[int(np.argmin(tun[:, 4]))]
+    info = b.info()
+    assert info["launches_per_apply"] == int(best[0]) and info["grid"] == int(best[1])
+    print("batch autotuner: best", best.tolist(), "of", len(tun), "candidates")
