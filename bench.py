@@ -189,8 +189,8 @@ def launch_work(name: str, s):
 # DRAM bytes per launch from one ncu capture, valid only for the kernel source it was taken on
 # (sha256 prefix of the file defining the kernel); otherwise the roofline's traffic is null.
 TRAFFIC = {
-    # k_plane_reg<float, 72, 72>, one full 144-band launch: 84.24 MB read + 24.07 MB written
-    "k_plane<f32>": (108304640, "paper_1702_04045_gb300/csrc/hpsi_passes_reg.cuh", "712e0592f863882b"),
+    # k_plane_reg<float, 72, 72, 9>, one full 144-band launch: 84.24 MB read + 24.14 MB written
+    "k_plane<f32>": (108380160, "paper_1702_04045_gb300/csrc/hpsi_passes_reg.cuh", "17078b132bc7da4c"),
 }
 
 

@@ -1065,10 +1065,50 @@ __global__ void k_band_norm2(int npw, const cplx<T>* __restrict__ x, int ldx, do
   if (threadIdx.x == 0) out[b] = acc;
 }
 
+// chunked form for long rows: partial sums per (band, chunk of 2048), then the chunks in order
+template <typename T>
+__global__ void k_band_norm2_part(int npw, const cplx<T>* __restrict__ x, int ldx, double* __restrict__ part) {
+  __shared__ double red[32];
+  const int b = blockIdx.y, ch = blockIdx.x, nch = gridDim.x;
+  const cplx<T>* xb = x + (size_t)b * ldx;
+  const int g0 = ch * 2048, g1 = min(npw, g0 + 2048);
+  double acc = 0.0;
+  if constexpr (sizeof(T) == 4) {
+    float hi = 0.f, lo = 0.f;
+    for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) two_sum_acc(hi, lo, fmaf(xb[g].x, xb[g].x, xb[g].y * xb[g].y));
+    acc = (double)hi + (double)lo;
+  } else {
+    for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+      const double re = xb[g].x, im = xb[g].y;
+      acc += re * re + im * im;
+    }
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) part[(size_t)b * nch + ch] = acc;
+}
+
+__global__ void k_band_norm2_sum(int nb, int nch, const double* __restrict__ part, double* __restrict__ out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  double s = 0.0;
+  for (int ch = 0; ch < nch; ++ch) s += part[(size_t)b * nch + ch];
+  out[b] = s;
+}
+
 template <typename T>
 int band_norms(Ctx* c, int nb, int npw, const cplx<T>* x, int ldx, double* out_dev) {
-  k_band_norm2<T><<<nb, 256, 0, c->stream>>>(npw, x, ldx, out_dev);
-  PARO_LAUNCH(c, "k_band_norm2");
+  const int nch = (npw + 2047) / 2048;
+  if (nch <= 2) {
+    k_band_norm2<T><<<nb, 256, 0, c->stream>>>(npw, x, ldx, out_dev);
+    PARO_LAUNCH(c, "k_band_norm2");
+    return PARO_OK;
+  }
+  double* part = static_cast<double*>(ws_get(c, "band_norm_part", (size_t)nb * nch * sizeof(double)));
+  if (!part) return PARO_ERR_CUDA;
+  k_band_norm2_part<T><<<dim3(nch, nb), 256, 0, c->stream>>>(npw, x, ldx, part);
+  PARO_LAUNCH(c, "k_band_norm2_part");
+  k_band_norm2_sum<<<(nb + 127) / 128, 128, 0, c->stream>>>(nb, nch, part, out_dev);
+  PARO_LAUNCH(c, "k_band_norm2_sum");
   return PARO_OK;
 }
 
