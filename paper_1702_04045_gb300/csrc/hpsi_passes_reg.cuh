@@ -287,7 +287,7 @@ static int passes_reg_dispatch(Ctx* c, const Basis& B, int nb, const cplx<T>* ps
   *used = false;
   const int n = c->N[0];
   if (c->N[1] != n || c->N[2] != n) return PARO_OK;
-  if ((size_t)sizeof(cplx<T>) * (2 * n + n * (n + 1)) > 227 * 1024) return PARO_OK;
+  if ((size_t)sizeof(cplx<T>) * (2 * n + n * (n + (n == 72 ? 2 : 1))) > 227 * 1024) return PARO_OK;  // PlaneStride
   *used = true;
   switch (n) {
     case 32: return passes_reg<T, 32>(c, B, nb, psi, S, hpsi, shift, active, vplane, acc);
@@ -303,8 +303,8 @@ static int passes_reg_dispatch(Ctx* c, const Basis& B, int nb, const cplx<T>* ps
 // x of each band, |psi(r)|^2 summed in FP64 in shared memory, the group's plane written to part.
 // TACC: accumulator of the |psi|^2 sum over the group's bands (at most gsize = 8): float for FP32 orbitals
 // (an 8-term FP32 sum, the groups then summed in FP64 by the caller), double for FP64 orbitals.
-template <typename T, int N1, int N2, typename TACC>
-__global__ void __launch_bounds__(256) k_plane_density_reg(const cplx<T>* __restrict__ S, int ncol, int nbands,
+template <typename T, int N1, int N2, typename TACC, int NW = PlaneWarps<N1>::value>
+__global__ void __launch_bounds__(32 * NW) k_plane_density_reg(const cplx<T>* __restrict__ S, int ncol, int nbands,
                                                            int gsize, const int* __restrict__ col_x,
                                                            const int* __restrict__ col_y,
                                                            const int* __restrict__ xrows, int nxr,
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(256) k_plane_density_reg(const cplx<T>* __rest
                                                            double* __restrict__ part) {
   using SX = LineShape<N1>;
   using SY = LineShape<N2>;
-  constexpr int LS = N2 + 1;
+  constexpr int LS = PlaneStride<N2>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* tx = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* ty = tx + N1;
@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(256) k_plane_density_reg(const cplx<T>* __rest
 
 template <typename T, int N, typename TACC>
 static size_t density_reg_smem() {
-  return (size_t)sizeof(cplx<T>) * (2 * N + N * (N + 1)) + (size_t)N * N * sizeof(TACC);
+  return (size_t)sizeof(cplx<T>) * (2 * N + N * PlaneStride<N>::value) + (size_t)N * N * sizeof(TACC);
 }
 
 template <typename T, int N, typename TACC>
@@ -395,7 +395,7 @@ static int density_planes_reg_acc(Ctx* c, const Basis& B, const cplx<T>* S, int 
   int st;
   if ((st = set_smem_once(c, k_plane_density_reg<T, N, N, TACC>, done))) return st;
   const size_t smem = density_reg_smem<T, N, TACC>();
-  k_plane_density_reg<T, N, N, TACC><<<dim3(N, ngrp), 256, smem, c->stream>>>(
+  k_plane_density_reg<T, N, N, TACC><<<dim3(N, ngrp), 32 * PlaneWarps<N>::value, smem, c->stream>>>(
       S, B.ncol, nbands, gsize, B.d_col_x, B.d_col_y, B.d_xrows, B.nxr, tw_of<T>(c, 0), tw_of<T>(c, 1), wfac, part);
   PARO_LAUNCH(c, "k_plane_density_reg");
   return PARO_OK;
@@ -420,7 +420,8 @@ int density_planes_reg(Ctx* c, int ik, const cplx<T>* S, int nbands, int ngrp, i
   const int n = c->N[0];
   if (c->N[1] != n || c->N[2] != n) return PARO_OK;
   const size_t acc_bytes = (sizeof(T) == 4 && gsize <= 8) ? sizeof(float) : sizeof(double);
-  if ((size_t)sizeof(cplx<T>) * (2 * n + n * (n + 1)) + (size_t)n * n * acc_bytes > 227 * 1024) return PARO_OK;
+  if ((size_t)sizeof(cplx<T>) * (2 * n + n * (n + (n == 72 ? 2 : 1))) + (size_t)n * n * acc_bytes > 227 * 1024)
+    return PARO_OK;  // the plane at its PlaneStride and the accumulator
   const Basis& B = c->bases[ik];
   *used = true;
   switch (n) {
