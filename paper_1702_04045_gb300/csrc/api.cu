@@ -47,6 +47,47 @@ void* ws_get(Ctx* c, const char* name, size_t bytes) {
   return p;
 }
 
+// pinned buffer `name` of at least `bytes`, once its previous copy has completed
+static Ctx::Pinned* pinned_get(Ctx* c, const char* name, size_t bytes) {
+  Ctx::Pinned& p = c->pinned[name];
+  if (p.ev && cudaEventSynchronize(p.ev) != cudaSuccess) return nullptr;
+  if (p.bytes < bytes) {
+    if (p.h) cudaFreeHost(p.h);
+    p.h = nullptr;
+    p.bytes = 0;
+    if (cudaMallocHost(&p.h, bytes) != cudaSuccess) return nullptr;
+    p.bytes = bytes;
+  }
+  if (!p.ev && cudaEventCreateWithFlags(&p.ev, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+  return &p;
+}
+
+int h2d_async(Ctx* c, const char* name, void* dst, const void* src, size_t bytes) {
+  if (!bytes) return PARO_OK;
+  Ctx::Pinned* p = pinned_get(c, name, bytes);
+  if (!p) return fail(c, PARO_ERR_CUDA, std::string("pinned staging buffer ") + name);
+  std::memcpy(p->h, src, bytes);
+  PARO_CU(c, cudaMemcpyAsync(dst, p->h, bytes, cudaMemcpyHostToDevice, c->stream));
+  PARO_CU(c, cudaEventRecord(p->ev, c->stream));
+  return PARO_OK;
+}
+
+int d2h_async(Ctx* c, const char* name, const void* src, size_t bytes, void** h) {
+  Ctx::Pinned* p = pinned_get(c, name, bytes > 0 ? bytes : 8);
+  if (!p) return fail(c, PARO_ERR_CUDA, std::string("pinned read-back buffer ") + name);
+  if (bytes) PARO_CU(c, cudaMemcpyAsync(p->h, src, bytes, cudaMemcpyDeviceToHost, c->stream));
+  PARO_CU(c, cudaEventRecord(p->ev, c->stream));
+  if (h) *h = p->h;
+  return PARO_OK;
+}
+
+int pinned_wait(Ctx* c, const char* name) {
+  auto it = c->pinned.find(name);
+  if (it == c->pinned.end() || !it->second.ev) return PARO_OK;
+  PARO_CU(c, cudaEventSynchronize(it->second.ev));
+  return PARO_OK;
+}
+
 // ------------------------------------------------------------------------------------------------
 // setup helpers
 // ------------------------------------------------------------------------------------------------
@@ -214,6 +255,7 @@ static int setup_bases(Ctx* c) {
   return check_fft_support(c, c->prec == PARO_MIXED ? 8 : 16);
 }
 
+// PCG shift per k-point: below the spectrum of H by the bound V_min + sum of the negative KB terms, - 1/2
 static void update_sigma(Ctx* c) {
   c->sigma_k.assign(c->nk, 0.0);
   for (int ik = 0; ik < c->nk; ++ik) {
@@ -226,6 +268,19 @@ static void update_sigma(Ctx* c) {
       }
     c->sigma_k[ik] = lb - 0.5;
   }
+}
+
+int veff_stats(Ctx* c) {
+  if (c->vstats_pending) {
+    int st = pinned_wait(c, "vstats");
+    if (st) return st;
+    const double* h = static_cast<const double*>(c->pinned["vstats"].h);
+    c->vmean = h[0] / c->ngrid;
+    c->vmin = h[1];
+    c->vstats_pending = false;
+  }
+  update_sigma(c);
+  return PARO_OK;
 }
 
 static int alloc_orbitals(Ctx* c, Basis& b) {
@@ -340,12 +395,16 @@ static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal, cplx<T>
   } else if ((st = residual_norms(c, nb, npw, b.d_psi, b.d_hpsi, w, res))) {
     return st;
   }
-  b.eps.resize(nb);
-  b.res.resize(nb);
-  PARO_CU(c, cudaMemcpyAsync(b.eps.data(), w, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  PARO_CU(c, cudaMemcpyAsync(b.res.data(), res, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  PARO_CU(c, cudaStreamSynchronize(c->stream));
-  if ((st = tc_check(c))) return st;
+  // Ritz values, residual norms and the tensor-core error flag come back with one wait
+  void *he = nullptr, *hr = nullptr;
+  const int* htc = nullptr;
+  if ((st = d2h_async(c, "proj_eps", w, nb * sizeof(double), &he)) ||
+      (st = d2h_async(c, "proj_res", res, nb * sizeof(double), &hr)) || (st = tc_flag_readback(c, &htc)) ||
+      (st = pinned_wait(c, htc ? "tc_err" : "proj_res")))
+    return st;
+  b.eps.assign(static_cast<const double*>(he), static_cast<const double*>(he) + nb);
+  b.res.assign(static_cast<const double*>(hr), static_cast<const double*>(hr) + nb);
+  if (htc && *htc) return fail(c, PARO_ERR_TIMEOUT, "tensor-core product: mbarrier wait gave up");
   b.have_psi = true;
   return PARO_OK;
 }
@@ -367,12 +426,14 @@ static int source_rhs(Ctx* c, int ik, bool alg2, cplx<T>* rhs) {
   double* f = static_cast<double*>(ws_get(c, "rhs_f", (size_t)nb * sizeof(double)));
   double2* tmp = static_cast<double2*>(ws_get(c, "rhs_tmp", (size_t)nb * npw * sizeof(double2)));
   if (!f || !tmp) return PARO_ERR_CUDA;
+  int st = veff_stats(c);
+  if (st) return st;
   std::vector<double> hf(nb);
   for (int i = 0; i < nb; ++i) hf[i] = alg2 ? b.eps[i] : b.eps[i] - c->sigma_k[ik];
-  PARO_CU(c, cudaMemcpyAsync(f, hf.data(), nb * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if ((st = h2d_async(c, "rhs_f", f, hf.data(), nb * sizeof(double)))) return st;
   if (sizeof(T) == 4 && !alg2 && b.d_psi32)  // (eps - sigma) psi straight from the FP32 orbitals
     return scale_rows<float>(c, nb, npw, b.d_psi32, f, reinterpret_cast<float2*>(rhs));
-  int st = scale_rows<double>(c, nb, npw, b.d_psi, f, tmp);
+  st = scale_rows<double>(c, nb, npw, b.d_psi, f, tmp);
   if (st) return st;
   if (alg2) {
     k_axpy_rows<double><<<dim3((npw + 255) / 256, nb), 256, 0, c->stream>>>(npw, tmp, b.d_hpsi, -1.0);
@@ -487,6 +548,18 @@ static double fermi_g(double x) {  // 1 / (1 + e^x) without overflow
 
 int update_occupations(Ctx* c) {
   const int nk = c->nk, nb = c->nb;
+  // unchanged Ritz values, kT and electron count leave the occupations as they are (the SCF iteration asks
+  // at its start for those of the values its last energy evaluation used)
+  std::vector<double> key{c->kT, (double)c->nocc};
+  if (c->kT > 0) {
+    key.reserve(2 + (size_t)nk * nb);
+    for (int ik = 0; ik < nk; ++ik) {
+      if ((int)c->bases[ik].eps.size() < nb) return fail(c, PARO_ERR_STATE, "occupations: no Ritz values");
+      key.insert(key.end(), c->bases[ik].eps.begin(), c->bases[ik].eps.begin() + nb);
+    }
+  }
+  if (key == c->occ_key && c->occ.size() == (size_t)nk * nb) return PARO_OK;
+  c->occ_key.clear();
   c->occ.assign((size_t)nk * nb, 0.0);
   if (c->kT <= 0) {
     for (int ik = 0; ik < nk; ++ik)
@@ -494,31 +567,47 @@ int update_occupations(Ctx* c) {
     c->nocc_eff = c->nocc;
     c->mu = 0;
     c->mts = 0;
+    c->occ_key.swap(key);
     return PARO_OK;
   }
   double lo = 1e300, hi = -1e300;
-  for (int ik = 0; ik < nk; ++ik) {
-    if ((int)c->bases[ik].eps.size() < nb) return fail(c, PARO_ERR_STATE, "occupations: no Ritz values");
+  for (int ik = 0; ik < nk; ++ik)
     for (int i = 0; i < nb; ++i) {
       lo = std::min(lo, c->bases[ik].eps[i]);
       hi = std::max(hi, c->bases[ik].eps[i]);
     }
-  }
   const double kT = c->kT, nel = 2.0 * c->nocc;
-  lo -= 40 * kT + 1;
+  lo -= 40 * kT + 1;  // N(lo) < nel < N(hi)
   hi += 40 * kT + 1;
-  auto count = [&](double mu) {
-    double n = 0;
+  // N(mu) - nel and its derivative sum_k w_k sum_i 2 g (1 - g) / kT
+  auto excess = [&](double mu, double* dn) {
+    double n = 0, d = 0;
     for (int ik = 0; ik < nk; ++ik)
-      for (int i = 0; i < nb; ++i) n += c->kw[ik] * 2.0 * fermi_g((c->bases[ik].eps[i] - mu) / kT);
-    return n;
+      for (int i = 0; i < nb; ++i) {
+        const double g = fermi_g((c->bases[ik].eps[i] - mu) / kT);
+        n += c->kw[ik] * 2.0 * g;
+        d += c->kw[ik] * 2.0 * g * (1.0 - g);
+      }
+    *dn = d / kT;
+    return n - nel;
   };
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (count(mid) < nel) lo = mid;
-    else hi = mid;
+  // N(mu) = nel by Newton's method inside a shrinking bracket, bisecting whenever the Newton point leaves the
+  // bracket or the step has not at least halved since the one before; ends when mu no longer moves
+  double mu = 0.5 * (lo + hi), d = 0, step = hi - lo, step_prev = step;
+  double f = excess(mu, &d);
+  for (int it = 0; it < 400 && f != 0.0; ++it) {
+    if (f < 0) lo = mu;
+    else hi = mu;
+    const double newton = d > 0 ? mu - f / d : lo;
+    const bool take = newton > lo && newton < hi && std::fabs(2.0 * f) <= std::fabs(step_prev * d);
+    const double next = take ? newton : 0.5 * (lo + hi);
+    step_prev = step;
+    step = next - mu;
+    if (next == mu || next <= lo || next >= hi) break;
+    mu = next;
+    f = excess(mu, &d);
   }
-  c->mu = 0.5 * (lo + hi);
+  c->mu = mu;
   double ts = 0;
   int neff = 0;
   std::vector<double> sq((size_t)nk * nb);
@@ -535,10 +624,9 @@ int update_occupations(Ctx* c) {
   c->mts = -ts;
   c->nocc_eff = std::max(neff, 1);
   if (!c->d_occ_sqrt) PARO_CU(c, cudaMalloc(&c->d_occ_sqrt, (size_t)nk * nb * sizeof(double)));
-  PARO_CU(c, cudaMemcpyAsync(c->d_occ_sqrt, sq.data(), sq.size() * sizeof(double), cudaMemcpyHostToDevice,
-                             c->stream));
-  // the host vector is read by the copy engine until the stream reaches it
-  PARO_CU(c, cudaStreamSynchronize(c->stream));
+  int st = h2d_async(c, "occ_sqrt", c->d_occ_sqrt, sq.data(), sq.size() * sizeof(double));
+  if (st) return st;
+  c->occ_key.swap(key);
   return PARO_OK;
 }
 
@@ -578,7 +666,7 @@ static int source_step(Ctx* c, int ik, int alg, double rel_tol, int max_it, cplx
 
 // Cholesky-orthonormalise the first nx rows of X in place (Y = conj(L)^{-1} X); Gram in FP64.
 template <typename T>
-static int orthonormalize(Ctx* c, int ik, cplx<T>* X, int nx, cplx<T>* HX = nullptr) {
+static int orthonormalize(Ctx* c, int ik, cplx<T>* X, int nx, cplx<T>* HX = nullptr, bool defer = false) {
   const int npw = c->bases[ik].npw;
   const bool f64 = sizeof(T) == 8;
   double2* S = static_cast<double2*>(ws_get(c, "proj_S", (size_t)nx * nx * sizeof(double2)));
@@ -590,7 +678,7 @@ static int orthonormalize(Ctx* c, int ik, cplx<T>* X, int nx, cplx<T>* HX = null
     ProfTag t(c, "gram");
     if ((st = gemm_cn<T, T, T>(c, nx, nx, npw, X, npw, X, npw, S, nx, true, true))) return st;
     if (gamma_on(c) && (st = gamma_real_matrix(c, nx, S))) return st;
-    if ((st = chol_inv(c, nx, S, G))) return st;
+    if ((st = chol_inv(c, nx, S, G, defer))) return st;
   }
   ProfTag t(c, "orth");
   if ((st = gemm_wx<T, T>(c, nx, npw, nx, G, nx, true, nullptr, X, npw, Y, npw, 0.0, nullptr, true))) return st;
@@ -690,6 +778,7 @@ static int scf_iteration(Ctx* c, const paro_scf_opts* o) {
   std::vector<cplx<T>*> xs(c->nk), hxs(c->nk, nullptr);
   std::vector<int> nxs(c->nk);
   int st;
+  c->chol_pending.clear();  // flags left by an iteration that stopped early
   // the source solutions x_i carry the occupations of the eps_i^n they are solved with
   if ((st = update_occupations(c))) return st;
   bool carry = false;  // some k-point carries H X this iteration (then dV is needed)
@@ -702,7 +791,8 @@ static int scf_iteration(Ctx* c, const paro_scf_opts* o) {
     }
     if ((st = source_step<T>(c, ik, o->alg, o->inner_rel_tol, o->inner_max_it, xs[ik], &nxs[ik], hxs[ik])))
       return st;
-    if ((st = orthonormalize<T>(c, ik, xs[ik], nxs[ik], hxs[ik]))) return st;
+    // a Cholesky breakdown is reported below, before anything of the state changes
+    if ((st = orthonormalize<T>(c, ik, xs[ik], nxs[ik], hxs[ik], true))) return st;
   }
   // the potential planes of the inner solves, to form dV once the mixing has moved the potential
   T* dv = nullptr;
@@ -720,10 +810,10 @@ static int scf_iteration(Ctx* c, const paro_scf_opts* o) {
   {
     ProfTag t(c, "mix");
     if ((st = density<T>(c, dens_src.data(), rho_out))) return st;
+    if ((st = chol_check(c))) return st;  // the GPU still has the density pass queued
     if ((st = pulay_mix(c, rho_out, o->pulay_depth, o->pulay_beta))) return st;
     if ((st = veff_from_density(c, c->d_rho_in, nullptr, nullptr))) return st;
   }
-  update_sigma(c);
   if (carry) {
     k_plane_delta<T><<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, vplane_dev<T>(c), dv);
     PARO_LAUNCH(c, "k_plane_delta");
@@ -872,8 +962,7 @@ static int set_ecut(Ctx* c, double ecut_new) {
       }
       if ((st = set_veff_device(c, fr))) return st;
     }
-    update_sigma(c);
-  }
+    }
   // 5. the orbitals embedded in the new bases, eigenvalue estimates kept
   for (int ik = 0; ik < c->nk; ++ik) {
     if (!old_psi[ik]) continue;
@@ -997,6 +1086,10 @@ void paro_destroy(paro_ctx* ctx) {
     cudaEventDestroy(e.b);
   }
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
+  for (auto& kv : c->pinned) {
+    if (kv.second.ev) cudaEventDestroy(kv.second.ev);
+    if (kv.second.h) cudaFreeHost(kv.second.h);
+  }
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete ctx;
 }
@@ -1025,7 +1118,10 @@ int paro_miller(const paro_ctx* ctx, int ik, int* hkl) {
 int paro_sigma(const paro_ctx* ctx, double* sigma) {
   if (!ctx || !sigma) return PARO_ERR_ARG;
   if (!ctx->c.have_veff) return PARO_ERR_STATE;
-  *sigma = ctx->c.sigma_k[0];
+  Ctx* c = const_cast<Ctx*>(&ctx->c);  // completes the pending read-back of the potential's minimum
+  int st = veff_stats(c);
+  if (st) return st;
+  *sigma = c->sigma_k[0];
   return PARO_OK;
 }
 
@@ -1038,7 +1134,6 @@ int paro_set_local_pp(paro_ctx* ctx, double Z, double rc, double A, double a) {
   c->have_pp = true;
   c->e_ewald = ewald(c);
   if ((st = set_veff_device(c, c->d_vloc))) return st;
-  update_sigma(c);
   return PARO_OK;
 }
 
@@ -1057,7 +1152,6 @@ int paro_set_kb(paro_ctx* ctx, double rc, const double* D) {
   if (!c->d_dvec) PARO_CU(c, cudaMalloc(&c->d_dvec, std::max(c->nproj, 1) * sizeof(double)));
   PARO_CU(c, cudaMemcpy(c->d_dvec, dv.data(), c->nproj * sizeof(double), cudaMemcpyHostToDevice));
   c->have_kb = c->nproj > 0;
-  update_sigma(c);
   return PARO_OK;
 }
 
@@ -1089,7 +1183,6 @@ int paro_set_positions(paro_ctx* ctx, const double* pos) {
     }
     if ((st = set_veff_device(c, v))) return st;
   }
-  update_sigma(c);
   for (int ik = 0; ik < c->nk; ++ik)
     if (c->bases[ik].have_psi && (st = reproject(c, ik))) return st;
   return PARO_OK;
@@ -1104,7 +1197,6 @@ int paro_set_veff(paro_ctx* ctx, const double* v_r, int on_device) {
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
   int st = set_veff_device(c, tmp);
   if (st) return st;
-  update_sigma(c);
   return PARO_OK;
 }
 
@@ -1120,7 +1212,6 @@ int paro_set_veff_rest(paro_ctx* ctx, const double* v_rest, int on_device) {
   PARO_LAUNCH(c, "k_axpy_grid");
   int st = set_veff_device(c, tmp);
   if (st) return st;
-  update_sigma(c);
   return PARO_OK;
 }
 
@@ -1151,7 +1242,6 @@ int paro_set_density(paro_ctx* ctx, const double* rho, int on_device) {
   int st = veff_from_density(c, c->d_rho_in, nullptr, nullptr);
   if (st) return st;
   c->have_rho = true;
-  update_sigma(c);
   return PARO_OK;
 }
 
@@ -1254,9 +1344,11 @@ int paro_solve_source(paro_ctx* ctx, int ik, int nb, int dtype, const double* ep
   const int npw = c->bases[ik].npw;
   double* f = static_cast<double*>(ws_get(c, "ss_f", (size_t)nb * sizeof(double)));
   if (!f) return PARO_ERR_CUDA;
+  int st0 = veff_stats(c);
+  if (st0) return st0;
   std::vector<double> hf(nb);
   for (int i = 0; i < nb; ++i) hf[i] = eps[i] - c->sigma_k[ik];
-  PARO_CU(c, cudaMemcpyAsync(f, hf.data(), nb * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if ((st0 = h2d_async(c, "ss_f", f, hf.data(), nb * sizeof(double)))) return st0;
   if (dtype == PARO_C64) {
     double2* rhs = static_cast<double2*>(ws_get(c, "src_rhs64", (size_t)nb * npw * sizeof(double2)));
     if (!rhs) return PARO_ERR_CUDA;
@@ -1375,8 +1467,7 @@ int paro_scf_step(paro_ctx* ctx, const paro_scf_opts* o, double energy[7], doubl
     k_fill<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, 2.0 * c->nocc / c->omega, c->d_rho_in);
     PARO_LAUNCH(c, "k_fill");
     if ((st = veff_from_density(c, c->d_rho_in, nullptr, nullptr))) return st;
-    update_sigma(c);
-    for (int ik = 0; ik < c->nk; ++ik)
+      for (int ik = 0; ik < c->nk; ++ik)
       if ((st = reproject(c, ik))) return st;
     c->have_rho = true;
     c->scf_iter = 0;

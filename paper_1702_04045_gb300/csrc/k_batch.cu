@@ -1046,7 +1046,8 @@ void free_batch(paro_batch* b) {
 int refresh_scalars(paro_batch* b) {
   // eigenvalues of the current orbitals and each problem's shift, from the contexts
   for (int i = 0; i < b->nprob; ++i) {
-    const Ctx& c = *unwrap(b->ctxs[b->pk[i].first]);
+    Ctx& c = *unwrap(b->ctxs[b->pk[i].first]);
+    if (veff_stats(&c)) return berr(b, PARO_ERR_CUDA, "batch: " + c.err);
     const Basis& B = c.bases[b->pk[i].second];
     if (!B.have_psi || (int)B.eps.size() < c.nb)
       return berr(b, PARO_ERR_STATE, "batch: every context needs orbitals (paro_set_orbitals) first");

@@ -267,13 +267,13 @@ int* tc_err_flag(Ctx* c) {
   return c->d_tc_err;
 }
 
-int tc_check(Ctx* c) {
+int tc_flag_readback(Ctx* c, const int** h) {
+  *h = nullptr;
   if (!c->d_tc_err) return PARO_OK;
-  int h = 0;
-  PARO_CU(c, cudaMemcpyAsync(&h, c->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  PARO_CU(c, cudaStreamSynchronize(c->stream));
-  if (h) return fail(c, PARO_ERR_TIMEOUT, "tensor-core product: mbarrier wait gave up");
-  return PARO_OK;
+  void* p = nullptr;
+  const int st = d2h_async(c, "tc_err", c->d_tc_err, sizeof(int), &p);
+  *h = static_cast<const int*>(p);
+  return st;
 }
 
 template <typename TA, typename TB, typename ACC>
@@ -985,7 +985,20 @@ static int chol_cluster_shape(Ctx* c, int n, Ctx::CholShape* out) {
   return PARO_OK;
 }
 
-int chol_inv(Ctx* c, int n, const double2* s, double2* g) {
+int chol_check(Ctx* c) {
+  int bad = 0;
+  for (const std::string& nm : c->chol_pending) {
+    int st = pinned_wait(c, nm.c_str());
+    if (st) return st;
+    const int h = *static_cast<const int*>(c->pinned[nm].h);
+    if (h && !bad) bad = h;
+  }
+  c->chol_pending.clear();
+  if (bad) return fail(c, PARO_ERR_BREAKDOWN, "Cholesky pivot <= 0 at column " + std::to_string(bad - 1));
+  return PARO_OK;
+}
+
+int chol_inv(Ctx* c, int n, const double2* s, double2* g, bool defer) {
   {
     Ctx::CholShape sh;
     int st;
@@ -1010,6 +1023,12 @@ int chol_inv(Ctx* c, int n, const double2* s, double2* g) {
       else PARO_CU(c, cudaLaunchKernelEx(&cfg, k_chol_cluster, n, s, g, flags));
       ++c->launches;
       prof_end(c, "k_chol_cluster", ev);
+      if (defer) {  // the flag comes back without waiting; chol_check() reads it
+        const std::string nm = "chol_flag_" + std::to_string(c->chol_pending.size());
+        if ((st = d2h_async(c, nm.c_str(), flags, sizeof(int), nullptr))) return st;
+        c->chol_pending.push_back(nm);
+        return PARO_OK;
+      }
       int h = 0;
       PARO_CU(c, cudaMemcpyAsync(&h, flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
       PARO_CU(c, cudaStreamSynchronize(c->stream));

@@ -339,6 +339,8 @@ int minres_run(Ctx* c, int ik, int nb, const cplx<T>* psi, const cplx<T>* hpsi, 
   const Basis& B = c->bases[ik];
   const int npw = B.npw;
   const int nchunk = (npw + kMChunk - 1) / kMChunk;
+  int st0 = veff_stats(c);
+  if (st0) return st0;
   const T pshift = (T)(c->vmean - c->sigma_k[ik]);
   const size_t vb = (size_t)nb * npw * sizeof(cplx<T>);
   const bool f64 = sizeof(T) == 8;
@@ -360,7 +362,7 @@ int minres_run(Ctx* c, int ik, int nb, const cplx<T>* psi, const cplx<T>* hpsi, 
   const dim3 gv(nchunk, nb);
   const int tb = (nb + 127) / 128;
   const T* kin = kin_of_b<T>(B);
-  PARO_CU(c, cudaMemcpyAsync(deps, eps, nb * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if ((st0 = h2d_async(c, "mr_eps", deps, eps, nb * sizeof(double)))) return st0;
   PARO_CU(c, cudaMemsetAsync(flags, 0, 2 * sizeof(int), c->stream));
   // v_1 = P b, z_1 = P D v_1, gamma_1 = sqrt(<z_1, v_1>)
   k_mr_rhs<T><<<gv, kMT, 0, c->stream>>>(npw, nchunk, psi, hpsi, deps, v, part);

@@ -232,6 +232,8 @@ int pcg_run(Ctx* c, int ik, int nb, const cplx<T>* rhs, cplx<T>* x, bool x0_zero
   const Basis& B = c->bases[ik];
   const int npw = B.npw;
   const int nchunk = (npw + kChunk - 1) / kChunk;
+  int st = veff_stats(c);
+  if (st) return st;
   const double sigma = c->sigma_k[ik];
   const T pshift = (T)(c->vmean - sigma);
   const size_t vb = (size_t)nb * npw * sizeof(cplx<T>);
@@ -249,7 +251,6 @@ int pcg_run(Ctx* c, int ik, int nb, const cplx<T>* rhs, cplx<T>* x, bool x0_zero
   const dim3 gv(nchunk, nb);
   const int tb = (nb + 127) / 128;
   PARO_CU(c, cudaMemsetAsync(flags, 0, 2 * sizeof(int), c->stream));
-  int st;
   if (hx) {
     if (x0_zero) PARO_CU(c, cudaMemsetAsync(hx, 0, vb, c->stream));
     else if (hx0) PARO_CU(c, cudaMemcpyAsync(hx, hx0, vb, cudaMemcpyDeviceToDevice, c->stream));
@@ -269,9 +270,9 @@ int pcg_run(Ctx* c, int ik, int nb, const cplx<T>* rhs, cplx<T>* x, bool x0_zero
   PARO_LAUNCH(c, "k_pcg_init");
   k_pcg_band_init<<<tb, 128, 0, c->stream>>>(nb, nchunk, prz, prr, rz, r0n, active, its, flags);
   PARO_LAUNCH(c, "k_pcg_band_init");
-  int hflags[2] = {0, 0};
-  PARO_CU(c, cudaMemcpyAsync(hflags, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  PARO_CU(c, cudaStreamSynchronize(c->stream));
+  // the first step runs without reading the active count back: every orbital with a nonzero initial
+  // residual is active, and the kernels pass over the others
+  int hflags[2] = {1, 0};
   for (int it = 0; it < max_it && hflags[0] > 0; ++it) {
     st = apply_h<T>(c, ik, nb, p, ap, sigma, active);
     if (st) return st;

@@ -453,11 +453,11 @@ int set_veff_device(Ctx* c, const double* v_dev) {
   PARO_LAUNCH(c, "k_min_sum");
   k_min_sum_final<<<1, 32, 0, c->stream>>>(nblk, ms + 2, ms);
   PARO_LAUNCH(c, "k_min_sum_final");
-  double h[2];
-  PARO_CU(c, cudaMemcpyAsync(h, ms, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
-  PARO_CU(c, cudaStreamSynchronize(c->stream));
-  c->vmean = h[0] / c->ngrid;
-  c->vmin = h[1];
+  // the sum and the minimum come back without waiting for the stream; veff_stats() reads them when the
+  // PCG shift is next needed
+  int st = d2h_async(c, "vstats", ms, 2 * sizeof(double), nullptr);
+  if (st) return st;
+  c->vstats_pending = true;
   c->have_veff = true;
   return PARO_OK;
 }
@@ -830,7 +830,7 @@ int density(Ctx* c, const cplx<T>* const* psis, double* rho_dev) {
   double* part = static_cast<double*>(ws_get(c, "dens_sum_part", (nblk + 1) * sizeof(double)));
   double* wk = static_cast<double*>(ws_get(c, "dens_kw", (size_t)c->nk * sizeof(double)));
   if (!part || !wk) return PARO_ERR_CUDA;
-  PARO_CU(c, cudaMemcpyAsync(wk, c->kw.data(), c->nk * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (int st = h2d_async(c, "dens_kw", wk, c->kw.data(), c->nk * sizeof(double))) return st;
   k_grid_sum<<<nblk, 256, 0, c->stream>>>(c->ngrid, rho_dev, part);
   PARO_LAUNCH(c, "k_grid_sum");
   // smeared rows already carry sqrt(f) in their norms; otherwise f = 2
@@ -1109,7 +1109,7 @@ int pulay_mix(Ctx* c, const double* rho_out, int depth, double beta) {
   c->pulay_head = (c->pulay_head + 1) % depth;
   if (c->pulay_n < depth) ++c->pulay_n;
   const int m = c->pulay_n;
-  // oldest first; kept in the context, so the asynchronous copy below may read it after this returns
+  // oldest first
   c->pulay_slots.resize(m);
   for (int i = 0; i < m; ++i) c->pulay_slots[i] = ((c->pulay_head - m + i) % depth + depth) % depth;
   int* dslot = static_cast<int*>(ws_get(c, "pulay_slot", 16 * sizeof(int)));
@@ -1117,7 +1117,7 @@ int pulay_mix(Ctx* c, const double* rho_out, int depth, double beta) {
   double* part = static_cast<double*>(ws_get(c, "pulay_part", (size_t)nblk * 16 * sizeof(double)));
   double* coef = static_cast<double*>(ws_get(c, "pulay_coef", 16 * sizeof(double)));
   if (!dslot || !part || !coef) return PARO_ERR_CUDA;
-  PARO_CU(c, cudaMemcpyAsync(dslot, c->pulay_slots.data(), m * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  if (int st = h2d_async(c, "pulay_slots", dslot, c->pulay_slots.data(), m * sizeof(int))) return st;
   k_pulay_dots<<<nblk, 256, 0, c->stream>>>(n, m, c->d_pulay_res, dslot, slot_new, part);
   PARO_LAUNCH(c, "k_pulay_dots");
   k_pulay_solve<<<1, 256, 0, c->stream>>>(m, nblk, part, dslot, slot_new, c->d_pulay_gram, coef);

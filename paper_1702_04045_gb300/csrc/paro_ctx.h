@@ -82,8 +82,11 @@ struct Ctx {
   double* d_veff = nullptr;       // V_eff(r), C order
   double* d_vplane = nullptr;     // V_eff / N_grid, plane-major [z][x][y]
   float* d_vplane32 = nullptr;
+  // mean and minimum of V_eff and the PCG shift per k-point: read back from the device without waiting
+  // (an event marks the copy); veff_stats() completes the read when a host computation needs them
   double vmean = 0, vmin = 0;
-  std::vector<double> sigma_k;    // PCG shift per k-point
+  std::vector<double> sigma_k;
+  bool vstats_pending = false;
   double e_ewald = 0;
   // SCF state
   double* d_rho_in = nullptr;
@@ -100,6 +103,7 @@ struct Ctx {
   // free energy E - T S (mts = -T S)
   double kT = 0, mu = 0, mts = 0;
   std::vector<double> occ;  // nk x nb, f_ik
+  std::vector<double> occ_key;  // the Ritz values, kT and electron count the occupations were formed from
   int nocc_eff = 0;         // bands per k from the first up to the last with an occupation above 1e-15
   double* d_occ_sqrt = nullptr;  // nk x nb, sqrt(f_ik), for the density of smeared orbitals
   // Gamma-point real-wavefunction mode: the ParO iteration treats its orbitals as real functions (two per
@@ -121,6 +125,14 @@ struct Ctx {
   const char* prof_tag = nullptr;  // phase prefix of recorded names ("pcg", "rr", ...)
   // workspaces by name
   std::map<std::string, std::pair<void*, size_t>> ws;
+  // pinned host buffers by name for the small copies of every iteration, each with the event of its last
+  // copy: a buffer is rewritten only after that copy has completed, so no copy waits for the stream
+  struct Pinned {
+    void* h = nullptr;
+    size_t bytes = 0;
+    cudaEvent_t ev = nullptr;
+  };
+  std::map<std::string, Pinned> pinned;
   int* d_tc_err = nullptr;  // set by a tensor-core kernel whose mbarrier wait gave up
   // FP32 products may run on the tensor cores (3xTF32): inside the inexact inner solves and the adjoint,
   // not in the Rayleigh-Ritz step, the rotations or the energy, which fix the self-consistent result
@@ -129,6 +141,7 @@ struct Ctx {
     int n = -1, dev = -1, kind = 0, cls = 0, thr = 0;
     size_t smem = 0;
   } chol_shape;
+  std::vector<std::string> chol_pending;  // pinned flags of deferred Cholesky breakdown checks
   bool have_inv_g2 = false;  // the 1/|G|^2 table of the Hartree solve is in the "inv_g2" workspace
 };
 
@@ -136,6 +149,15 @@ struct Ctx {
 int fail(Ctx* c, int code, const std::string& msg);
 int cuda_fail(Ctx* c, cudaError_t e, const char* where);
 void* ws_get(Ctx* c, const char* name, size_t bytes);  // nullptr on failure (err set)
+// host -> device copy on the context's stream through the pinned buffer `name`; src may change as soon as
+// this returns, and the call does not wait for the stream (only, rarely, for the buffer's previous copy)
+int h2d_async(Ctx* c, const char* name, void* dst, const void* src, size_t bytes);
+// device -> host copy into the pinned buffer `name` (returned in *h) and an event that marks its end;
+// the host reads *h after pinned_wait(c, name)
+int d2h_async(Ctx* c, const char* name, const void* src, size_t bytes, void** h);
+int pinned_wait(Ctx* c, const char* name);
+// completes a pending read-back of the V_eff mean and minimum and updates the PCG shifts
+int veff_stats(Ctx* c);
 
 #define PARO_CU(c, call)                                               \
   do {                                                                 \
@@ -207,11 +229,16 @@ int gemm_wx_tc(Ctx* c, int M, int N, int K, const double2* W, int ldw, bool wt, 
 // Tensor-core paths enabled (not when PARO_NO_TC is set in the environment), and their sticky error flag.
 bool tc_enabled();
 int* tc_err_flag(Ctx* c);
-int tc_check(Ctx* c);  // PARO_ERR_TIMEOUT once a tensor-core kernel gave up waiting (synchronises)
+// enqueues the read-back of the tensor-core error flag (set once a kernel gave up waiting) into pinned
+// memory; *h (null when no tensor-core kernel ran) is valid after pinned_wait(c, "tc_err")
+int tc_flag_readback(Ctx* c, const int** h);
 // The context behind a C-ABI handle (api.cu).
 Ctx* unwrap(paro_ctx* h);
 // Cholesky S = L L^H (n x n, row-major, device), then writes G = conj(L)^{-1} (lower) into g.
-int chol_inv(Ctx* c, int n, const double2* s, double2* g);
+// defer: the breakdown flag of the cluster form is read back without waiting, and chol_check() (which waits
+// for it) reports a breakdown; the inverse is meaningless until then
+int chol_inv(Ctx* c, int n, const double2* s, double2* g, bool defer = false);
+int chol_check(Ctx* c);
 // Hermitian eigensolver, FP64 (k_eigh.cu): w ascending, v columns = eigenvectors (row-major n x n).
 int eigh(Ctx* c, int n, const double2* a, double* w, double2* v);
 // The same result from an FP32 solve refined in FP64 (k_eigh_mixed.cu); FP64 solver for n > 160. Each
