@@ -175,12 +175,17 @@ static int build_basis(Ctx* c, Basis& b) {
   std::sort(xr.begin(), xr.end());
   xr.erase(std::unique(xr.begin(), xr.end()), xr.end());
   b.nxr = (int)xr.size();
+  std::vector<int> xrc(c->N[0], -1);
+  for (int r = 0; r < b.nxr; ++r) xrc[xr[r]] = r;
+  std::vector<int> stick_of((size_t)b.nxr * c->N[1], -1);
+  for (int cc = 0; cc < b.ncol; ++cc) stick_of[(size_t)xrc[col_x[cc]] * c->N[1] + col_y[cc]] = cc;
   std::vector<float> kin32(b.kin.begin(), b.kin.end());
   int st;
   if ((st = upload(c, &b.d_miller, mil)) || (st = upload(c, &b.d_kin, b.kin)) || (st = upload(c, &b.d_kin32, kin32)) ||
       (st = upload(c, &b.d_col_x, col_x)) || (st = upload(c, &b.d_col_y, col_y)) ||
       (st = upload(c, &b.d_col_off, col_off)) || (st = upload(c, &b.d_g_col, g_col)) ||
-      (st = upload(c, &b.d_g_z, g_z)) || (st = upload(c, &b.d_xrows, xr)))
+      (st = upload(c, &b.d_g_z, g_z)) || (st = upload(c, &b.d_xrows, xr)) || (st = upload(c, &b.d_xrow_c, xrc)) ||
+      (st = upload(c, &b.d_stick_of, stick_of)))
     return st;
   return PARO_OK;
 }
@@ -189,7 +194,7 @@ static int build_basis(Ctx* c, Basis& b) {
 static void free_basis(Basis& b) {
   void** ps[] = {(void**)&b.d_miller, (void**)&b.d_kin,    (void**)&b.d_kin32,  (void**)&b.d_col_x,
                  (void**)&b.d_col_y,  (void**)&b.d_col_off, (void**)&b.d_g_col,  (void**)&b.d_g_z,
-                 (void**)&b.d_xrows,  (void**)&b.d_beta,   (void**)&b.d_beta32, (void**)&b.d_prec_base,
+                 (void**)&b.d_xrows,  (void**)&b.d_xrow_c, (void**)&b.d_stick_of, (void**)&b.d_beta,   (void**)&b.d_beta32, (void**)&b.d_prec_base,
                  (void**)&b.d_mg,
                  (void**)&b.d_psi,    (void**)&b.d_hpsi,   (void**)&b.d_psi32,  (void**)&b.d_hpsi32};
   for (void** p : ps) {

@@ -73,50 +73,70 @@ template <> struct PlaneWarps<72> { static constexpr int value = 9; };
 template <int N> struct PlaneStride { static constexpr int value = N + 1; };
 template <> struct PlaneStride<72> { static constexpr int value = 74; };
 
+// Resident CTAs per SM the plane pass is compiled for (a register cap of 65536 / (CTAs x threads)): the
+// compact FP32 plane of the 72-point grid lets four CTAs of nine warps share an SM.
+template <typename T, int N> struct PlaneMinBlocks { static constexpr int value = 1; };
+template <> struct PlaneMinBlocks<float, 72> { static constexpr int value = 4; };
+
+// Shared memory of the plane pass: the warps' exchange tiles, the row-offset table and the nxr stick rows
+// of the plane.
+template <typename T, int N>
+static size_t plane_reg_smem(int nxr) {
+  constexpr int kWT = PlaneLines<T, N>::kWarpTile;
+  return sizeof(cplx<T>) * (PlaneWarps<N>::value * kWT + (size_t)nxr * PlaneStride<N>::value) + N * sizeof(int);
+}
+
+// The plane is kept compact in shared memory: only its nxr rows that hold sticks (row r at Pl + r LS is
+// grid row xrows[r]; xrow_c maps a grid row to r or -1). The inverse pass along y reads its lines straight
+// from the stick buffer (stick_of[r N2 + j2]: the stick at grid row xrows[r], column j2, or -1) and the
+// forward pass writes them straight back, so the plane is neither cleared nor scattered nor gathered. The
+// inverse transform along x reads the rows without sticks as the zeros they are, and the forward transform
+// writes back only the stick rows, which are all that the forward pass along y reads. Two block barriers
+// per plane; the twiddles are read through the L1 cache.
 template <typename T, int N1, int N2, int NW = PlaneWarps<N1>::value>
-__global__ void __launch_bounds__(32 * NW) k_plane_reg(cplx<T>* __restrict__ S, int ncol, const int* __restrict__ col_x,
-                                                   const int* __restrict__ col_y, const int* __restrict__ xrows,
-                                                   int nxr, const cplx<T>* __restrict__ twx,
-                                                   const cplx<T>* __restrict__ twy, const T* __restrict__ vplane,
-                                                   const int* __restrict__ active) {
+__global__ void __launch_bounds__(32 * NW, PlaneMinBlocks<T, N1>::value)
+    k_plane_reg(cplx<T>* __restrict__ S, int ncol, const int* __restrict__ stick_of, const int* __restrict__ xrow_c,
+                int nxr, const cplx<T>* __restrict__ twx, const cplx<T>* __restrict__ twy,
+                const T* __restrict__ vplane, const int* __restrict__ active) {
   using SX = LineShape<N1>;
   using SY = LineShape<N2>;
   using LX = PlaneLines<T, N1>;
   using LY = PlaneLines<T, N2>;
   constexpr int LS = PlaneStride<N2>::value;
+  static_assert(N1 % 4 == 0, "row-offset table keeps the plane 16-byte aligned");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<T>* tx = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* ty = tx + N1;
-  cplx<T>* Pl = ty + N2;
-  cplx<T>* tiles = Pl + N1 * LS;  // per warp: the larger of the two lines' kWarpTile
+  cplx<T>* tiles = reinterpret_cast<cplx<T>*>(smem_raw);  // per warp: the larger of the two lines' kWarpTile
   constexpr int kWT = LX::kWarpTile > LY::kWarpTile ? LX::kWarpTile : LY::kWarpTile;
+  int* roff = reinterpret_cast<int*>(tiles + NW * kWT);  // grid row -> offset of its compact row, or -1
+  cplx<T>* Pl = reinterpret_cast<cplx<T>*>(roff + N1);
   const int z = blockIdx.x, b = blockIdx.y, N3 = gridDim.x;
   if (active != nullptr && active[b] == 0) return;
-  for (int i = threadIdx.x; i < N1; i += blockDim.x) tx[i] = twx[i];
-  for (int i = threadIdx.x; i < N2; i += blockDim.x) ty[i] = twy[i];
-  for (int i = threadIdx.x; i < N1 * LS; i += blockDim.x) Pl[i] = mk<T>(0, 0);
-  __syncthreads();
+  for (int i = threadIdx.x; i < N1; i += blockDim.x) {
+    const int r = xrow_c[i];
+    roff[i] = r >= 0 ? r * LS : -1;
+  }
   cplx<T>* Sz = S + ((size_t)b * N3 + z) * ncol;
-  for (int c = threadIdx.x; c < ncol; c += blockDim.x) Pl[col_x[c] * LS + col_y[c]] = Sz[c];
-  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  {  // inverse along y, rows that hold sticks
+  {  // inverse along y, rows that hold sticks, from the stick buffer
     constexpr int Q = SY::Q, P = SY::P, G = 32 / P;
     const int grp = lane / P, p = lane % P, pr = bitrev_lane<P>(p);
     for (int r0 = warp * G; r0 < nxr; r0 += nw * G) {
       const int r = r0 + grp;
       const bool ok = r < nxr;
-      cplx<T>* row = Pl + (ok ? xrows[r] : 0) * LS;
+      const int* so = stick_of + (size_t)(ok ? r : 0) * N2;
       cplx<T> v[Q];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) v[q] = ok ? row[P * q + p] : mk<T>(0, 0);
-      if constexpr (LY::kTile) line_inv_t<T, Q, P>(v, p, ty, tiles + warp * kWT + grp * P * (P + 1), 1, true);
-      else line_inv<T, Q, P>(v, p, ty);
-      __syncwarp();
-      if (ok)
+      for (int q = 0; q < Q; ++q) {
+        const int cs = ok ? so[P * q + p] : -1;
+        v[q] = cs >= 0 ? Sz[cs] : mk<T>(0, 0);
+      }
+      if constexpr (LY::kTile) line_inv_t<T, Q, P>(v, p, twy, tiles + warp * kWT + grp * P * (P + 1), 1, true);
+      else line_inv<T, Q, P>(v, p, twy);
+      if (ok) {
+        cplx<T>* row = Pl + r * LS;
 #pragma unroll
         for (int k = 0; k < Q; ++k) row[LY::kTile ? dt_index<Q, P>(p, pr, k) : k + Q * pr] = v[k];
-      __syncwarp();
+      }
     }
   }
   __syncthreads();
@@ -129,46 +149,52 @@ __global__ void __launch_bounds__(32 * NW) k_plane_reg(cplx<T>* __restrict__ S, 
       const bool ok = y < N2;
       cplx<T> v[Q];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) v[q] = ok ? Pl[(P * q + p) * LS + y] : mk<T>(0, 0);
+      for (int q = 0; q < Q; ++q) {
+        const int o = roff[P * q + p];
+        v[q] = ok && o >= 0 ? Pl[o + y] : mk<T>(0, 0);
+      }
       if constexpr (LX::kTile) {
         cplx<T>* tile = tiles + warp * kWT + grp * P * (P + 1);
-        line_inv_t<T, Q, P>(v, p, tx, tile, 1, true);
+        line_inv_t<T, Q, P>(v, p, twx, tile, 1, true);
 #pragma unroll
         for (int k = 0; k < Q; ++k) v[k] = cscale(v[k], ok ? V[dt_index<Q, P>(p, pr, k) * N2 + y] : (T)0);
-        line_fwd_t<T, Q, P>(v, p, tx, tile, 1, true);
+        line_fwd_t<T, Q, P>(v, p, twx, tile, 1, true);
       } else {
-        line_inv<T, Q, P>(v, p, tx);
+        line_inv<T, Q, P>(v, p, twx);
 #pragma unroll
         for (int k = 0; k < Q; ++k) v[k] = cscale(v[k], ok ? V[(k + Q * pr) * N2 + y] : (T)0);
-        line_fwd<T, Q, P>(v, p, tx);
+        line_fwd<T, Q, P>(v, p, twx);
       }
-      if (ok)
 #pragma unroll
-        for (int q = 0; q < Q; ++q) Pl[(P * q + p) * LS + y] = v[q];
+      for (int q = 0; q < Q; ++q) {
+        const int o = roff[P * q + p];
+        if (ok && o >= 0) Pl[o + y] = v[q];
+      }
     }
   }
   __syncthreads();
-  {  // forward along y, rows that hold sticks
+  {  // forward along y, rows that hold sticks, into the stick buffer
     constexpr int Q = SY::Q, P = SY::P, G = 32 / P;
     const int grp = lane / P, p = lane % P, pr = bitrev_lane<P>(p);
     for (int r0 = warp * G; r0 < nxr; r0 += nw * G) {
       const int r = r0 + grp;
       const bool ok = r < nxr;
-      cplx<T>* row = Pl + (ok ? xrows[r] : 0) * LS;
+      const cplx<T>* row = Pl + (ok ? r : 0) * LS;
       cplx<T> v[Q];
 #pragma unroll
       for (int k = 0; k < Q; ++k) v[k] = ok ? row[LY::kTile ? dt_index<Q, P>(p, pr, k) : k + Q * pr] : mk<T>(0, 0);
-      if constexpr (LY::kTile) line_fwd_t<T, Q, P>(v, p, ty, tiles + warp * kWT + grp * P * (P + 1), 1, true);
-      else line_fwd<T, Q, P>(v, p, ty);
-      __syncwarp();
-      if (ok)
+      if constexpr (LY::kTile) line_fwd_t<T, Q, P>(v, p, twy, tiles + warp * kWT + grp * P * (P + 1), 1, true);
+      else line_fwd<T, Q, P>(v, p, twy);
+      if (ok) {
+        const int* so = stick_of + (size_t)r * N2;
 #pragma unroll
-        for (int q = 0; q < Q; ++q) row[P * q + p] = v[q];
-      __syncwarp();
+        for (int q = 0; q < Q; ++q) {
+          const int cs = so[P * q + p];
+          if (cs >= 0) Sz[cs] = v[q];
+        }
+      }
     }
   }
-  __syncthreads();
-  for (int c = threadIdx.x; c < ncol; c += blockDim.x) Sz[c] = Pl[col_x[c] * LS + col_y[c]];
 }
 
 // ACC: hpsi += the transformed potential term alone (no kinetic or shift term)
@@ -235,6 +261,7 @@ template <typename K> static int set_smem_once(Ctx* c, K kernel, int* done) {
   PARO_CU(c, cudaGetDevice(&dev));
   if (dev >= 0 && dev < 64 && done[dev]) return PARO_OK;
   PARO_CU(c, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  PARO_CU(c, cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   if (dev >= 0 && dev < 64) done[dev] = 1;
   return PARO_OK;
 }
@@ -247,7 +274,7 @@ static int passes_reg(Ctx* c, const Basis& B, int nb, const cplx<T>* psi, cplx<T
   const bool f64 = sizeof(T) == 8;
   const size_t smz = (size_t)eb * (N + kStickBatch * (N + 1));
   constexpr int kPW = PlaneWarps<N>::value;
-  const size_t smp = (size_t)eb * (2 * N + N * PlaneStride<N>::value + kPW * PlaneLines<T, N>::kWarpTile);
+  const size_t smp = plane_reg_smem<T, N>(B.nxr);
   int st;
   if ((st = set_smem_once(c, k_zpass_inv_reg<T, N>, done[0])) || (st = set_smem_once(c, k_plane_reg<T, N, N>, done[1])) ||
       (st = set_smem_once(c, k_zpass_fwd_reg<T, N>, done[2])) ||
@@ -260,7 +287,7 @@ static int passes_reg(Ctx* c, const Basis& B, int nb, const cplx<T>* psi, cplx<T
   PARO_LAUNCH(c, "k_zpass_inv_reg");
   prof_end(c, f64 ? "k_zpass_inv<f64>" : "k_zpass_inv<f32>", ev);
   ev = prof_begin(c);
-  k_plane_reg<T, N, N><<<dim3(c->N[2], nb), 32 * kPW, smp, c->stream>>>(S, B.ncol, B.d_col_x, B.d_col_y, B.d_xrows, B.nxr,
+  k_plane_reg<T, N, N><<<dim3(c->N[2], nb), 32 * kPW, smp, c->stream>>>(S, B.ncol, B.d_stick_of, B.d_xrow_c, B.nxr,
                                                                    tw_of<T>(c, 0), tw_of<T>(c, 1),
                                                                    vplane ? vplane : vplane_of<T>(c), active);
   PARO_LAUNCH(c, "k_plane_reg");
@@ -300,37 +327,45 @@ static int passes_reg_dispatch(Ctx* c, const Basis& B, int nb, const cplx<T>* ps
 }
 
 // Density planes with the register FFT: per (z-plane, band group) the inverse transforms along y and
-// x of each band, |psi(r)|^2 summed in FP64 in shared memory, the group's plane written to part.
+// x of each band, |psi(r)|^2 summed in shared memory, the group's plane written to part.
 // TACC: accumulator of the |psi|^2 sum over the group's bands (at most gsize = 8): float for FP32 orbitals
 // (an 8-term FP32 sum, the groups then summed in FP64 by the caller), double for FP64 orbitals.
+// The plane is compact as in k_plane_reg (stick rows only, lines along y read straight from the stick
+// buffer); two block barriers per band.
 template <typename T, int N1, int N2, typename TACC, int NW = PlaneWarps<N1>::value>
 __global__ void __launch_bounds__(32 * NW) k_plane_density_reg(const cplx<T>* __restrict__ S, int ncol, int nbands,
-                                                           int gsize, const int* __restrict__ col_x,
-                                                           const int* __restrict__ col_y,
-                                                           const int* __restrict__ xrows, int nxr,
+                                                           int gsize, const int* __restrict__ stick_of,
+                                                           const int* __restrict__ xrow_c, int nxr,
                                                            const cplx<T>* __restrict__ twx,
                                                            const cplx<T>* __restrict__ twy, double wfac,
                                                            double* __restrict__ part) {
   using SX = LineShape<N1>;
   using SY = LineShape<N2>;
+  using LX = PlaneLines<T, N1>;
+  using LY = PlaneLines<T, N2>;
   constexpr int LS = PlaneStride<N2>::value;
+  constexpr int kWT = LX::kWarpTile > LY::kWarpTile ? LX::kWarpTile : LY::kWarpTile;
+  static_assert(N1 % 4 == 0, "row-offset table keeps the plane 16-byte aligned");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<T>* tx = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* ty = tx + N1;
-  cplx<T>* Pl = ty + N2;
-  TACC* acc = reinterpret_cast<TACC*>(Pl + N1 * LS);
+  TACC* acc = reinterpret_cast<TACC*>(smem_raw);  // N1 N2, a multiple of 16 bytes
+  cplx<T>* tx = reinterpret_cast<cplx<T>*>(acc + N1 * N2);  // twiddles in shared memory: the lanes' register
+  cplx<T>* ty = tx + N1;                                    // copies are formed again for every band
+  cplx<T>* tiles = ty + N2;
+  int* roff = reinterpret_cast<int*>(tiles + NW * kWT);
+  cplx<T>* Pl = reinterpret_cast<cplx<T>*>(roff + N1);
   const int z = blockIdx.x, grp_b = blockIdx.y, N3 = gridDim.x;
-  for (int i = threadIdx.x; i < N1; i += blockDim.x) tx[i] = twx[i];
+  for (int i = threadIdx.x; i < N1; i += blockDim.x) {
+    const int r = xrow_c[i];
+    roff[i] = r >= 0 ? r * LS : -1;
+    tx[i] = twx[i];
+  }
   for (int i = threadIdx.x; i < N2; i += blockDim.x) ty[i] = twy[i];
   for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) acc[i] = (TACC)0;
+  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int b0 = grp_b * gsize, b1 = min(nbands, b0 + gsize);
   for (int b = b0; b < b1; ++b) {
-    for (int i = threadIdx.x; i < N1 * LS; i += blockDim.x) Pl[i] = mk<T>(0, 0);
-    __syncthreads();
     const cplx<T>* Sz = S + ((size_t)b * N3 + z) * ncol;
-    for (int c = threadIdx.x; c < ncol; c += blockDim.x) Pl[col_x[c] * LS + col_y[c]] = Sz[c];
-    __syncthreads();
     {
       constexpr int Q = SY::Q, P = SY::P, G = 32 / P;
       const int grp = lane / P, p = lane % P, pr = bitrev_lane<P>(p);
@@ -338,17 +373,20 @@ __global__ void __launch_bounds__(32 * NW) k_plane_density_reg(const cplx<T>* __
       for (int r0 = warp * G; r0 < nxr; r0 += nw * G) {
         const int r = r0 + grp;
         const bool ok = r < nxr;
-        cplx<T>* row = Pl + (ok ? xrows[r] : 0) * LS;
+        const int* so = stick_of + (size_t)(ok ? r : 0) * N2;
         cplx<T> v[Q];
 #pragma unroll
-        for (int q = 0; q < Q; ++q) v[q] = ok ? row[P * q + p] : mk<T>(0, 0);
-        if constexpr (PlaneLines<T, N2>::kTile) line_inv_tr<T, Q, P>(v, p, lty, row, 1, ok);
+        for (int q = 0; q < Q; ++q) {
+          const int cs = ok ? so[P * q + p] : -1;
+          v[q] = cs >= 0 ? Sz[cs] : mk<T>(0, 0);
+        }
+        if constexpr (LY::kTile) line_inv_tr<T, Q, P>(v, p, lty, tiles + warp * kWT + grp * P * (P + 1), 1, true);
         else line_inv<T, Q, P>(v, p, ty);
-        __syncwarp();
-        if (ok)
+        if (ok) {
+          cplx<T>* row = Pl + r * LS;
 #pragma unroll
-          for (int k = 0; k < Q; ++k) row[PlaneLines<T, N2>::kTile ? dt_index<Q, P>(p, pr, k) : k + Q * pr] = v[k];
-        __syncwarp();
+          for (int k = 0; k < Q; ++k) row[LY::kTile ? dt_index<Q, P>(p, pr, k) : k + Q * pr] = v[k];
+        }
       }
     }
     __syncthreads();
@@ -361,14 +399,17 @@ __global__ void __launch_bounds__(32 * NW) k_plane_density_reg(const cplx<T>* __
         const bool ok = y < N2;
         cplx<T> v[Q];
 #pragma unroll
-        for (int q = 0; q < Q; ++q) v[q] = ok ? Pl[(P * q + p) * LS + y] : mk<T>(0, 0);
-        if constexpr (PlaneLines<T, N1>::kTile) line_inv_tr<T, Q, P>(v, p, ltx, Pl + (ok ? y : 0), LS, ok);
+        for (int q = 0; q < Q; ++q) {
+          const int o = roff[P * q + p];
+          v[q] = ok && o >= 0 ? Pl[o + y] : mk<T>(0, 0);
+        }
+        if constexpr (LX::kTile) line_inv_tr<T, Q, P>(v, p, ltx, tiles + warp * kWT + grp * P * (P + 1), 1, true);
         else line_inv<T, Q, P>(v, p, tx);
         if (ok)
 #pragma unroll
           for (int k = 0; k < Q; ++k) {
             const TACC re = v[k].x, im = v[k].y;
-            acc[(PlaneLines<T, N1>::kTile ? dt_index<Q, P>(p, pr, k) : k + Q * pr) * N2 + y] += re * re + im * im;
+            acc[(LX::kTile ? dt_index<Q, P>(p, pr, k) : k + Q * pr) * N2 + y] += re * re + im * im;
           }
       }
     }
@@ -384,8 +425,10 @@ __global__ void __launch_bounds__(32 * NW) k_plane_density_reg(const cplx<T>* __
 }
 
 template <typename T, int N, typename TACC>
-static size_t density_reg_smem() {
-  return (size_t)sizeof(cplx<T>) * (2 * N + N * PlaneStride<N>::value) + (size_t)N * N * sizeof(TACC);
+static size_t density_reg_smem(int nxr) {
+  constexpr int kWT = PlaneLines<T, N>::kWarpTile;
+  return (size_t)N * N * sizeof(TACC) +
+         sizeof(cplx<T>) * (2 * N + PlaneWarps<N>::value * kWT + (size_t)nxr * PlaneStride<N>::value) + N * sizeof(int);
 }
 
 template <typename T, int N, typename TACC>
@@ -394,9 +437,9 @@ static int density_planes_reg_acc(Ctx* c, const Basis& B, const cplx<T>* S, int 
   static int done[64];
   int st;
   if ((st = set_smem_once(c, k_plane_density_reg<T, N, N, TACC>, done))) return st;
-  const size_t smem = density_reg_smem<T, N, TACC>();
+  const size_t smem = density_reg_smem<T, N, TACC>(B.nxr);
   k_plane_density_reg<T, N, N, TACC><<<dim3(N, ngrp), 32 * PlaneWarps<N>::value, smem, c->stream>>>(
-      S, B.ncol, nbands, gsize, B.d_col_x, B.d_col_y, B.d_xrows, B.nxr, tw_of<T>(c, 0), tw_of<T>(c, 1), wfac, part);
+      S, B.ncol, nbands, gsize, B.d_stick_of, B.d_xrow_c, B.nxr, tw_of<T>(c, 0), tw_of<T>(c, 1), wfac, part);
   PARO_LAUNCH(c, "k_plane_density_reg");
   return PARO_OK;
 }
@@ -407,7 +450,7 @@ static int density_planes_reg_n(Ctx* c, const Basis& B, const cplx<T>* S, int nb
   // FP32 orbitals: the group's |psi|^2 sum in FP32 (an 8-term sum, rounding of the FP32 FFT's own size) keeps
   // the per-point accumulation off GB300's slow FP64 pipe; the groups are summed in FP64 by the caller
   if constexpr (sizeof(T) == 4) return density_planes_reg_acc<T, N, float>(c, B, S, nbands, ngrp, gsize, wfac, part);
-  if (density_reg_smem<T, N, double>() <= 227 * 1024)
+  if (density_reg_smem<T, N, double>(B.nxr) <= 227 * 1024)
     return density_planes_reg_acc<T, N, double>(c, B, S, nbands, ngrp, gsize, wfac, part);
   return fail(c, PARO_ERR_ARG, "density: plane too large for shared memory");
 }

@@ -1023,12 +1023,15 @@ __global__ void __launch_bounds__(256) k_pulay_dots(int n, int m, const double* 
   }
 }
 
-// one CTA: the new row of the Gram cache from the partials, then the bordered system by one thread,
-// Gaussian elimination with partial pivoting
+// one CTA: the new row of the Gram cache from the partials, then the bordered system
+//   [G 1; 1^T 0] [a; lambda] = [0; 1]
+// by Gauss-Jordan elimination with partial pivoting, every step spread over the CTA's threads
 __global__ void __launch_bounds__(256) k_pulay_solve(int m, int nblk, const double* __restrict__ part,
                                                      const int* __restrict__ slot, int snew,
                                                      double* __restrict__ gram, double* __restrict__ coef) {
-  __shared__ double sa[16 * 16];
+  __shared__ double a[17][19];
+  __shared__ double fac[17];
+  __shared__ int s_piv;
   {  // the block partials of each new dot summed by one warp (lane-strided, then a shuffle tree)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int i = warp; i < m; i += nw) {
@@ -1043,38 +1046,50 @@ __global__ void __launch_bounds__(256) k_pulay_solve(int m, int nblk, const doub
     }
   }
   __syncthreads();
-  for (int ij = threadIdx.x; ij < m * m; ij += blockDim.x) {
-    const int i = ij / m, j = ij - i * m;
-    sa[ij] = gram[slot[i] * 16 + slot[j]];
+  const int n = m + 1;  // unknowns; column n holds the right-hand side
+  for (int ij = threadIdx.x; ij < n * (n + 1); ij += blockDim.x) {
+    const int i = ij / (n + 1), j = ij - i * (n + 1);
+    double v;
+    if (j == n) v = i == m ? 1.0 : 0.0;
+    else if (i < m && j < m) v = gram[slot[i] * 16 + slot[j]];
+    else v = i == j ? 0.0 : 1.0;  // the border of ones, zero in the corner
+    a[i][j] = v;
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  double a[17][18];
-  const int n = m + 1;
-  for (int i = 0; i < m; ++i)
-    for (int j = i; j < m; ++j) a[i][j] = a[j][i] = sa[i * m + j];
-  for (int i = 0; i < m; ++i) { a[i][m] = 1.0; a[m][i] = 1.0; a[i][n] = 0.0; }
-  a[m][m] = 0.0;
-  a[m][n] = 1.0;
   for (int col = 0; col < n; ++col) {
-    int piv = col;
-    for (int r = col + 1; r < n; ++r)
-      if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;
-    if (piv != col)
-      for (int k = 0; k <= n; ++k) { const double t = a[col][k]; a[col][k] = a[piv][k]; a[piv][k] = t; }
-    const double d = a[col][col];
-    for (int r = col + 1; r < n; ++r) {
-      const double f = a[r][col] / d;
-      for (int k = col; k <= n; ++k) a[r][k] -= f * a[col][k];
+    if (threadIdx.x < 32) {  // pivot: the largest |a[r][col]| for r >= col, the first one on ties
+      const int r = col + (int)threadIdx.x;
+      double best = r < n ? fabs(a[r][col]) : -1.0;
+      int at = r < n ? r : n;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oa = __shfl_xor_sync(0xffffffffu, at, o);
+        if (ob > best || (ob == best && oa < at)) {
+          best = ob;
+          at = oa;
+        }
+      }
+      if (threadIdx.x == 0) s_piv = at;
     }
+    __syncthreads();
+    const int piv = s_piv;
+    if (piv != col)
+      for (int k = threadIdx.x; k <= n; k += blockDim.x) {
+        const double t = a[col][k];
+        a[col][k] = a[piv][k];
+        a[piv][k] = t;
+      }
+    __syncthreads();
+    for (int r = threadIdx.x; r < n; r += blockDim.x) fac[r] = r == col ? 0.0 : a[r][col] / a[col][col];
+    __syncthreads();
+    for (int ij = threadIdx.x; ij < n * (n + 1 - col); ij += blockDim.x) {
+      const int r = ij / (n + 1 - col), k = col + ij - r * (n + 1 - col);
+      if (r != col) a[r][k] -= fac[r] * a[col][k];
+    }
+    __syncthreads();
   }
-  double x[17];
-  for (int r = n - 1; r >= 0; --r) {
-    double s = a[r][n];
-    for (int k = r + 1; k < n; ++k) s -= a[r][k] * x[k];
-    x[r] = s / a[r][r];
-  }
-  for (int i = 0; i < m; ++i) coef[i] = x[i];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) coef[i] = a[i][n] / a[i][i];
 }
 
 __global__ void k_pulay_mix(int n, int m, const double* __restrict__ hr, const double* __restrict__ hres,

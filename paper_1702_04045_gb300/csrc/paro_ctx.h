@@ -33,6 +33,8 @@ struct Basis {
   int* d_g_col = nullptr;         // stick of coefficient g
   int* d_g_z = nullptr;           // grid index j3 of coefficient g
   int* d_xrows = nullptr;         // the nxr rows j1 with sticks
+  int* d_xrow_c = nullptr;        // N1 entries: r where d_xrows[r] = j1, or -1 for a row without sticks
+  int* d_stick_of = nullptr;      // nxr x N2: the stick at grid row d_xrows[r], column j2, or -1
   int* d_mg = nullptr;            // real-wavefunction mode (k = 0): index of -G for every G
   double2* d_beta = nullptr;      // KB projectors, nproj x npw
   float2* d_beta32 = nullptr;
