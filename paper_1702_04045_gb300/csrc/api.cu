@@ -669,6 +669,10 @@ static int source_step(Ctx* c, int ik, int alg, double rel_tol, int max_it, cplx
   return build_alg2_basis<T>(c, ik, E, X, nx);
 }
 
+// ||S - I||_F up to which the mixed SCF iteration orthonormalises its sources by the first-order factor:
+// the rows are then orthonormal to 3 tol^2 = 7.5e-9, below the FP32 rounding of the rows themselves.
+static const double kOrthFirstTol = 5e-5;
+
 // Cholesky-orthonormalise the first nx rows of X in place (Y = conj(L)^{-1} X); Gram in FP64.
 template <typename T>
 static int orthonormalize(Ctx* c, int ik, cplx<T>* X, int nx, cplx<T>* HX = nullptr, bool defer = false) {
@@ -683,7 +687,14 @@ static int orthonormalize(Ctx* c, int ik, cplx<T>* X, int nx, cplx<T>* HX = null
     ProfTag t(c, "gram");
     if ((st = gemm_cn<T, T, T>(c, nx, nx, npw, X, npw, X, npw, S, nx, true, true))) return st;
     if (gamma_on(c) && (st = gamma_real_matrix(c, nx, S))) return st;
-    if ((st = chol_inv(c, nx, S, G, defer))) return st;
+    // mixed-precision SCF iteration: near convergence the sources are orthonormal to ~1e-5 and the
+    // first-order factor (orthonormal to ~3 ||E||^2, below the FP32 rounding of the rows) replaces the
+    // FP64 Cholesky, decided on the device; the Cholesky kernel then returns at once
+    int* skip = nullptr;
+    bool cl_ok = false;
+    if (defer && !f64 && (st = chol_cluster_available(c, nx, &cl_ok))) return st;
+    if (cl_ok && (st = orth_first_order(c, nx, S, G, kOrthFirstTol, &skip))) return st;
+    if ((st = chol_inv(c, nx, S, G, defer, skip))) return st;
   }
   ProfTag t(c, "orth");
   if ((st = gemm_wx<T, T>(c, nx, npw, nx, G, nx, true, nullptr, X, npw, Y, npw, 0.0, nullptr, true))) return st;

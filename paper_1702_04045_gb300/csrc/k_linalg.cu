@@ -643,10 +643,14 @@ int coop_grid(Ctx* c, const void* kernel, int threads, size_t smem, int cap, int
 // parity of j), so each step reads its pivot locally; one cluster barrier per column orders the steps.
 // info: first column + 1 with a_jj <= 0 (the elimination then continues with a_jj = 1).
 __global__ void __launch_bounds__(1024) k_chol_cluster(int n, const double2* __restrict__ s, double2* __restrict__ g,
-                                                       int* __restrict__ info) {
+                                                       int* __restrict__ info, const int* __restrict__ skip) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks(), q = (int)cl.block_rank();
+  if (skip != nullptr && *skip) {  // the factor is already formed (k_orth_first_order); every CTA leaves at once
+    if (q == 0 && threadIdx.x == 0) *info = 0;
+    return;
+  }
   const int R = (n + C - 1) / C, W2 = 2 * n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* rows = reinterpret_cast<double2*>(smem_raw);  // R x 2n: [a_i | b_i]
@@ -747,10 +751,14 @@ __device__ __forceinline__ double2 zfma_conj(double2 acc, double2 a, double2 b) 
 }
 
 __global__ void __launch_bounds__(512) k_chol_blocked(int n, const double2* __restrict__ s, double2* __restrict__ g,
-                                                      int* __restrict__ info) {
+                                                      int* __restrict__ info, const int* __restrict__ skip) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks(), q = (int)cl.block_rank();
+  if (skip != nullptr && *skip) {  // the factor is already formed (k_orth_first_order); every CTA leaves at once
+    if (q == 0 && threadIdx.x == 0) *info = 0;
+    return;
+  }
   const int R = (n + C - 1) / C, W2 = 2 * n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* rows = reinterpret_cast<double2*>(smem_raw);  // R x 2n
@@ -998,7 +1006,56 @@ int chol_check(Ctx* c) {
   return PARO_OK;
 }
 
-int chol_inv(Ctx* c, int n, const double2* s, double2* g, bool defer) {
+// First-order inverse Cholesky factor of a Gram matrix close to the identity. With S = I + E = L L^H and
+// F = strictly lower(E) + diag(E) / 2, L = I + F + O(E^2), so G = conj(L)^{-1} = I - conj(F) + O(E^2), and the
+// rows G X are orthonormal up to about 3 ||E||^2. One CTA forms ||E||_F (into *enorm); when it is at most
+// tol it writes G (lower triangular, as the Cholesky kernels do) and *use = 1, else *use = 0 and leaves G.
+__global__ void __launch_bounds__(1024) k_orth_first_order(int n, const double2* __restrict__ s,
+                                                           double2* __restrict__ g, double tol, int* __restrict__ use,
+                                                           double* __restrict__ enorm) {
+  __shared__ double red[32];
+  __shared__ int s_use;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+    const int r = i / n, k = i - r * n;
+    double2 v = s[i];
+    if (r == k) v.x -= 1.0;
+    acc += v.x * v.x + v.y * v.y;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) {
+    const double e = sqrt(acc);
+    *enorm = e;
+    s_use = e <= tol ? 1 : 0;
+    *use = s_use;
+  }
+  __syncthreads();
+  if (!s_use) return;
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+    const int r = i / n, k = i - r * n;
+    const double2 v = s[i];
+    g[i] = k > r ? make_double2(0.0, 0.0) : k == r ? make_double2(1.0 - 0.5 * (v.x - 1.0), 0.0) : make_double2(-v.x, v.y);
+  }
+}
+
+int chol_cluster_available(Ctx* c, int n, bool* avail) {
+  Ctx::CholShape sh;
+  const int st = chol_cluster_shape(c, n, &sh);
+  *avail = st == PARO_OK && sh.kind > 0;
+  return st;
+}
+
+int orth_first_order(Ctx* c, int n, const double2* s, double2* g, double tol, int** use_dev) {
+  int* use = static_cast<int*>(ws_get(c, "orth_first_use", sizeof(int)));
+  double* enorm = static_cast<double*>(ws_get(c, "orth_first_enorm", sizeof(double)));
+  if (!use || !enorm) return PARO_ERR_CUDA;
+  k_orth_first_order<<<1, 1024, 0, c->stream>>>(n, s, g, tol, use, enorm);
+  PARO_LAUNCH(c, "k_orth_first_order");
+  *use_dev = use;
+  return PARO_OK;
+}
+
+int chol_inv(Ctx* c, int n, const double2* s, double2* g, bool defer, const int* skip) {
   {
     Ctx::CholShape sh;
     int st;
@@ -1019,8 +1076,8 @@ int chol_inv(Ctx* c, int n, const double2* s, double2* g, bool defer) {
       cfg.attrs = at;
       cfg.numAttrs = 1;
       cudaEvent_t ev = prof_begin(c);
-      if (sh.kind == 1) PARO_CU(c, cudaLaunchKernelEx(&cfg, k_chol_blocked, n, s, g, flags));
-      else PARO_CU(c, cudaLaunchKernelEx(&cfg, k_chol_cluster, n, s, g, flags));
+      if (sh.kind == 1) PARO_CU(c, cudaLaunchKernelEx(&cfg, k_chol_blocked, n, s, g, flags, skip));
+      else PARO_CU(c, cudaLaunchKernelEx(&cfg, k_chol_cluster, n, s, g, flags, skip));
       ++c->launches;
       prof_end(c, "k_chol_cluster", ev);
       if (defer) {  // the flag comes back without waiting; chol_check() reads it

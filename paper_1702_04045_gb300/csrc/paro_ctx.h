@@ -239,8 +239,15 @@ Ctx* unwrap(paro_ctx* h);
 // Cholesky S = L L^H (n x n, row-major, device), then writes G = conj(L)^{-1} (lower) into g.
 // defer: the breakdown flag of the cluster form is read back without waiting, and chol_check() (which waits
 // for it) reports a breakdown; the inverse is meaningless until then
-int chol_inv(Ctx* c, int n, const double2* s, double2* g, bool defer = false);
+// skip (device flag, may be null): when set at run time the cluster Cholesky leaves g as it is and reports
+// no breakdown (the factor was formed by orth_first_order); the stream-ordered launch costs no wait.
+int chol_inv(Ctx* c, int n, const double2* s, double2* g, bool defer = false, const int* skip = nullptr);
 int chol_check(Ctx* c);
+// The first-order inverse Cholesky factor of S = I + E when ||E||_F <= tol (decided on the device: *use_dev
+// receives the flag for chol_inv's skip).
+int orth_first_order(Ctx* c, int n, const double2* s, double2* g, double tol, int** use_dev);
+// whether the cluster form of the Cholesky runs for order n on this device (the form that honours skip)
+int chol_cluster_available(Ctx* c, int n, bool* avail);
 // Hermitian eigensolver, FP64 (k_eigh.cu): w ascending, v columns = eigenvectors (row-major n x n).
 int eigh(Ctx* c, int n, const double2* a, double* w, double2* v);
 // The same result from an FP32 solve refined in FP64 (k_eigh_mixed.cu); FP64 solver for n > 160. Each
