@@ -455,9 +455,9 @@ static int zgemm(Ctx* c, int n, const double2* A, bool ah, const double2* B, dou
   return PARO_OK;
 }
 
-// Warm start of the refinement: X = the permutation that sorts the diagonal of A (one CTA, n <= 1024):
-// column rank(i) is e_i, rank(i) = #{j : a_jj < a_ii, or a_jj = a_ii and j < i}
-__global__ void k_warm_perm(int n, const double2* __restrict__ A, double2* __restrict__ X) {
+// Warm start of the refinement: X0 = the permutation that sorts the diagonal of A, X0[i][rank(i)] = 1 with
+// rank(i) = #{j : a_jj < a_ii, or a_jj = a_ii and j < i}; at_rank is its inverse (one CTA, n <= 1024)
+__global__ void k_warm_perm(int n, const double2* __restrict__ A, int* __restrict__ rank, int* __restrict__ at_rank) {
   const int i = threadIdx.x;
   if (i >= n) return;
   const double d = A[(size_t)i * n + i].x;
@@ -466,7 +466,44 @@ __global__ void k_warm_perm(int n, const double2* __restrict__ A, double2* __res
     const double e = A[(size_t)j * n + j].x;
     r += (e < d || (e == d && j < i)) ? 1 : 0;
   }
-  X[(size_t)i * n + r] = make_double2(1.0, 0.0);
+  rank[i] = r;
+  at_rank[r] = i;
+}
+
+// The first refinement step from X0 needs no products: G = X0^H X0 = I and S = X0^H A X0 = A with rows and
+// columns in rank order. nrm as k_zreduce leaves it for the pair (G, S): per CTA of 256 entries, zero for
+// G and the off-diagonal sum of |S_ij|^2 for S.
+__global__ void __launch_bounds__(256) k_warm_s(int n, const double2* __restrict__ A, const int* __restrict__ at_rank,
+                                                double2* __restrict__ G, double2* __restrict__ S,
+                                                float* __restrict__ nrm, int nnrm) {
+  __shared__ float red[32];
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  float e = 0.f;
+  if (idx < n * n) {
+    const int r = idx / n, q = idx - r * n;
+    const double2 v = A[(size_t)at_rank[r] * n + at_rank[q]];
+    S[idx] = v;
+    G[idx] = make_double2(r == q ? 1.0 : 0.0, 0.0);
+    if (r != q) {
+      const float x = (float)v.x, y = (float)v.y;
+      e = x * x + y * y;
+    }
+  }
+  e = block_sumf(e, red);
+  if (threadIdx.x == 0) {
+    nrm[blockIdx.x] = 0.f;
+    nrm[nnrm + blockIdx.x] = e;
+  }
+}
+
+// X1 = X0 (I + E): row i of X1 is row rank(i) of I + E
+__global__ void k_warm_x1(int n, const int* __restrict__ rank, const double2* __restrict__ E, double2* __restrict__ X) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int i = idx / n, j = idx - i * n, r = rank[i];
+  double2 v = E[(size_t)r * n + j];
+  if (r == j) v.x += 1.0;
+  X[idx] = v;
 }
 
 // max |E_ij| over the matrix into *out (one CTA; the warm start's convergence test)
@@ -528,11 +565,12 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
     --c->eig_warm_skip;
   } else if (warm) {
     cudaEvent_t evw = prof_begin(c);
-    PARO_CU(c, cudaMemsetAsync(X, 0, nn * sizeof(double2), c->stream));
-    k_warm_perm<<<1, 1024, 0, c->stream>>>(n, Af, X);
+    int* rk = static_cast<int*>(ws_get(c, "em_rank", (size_t)2 * n * sizeof(int)));
+    if (!rk) return PARO_ERR_CUDA;
+    k_warm_perm<<<1, 1024, 0, c->stream>>>(n, Af, rk, rk + n);
     PARO_LAUNCH(c, "k_warm_perm");
-    // one refinement step; with absmax, the largest entry of its correction into r32[0]
-    auto refine_step = [&](bool absmax) -> int {
+    // one refinement step, the largest entry of its correction into r32[0]
+    auto refine_step = [&]() -> int {
       int s2;
       if ((s2 = zgemm(c, n, X, true, X, G, false, part, true, nrm, true))) return s2;
       if ((s2 = zgemm(c, n, Af, false, X, T1, false, part))) return s2;
@@ -541,10 +579,8 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
       PARO_LAUNCH(c, "k_refine_lam");
       k_refine_e<<<(n * n + 255) / 256, 256, 0, c->stream>>>(n, G, S, lam, cl, T1);
       PARO_LAUNCH(c, "k_refine_e");
-      if (absmax) {
-        k_absmax<<<1, 1024, 0, c->stream>>>((int)nn, T1, r32);
-        PARO_LAUNCH(c, "k_absmax");
-      }
+      k_absmax<<<1, 1024, 0, c->stream>>>((int)nn, T1, r32);
+      PARO_LAUNCH(c, "k_absmax");
       return zgemm(c, n, X, false, T1, X, true, part);
     };
     auto read_emax = [&](float* e) -> int {
@@ -554,12 +590,21 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
       *e = *static_cast<const float*>(h);
       return PARO_OK;
     };
+    // step 1 from the permutation, without products
+    k_warm_s<<<nnrm, 256, 0, c->stream>>>(n, Af, rk + n, G, S, nrm, nnrm);
+    PARO_LAUNCH(c, "k_warm_s");
+    k_refine_lam<<<1, 1024, 0, c->stream>>>(n, G, S, nrm, nnrm, lam, cl, cst, ncl);
+    PARO_LAUNCH(c, "k_refine_lam");
+    k_refine_e<<<(n * n + 255) / 256, 256, 0, c->stream>>>(n, G, S, lam, cl, T1);
+    PARO_LAUNCH(c, "k_refine_e");
+    k_warm_x1<<<(n * n + 255) / 256, 256, 0, c->stream>>>(n, rk, T1, X);
+    PARO_LAUNCH(c, "k_warm_x1");
     float emax = 1.f;
-    if ((st = refine_step(false)) || (st = refine_step(true)) || (st = read_emax(&emax))) return st;
+    if ((st = refine_step()) || (st = read_emax(&emax))) return st;
     // a pair of close but separate eigenvalues converges more slowly: a third step decides (measured on the
     // 64-atom cell near convergence, the second correction lies between 1e-4 and 1e-3 in about one
     // Rayleigh-Ritz step in twelve)
-    if (emax >= 1e-4f && emax < 1e-2f && ((st = refine_step(true)) || (st = read_emax(&emax)))) return st;
+    if (emax >= 1e-4f && emax < 1e-2f && ((st = refine_step()) || (st = read_emax(&emax)))) return st;
     prof_end(c, "eigh_warm", evw);
     if (emax < 1e-4f) return eigh_finish(c, n, a, Af, X, T1, S, part, cl, cst, ncl, lam, w, v, perm, info, true);
     c->eig_warm_skip = 8;  // not close enough yet: the FP32 solve for the next calls
