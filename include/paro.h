@@ -178,6 +178,22 @@ int paro_sigma(const paro_ctx* ctx, double* sigma);
 int paro_apply_h(paro_ctx* ctx, int ik, int nb, int dtype, const void* psi, void* hpsi);
 
 /*
+ * paro_apply_vnl -- the nonlocal term of H alone for nb orbitals of k-point ik (Section 2.2's V_nl in the
+ * Kleinman-Bylander form):  out_b(G) = sum_p beta_p(G) D_p <beta_p|psi_b>.
+ *   dtype  PARO_C64 or PARO_C32, as paro_apply_h; psi, out device, nb x npw complex of dtype (out is
+ *          overwritten and must not alias psi).
+ *   form   PARO_VNL_ACCURATE: FP64 products (PARO_C64), or FP32 products whose sums are carried in a
+ *          two-sum pair (PARO_C32) -- the form the Rayleigh-Ritz step and the energy use;
+ *          PARO_VNL_TENSOR (PARO_C32 only): the form of the inexact inner solves, 3xTF32 on the tensor
+ *          cores with the projectors' split formed once per position set (relative error about 1e-5).
+ *   Errors: PARO_ERR_ARG (bad argument, PARO_VNL_TENSOR with PARO_C64), PARO_ERR_STATE (no projectors
+ *   set), PARO_ERR_TIMEOUT (a tensor-core kernel's bounded wait gave up; the output is then undefined).
+ */
+#define PARO_VNL_ACCURATE 0
+#define PARO_VNL_TENSOR 1
+int paro_apply_vnl(paro_ctx* ctx, int ik, int nb, int dtype, const void* psi, void* out, int form);
+
+/*
  * paro_apply_h_noalloc -- the same H psi as paro_apply_h, for callers that cannot let the library
  * allocate device memory during the call: applications that give all device memory to their own
  * pool up front and run under a fixed budget, and callers that must keep the implicit device-wide

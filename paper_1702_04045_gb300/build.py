@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libparo.so")
-SOURCES = ["api.cu", "k_adjoint.cu", "k_batch.cu", "k_eigh.cu", "k_eigh_mixed.cu", "k_gamma.cu", "k_hpsi.cu", "k_linalg.cu", "k_minres.cu", "k_pcg.cu", "k_scf.cu", "k_tc.cu"]
+SOURCES = ["api.cu", "k_adjoint.cu", "k_batch.cu", "k_eigh.cu", "k_eigh_mixed.cu", "k_gamma.cu", "k_hpsi.cu", "k_linalg.cu", "k_minres.cu", "k_pcg.cu", "k_scf.cu", "k_tc.cu", "k_tc_beta.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "-Xptxas", "-v"]
 

@@ -194,7 +194,7 @@ static int build_basis(Ctx* c, Basis& b) {
 static void free_basis(Basis& b) {
   void** ps[] = {(void**)&b.d_miller, (void**)&b.d_kin,    (void**)&b.d_kin32,  (void**)&b.d_col_x,
                  (void**)&b.d_col_y,  (void**)&b.d_col_off, (void**)&b.d_g_col,  (void**)&b.d_g_z,
-                 (void**)&b.d_xrows,  (void**)&b.d_xrow_c, (void**)&b.d_stick_of, (void**)&b.d_beta,   (void**)&b.d_beta32, (void**)&b.d_prec_base,
+                 (void**)&b.d_xrows,  (void**)&b.d_xrow_c, (void**)&b.d_stick_of, (void**)&b.d_beta,   (void**)&b.d_beta32, (void**)&b.d_beta_img_cn, (void**)&b.d_beta_img_wx, (void**)&b.d_prec_base,
                  (void**)&b.d_mg,
                  (void**)&b.d_psi,    (void**)&b.d_hpsi,   (void**)&b.d_psi32,  (void**)&b.d_hpsi32};
   for (void** p : ps) {
@@ -1320,6 +1320,33 @@ int paro_apply_h(paro_ctx* ctx, int ik, int nb, int dtype, const void* psi, void
   return dtype == PARO_C64
              ? apply_h<double>(c, ik, nb, static_cast<const double2*>(psi), static_cast<double2*>(hpsi), 0.0, nullptr)
              : apply_h<float>(c, ik, nb, static_cast<const float2*>(psi), static_cast<float2*>(hpsi), 0.0, nullptr);
+}
+
+int paro_apply_vnl(paro_ctx* ctx, int ik, int nb, int dtype, const void* psi, void* out, int form) {
+  CTX_CHECK(ctx);
+  if (ik < 0 || ik >= c->nk || nb < 1 || !psi || !out || psi == out || (dtype != PARO_C64 && dtype != PARO_C32) ||
+      (form != PARO_VNL_ACCURATE && form != PARO_VNL_TENSOR) || (form == PARO_VNL_TENSOR && dtype != PARO_C32))
+    return fail(c, PARO_ERR_ARG, "paro_apply_vnl: bad argument");
+  if (!c->have_kb) return fail(c, PARO_ERR_STATE, "paro_apply_vnl: no Kleinman-Bylander projectors set");
+  const size_t eb = dtype == PARO_C64 ? sizeof(double2) : sizeof(float2);
+  PARO_CU(c, cudaMemsetAsync(out, 0, (size_t)nb * c->bases[ik].npw * eb, c->stream));
+  int st;
+  if (dtype == PARO_C64) {
+    st = kb_apply<double>(c, ik, nb, static_cast<const double2*>(psi), static_cast<double2*>(out));
+  } else if (form == PARO_VNL_TENSOR) {
+    TcScope tcs(c);
+    st = kb_apply<float>(c, ik, nb, static_cast<const float2*>(psi), static_cast<float2*>(out));
+  } else {
+    st = kb_apply<float>(c, ik, nb, static_cast<const float2*>(psi), static_cast<float2*>(out));
+  }
+  if (st) return st;
+  const int* htc = nullptr;
+  if ((st = tc_flag_readback(c, &htc))) return st;
+  if (htc) {
+    if ((st = pinned_wait(c, "tc_err"))) return st;
+    if (*htc) return fail(c, PARO_ERR_TIMEOUT, "tensor-core product: mbarrier wait gave up");
+  }
+  return PARO_OK;
 }
 
 int paro_apply_h_adjoint(paro_ctx* ctx, int ik, int nb, int dtype, const void* psi, const void* w, void* g_psi,

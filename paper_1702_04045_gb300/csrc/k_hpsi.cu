@@ -272,6 +272,22 @@ int kb_apply(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* hpsi) {
   const Basis& B = c->bases[ik];
   double2* P = static_cast<double2*>(ws_get(c, "kb_proj", (size_t)c->nproj * nb * sizeof(double2)));
   if (!P) return PARO_ERR_CUDA;
+  // inside the inexact inner solves: the tensor-core products fed by the projectors' presplit images
+  if constexpr (sizeof(T) == 4) {
+    if (c->tc_scope && tc_enabled()) {
+      int* err = tc_err_flag(c);
+      if (!err) return PARO_ERR_CUDA;
+      int st = beta_images(c, ik);
+      if (st) return st;
+      cudaEvent_t ev = prof_begin(c);
+      if ((st = gemm_cn_tc_beta(c, ik, nb, reinterpret_cast<const float2*>(psi), P, err))) return st;
+      prof_end(c, "k_gemm_cn_tcb", ev);
+      ev = prof_begin(c);
+      if ((st = gemm_wx_tc_beta(c, ik, nb, P, c->d_dvec, reinterpret_cast<float2*>(hpsi), err))) return st;
+      prof_end(c, "k_gemm_wx_tcb", ev);
+      return PARO_OK;
+    }
+  }
   // FP32 projections outside the inexact inner solves carry their sums in a two-sum pair: a long FP32
   // accumulation biases |<beta|psi>|^2 (and with it the Rayleigh-Ritz H and the energy) at the 1e-6 level
   const bool carry = sizeof(T) == 4 && !c->tc_scope;

@@ -360,6 +360,13 @@ int build_beta(Ctx* c) {
       PARO_CU(c, cudaMalloc(&b.d_beta, (size_t)c->nproj * b.npw * sizeof(double2)));
       PARO_CU(c, cudaMalloc(&b.d_beta32, (size_t)c->nproj * b.npw * sizeof(float2)));
     }
+    for (float4** img : {&b.d_beta_img_cn, &b.d_beta_img_wx}) {  // formed again from the new projectors
+      if (*img) {
+        PARO_CU(c, cudaStreamSynchronize(c->stream));
+        cudaFree(*img);
+        *img = nullptr;
+      }
+    }
     k_beta<<<dim3((b.npw + 127) / 128, c->nat), 128, 0, c->stream>>>(b.npw, c->nat, c->N[0], c->N[1], c->N[2], B,
                                                                     b.kcart[0], b.kcart[1], b.kcart[2], b.d_miller,
                                                                     ph, kph, c->kb_rc, c->omega, b.d_beta,

@@ -24,33 +24,6 @@ static const int kTcM = 128;       // rows of A per CTA = TMEM lanes
 static const int kTcThreads = 256;
 static const uint32_t kTcPolls = 1u << 24;
 
-// byte offset of (row, 16-byte chunk) in a K-major tile with ch chunks per row: 128-byte swizzle when a
-// row is exactly 128 bytes (ch = 8: 8-row atoms of 1024 bytes, chunk c of row r at c ^ (r % 8)), else the
-// no-swizzle core-matrix layout (8 rows x 16 bytes contiguous)
-__device__ __forceinline__ uint32_t tc_off(int row, int chunk, int ch) {
-  if (ch == 8) return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
-  return (uint32_t)(((row >> 3) * ch + chunk) * 128 + (row & 7) * 16);
-}
-
-// descriptor of the K step s2 (8 TF32 values) of a tile at shared address base, layout as in tc_off
-__device__ __forceinline__ uint64_t tc_desc(uint32_t base, int s2, int ch) {
-  if (ch == 8) return tc::smem_desc_sw128(base + (uint32_t)s2 * 32u);
-  return tc::smem_desc(base + (uint32_t)s2 * 256u, 128u, (uint32_t)ch * 128u);
-}
-
-// dynamic shared memory rounded up to the 1024-byte alignment of the swizzle atoms (1 KB extra allocated)
-__device__ __forceinline__ unsigned char* tc_align1024(unsigned char* p) {
-  const uint32_t a = tc::smem_addr(p);
-  return p + ((1024u - (a & 1023u)) & 1023u);
-}
-
-// split (v0, v1) into hi and lo TF32 quadruples (re0, im0, re1, im1)
-__device__ __forceinline__ void tc_split(float2 v0, float2 v1, float4& h, float4& l) {
-  h.x = tc::tf32_round(v0.x); h.y = tc::tf32_round(v0.y); h.z = tc::tf32_round(v1.x); h.w = tc::tf32_round(v1.y);
-  l.x = tc::tf32_round(v0.x - h.x); l.y = tc::tf32_round(v0.y - h.y);
-  l.z = tc::tf32_round(v1.x - h.z); l.w = tc::tf32_round(v1.y - h.w);
-}
-
 // Pipeline of the tensor-core kernels: two shared-memory buffers, one mbarrier each. Stage s is staged into
 // buffer s & 1 while the MMAs of stage s - 1 run on the other; before a buffer is overwritten, the MMAs of
 // stage s - 2 (its previous use) must have completed. Every wait is bounded; on a time-out the kernel
@@ -488,7 +461,7 @@ static size_t cn_smem_bytes(int NT, int NR) {
 // K split of the tensor-core product: one CTA per SM, the slice count minimising waves x stages per
 // slice (at least 4 stages per slice), and no slice longer than 8192 complex terms, so the FP32 sum in
 // tensor memory stays short (slices are added in an FP32 two-sum pair).
-static void gemm_cn_tc_plan(int M, int N, int K, int* nz_out, int* kslice_out) {
+void tc_cn_plan(int M, int N, int K, int* nz_out, int* kslice_out) {
   const int ntiles = (N + 255) / 256;
   const int mtiles = (M + kTcM - 1) / kTcM;
   const int tiles = mtiles * ntiles;
@@ -520,7 +493,7 @@ int gemm_cn_tc(Ctx* c, int M, int N, int K, const float2* A, int lda, const floa
   const int nt = ((N + ntiles - 1) / ntiles + 15) / 16 * 16;
   const int mtiles = (M + kTcM - 1) / kTcM;
   int nz = 1, kslice = kCnKC;
-  gemm_cn_tc_plan(M, N, K, &nz, &kslice);
+  tc_cn_plan(M, N, K, &nz, &kslice);
   float2* part = static_cast<float2*>(ws_get(c, "tc_parts32", (size_t)nz * M * N * sizeof(float2)));
   if (!part) return PARO_ERR_CUDA;
   int nr = 5;
@@ -544,8 +517,20 @@ int gemm_cn_tc(Ctx* c, int M, int N, int K, const float2* A, int lda, const floa
   else
     k_gemm_cn_tc<3><<<grid, kTcThreads, sm, c->stream>>>(M, N, K, kslice, nt, A, lda, B, ldb, part, err);
   PARO_LAUNCH(c, "k_gemm_cn_tc");
+  return reduce_parts32(c, M, N, nz, part, C, ldc);
+}
+
+int reduce_parts32(Ctx* c, int M, int N, int nz, const float2* part, double2* C, int ldc) {
   k_reduce_parts32<<<(M * N + 255) / 256, 256, 0, c->stream>>>(M, N, nz, part, C, ldc);
   PARO_LAUNCH(c, "k_reduce_parts32");
+  return PARO_OK;
+}
+
+int wx_presplit(Ctx* c, int M, int K, int NT, int KC, const double2* W, int ldw, bool wt, const double* s,
+                float4* Wp) {
+  const int mtiles = (M + NT - 1) / NT;
+  k_wx_presplit<<<dim3(64, mtiles), 256, 0, c->stream>>>(M, K, NT, KC, W, ldw, wt ? 1 : 0, s, Wp);
+  PARO_LAUNCH(c, "k_wx_presplit");
   return PARO_OK;
 }
 

@@ -38,6 +38,11 @@ struct Basis {
   int* d_mg = nullptr;            // real-wavefunction mode (k = 0): index of -G for every G
   double2* d_beta = nullptr;      // KB projectors, nproj x npw
   float2* d_beta32 = nullptr;
+  // the projectors' TF32 hi/lo split in the shared-memory image of each stage of the tensor-core products
+  // (k_tc_beta.cu; formed on first use, dropped when the projectors change)
+  float4* d_beta_img_cn = nullptr;
+  float4* d_beta_img_wx = nullptr;
+  int img_cn_nstage = 0, img_wx_nstage = 0;
   double* d_prec_base = nullptr;  // |k+G|^2/2 (copy used by the preconditioner)
   // orbitals
   double2* d_psi = nullptr;       // n_bands x npw, orthonormal
@@ -234,6 +239,17 @@ int* tc_err_flag(Ctx* c);
 // enqueues the read-back of the tensor-core error flag (set once a kernel gave up waiting) into pinned
 // memory; *h (null when no tensor-core kernel ran) is valid after pinned_wait(c, "tc_err")
 int tc_flag_readback(Ctx* c, const int** h);
+// ---- tensor-core products with the projectors as the fixed operand (k_tc_beta.cu) ----
+int beta_images(Ctx* c, int ik);  // forms the two images of k-point ik if they are missing
+// P[p][b] = <beta_p | x_b> for nb rows x (FP32, ld = N_pw)
+int gemm_cn_tc_beta(Ctx* c, int ik, int nb, const float2* x, double2* P, int* err);
+// y_b += sum_p beta_p D_p P[p][b] (y: nb rows, FP32, ld = N_pw)
+int gemm_wx_tc_beta(Ctx* c, int ik, int nb, const double2* P, const double* dvec, float2* y, int* err);
+// pieces of k_tc.cu the projector products share
+void tc_cn_plan(int M, int N, int K, int* nz_out, int* kslice_out);
+int reduce_parts32(Ctx* c, int M, int N, int nz, const float2* part, double2* C, int ldc);
+int wx_presplit(Ctx* c, int M, int K, int NT, int KC, const double2* W, int ldw, bool wt, const double* s,
+                float4* Wp);
 // The context behind a C-ABI handle (api.cu).
 Ctx* unwrap(paro_ctx* h);
 // Cholesky S = L L^H (n x n, row-major, device), then writes G = conj(L)^{-1} (lower) into g.

@@ -43,6 +43,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
   return false;
 }
 
+// one plain arrival
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 // one arrival that also expects `bytes` of asynchronous copies on the current phase
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
@@ -55,6 +60,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                    smem_addr(dst)),
                "l"(src), "r"(bytes), "r"(smem_addr(bar))
                : "memory");
+}
+
+// barrier `id` (1..15) over `count` threads (whole warps) of the CTA
+__device__ __forceinline__ void named_bar(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 // ---- fences ----
@@ -135,5 +145,44 @@ __device__ __forceinline__ void tmem_ld_x8(uint32_t taddr, float* v) {
   v[4] = __uint_as_float(r4); v[5] = __uint_as_float(r5); v[6] = __uint_as_float(r6); v[7] = __uint_as_float(r7);
 }
 
+// the same lanes and columns written from registers; tmem_st_wait() before the values are used
+__device__ __forceinline__ void tmem_st_x8(uint32_t taddr, const float* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+               "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+               "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 }  // namespace tc
+
+// ---- operand tiles of the tf32 products (shared by the tensor-core kernels) ----
+// byte offset of (row, 16-byte chunk) in a K-major tile with ch chunks per row: 128-byte swizzle when a
+// row is exactly 128 bytes (ch = 8: 8-row atoms of 1024 bytes, chunk c of row r at c ^ (r % 8)), else the
+// no-swizzle core-matrix layout (8 rows x 16 bytes contiguous)
+__host__ __device__ __forceinline__ uint32_t tc_off(int row, int chunk, int ch) {
+  if (ch == 8) return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
+  return (uint32_t)(((row >> 3) * ch + chunk) * 128 + (row & 7) * 16);
+}
+
+// descriptor of the K step s2 (8 TF32 values) of a tile at shared address base, layout as in tc_off
+__device__ __forceinline__ uint64_t tc_desc(uint32_t base, int s2, int ch) {
+  if (ch == 8) return tc::smem_desc_sw128(base + (uint32_t)s2 * 32u);
+  return tc::smem_desc(base + (uint32_t)s2 * 256u, 128u, (uint32_t)ch * 128u);
+}
+
+// dynamic shared memory rounded up to the 1024-byte alignment of the swizzle atoms (1 KB extra allocated)
+__device__ __forceinline__ unsigned char* tc_align1024(unsigned char* p) {
+  const uint32_t a = tc::smem_addr(p);
+  return p + ((1024u - (a & 1023u)) & 1023u);
+}
+
+// split (v0, v1) into hi and lo TF32 quadruples (re0, im0, re1, im1)
+__device__ __forceinline__ void tc_split(float2 v0, float2 v1, float4& h, float4& l) {
+  h.x = tc::tf32_round(v0.x); h.y = tc::tf32_round(v0.y); h.z = tc::tf32_round(v1.x); h.w = tc::tf32_round(v1.y);
+  l.x = tc::tf32_round(v0.x - h.x); l.y = tc::tf32_round(v0.y - h.y);
+  l.z = tc::tf32_round(v1.x - h.z); l.w = tc::tf32_round(v1.y - h.w);
+}
+
 }  // namespace paro

@@ -20,6 +20,7 @@ PARO_OK, PARO_ERR_ARG, PARO_ERR_CUDA, PARO_ERR_BREAKDOWN, PARO_ERR_NOT_CONVERGED
 PARO_FP64, PARO_MIXED = 0, 1
 PARO_C64, PARO_C32 = 0, 1
 PARO_ALG1, PARO_ALG2, PARO_ALG3 = 1, 2, 3
+PARO_VNL_ACCURATE, PARO_VNL_TENSOR = 0, 1
 ENERGY_TERMS = ("kinetic", "nonlocal", "local", "hartree", "xc", "ewald", "total")
 
 # Every symbol include/paro.h declares.
@@ -27,7 +28,7 @@ EXPORTS = (
     "paro_create", "paro_set_local_pp", "paro_set_kb", "paro_set_positions", "paro_set_veff", "paro_set_veff_rest",
     "paro_get_veff",
     "paro_get_vloc", "paro_set_density", "paro_set_ecut", "paro_set_gamma_real", "paro_set_smearing", "paro_get_occupations", "paro_grid", "paro_npw", "paro_miller", "paro_sigma", "paro_apply_h",
-    "paro_apply_h_noalloc", "paro_apply_h_adjoint", "paro_orthonormalize", "paro_solve_source", "paro_batch_create", "paro_batch_apply_h",
+    "paro_apply_h_noalloc", "paro_apply_vnl", "paro_apply_h_adjoint", "paro_orthonormalize", "paro_solve_source", "paro_batch_create", "paro_batch_apply_h",
     "paro_batch_step", "paro_batch_info", "paro_batch_tuning", "paro_batch_destroy",
     "paro_set_orbitals", "paro_get_orbitals", "paro_get_eigenvalues", "paro_get_residuals", "paro_step",
     "paro_eigh", "paro_density", "paro_energy", "paro_scf_step", "paro_scf", "paro_set_state", "paro_profile",
@@ -70,6 +71,7 @@ _SIGS = {
     "paro_sigma": (ctypes.c_int, [_vp, _c_dbl_p]),
     "paro_apply_h": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "paro_apply_h_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),
+    "paro_apply_vnl": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int]),
     "paro_apply_h_adjoint": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp,
                                             _vp]),
     "paro_set_positions": (ctypes.c_int, [_vp, _c_dbl_p]),
@@ -296,6 +298,17 @@ class Context:
         psi = psi.contiguous()
         self._check(self.lib.paro_apply_h_noalloc(self.h, ik, psi.shape[0], dt, _vp(psi.data_ptr()),
                                                   _vp(out.data_ptr())))
+        return out
+
+    def apply_vnl(self, psi, form=PARO_VNL_ACCURATE, ik=0):
+        """The nonlocal term V_nl psi alone (device tensor of psi's shape and dtype); form PARO_VNL_TENSOR
+        (complex64 only) is the tensor-core product of the inner solves."""
+        torch = self.torch
+        dt = PARO_C64 if psi.dtype == torch.complex128 else PARO_C32
+        psi = psi.contiguous()
+        out = torch.empty_like(psi)
+        self._check(self.lib.paro_apply_vnl(self.h, ik, psi.shape[0], dt, _vp(psi.data_ptr()), _vp(out.data_ptr()),
+                                            int(form)))
         return out
 
     def apply_h_adjoint(self, psi, w, ik=0, grads=("psi", "v", "pos")):
