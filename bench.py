@@ -165,7 +165,7 @@ def launch_work(name: str, s):
     if kern.startswith("k_gemm_cn") and tag in ("gram", "hsub"):
         # Hermitian products: the nb (nb + 1) / 2 distinct entries are the algorithmic work
         return "alu32", 8 * nb * (nb + 1) // 2 * npw
-    if kern in ("k_gemm_cn_tc", "k_gemm_wx_tc") and tag == "pcg":
+    if kern in ("k_gemm_cn_tc", "k_gemm_wx_tc", "k_gemm_cn_tcb", "k_gemm_wx_tcb") and tag == "pcg":
         # projector products of the inner solves: every source column, whatever the active set
         return "tensor", 8 * npj * nb * npw
     if kern == "k_gemm_wx_tc" and tag in ("orth",):
@@ -189,8 +189,8 @@ def launch_work(name: str, s):
 # DRAM bytes per launch from one ncu capture, valid only for the kernel source it was taken on
 # (sha256 prefix of the file defining the kernel); otherwise the roofline's traffic is null.
 TRAFFIC = {
-    # k_plane_reg<float, 72, 72, 9>, one full 144-band launch: 84.24 MB read + 24.14 MB written
-    "k_plane<f32>": (108380160, "paper_1702_04045_gb300/csrc/hpsi_passes_reg.cuh", "17078b132bc7da4c"),
+    # k_plane_reg<float, 72, 72, 9>, one full 144-band launch: 84.24 MB read + 27.49 MB written
+    "k_plane<f32>": (111727360, "paper_1702_04045_gb300/csrc/hpsi_passes_reg.cuh", "00b23b2d37ce29a1"),
 }
 
 
@@ -359,7 +359,15 @@ def run_ours(args, rank, world, local, pg):
                 break
         if roof:
             break
-    roof_tensor = {k: roof_of(k) for k in ("pcg:k_gemm_cn_tc", "pcg:k_gemm_wx_tc") if k in prof} or None
+    roof_tensor = {k: roof_of(k) for k in ("pcg:k_gemm_cn_tcb", "pcg:k_gemm_wx_tcb") if k in prof} or None
+    if roof_tensor:  # the same launches against HBM: the projector image (hi + lo, 16 bytes per complex entry)
+        # and the orbital rows read; the update also reads and writes H x
+        for k, r in roof_tensor.items():
+            if r:
+                nbytes = 16 * s["nproj"] * s["npw"] + 8 * s["nb"] * s["npw"] * (1 if "cn" in k else 2)
+                r["bytes_per_launch"] = nbytes
+                r["hbm_gbs"] = nbytes / (r["avg_launch_ms"] / 1e3) / 1e9
+                r["hbm_frac"] = r["hbm_gbs"] / hbm
     bsz = 16 if args.precision == "fp64" else 8
     tag = "f64" if bsz == 16 else "f32"
     hpsi = None
