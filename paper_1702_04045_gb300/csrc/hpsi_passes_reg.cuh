@@ -338,6 +338,7 @@ __global__ void __launch_bounds__(32 * NW) k_plane_density_reg(const cplx<T>* __
                                                            const int* __restrict__ xrow_c, int nxr,
                                                            const cplx<T>* __restrict__ twx,
                                                            const cplx<T>* __restrict__ twy, double wfac,
+                                                           const double* __restrict__ wsq,
                                                            double* __restrict__ part) {
   using SX = LineShape<N1>;
   using SY = LineShape<N2>;
@@ -394,6 +395,7 @@ __global__ void __launch_bounds__(32 * NW) k_plane_density_reg(const cplx<T>* __
       constexpr int Q = SX::Q, P = SX::P, G = 32 / P;
       const int grp = lane / P, p = lane % P, pr = bitrev_lane<P>(p);
       const LaneTw<T, Q, P> ltx(tx, p);
+      const TACC wb = wsq ? (TACC)(wsq[b] * wsq[b]) : (TACC)1;  // the band's occupation weight
       for (int c0 = warp * G; c0 < N2; c0 += nw * G) {
         const int y = c0 + grp;
         const bool ok = y < N2;
@@ -409,7 +411,7 @@ __global__ void __launch_bounds__(32 * NW) k_plane_density_reg(const cplx<T>* __
 #pragma unroll
           for (int k = 0; k < Q; ++k) {
             const TACC re = v[k].x, im = v[k].y;
-            acc[(LX::kTile ? dt_index<Q, P>(p, pr, k) : k + Q * pr) * N2 + y] += re * re + im * im;
+            acc[(LX::kTile ? dt_index<Q, P>(p, pr, k) : k + Q * pr) * N2 + y] += wb * (re * re + im * im);
           }
       }
     }
@@ -433,31 +435,32 @@ static size_t density_reg_smem(int nxr) {
 
 template <typename T, int N, typename TACC>
 static int density_planes_reg_acc(Ctx* c, const Basis& B, const cplx<T>* S, int nbands, int ngrp, int gsize,
-                                  double wfac, double* part) {
+                                  double wfac, const double* wsq, double* part) {
   static int done[64];
   int st;
   if ((st = set_smem_once(c, k_plane_density_reg<T, N, N, TACC>, done))) return st;
   const size_t smem = density_reg_smem<T, N, TACC>(B.nxr);
   k_plane_density_reg<T, N, N, TACC><<<dim3(N, ngrp), 32 * PlaneWarps<N>::value, smem, c->stream>>>(
-      S, B.ncol, nbands, gsize, B.d_stick_of, B.d_xrow_c, B.nxr, tw_of<T>(c, 0), tw_of<T>(c, 1), wfac, part);
+      S, B.ncol, nbands, gsize, B.d_stick_of, B.d_xrow_c, B.nxr, tw_of<T>(c, 0), tw_of<T>(c, 1), wfac, wsq, part);
   PARO_LAUNCH(c, "k_plane_density_reg");
   return PARO_OK;
 }
 
 template <typename T, int N>
 static int density_planes_reg_n(Ctx* c, const Basis& B, const cplx<T>* S, int nbands, int ngrp, int gsize,
-                                double wfac, double* part) {
+                                double wfac, const double* wsq, double* part) {
   // FP32 orbitals: the group's |psi|^2 sum in FP32 (an 8-term sum, rounding of the FP32 FFT's own size) keeps
   // the per-point accumulation off GB300's slow FP64 pipe; the groups are summed in FP64 by the caller
-  if constexpr (sizeof(T) == 4) return density_planes_reg_acc<T, N, float>(c, B, S, nbands, ngrp, gsize, wfac, part);
+  if constexpr (sizeof(T) == 4)
+    return density_planes_reg_acc<T, N, float>(c, B, S, nbands, ngrp, gsize, wfac, wsq, part);
   if (density_reg_smem<T, N, double>(B.nxr) <= 227 * 1024)
-    return density_planes_reg_acc<T, N, double>(c, B, S, nbands, ngrp, gsize, wfac, part);
+    return density_planes_reg_acc<T, N, double>(c, B, S, nbands, ngrp, gsize, wfac, wsq, part);
   return fail(c, PARO_ERR_ARG, "density: plane too large for shared memory");
 }
 
 template <typename T>
-int density_planes_reg(Ctx* c, int ik, const cplx<T>* S, int nbands, int ngrp, int gsize, double wfac, double* part,
-                       bool* used, bool* f32part) {
+int density_planes_reg(Ctx* c, int ik, const cplx<T>* S, int nbands, int ngrp, int gsize, double wfac,
+                       const double* wsq, double* part, bool* used, bool* f32part) {
   *used = false;
   *f32part = sizeof(T) == 4;  // FP32 orbitals: unscaled FP32 partial planes (density_planes_reg_n)
   const int n = c->N[0];
@@ -468,11 +471,11 @@ int density_planes_reg(Ctx* c, int ik, const cplx<T>* S, int nbands, int ngrp, i
   const Basis& B = c->bases[ik];
   *used = true;
   switch (n) {
-    case 32: return density_planes_reg_n<T, 32>(c, B, S, nbands, ngrp, gsize, wfac, part);
-    case 36: return density_planes_reg_n<T, 36>(c, B, S, nbands, ngrp, gsize, wfac, part);
-    case 48: return density_planes_reg_n<T, 48>(c, B, S, nbands, ngrp, gsize, wfac, part);
-    case 72: return density_planes_reg_n<T, 72>(c, B, S, nbands, ngrp, gsize, wfac, part);
-    case 128: return density_planes_reg_n<T, 128>(c, B, S, nbands, ngrp, gsize, wfac, part);
+    case 32: return density_planes_reg_n<T, 32>(c, B, S, nbands, ngrp, gsize, wfac, wsq, part);
+    case 36: return density_planes_reg_n<T, 36>(c, B, S, nbands, ngrp, gsize, wfac, wsq, part);
+    case 48: return density_planes_reg_n<T, 48>(c, B, S, nbands, ngrp, gsize, wfac, wsq, part);
+    case 72: return density_planes_reg_n<T, 72>(c, B, S, nbands, ngrp, gsize, wfac, wsq, part);
+    case 128: return density_planes_reg_n<T, 128>(c, B, S, nbands, ngrp, gsize, wfac, wsq, part);
     default: *used = false; return PARO_OK;
   }
 }

@@ -259,8 +259,10 @@ int sticks_inverse(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* S) {
 
 template int sticks_inverse<double>(Ctx*, int, int, const double2*, double2*);
 template int sticks_inverse<float>(Ctx*, int, int, const float2*, float2*);
-template int density_planes_reg<double>(Ctx*, int, const double2*, int, int, int, double, double*, bool*, bool*);
-template int density_planes_reg<float>(Ctx*, int, const float2*, int, int, int, double, double*, bool*, bool*);
+template int density_planes_reg<double>(Ctx*, int, const double2*, int, int, int, double, const double*, double*,
+                                         bool*, bool*);
+template int density_planes_reg<float>(Ctx*, int, const float2*, int, int, int, double, const double*, double*,
+                                        bool*, bool*);
 
 template <typename T> static const cplx<T>* beta_of(const Basis& b);
 template <> const double2* beta_of<double>(const Basis& b) { return b.d_beta; }

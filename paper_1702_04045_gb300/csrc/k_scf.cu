@@ -534,6 +534,35 @@ __device__ __forceinline__ void lda_pz(R rho, R* eps, R* v) {
   *v = vx + vc;
 }
 
+// eps_xc of the same functional in FP64 accuracy with a fraction of the FP64 instructions (the energy's
+// grid sum; GB300's FP64 pipe makes CUDA's FP64 cube root the cost of that pass): the cube root of rho, its
+// reciprocal, the square root of r_s and the reciprocal of the correlation denominator each start from an
+// FP32 estimate and take one Newton step in FP64, which squares the estimate's ~1e-7 relative error; the
+// high-density branch keeps the FP64 logarithm.
+__device__ __forceinline__ double lda_pz_eps64(double rho) {
+  if (!(rho >= 1e-30)) return 0.0;
+  const float c0f = cbrtf((float)rho);
+  const double c0 = c0f;
+  const double c = fma(fma(-c0 * c0, c0, rho), (double)(1.0f / (3.0f * c0f * c0f)), c0);  // rho^(1/3)
+  const double i0 = (double)(1.0f / c0f);
+  const double ic = fma(i0, fma(-c, i0, 1.0), i0);  // 1 / c
+  const double ex = -0.75 * 0.9847450218426965 * c;  // -(3/4) (3 rho / pi)^(1/3)
+  const double rs = 0.6203504908994001 * ic;         // (3 / (4 pi rho))^(1/3)
+  double ec;
+  if (rs >= 1.0) {
+    const float s0f = sqrtf((float)rs);
+    const double s0 = s0f;
+    const double sq = fma(fma(-s0, s0, rs), (double)(0.5f / s0f), s0);
+    const double den = fma(0.3334, rs, fma(1.0529, sq, 1.0));
+    const double d0 = (double)(1.0f / (float)den);
+    ec = -0.1423 * fma(d0, fma(-den, d0, 1.0), d0);
+  } else {
+    const double lr = log(rs);
+    ec = 0.0311 * lr - 0.048 + 0.0020 * rs * lr - 0.0116 * rs;
+  }
+  return ex + ec;
+}
+
 template <typename R>
 __global__ void k_veff_combine(int n, const double* __restrict__ vloc, const double2* __restrict__ vh,
                                const double* __restrict__ rho, double* __restrict__ veff) {
@@ -656,7 +685,7 @@ __global__ void __launch_bounds__(512, 1) k_plane_density(const cplx<T>* __restr
                                 const int* __restrict__ col_x, const int* __restrict__ col_y,
                                 const int* __restrict__ xrows, int nxr, FftPlan px, FftPlan py,
                                 const cplx<T>* __restrict__ twx, const cplx<T>* __restrict__ twy, double wfac,
-                                double* __restrict__ part) {
+                                const double* __restrict__ wsq, double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N1 = px.n, N2 = py.n;
   cplx<T>* tx = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -676,9 +705,10 @@ __global__ void __launch_bounds__(512, 1) k_plane_density(const cplx<T>* __restr
     __syncthreads();
     fft_lines<T, true, false>(P, py, nxr, 1, LinesMapped{xrows, N2}, ty);
     fft_lines<T, true, true>(P, px, N2, N2, LinesDirect{1}, tx);
+    const double w = wsq ? wsq[b] * wsq[b] : 1.0;
     for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) {
       const double re = P[i].x, im = P[i].y;
-      acc[i] += re * re + im * im;
+      acc[i] += w * (re * re + im * im);
     }
     __syncthreads();
   }
@@ -720,7 +750,8 @@ template <> const float2* twid<float>(const Ctx* c, int ax) { return c->d_tw32[a
 
 // rho(r) (+)= wfac sum_b |psi~_b(r)|^2 for nbands orbitals of k-point ik (the FFTs in T, sums in FP64)
 template <typename T>
-int density_bands(Ctx* c, int ik, int nbands, const cplx<T>* psi, double wfac, double* rho_dev, bool accumulate) {
+int density_bands(Ctx* c, int ik, int nbands, const cplx<T>* psi, double wfac, double* rho_dev, bool accumulate,
+                  const double* wsq) {
   const int N1 = c->N[0], N2 = c->N[1], N3 = c->N[2];
   const int gsize = 8;
   const int ngrp = (nbands + gsize - 1) / gsize;
@@ -737,13 +768,13 @@ int density_bands(Ctx* c, int ik, int nbands, const cplx<T>* psi, double wfac, d
   if (st) return st;
   cudaEvent_t ev = prof_begin(c);
   bool used = false, f32part = false;
-  if ((st = density_planes_reg<T>(c, ik, S, nbands, ngrp, gsize, wfac, part, &used, &f32part))) return st;
+  if ((st = density_planes_reg<T>(c, ik, S, nbands, ngrp, gsize, wfac, wsq, part, &used, &f32part))) return st;
   if (!used) {
     if (smem > 227 * 1024) return fail(c, PARO_ERR_ARG, "density: plane too large for shared memory");
     PARO_CU(c, cudaFuncSetAttribute(k_plane_density<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     k_plane_density<T><<<dim3(N3, ngrp), threads, smem, c->stream>>>(
         S, B.ncol, nbands, gsize, B.d_col_x, B.d_col_y, B.d_xrows, B.nxr, c->plan[0], c->plan[1], twid<T>(c, 0),
-        twid<T>(c, 1), wfac, part);
+        twid<T>(c, 1), wfac, wsq, part);
     PARO_LAUNCH(c, "k_plane_density");
   }
   prof_end(c, sizeof(T) == 8 ? "k_plane_density<f64>" : "k_plane_density<f32>", ev);
@@ -770,12 +801,15 @@ __global__ void k_grid_sum(int n, const double* __restrict__ x, double* __restri
 // norms[k][b] (one warp, fixed order); the scale stays on the device
 __global__ void k_renorm_scalar(int nblk, const double* __restrict__ part, int nk, int nb, int nrow,
                                 const double* __restrict__ wk, double fac, const double* __restrict__ norms,
-                                double dv, double* __restrict__ a) {
+                                const double* __restrict__ wsq, double dv, double* __restrict__ a) {
   const int lane = threadIdx.x;
   double t = 0.0, g = 0.0;
   for (int i = lane; i < nblk; i += 32) t += part[i];
   for (int k = 0; k < nk; ++k)
-    for (int b = lane; b < nrow; b += 32) g += wk[k] * fac * norms[(size_t)k * nb + b];
+    for (int b = lane; b < nrow; b += 32) {
+      const size_t o = (size_t)k * nb + b;
+      g += wk[k] * fac * (wsq ? wsq[o] * wsq[o] : 1.0) * norms[o];
+    }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     t += __shfl_xor_sync(0xffffffffu, t, o);
@@ -810,7 +844,10 @@ int density(Ctx* c, const cplx<T>* const* psis, double* rho_dev) {
     int st;
     const int npw = c->bases[ik].npw;
     const cplx<T>* rows = psis[ik];
-    if (c->kT > 0) {
+    // smeared occupations: the density passes weight each band by f (sqrt(f) squared); in the
+    // real-wavefunction mode, whose transforms carry two bands, the rows are scaled by sqrt(f) first
+    const double* wsq = c->kT > 0 && !gamma_on(c) ? c->d_occ_sqrt + (size_t)ik * c->nb : nullptr;
+    if (c->kT > 0 && gamma_on(c)) {
       cplx<T>* y = static_cast<cplx<T>*>(
           ws_get(c, sizeof(T) == 8 ? "dens_scaled64" : "dens_scaled32", (size_t)nrow * npw * sizeof(cplx<T>)));
       if (!y) return PARO_ERR_CUDA;
@@ -822,7 +859,7 @@ int density(Ctx* c, const cplx<T>* const* psis, double* rho_dev) {
     if (gamma_on(c)) {  // real orbitals: two per transform, |a + i b|^2 = a^2 + b^2
       st = gamma_density_rows<T>(c, ik, nrow, rows, wfac, rho_dev, ik > 0, &nnorm, &rows);
     } else {
-      st = density_bands<T>(c, ik, nrow, rows, wfac, rho_dev, ik > 0);
+      st = density_bands<T>(c, ik, nrow, rows, wfac, rho_dev, ik > 0, wsq);
     }
     if (st) return st;
     if (renorm) {
@@ -840,17 +877,19 @@ int density(Ctx* c, const cplx<T>* const* psis, double* rho_dev) {
   if (int st = h2d_async(c, "dens_kw", wk, c->kw.data(), c->nk * sizeof(double))) return st;
   k_grid_sum<<<nblk, 256, 0, c->stream>>>(c->ngrid, rho_dev, part);
   PARO_LAUNCH(c, "k_grid_sum");
-  // smeared rows already carry sqrt(f) in their norms; otherwise f = 2
+  // smeared: each norm weighted by f (the scaled rows of the real-wavefunction mode already carry it);
+  // otherwise f = 2
+  const bool weighted = c->kT > 0 && !gamma_on(c);
   k_renorm_scalar<<<1, 32, 0, c->stream>>>(nblk, part, c->nk, c->nb, nrow, wk, c->kT > 0 ? 1.0 : 2.0, norms,
-                                           c->omega / c->ngrid, part + nblk);
+                                           weighted ? c->d_occ_sqrt : nullptr, c->omega / c->ngrid, part + nblk);
   PARO_LAUNCH(c, "k_renorm_scalar");
   k_grid_scale<<<(c->ngrid + 255) / 256, 256, 0, c->stream>>>(c->ngrid, part + nblk, rho_dev);
   PARO_LAUNCH(c, "k_grid_scale");
   return PARO_OK;
 }
 
-template int density_bands<double>(Ctx*, int, int, const double2*, double, double*, bool);
-template int density_bands<float>(Ctx*, int, int, const float2*, double, double*, bool);
+template int density_bands<double>(Ctx*, int, int, const double2*, double, double*, bool, const double*);
+template int density_bands<float>(Ctx*, int, int, const float2*, double, double*, bool, const double*);
 template int density<double>(Ctx*, const double2* const*, double*);
 template int density<float>(Ctx*, const float2* const*, double*);
 
@@ -904,10 +943,16 @@ __global__ void k_grid_energies(int n, const double* __restrict__ vloc, const do
   __shared__ double red[32];
   double sl = 0.0, sx = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    R e, v;
-    lda_pz<R>((R)rho[i], &e, &v);
+    double e;
+    if constexpr (sizeof(R) == 8) {
+      e = lda_pz_eps64(rho[i]);
+    } else {
+      R ef, vf;
+      lda_pz<R>((R)rho[i], &ef, &vf);
+      e = (double)ef;
+    }
     sl += vloc[i] * rho[i];
-    sx += rho[i] * (double)e;
+    sx += rho[i] * e;
   }
   sl = block_sum(sl, red);
   if (threadIdx.x == 0) part[2 * blockIdx.x] = sl;

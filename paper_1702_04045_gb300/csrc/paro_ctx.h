@@ -333,11 +333,13 @@ template <typename T>
 int sticks_inverse(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* S);
 // density planes with the register FFT (cubic grids it supports); *used = false otherwise
 template <typename T>
-int density_planes_reg(Ctx* c, int ik, const cplx<T>* S, int nbands, int ngrp, int gsize, double wfac, double* part,
-                       bool* used, bool* f32part);
+int density_planes_reg(Ctx* c, int ik, const cplx<T>* S, int nbands, int ngrp, int gsize, double wfac,
+                       const double* wsq, double* part, bool* used, bool* f32part);
 // rho(r) (+)= wfac sum_b |psi~_b(r)|^2 over nbands rows of psi at k-point ik (psi~: unnormalised inverse DFT)
 template <typename T>
-int density_bands(Ctx* c, int ik, int nbands, const cplx<T>* psi, double wfac, double* rho_dev, bool accumulate);
+// wsq (device, may be null): per-band sqrt(f) of these rows; each band's |psi|^2 is then weighted by f
+int density_bands(Ctx* c, int ik, int nbands, const cplx<T>* psi, double wfac, double* rho_dev, bool accumulate,
+                  const double* wsq = nullptr);
 
 // ---- adjoint of H psi (k_adjoint.cu, k_scf.cu) ----
 int apply_h_adjoint(Ctx* c, int ik, int nb, int dtype, const void* psi, const void* w, void* gpsi, double* gv,
