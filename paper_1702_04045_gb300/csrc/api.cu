@@ -422,28 +422,20 @@ __global__ void k_axpy_rows(int npw, cplx<T>* __restrict__ y, const cplx<T>* __r
     y[o + g] = cadd(y[o + g], cscale(x[o + g], sx));
 }
 
-// rhs_b = (eps_b - sigma) psi_b (Algorithm 1) or -(H psi_b - eps_b psi_b) (Algorithm 2), formed in
-// FP64 from the current orbitals and stored in T
+// rhs_b = -(H psi_b - eps_b psi_b) (Algorithms 2 and 3's correction equations), formed in FP64 from the
+// current orbitals and stored in T
 template <typename T>
-static int source_rhs(Ctx* c, int ik, bool alg2, cplx<T>* rhs) {
+static int source_rhs(Ctx* c, int ik, cplx<T>* rhs) {
   Basis& b = c->bases[ik];
   const int nb = c->nb, npw = b.npw;
   double* f = static_cast<double*>(ws_get(c, "rhs_f", (size_t)nb * sizeof(double)));
   double2* tmp = static_cast<double2*>(ws_get(c, "rhs_tmp", (size_t)nb * npw * sizeof(double2)));
   if (!f || !tmp) return PARO_ERR_CUDA;
-  int st = veff_stats(c);
-  if (st) return st;
-  std::vector<double> hf(nb);
-  for (int i = 0; i < nb; ++i) hf[i] = alg2 ? b.eps[i] : b.eps[i] - c->sigma_k[ik];
-  if ((st = h2d_async(c, "rhs_f", f, hf.data(), nb * sizeof(double)))) return st;
-  if (sizeof(T) == 4 && !alg2 && b.d_psi32)  // (eps - sigma) psi straight from the FP32 orbitals
-    return scale_rows<float>(c, nb, npw, b.d_psi32, f, reinterpret_cast<float2*>(rhs));
-  st = scale_rows<double>(c, nb, npw, b.d_psi, f, tmp);
-  if (st) return st;
-  if (alg2) {
-    k_axpy_rows<double><<<dim3((npw + 255) / 256, nb), 256, 0, c->stream>>>(npw, tmp, b.d_hpsi, -1.0);
-    PARO_LAUNCH(c, "k_axpy_rows");
-  }
+  int st;
+  if ((st = h2d_async(c, "rhs_f", f, b.eps.data(), nb * sizeof(double)))) return st;
+  if ((st = scale_rows<double>(c, nb, npw, b.d_psi, f, tmp))) return st;
+  k_axpy_rows<double><<<dim3((npw + 255) / 256, nb), 256, 0, c->stream>>>(npw, tmp, b.d_hpsi, -1.0);
+  PARO_LAUNCH(c, "k_axpy_rows");
   if (sizeof(T) == 8) {
     PARO_CU(c, cudaMemcpyAsync(rhs, tmp, (size_t)nb * npw * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
     return PARO_OK;
@@ -457,16 +449,22 @@ static int solve_sources(Ctx* c, int ik, bool alg2, double rel_tol, int max_it, 
   Basis& b = c->bases[ik];
   const int nb = c->nb, npw = b.npw;
   const bool f64 = sizeof(T) == 8;
+  int st;
+  if (!alg2) {
+    // Algorithm 1: rhs = (eps - sigma) psi, started at the orbitals, whose H psi the last Rayleigh-Ritz step
+    // left in hpsi; the solver's first pass forms rhs, the start vectors and their residuals together
+    double* f = static_cast<double*>(ws_get(c, "rhs_f", (size_t)nb * sizeof(double)));
+    if (!f) return PARO_ERR_CUDA;
+    if ((st = veff_stats(c))) return st;
+    std::vector<double> hf(nb);
+    for (int i = 0; i < nb; ++i) hf[i] = b.eps[i] - c->sigma_k[ik];
+    if ((st = h2d_async(c, "rhs_f", f, hf.data(), nb * sizeof(double)))) return st;
+    return pcg_run<T>(c, ik, nb, nullptr, x, false, rel_tol, max_it, nullptr, hpsi_of<T>(b), hx, psi_of<T>(b), f);
+  }
   cplx<T>* rhs = static_cast<cplx<T>*>(ws_get(c, wsn(f64, "src_rhs64", "src_rhs32"), (size_t)nb * npw * sizeof(cplx<T>)));
   if (!rhs) return PARO_ERR_CUDA;
-  int st = source_rhs<T>(c, ik, alg2, rhs);
-  if (st) return st;
-  if (!alg2)
-    PARO_CU(c, cudaMemcpyAsync(x, psi_of<T>(b), (size_t)nb * npw * sizeof(cplx<T>), cudaMemcpyDeviceToDevice,
-                               c->stream));
-  // Algorithm 1 starts from the orbitals, whose H psi the last Rayleigh-Ritz step left in hpsi
-  return pcg_run<T>(c, ik, nb, rhs, x, alg2, rel_tol, max_it, nullptr, alg2 ? nullptr : hpsi_of<T>(b),
-                    alg2 ? nullptr : hx);
+  if ((st = source_rhs<T>(c, ik, rhs))) return st;
+  return pcg_run<T>(c, ik, nb, rhs, x, true, rel_tol, max_it, nullptr, nullptr, nullptr);
 }
 
 template <typename T>

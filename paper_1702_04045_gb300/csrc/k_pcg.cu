@@ -52,6 +52,40 @@ __global__ void __launch_bounds__(kVT) k_pcg_init(int npw, int nchunk, const cpl
   if (threadIdx.x == 0) prr[(size_t)b * nchunk + ch] = rr;
 }
 
+// The start of the source solves from x0 = psi with H psi known: rhs = f psi, r = rhs - (H psi - sigma psi),
+// z = M r, p = z, partials of <r,z> and |r|^2, and x = psi, hx = H psi (hx may be null) in the same pass
+template <typename T>
+__global__ void __launch_bounds__(kVT) k_pcg_init_src(int npw, int nchunk, const cplx<T>* __restrict__ psi,
+                                                      const cplx<T>* __restrict__ hpsi, const double* __restrict__ f,
+                                                      T sigma, cplx<T>* __restrict__ x, cplx<T>* __restrict__ hx,
+                                                      cplx<T>* __restrict__ r, cplx<T>* __restrict__ p,
+                                                      const T* __restrict__ kin, T pshift, double* __restrict__ prz,
+                                                      double* __restrict__ prr) {
+  __shared__ double red[32];
+  const int b = blockIdx.y, ch = blockIdx.x;
+  const size_t o = (size_t)b * npw;
+  const T fb = (T)f[b];
+  DotAcc<T> az, ar;
+  const int g0 = ch * kChunk, g1 = min(npw, g0 + kChunk);
+  for (int g = g0 + threadIdx.x; g < g1; g += kVT) {
+    const cplx<T> v = psi[o + g], h = hpsi[o + g];
+    const cplx<T> ap = mk<T>(h.x - sigma * v.x, h.y - sigma * v.y);
+    const cplx<T> rv = csub(cscale(v, fb), ap);
+    const T m = (T)1 / (kin[g] + pshift);
+    x[o + g] = v;
+    if (hx) hx[o + g] = h;
+    r[o + g] = rv;
+    p[o + g] = cscale(rv, m);
+    const T q = rv.x * rv.x + rv.y * rv.y;
+    ar.add(q);
+    az.add(q * m);
+  }
+  double rz = block_sum(az.value(), red);
+  if (threadIdx.x == 0) prz[(size_t)b * nchunk + ch] = rz;
+  double rr = block_sum(ar.value(), red);
+  if (threadIdx.x == 0) prr[(size_t)b * nchunk + ch] = rr;
+}
+
 __global__ void k_pcg_band_init(int nb, int nchunk, const double* __restrict__ prz, const double* __restrict__ prr,
                                 double* __restrict__ rz, double* __restrict__ r0n, int* __restrict__ active,
                                 int* __restrict__ its, int* __restrict__ nactive) {
@@ -224,9 +258,11 @@ __global__ void k_shift_known(int npw, const cplx<T>* __restrict__ hx, const cpl
 // of the start vectors when the caller already has it (the orbitals' H psi from the last
 // Rayleigh-Ritz step), which saves the first H application. hx (may be null; needs hx0 or x0_zero):
 // receives H x of the solutions, carried along the iteration from the products the solver forms anyway.
+// x0src, fsrc (both or neither): rhs = diag(fsrc) x0src and x0 = x0src, formed in the first pass (rhs is then
+// not read; needs hx0 = H x0src).
 template <typename T>
 int pcg_run(Ctx* c, int ik, int nb, const cplx<T>* rhs, cplx<T>* x, bool x0_zero, double rel_tol, int max_it,
-            int* iters, const cplx<T>* hx0, cplx<T>* hx) {
+            int* iters, const cplx<T>* hx0, cplx<T>* hx, const cplx<T>* x0src, const double* fsrc) {
   ProfTag tag(c, "pcg");
   TcScope tcs(c);  // the inner solves tolerate the 3xTF32 products
   const Basis& B = c->bases[ik];
@@ -251,23 +287,30 @@ int pcg_run(Ctx* c, int ik, int nb, const cplx<T>* rhs, cplx<T>* x, bool x0_zero
   const dim3 gv(nchunk, nb);
   const int tb = (nb + 127) / 128;
   PARO_CU(c, cudaMemsetAsync(flags, 0, 2 * sizeof(int), c->stream));
-  if (hx) {
-    if (x0_zero) PARO_CU(c, cudaMemsetAsync(hx, 0, vb, c->stream));
-    else if (hx0) PARO_CU(c, cudaMemcpyAsync(hx, hx0, vb, cudaMemcpyDeviceToDevice, c->stream));
-    else return fail(c, PARO_ERR_ARG, "pcg_run: H x of the solutions needs H x of the start vectors");
-  }
-  if (!x0_zero && hx0) {
-    k_shift_known<T><<<dim3((npw + 255) / 256, nb), 256, 0, c->stream>>>(npw, hx0, x, (T)sigma, ap);
-    PARO_LAUNCH(c, "k_shift_known");
-  } else if (!x0_zero) {
-    st = apply_h<T>(c, ik, nb, x, ap, sigma, nullptr);
-    if (st) return st;
+  if (fsrc) {
+    if (!x0src || !hx0 || x0_zero) return fail(c, PARO_ERR_ARG, "pcg_run: the source form needs x0 and H x0");
+    k_pcg_init_src<T><<<gv, kVT, 0, c->stream>>>(npw, nchunk, x0src, hx0, fsrc, (T)sigma, x, hx, r, p, kin_ptr<T>(B),
+                                                 pshift, prz, prr);
+    PARO_LAUNCH(c, "k_pcg_init_src");
   } else {
-    PARO_CU(c, cudaMemsetAsync(x, 0, vb, c->stream));
+    if (hx) {
+      if (x0_zero) PARO_CU(c, cudaMemsetAsync(hx, 0, vb, c->stream));
+      else if (hx0) PARO_CU(c, cudaMemcpyAsync(hx, hx0, vb, cudaMemcpyDeviceToDevice, c->stream));
+      else return fail(c, PARO_ERR_ARG, "pcg_run: H x of the solutions needs H x of the start vectors");
+    }
+    if (!x0_zero && hx0) {
+      k_shift_known<T><<<dim3((npw + 255) / 256, nb), 256, 0, c->stream>>>(npw, hx0, x, (T)sigma, ap);
+      PARO_LAUNCH(c, "k_shift_known");
+    } else if (!x0_zero) {
+      st = apply_h<T>(c, ik, nb, x, ap, sigma, nullptr);
+      if (st) return st;
+    } else {
+      PARO_CU(c, cudaMemsetAsync(x, 0, vb, c->stream));
+    }
+    k_pcg_init<T><<<gv, kVT, 0, c->stream>>>(npw, nchunk, rhs, x0_zero ? nullptr : ap, r, p, kin_ptr<T>(B), pshift,
+                                             prz, prr);
+    PARO_LAUNCH(c, "k_pcg_init");
   }
-  k_pcg_init<T><<<gv, kVT, 0, c->stream>>>(npw, nchunk, rhs, x0_zero ? nullptr : ap, r, p, kin_ptr<T>(B), pshift, prz,
-                                           prr);
-  PARO_LAUNCH(c, "k_pcg_init");
   k_pcg_band_init<<<tb, 128, 0, c->stream>>>(nb, nchunk, prz, prr, rz, r0n, active, its, flags);
   PARO_LAUNCH(c, "k_pcg_band_init");
   // the first step runs without reading the active count back: every orbital with a nonzero initial
@@ -305,8 +348,9 @@ int pcg_run(Ctx* c, int ik, int nb, const cplx<T>* rhs, cplx<T>* x, bool x0_zero
 }
 
 template int pcg_run<double>(Ctx*, int, int, const double2*, double2*, bool, double, int, int*, const double2*,
-                             double2*);
-template int pcg_run<float>(Ctx*, int, int, const float2*, float2*, bool, double, int, int*, const float2*, float2*);
+                             double2*, const double2*, const double*);
+template int pcg_run<float>(Ctx*, int, int, const float2*, float2*, bool, double, int, int*, const float2*, float2*,
+                            const float2*, const double*);
 template int scale_rows<double>(Ctx*, int, int, const double2*, const double*, double2*);
 template int scale_rows<float>(Ctx*, int, int, const float2*, const double*, float2*);
 

@@ -350,7 +350,8 @@ int vloc_position_grad(Ctx* c, const double* gv, double* gpos);
 // ---- batched PCG (k_pcg.cu) ----
 template <typename T>
 int pcg_run(Ctx* c, int ik, int nb, const cplx<T>* rhs, cplx<T>* x, bool x0_zero, double rel_tol, int max_it,
-            int* iters, const cplx<T>* hx0 = nullptr, cplx<T>* hx = nullptr);
+            int* iters, const cplx<T>* hx0 = nullptr, cplx<T>* hx = nullptr, const cplx<T>* x0src = nullptr,
+            const double* fsrc = nullptr);
 template <typename T>
 int scale_rows(Ctx* c, int nb, int npw, const cplx<T>* x, const double* f_dev, cplx<T>* y);
 
