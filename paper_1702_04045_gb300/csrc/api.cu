@@ -288,6 +288,21 @@ int veff_stats(Ctx* c) {
   return PARO_OK;
 }
 
+// The mixed-precision iteration works on the FP32 orbitals and H psi; their FP64 copies are formed only
+// when a call reads them (orbitals out, Algorithm 2's right-hand sides, a restart, a cutoff step, a batch).
+int fp64_current(Ctx* c, Basis& b) {
+  const size_t n = (size_t)c->nb * b.npw;
+  if (b.psi64_stale) {
+    if (int st = convert<float, double>(c, n, b.d_psi32, b.d_psi)) return st;
+    b.psi64_stale = false;
+  }
+  if (b.hpsi64_stale) {
+    if (int st = convert<float, double>(c, n, b.d_hpsi32, b.d_hpsi)) return st;
+    b.hpsi64_stale = false;
+  }
+  return PARO_OK;
+}
+
 static int alloc_orbitals(Ctx* c, Basis& b) {
   if (!b.d_psi) {
     PARO_CU(c, cudaMalloc(&b.d_psi, (size_t)c->nb * b.npw * sizeof(double2)));
@@ -394,8 +409,7 @@ static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal, cplx<T>
     }
   }
   if (!f64) {
-    if ((st = convert<float, double>(c, (size_t)nb * npw, b.d_psi32, b.d_psi))) return st;
-    if ((st = convert<float, double>(c, (size_t)nb * npw, b.d_hpsi32, b.d_hpsi))) return st;
+    b.psi64_stale = b.hpsi64_stale = true;
     if ((st = residual_norms32(c, nb, npw, b.d_psi32, b.d_hpsi32, w, res))) return st;
   } else if ((st = residual_norms(c, nb, npw, b.d_psi, b.d_hpsi, w, res))) {
     return st;
@@ -432,7 +446,7 @@ static int source_rhs(Ctx* c, int ik, cplx<T>* rhs) {
   double2* tmp = static_cast<double2*>(ws_get(c, "rhs_tmp", (size_t)nb * npw * sizeof(double2)));
   if (!f || !tmp) return PARO_ERR_CUDA;
   int st;
-  if ((st = h2d_async(c, "rhs_f", f, b.eps.data(), nb * sizeof(double)))) return st;
+  if ((st = fp64_current(c, b)) || (st = h2d_async(c, "rhs_f", f, b.eps.data(), nb * sizeof(double)))) return st;
   if ((st = scale_rows<double>(c, nb, npw, b.d_psi, f, tmp))) return st;
   k_axpy_rows<double><<<dim3((npw + 255) / 256, nb), 256, 0, c->stream>>>(npw, tmp, b.d_hpsi, -1.0);
   PARO_LAUNCH(c, "k_axpy_rows");
@@ -721,14 +735,18 @@ static int adopt_orbitals(Ctx* c, int ik) {
   double* res = static_cast<double*>(ws_get(c, "state_res", (size_t)c->nb * sizeof(double)));
   if (!w || !res) return PARO_ERR_CUDA;
   PARO_CU(c, cudaMemcpyAsync(w, b.eps.data(), c->nb * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  b.psi64_stale = false;  // the FP64 orbitals are the ones given
   if (c->prec == PARO_MIXED) {
     if ((st = convert<double, float>(c, (size_t)c->nb * b.npw, b.d_psi, b.d_psi32))) return st;
     if ((st = apply_h<float>(c, ik, c->nb, b.d_psi32, b.d_hpsi32, 0.0, nullptr))) return st;
-    if ((st = convert<float, double>(c, (size_t)c->nb * b.npw, b.d_hpsi32, b.d_hpsi))) return st;
-  } else if ((st = apply_h<double>(c, ik, c->nb, b.d_psi, b.d_hpsi, 0.0, nullptr))) {
-    return st;
+    b.hpsi64_stale = true;
+    if ((st = residual_norms32(c, c->nb, b.npw, b.d_psi32, b.d_hpsi32, w, res))) return st;
+  } else {
+    b.hpsi64_stale = false;
+    if ((st = apply_h<double>(c, ik, c->nb, b.d_psi, b.d_hpsi, 0.0, nullptr)) ||
+        (st = residual_norms(c, c->nb, b.npw, b.d_psi, b.d_hpsi, w, res)))
+      return st;
   }
-  if ((st = residual_norms(c, c->nb, b.npw, b.d_psi, b.d_hpsi, w, res))) return st;
   b.res.resize(c->nb);
   PARO_CU(c, cudaMemcpyAsync(b.res.data(), res, c->nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   PARO_CU(c, cudaStreamSynchronize(c->stream));
@@ -744,7 +762,9 @@ static int reproject(Ctx* c, int ik) {
   if (c->prec == PARO_MIXED) {
     float2* X = rows_ws<float>(c, "X", ik);
     if (!X) return PARO_ERR_CUDA;
-    int st = convert<double, float>(c, n, b.d_psi, X);
+    int st = fp64_current(c, b);
+    if (st) return st;
+    st = convert<double, float>(c, n, b.d_psi, X);
     return st ? st : project<float>(c, ik, X, c->nb, false);
   }
   double2* X = rows_ws<double>(c, "X", ik);
@@ -924,6 +944,7 @@ static int set_ecut(Ctx* c, double ecut_new) {
   for (int ik = 0; ik < c->nk; ++ik) {
     Basis& b = c->bases[ik];
     if (!b.have_psi) continue;
+    if ((st = fp64_current(c, b))) return st;
     old_psi[ik] = b.d_psi;
     b.d_psi = nullptr;
     old_mil[ik] = b.miller;
@@ -1283,6 +1304,7 @@ int paro_set_gamma_real(paro_ctx* ctx, int enable) {
   if (st) return st;
   c->gamma_real = true;
   if (c->bases[0].have_psi) {  // the current orbitals become real and take their Ritz pairs again
+    if ((st = fp64_current(c, c->bases[0]))) return st;
     if ((st = gamma_real_rows<double>(c, 0, c->nb, c->bases[0].d_psi))) return st;
     if ((st = reproject(c, 0))) return st;
   }
@@ -1424,6 +1446,7 @@ int paro_get_orbitals(paro_ctx* ctx, int ik, void* psi, int on_device) {
   if (ik < 0 || ik >= c->nk || !psi) return PARO_ERR_ARG;
   Basis& b = c->bases[ik];
   if (!b.have_psi) return fail(c, PARO_ERR_STATE, "no orbitals");
+  if (int st = fp64_current(c, b)) return st;
   PARO_CU(c, cudaMemcpyAsync(psi, b.d_psi, (size_t)c->nb * b.npw * sizeof(double2),
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
   PARO_CU(c, cudaStreamSynchronize(c->stream));

@@ -1244,6 +1244,13 @@ int paro_batch_apply_h(paro_batch* b, int dtype, const void* const* psi, void* c
 int paro_batch_step(paro_batch* b, double rel_tol, int max_it, double* max_resid_out) {
   if (!b || max_it < 0 || !(rel_tol >= 0)) return PARO_ERR_ARG;
   int st;
+  // the batch reads each context's FP64 orbitals and H psi (it writes both precisions back)
+  for (int i = 0; i < b->nprob; ++i) {
+    Ctx& cx = *unwrap(b->ctxs[b->pk[i].first]);
+    Basis& B = cx.bases[b->pk[i].second];
+    if ((B.psi64_stale || B.hpsi64_stale) && fp64_current(&cx, B)) return berr(b, PARO_ERR_CUDA, "batch: " + cx.err);
+    B.psi64_stale = B.hpsi64_stale = false;
+  }
   BCU(b, cudaEventRecord(b->ev, b->st));  // work queued on the contexts' stream comes first
   BCU(b, cudaStreamWaitEvent(b->gst, b->ev, 0));
   if ((st = refresh_scalars(b))) return st;

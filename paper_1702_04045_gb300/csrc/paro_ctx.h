@@ -49,6 +49,8 @@ struct Basis {
   double2* d_hpsi = nullptr;      // H psi of the current orbitals
   float2* d_psi32 = nullptr;      // mixed precision: the same orbitals and H psi in FP32
   float2* d_hpsi32 = nullptr;
+  // mixed precision: the FP64 orbitals / H psi lag the FP32 ones until a call that reads them (fp64_current)
+  bool psi64_stale = false, hpsi64_stale = false;
   std::vector<double> eps;        // Ritz values
   std::vector<double> res;        // residual norms
   bool have_psi = false;
@@ -151,6 +153,9 @@ struct Ctx {
   std::vector<std::string> chol_pending;  // pinned flags of deferred Cholesky breakdown checks
   bool have_inv_g2 = false;  // the 1/|G|^2 table of the Hartree solve is in the "inv_g2" workspace
 };
+
+// brings the FP64 orbitals and H psi of a mixed-precision basis up to date with the FP32 ones (api.cu)
+int fp64_current(Ctx* c, Basis& b);
 
 // Status helpers (api.cu)
 int fail(Ctx* c, int code, const std::string& msg);
