@@ -344,14 +344,18 @@ static const char* wsn(bool f64, const char* a, const char* b) { return f64 ? a 
 // HX (may be null): H X of the rows of X at the potential of the inner solves; dvplane (may be null): the
 // change of the local potential since then (V-plane layout). With HX, H Y = G H X (+ dV Y) replaces the
 // H application.
+// defer: the residual norms and the tensor-core flag are left to project_readback (the SCF iteration
+// reads them after its energy)
 template <typename T>
-static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal, cplx<T>* HX, const T* dvplane);
+static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal, cplx<T>* HX, const T* dvplane,
+                   bool defer = false);
+static int project_readback(Ctx* c, int ik);
 template <typename T>
 static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal) {
   return project<T>(c, ik, X, nx, orthonormal, nullptr, nullptr);
 }
 template <typename T>
-static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal, cplx<T>* HX, const T* dvplane) {
+static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal, cplx<T>* HX, const T* dvplane, bool defer) {
   Basis& b = c->bases[ik];
   const int npw = b.npw, nb = c->nb;
   const bool f64 = sizeof(T) == 8;
@@ -390,41 +394,73 @@ static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal, cplx<T>
     }
     if (!done && (st = apply_h<T>(c, ik, nx, Y, HY, 0.0, nullptr))) return st;
   }
+  const int* hinfo = nullptr;
   {
     ProfTag t(c, "hsub");
     if ((st = gemm_cn<T, T, T>(c, nx, nx, npw, Y, npw, HY, npw, S, nx, true, true))) return st;
     if (gamma_on(c) && (st = gamma_real_matrix(c, nx, S))) return st;  // real orbitals: real symmetric H_sub
     k_hermitize<<<(nx * nx + 255) / 256, 256, 0, c->stream>>>(nx, S);
     PARO_LAUNCH(c, "k_hermitize");
-    // mixed: one refinement step (FP64 Ritz values, vectors well below the FP32 level of the orbitals)
-    if ((st = f64 ? eigh(c, nx, S, w, G) : eigh_mixed(c, nx, S, w, G, 1, true))) return st;  // G <- eigenvectors C
+    // mixed: one refinement step (FP64 Ritz values, vectors well below the FP32 level of the orbitals); its
+    // cluster check is read back below, with the Ritz values
+    if ((st = f64 ? eigh(c, nx, S, w, G) : eigh_mixed(c, nx, S, w, G, 1, true, &hinfo))) return st;  // G <- C
   }
-  {
+  // the rotations, H psi of the new orbitals and their residual norms
+  auto rotate = [&]() -> int {
     ProfTag t(c, "rot");
-    if ((st = gemm_wx<T, T>(c, nb, npw, nx, G, nx, false, nullptr, Y, npw, psi_of<T>(b), npw, 0.0))) return st;
-    if ((st = gemm_wx<T, T>(c, nb, npw, nx, G, nx, false, nullptr, HY, npw, hpsi_of<T>(b), npw, 0.0))) return st;
+    int s2;
+    if ((s2 = gemm_wx<T, T>(c, nb, npw, nx, G, nx, false, nullptr, Y, npw, psi_of<T>(b), npw, 0.0))) return s2;
+    if ((s2 = gemm_wx<T, T>(c, nb, npw, nx, G, nx, false, nullptr, HY, npw, hpsi_of<T>(b), npw, 0.0))) return s2;
     if (gamma_on(c)) {  // real orbitals stay real (the rotation's rounding may not keep c(-G) = conj c(G))
-      if ((st = gamma_real_rows<T>(c, ik, nb, psi_of<T>(b))) || (st = gamma_real_rows<T>(c, ik, nb, hpsi_of<T>(b))))
-        return st;
+      if ((s2 = gamma_real_rows<T>(c, ik, nb, psi_of<T>(b))) || (s2 = gamma_real_rows<T>(c, ik, nb, hpsi_of<T>(b))))
+        return s2;
     }
-  }
-  if (!f64) {
-    b.psi64_stale = b.hpsi64_stale = true;
-    if ((st = residual_norms32(c, nb, npw, b.d_psi32, b.d_hpsi32, w, res))) return st;
-  } else if ((st = residual_norms(c, nb, npw, b.d_psi, b.d_hpsi, w, res))) {
-    return st;
-  }
-  // Ritz values, residual norms and the tensor-core error flag come back with one wait
+    if (!f64) {
+      b.psi64_stale = b.hpsi64_stale = true;
+      return residual_norms32(c, nb, npw, b.d_psi32, b.d_hpsi32, w, res);
+    }
+    return residual_norms(c, nb, npw, b.d_psi, b.d_hpsi, w, res);
+  };
+  // The Ritz values come back while the rotations run: the host waits only for the eigensolve, and the
+  // caller's next work (occupations, energy) is queued behind the rotations. Residual norms and the
+  // tensor-core flag are read by project_readback.
+  const std::string rname = "proj_res_" + std::to_string(ik);
   void *he = nullptr, *hr = nullptr;
   const int* htc = nullptr;
-  if ((st = d2h_async(c, "proj_eps", w, nb * sizeof(double), &he)) ||
-      (st = d2h_async(c, "proj_res", res, nb * sizeof(double), &hr)) || (st = tc_flag_readback(c, &htc)) ||
-      (st = pinned_wait(c, htc ? "tc_err" : "proj_res")))
+  if ((st = d2h_async(c, "proj_eps", w, nb * sizeof(double), &he)) || (st = rotate()) ||
+      (st = d2h_async(c, rname.c_str(), res, nb * sizeof(double), &hr)) || (st = tc_flag_readback(c, &htc)) ||
+      (st = pinned_wait(c, "proj_eps")))
     return st;
+  if (hinfo && (*hinfo & (1 | 4 | 8))) {
+    // a cluster the mixed refinement could not resolve (rare): the FP64 solver, then the rotations again
+    // from the unchanged Rayleigh-Ritz basis
+    if ((st = eigh_mixed_check(c, nx, S, w, G, *hinfo))) return st;
+    if ((st = d2h_async(c, "proj_eps", w, nb * sizeof(double), &he)) || (st = rotate()) ||
+        (st = d2h_async(c, rname.c_str(), res, nb * sizeof(double), &hr)) || (st = tc_flag_readback(c, &htc)) ||
+        (st = pinned_wait(c, "proj_eps")))
+      return st;
+  }
   b.eps.assign(static_cast<const double*>(he), static_cast<const double*>(he) + nb);
-  b.res.assign(static_cast<const double*>(hr), static_cast<const double*>(hr) + nb);
-  if (htc && *htc) return fail(c, PARO_ERR_TIMEOUT, "tensor-core product: mbarrier wait gave up");
+  b.res_pending = true;
   b.have_psi = true;
+  return defer ? PARO_OK : project_readback(c, ik);
+}
+
+// The residual norms of the last Rayleigh-Ritz step of k-point ik and the tensor-core error flag.
+static int project_readback(Ctx* c, int ik) {
+  Basis& b = c->bases[ik];
+  if (!b.res_pending) return PARO_OK;
+  const std::string rname = "proj_res_" + std::to_string(ik);
+  int st = pinned_wait(c, rname.c_str());
+  if (st) return st;
+  const double* hr = static_cast<const double*>(c->pinned[rname].h);
+  b.res.assign(hr, hr + c->nb);
+  b.res_pending = false;
+  auto it = c->pinned.find("tc_err");
+  if (it != c->pinned.end() && it->second.h) {
+    if ((st = pinned_wait(c, "tc_err"))) return st;
+    if (*static_cast<const int*>(it->second.h)) return fail(c, PARO_ERR_TIMEOUT, "tensor-core product: mbarrier wait gave up");
+  }
   return PARO_OK;
 }
 
@@ -854,7 +890,7 @@ static int scf_iteration(Ctx* c, const paro_scf_opts* o) {
   }
   // step 4: Rayleigh-Ritz with V(rho_in^{n+1/2}) in the already orthonormal span
   for (int ik = 0; ik < c->nk; ++ik)
-    if ((st = project<T>(c, ik, xs[ik], nxs[ik], true, hxs[ik], dv))) return st;
+    if ((st = project<T>(c, ik, xs[ik], nxs[ik], true, hxs[ik], dv, true))) return st;
   return PARO_OK;
 }
 
@@ -1468,6 +1504,7 @@ int paro_get_residuals(paro_ctx* ctx, double* res) {
   if (!res) return PARO_ERR_ARG;
   for (int ik = 0; ik < c->nk; ++ik) {
     if (!c->bases[ik].have_psi) return fail(c, PARO_ERR_STATE, "no orbitals");
+    if (int st = project_readback(c, ik)) return st;
     std::copy(c->bases[ik].res.begin(), c->bases[ik].res.end(), res + (size_t)ik * c->nb);
   }
   return PARO_OK;
@@ -1547,6 +1584,8 @@ int paro_scf_step(paro_ctx* ctx, const paro_scf_opts* o, double energy[7], doubl
     if ((st = paro_energy(ctx, terms))) return st;
   }
   if (energy) std::copy(terms, terms + 7, energy);
+  for (int ik = 0; ik < c->nk; ++ik)
+    if ((st = project_readback(c, ik))) return st;
   if (max_resid_out) *max_resid_out = max_occ_resid(c);
   const double e = terms[PARO_E_TOTAL];
   if (c->scf_iter > 0 && std::fabs(e - c->e_prev) / std::max(c->nat, 1) < o->tol_per_atom)

@@ -524,9 +524,11 @@ __global__ void k_absmax(int nn, const double2* __restrict__ E, float* __restric
 
 static int eigh_finish(Ctx* c, int n, const double2* a, const double2* Af, double2* X, double2* T1, double2* S,
                        double2* part, const int* cl, const int* cst, const int* ncl, double* lam, double* w,
-                       double2* v, int* perm, int* info, bool clusters);
+                       double2* v, int* perm, int* info, bool clusters, const int** info_out);
 
-int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refine_steps, bool warm) {
+int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refine_steps, bool warm,
+               const int** info_out) {
+  if (info_out) *info_out = nullptr;
   if (n < 2 || n > kMixMaxN) return eigh(c, n, a, w, v);
   const size_t nn = (size_t)n * n;
   double2* Af = static_cast<double2*>(ws_get(c, "em_A", nn * sizeof(double2)));
@@ -606,7 +608,8 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
     // Rayleigh-Ritz step in twelve)
     if (emax >= 1e-4f && emax < 1e-2f && ((st = refine_step()) || (st = read_emax(&emax)))) return st;
     prof_end(c, "eigh_warm", evw);
-    if (emax < 1e-4f) return eigh_finish(c, n, a, Af, X, T1, S, part, cl, cst, ncl, lam, w, v, perm, info, true);
+    if (emax < 1e-4f)
+      return eigh_finish(c, n, a, Af, X, T1, S, part, cl, cst, ncl, lam, w, v, perm, info, true, info_out);
     c->eig_warm_skip = 8;  // not close enough yet: the FP32 solve for the next calls
   }
   // 1. FP32 solve
@@ -637,14 +640,14 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
     if ((st = zgemm(c, n, X, false, T1, X, true, part))) return st;    // X += X E
   }
   prof_end(c, "eigh_refine", ev);
-  return eigh_finish(c, n, a, Af, X, T1, S, part, cl, cst, ncl, lam, w, v, perm, info, refine_steps > 0);
+  return eigh_finish(c, n, a, Af, X, T1, S, part, cl, cst, ncl, lam, w, v, perm, info, refine_steps > 0, info_out);
 }
 
 // The end of the mixed solve from refined vectors X: T1 = A X, S = X^H A X (inside the clusters when they
 // exist), Rayleigh-Ritz inside each cluster, eigenvalues sorted.
 static int eigh_finish(Ctx* c, int n, const double2* a, const double2* Af, double2* X, double2* T1, double2* S,
                        double2* part, const int* cl, const int* cst, const int* ncl, double* lam, double* w,
-                       double2* v, int* perm, int* info, bool clusters) {
+                       double2* v, int* perm, int* info, bool clusters, const int** info_out) {
   const size_t nn = (size_t)n * n;
   int st;
   cudaEvent_t ev = prof_begin(c);
@@ -666,11 +669,22 @@ static int eigh_finish(Ctx* c, int n, const double2* a, const double2* Af, doubl
   k_eig_permute<<<(int)((nn + 255) / 256), 256, 0, c->stream>>>(n, lam, X, perm, w, v);
   PARO_LAUNCH(c, "k_eig_permute");
   prof_end(c, "eigh_cluster_rr", ev);
+  if (info_out) {  // the caller reads the cluster check later (eigh_mixed_check) without a wait here
+    void* h = nullptr;
+    int st = d2h_async(c, "eig_info", info, sizeof(int), &h);
+    if (st) return st;
+    *info_out = static_cast<const int*>(h);
+    return PARO_OK;
+  }
   int h = 0;
   PARO_CU(c, cudaMemcpyAsync(&h, info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   PARO_CU(c, cudaStreamSynchronize(c->stream));
-  if (h & 1) return fail(c, PARO_ERR_NOT_CONVERGED, "eigh (mixed): inverse iteration produced a zero vector");
-  if (h & (4 | 8)) return eigh(c, n, a, w, v);  // a cluster the refinement cannot resolve: FP64 solver
+  return eigh_mixed_check(c, n, a, w, v, h);
+}
+
+int eigh_mixed_check(Ctx* c, int n, const double2* a, double* w, double2* v, int info) {
+  if (info & 1) return fail(c, PARO_ERR_NOT_CONVERGED, "eigh (mixed): inverse iteration produced a zero vector");
+  if (info & (4 | 8)) return eigh(c, n, a, w, v);  // a cluster the refinement cannot resolve: FP64 solver
   return PARO_OK;
 }
 

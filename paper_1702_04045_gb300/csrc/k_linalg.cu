@@ -1008,33 +1008,42 @@ int chol_check(Ctx* c) {
 
 // First-order inverse Cholesky factor of a Gram matrix close to the identity. With S = I + E = L L^H and
 // F = strictly lower(E) + diag(E) / 2, L = I + F + O(E^2), so G = conj(L)^{-1} = I - conj(F) + O(E^2), and the
-// rows G X are orthonormal up to about 3 ||E||^2. One CTA forms ||E||_F (into *enorm); when it is at most
-// tol it writes G (lower triangular, as the Cholesky kernels do) and *use = 1, else *use = 0 and leaves G.
+// rows G X are orthonormal up to about 3 ||E||^2. Every CTA forms ||E||_F (in FP32: it only decides the
+// path, and one CTA's FP64 pipe would take tens of microseconds over the n^2 entries) in the same order,
+// so all of them reach the same verdict; when it is at most tol each writes its rows of G (lower
+// triangular, as the Cholesky kernels do) and CTA 0 sets *use, else *use = 0 and G is left alone.
 __global__ void __launch_bounds__(1024) k_orth_first_order(int n, const double2* __restrict__ s,
                                                            double2* __restrict__ g, double tol, int* __restrict__ use,
                                                            double* __restrict__ enorm) {
-  __shared__ double red[32];
+  __shared__ float red[32];
   __shared__ int s_use;
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
-    const int r = i / n, k = i - r * n;
-    double2 v = s[i];
-    if (r == k) v.x -= 1.0;
-    acc += v.x * v.x + v.y * v.y;
-  }
-  acc = block_sum(acc, red);
-  if (threadIdx.x == 0) {
-    const double e = sqrt(acc);
-    *enorm = e;
-    s_use = e <= tol ? 1 : 0;
-    *use = s_use;
-  }
-  __syncthreads();
-  if (!s_use) return;
+  float acc = 0.f;
   for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
     const int r = i / n, k = i - r * n;
     const double2 v = s[i];
-    g[i] = k > r ? make_double2(0.0, 0.0) : k == r ? make_double2(1.0 - 0.5 * (v.x - 1.0), 0.0) : make_double2(-v.x, v.y);
+    const float x = r == k ? (float)(v.x - 1.0) : (float)v.x, y = (float)v.y;
+    acc = fmaf(x, x, fmaf(y, y, acc));
+  }
+  acc = block_sumf(acc, red);
+  if (threadIdx.x == 0) {
+    const float e = sqrtf(acc);
+    s_use = (double)e <= tol ? 1 : 0;
+    if (blockIdx.x == 0) {
+      *enorm = (double)e;
+      *use = s_use;
+    }
+  }
+  __syncthreads();
+  if (!s_use) return;
+  const int r0 = (int)((long long)n * blockIdx.x / gridDim.x), r1 = (int)((long long)n * (blockIdx.x + 1) / gridDim.x);
+  for (int i = r0 * n + threadIdx.x; i < r1 * n; i += blockDim.x) {
+    const int r = i / n, k = i - r * n;
+    const double2 v = s[i];
+    // -conj(v) below the diagonal: a sign flip of the real part's bits, no FP64 arithmetic
+    g[i] = k > r ? make_double2(0.0, 0.0)
+                 : k == r ? make_double2(1.5 - 0.5 * v.x, 0.0)
+                          : make_double2(__longlong_as_double(__double_as_longlong(v.x) ^ (long long)0x8000000000000000ULL),
+                                         v.y);
   }
 }
 
@@ -1049,7 +1058,7 @@ int orth_first_order(Ctx* c, int n, const double2* s, double2* g, double tol, in
   int* use = static_cast<int*>(ws_get(c, "orth_first_use", sizeof(int)));
   double* enorm = static_cast<double*>(ws_get(c, "orth_first_enorm", sizeof(double)));
   if (!use || !enorm) return PARO_ERR_CUDA;
-  k_orth_first_order<<<1, 1024, 0, c->stream>>>(n, s, g, tol, use, enorm);
+  k_orth_first_order<<<16, 1024, 0, c->stream>>>(n, s, g, tol, use, enorm);
   PARO_LAUNCH(c, "k_orth_first_order");
   *use_dev = use;
   return PARO_OK;

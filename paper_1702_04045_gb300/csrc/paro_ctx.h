@@ -51,6 +51,7 @@ struct Basis {
   float2* d_hpsi32 = nullptr;
   // mixed precision: the FP64 orbitals / H psi lag the FP32 ones until a call that reads them (fp64_current)
   bool psi64_stale = false, hpsi64_stale = false;
+  bool res_pending = false;       // the residual norms of the last Rayleigh-Ritz step are still in pinned memory
   std::vector<double> eps;        // Ritz values
   std::vector<double> res;        // residual norms
   bool have_psi = false;
@@ -277,7 +278,12 @@ int eigh(Ctx* c, int n, const double2* a, double* w, double2* v);
 // warm: the matrix may already be nearly diagonal (a Rayleigh-Ritz basis close to the eigenvectors); then
 // two refinement steps from the permutation that sorts its diagonal replace the FP32 solve when their last
 // correction is small, with the FP32 solve as the fallback.
-int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refine_steps, bool warm = false);
+// info_out (may be null): instead of waiting for the cluster check, its result is read back into pinned
+// memory (*info_out, valid after pinned_wait(c, "eig_info")) and the caller passes it to eigh_mixed_check
+int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refine_steps, bool warm = false,
+               const int** info_out = nullptr);
+// the end of a mixed solve from its cluster check: the FP64 solver when a cluster could not be resolved
+int eigh_mixed_check(Ctx* c, int n, const double2* a, double* w, double2* v, int info);
 // Per-band partial sums: out[b] = sum_g Re conj(x[b][g]) y[b][g] (weights optional) — helpers.
 template <typename T>
 int band_norms(Ctx* c, int nb, int npw, const cplx<T>* x, int ldx, double* out_dev);
