@@ -141,14 +141,17 @@ __global__ void k_reduce_parts(int M, int N, int nz, const double2* __restrict__
   C[(size_t)m * ldc + n] = mirror ? cconj(s) : s;
 }
 
-// micro-tile R (tile 16 R) with the least padded work for an M x N product; ties go to larger R
+// micro-tile R (tile 16 R) for an M x N product: the least padded work, weighted by the micro-tile's cost
+// per useful product (a thread's 2 R shared-memory loads feed 4 R^2 multiply-adds, so R = 2 spends about
+// half its issue slots on loads)
 static int pick_r(int M, int N, bool herm) {
   int best = 4;
   double best_work = 1e300;
+  const double cost[5] = {0, 0, 1.5, 1.15, 1.0};
   for (int r = 4; r >= 2; --r) {
     const int t = 16 * r, tm = (M + t - 1) / t, tn = (N + t - 1) / t;
     const double tiles = herm ? tm * (tm + 1) / 2.0 : (double)tm * tn;
-    const double work = tiles * t * t;
+    const double work = tiles * t * t * cost[r];
     if (work < best_work * 0.999) {
       best_work = work;
       best = r;
