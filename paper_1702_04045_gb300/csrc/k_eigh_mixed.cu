@@ -608,9 +608,15 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
     // Rayleigh-Ritz step in twelve)
     if (emax >= 1e-4f && emax < 1e-2f && ((st = refine_step()) || (st = read_emax(&emax)))) return st;
     prof_end(c, "eigh_warm", evw);
-    if (emax < 1e-4f)
+    if (emax < 1e-4f) {
+      c->eig_warm_fails = 0;
       return eigh_finish(c, n, a, Af, X, T1, S, part, cl, cst, ncl, lam, w, v, perm, info, true, info_out);
-    c->eig_warm_skip = 8;  // not close enough yet: the FP32 solve for the next calls
+    }
+    // not close enough: the FP32 solve now and for the next 1, 2, 4, then 8 calls after consecutive
+    // failures (far from convergence the warm start keeps failing; near it a failure is a passing pair of
+    // close eigenvalues, and the next step usually succeeds)
+    c->eig_warm_skip = std::min(8, 1 << std::min(c->eig_warm_fails, 3)) - 1;
+    ++c->eig_warm_fails;
   }
   // 1. FP32 solve
   cudaEvent_t ev = prof_begin(c);

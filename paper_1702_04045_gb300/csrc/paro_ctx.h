@@ -121,7 +121,8 @@ struct Ctx {
   // gamma_pack_off suspends it for calls on general complex vectors
   bool gamma_real = false;
   bool gamma_pack_off = false;
-  int eig_warm_skip = 0;  // Rayleigh-Ritz eigensolves left before the warm start is tried again
+  int eig_warm_skip = 0;   // Rayleigh-Ritz eigensolves left before the warm start is tried again
+  int eig_warm_fails = 0;  // consecutive warm starts that were not accepted
   bool fft_configured[2] = {false, false};
   // instrumentation: kernels launched, and CUDA-event pairs around named kernels while profiling
   long long launches = 0;
