@@ -189,8 +189,8 @@ def launch_work(name: str, s):
 # DRAM bytes per launch from one ncu capture, valid only for the kernel source it was taken on
 # (sha256 prefix of the file defining the kernel); otherwise the roofline's traffic is null.
 TRAFFIC = {
-    # k_plane_reg<float, 72, 72, 9>, one full 144-band launch: 84.24 MB read + 27.49 MB written
-    "k_plane<f32>": (111727360, "paper_1702_04045_gb300/csrc/hpsi_passes_reg.cuh", "00b23b2d37ce29a1"),
+    # k_plane_reg<float, 72, 72, 9>, one full 144-band launch: 84.24 MB read + 27.46 MB written
+    "k_plane<f32>": (111695360, "paper_1702_04045_gb300/csrc/hpsi_passes_reg.cuh", "7cba8b0d0c9bce73"),
 }
 
 
