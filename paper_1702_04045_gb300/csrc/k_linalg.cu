@@ -29,11 +29,17 @@ template <typename TO, typename TI> __device__ __forceinline__ cplx<TO> cvt(cplx
 // so the FP32 rounding is that of a 16-term sum (the size of the rounding already in FP32 operands) and
 // does not grow with K, without FP64 instructions in the loop (FP64 issues at 1/64 of the FP32 rate here).
 // ------------------------------------------------------------------------------------------------
+// K values per pipeline stage: 32 for FP32 operands (half the barriers per product of the 16-value stage),
+// 16 for FP64 (the stage's shared memory doubles with the element size)
+template <typename ACC> struct CnStepK { static constexpr int value = 32; };
+template <> struct CnStepK<double> { static constexpr int value = 16; };
+
 template <typename TA, typename TB, typename ACC, int R, bool CARRY>
 __global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kslice, const cplx<TA>* __restrict__ A,
                                                  int lda, const cplx<TB>* __restrict__ B, int ldb,
                                                  double2* __restrict__ part, int herm) {
-  constexpr int TILE = 16 * R, LD = TILE + 1, STG = 2 * 16 * LD;  // elements per stage (A then B)
+  constexpr int KS = CnStepK<ACC>::value;                          // K values per stage
+  constexpr int TILE = 16 * R, LD = TILE + 1, STG = 2 * KS * LD;  // elements per stage (A then B)
   const int tm = blockIdx.y * TILE, tn = blockIdx.x * TILE;
   if (herm && tm > tn) return;
   const int k0 = blockIdx.z * kslice, k1 = min(K, k0 + kslice);
@@ -46,11 +52,11 @@ __global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kslice
   // K step kk into stage buffer st by asynchronous copies (zero-filled outside); A is kept unconjugated
   auto stage = [&](int kk, int st) {
     cplx<ACC>* As = cn_smem + st * STG;
-    cplx<ACC>* Bs = As + 16 * LD;
+    cplx<ACC>* Bs = As + KS * LD;
 #pragma unroll
-    for (int t = 0; t < R; ++t) {
+    for (int t = 0; t < R * (KS / 16); ++t) {
       const int i = tid + 256 * t;
-      const int r = i >> 4, kx = i & 15, gk = kk + kx;
+      const int r = i / KS, kx = i % KS, gk = kk + kx;
       const int gm = tm + r, gn = tn + r;
       const bool ia = gm < M && gk < k1, ib = gn < N && gk < k1;
       const cplx<TA>* sa = ia ? A + (size_t)gm * lda + gk : A;
@@ -74,20 +80,22 @@ __global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kslice
       acc[i][j] = mk<ACC>(0, 0);
       chi[i][j] = clo[i][j] = make_float2(0.f, 0.f);
     }
-  const int nk = k1 > k0 ? (k1 - k0 + 15) / 16 : 0;
+  const int nk = k1 > k0 ? (k1 - k0 + KS - 1) / KS : 0;
   if (nk > 0) stage(k0, 0);
   for (int kt = 0; kt < nk; ++kt) {
     if (kt + 1 < nk) {
-      stage(k0 + 16 * (kt + 1), (kt + 1) & 1);  // the other buffer: its readers passed the last barrier
+      stage(k0 + KS * (kt + 1), (kt + 1) & 1);  // the other buffer: its readers passed the last barrier
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncthreads();
     const cplx<ACC>* As = cn_smem + (kt & 1) * STG;
-    const cplx<ACC>* Bs = As + 16 * LD;
+    const cplx<ACC>* Bs = As + KS * LD;
+#pragma unroll
+    for (int kh = 0; kh < KS / 16; ++kh) {  // 16 K values, then the carry
 #pragma unroll 4
-    for (int kx = 0; kx < 16; ++kx) {
+    for (int kx = 16 * kh; kx < 16 * kh + 16; ++kx) {
       cplx<ACC> a[R], b[R];
 #pragma unroll
       for (int i = 0; i < R; ++i) {
@@ -113,6 +121,7 @@ __global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kslice
           two_sum_acc(chi[i][j].y, clo[i][j].y, (float)acc[i][j].y);
           acc[i][j] = mk<ACC>(0, 0);
         }
+    }
     }
     __syncthreads();
   }
@@ -161,10 +170,11 @@ static int pick_r(int M, int N, bool herm) {
 }
 
 // K slices: the count nz (at most one per 256 of K, at most max_slices) that minimises the modelled
-// makespan, ceil(tiles nz / 152) waves of CTAs sharing an SM times the 16-wide steps of one slice;
-// ties go to fewer slices (less partial-sum traffic).
-static void split_k(int tiles, int K, size_t max_slices, int* nz_out, int* kslice_out, int resident = 1) {
-  const int steps = (K + 15) / 16;
+// makespan, ceil(tiles nz / 152) waves of CTAs sharing an SM times the steps (of `step` K values, the
+// kernel's stage) of one slice; ties go to fewer slices (less partial-sum traffic).
+static void split_k(int tiles, int K, size_t max_slices, int* nz_out, int* kslice_out, int resident = 1,
+                    int step = 16) {
+  const int steps = (K + step - 1) / step;
   int maxz = (K + 255) / 256;
   if ((size_t)maxz > max_slices) maxz = (int)max_slices;
   if (maxz < 1) maxz = 1;
@@ -183,7 +193,7 @@ static void split_k(int tiles, int K, size_t max_slices, int* nz_out, int* kslic
     }
   }
   *nz_out = best_nz;
-  *kslice_out = best_steps * 16;
+  *kslice_out = best_steps * step;
 }
 
 // dynamic shared memory above the 48 KB default (the FP64 forms with R >= 3), set once per device
@@ -200,7 +210,7 @@ static void cn_smem_attr(size_t sm) {
 template <typename TA, typename TB, typename ACC, bool CARRY>
 static void launch_cn_r(int r, dim3 grid, cudaStream_t st, int M, int N, int K, int kslice, const cplx<TA>* A,
                         int lda, const cplx<TB>* B, int ldb, double2* part, int herm) {
-  const size_t sm = (size_t)2 * 2 * 16 * (16 * r + 1) * sizeof(cplx<ACC>);  // two stages of A and B
+  const size_t sm = (size_t)2 * 2 * CnStepK<ACC>::value * (16 * r + 1) * sizeof(cplx<ACC>);  // two stages of A, B
   if (r == 2) {
     cn_smem_attr<TA, TB, ACC, 2, CARRY>(sm);
     k_gemm_cn<TA, TB, ACC, 2, CARRY><<<grid, 256, sm, st>>>(M, N, K, kslice, A, lda, B, ldb, part, herm);
@@ -219,7 +229,7 @@ static int cn_resident_r(int r) {
   static int cached[5] = {0, 0, 0, 0, 0};
   if (r < 2 || r > 4) return 1;
   if (cached[r]) return cached[r];
-  const size_t sm = (size_t)2 * 2 * 16 * (16 * r + 1) * sizeof(cplx<ACC>);
+  const size_t sm = (size_t)2 * 2 * CnStepK<ACC>::value * (16 * r + 1) * sizeof(cplx<ACC>);
   int nb = 1;
   cudaError_t e;
   if (r == 2) {
@@ -298,7 +308,7 @@ int gemm_cn(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, const cplx<
   const int tiles_m = (M + tile - 1) / tile, tiles_n = (N + tile - 1) / tile;
   const int tiles = herm ? tiles_m * (tiles_m + 1) / 2 : tiles_m * tiles_n;
   int nz = 1, kslice = 16;
-  split_k(tiles, K, (size_t)1 << 20, &nz, &kslice, cn_resident<TA, TB, ACC>(r, carry));
+  split_k(tiles, K, (size_t)1 << 20, &nz, &kslice, cn_resident<TA, TB, ACC>(r, carry), CnStepK<ACC>::value);
   double2* part = static_cast<double2*>(ws_get(c, "gemm_parts", (size_t)nz * M * N * sizeof(double2)));
   if (!part) return PARO_ERR_CUDA;
   if (K == 0) {
@@ -328,7 +338,7 @@ int gemm_cn_scratch(Ctx* c, int M, int N, int K, const cplx<TA>* A, int lda, con
   const int r = pick_r(M, N, false), tile = 16 * r;
   const int tiles_m = (M + tile - 1) / tile, tiles_n = (N + tile - 1) / tile;
   int nz = 1, kslice = 16;
-  split_k(tiles_m * tiles_n, K, part_elems / slice, &nz, &kslice);
+  split_k(tiles_m * tiles_n, K, part_elems / slice, &nz, &kslice, 1, CnStepK<ACC>::value);
   launch_cn<TA, TB, ACC>(r, false, dim3(tiles_n, tiles_m, nz), c->stream, M, N, K, kslice, A, lda, B, ldb, part,
                          0);
   PARO_LAUNCH(c, "k_gemm_cn");
