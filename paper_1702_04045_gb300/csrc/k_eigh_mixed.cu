@@ -15,7 +15,9 @@
 //     the error of X across clusters.
 //  3. Clusters of close eigenvalues are only orthonormalised by step 2; a Rayleigh-Ritz inside each
 //     cluster (FP64 Jacobi on X_c^H A X_c) resolves them.
-// The products are FP64 n x n complex GEMMs spread over many CTAs (k_zgemm16).
+// The products are FP64 n x n complex GEMMs spread over many CTAs (k_zgemm16). Near convergence the
+// refinement starts instead from the permutation that sorts the diagonal (a warm start) and keeps X in the
+// form P (I + F), where every product is one of small matrices and runs in FP32 (k_fgemm16).
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
@@ -522,9 +524,134 @@ __global__ void k_absmax(int nn, const double2* __restrict__ E, float* __restric
   }
 }
 
+// ------------------------------------------------------------------------------------------------
+// Warm-start refinement in the form X = P (I + F): P the permutation that sorts the diagonal, A' = P^H A P
+// (exact, FP64) and F the accumulated correction, small near convergence. Then
+//   X^H X     = I + F + F^H + F^H F,
+//   X^H A X   = A' + A'F + (A'F)^H + F^H (A'F),
+//   X (I + E) = P (I + F + E + F E),
+// and with A' = D + N (D its diagonal, N the off-diagonal part, of the size of the residuals) every
+// product that remains, N F, F^H F, F^H (A'F) and F E, is one of small quantities: rounded in FP32 its
+// error is ~1e-7 of a product that is itself far below 1, so these products run on the FP32 pipe, and
+// only the exact parts (I, D F, A') are added in FP64. (GB300's FP64 rate is 1/64 of its FP32 rate.)
+// ------------------------------------------------------------------------------------------------
+struct FProd {
+  const double2* A;  // n x n, row-major
+  const double2* B;
+  double2* C;
+  int ah;       // op(A) = A^H
+  int diag;     // leave the k = i term out of the FP32 sum and add A_ii B_ij in FP64 (A' F as D F + N F)
+  int add_a;    // add op(A)_ij to the result
+  int add_ab;   // add A_ij + B_ij to the result (F + E + F E)
+};
+
+// C = op(A) B (+ the epilogue terms) for one or two products (blockIdx.z), 16 x 16 outputs per CTA; FP32
+// products with the partial sum of every 16 terms carried in FP64
+__global__ void __launch_bounds__(256) k_fgemm16(int n, FProd p0, FProd p1) {
+  __shared__ float2 As[16][17], Bs[16][17];
+  const FProd& p = blockIdx.z ? p1 : p0;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  const int i0 = blockIdx.y * 16, j0 = blockIdx.x * 16;
+  const int i = i0 + ty, j = j0 + tx;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int kk = 0; kk < n; kk += 16) {
+    const int ia = i0 + ty, ka = kk + tx;
+    float2 av = make_float2(0.f, 0.f);
+    if (ia < n && ka < n && !(p.diag && ia == ka)) {
+      const double2 a = p.ah ? cconj(p.A[(size_t)ka * n + ia]) : p.A[(size_t)ia * n + ka];
+      av = make_float2((float)a.x, (float)a.y);
+    }
+    As[ty][tx] = av;
+    const int kb = kk + ty, jb = j0 + tx;
+    float2 bv = make_float2(0.f, 0.f);
+    if (kb < n && jb < n) {
+      const double2 b = p.B[(size_t)kb * n + jb];
+      bv = make_float2((float)b.x, (float)b.y);
+    }
+    Bs[ty][tx] = bv;
+    __syncthreads();
+    float sx = 0.f, sy = 0.f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const float2 x = As[ty][k], y = Bs[k][tx];
+      sx = fmaf(x.x, y.x, fmaf(-x.y, y.y, sx));
+      sy = fmaf(x.x, y.y, fmaf(x.y, y.x, sy));
+    }
+    acc.x += (double)sx;
+    acc.y += (double)sy;
+    __syncthreads();
+  }
+  if (i >= n || j >= n) return;
+  if (p.diag) {  // A_ii B_ij in FP64 (op(A)_ii = conj(A_ii) when ah)
+    double2 d = p.A[(size_t)i * n + i];
+    if (p.ah) d = cconj(d);
+    acc = cadd(acc, cmul(d, p.B[(size_t)i * n + j]));
+  }
+  if (p.add_a) acc = cadd(acc, p.ah ? cconj(p.A[(size_t)j * n + i]) : p.A[(size_t)i * n + j]);
+  if (p.add_ab) acc = cadd(acc, cadd(p.A[(size_t)i * n + j], p.B[(size_t)i * n + j]));
+  p.C[(size_t)i * n + j] = acc;
+}
+
+// G = I + F + F^H + FF and S = A' + AF + AF^H + FAF, with the per-CTA sums of k_zreduce for the cluster
+// threshold: nrm[b] = sum |G_ij - d_ij|^2, nrm[nnrm + b] = sum over i != j of |S_ij|^2
+__global__ void __launch_bounds__(256) k_fassemble(int n, const double2* __restrict__ Ap, const double2* __restrict__ F,
+                                                   const double2* __restrict__ AF, const double2* __restrict__ FF,
+                                                   const double2* __restrict__ FAF, double2* __restrict__ G,
+                                                   double2* __restrict__ S, float* __restrict__ nrm, int nnrm) {
+  __shared__ float red[32];
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  float eg = 0.f, es = 0.f;
+  if (idx < n * n) {
+    const int i = idx / n, j = idx - i * n;
+    const size_t t = (size_t)j * n + i;
+    const double2 r = cadd(cadd(F[idx], cconj(F[t])), FF[idx]);  // G - I
+    G[idx] = make_double2(r.x + (i == j ? 1.0 : 0.0), r.y);
+    const double2 s = cadd(cadd(Ap[idx], cadd(AF[idx], cconj(AF[t]))), FAF[idx]);
+    S[idx] = s;
+    eg = (float)(r.x * r.x + r.y * r.y);
+    if (i != j) es = (float)(s.x * s.x + s.y * s.y);
+  }
+  eg = block_sumf(eg, red);
+  __syncthreads();
+  es = block_sumf(es, red);
+  if (threadIdx.x == 0) {
+    nrm[blockIdx.x] = eg;
+    nrm[nnrm + blockIdx.x] = es;
+  }
+}
+
+// X = P X': row i of X is row rank(i) of X'; Xp = I + F first when F is given (then Xp is written)
+__global__ void k_rows_from_rank(int n, const int* __restrict__ rank, const double2* __restrict__ Xp,
+                                 double2* __restrict__ X) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int i = idx / n, j = idx - i * n;
+  X[idx] = Xp[(size_t)rank[i] * n + j];
+}
+
+// Xp = I + F
+__global__ void k_identity_plus(int n, const double2* __restrict__ F, double2* __restrict__ Xp) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int i = idx / n, j = idx - i * n;
+  double2 v = F[idx];
+  if (i == j) v.x += 1.0;
+  Xp[idx] = v;
+}
+
+static int fgemm(Ctx* c, int n, const FProd& p0, const FProd* p1) {
+  const int t = (n + 15) / 16;
+  k_fgemm16<<<dim3(t, t, p1 ? 2 : 1), 256, 0, c->stream>>>(n, p0, p1 ? *p1 : p0);
+  PARO_LAUNCH(c, "k_fgemm16");
+  return PARO_OK;
+}
+
 static int eigh_finish(Ctx* c, int n, const double2* a, const double2* Af, double2* X, double2* T1, double2* S,
                        double2* part, const int* cl, const int* cst, const int* ncl, double* lam, double* w,
                        double2* v, int* perm, int* info, bool clusters, const int** info_out);
+static int eigh_finish_tail(Ctx* c, int n, const double2* a, double2* X, const double2* S, const int* cst,
+                            const int* ncl, double* lam, double* w, double2* v, int* perm, int* info,
+                            const int** info_out, const int* rank, double2* Xr);
 
 int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refine_steps, bool warm,
                const int** info_out) {
@@ -568,22 +695,35 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
   } else if (warm) {
     cudaEvent_t evw = prof_begin(c);
     int* rk = static_cast<int*>(ws_get(c, "em_rank", (size_t)2 * n * sizeof(int)));
-    if (!rk) return PARO_ERR_CUDA;
+    double2* Ap = static_cast<double2*>(ws_get(c, "em_Ap", nn * sizeof(double2)));
+    double2* F = static_cast<double2*>(ws_get(c, "em_F0", nn * sizeof(double2)));
+    double2* Fn = static_cast<double2*>(ws_get(c, "em_F1", nn * sizeof(double2)));
+    double2* AF = static_cast<double2*>(ws_get(c, "em_AF", nn * sizeof(double2)));
+    double2* FF = static_cast<double2*>(ws_get(c, "em_FF", nn * sizeof(double2)));
+    double2* FAF = static_cast<double2*>(ws_get(c, "em_FAF", nn * sizeof(double2)));
+    if (!rk || !Ap || !F || !Fn || !AF || !FF || !FAF) return PARO_ERR_CUDA;
     k_warm_perm<<<1, 1024, 0, c->stream>>>(n, Af, rk, rk + n);
     PARO_LAUNCH(c, "k_warm_perm");
-    // one refinement step, the largest entry of its correction into r32[0]
+    const int ge = (n * n + 255) / 256;
+    // one refinement step in the form X = P (I + F) (see FProd): the products of small quantities in FP32,
+    // E into T1, its largest entry into r32[0], F <- F + E + F E
     auto refine_step = [&]() -> int {
       int s2;
-      if ((s2 = zgemm(c, n, X, true, X, G, false, part, true, nrm, true))) return s2;
-      if ((s2 = zgemm(c, n, Af, false, X, T1, false, part))) return s2;
-      if ((s2 = zgemm(c, n, X, true, T1, S, false, part, true, nrm + nnrm, false))) return s2;
+      const FProd paf{Ap, F, AF, 0, 1, 0, 0};  // A'F = D F + N F
+      const FProd pff{F, F, FF, 1, 0, 0, 0}, pfaf{F, AF, FAF, 1, 0, 0, 0};
+      if ((s2 = fgemm(c, n, paf, nullptr)) || (s2 = fgemm(c, n, pff, &pfaf))) return s2;
+      k_fassemble<<<ge, 256, 0, c->stream>>>(n, Ap, F, AF, FF, FAF, G, S, nrm, nnrm);
+      PARO_LAUNCH(c, "k_fassemble");
       k_refine_lam<<<1, 1024, 0, c->stream>>>(n, G, S, nrm, nnrm, lam, cl, cst, ncl);
       PARO_LAUNCH(c, "k_refine_lam");
-      k_refine_e<<<(n * n + 255) / 256, 256, 0, c->stream>>>(n, G, S, lam, cl, T1);
+      k_refine_e<<<ge, 256, 0, c->stream>>>(n, G, S, lam, cl, T1);
       PARO_LAUNCH(c, "k_refine_e");
       k_absmax<<<1, 1024, 0, c->stream>>>((int)nn, T1, r32);
       PARO_LAUNCH(c, "k_absmax");
-      return zgemm(c, n, X, false, T1, X, true, part);
+      const FProd pup{F, T1, Fn, 0, 0, 0, 1};  // F + E + F E
+      if ((s2 = fgemm(c, n, pup, nullptr))) return s2;
+      std::swap(F, Fn);
+      return PARO_OK;
     };
     auto read_emax = [&](float* e) -> int {
       void* h = nullptr;
@@ -592,15 +732,13 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
       *e = *static_cast<const float*>(h);
       return PARO_OK;
     };
-    // step 1 from the permutation, without products
-    k_warm_s<<<nnrm, 256, 0, c->stream>>>(n, Af, rk + n, G, S, nrm, nnrm);
+    // step 1 from the permutation, without products: G = I, S = A' (kept in Ap), F = E
+    k_warm_s<<<nnrm, 256, 0, c->stream>>>(n, Af, rk + n, G, Ap, nrm, nnrm);
     PARO_LAUNCH(c, "k_warm_s");
-    k_refine_lam<<<1, 1024, 0, c->stream>>>(n, G, S, nrm, nnrm, lam, cl, cst, ncl);
+    k_refine_lam<<<1, 1024, 0, c->stream>>>(n, G, Ap, nrm, nnrm, lam, cl, cst, ncl);
     PARO_LAUNCH(c, "k_refine_lam");
-    k_refine_e<<<(n * n + 255) / 256, 256, 0, c->stream>>>(n, G, S, lam, cl, T1);
+    k_refine_e<<<ge, 256, 0, c->stream>>>(n, G, Ap, lam, cl, F);
     PARO_LAUNCH(c, "k_refine_e");
-    k_warm_x1<<<(n * n + 255) / 256, 256, 0, c->stream>>>(n, rk, T1, X);
-    PARO_LAUNCH(c, "k_warm_x1");
     float emax = 1.f;
     if ((st = refine_step()) || (st = read_emax(&emax))) return st;
     // a pair of close but separate eigenvalues converges more slowly: up to two more steps decide while the
@@ -612,7 +750,17 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
     prof_end(c, "eigh_warm", evw);
     if (emax < 1e-4f) {
       c->eig_warm_fails = 0;
-      return eigh_finish(c, n, a, Af, X, T1, S, part, cl, cst, ncl, lam, w, v, perm, info, true, info_out);
+      // finish in the same form: X' = I + F, T1 = A' X' = A' + A'F, S = X'^H A' X' inside the clusters,
+      // Rayleigh-Ritz there on the columns of X', then X = P X'
+      cudaEvent_t evf = prof_begin(c);
+      k_identity_plus<<<ge, 256, 0, c->stream>>>(n, F, X);
+      PARO_LAUNCH(c, "k_identity_plus");
+      const FProd pt{Ap, F, T1, 0, 1, 1, 0};
+      if ((st = fgemm(c, n, pt, nullptr))) return st;
+      k_blockdiag_xhat<<<(int)((nn + 7) / 8), 256, 0, c->stream>>>(n, X, T1, cl, S);
+      PARO_LAUNCH(c, "k_blockdiag_xhat");
+      prof_end(c, "eigh_finish", evf);
+      return eigh_finish_tail(c, n, a, X, S, cst, ncl, lam, w, v, perm, info, info_out, rk, G);
     }
     // not close enough: the FP32 solve now and for the next 1, 2, 4, then 8 calls after consecutive
     // failures (far from convergence the warm start keeps failing; near it a failure is a passing pair of
@@ -667,11 +815,25 @@ static int eigh_finish(Ctx* c, int n, const double2* a, const double2* Af, doubl
     return st;
   }
   prof_end(c, "eigh_finish", ev);
-  ev = prof_begin(c);
+  return eigh_finish_tail(c, n, a, X, S, cst, ncl, lam, w, v, perm, info, info_out, nullptr, nullptr);
+}
+
+// Rayleigh-Ritz inside the clusters on the columns of X, then (with rank) the rows put back in the original
+// order into Xr (X = P X'), eigenvalues sorted; the cluster check is read back (or deferred via info_out).
+static int eigh_finish_tail(Ctx* c, int n, const double2* a, double2* X, const double2* S, const int* cst,
+                            const int* ncl, double* lam, double* w, double2* v, int* perm, int* info,
+                            const int** info_out, const int* rank, double2* Xr) {
+  const size_t nn = (size_t)n * n;
+  cudaEvent_t ev = prof_begin(c);
   const size_t sm3 = (size_t)2 * 64 * 65 * sizeof(double2);
   PARO_CU(c, cudaFuncSetAttribute(k_cluster_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
   k_cluster_rr<<<n, 256, sm3, c->stream>>>(n, S, cst, ncl, X, lam, info);
   PARO_LAUNCH(c, "k_cluster_rr");
+  if (rank) {
+    k_rows_from_rank<<<(int)((nn + 255) / 256), 256, 0, c->stream>>>(n, rank, X, Xr);
+    PARO_LAUNCH(c, "k_rows_from_rank");
+    X = Xr;
+  }
   k_eig_sort<<<(n + 127) / 128, 128, 0, c->stream>>>(n, lam, X, w, v, perm);
   PARO_LAUNCH(c, "k_eig_sort");
   k_eig_permute<<<(int)((nn + 255) / 256), 256, 0, c->stream>>>(n, lam, X, perm, w, v);
