@@ -395,6 +395,7 @@ static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal, cplx<T>
     if (!done && (st = apply_h<T>(c, ik, nx, Y, HY, 0.0, nullptr))) return st;
   }
   const int* hinfo = nullptr;
+  const float* hemax = nullptr;
   {
     ProfTag t(c, "hsub");
     if ((st = gemm_cn<T, T, T>(c, nx, nx, npw, Y, npw, HY, npw, S, nx, true, true))) return st;
@@ -403,7 +404,7 @@ static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal, cplx<T>
     PARO_LAUNCH(c, "k_hermitize");
     // mixed: one refinement step (FP64 Ritz values, vectors well below the FP32 level of the orbitals); its
     // cluster check is read back below, with the Ritz values
-    if ((st = f64 ? eigh(c, nx, S, w, G) : eigh_mixed(c, nx, S, w, G, 1, true, &hinfo))) return st;  // G <- C
+    if ((st = f64 ? eigh(c, nx, S, w, G) : eigh_mixed(c, nx, S, w, G, 1, true, &hinfo, &hemax))) return st;  // G <- C
   }
   // the rotations, H psi of the new orbitals and their residual norms
   auto rotate = [&]() -> int {
@@ -427,18 +428,26 @@ static int project(Ctx* c, int ik, cplx<T>* X, int nx, bool orthonormal, cplx<T>
   const std::string rname = "proj_res_" + std::to_string(ik);
   void *he = nullptr, *hr = nullptr;
   const int* htc = nullptr;
-  if ((st = d2h_async(c, "proj_eps", w, nb * sizeof(double), &he)) || (st = rotate()) ||
-      (st = d2h_async(c, rname.c_str(), res, nb * sizeof(double), &hr)) || (st = tc_flag_readback(c, &htc)) ||
-      (st = pinned_wait(c, "proj_eps")))
-    return st;
+  auto finish = [&]() -> int {
+    int s2;
+    if ((s2 = d2h_async(c, "proj_eps", w, nb * sizeof(double), &he)) || (s2 = rotate()) ||
+        (s2 = d2h_async(c, rname.c_str(), res, nb * sizeof(double), &hr)) || (s2 = tc_flag_readback(c, &htc)) ||
+        (s2 = pinned_wait(c, "proj_eps")))
+      return s2;
+    return PARO_OK;
+  };
+  if ((st = finish())) return st;
+  if (hemax && (st = pinned_wait(c, "eig_warm_emax"))) return st;
+  if (hemax && !eigh_mixed_accept(c, *hemax)) {
+    // a warm start that went on without waiting and was not accepted (rare near convergence): the FP32
+    // solve, then the rotations again from the unchanged Rayleigh-Ritz basis
+    hinfo = nullptr;
+    if ((st = eigh_mixed(c, nx, S, w, G, 1, false, &hinfo)) || (st = finish())) return st;
+  }
   if (hinfo && (*hinfo & (1 | 4 | 8))) {
     // a cluster the mixed refinement could not resolve (rare): the FP64 solver, then the rotations again
     // from the unchanged Rayleigh-Ritz basis
-    if ((st = eigh_mixed_check(c, nx, S, w, G, *hinfo))) return st;
-    if ((st = d2h_async(c, "proj_eps", w, nb * sizeof(double), &he)) || (st = rotate()) ||
-        (st = d2h_async(c, rname.c_str(), res, nb * sizeof(double), &hr)) || (st = tc_flag_readback(c, &htc)) ||
-        (st = pinned_wait(c, "proj_eps")))
-      return st;
+    if ((st = eigh_mixed_check(c, nx, S, w, G, *hinfo)) || (st = finish())) return st;
   }
   b.eps.assign(static_cast<const double*>(he), static_cast<const double*>(he) + nb);
   b.res_pending = true;

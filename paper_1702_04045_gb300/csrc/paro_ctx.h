@@ -123,6 +123,7 @@ struct Ctx {
   bool gamma_pack_off = false;
   int eig_warm_skip = 0;   // Rayleigh-Ritz eigensolves left before the warm start is tried again
   int eig_warm_fails = 0;  // consecutive warm starts that were not accepted
+  float eig_warm_last = 1.f;  // the last correction of the latest warm start (1 before the first)
   bool fft_configured[2] = {false, false};
   // instrumentation: kernels launched, and CUDA-event pairs around named kernels while profiling
   long long launches = 0;
@@ -281,8 +282,15 @@ int eigh(Ctx* c, int n, const double2* a, double* w, double2* v);
 // correction is small, with the FP32 solve as the fallback.
 // info_out (may be null): instead of waiting for the cluster check, its result is read back into pinned
 // memory (*info_out, valid after pinned_wait(c, "eig_info")) and the caller passes it to eigh_mixed_check
+// emax_out (may be null): when the last warm starts were well converged, the warm start is not waited for
+// either: its last correction is read back into pinned memory (*emax_out, valid after
+// pinned_wait(c, "eig_warm_emax")) and the caller passes it to eigh_mixed_accept before using w and v;
+// *emax_out is left null when the solve decided by itself
 int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refine_steps, bool warm = false,
-               const int** info_out = nullptr);
+               const int** info_out = nullptr, const float** emax_out = nullptr);
+// a deferred warm start's verdict from its last correction: true when it is accepted (else the caller solves
+// again with warm = false)
+bool eigh_mixed_accept(Ctx* c, float emax);
 // the end of a mixed solve from its cluster check: the FP64 solver when a cluster could not be resolved
 int eigh_mixed_check(Ctx* c, int n, const double2* a, double* w, double2* v, int info);
 // Per-band partial sums: out[b] = sum_g Re conj(x[b][g]) y[b][g] (weights optional) — helpers.
