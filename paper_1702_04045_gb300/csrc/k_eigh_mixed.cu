@@ -512,12 +512,14 @@ __global__ void k_eig_sort(int n, const double* __restrict__ lam, const double2*
   }
 }
 
+// rank (may be null): X holds P^H times the vectors (the warm start's permuted rows): V[i][:] = X[rank(i)][:]
 __global__ void k_eig_permute(int n, const double* __restrict__ lam, const double2* __restrict__ X,
-                              const int* __restrict__ perm, double* __restrict__ w, double2* __restrict__ V) {
+                              const int* __restrict__ perm, const int* __restrict__ rank, double* __restrict__ w,
+                              double2* __restrict__ V) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * n) return;
   const int i = idx / n, j = idx - i * n;
-  V[idx] = X[(size_t)i * n + perm[j]];
+  V[idx] = X[(size_t)(rank ? rank[i] : i) * n + perm[j]];
   if (i == 0) w[j] = lam[perm[j]];
 }
 
@@ -570,7 +572,7 @@ __global__ void k_warm_perm(int n, const double2* __restrict__ A, int* __restric
 }
 
 // The first refinement step from X0 needs no products: G = X0^H X0 = I and S = X0^H A X0 = A with rows and
-// columns in rank order. nrm as k_zreduce leaves it for the pair (G, S): per CTA of 256 entries, zero for
+// columns in rank order (A given by its lower triangle). nrm as k_zreduce leaves it for the pair (G, S): per CTA of 256 entries, zero for
 // G and the off-diagonal sum of |S_ij|^2 for S.
 __global__ void __launch_bounds__(256) k_warm_s(int n, const double2* __restrict__ A, const int* __restrict__ at_rank,
                                                 double2* __restrict__ G, double2* __restrict__ S,
@@ -579,8 +581,8 @@ __global__ void __launch_bounds__(256) k_warm_s(int n, const double2* __restrict
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   float e = 0.f;
   if (idx < n * n) {
-    const int r = idx / n, q = idx - r * n;
-    const double2 v = A[(size_t)at_rank[r] * n + at_rank[q]];
+    const int r = idx / n, q = idx - r * n, i = at_rank[r], j = at_rank[q];
+    const double2 v = i >= j ? A[(size_t)i * n + j] : cconj(A[(size_t)j * n + i]);  // A: its lower triangle
     S[idx] = v;
     G[idx] = make_double2(r == q ? 1.0 : 0.0, 0.0);
     if (r != q) {
@@ -624,6 +626,7 @@ struct FProd {
   int diag;     // leave the k = i term out of the FP32 sum and add A_ii B_ij in FP64 (A' F as D F + N F)
   int add_a;    // add op(A)_ij to the result
   int add_ab;   // add A_ij + B_ij to the result (F + E + F E)
+  double2* xp;  // (may be null) also I + B into xp (X' = I + F beside T1 = A' X')
 };
 
 // C = op(A) B (+ the epilogue terms) for one or two products (blockIdx.z), 16 x 16 outputs per CTA (n <=
@@ -684,6 +687,11 @@ __global__ void __launch_bounds__(256) k_fgemm16(int n, FProd p0, FProd p1) {
   if (p.add_a) acc = cadd(acc, p.ah ? cconj(p.A[(size_t)j * n + i]) : p.A[(size_t)i * n + j]);
   if (p.add_ab) acc = cadd(acc, cadd(p.A[(size_t)i * n + j], p.B[(size_t)i * n + j]));
   p.C[(size_t)i * n + j] = acc;
+  if (p.xp) {
+    double2 x = p.B[(size_t)i * n + j];
+    if (i == j) x.x += 1.0;
+    p.xp[(size_t)i * n + j] = x;
+  }
 }
 
 // G = I + F + F^H + FF and S = A' + AF + AF^H + FAF, with the per-CTA sums of k_zreduce for the cluster
@@ -714,25 +722,6 @@ __global__ void __launch_bounds__(256) k_fassemble(int n, const double2* __restr
   }
 }
 
-// X = P X': row i of X is row rank(i) of X'; Xp = I + F first when F is given (then Xp is written)
-__global__ void k_rows_from_rank(int n, const int* __restrict__ rank, const double2* __restrict__ Xp,
-                                 double2* __restrict__ X) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n * n) return;
-  const int i = idx / n, j = idx - i * n;
-  X[idx] = Xp[(size_t)rank[i] * n + j];
-}
-
-// Xp = I + F
-__global__ void k_identity_plus(int n, const double2* __restrict__ F, double2* __restrict__ Xp) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n * n) return;
-  const int i = idx / n, j = idx - i * n;
-  double2 v = F[idx];
-  if (i == j) v.x += 1.0;
-  Xp[idx] = v;
-}
-
 static int fgemm(Ctx* c, int n, const FProd& p0, const FProd* p1) {
   const int t = (n + 15) / 16;
   k_fgemm16<<<dim3(t, t, p1 ? 2 : 1), 256, 0, c->stream>>>(n, p0, p1 ? *p1 : p0);
@@ -745,7 +734,7 @@ static int eigh_finish(Ctx* c, int n, const double2* a, const double2* Af, doubl
                        double2* v, int* perm, int* info, bool clusters, const int** info_out);
 static int eigh_finish_tail(Ctx* c, int n, const double2* a, double2* X, const double2* S, const int* cst,
                             const int* ncl, double* lam, double* w, double2* v, int* perm, int* info,
-                            const int** info_out, const int* rank, double2* Xr);
+                            const int** info_out, const int* rank);
 
 // warm-start bookkeeping: accepted when the last correction is below 1e-4 (the remaining error is of its
 // square); after a failure the FP32 solve runs for the next 1, 2, 4, then 8 calls after consecutive failures
@@ -795,8 +784,6 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
   float2* ecx32 = static_cast<float2*>(ws_get(c, "em_ecx32", (size_t)n * sizeof(float2)));
   if (!ecx32) return PARO_ERR_CUDA;
   PARO_CU(c, cudaMemsetAsync(flags, 0, 6 * sizeof(int), c->stream));
-  k_herm_full_mixed<<<(int)((nn + 255) / 256), 256, 0, c->stream>>>(n, a, Af);
-  PARO_LAUNCH(c, "k_herm_full");
   int st;
   // Rayleigh-Ritz near convergence: the matrix of a basis that already is close to the eigenvectors is
   // nearly diagonal, and two (or three) refinement steps from the permutation that sorts its diagonal reach
@@ -814,15 +801,15 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
     double2* FF = static_cast<double2*>(ws_get(c, "em_FF", nn * sizeof(double2)));
     double2* FAF = static_cast<double2*>(ws_get(c, "em_FAF", nn * sizeof(double2)));
     if (!rk || !Ap || !F || !Fn || !AF || !FF || !FAF) return PARO_ERR_CUDA;
-    k_warm_perm<<<1, 1024, 0, c->stream>>>(n, Af, rk, rk + n);
+    k_warm_perm<<<1, 1024, 0, c->stream>>>(n, a, rk, rk + n);
     PARO_LAUNCH(c, "k_warm_perm");
     const int ge = (n * n + 255) / 256;
     // one refinement step in the form X = P (I + F) (see FProd): the products of small quantities in FP32,
     // E into T1, its largest entry into r32[0] (by k_refine_e), F <- F + E + F E
     auto refine_step = [&]() -> int {
       int s2;
-      const FProd paf{Ap, F, AF, 0, 1, 0, 0};  // A'F = D F + N F
-      const FProd pff{F, F, FF, 1, 0, 0, 0}, pfaf{F, AF, FAF, 1, 0, 0, 0};
+      const FProd paf{Ap, F, AF, 0, 1, 0, 0, nullptr};  // A'F = D F + N F
+      const FProd pff{F, F, FF, 1, 0, 0, 0, nullptr}, pfaf{F, AF, FAF, 1, 0, 0, 0, nullptr};
       if ((s2 = fgemm(c, n, paf, nullptr)) || (s2 = fgemm(c, n, pff, &pfaf))) return s2;
       k_fassemble<<<ge, 256, 0, c->stream>>>(n, Ap, F, AF, FF, FAF, G, S, nrm, nnrm);
       PARO_LAUNCH(c, "k_fassemble");
@@ -830,7 +817,7 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
       PARO_LAUNCH(c, "k_refine_lam");
       k_refine_e<<<ge, 256, 0, c->stream>>>(n, G, S, lam, cl, T1, r32);
       PARO_LAUNCH(c, "k_refine_e");
-      const FProd pup{F, T1, Fn, 0, 0, 0, 1};  // F + E + F E
+      const FProd pup{F, T1, Fn, 0, 0, 0, 1, nullptr};  // F + E + F E
       if ((s2 = fgemm(c, n, pup, nullptr))) return s2;
       std::swap(F, Fn);
       return PARO_OK;
@@ -843,7 +830,7 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
       return PARO_OK;
     };
     // step 1 from the permutation, without products: G = I, S = A' (kept in Ap), F = E
-    k_warm_s<<<nnrm, 256, 0, c->stream>>>(n, Af, rk + n, G, Ap, nrm, nnrm);
+    k_warm_s<<<nnrm, 256, 0, c->stream>>>(n, a, rk + n, G, Ap, nrm, nnrm);
     PARO_LAUNCH(c, "k_warm_s");
     k_refine_lam<<<1, 1024, 0, c->stream>>>(n, G, Ap, nrm, nnrm, lam, cl, cst, ncl, nullptr);
     PARO_LAUNCH(c, "k_refine_lam");
@@ -874,17 +861,18 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
       // finish in the same form: X' = I + F, T1 = A' X' = A' + A'F, S = X'^H A' X' inside the clusters,
       // Rayleigh-Ritz there on the columns of X', then X = P X'
       cudaEvent_t evf = prof_begin(c);
-      k_identity_plus<<<ge, 256, 0, c->stream>>>(n, F, X);
-      PARO_LAUNCH(c, "k_identity_plus");
-      const FProd pt{Ap, F, T1, 0, 1, 1, 0};
+      const FProd pt{Ap, F, T1, 0, 1, 1, 0, X};
       if ((st = fgemm(c, n, pt, nullptr))) return st;
       k_blockdiag_xhat<<<(int)((nn + 7) / 8), 256, 0, c->stream>>>(n, X, T1, cl, S);
       PARO_LAUNCH(c, "k_blockdiag_xhat");
       prof_end(c, "eigh_finish", evf);
-      return eigh_finish_tail(c, n, a, X, S, cst, ncl, lam, w, v, perm, info, info_out, rk, G);
+      return eigh_finish_tail(c, n, a, X, S, cst, ncl, lam, w, v, perm, info, info_out, rk);
     }
     // not close enough: the FP32 solve (warm_verdict has set the calls to skip)
   }
+  // the full Hermitian matrix (the input holds its lower triangle)
+  k_herm_full_mixed<<<(int)((nn + 255) / 256), 256, 0, c->stream>>>(n, a, Af);
+  PARO_LAUNCH(c, "k_herm_full");
   // 1. FP32 solve
   cudaEvent_t ev = prof_begin(c);
   const size_t sm1 = ((size_t)n * (n + 1) + 2 * (size_t)n) * sizeof(float2);
@@ -932,28 +920,23 @@ static int eigh_finish(Ctx* c, int n, const double2* a, const double2* Af, doubl
     return st;
   }
   prof_end(c, "eigh_finish", ev);
-  return eigh_finish_tail(c, n, a, X, S, cst, ncl, lam, w, v, perm, info, info_out, nullptr, nullptr);
+  return eigh_finish_tail(c, n, a, X, S, cst, ncl, lam, w, v, perm, info, info_out, nullptr);
 }
 
-// Rayleigh-Ritz inside the clusters on the columns of X, then (with rank) the rows put back in the original
-// order into Xr (X = P X'), eigenvalues sorted; the cluster check is read back (or deferred via info_out).
+// Rayleigh-Ritz inside the clusters on the columns of X, eigenvalues sorted (with rank, the rows put back in
+// the original order: v = P X'); the cluster check is read back (or deferred via info_out).
 static int eigh_finish_tail(Ctx* c, int n, const double2* a, double2* X, const double2* S, const int* cst,
                             const int* ncl, double* lam, double* w, double2* v, int* perm, int* info,
-                            const int** info_out, const int* rank, double2* Xr) {
+                            const int** info_out, const int* rank) {
   const size_t nn = (size_t)n * n;
   cudaEvent_t ev = prof_begin(c);
   const size_t sm3 = (size_t)2 * 64 * 65 * sizeof(double2);
   PARO_CU(c, cudaFuncSetAttribute(k_cluster_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
   k_cluster_rr<<<n, 256, sm3, c->stream>>>(n, S, cst, ncl, X, lam, info);
   PARO_LAUNCH(c, "k_cluster_rr");
-  if (rank) {
-    k_rows_from_rank<<<(int)((nn + 255) / 256), 256, 0, c->stream>>>(n, rank, X, Xr);
-    PARO_LAUNCH(c, "k_rows_from_rank");
-    X = Xr;
-  }
   k_eig_sort<<<(n + 127) / 128, 128, 0, c->stream>>>(n, lam, X, w, v, perm);
   PARO_LAUNCH(c, "k_eig_sort");
-  k_eig_permute<<<(int)((nn + 255) / 256), 256, 0, c->stream>>>(n, lam, X, perm, w, v);
+  k_eig_permute<<<(int)((nn + 255) / 256), 256, 0, c->stream>>>(n, lam, X, perm, rank, w, v);
   PARO_LAUNCH(c, "k_eig_permute");
   prof_end(c, "eigh_cluster_rr", ev);
   if (info_out) {  // the caller reads the cluster check later (eigh_mixed_check) without a wait here

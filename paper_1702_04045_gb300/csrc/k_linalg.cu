@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(256) k_gemm_wx32(int M, int N, int K, const fl
                                                    const float2* __restrict__ X, int ldx, float2* __restrict__ Y,
                                                    int ldy, float beta) {
   constexpr int TM = 16 * RM, TN = 16 * RN, STG = 16 * (TM + TN);  // float2 per stage buffer
-  extern __shared__ __align__(16) float2 wx_smem[];                // two stages: Ws[16][TM], Xs[16][TN]
+  extern __shared__ __align__(16) float2 wx_smem[];                // three stages: Ws[16][TM], Xs[16][TN]
   const int tm = blockIdx.y * TM, tn = blockIdx.x * TN;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   // the K step k0 into stage buffer st by asynchronous 8-byte copies (zero-filled outside the matrices)
@@ -456,17 +456,17 @@ __global__ void __launch_bounds__(256) k_gemm_wx32(int M, int N, int K, const fl
 #pragma unroll
     for (int j = 0; j < RN; ++j) acc[i][j] = make_float2(0.f, 0.f);
   const int nk = LW ? min((K + 15) / 16, (tm + TM + 15) / 16) : (K + 15) / 16;
+  // a ring of three stages, one barrier per stage: the barrier that publishes stage kt also marks stage
+  // kt - 1 as read, and its buffer takes stage kt + 2
   if (nk > 0) stage(0, 0);
+  if (nk > 1) stage(16, 1);
   const int warp_last_row = tm + RM * (ty | 1) + RM - 1;
   for (int kt = 0; kt < nk; ++kt) {
-    if (kt + 1 < nk) {
-      stage(16 * (kt + 1), (kt + 1) & 1);  // the other buffer: its readers passed the barrier below
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
+    if (kt + 1 < nk) cp_async_wait<1>();  // stages committed so far: kt + 2 (kt + 1 at the last)
+    else cp_async_wait<0>();
     __syncthreads();
-    const float2* Ws = wx_smem + (kt & 1) * STG;
+    if (kt + 2 < nk) stage(16 * (kt + 2), (kt + 2) % 3);
+    const float2* Ws = wx_smem + (kt % 3) * STG;
     const float2* Xs = Ws + 16 * TM;
     if (!LW || 16 * kt <= warp_last_row)
 #pragma unroll 4
@@ -486,7 +486,6 @@ __global__ void __launch_bounds__(256) k_gemm_wx32(int M, int N, int K, const fl
           acc[i][j].y = fmaf(w[i].y, x[j].x, acc[i][j].y);
         }
     }
-    __syncthreads();
   }
 #pragma unroll
   for (int i = 0; i < RM; ++i) {
@@ -526,13 +525,15 @@ static int launch_wx32(Ctx* c, int M, int N, int K, const double2* W, int ldw, b
     PARO_LAUNCH(c, "k_w_to_f32");
   }
   const int rm = big ? 9 : 4, rn = rn4 ? 4 : 2;
-  const size_t sm = (size_t)2 * 16 * 16 * (rm + rn) * sizeof(float2);  // two stages
-  static int attr_dev = -1;  // dynamic shared memory above 48 KB for the 9 x 4 form, set per device
+  const size_t sm = (size_t)3 * 16 * 16 * (rm + rn) * sizeof(float2);  // three stages
+  static int attr_dev = -1;  // dynamic shared memory above 48 KB, set per device
   int dev = 0;
   PARO_CU(c, cudaGetDevice(&dev));
   if (attr_dev != dev) {
-    PARO_CU(c, cudaFuncSetAttribute(k_gemm_wx32<9, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
-    PARO_CU(c, cudaFuncSetAttribute(k_gemm_wx32<9, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+    for (const void* f : {(const void*)k_gemm_wx32<9, 4>, (const void*)k_gemm_wx32<9, 4, true>,
+                          (const void*)k_gemm_wx32<9, 2>, (const void*)k_gemm_wx32<9, 2, true>,
+                          (const void*)k_gemm_wx32<4, 4>, (const void*)k_gemm_wx32<4, 2>})
+      PARO_CU(c, cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
     attr_dev = dev;
   }
   if (big && lower) {
