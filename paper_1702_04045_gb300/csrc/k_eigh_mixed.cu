@@ -34,8 +34,12 @@ int eigh_fp32_pieces(Ctx* c, int n, const float* d, const float* e, float* w, co
                      const float2* ph, float* Z, float2* V, int* info);
 
 static const int kMixMaxN = 160;  // largest n whose FP32 matrix fits one CTA's shared memory
-// a pair whose refinement correction exceeds this joins one cluster (k_refine_lam)
+// a pair whose refinement correction exceeds this joins one cluster (k_refine_lam), as long as no cluster
+// grows beyond kCoupleMaxCluster columns; only while at least half of the last eight warm starts ended with a
+// correction below 1e-5 (near convergence: far from it most pairs are coupled, and the FP32 solve is the
+// faster route)
 static const double kCouple = 1e-2;
+static const int kCoupleMaxCluster = 8;
 
 // ------------------------------------------------------------------------------------------------
 // Householder tridiagonalisation, one CTA, matrix (FP32) in shared memory. The same reflectors and outputs
@@ -262,7 +266,7 @@ __global__ void __launch_bounds__(1024) k_refine_lam(int n, const double2* __res
                                                      const double2* __restrict__ S, const float* __restrict__ nrm,
                                                      int nnrm, double* __restrict__ lam, int* __restrict__ cl,
                                                      int* __restrict__ cst, int* __restrict__ ncl,
-                                                     float* __restrict__ emax) {
+                                                     float* __restrict__ emax, double couple) {
   __shared__ float red[32];
   __shared__ double s_lam[kMixMaxN];
   __shared__ int s_reach[kMixMaxN], s_cl[kMixMaxN], s_cst[kMixMaxN + 1];
@@ -298,19 +302,19 @@ __global__ void __launch_bounds__(1024) k_refine_lam(int n, const double2* __res
     s_delta = fmax(2.0 * ((double)sqrtf(ns) + (double)mx * (double)sqrtf(nr)), 1e-3 * (double)mx);
   }
   __syncthreads();
-  // Pairs whose correction would not be small, |S_ij + lambda_j R_ij| > kCouple |lambda_j - lambda_i| (a pair
+  // Pairs whose correction would not be small, |S_ij + lambda_j R_ij| > couple |lambda_j - lambda_i| (a pair
   // of close eigenvalues that the potential's change has mixed), join one cluster: the Rayleigh-Ritz inside
   // the cluster resolves them exactly, where the refinement would need several steps. Pairs up to 32 columns
   // apart; reach[i] = the last column coupled to i.
   for (int i = warp; i < n; i += (int)(blockDim.x >> 5)) {
     int r = i;
     const int j = i + 1 + lane;
-    if (j < n) {
+    if (couple > 0.0 && j < n) {
       const double2 g = G[(size_t)i * n + j], sv = S[(size_t)i * n + j];
       const double lj = s_lam[j];
       const double nx = sv.x - lj * g.x, ny = sv.y - lj * g.y;  // S_ij + lambda_j R_ij with R = I - G (i != j)
       const double gap = lj - s_lam[i];
-      if (nx * nx + ny * ny > kCouple * kCouple * gap * gap) r = j;
+      if (nx * nx + ny * ny > couple * couple * gap * gap) r = j;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) r = max(r, __shfl_xor_sync(0xffffffffu, r, o));
@@ -326,8 +330,9 @@ __global__ void __launch_bounds__(1024) k_refine_lam(int n, const double2* __res
   }
   // A new cluster starts at i when lambda_i - lambda_{i-1} > delta and no coupled pair spans i (prefix reach
   // below i); cluster index = inclusive count of starts up to i (ballot within a warp, then the warps' counts
-  // in order). Without the coupled pairs when they would make a cluster longer than the 64 columns of the
-  // Rayleigh-Ritz inside it.
+  // in order). Without the coupled pairs when they would make a cluster longer than kCoupleMaxCluster
+  // columns: far from convergence most pairs are coupled, and one large cluster would turn the warm start
+  // into a Jacobi diagonalisation in FP64 (the FP32 solve is faster there).
   const int nw = (n + 31) / 32;
   for (int pass = 0; pass < 2; ++pass) {
     const bool start = tid < n && tid > 0 && s_lam[tid] - s_lam[tid - 1] > s_delta &&
@@ -347,7 +352,7 @@ __global__ void __launch_bounds__(1024) k_refine_lam(int n, const double2* __res
       }
     }
     __syncthreads();
-    if (tid < s_ncl && s_cst[tid + 1] - s_cst[tid] > 64) s_long = 1;
+    if (tid < s_ncl && s_cst[tid + 1] - s_cst[tid] > kCoupleMaxCluster) s_long = 1;
     __syncthreads();
     if (!s_long) break;
   }
@@ -742,6 +747,7 @@ static int eigh_finish_tail(Ctx* c, int n, const double2* a, double2* X, const d
 // eigenvalues, and the next step usually succeeds)
 static bool warm_verdict(Ctx* c, float emax) {
   c->eig_warm_last = emax;
+  c->eig_warm_hist = ((c->eig_warm_hist << 1) | (emax < 1e-5f ? 1u : 0u)) & 0xffu;
   if (emax < 1e-4f) {
     c->eig_warm_fails = 0;
     return true;
@@ -804,6 +810,7 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
     k_warm_perm<<<1, 1024, 0, c->stream>>>(n, a, rk, rk + n);
     PARO_LAUNCH(c, "k_warm_perm");
     const int ge = (n * n + 255) / 256;
+    const double couple = __builtin_popcount(c->eig_warm_hist) >= 4 ? kCouple : 0.0;
     // one refinement step in the form X = P (I + F) (see FProd): the products of small quantities in FP32,
     // E into T1, its largest entry into r32[0] (by k_refine_e), F <- F + E + F E
     auto refine_step = [&]() -> int {
@@ -813,7 +820,7 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
       if ((s2 = fgemm(c, n, paf, nullptr)) || (s2 = fgemm(c, n, pff, &pfaf))) return s2;
       k_fassemble<<<ge, 256, 0, c->stream>>>(n, Ap, F, AF, FF, FAF, G, S, nrm, nnrm);
       PARO_LAUNCH(c, "k_fassemble");
-      k_refine_lam<<<1, 1024, 0, c->stream>>>(n, G, S, nrm, nnrm, lam, cl, cst, ncl, r32);
+      k_refine_lam<<<1, 1024, 0, c->stream>>>(n, G, S, nrm, nnrm, lam, cl, cst, ncl, r32, couple);
       PARO_LAUNCH(c, "k_refine_lam");
       k_refine_e<<<ge, 256, 0, c->stream>>>(n, G, S, lam, cl, T1, r32);
       PARO_LAUNCH(c, "k_refine_e");
@@ -832,7 +839,7 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
     // step 1 from the permutation, without products: G = I, S = A' (kept in Ap), F = E
     k_warm_s<<<nnrm, 256, 0, c->stream>>>(n, a, rk + n, G, Ap, nrm, nnrm);
     PARO_LAUNCH(c, "k_warm_s");
-    k_refine_lam<<<1, 1024, 0, c->stream>>>(n, G, Ap, nrm, nnrm, lam, cl, cst, ncl, nullptr);
+    k_refine_lam<<<1, 1024, 0, c->stream>>>(n, G, Ap, nrm, nnrm, lam, cl, cst, ncl, nullptr, couple);
     PARO_LAUNCH(c, "k_refine_lam");
     k_refine_e<<<ge, 256, 0, c->stream>>>(n, G, Ap, lam, cl, F, nullptr);
     PARO_LAUNCH(c, "k_refine_e");
@@ -891,7 +898,7 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
     if ((st = zgemm(c, n, Af, false, X, T1, false, part))) return st;                         // T1 = A X
     if ((st = zgemm(c, n, X, true, T1, S, false, part, true, nrm + nnrm, false))) return st;  // S = X^H A X
     cudaEvent_t ev2 = prof_begin(c);
-    k_refine_lam<<<1, 1024, 0, c->stream>>>(n, G, S, nrm, nnrm, lam, cl, cst, ncl, nullptr);
+    k_refine_lam<<<1, 1024, 0, c->stream>>>(n, G, S, nrm, nnrm, lam, cl, cst, ncl, nullptr, 0.0);
     PARO_LAUNCH(c, "k_refine_lam");
     prof_end(c, "k_refine_lam", ev2);
     ev2 = prof_begin(c);

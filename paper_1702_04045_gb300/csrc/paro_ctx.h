@@ -124,6 +124,7 @@ struct Ctx {
   int eig_warm_skip = 0;   // Rayleigh-Ritz eigensolves left before the warm start is tried again
   int eig_warm_fails = 0;  // consecutive warm starts that were not accepted
   float eig_warm_last = 1.f;  // the last correction of the latest warm start (1 before the first)
+  unsigned eig_warm_hist = 0;  // the last eight warm starts, bit set when the correction ended below 1e-5
   bool fft_configured[2] = {false, false};
   // instrumentation: kernels launched, and CUDA-event pairs around named kernels while profiling
   long long launches = 0;
