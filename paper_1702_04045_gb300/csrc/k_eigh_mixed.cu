@@ -266,7 +266,8 @@ __global__ void __launch_bounds__(1024) k_refine_lam(int n, const double2* __res
                                                      const double2* __restrict__ S, const float* __restrict__ nrm,
                                                      int nnrm, double* __restrict__ lam, int* __restrict__ cl,
                                                      int* __restrict__ cst, int* __restrict__ ncl,
-                                                     float* __restrict__ emax, double couple) {
+                                                     float* __restrict__ emax, double couple,
+                                                     const float2* __restrict__ S32, const float2* __restrict__ Gm32) {
   __shared__ float red[32];
   __shared__ double s_lam[kMixMaxN];
   __shared__ int s_reach[kMixMaxN], s_cl[kMixMaxN], s_cst[kMixMaxN + 1];
@@ -309,12 +310,12 @@ __global__ void __launch_bounds__(1024) k_refine_lam(int n, const double2* __res
   for (int i = warp; i < n; i += (int)(blockDim.x >> 5)) {
     int r = i;
     const int j = i + 1 + lane;
-    if (couple > 0.0 && j < n) {
-      const double2 g = G[(size_t)i * n + j], sv = S[(size_t)i * n + j];
-      const double lj = s_lam[j];
-      const double nx = sv.x - lj * g.x, ny = sv.y - lj * g.y;  // S_ij + lambda_j R_ij with R = I - G (i != j)
-      const double gap = lj - s_lam[i];
-      if (nx * nx + ny * ny > couple * couple * gap * gap) r = j;
+    if (couple > 0.0 && j < n) {  // in FP32 (a threshold test) from the FP32 copies of S and G - I
+      const float2 g = Gm32 ? Gm32[(size_t)i * n + j] : make_float2(0.f, 0.f), sv = S32[(size_t)i * n + j];
+      const float lj = (float)s_lam[j];
+      const float nx = sv.x - lj * g.x, ny = sv.y - lj * g.y;  // S_ij + lambda_j R_ij with R = I - G (i != j)
+      const float gap = lj - (float)s_lam[i], cf = (float)couple;
+      if (nx * nx + ny * ny > cf * cf * gap * gap) r = j;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) r = max(r, __shfl_xor_sync(0xffffffffu, r, o));
@@ -371,7 +372,8 @@ __global__ void __launch_bounds__(1024) k_refine_lam(int n, const double2* __res
 // test), by one atomic maximum per CTA on the float's bits (non-negative floats order as their bits)
 __global__ void __launch_bounds__(256) k_refine_e(int n, const double2* __restrict__ G, const double2* __restrict__ S,
                                                   const double* __restrict__ lam, const int* __restrict__ cl,
-                                                  double2* __restrict__ E, float* __restrict__ emax) {
+                                                  double2* __restrict__ E, float* __restrict__ emax,
+                                                  float2* __restrict__ E32) {
   __shared__ float red[32];
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   float m = 0.f;
@@ -389,7 +391,9 @@ __global__ void __launch_bounds__(256) k_refine_e(int n, const double2* __restri
       e = make_double2((double)((float)num.x * inv), (double)((float)num.y * inv));
     }
     E[idx] = e;
-    m = (float)fmax(fabs(e.x), fabs(e.y));
+    const float2 ef = make_float2((float)e.x, (float)e.y);
+    if (E32) E32[idx] = ef;
+    m = fmaxf(fabsf(ef.x), fabsf(ef.y));
   }
   if (!emax) return;
 #pragma unroll
@@ -499,18 +503,26 @@ __global__ void __launch_bounds__(256) k_cluster_rr(int n, const double2* __rest
 }
 
 // ascending order (ties by index): w[j] = lam[perm j], V[:, j] = X[:, perm j]
-// (n <= 1024: the eigenvalues are staged in shared memory)
+// a 64-bit integer that orders as the double does (sign and magnitude bits turned into a two's complement
+// order): the sorting counts compare these on the integer pipe, where GB300's FP64 compares would take the
+// slow FP64 pipe
+__device__ __forceinline__ long long order_key(double d) {
+  const long long b = __double_as_longlong(d);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+
+// (n <= 1024: the eigenvalues' order keys are staged in shared memory)
 __global__ void k_eig_sort(int n, const double* __restrict__ lam, const double2* __restrict__ X, double* __restrict__ w,
                            double2* __restrict__ V, int* __restrict__ perm) {
-  __shared__ double s_l[1024];
-  for (int j = threadIdx.x; j < n; j += blockDim.x) s_l[j] = lam[j];
+  __shared__ long long s_l[1024];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) s_l[j] = order_key(lam[j]);
   __syncthreads();
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid < n) {
-    const double a = s_l[tid];
+    const long long a = s_l[tid];
     int r = 0;
     for (int j = 0; j < n; ++j) {
-      const double b = s_l[j];
+      const long long b = s_l[j];
       r += (b < a) || (b == a && j < tid);
     }
     perm[r] = tid;
@@ -561,15 +573,15 @@ static int zgemm(Ctx* c, int n, const double2* A, bool ah, const double2* B, dou
 // Warm start of the refinement: X0 = the permutation that sorts the diagonal of A, X0[i][rank(i)] = 1 with
 // rank(i) = #{j : a_jj < a_ii, or a_jj = a_ii and j < i}; at_rank is its inverse (one CTA, n <= 1024)
 __global__ void k_warm_perm(int n, const double2* __restrict__ A, int* __restrict__ rank, int* __restrict__ at_rank) {
-  __shared__ double s_d[1024];
+  __shared__ long long s_d[1024];
   const int i = threadIdx.x;
-  if (i < n) s_d[i] = A[(size_t)i * n + i].x;
+  if (i < n) s_d[i] = order_key(A[(size_t)i * n + i].x);
   __syncthreads();
   if (i >= n) return;
-  const double d = s_d[i];
+  const long long d = s_d[i];
   int r = 0;
   for (int j = 0; j < n; ++j) {
-    const double e = s_d[j];
+    const long long e = s_d[j];
     r += (e < d || (e == d && j < i)) ? 1 : 0;
   }
   rank[i] = r;
@@ -577,11 +589,11 @@ __global__ void k_warm_perm(int n, const double2* __restrict__ A, int* __restric
 }
 
 // The first refinement step from X0 needs no products: G = X0^H X0 = I and S = X0^H A X0 = A with rows and
-// columns in rank order (A given by its lower triangle). nrm as k_zreduce leaves it for the pair (G, S): per CTA of 256 entries, zero for
+// columns in rank order (A given by its lower triangle); N32: the off-diagonal part of S in FP32. nrm as k_zreduce leaves it for the pair (G, S): per CTA of 256 entries, zero for
 // G and the off-diagonal sum of |S_ij|^2 for S.
 __global__ void __launch_bounds__(256) k_warm_s(int n, const double2* __restrict__ A, const int* __restrict__ at_rank,
                                                 double2* __restrict__ G, double2* __restrict__ S,
-                                                float* __restrict__ nrm, int nnrm) {
+                                                float* __restrict__ nrm, int nnrm, float2* __restrict__ N32) {
   __shared__ float red[32];
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   float e = 0.f;
@@ -590,10 +602,9 @@ __global__ void __launch_bounds__(256) k_warm_s(int n, const double2* __restrict
     const double2 v = i >= j ? A[(size_t)i * n + j] : cconj(A[(size_t)j * n + i]);  // A: its lower triangle
     S[idx] = v;
     G[idx] = make_double2(r == q ? 1.0 : 0.0, 0.0);
-    if (r != q) {
-      const float x = (float)v.x, y = (float)v.y;
-      e = x * x + y * y;
-    }
+    const float x = (float)v.x, y = (float)v.y;
+    N32[idx] = r != q ? make_float2(x, y) : make_float2(0.f, 0.f);  // N, the off-diagonal part, in FP32
+    if (r != q) e = x * x + y * y;
   }
   e = block_sumf(e, red);
   if (threadIdx.x == 0) {
@@ -624,9 +635,12 @@ __global__ void k_warm_x1(int n, const int* __restrict__ rank, const double2* __
 // only the exact parts (I, D F, A') are added in FP64. (GB300's FP64 rate is 1/64 of its FP32 rate.)
 // ------------------------------------------------------------------------------------------------
 struct FProd {
-  const double2* A;  // n x n, row-major
+  const float2* A32;  // the operands of the FP32 product (n x n, row-major; FP32 copies)
+  const float2* B32;
+  const double2* A;   // the same in FP64, for the epilogue terms (may be null when no term reads them)
   const double2* B;
   double2* C;
+  float2* C32;  // (may be null) an FP32 copy of the result, for the next product
   int ah;       // op(A) = A^H
   int diag;     // leave the k = i term out of the FP32 sum and add A_ii B_ij in FP64 (A' F as D F + N F)
   int add_a;    // add op(A)_ij to the result
@@ -635,8 +649,10 @@ struct FProd {
 };
 
 // C = op(A) B (+ the epilogue terms) for one or two products (blockIdx.z), 16 x 16 outputs per CTA (n <=
-// kMixMaxN): the CTA's 16 rows of op(A) and 16 columns of B are staged whole in shared memory (one round of
-// loads), then FP32 products with the partial sum of every 16 terms carried in FP64
+// kMixMaxN): the CTA's 16 rows of op(A) and 16 columns of B are staged whole in shared memory from the
+// operands' FP32 copies (one round of loads, no conversions), then FP32 products, the partial sum of every
+// 16 terms added into an FP32 two-sum pair; FP64 only in the epilogue (GB300's FP64 pipe, conversions
+// included, runs at 1/64 of the FP32 rate)
 __global__ void __launch_bounds__(256) k_fgemm16(int n, FProd p0, FProd p1) {
   __shared__ float2 As[16][kMixMaxN + 1], Bs[kMixMaxN][17];
   const FProd& p = blockIdx.z ? p1 : p0;
@@ -656,22 +672,17 @@ __global__ void __launch_bounds__(256) k_fgemm16(int n, FProd p0, FProd p1) {
     const int ia = i0 + r;
     float2 av = make_float2(0.f, 0.f);
     if (ia < n && k < n && !(p.diag && ia == k)) {
-      const double2 v = p.ah ? cconj(p.A[(size_t)k * n + ia]) : p.A[(size_t)ia * n + k];
-      av = make_float2((float)v.x, (float)v.y);
+      av = p.ah ? p.A32[(size_t)k * n + ia] : p.A32[(size_t)ia * n + k];
+      if (p.ah) av.y = -av.y;
     }
     As[r][k] = av;
   }
   for (int idx = threadIdx.x; idx < 16 * n16; idx += blockDim.x) {
     const int k = idx >> 4, cc = idx & 15, jb = j0 + cc;
-    float2 bv = make_float2(0.f, 0.f);
-    if (k < n && jb < n) {
-      const double2 v = p.B[(size_t)k * n + jb];
-      bv = make_float2((float)v.x, (float)v.y);
-    }
-    Bs[k][cc] = bv;
+    Bs[k][cc] = (k < n && jb < n) ? p.B32[(size_t)k * n + jb] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  double2 acc = make_double2(0.0, 0.0);
+  float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
   for (int kk = 0; kk < n16; kk += 16) {
     float sx = 0.f, sy = 0.f;
 #pragma unroll
@@ -680,10 +691,11 @@ __global__ void __launch_bounds__(256) k_fgemm16(int n, FProd p0, FProd p1) {
       sx = fmaf(x.x, y.x, fmaf(-x.y, y.y, sx));
       sy = fmaf(x.x, y.y, fmaf(x.y, y.x, sy));
     }
-    acc.x += (double)sx;
-    acc.y += (double)sy;
+    two_sum_acc(hx, lx, sx);
+    two_sum_acc(hy, ly, sy);
   }
   if (i >= n || j >= n) return;
+  double2 acc = make_double2((double)hx + (double)lx, (double)hy + (double)ly);
   if (p.diag) {  // A_ii B_ij in FP64 (op(A)_ii = conj(A_ii) when ah)
     double2 d = p.A[(size_t)i * n + i];
     if (p.ah) d = cconj(d);
@@ -692,6 +704,7 @@ __global__ void __launch_bounds__(256) k_fgemm16(int n, FProd p0, FProd p1) {
   if (p.add_a) acc = cadd(acc, p.ah ? cconj(p.A[(size_t)j * n + i]) : p.A[(size_t)i * n + j]);
   if (p.add_ab) acc = cadd(acc, cadd(p.A[(size_t)i * n + j], p.B[(size_t)i * n + j]));
   p.C[(size_t)i * n + j] = acc;
+  if (p.C32) p.C32[(size_t)i * n + j] = make_float2((float)acc.x, (float)acc.y);
   if (p.xp) {
     double2 x = p.B[(size_t)i * n + j];
     if (i == j) x.x += 1.0;
@@ -699,12 +712,14 @@ __global__ void __launch_bounds__(256) k_fgemm16(int n, FProd p0, FProd p1) {
   }
 }
 
-// G = I + F + F^H + FF and S = A' + AF + AF^H + FAF, with the per-CTA sums of k_zreduce for the cluster
-// threshold: nrm[b] = sum |G_ij - d_ij|^2, nrm[nnrm + b] = sum over i != j of |S_ij|^2
+// G = I + F + F^H + FF and S = A' + AF + AF^H + FAF (and FP32 copies of G - I and S for the coupling test),
+// with the per-CTA sums of k_zreduce for the cluster threshold: nrm[b] = sum |G_ij - d_ij|^2,
+// nrm[nnrm + b] = sum over i != j of |S_ij|^2
 __global__ void __launch_bounds__(256) k_fassemble(int n, const double2* __restrict__ Ap, const double2* __restrict__ F,
                                                    const double2* __restrict__ AF, const double2* __restrict__ FF,
                                                    const double2* __restrict__ FAF, double2* __restrict__ G,
-                                                   double2* __restrict__ S, float* __restrict__ nrm, int nnrm) {
+                                                   double2* __restrict__ S, float* __restrict__ nrm, int nnrm,
+                                                   float2* __restrict__ S32, float2* __restrict__ Gm32) {
   __shared__ float red[32];
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   float eg = 0.f, es = 0.f;
@@ -715,8 +730,11 @@ __global__ void __launch_bounds__(256) k_fassemble(int n, const double2* __restr
     G[idx] = make_double2(r.x + (i == j ? 1.0 : 0.0), r.y);
     const double2 s = cadd(cadd(Ap[idx], cadd(AF[idx], cconj(AF[t]))), FAF[idx]);
     S[idx] = s;
-    eg = (float)(r.x * r.x + r.y * r.y);
-    if (i != j) es = (float)(s.x * s.x + s.y * s.y);
+    const float2 rf = make_float2((float)r.x, (float)r.y), sf = make_float2((float)s.x, (float)s.y);
+    Gm32[idx] = rf;
+    S32[idx] = sf;
+    eg = rf.x * rf.x + rf.y * rf.y;
+    if (i != j) es = sf.x * sf.x + sf.y * sf.y;
   }
   eg = block_sumf(eg, red);
   __syncthreads();
@@ -806,7 +824,11 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
     double2* AF = static_cast<double2*>(ws_get(c, "em_AF", nn * sizeof(double2)));
     double2* FF = static_cast<double2*>(ws_get(c, "em_FF", nn * sizeof(double2)));
     double2* FAF = static_cast<double2*>(ws_get(c, "em_FAF", nn * sizeof(double2)));
-    if (!rk || !Ap || !F || !Fn || !AF || !FF || !FAF) return PARO_ERR_CUDA;
+    // FP32 copies: N (off-diagonal part of A'), F and the next F, A'F, E, S and G - I
+    float2* f32 = static_cast<float2*>(ws_get(c, "em_f32", 7 * nn * sizeof(float2)));
+    if (!rk || !Ap || !F || !Fn || !AF || !FF || !FAF || !f32) return PARO_ERR_CUDA;
+    float2 *N32 = f32, *F32 = f32 + nn, *Fn32 = f32 + 2 * nn, *AF32 = f32 + 3 * nn, *E32 = f32 + 4 * nn,
+           *S32 = f32 + 5 * nn, *Gm32 = f32 + 6 * nn;
     k_warm_perm<<<1, 1024, 0, c->stream>>>(n, a, rk, rk + n);
     PARO_LAUNCH(c, "k_warm_perm");
     const int ge = (n * n + 255) / 256;
@@ -815,18 +837,20 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
     // E into T1, its largest entry into r32[0] (by k_refine_e), F <- F + E + F E
     auto refine_step = [&]() -> int {
       int s2;
-      const FProd paf{Ap, F, AF, 0, 1, 0, 0, nullptr};  // A'F = D F + N F
-      const FProd pff{F, F, FF, 1, 0, 0, 0, nullptr}, pfaf{F, AF, FAF, 1, 0, 0, 0, nullptr};
+      const FProd paf{N32, F32, Ap, F, AF, AF32, 0, 1, 0, 0, nullptr};  // A'F = D F + N F
+      const FProd pff{F32, F32, nullptr, nullptr, FF, nullptr, 1, 0, 0, 0, nullptr};
+      const FProd pfaf{F32, AF32, nullptr, nullptr, FAF, nullptr, 1, 0, 0, 0, nullptr};
       if ((s2 = fgemm(c, n, paf, nullptr)) || (s2 = fgemm(c, n, pff, &pfaf))) return s2;
-      k_fassemble<<<ge, 256, 0, c->stream>>>(n, Ap, F, AF, FF, FAF, G, S, nrm, nnrm);
+      k_fassemble<<<ge, 256, 0, c->stream>>>(n, Ap, F, AF, FF, FAF, G, S, nrm, nnrm, S32, Gm32);
       PARO_LAUNCH(c, "k_fassemble");
-      k_refine_lam<<<1, 1024, 0, c->stream>>>(n, G, S, nrm, nnrm, lam, cl, cst, ncl, r32, couple);
+      k_refine_lam<<<1, 1024, 0, c->stream>>>(n, G, S, nrm, nnrm, lam, cl, cst, ncl, r32, couple, S32, Gm32);
       PARO_LAUNCH(c, "k_refine_lam");
-      k_refine_e<<<ge, 256, 0, c->stream>>>(n, G, S, lam, cl, T1, r32);
+      k_refine_e<<<ge, 256, 0, c->stream>>>(n, G, S, lam, cl, T1, r32, E32);
       PARO_LAUNCH(c, "k_refine_e");
-      const FProd pup{F, T1, Fn, 0, 0, 0, 1, nullptr};  // F + E + F E
+      const FProd pup{F32, E32, F, T1, Fn, Fn32, 0, 0, 0, 1, nullptr};  // F + E + F E
       if ((s2 = fgemm(c, n, pup, nullptr))) return s2;
       std::swap(F, Fn);
+      std::swap(F32, Fn32);
       return PARO_OK;
     };
     auto read_emax = [&](float* e) -> int {
@@ -837,11 +861,11 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
       return PARO_OK;
     };
     // step 1 from the permutation, without products: G = I, S = A' (kept in Ap), F = E
-    k_warm_s<<<nnrm, 256, 0, c->stream>>>(n, a, rk + n, G, Ap, nrm, nnrm);
+    k_warm_s<<<nnrm, 256, 0, c->stream>>>(n, a, rk + n, G, Ap, nrm, nnrm, N32);
     PARO_LAUNCH(c, "k_warm_s");
-    k_refine_lam<<<1, 1024, 0, c->stream>>>(n, G, Ap, nrm, nnrm, lam, cl, cst, ncl, nullptr, couple);
+    k_refine_lam<<<1, 1024, 0, c->stream>>>(n, G, Ap, nrm, nnrm, lam, cl, cst, ncl, nullptr, couple, N32, nullptr);
     PARO_LAUNCH(c, "k_refine_lam");
-    k_refine_e<<<ge, 256, 0, c->stream>>>(n, G, Ap, lam, cl, F, nullptr);
+    k_refine_e<<<ge, 256, 0, c->stream>>>(n, G, Ap, lam, cl, F, nullptr, F32);
     PARO_LAUNCH(c, "k_refine_e");
     float emax = 1.f;
     if ((st = refine_step())) return st;
@@ -868,7 +892,7 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
       // finish in the same form: X' = I + F, T1 = A' X' = A' + A'F, S = X'^H A' X' inside the clusters,
       // Rayleigh-Ritz there on the columns of X', then X = P X'
       cudaEvent_t evf = prof_begin(c);
-      const FProd pt{Ap, F, T1, 0, 1, 1, 0, X};
+      const FProd pt{N32, F32, Ap, F, T1, nullptr, 0, 1, 1, 0, X};
       if ((st = fgemm(c, n, pt, nullptr))) return st;
       k_blockdiag_xhat<<<(int)((nn + 7) / 8), 256, 0, c->stream>>>(n, X, T1, cl, S);
       PARO_LAUNCH(c, "k_blockdiag_xhat");
@@ -898,11 +922,12 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
     if ((st = zgemm(c, n, Af, false, X, T1, false, part))) return st;                         // T1 = A X
     if ((st = zgemm(c, n, X, true, T1, S, false, part, true, nrm + nnrm, false))) return st;  // S = X^H A X
     cudaEvent_t ev2 = prof_begin(c);
-    k_refine_lam<<<1, 1024, 0, c->stream>>>(n, G, S, nrm, nnrm, lam, cl, cst, ncl, nullptr, 0.0);
+    k_refine_lam<<<1, 1024, 0, c->stream>>>(n, G, S, nrm, nnrm, lam, cl, cst, ncl, nullptr, 0.0, nullptr,
+                                            nullptr);
     PARO_LAUNCH(c, "k_refine_lam");
     prof_end(c, "k_refine_lam", ev2);
     ev2 = prof_begin(c);
-    k_refine_e<<<(n * n + 255) / 256, 256, 0, c->stream>>>(n, G, S, lam, cl, T1, nullptr);  // T1 = E
+    k_refine_e<<<(n * n + 255) / 256, 256, 0, c->stream>>>(n, G, S, lam, cl, T1, nullptr, nullptr);  // T1 = E
     PARO_LAUNCH(c, "k_refine_e");
     prof_end(c, "k_refine_e", ev2);
     if ((st = zgemm(c, n, X, false, T1, X, true, part))) return st;    // X += X E
