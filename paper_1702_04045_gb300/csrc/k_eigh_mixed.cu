@@ -589,8 +589,9 @@ __global__ void k_warm_perm(int n, const double2* __restrict__ A, int* __restric
 }
 
 // The first refinement step from X0 needs no products: G = X0^H X0 = I and S = X0^H A X0 = A with rows and
-// columns in rank order (A given by its lower triangle); N32: the off-diagonal part of S in FP32. nrm as k_zreduce leaves it for the pair (G, S): per CTA of 256 entries, zero for
-// G and the off-diagonal sum of |S_ij|^2 for S.
+// columns in rank order (A given by its lower triangle); N32: the off-diagonal part of S in FP32. nrm as
+// k_zreduce leaves it for the pair (G, S): per CTA of 256 entries, zero for G and the off-diagonal sum of
+// |S_ij|^2 for S.
 __global__ void __launch_bounds__(256) k_warm_s(int n, const double2* __restrict__ A, const int* __restrict__ at_rank,
                                                 double2* __restrict__ G, double2* __restrict__ S,
                                                 float* __restrict__ nrm, int nnrm, float2* __restrict__ N32) {
