@@ -118,6 +118,8 @@ static FftPlan make_plan(int n) {
   return p;
 }
 
+FftPlan fft_plan(int n) { return make_plan(n); }
+
 // Miller indices with |k+G|^2/2 <= ecut, lexicographic (n1, n2, n3); kinetic energies.
 static void sphere(const Ctx* c, const double kf[3], double ecut, std::vector<int>& mil, std::vector<double>& kin) {
   const double* B = c->bmat;
@@ -1009,6 +1011,7 @@ static int set_ecut(Ctx* c, double ecut_new) {
   c->d_vplane32 = nullptr;
   c->pulay_n = c->pulay_head = 0;
   c->have_inv_g2 = false;
+  c->have_tw_half = false;
   c->have_veff = false;
   c->ecut = ecut_new;
   c->scf_iter = c->scf_small = 0;

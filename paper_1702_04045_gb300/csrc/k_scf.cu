@@ -589,8 +589,99 @@ static const double* inv_g2_table(Ctx* c);
 // when potential, V_H(r) in z (real parts). Launches only: the energy alone needs only the forward FFT
 // and no host synchronisation until the caller reads the partials.
 static int hartree_blocks(const Ctx* c) { return (c->ngrid + 255) / 256; }
+// ------------------------------------------------------------------------------------------------
+// Hartree energy of the real density from one half-length transform: the even and odd z planes packed as
+// the real and imaginary parts of one complex array on the (N1, N2, M = N3/2) grid, transformed, then
+// unpacked with k = (kx, ky, kz), kz < M, and -k taken modulo (N1, N2, M):
+//   A(k) = (Z(k) + conj Z(-k)) / 2,  B(k) = (Z(k) - conj Z(-k)) / (2i)   (the transforms of the even and odd
+//   planes), rho(kx, ky, kz) = A(k) + W^kz B(k), rho(kx, ky, kz + M) = A(k) - W^kz B(k), W = exp(-2 pi i / N3).
+// The same coefficients as the full complex transform, for half its work on GB300's slow FP64 pipe.
+// ------------------------------------------------------------------------------------------------
+__global__ void k_pack_even_odd(int n, int M, const double* __restrict__ rho, double2* __restrict__ z) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over nxy * M
+  if (i >= n) return;
+  const int xy = i / M, m = i - xy * M;
+  const double* r = rho + (size_t)xy * 2 * M + 2 * m;
+  z[i] = make_double2(r[0], r[1]);
+}
+
+// per-CTA partial sums of |rho(G)|^2 / |G|^2 over both G of each half-grid point (the layout of
+// k_hartree_tab's partials: one per 256 full-grid points, the CTAs beyond the half grid write zero)
+__global__ void k_hartree_half(int N1, int N2, int M, const double* __restrict__ ig2, const double2* __restrict__ z,
+                               const double2* __restrict__ tw3, double* __restrict__ part) {
+  __shared__ double red[32];
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nh = N1 * N2 * M, N3 = 2 * M;
+  double e = 0.0;
+  if (idx < nh) {
+    const int kx = idx / (N2 * M), rem = idx - kx * (N2 * M), ky = rem / M, km = rem - ky * M;
+    const int nkx = kx ? N1 - kx : 0, nky = ky ? N2 - ky : 0, nkm = km ? M - km : 0;
+    const double2 zk = z[idx], zn = cconj(z[((size_t)nkx * N2 + nky) * M + nkm]);
+    const double2 a = cscale(cadd(zk, zn), 0.5);
+    const double2 d = csub(zk, zn);
+    const double2 b = make_double2(0.5 * d.y, -0.5 * d.x);  // d / (2i)
+    const double2 wb = cmul(tw3[km], b);                      // tw3[j] = exp(-2 pi i j / N3)
+    const double inv = 1.0 / ((double)N1 * N2 * N3);
+    const double2 r1 = cscale(cadd(a, wb), inv), r2 = cscale(csub(a, wb), inv);
+    const size_t base = ((size_t)kx * N2 + ky) * N3 + km;
+    e = ig2[base] * (r1.x * r1.x + r1.y * r1.y) + ig2[base + M] * (r2.x * r2.x + r2.y * r2.y);
+  }
+  e = block_sum(e, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = e;
+}
+
+// the N3/2-point FP64 twiddle table (built once per grid)
+static const double2* half_twiddles(Ctx* c) {
+  const int M = c->N[2] / 2;
+  double2* t64 = static_cast<double2*>(ws_get(c, "tw64_half", (size_t)M * sizeof(double2)));
+  float2* t32 = static_cast<float2*>(ws_get(c, "tw32_half", (size_t)M * sizeof(float2)));
+  if (!t64 || !t32) return nullptr;
+  if (!c->have_tw_half) {
+    k_twiddle<<<(M + 127) / 128, 128, 0, c->stream>>>(M, t64, t32);
+    if (cudaGetLastError() != cudaSuccess) return nullptr;
+    c->have_tw_half = true;
+  }
+  return t64;
+}
+
+// forward transform (FP64, unnormalised) of the (N1, N2, N3/2) grid in z
+static int fft3d_half_fwd(Ctx* c, double2* z) {
+  const int N1 = c->N[0], N2 = c->N[1], M = c->N[2] / 2;
+  const double2* twh = half_twiddles(c);
+  if (!twh) return fail(c, PARO_ERR_CUDA, "hartree: half-length twiddles");
+  const FftPlan ph = fft_plan(M);
+  const size_t eb = sizeof(double2);
+  const size_t smz = (size_t)(M + kLB * (M + 1)) * eb;
+  const size_t smy = (size_t)(N2 + kLB * (N2 + 1)) * eb;
+  const size_t smx = (size_t)(N1 + kLB * (N1 + 1)) * eb;
+  PARO_CU(c, cudaFuncSetAttribute(k_fft_z<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+  PARO_CU(c, cudaFuncSetAttribute(k_fft_strided<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  100 * 1024));
+  cudaEvent_t ev = prof_begin(c);
+  k_fft_z<double, false><<<(N1 * N2 + kLB - 1) / kLB, 256, smz, c->stream>>>(z, N1 * N2, ph, twh);
+  k_fft_strided<double, false><<<dim3((M + kLB - 1) / kLB, N1), 256, smy, c->stream>>>(z, c->plan[1], M, N2 * M, M,
+                                                                                    c->d_tw64[1]);
+  k_fft_strided<double, false><<<dim3((M + kLB - 1) / kLB, N2), 256, smx, c->stream>>>(z, c->plan[0], N2 * M, M, M,
+                                                                                    c->d_tw64[0]);
+  PARO_LAUNCH(c, "fft3d_half");
+  prof_end(c, "fft3d<f64>", ev);
+  return PARO_OK;
+}
+
 static int hartree_g(Ctx* c, const double* rho_dev, double2* z, double* part, bool potential) {
   const int nblk = hartree_blocks(c);
+  if (!potential && c->N[2] % 2 == 0) {  // the energy alone: the half-length transform of the real density
+    const int M = c->N[2] / 2, nh = c->N[0] * c->N[1] * M;
+    k_pack_even_odd<<<(nh + 255) / 256, 256, 0, c->stream>>>(nh, M, rho_dev, z);
+    PARO_LAUNCH(c, "k_pack_even_odd");
+    int st = fft3d_half_fwd(c, z);
+    if (st) return st;
+    const double* ig2 = inv_g2_table(c);
+    if (!ig2) return fail(c, PARO_ERR_CUDA, "hartree: 1/|G|^2 table");
+    k_hartree_half<<<nblk, 256, 0, c->stream>>>(c->N[0], c->N[1], M, ig2, z, c->d_tw64[2], part);
+    PARO_LAUNCH(c, "k_hartree_half");
+    return PARO_OK;
+  }
   k_to_complex<<<nblk, 256, 0, c->stream>>>(c->ngrid, rho_dev, z);
   PARO_LAUNCH(c, "k_to_complex");
   int st = fft3d<double>(c, z, false);

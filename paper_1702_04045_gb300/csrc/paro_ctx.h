@@ -156,6 +156,7 @@ struct Ctx {
   } chol_shape;
   std::vector<std::string> chol_pending;  // pinned flags of deferred Cholesky breakdown checks
   bool have_inv_g2 = false;  // the 1/|G|^2 table of the Hartree solve is in the "inv_g2" workspace
+  bool have_tw_half = false;  // the N3/2-point FP64 twiddles of the Hartree energy are in "tw64_half"
 };
 
 // brings the FP64 orbitals and H psi of a mixed-precision basis up to date with the FP32 ones (api.cu)
@@ -349,6 +350,8 @@ int fft3d(Ctx* c, cplx<T>* data, bool inverse);  // in place, unnormalised, C or
 double ewald(const Ctx* c);
 
 int build_twiddles(Ctx* c);
+// radix plan (2, 3, 4, 8) of an FFT of length n (n = 2^a 3^b)
+FftPlan fft_plan(int n);
 // pass 1 of H psi only (z-inverse FFT of the sticks), FP64, for the density
 template <typename T>
 int sticks_inverse(Ctx* c, int ik, int nb, const cplx<T>* psi, cplx<T>* S);
