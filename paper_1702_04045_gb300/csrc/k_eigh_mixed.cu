@@ -764,7 +764,7 @@ static int eigh_finish_tail(Ctx* c, int n, const double2* a, double2* X, const d
 // square); after a failure the FP32 solve runs for the next 1, 2, 4, then 8 calls after consecutive failures
 // (far from convergence the warm start keeps failing; near it a failure is a passing pair of close
 // eigenvalues, and the next step usually succeeds)
-static bool warm_verdict(Ctx* c, float emax) {
+static bool warm_outcome(Ctx* c, float emax) {
   c->eig_warm_last = emax;
   c->eig_warm_hist = ((c->eig_warm_hist << 1) | (emax < 1e-5f ? 1u : 0u)) & 0xffu;
   if (emax < 1e-4f) {
@@ -776,7 +776,7 @@ static bool warm_verdict(Ctx* c, float emax) {
   return false;
 }
 
-bool eigh_mixed_accept(Ctx* c, float emax) { return warm_verdict(c, emax); }
+bool eigh_mixed_accept(Ctx* c, float emax) { return warm_outcome(c, emax); }
 
 int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refine_steps, bool warm,
                const int** info_out, const float** emax_out) {
@@ -889,7 +889,7 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
     if (emax >= 1e-4f && emax < 1e-1f && ((st = refine_step()) || (st = read_emax(&emax)))) return st;
     if (emax >= 1e-4f && emax < 1e-2f && ((st = refine_step()) || (st = read_emax(&emax)))) return st;
     prof_end(c, "eigh_warm", evw);
-    if (defer || warm_verdict(c, emax)) {
+    if (defer || warm_outcome(c, emax)) {
       // finish in the same form: X' = I + F, T1 = A' X' = A' + A'F, S = X'^H A' X' inside the clusters,
       // Rayleigh-Ritz there on the columns of X', then X = P X'
       cudaEvent_t evf = prof_begin(c);
@@ -900,7 +900,7 @@ int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refin
       prof_end(c, "eigh_finish", evf);
       return eigh_finish_tail(c, n, a, X, S, cst, ncl, lam, w, v, perm, info, info_out, rk);
     }
-    // not close enough: the FP32 solve (warm_verdict has set the calls to skip)
+    // not close enough: the FP32 solve (warm_outcome has set the calls to skip)
   }
   // the full Hermitian matrix (the input holds its lower triangle)
   k_herm_full_mixed<<<(int)((nn + 255) / 256), 256, 0, c->stream>>>(n, a, Af);

@@ -290,7 +290,7 @@ int eigh(Ctx* c, int n, const double2* a, double* w, double2* v);
 // *emax_out is left null when the solve decided by itself
 int eigh_mixed(Ctx* c, int n, const double2* a, double* w, double2* v, int refine_steps, bool warm = false,
                const int** info_out = nullptr, const float** emax_out = nullptr);
-// a deferred warm start's verdict from its last correction: true when it is accepted (else the caller solves
+// the outcome of a deferred warm start from its last correction: true when it is accepted (else the caller solves
 // again with warm = false)
 bool eigh_mixed_accept(Ctx* c, float emax);
 // the end of a mixed solve from its cluster check: the FP64 solver when a cluster could not be resolved
